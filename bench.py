@@ -1,0 +1,332 @@
+"""Benchmark of the GB300 atlas packer.
+
+One step = one complete pack of one atlas through the whole hot path (prep,
+sort, envelope raster, compaction, row loop at every evaluated candidate
+scale, selection) on the synthetic stand-in for the 2,000-chart workload:
+2,000 star-shaped charts (6-64 vertices, log-normal areas sigma 1.0, aspect
+1:1-1:8) into a 2048 x 2048 atlas, 1-px gutters, 64 candidate scales.
+
+Prints one JSON line.  Device-timed value: inputs resident in HBM, L2 flushed
+(256 MiB write) before every step, each pack bracketed by CUDA events on the
+packing stream.  e2e: the same pack through the host-buffer C-ABI entry
+point (tabi_pack) from pinned host memory, host<->device copies inside the
+timed region.  --impl reference times the CPU oracle on the same workload.
+
+Multi-GPU: atlases are independent, so every rank packs its own copy (weak
+scaling, no collective on the data path); value = packs of all ranks / max
+rank time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "stars2k: 2000 star charts (6-64 verts, lognormal areas s=1.0, aspect 1:1-1:8), atlas 2048x2048"
+METRIC = "packs/sec (and p50/p99 ms per atlas), plain single-atlas GPU packer"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fanout", type=int, default=64)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self._stop = threading.Event()
+        self._t = threading.Thread(target=self._run, daemon=True)
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                                     timeout=5).stdout.strip()
+                if out:
+                    self.rows.append([x.strip() for x in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if len(r) > 3 + i and "Active" in r[3 + i]
+                          and "Not" not in r[3 + i]})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def cpu_baseline(cs, budget_s: float = 15.0):
+    """The oracle as it stands (single-threaded C, all 64 candidates walked
+    from the top down until the first success), on the same workload."""
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    packs = 0
+    while True:
+        r = oracle.pack(cs)
+        assert r.status == 0
+        packs += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": packs / dt, "unit": "packs/s", "cores": 1, "kind": "oracle",
+            "sample": f"{packs} full packs of the timed workload ({dt:.1f} s, one host core)"}
+
+
+def algorithmic_bytes(ctx, cs, tabi, n_eval_scales):
+    """Algorithmic HBM bytes of one pack, per stage: each
+    stage's unavoidable reads of its inputs and writes of its outputs."""
+    n = cs.n
+    out = {}
+    env_cols = env_rows = 0
+    placed = 0
+    for j in range(64):
+        hdr, _ = ctx.scale_result(j, n)
+        if not hdr[6]:
+            continue
+        raw = ctx._inspect(tabi.INSPECT_ENV, j)
+        meta = raw[:16 * n].view(np.int32).reshape(n, 4)
+        env_cols += int(meta[:, 0].sum())
+        env_rows += int(meta[:, 1].sum())
+        placed += int(hdr[5])
+    out["prep"] = 8 * cs.nv + 4 * (n + 1) + 432 * n + 208 * n
+    out["raster"] = 208 * n * n_eval_scales + 4 * (env_cols + env_rows) + 16 * n * n_eval_scales
+    out["hcompact"] = 4 * env_rows + 16 * n * n_eval_scales + 5 * n * n_eval_scales
+    # row loop: column envelopes read once, per-chart meta/distance/flags
+    # read, placements written
+    out["rowloop"] = 4 * env_cols + (16 + 4 + 1) * n * n_eval_scales + 16 * placed
+    return out
+
+
+def run_ours(args, rank, world, local):
+    import torch
+
+    import synth
+    from paper_2602_07782_gb300 import tabi
+
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+    cs = synth.stars2k()
+    params = tabi.params_default(scale_fanout=args.fanout)
+    ctx = tabi.Context(arena_bytes=tabi.arena_bytes(cs) + (256 << 20), device=local)
+    stream = torch.cuda.Stream(device=dev)
+    offs_d = torch.from_numpy(cs.offsets.view(np.int32).copy()).to(dev)
+    verts_d = torch.from_numpy(cs.verts.copy()).to(dev)
+    out_d = torch.zeros(12 * cs.n, dtype=torch.uint8, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def one(timed_events=None):
+        flush.fill_(1)  # evict L2 (129 MB) before the step
+        with torch.cuda.stream(stream):
+            if timed_events:
+                timed_events[0].record(stream)
+            st, k = ctx.pack_device(cs.n, cs.nv, cs.atlas_w, cs.atlas_h, offs_d, verts_d, out_d, params,
+                                    stream=stream)
+            if timed_events:
+                timed_events[1].record(stream)
+        assert st == 0, ctx.last_error()
+        return k
+
+    for _ in range(args.warmup):
+        k = one()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+
+    # timed region: K packs, per-pack events; per-stage events inside the library
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    ctx.stage_times(True)
+    gpu_id = local
+    if "CUDA_VISIBLE_DEVICES" in os.environ:
+        try:
+            gpu_id = int(os.environ["CUDA_VISIBLE_DEVICES"].split(",")[local])
+        except ValueError:
+            pass
+    torch.cuda.synchronize()
+    with ClockSampler(gpu_id) as clk:
+        t_wall = time.perf_counter()
+        for i in range(args.steps):
+            one(evs[i])
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall
+    stage_ms, stage_launches, npacks = ctx.stage_times(False)
+    per = np.array([a.elapsed_time(b) for a, b in evs])
+    total_ms = float(per.sum())
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+        torch.distributed.barrier()
+
+    # end to end through tabi_pack (host buffers, pinned), H2D + D2H inside
+    offs_h = torch.from_numpy(cs.offsets.view(np.int32).copy()).pin_memory()
+    verts_h = torch.from_numpy(cs.verts.copy()).pin_memory()
+    out_h = torch.zeros(12 * cs.n, dtype=torch.uint8).pin_memory()
+    e2e_times = []
+    for i in range(args.warmup + args.steps):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, k2 = ctx.pack_host_ptrs(cs.n, cs.nv, cs.atlas_w, cs.atlas_h, offs_h.data_ptr(), verts_h.data_ptr(),
+                                    out_h.data_ptr(), params, stream=stream)
+        dt = time.perf_counter() - t0
+        assert st == 0 and k2 == k
+        if i >= args.warmup:
+            e2e_times.append(dt)
+    e2e_s = float(np.sum(e2e_times))
+
+    # the evaluated candidates and algorithmic bytes of one pack (inspect the last)
+    n_eval = sum(int(ctx.scale_result(j, cs.n)[0][6]) for j in range(64))
+    alg = algorithmic_bytes(ctx, cs, tabi, n_eval)
+    stage_avg = {s: (stage_ms[s] / stage_launches[s] if stage_launches[s] else 0.0) for s in stage_ms}
+    kernels = {s: stage_ms[s] for s in ("prep", "sort", "layout", "raster", "hcompact", "rowloop", "select")}
+    dom = max(kernels, key=kernels.get)
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except OSError:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    dom_ms = stage_avg[dom]
+    dom_bytes = alg.get(dom, 0) / max(1, stage_launches[dom] // max(1, npacks))
+    achieved = dom_bytes / (dom_ms * 1e-3) / 1e9 if dom_ms > 0 else 0.0
+    launches_per_pack = int(sum(stage_launches[s] for s in kernels)) // max(1, npacks)
+    kernels_per_launch = {"prep": 2, "sort": 2, "layout": 1, "raster": 1, "hcompact": 1, "rowloop": 1,
+                          "select": 1}
+    gpu_launches = int(sum(stage_launches[s] * kernels_per_launch[s] for s in kernels))
+
+    res = {
+        "metric": METRIC,
+        "value": world * args.steps / (total_ms * 1e-3),
+        "unit": "packs/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps,
+        "p50_ms": float(np.percentile(per, 50)),
+        "p99_ms": float(np.percentile(per, 99)),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "int32/int64 (integer path)",
+        "data": "synthetic (seeded star charts; the paper's chart sets are not available)",
+        "config": {"workload": WORKLOAD, "atlas": [cs.atlas_w, cs.atlas_h], "charts": cs.n,
+                   "candidates": 64, "scale_fanout": args.fanout, "gutter": 1,
+                   "best_k": k, "scales_evaluated": n_eval,
+                   "l2": "flushed before every step (256 MiB write), outside the timed events",
+                   "parallelism": f"replicas x{world}"},
+        "e2e": {"value": world * args.steps / e2e_s, "unit": "packs/s",
+                "h2d_bytes_per_step": int(4 * (cs.n + 1) + 8 * cs.nv),
+                "d2h_bytes_per_step": int(12 * cs.n + 16)},
+        "gpu_launches": gpu_launches,
+        "stages_ms_per_pack": {s: round(stage_ms[s] / max(1, npacks), 4) for s in stage_ms},
+        "roofline": {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 2), "peak": hbm_peak,
+                     "unit": "GB/s", "frac": round(achieved / hbm_peak, 5), "traffic": None,
+                     "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6.8 TB/s",
+                     "algorithmic_bytes_per_launch": int(dom_bytes), "avg_launch_ms": round(dom_ms, 4)},
+        "clocks": clk.summary(),
+        "wall_s_timed_region": t_wall,
+    }
+    ctx.close()
+    return res, cs
+
+
+def run_reference(args, rank, world):
+    import oracle
+    import synth
+    if rank != 0:
+        return None
+    cs = synth.stars2k()
+    oracle.build()
+    for _ in range(args.warmup):
+        oracle.pack(cs)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        r = oracle.pack(cs)
+        times.append(time.perf_counter() - t0)
+        assert r.status == 0
+    tot = float(np.sum(times))
+    v = args.steps / tot
+    return {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "packs/s", "n_gpus": 0,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+        "p50_ms": 1e3 * float(np.percentile(times, 50)), "p99_ms": 1e3 * float(np.percentile(times, 99)),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64 (integer path)",
+        "data": "synthetic (seeded star charts)",
+        "config": {"workload": WORKLOAD, "atlas": [cs.atlas_w, cs.atlas_h], "charts": cs.n, "candidates": 64},
+        "cpu_baseline": {"value": v, "unit": "packs/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} full packs of the workload, one host core"},
+        "e2e": {"value": v, "unit": "packs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        res = run_reference(args, rank, world)
+        if res is not None:
+            print(json.dumps(res))
+        return
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    import __graft_entry__
+    __graft_entry__.build()
+    res, cs = run_ours(args, rank, world, local)
+    if rank == 0:
+        if not args.no_cpu_baseline:
+            res["cpu_baseline"] = cpu_baseline(cs)
+        print(json.dumps(res))
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

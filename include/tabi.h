@@ -1,0 +1,200 @@
+/*
+ * tabi.h -- C ABI of the GB300 atlas packer.
+ *
+ * Implements the data-parallel hot path of TABI (Gu, Vining, Sheffer,
+ * "TABI: Tight and Balanced Interactive Atlas Packing", arXiv 2602.07782).
+ * Problem statement (Sec. 4): a set of 2D charts (polygons in texel units)
+ * and a fixed atlas size in; one common scale and a rigid transform per
+ * chart (translation, 90-degree rotation, reflections) out, such that no two
+ * charts or their gutters overlap.
+ *
+ * Integer conventions.  Vertices are int32 in 1/256 texel ("Q.8"); every
+ * coordinate must lie in (-2^20, 2^20).  Candidate scales are k/1024 with
+ * k = 16*j, j = 1..64 -- the paper's 64 scales 1/64 .. 64/64 (Sec. 5).  All
+ * arithmetic on the path is integer and results are bit-exact with the CPU
+ * oracle that ships with the tests.
+ *
+ * Placement semantics.  For chart c with vertex v (Q.8, input coordinates),
+ * its position in the atlas (texels, y down, 0 = atlas top) is obtained by
+ *   1. p = v - (min_x, min_y) of the chart's input AABB;
+ *   2. if rot90:  p = (p.y, W0 - p.x)      (W0 = input AABB width, Q.8);
+ *   3. if flip_y: p.y = Hq - p.y;  if flip_x: p.x = Wq - p.x
+ *      (Wq, Hq = AABB size after step 2, Q.8);
+ *   4. t = p * k / 2^18  (texels);  w = ceil(Wq * k / 2^18);
+ *   5. if mirror: t.x = w - t.x;
+ *   6. atlas point = (x, y) + t.
+ * Every texel whose open square meets a placed chart lies in
+ * [x, x + w) x [y, y + h) inside the atlas, and the texels of two charts
+ * are at least 2*gutter texels apart (1-px gutters, Sec. 5).
+ *
+ * Ownership and streams.  The caller owns every input and output buffer.
+ * Calls are enqueued on the given CUDA stream (NULL = the legacy default
+ * stream) and return after the result is known (one stream synchronisation
+ * per call).  A context owns one device arena and must not be used by two
+ * host threads at once (TABI_ERR_BUSY otherwise).  No device memory is
+ * allocated per call: everything lives in the arena.
+ *
+ * Errors are returned as tabi_status codes; nothing is thrown across the
+ * ABI.  tabi_last_error() gives a one-line description of the last failure
+ * on a context.
+ */
+#ifndef TABI_H
+#define TABI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum tabi_status {
+  TABI_OK = 0,
+  TABI_ERR_INVALID_ARG = 1, /* n < 1, a chart with < 3 vertices, an AABB side
+                               below one texel, a coordinate outside
+                               (-2^20, 2^20), atlas side outside [1, 8192],
+                               bad params                                    */
+  TABI_ERR_NO_FIT = 2,      /* no candidate scale packs every chart          */
+  TABI_ERR_OOM = 3,         /* the context arena is too small for this input */
+  TABI_ERR_CUDA = 4,        /* a CUDA call failed (see tabi_last_error)      */
+  TABI_ERR_TIMEOUT = 5,     /* a bounded wait ran out (serving)              */
+  TABI_ERR_BUSY = 6         /* the context is in use by another call         */
+} tabi_status;
+
+#define TABI_PARAMS_VERSION 1
+
+/* Feature flags (all on = the paper's method; the others are the ablations
+ * of Tab. 3 and the boxes-only Chameleon baseline). */
+#define TABI_F_HC      1u /* horizontal compacting configurations, Sec. 4.1.2 */
+#define TABI_F_BALANCE 2u /* direction choice and knees, Sec. 4.2; off =
+                             static left/right alternation                   */
+#define TABI_F_OBB     4u /* OBB proxy in the envelopes, Sec. 4.1.1         */
+#define TABI_F_LAABB   8u /* local-AABB proxy in the envelopes, Sec. 4.1.1;
+                             OBB and LAABB both off = bounding boxes only    */
+#define TABI_F_ALL     15u
+
+typedef struct tabi_params {
+  int32_t version;      /* TABI_PARAMS_VERSION                                */
+  int32_t gutter;       /* gutter g in texels, 0..8 (Sec. 5 uses 1)           */
+  int32_t knee_abs_pct; /* knee: drop >= this % of the atlas height (10)     */
+  int32_t knee_rel_pct; /* knee: drop >= this % of the taller chart (20)     */
+  int32_t lr_sig_pct;   /* reflect left/right if areas differ by more than
+                           this % of the AABB area (10), App. A              */
+  int32_t knee_margin;  /* knee fold wins iff its max frontline is smaller
+                           by at least this many texels (1), Sec. 4.2        */
+  uint32_t flags;       /* TABI_F_*                                          */
+  int32_t scale_fanout; /* candidate scales evaluated per wave of the
+                           descending search, 1..64 (64 = all at once); the
+                           result is the same for every value               */
+} tabi_params;
+
+/* One placed chart; see "Placement semantics" above. */
+typedef struct tabi_placement {
+  int32_t x, y;
+  uint8_t rot90, flip_x, flip_y, mirror;
+} tabi_placement;
+
+typedef struct tabi_ctx tabi_ctx;
+
+/* Fill *p with the paper's defaults: gutter 1, knee 10 % / 20 %, left/right
+ * significance 10 %, knee margin 1, all features on, fan-out 64. */
+void tabi_params_default(tabi_params *p);
+
+/* Create a context on CUDA device `device`.  If `arena` is non-NULL it is a
+ * caller-owned device buffer of `arena_bytes` (256-byte aligned) that the
+ * context uses for all intermediate data and that must outlive the context;
+ * if NULL the context allocates `arena_bytes` itself (cudaMalloc) and frees
+ * it in tabi_ctx_destroy.  Returns TABI_ERR_INVALID_ARG for a bad device or
+ * alignment, TABI_ERR_CUDA if allocation fails. */
+tabi_status tabi_ctx_create(tabi_ctx **out, int device, void *arena, size_t arena_bytes);
+void tabi_ctx_destroy(tabi_ctx *ctx);
+const char *tabi_last_error(const tabi_ctx *ctx);
+const char *tabi_status_str(tabi_status s);
+
+/* Arena bytes a pack of this size needs (upper bound, host arithmetic only).
+ * `sum_extent_texels` = sum over charts of (input AABB width + height) in
+ * whole texels, rounded up. */
+size_t tabi_arena_bytes(int32_t n_charts, int32_t n_verts, int32_t atlas_w, int32_t atlas_h,
+                        int64_t sum_extent_texels, int32_t gutter);
+
+/* Pack one atlas (Sec. 4.3 Algorithm Summary; Algorithm 5 per candidate
+ * scale; largest successful scale, Sec. 3.1 / Sec. 5).  HOST buffers:
+ *   offsets[n_charts + 1]  vertex offsets (CSR), offsets[0] = 0,
+ *                          offsets[n_charts] = n_verts;
+ *   verts[2 * n_verts]     x0, y0, x1, y1, ... (Q.8), one closed loop per
+ *                          chart;
+ *   out[n_charts]          placements, input order (written on TABI_OK);
+ *   out_k                  the chosen k (scale k/1024); 0 on NO_FIT.
+ * The inputs are copied to the device on `stream`, the result back.
+ * Returns TABI_OK, TABI_ERR_NO_FIT, TABI_ERR_INVALID_ARG, TABI_ERR_OOM,
+ * TABI_ERR_CUDA or TABI_ERR_BUSY. */
+tabi_status tabi_pack(tabi_ctx *ctx, const tabi_params *params, int32_t atlas_w, int32_t atlas_h,
+                      int32_t n_charts, const uint32_t *offsets, const int32_t *verts,
+                      int32_t n_verts, tabi_placement *out, int32_t *out_k, void *stream);
+
+/* Same as tabi_pack with DEVICE pointers for offsets, verts and out; out_k
+ * is a host pointer. */
+tabi_status tabi_pack_device(tabi_ctx *ctx, const tabi_params *params, int32_t atlas_w,
+                             int32_t atlas_h, int32_t n_charts, const uint32_t *offsets,
+                             const int32_t *verts, int32_t n_verts, tabi_placement *out,
+                             int32_t *out_k, void *stream);
+
+/* Intermediate results of the last pack on this context, copied to host
+ * memory for inspection and step-by-step testing.  `what` selects:
+ *   TABI_INSPECT_CHARTS  tabi_chart_info[n], input order (prep, Sec. 3.1,
+ *                        Sec. 4.1.1, App. A);
+ *   TABI_INSPECT_PERM    int32[n]: input index of each sorted position;
+ *   TABI_INSPECT_ENV     for candidate index `scale` (k = 16*(scale+1)):
+ *                        int32[4n] meta (padded width w', padded height h',
+ *                        offset, max bottom) then uint32 pool; each column
+ *                        entry packs (Top' | Bot' << 16) and each row entry
+ *                        (L' | R' << 16); chart s's columns start at
+ *                        pool[offset] and its rows at pool[offset + wcap]
+ *                        with wcap = meta of TABI_INSPECT_ENV_CAP;
+ *   TABI_INSPECT_ENV_CAP int32[2n]: offset and column capacity per chart;
+ *   TABI_INSPECT_PAIRS   int32[n] compacting distance d(s, s+1) then
+ *                        uint8[n] flags (bit0 CannotMoveAbove(s, s+1),
+ *                        bit1 CannotMoveAbove(s+1, s)) for `scale`;
+ *   TABI_INSPECT_SCALE   int32[8]: success, rows, knee-folded rows, knees
+ *                        found, final max frontline, charts placed,
+ *                        evaluated, 0 -- then int32[4n] per sorted chart:
+ *                        x, y, row, bits (bit0 mirror, bit1 compacting on,
+ *                        bit2 knee-folded) for `scale`.
+ * Only candidates evaluated by the last pack are meaningful (all of them
+ * when scale_fanout = 64).  *needed receives the byte count; nothing is
+ * copied if cap is too small (TABI_ERR_INVALID_ARG). */
+enum {
+  TABI_INSPECT_CHARTS = 1,
+  TABI_INSPECT_PERM = 2,
+  TABI_INSPECT_ENV = 3,
+  TABI_INSPECT_ENV_CAP = 4,
+  TABI_INSPECT_PAIRS = 5,
+  TABI_INSPECT_SCALE = 6
+};
+tabi_status tabi_inspect(tabi_ctx *ctx, int32_t what, int32_t scale, void *host_dst, size_t cap,
+                         size_t *needed);
+
+/* Per-stage device time of the packs run on this context (CUDA events
+ * recorded on each pack's stream around every stage).  enable = 1 starts
+ * collection (and clears the totals), 0 stops it; with a non-NULL stage_ms
+ * the accumulated milliseconds are copied out before the state changes:
+ *   stage_ms[0..7] = prep, sort, layout, raster, hcompact, rowloop, select,
+ *                    whole pack;  launches[0..7] = launches of each;
+ *   *packs = packs timed.
+ * Timing adds event records between kernels; leave it off otherwise. */
+tabi_status tabi_stage_times(tabi_ctx *ctx, int32_t enable, double *stage_ms, int64_t *launches,
+                             int64_t *packs);
+
+/* Per-chart record of the prep step (TABI_INSPECT_CHARTS). */
+typedef struct tabi_chart_info {
+  int32_t orig, Wq, Hq, rot90, flip_y, flip_x, obb_m, valid;
+  int64_t u0, u1, v0, v1;                      /* OBB strips at angle obb_m */
+  int32_t ylo[10], yhi[10], xlo[10], xhi[10]; /* final local AABBs        */
+  int32_t tlo[10], bhi[10], llo[10], rhi[10]; /* refined pieces            */
+  int64_t area_top, area_bot, area_left, area_right, area_bl2, area_br2;
+} tabi_chart_info;
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TABI_H */

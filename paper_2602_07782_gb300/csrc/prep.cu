@@ -1,0 +1,353 @@
+// Chart preparation (Sec. 3.1, Sec. 4.1.1, App. A) and the height sort.
+//
+// prep_kernel: one warp per chart.  Lanes stride over the chart's edges; the
+// per-slice extrema and the per-angle OBB extents are combined with warp
+// shuffles, so no atomics are needed.  Three slice passes mirror the
+// orientation logic: slices of the rotated chart decide the vertical
+// reflection, slices of the vertically reflected chart decide the horizontal
+// one, slices of the final chart are the local-AABB proxy.
+//
+// sort_kernel: one CTA, stable LSD radix sort (three 7-bit digits of
+// 2^21 - 1 - Hq), so charts come out by decreasing AABB height with ties in
+// input order.  Ranking inside a warp uses __match_any_sync.
+#include "tabi_internal.cuh"
+
+namespace tabi {
+namespace {
+
+constexpr int64_t kI64Max = 0x7fffffffffffffffLL;
+constexpr int64_t kI64Min = -kI64Max - 1;
+
+// Chart-local transform: translate the AABB min to the origin, rotate
+// (x, y) -> (y, W0 - x) when wider than tall, then the reflections.
+struct Xf {
+  int64_t minx, miny, W0, Wq, Hq;
+  int rot, fy, fx;
+  __device__ __forceinline__ void apply(int32_t vx, int32_t vy, int64_t &x, int64_t &y) const {
+    const int64_t tx = (int64_t)vx - minx, ty = (int64_t)vy - miny;
+    if (rot) { x = ty; y = W0 - tx; } else { x = tx; y = ty; }
+    if (fy) y = Hq - y;
+    if (fx) x = Wq - x;
+  }
+};
+
+// Local AABBs of the K slices along one axis: for slice i = [B_i, B_{i+1}]
+// (B_i = floor(i * ext / K)), floor(min) and ceil(max) of the other
+// coordinate over the polygon's edges clipped to the slab.  Every lane ends
+// with all values.
+__device__ void warp_slices(const int32_t *__restrict__ v, int nv, const Xf &xf, bool xaxis,
+                            int64_t ext, int64_t (&lo)[kSlices], int64_t (&hi)[kSlices]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int i = 0; i < kSlices; ++i) { lo[i] = kI64Max; hi[i] = kI64Min; }
+  for (int e = lane; e < nv; e += 32) {
+    const int e1 = (e + 1 == nv) ? 0 : e + 1;
+    int64_t x0, y0, x1, y1;
+    xf.apply(v[2 * e], v[2 * e + 1], x0, y0);
+    xf.apply(v[2 * e1], v[2 * e1 + 1], x1, y1);
+    const int64_t u0 = xaxis ? x0 : y0, w0 = xaxis ? y0 : x0;
+    const int64_t u1 = xaxis ? x1 : y1, w1 = xaxis ? y1 : x1;
+    const int64_t ul = u0 < u1 ? u0 : u1, ur = u0 < u1 ? u1 : u0;
+    int64_t den = u1 - u0;
+    const bool vert = den == 0;
+    const int64_t sgn = den < 0 ? -1 : 1;
+    den *= sgn;
+#pragma unroll
+    for (int i = 0; i < kSlices; ++i) {
+      const int64_t a = (int64_t)i * ext / kSlices, b = (int64_t)(i + 1) * ext / kSlices;
+      if (vert) {
+        if (u0 >= a && u0 <= b) {
+          const int64_t mn = w0 < w1 ? w0 : w1, mx = w0 < w1 ? w1 : w0;
+          lo[i] = mn < lo[i] ? mn : lo[i];
+          hi[i] = mx > hi[i] ? mx : hi[i];
+        }
+        continue;
+      }
+      const int64_t ca = a > ul ? a : ul, cb = b < ur ? b : ur;
+      if (ca > cb) continue;
+#pragma unroll
+      for (int t = 0; t < 2; ++t) {
+        const int64_t u = t ? cb : ca;
+        const int64_t num = sgn * (w0 * (u1 - u0) + (u - u0) * (w1 - w0));
+        const int64_t f = floor_div(num, den), c = ceil_div(num, den);
+        lo[i] = f < lo[i] ? f : lo[i];
+        hi[i] = c > hi[i] ? c : hi[i];
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < kSlices; ++i) {
+    lo[i] = warp_min(lo[i]);
+    hi[i] = warp_max(hi[i]);
+  }
+}
+
+__global__ void __launch_bounds__(256) prep_kernel(Pack p) {
+  const int lane = threadIdx.x & 31;
+  const int c = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+  if (c >= p.n) return;
+  const uint32_t a = p.offsets[c], b = p.offsets[c + 1];
+  const int nv = (int)(b - a);
+  const int32_t *v = p.verts + 2 * (size_t)a;
+  tabi_chart_info *inf = p.info + c;
+  ChartShape *sh = p.shape_in + c;
+
+  // Sec. 3.1: the chart's AABB (and input validation)
+  int32_t mnx = 0x7fffffff, mny = 0x7fffffff, mxx = -0x7fffffff - 1, mxy = -0x7fffffff - 1;
+  int bad = (b < a) || (nv < 3) || (b > (uint32_t)p.nv);
+  if (!bad) {
+    for (int i = lane; i < nv; i += 32) {
+      const int32_t x = v[2 * i], y = v[2 * i + 1];
+      bad |= (x <= -(1 << 20)) | (x >= (1 << 20)) | (y <= -(1 << 20)) | (y >= (1 << 20));
+      mnx = min(mnx, x); mxx = max(mxx, x);
+      mny = min(mny, y); mxy = max(mxy, y);
+    }
+  }
+  bad = __any_sync(0xffffffffu, bad);
+  mnx = warp_min(mnx); mxx = warp_max(mxx);
+  mny = warp_min(mny); mxy = warp_max(mxy);
+  const int64_t W0 = (int64_t)mxx - mnx, H0 = (int64_t)mxy - mny;
+  const int rot = W0 > H0;  // rotate to be taller than wide (strictly wider)
+  const int64_t Wq = rot ? H0 : W0, Hq = rot ? W0 : H0;
+  if (bad || Wq < 256 || Hq < 256) {
+    // rejected: keep a harmless one-texel box so later kernels stay in bounds
+    if (lane == 0) {
+      inf->orig = c; inf->valid = 0; inf->Wq = 0; inf->Hq = 0;
+      sh->Wq = 256; sh->Hq = 256; sh->m = 0; sh->pad = 0;
+      sh->u0 = sh->u1 = sh->v0 = sh->v1 = 0;
+      atomicOr(p.err, kErrInvalid);
+    }
+    if (lane < kSlices) {
+      sh->tlo[lane] = 0; sh->bhi[lane] = 256; sh->llo[lane] = 0; sh->rhi[lane] = 256;
+    }
+    return;
+  }
+  Xf xf{mnx, mny, W0, Wq, Hq, rot, 0, 0};
+  int64_t ylo[kSlices], yhi[kSlices], xlo[kSlices], xhi[kSlices];
+
+  // App. A chart orientation, vertical reflection: top vs bottom empty area
+  warp_slices(v, nv, xf, true, Wq, ylo, yhi);
+  int64_t top = 0, bottom = 0;
+#pragma unroll
+  for (int i = 0; i < kSlices; ++i) {
+    const int64_t wi = (int64_t)(i + 1) * Wq / kSlices - (int64_t)i * Wq / kSlices;
+    top += wi * ylo[i];
+    bottom += wi * (Hq - yhi[i]);
+  }
+  xf.fy = top > bottom;
+
+  // horizontal reflection: left vs right empty area, else bottom-left vs
+  // bottom-right of the midline (doubled coordinates)
+  warp_slices(v, nv, xf, true, Wq, ylo, yhi);
+  warp_slices(v, nv, xf, false, Hq, xlo, xhi);
+  int64_t left = 0, right = 0, bl2 = 0, br2 = 0;
+#pragma unroll
+  for (int j = 0; j < kSlices; ++j) {
+    const int64_t hj = (int64_t)(j + 1) * Hq / kSlices - (int64_t)j * Hq / kSlices;
+    left += hj * xlo[j];
+    right += hj * (Wq - xhi[j]);
+  }
+#pragma unroll
+  for (int i = 0; i < kSlices; ++i) {
+    const int64_t e = Hq - yhi[i];
+    const int64_t a2 = 2 * ((int64_t)i * Wq / kSlices), b2 = 2 * ((int64_t)(i + 1) * Wq / kSlices);
+    const int64_t lenL = max((int64_t)0, min(b2, Wq) - max(a2, (int64_t)0));
+    const int64_t lenR = max((int64_t)0, min(b2, 2 * Wq) - max(a2, Wq));
+    bl2 += e * lenL;
+    br2 += e * lenR;
+  }
+  const int64_t diff = left - right;
+  const int64_t adiff = diff < 0 ? -diff : diff;
+  if (100 * adiff > (int64_t)p.lr_sig * Wq * Hq) xf.fx = diff > 0;
+  else xf.fx = bl2 > br2;
+
+  // final local AABBs
+  warp_slices(v, nv, xf, true, Wq, ylo, yhi);
+  warp_slices(v, nv, xf, false, Hq, xlo, xhi);
+
+  // Sec. 4.1.1 merge: tighten each slice by the other axis' slices
+  // (lanes 0..9: x-slices, lanes 16..25: y-slices)
+  int64_t r0 = 0, r1 = 0;
+  if (lane < kSlices) {
+    const int i = lane;
+    const int64_t Xi = (int64_t)i * Wq / kSlices, Xi1 = (int64_t)(i + 1) * Wq / kSlices;
+    int64_t t2 = kI64Max, b2v = kI64Min;
+#pragma unroll
+    for (int j = 0; j < kSlices; ++j)
+      if (xlo[j] <= Xi1 && xhi[j] >= Xi) {
+        const int64_t Yj = (int64_t)j * Hq / kSlices, Yj1 = (int64_t)(j + 1) * Hq / kSlices;
+        t2 = min(t2, Yj);
+        b2v = max(b2v, Yj1);
+      }
+    int64_t yl = 0, yh = 0;
+#pragma unroll
+    for (int q = 0; q < kSlices; ++q) if (q == i) { yl = ylo[q]; yh = yhi[q]; }
+    r0 = max(yl, t2);
+    r1 = min(yh, b2v);
+  } else if (lane >= 16 && lane < 16 + kSlices) {
+    const int j = lane - 16;
+    const int64_t Yj = (int64_t)j * Hq / kSlices, Yj1 = (int64_t)(j + 1) * Hq / kSlices;
+    int64_t l2 = kI64Max, r2 = kI64Min;
+#pragma unroll
+    for (int i = 0; i < kSlices; ++i)
+      if (ylo[i] <= Yj1 && yhi[i] >= Yj) {
+        const int64_t Xi = (int64_t)i * Wq / kSlices, Xi1 = (int64_t)(i + 1) * Wq / kSlices;
+        l2 = min(l2, Xi);
+        r2 = max(r2, Xi1);
+      }
+    int64_t xl = 0, xh = 0;
+#pragma unroll
+    for (int q = 0; q < kSlices; ++q) if (q == j) { xl = xlo[q]; xh = xhi[q]; }
+    r0 = max(xl, l2);
+    r1 = min(xh, r2);
+  }
+
+  // App. A OBB: 8 angles, extents of u = xC + yS, v = -xS + yC
+  int64_t bu0 = 0, bu1 = 0, bv0 = 0, bv1 = 0;
+  int best = 0;
+  __int128 best_area = 0, best_n = 1;
+  for (int m = 0; m < kAngles; ++m) {
+    const int64_t C = kObbCos[m], S = kObbSin[m];
+    int64_t u0 = kI64Max, u1 = kI64Min, v0 = kI64Max, v1 = kI64Min;
+    for (int i = lane; i < nv; i += 32) {
+      int64_t x, y;
+      xf.apply(v[2 * i], v[2 * i + 1], x, y);
+      const int64_t uu = x * C + y * S, vv = -x * S + y * C;
+      u0 = min(u0, uu); u1 = max(u1, uu);
+      v0 = min(v0, vv); v1 = max(v1, vv);
+    }
+    u0 = warp_min(u0); u1 = warp_max(u1);
+    v0 = warp_min(v0); v1 = warp_max(v1);
+    const __int128 area = (__int128)(u1 - u0) * (v1 - v0);
+    const __int128 nrm = (__int128)(C * C + S * S);
+    if (m == 0 || area * best_n < best_area * nrm) {
+      best = m; best_area = area; best_n = nrm;
+      bu0 = u0; bu1 = u1; bv0 = v0; bv1 = v1;
+    }
+  }
+
+  // write the records
+  if (lane == 0) {
+    inf->orig = c; inf->Wq = (int32_t)Wq; inf->Hq = (int32_t)Hq;
+    inf->rot90 = rot; inf->flip_y = xf.fy; inf->flip_x = xf.fx; inf->obb_m = best; inf->valid = 1;
+    inf->u0 = bu0; inf->u1 = bu1; inf->v0 = bv0; inf->v1 = bv1;
+    inf->area_top = top; inf->area_bot = bottom; inf->area_left = left; inf->area_right = right;
+    inf->area_bl2 = bl2; inf->area_br2 = br2;
+#pragma unroll
+    for (int i = 0; i < kSlices; ++i) {
+      inf->ylo[i] = (int32_t)ylo[i]; inf->yhi[i] = (int32_t)yhi[i];
+      inf->xlo[i] = (int32_t)xlo[i]; inf->xhi[i] = (int32_t)xhi[i];
+    }
+    sh->Wq = (int32_t)Wq; sh->Hq = (int32_t)Hq; sh->m = best; sh->pad = 0;
+    sh->u0 = bu0; sh->u1 = bu1; sh->v0 = bv0; sh->v1 = bv1;
+  }
+  if (lane < kSlices) {
+    inf->tlo[lane] = (int32_t)r0; inf->bhi[lane] = (int32_t)r1;
+    sh->tlo[lane] = (int32_t)r0; sh->bhi[lane] = (int32_t)r1;
+  } else if (lane >= 16 && lane < 16 + kSlices) {
+    inf->llo[lane - 16] = (int32_t)r0; inf->rhi[lane - 16] = (int32_t)r1;
+    sh->llo[lane - 16] = (int32_t)r0; sh->rhi[lane - 16] = (int32_t)r1;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// stable radix sort by decreasing Hq (one CTA)
+// ---------------------------------------------------------------------------
+constexpr int kSortThreads = 1024;
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kDigits = 128;  // 7-bit digits, 3 passes over 21 bits
+
+__global__ void __launch_bounds__(kSortThreads) sort_kernel(Pack p) {
+  __shared__ uint32_t hist[kDigits * kSortWarps];  // [digit][warp]
+  __shared__ uint32_t part[kSortWarps];
+  const int n = p.n, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  uint32_t *kA = p.sort_tmp, *vA = kA + n, *kB = vA + n, *vB = kB + n;
+  for (int c = tid; c < n; c += kSortThreads) {
+    kA[c] = (uint32_t)((1 << 21) - 1 - p.shape_in[c].Hq);
+    vA[c] = (uint32_t)c;
+  }
+  const int chunk = ((n + kSortWarps - 1) / kSortWarps + 31) & ~31;
+  const int beg = w * chunk, end = min(n, beg + chunk);
+  const unsigned lt = (1u << lane) - 1u;
+  __syncthreads();
+  for (int pass = 0; pass < 3; ++pass) {
+    const int shift = 7 * pass;
+    const uint32_t *ks = (pass & 1) ? kB : kA, *vs = (pass & 1) ? vB : vA;
+    uint32_t *kd = (pass & 1) ? kA : kB, *vd = (pass & 1) ? vA : vB;
+    for (int i = tid; i < kDigits * kSortWarps; i += kSortThreads) hist[i] = 0;
+    __syncthreads();
+    for (int base = beg; base < end; base += 32) {
+      const int i = base + lane;
+      const bool ok = i < end;
+      const uint32_t d = ok ? (ks[i] >> shift) & (kDigits - 1) : kDigits;
+      const unsigned peers = __match_any_sync(0xffffffffu, d);
+      if (ok && lane == __ffs(peers) - 1) hist[d * kSortWarps + w] += __popc(peers);
+    }
+    __syncthreads();
+    // exclusive scan of hist in digit-major order (4 entries per thread)
+    uint32_t loc[4], sum = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) { loc[q] = hist[tid * 4 + q]; sum += loc[q]; }
+    uint32_t incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += u;
+    }
+    if (lane == 31) part[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+      uint32_t x = part[lane], y = x;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t u = __shfl_up_sync(0xffffffffu, y, o);
+        if (lane >= o) y += u;
+      }
+      part[lane] = y - x;
+    }
+    __syncthreads();
+    uint32_t run = part[w] + incl - sum;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) { hist[tid * 4 + q] = run; run += loc[q]; }
+    __syncthreads();
+    for (int base = beg; base < end; base += 32) {
+      const int i = base + lane;
+      const bool ok = i < end;
+      const uint32_t key = ok ? ks[i] : 0u;
+      const uint32_t d = ok ? (key >> shift) & (kDigits - 1) : kDigits;
+      const unsigned peers = __match_any_sync(0xffffffffu, d);
+      uint32_t dst = 0;
+      if (ok) dst = hist[d * kSortWarps + w] + __popc(peers & lt);
+      __syncwarp();
+      if (ok && lane == __ffs(peers) - 1) hist[d * kSortWarps + w] += __popc(peers);
+      __syncwarp();
+      if (ok) { kd[dst] = key; vd[dst] = vs[i]; }
+    }
+    __syncthreads();
+  }
+  // three passes: A->B, B->A, A->B
+  for (int s = tid; s < n; s += kSortThreads) p.perm[s] = (int32_t)vB[s];
+}
+
+__global__ void gather_kernel(Pack p) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= p.n) return;
+  const int c = p.perm[s];
+  p.shape[s] = p.shape_in[c];
+  p.hq[s] = p.shape_in[c].Hq;
+}
+
+}  // namespace
+
+void launch_prep(const Pack &p, cudaStream_t st) {
+  const int warps_per_block = 8;
+  const int blocks = (p.n + warps_per_block - 1) / warps_per_block;
+  prep_kernel<<<blocks, warps_per_block * 32, 0, st>>>(p);
+}
+
+void launch_sort(const Pack &p, cudaStream_t st) {
+  sort_kernel<<<1, kSortThreads, 0, st>>>(p);
+  gather_kernel<<<(p.n + 255) / 256, 256, 0, st>>>(p);
+}
+
+}  // namespace tabi

@@ -1,0 +1,226 @@
+"""GPU parity: every step of the CUDA path against the CPU oracle, bit for
+bit, through the C ABI (include/tabi.h) and its Python binding.
+
+Integer path: the bar is exact equality of every chart record, permutation,
+envelope, compacting distance, interlock flag, per-scale success and
+placement, and the final scale and placements.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # the -m gpu suite runs on a GPU machine only
+    pytest.skip("CUDA not available", allow_module_level=True)
+
+from paper_2602_07782_gb300 import tabi  # noqa: E402
+
+R = oracle.R
+K = oracle.K
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = tabi.Context(arena_bytes=3 << 30)
+    yield c
+    c.close()
+
+
+def gpu_params(**kw):
+    kw.setdefault("scale_fanout", 64)
+    return tabi.params_default(**kw)
+
+
+def oracle_params(p):
+    return oracle.default_params(gutter=p.gutter, knee_abs=p.knee_abs_pct, knee_rel=p.knee_rel_pct,
+                                 lr_sig=p.lr_sig_pct, knee_margin=p.knee_margin, flags=p.flags)
+
+
+SMALL = {
+    "plain64_s1": lambda: synth.plain64(seed=1),
+    "plain64_s2": lambda: synth.plain64(seed=2),
+    "stars300": lambda: synth.stars(3, 300, 512),
+    "knees300": lambda: synth.knees(1, 300, 1024),
+    "knees200_512": lambda: synth.knees(5, 200, 512),
+    "strips": lambda: synth.pareto20k(seed=9, n=1500, atlas=1024),
+}
+
+
+def _check_prep(ctx, cs, op):
+    info = ctx.charts()
+    rec = oracle.prep(cs, op)
+    assert np.all(info["valid"] == 1)
+    for f, col in (("Wq", "WQ"), ("Hq", "HQ"), ("rot90", "ROT"), ("flip_y", "FLIPY"),
+                   ("flip_x", "FLIPX"), ("obb_m", "OBBM"), ("u0", "U0"), ("u1", "U1"),
+                   ("v0", "V0"), ("v1", "V1"), ("area_top", "ATOP"), ("area_bot", "ABOT"),
+                   ("area_left", "ALEFT"), ("area_right", "ARIGHT"), ("area_bl2", "ABL2"),
+                   ("area_br2", "ABR2")):
+        assert np.array_equal(info[f].astype(np.int64), rec[:, R[col]]), f
+    for f, col in (("ylo", "YLO"), ("yhi", "YHI"), ("xlo", "XLO"), ("xhi", "XHI"),
+                   ("tlo", "TLO"), ("bhi", "BHI"), ("llo", "LLO"), ("rhi", "RHI")):
+        assert np.array_equal(info[f].astype(np.int64), rec[:, R[col]:R[col] + K]), f
+    perm = ctx.perm()
+    assert np.array_equal(perm, oracle.sort(rec))
+    return rec, perm
+
+
+@pytest.mark.parametrize("name", list(SMALL))
+def test_steps_parity(ctx, name):
+    """prep, sort, envelopes, distances/flags and every candidate's row loop."""
+    cs = SMALL[name]()
+    p = gpu_params()
+    op = oracle_params(p)
+    res = ctx.pack(cs, p)
+    assert res.status == tabi.TABI_OK, ctx.last_error()
+    rec, perm = _check_prep(ctx, cs, op)
+    for j in range(0, 64, 1 if cs.n <= 300 else 7):
+        k = 16 * (j + 1)
+        env = ctx.envelopes(j, cs.n)
+        for s in range(cs.n):
+            e = oracle.envelope_padded(rec[perm[s]], k, op)
+            wp, hp, top, bot, left, right, mb = env[s]
+            assert (wp, hp) == (e.w, e.h), (j, s)
+            assert np.array_equal(top, e.top) and np.array_equal(bot, e.bot), (j, s)
+            assert np.array_equal(left, e.left) and np.array_equal(right, e.right), (j, s)
+            assert mb == e.bot.max()
+        d, ca, cb = ctx.pairs(j, cs.n)
+        od, oca, ocb, owp, ohp = oracle.scale_pairs(rec, perm, k, op)
+        assert np.array_equal(d[:-1], od[:-1]), j
+        assert np.array_equal(ca[:-1], oca[:-1]) and np.array_equal(cb[:-1], ocb[:-1]), j
+        hdr, place = ctx.scale_result(j, cs.n)
+        ok, opl, ost = oracle.pack_scale(rec, perm, cs.atlas_w, cs.atlas_h, k, op)
+        assert hdr[0] == int(ok), j
+        assert list(hdr[1:6]) == [ost[0], ost[1], ost[2], ost[3], ost[4]], j
+        placed = int(ost[4])
+        bits = opl[:placed, 2] | (opl[:placed, 4] << 1) | (opl[:placed, 5] << 2)
+        assert np.array_equal(place[:placed, 0], opl[:placed, 0]), j
+        assert np.array_equal(place[:placed, 1], opl[:placed, 1]), j
+        assert np.array_equal(place[:placed, 2], opl[:placed, 3]), j
+        assert np.array_equal(place[:placed, 3], bits), j
+
+
+def _compare_pack(cs, res, op):
+    o = oracle.pack(cs, op)
+    assert res.status == {0: 0, 2: 2, 1: 1}[o.status]
+    assert res.k == o.k
+    if o.status == 0:
+        pl = res.place
+        assert np.array_equal(pl["x"], o.place[:, 0])
+        assert np.array_equal(pl["y"], o.place[:, 1])
+        assert np.array_equal(pl["rot90"], o.place[:, 2])
+        assert np.array_equal(pl["flip_x"], o.place[:, 3])
+        assert np.array_equal(pl["flip_y"], o.place[:, 4])
+        assert np.array_equal(pl["mirror"], o.place[:, 5])
+    return o
+
+
+@pytest.mark.parametrize("name", list(SMALL))
+@pytest.mark.parametrize("fanout", [64, 8, 1])
+def test_pack_parity(ctx, name, fanout):
+    cs = SMALL[name]()
+    p = gpu_params(scale_fanout=fanout)
+    res = ctx.pack(cs, p)
+    _compare_pack(cs, res, oracle_params(p))
+
+
+@pytest.mark.parametrize("name,make", [("stars2k", synth.stars2k), ("pareto20k", synth.pareto20k)])
+def test_full_size_parity(ctx, name, make):
+    """The full-size workloads, in the launch configuration the benchmark
+    times (scale_fanout 64), bit-exact against the oracle."""
+    cs = make()
+    p = gpu_params()
+    res = ctx.pack(cs, p)
+    assert res.status == 0, ctx.last_error()
+    _compare_pack(cs, res, oracle_params(p))
+
+
+@pytest.mark.parametrize("flags", [tabi.F_ALL & ~tabi.F_HC, tabi.F_ALL & ~tabi.F_BALANCE,
+                                   tabi.F_HC | tabi.F_BALANCE, tabi.F_ALL & ~tabi.F_OBB,
+                                   tabi.F_ALL & ~tabi.F_LAABB, 0])
+def test_ablation_parity(ctx, flags):
+    cs = synth.knees(2, 250, 1024)
+    p = gpu_params(flags=flags)
+    _compare_pack(cs, ctx.pack(cs, p), oracle_params(p))
+
+
+@pytest.mark.parametrize("gutter", [0, 2, 3])
+def test_gutter_parity(ctx, gutter):
+    cs = synth.stars(6, 200, 512)
+    p = gpu_params(gutter=gutter)
+    _compare_pack(cs, ctx.pack(cs, p), oracle_params(p))
+
+
+def test_edge_cases(ctx):
+    p = gpu_params()
+    op = oracle_params(p)
+    # a single chart
+    cs = synth.stars(21, 1, 256, density=0.3)
+    _compare_pack(cs, ctx.pack(cs, p), op)
+    # equal squares (every direction ties)
+    cs = synth.rectangles([(7, 7)] * 50, 100, 60)
+    _compare_pack(cs, ctx.pack(cs, p), op)
+    # a chart that fits at no candidate scale
+    cs = synth.rectangles([(300, 300)], 2, 2)
+    assert ctx.pack(cs, p).status == tabi.TABI_ERR_NO_FIT
+    # non-square atlas, knees, ragged sizes
+    cs = synth.knees(7, 123, 777)
+    cs.atlas_h = 333
+    _compare_pack(cs, ctx.pack(cs, p), op)
+    # the nesting diamonds where the second-neighbour clamp binds
+    def diamond(W, H):
+        W, H = W * 256, H * 256
+        return [(W // 2, 0), (W, H // 2), (W // 2, H), (0, H // 2)]
+    cs = synth.from_polygons([diamond(60, 100), diamond(10, 20), diamond(10, 10)], 78, 300)
+    _compare_pack(cs, ctx.pack(cs, p), op)
+
+
+def test_invalid_inputs(ctx):
+    p = gpu_params()
+    bad = [synth.from_polygons([[(0, 0), (100, 0), (100, 600)]], 32, 32),      # < 1 texel wide
+           synth.from_polygons([[(0, 0), (1 << 20, 0), (0, 600)]], 32, 32)]    # out of range
+    for cs in bad:
+        assert ctx.pack(cs, p).status == tabi.TABI_ERR_INVALID_ARG
+    cs = synth.rectangles([(3, 5)], 32, 32)
+    cs.atlas_w = 0
+    assert ctx.pack(cs, p).status == tabi.TABI_ERR_INVALID_ARG
+    # the context still works afterwards
+    cs = synth.rectangles([(3, 5)], 32, 32)
+    assert ctx.pack(cs, p).status == tabi.TABI_OK
+
+
+def test_device_entry_point_matches_host(ctx):
+    cs = synth.knees(3, 400, 1024)
+    p = gpu_params()
+    host = ctx.pack(cs, p)
+    dev = torch.device("cuda:0")
+    offs = torch.from_numpy(cs.offsets.view(np.int32).copy()).to(dev)
+    verts = torch.from_numpy(cs.verts.copy()).to(dev)
+    out = torch.zeros(12 * cs.n, dtype=torch.uint8, device=dev)
+    st, k = ctx.pack_device(cs.n, cs.nv, cs.atlas_w, cs.atlas_h, offs, verts, out, p)
+    torch.cuda.synchronize()
+    assert st == 0 and k == host.k
+    got = out.cpu().numpy().view(tabi.PLACEMENT_DTYPE)
+    assert np.array_equal(got, host.place)
+
+
+def test_deterministic(ctx):
+    cs = synth.stars(12, 700, 1024)
+    p = gpu_params()
+    a = ctx.pack(cs, p)
+    b = ctx.pack(cs, p)
+    assert a.k == b.k and np.array_equal(a.place, b.place)
+
+
+def test_small_arena_reports_oom():
+    c = tabi.Context(arena_bytes=2 << 20)
+    try:
+        cs = synth.stars2k()
+        assert c.pack(cs, gpu_params()).status == tabi.TABI_ERR_OOM
+    finally:
+        c.close()
