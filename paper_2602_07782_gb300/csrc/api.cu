@@ -191,6 +191,10 @@ tabi_status run_pack(tabi_ctx *ctx, const tabi_params *params, int32_t W, int32_
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e = cudaSetDevice(ctx->device);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
+  int smem_optin = 0;
+  cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
+  if (rowloop_smem_bytes(W, params->gutter) > (size_t)smem_optin)
+    return fail(ctx, TABI_ERR_INVALID_ARG, "atlas too wide for this gutter: the row working set exceeds shared memory");
 
   Carve cv{ctx->arena, ctx->arena_bytes};
   Pack p{};

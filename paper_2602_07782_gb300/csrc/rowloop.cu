@@ -470,12 +470,24 @@ __global__ void __launch_bounds__(kNT) rowloop_kernel(Pack p, int j_lo, int maxr
 
 }  // namespace
 
-int rowloop_maxrow(const Pack &p) { return (p.W + 2 * p.g) / 3 + 2; }
+// Row capacity: charts in a row start at least 2g + 1 texels apart (each
+// padded scanline spans 2g + 1 texels or more), so a row holds at most
+// W'/(2g+1) + 1 charts.
+static int rowloop_maxrow(int W, int g) {
+  const int Wp = W + 2 * g;
+  return (Wp / (2 * g + 1) + 2 + 3) & ~3;
+}
+
+size_t rowloop_smem_bytes(int W, int g) {
+  const int Wp = W + 2 * g;
+  const int wp_pad = (Wp + 3) & ~3;
+  return sizeof(int32_t) * ((size_t)wp_pad + 14 * (size_t)rowloop_maxrow(W, g) + 4) + sizeof(Ctl);
+}
 
 cudaError_t launch_rowloop(const Pack &p, int j_lo, int j_hi, cudaStream_t st) {
   const int Wp = p.W + 2 * p.g;
   const int wp_pad = (Wp + 3) & ~3;
-  const int maxrow = (Wp / 3 + 2 + 3) & ~3;
+  const int maxrow = rowloop_maxrow(p.W, p.g);
   const size_t smem = sizeof(int32_t) * ((size_t)wp_pad + 14 * (size_t)maxrow + 4);
   cudaError_t e = cudaFuncSetAttribute(rowloop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

@@ -77,6 +77,7 @@ void launch_layout(const Pack &p, cudaStream_t st);
 void launch_raster(const Pack &p, int j_lo, int j_hi, cudaStream_t st);
 void launch_hcompact(const Pack &p, int j_lo, int j_hi, cudaStream_t st);
 cudaError_t launch_rowloop(const Pack &p, int j_lo, int j_hi, cudaStream_t st);
+size_t rowloop_smem_bytes(int W, int g);  // shared memory one row-loop CTA needs
 void launch_select(const Pack &p, cudaStream_t st);
 void launch_init(const Pack &p, cudaStream_t st);
 
