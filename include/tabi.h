@@ -187,6 +187,30 @@ tabi_status tabi_inspect(tabi_ctx *ctx, int32_t what, int32_t scale, void *host_
 tabi_status tabi_stage_times(tabi_ctx *ctx, int32_t enable, double *stage_ms, int64_t *launches,
                              int64_t *packs);
 
+/* Height sort with no device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that cannot call cudaMalloc -- engines
+ * and interactive tools that own a fixed, pre-budgeted device memory pool
+ * and forbid allocations outside it, or frame loops where an allocation
+ * (which may synchronise the device) would stall the frame.
+ *
+ * Sorts chart indices 0..n-1 by decreasing height, ties in index order --
+ * the same order the pack uses.  DEVICE buffers, owned by the caller:
+ *   heights[n]  chart heights (Q.8), expected in [0, 2^21); values outside
+ *               are clamped into that range;
+ *   perm[n]     output: perm[s] = index of the chart at sorted position s.
+ * The sort's scratch is a fixed device array inside the library (1 MiB,
+ * kept on every GPU that loads the library until the process exits), so
+ * n is limited to 65,536: larger n returns TABI_ERR_INVALID_ARG, as does a
+ * NULL pointer or n < 1.  The call allocates nothing and is asynchronous on
+ * `stream` (NULL = legacy default stream); synchronise before reading perm.
+ * The first call on each device looks up the scratch array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  Every call shares the one scratch array,
+ * so calls that overlap on the GPU (concurrent streams) race: serialise
+ * them.  Returns TABI_OK, TABI_ERR_INVALID_ARG or TABI_ERR_CUDA (launch or
+ * address lookup failed). */
+tabi_status tabi_sort_heights_noalloc(const int32_t *heights, int32_t n, int32_t *perm, void *stream);
+
 /* Per-chart record of the prep step (TABI_INSPECT_CHARTS). */
 typedef struct tabi_chart_info {
   int32_t orig, Wq, Hq, rot90, flip_y, flip_x, obb_m, valid;
