@@ -55,7 +55,7 @@ typedef enum tabi_status {
                                (-2^20, 2^20), atlas side outside [1, 8192],
                                bad params, or an atlas too wide for the
                                gutter (gutter 0 supports widths up to about
-                               3,500 texels, gutter >= 1 every width)       */
+                               4,000 texels, gutter >= 1 every width)       */
   TABI_ERR_NO_FIT = 2,      /* no candidate scale packs every chart          */
   TABI_ERR_OOM = 3,         /* the context arena is too small for this input */
   TABI_ERR_CUDA = 4,        /* a CUDA call failed (see tabi_last_error)      */

@@ -16,6 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libtabi.so")
 SOURCES = ["prep.cu", "raster.cu", "rowloop.cu", "api.cu", "noalloc.cu"]
+HEADERS = ["tabi_internal.cuh", "raster_math.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 
@@ -36,8 +37,7 @@ def _stale(target: str, deps: list[str]) -> bool:
 
 def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(OUT, exist_ok=True)
-    headers = [os.path.join(CSRC, "tabi_internal.cuh"),
-               os.path.join(HERE, "..", "include", "tabi.h")]
+    headers = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(HERE, "..", "include", "tabi.h")]
     objs = []
     jobs = []
     for src in SOURCES:

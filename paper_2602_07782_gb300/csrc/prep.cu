@@ -5,7 +5,9 @@
 // shuffles, so no atomics are needed.  Three slice passes mirror the
 // orientation logic: slices of the rotated chart decide the vertical
 // reflection, slices of the vertically reflected chart decide the horizontal
-// one, slices of the final chart are the local-AABB proxy.
+// one, slices of the final chart are the local-AABB proxy.  A reflection
+// mirrors the other axis' slice extents exactly, so only the slices along
+// the reflected axis are recomputed (two or three slab passes, not five).
 //
 // sort_kernel: one CTA, stable LSD radix sort (three 7-bit digits of
 // 2^21 - 1 - Hq), so charts come out by decreasing AABB height with ties in
@@ -136,9 +138,20 @@ __global__ void __launch_bounds__(256) prep_kernel(Pack p) {
   }
   xf.fy = top > bottom;
 
+  // A reflection mirrors the extents of the slices along the other axis
+  // exactly (floor(min(H - v)) = H - ceil(max v)); the slices along the
+  // reflected axis must be recomputed, their boundaries do not mirror.
+  if (xf.fy) {
+#pragma unroll
+    for (int i = 0; i < kSlices; ++i) {
+      const int64_t lo = Hq - yhi[i], hi = Hq - ylo[i];
+      ylo[i] = lo;
+      yhi[i] = hi;
+    }
+  }
+
   // horizontal reflection: left vs right empty area, else bottom-left vs
   // bottom-right of the midline (doubled coordinates)
-  warp_slices(v, nv, xf, true, Wq, ylo, yhi);
   warp_slices(v, nv, xf, false, Hq, xlo, xhi);
   int64_t left = 0, right = 0, bl2 = 0, br2 = 0;
 #pragma unroll
@@ -162,8 +175,15 @@ __global__ void __launch_bounds__(256) prep_kernel(Pack p) {
   else xf.fx = bl2 > br2;
 
   // final local AABBs
-  warp_slices(v, nv, xf, true, Wq, ylo, yhi);
-  warp_slices(v, nv, xf, false, Hq, xlo, xhi);
+  if (xf.fx) {
+#pragma unroll
+    for (int j = 0; j < kSlices; ++j) {
+      const int64_t lo = Wq - xhi[j], hi = Wq - xlo[j];
+      xlo[j] = lo;
+      xhi[j] = hi;
+    }
+    warp_slices(v, nv, xf, true, Wq, ylo, yhi);
+  }
 
   // Sec. 4.1.1 merge: tighten each slice by the other axis' slices
   // (lanes 0..9: x-slices, lanes 16..25: y-slices)

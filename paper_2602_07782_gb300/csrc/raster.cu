@@ -5,115 +5,39 @@
 //   * per padded column i (w' = w + 2g of them): Top'(i) | Bot'(i) << 16,
 //   * per padded row r (h' = h + 2g of them):   L'(r) | R'(r) << 16,
 // packed as uint32 into that scale's envelope pool, plus the chart's padded
-// size and maximum bottom.  Lane l of chunk t handles raw column 32t + l:
-// the local-AABB pieces meeting the open column interval give one bound, the
-// OBB's boundary lines (minimum at the box corner if the corner falls inside
-// the column, else at the nearer column end) the other; the tighter wins.
+// size and maximum bottom.  The warp first derives the chart's per-scale
+// constants (local-AABB piece ranges, OBB line terms and corners; see
+// raster_math.cuh) lane-parallel into shared memory; lane l of chunk t then
+// handles raw column 32t + l with 32-bit arithmetic.
 // The gutter dilation min/max over raw columns i-2g..i takes the values from
 // lanes l-o of the current chunk or, across the chunk seam, of the previous
 // chunk (kept in registers), so each raw value is computed exactly once.
 //
 // The pool layout is fixed by the sizes at k = 1024 (the largest scale), so
 // one prefix sum serves every candidate.
+#include "raster_math.cuh"
 #include "tabi_internal.cuh"
 
 namespace tabi {
 namespace {
 
 constexpr int32_t kBig = 0x3fffffff;
+constexpr int kRasterThreads = 256;
+constexpr int kRasterWarps = kRasterThreads / 32;
 
-// Raw bounds of column c (axis = 0) or row c (axis = 1) at scale k.
-// Column: lo = TopEdge, hi = BottomEdge.  Row: lo = left, hi = right.
-__device__ __forceinline__ void raw_bounds(const ChartShape &sh, int64_t k, int64_t c, int axis,
-                                           uint32_t flags, int64_t len_other, int32_t &lo_out,
-                                           int32_t &hi_out) {
-  const int64_t ext = axis == 0 ? sh.Wq : sh.Hq;  // extent along the scanned axis
-  const int64_t a = c * kFix;
-  const int64_t b = min((c + 1) * kFix, ext * k);
-  int64_t lo = 0, hi = len_other;
-  if (flags & TABI_F_LAABB) {
-    int64_t pl = 0x7fffffffffffffffLL, ph = -0x7fffffffffffffffLL;
-#pragma unroll
-    for (int i = 0; i < kSlices; ++i) {
-      const int64_t s0 = (int64_t)i * ext / kSlices * k, s1 = (int64_t)(i + 1) * ext / kSlices * k;
-      if (s0 < b && s1 > a) {
-        const int64_t l = axis == 0 ? sh.tlo[i] : sh.llo[i];
-        const int64_t h = axis == 0 ? sh.bhi[i] : sh.rhi[i];
-        pl = l < pl ? l : pl;
-        ph = h > ph ? h : ph;
-      }
-    }
-    lo = max(lo, floor_fix(pl * k));
-    hi = min(hi, ceil_fix(ph * k));
-  }
-  if ((flags & TABI_F_OBB) && sh.m > 0) {
-    const int64_t C = kObbCos[sh.m], S = kObbSin[sh.m];
-    const int64_t N = C * C + S * S;
-    const int64_t U0 = sh.u0 * k, U1 = sh.u1 * k, V0 = sh.v0 * k, V1 = sh.v1 * k;
-    const int64_t aN = a * N, bN = b * N;
-    if (axis == 0) {
-      // top: y(X) = max((U0 - X C)/S, (V0 + X S)/C); corner u = U0, v = V0
-      const int64_t xc = U0 * C - V0 * S;
-      int64_t t;
-      if (aN <= xc && xc <= bN) {
-        t = floor_div(U0 * S + V0 * C, N * kFix);
-      } else {
-        const int64_t X = xc < aN ? a : b;
-        t = max(floor_div(U0 - X * C, S * kFix), floor_div(V0 + X * S, C * kFix));
-      }
-      // bottom: y(X) = min((U1 - X C)/S, (V1 + X S)/C); corner u = U1, v = V1
-      const int64_t xb = U1 * C - V1 * S;
-      int64_t bo;
-      if (aN <= xb && xb <= bN) {
-        bo = ceil_div(U1 * S + V1 * C, N * kFix);
-      } else {
-        const int64_t X = xb < aN ? a : b;
-        bo = min(ceil_div(U1 - X * C, S * kFix), ceil_div(V1 + X * S, C * kFix));
-      }
-      lo = max(lo, t);
-      hi = min(hi, bo);
-    } else {
-      // left: x(Y) = max((U0 - Y S)/C, (Y C - V1)/S); corner u = U0, v = V1
-      const int64_t yl = U0 * S + V1 * C;
-      int64_t l;
-      if (aN <= yl && yl <= bN) {
-        l = floor_div(U0 * C - V1 * S, N * kFix);
-      } else {
-        const int64_t Y = yl < aN ? a : b;
-        l = max(floor_div(U0 - Y * S, C * kFix), floor_div(Y * C - V1, S * kFix));
-      }
-      // right: x(Y) = min((U1 - Y S)/C, (Y C - V0)/S); corner u = U1, v = V0
-      const int64_t yr = U1 * S + V0 * C;
-      int64_t r;
-      if (aN <= yr && yr <= bN) {
-        r = ceil_div(U1 * C - V0 * S, N * kFix);
-      } else {
-        const int64_t Y = yr < aN ? a : b;
-        r = min(ceil_div(U1 - Y * S, C * kFix), ceil_div(Y * C - V0, S * kFix));
-      }
-      lo = max(lo, l);
-      hi = min(hi, r);
-    }
-  }
-  // keep each scanline a non-empty interval inside [0, len_other]
-  lo = max((int64_t)0, min(lo, len_other - 1));
-  hi = max(lo + 1, min(hi, len_other));
-  lo_out = (int32_t)lo;
-  hi_out = (int32_t)hi;
-}
-
-// One axis of one chart: raw scanlines 0..len-1, padded 0..len+2g-1.
-__device__ __forceinline__ int32_t warp_axis(const ChartShape &sh, int64_t k, int axis, int64_t len,
-                                             int64_t len_other, int g, uint32_t flags,
-                                             uint32_t *__restrict__ dst) {
+// One axis of one chart: raw scanlines 0..len-1 from the per-warp constants,
+// padded scanlines 0..len+2g-1 written to dst.  Returns max upper' (axis 0:
+// the chart's deepest padded BottomEdge).
+__device__ __forceinline__ int32_t warp_axis(const rmath::AxisK &ak, int g, uint32_t *__restrict__ dst) {
   const int lane = threadIdx.x & 31;
-  const int64_t padded = len + 2 * g;
+  const int32_t len = ak.len;
+  const int32_t padded = len + 2 * g;
   int32_t prev_lo = kBig, prev_hi = -kBig;
   int32_t maxhi = 0;
-  for (int64_t base = 0; base < padded; base += 32) {
-    const int64_t c = base + lane;
+  for (int32_t base = 0; base < padded; base += 32) {
+    const int32_t c = base + lane;
     int32_t lo = kBig, hi = -kBig;
-    if (c < len) raw_bounds(sh, k, c, axis, flags, len_other, lo, hi);
+    if (c < len) rmath::scanline(ak, c, lo, hi);
     int32_t dlo = lo, dhi = hi;
     for (int o = 1; o <= 2 * g; ++o) {
       const int32_t clo = __shfl_sync(0xffffffffu, lo, (lane - o) & 31);
@@ -135,8 +59,9 @@ __device__ __forceinline__ int32_t warp_axis(const ChartShape &sh, int64_t k, in
   return warp_max(maxhi);
 }
 
-__global__ void __launch_bounds__(256) raster_kernel(Pack p, int j_lo, int nj) {
-  const int lane = threadIdx.x & 31;
+__global__ void __launch_bounds__(kRasterThreads, 4) raster_kernel(Pack p, int j_lo, int nj) {
+  __shared__ rmath::AxisK axk[kRasterWarps][2];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t n = p.n;
   if (gw >= n * nj) return;
@@ -145,17 +70,31 @@ __global__ void __launch_bounds__(256) raster_kernel(Pack p, int j_lo, int nj) {
   const int j = j_lo + (int)(gw / n);
   const int s = (int)(gw % n);
   const int64_t k = 16 * (j + 1);
-  const ChartShape sh = p.shape[s];
-  const int64_t w = (sh.Wq * k + kFix - 1) >> 18, h = (sh.Hq * k + kFix - 1) >> 18;
+  const ChartShape &sh = p.shape[s];
+  const bool use_l = (p.flags & TABI_F_LAABB) != 0, use_o = (p.flags & TABI_F_OBB) != 0;
+  // per-(chart, scale) constants, lane-parallel: lanes 0-9 column pieces,
+  // 10-19 row pieces, 20/21 the OBB terms of each axis
+  rmath::AxisK &a0 = axk[wib][0], &a1 = axk[wib][1];
+  if (lane < rmath::kK) {
+    rmath::setup_piece(a0, lane, sh.Wq, k, sh.tlo[lane], sh.bhi[lane]);
+  } else if (lane < 2 * rmath::kK) {
+    const int i = lane - rmath::kK;
+    rmath::setup_piece(a1, i, sh.Hq, k, sh.llo[i], sh.rhi[i]);
+  } else if (lane < 2 * rmath::kK + 2) {
+    const int m = sh.m;
+    rmath::setup_obb(lane == 2 * rmath::kK ? a0 : a1, lane - 2 * rmath::kK, sh.Wq, sh.Hq, k, m,
+                     kObbCos[m], kObbSin[m], sh.u0, sh.u1, sh.v0, sh.v1, use_l, use_o);
+  }
+  __syncwarp();
   const int32_t off = p.env_off[2 * s], wcap = p.env_off[2 * s + 1];
   const int g = p.g;
   uint32_t *base = p.pool + (int64_t)j * p.pool_stride + off;
-  const int32_t maxbot = warp_axis(sh, k, 0, w, h, g, p.flags, base);
-  warp_axis(sh, k, 1, h, w, g, p.flags, base + wcap);
+  const int32_t maxbot = warp_axis(a0, g, base);
+  warp_axis(a1, g, base + wcap);
   if (lane == 0) {
     int32_t *m = p.meta + ((int64_t)j * n + s) * 4;
-    m[0] = (int32_t)(w + 2 * g);
-    m[1] = (int32_t)(h + 2 * g);
+    m[0] = a0.len + 2 * g;
+    m[1] = a1.len + 2 * g;
     m[2] = off;
     m[3] = maxbot;
   }

@@ -1,0 +1,167 @@
+// Per-scanline envelope arithmetic of the rasterizer (App. A "Parallel
+// Pushing Algorithm"), shared by the raster kernel and usable on the host.
+//
+// A scanline is a texel column (axis 0: TopEdge/BottomEdge over x in
+// (cF, (c+1)F)) or a texel row (axis 1: left/right extents over y), in
+// scaled units (F = 2^18 per texel, scaled coordinate = Q.8 * k).
+//
+// OBB boundaries.  Each side of the box is the max (or min) of two lines.
+// With generic constants (A1, A2, B1, B2 scaled by k; b1, b2 the line
+// slopes' numerators; d1, d2 their denominators, all from C_m, S_m):
+//   lower(X) = max( floor((A1 - X b1) / (d1 F)), floor((A2 + X b2) / (d2 F)) )
+//   upper(X) = min( -floor((B1 + X b1) / (d1 F)), -floor((B2 - X b2) / (d2 F)) )
+//   axis 0: A1 = U0, b1 = C, d1 = S, A2 = V0, b2 = S, d2 = C, B1 = -U1, B2 = -V1
+//   axis 1: A1 = U0, b1 = S, d1 = C, A2 = -V1, b2 = C, d2 = S, B1 = -U1, B2 = V0
+// At a scanline boundary X = cF the F cancels:  floor((A - c b F)/(d F)) =
+// floor((floor(A / F) - c b) / d), because adding the remainder (a fraction
+// in [0, 1)) to an integer numerator never changes a floor by a positive
+// integer d.  All such numerators fit 32 bits (|A|/F < 2^28, c b < 2^27), so
+// the per-scanline work is 32-bit; only a scanline clipped by the chart's
+// end (X = ext * k, not a multiple of F) uses the 64-bit form.
+// Lower is convex and upper concave in X, so over [a, b] each reaches its
+// extreme at the box corner when the corner lies in [a, b], else at the
+// nearer end; the corner's position is kept as floor/ceil(pos / N),
+// N = C^2 + S^2, which decides both tests exactly for integer a, b.
+#pragma once
+
+#include <stdint.h>
+
+#if defined(__CUDACC__)
+#define TABI_HD __host__ __device__ __forceinline__
+#else
+#define TABI_HD inline
+#endif
+
+namespace tabi {
+namespace rmath {
+
+constexpr int kK = 10;
+constexpr int64_t kF = 1LL << 18;
+constexpr int32_t kInf = 0x3fffffff;
+
+struct AxisK {
+  // local-AABB pieces: scanline range [plo, phi] and scaled bounds
+  int32_t plo[kK], phi[kK], lo[kK], hi[kK];
+  // OBB, fast path (X = multiple of F)
+  int32_t ah1, ah2, bh1, bh2;   // floor(A1/F), floor(A2/F), floor(B1/F), floor(B2/F)
+  int32_t b1, b2, d1, d2;
+  int32_t corner_lo, corner_hi; // extreme values at the corners
+  int32_t len, len_other, use_l, use_o;
+  int64_t plo_f, plo_c, phi_f, phi_c;  // floor/ceil(corner position / N)
+  int64_t end;                         // ext * k
+  int64_t A1, A2, B1, B2;              // 64-bit form for the clipped scanline
+};
+
+TABI_HD int64_t fdiv64(int64_t a, int64_t b) {  // floor, b > 0
+  int64_t q = a / b;
+  if ((a % b) != 0 && a < 0) --q;
+  return q;
+}
+TABI_HD int32_t fdiv32(int32_t a, int32_t b) {  // floor, b > 0
+  int32_t q = a / b;
+  if ((a % b) != 0 && a < 0) --q;
+  return q;
+}
+TABI_HD int64_t imin64(int64_t a, int64_t b) { return a < b ? a : b; }
+TABI_HD int64_t imax64(int64_t a, int64_t b) { return a > b ? a : b; }
+TABI_HD int32_t imin32(int32_t a, int32_t b) { return a < b ? a : b; }
+TABI_HD int32_t imax32(int32_t a, int32_t b) { return a > b ? a : b; }
+
+// Setup item i < kK: local-AABB piece i of `axis`.  `ext` = Wq (axis 0) or
+// Hq (axis 1); `lo_q8`, `hi_q8` = the refined piece bounds (tlo/bhi or
+// llo/rhi).
+TABI_HD void setup_piece(AxisK &ak, int i, int64_t ext, int64_t k, int32_t lo_q8, int32_t hi_q8) {
+  const int64_t s0 = (int64_t)i * ext / kK * k, s1 = (int64_t)(i + 1) * ext / kK * k;
+  ak.plo[i] = (int32_t)(s0 >> 18);               // floor(s0 / F)
+  ak.phi[i] = (int32_t)((s1 + kF - 1) >> 18) - 1; // ceil(s1 / F) - 1
+  ak.lo[i] = (int32_t)(((int64_t)lo_q8 * k) >> 18);
+  ak.hi[i] = (int32_t)(((int64_t)hi_q8 * k + kF - 1) >> 18);
+}
+
+// Setup of the OBB constants of `axis` (C, S of the chart's angle; u0..v1
+// its strips) and of the scanline counts.
+TABI_HD void setup_obb(AxisK &ak, int axis, int64_t Wq, int64_t Hq, int64_t k, int m, int64_t C, int64_t S,
+                       int64_t u0, int64_t u1, int64_t v0, int64_t v1, bool use_l, bool use_o) {
+  const int64_t w = (Wq * k + kF - 1) >> 18, h = (Hq * k + kF - 1) >> 18;
+  ak.len = (int32_t)(axis == 0 ? w : h);
+  ak.len_other = (int32_t)(axis == 0 ? h : w);
+  ak.end = (axis == 0 ? Wq : Hq) * k;
+  ak.use_l = use_l;
+  ak.use_o = use_o && m > 0;
+  if (!ak.use_o) return;
+  const int64_t U0 = u0 * k, U1 = u1 * k, V0 = v0 * k, V1 = v1 * k, N = C * C + S * S;
+  int64_t posL, posH;
+  if (axis == 0) {
+    ak.A1 = U0; ak.A2 = V0; ak.B1 = -U1; ak.B2 = -V1;
+    ak.b1 = (int32_t)C; ak.d1 = (int32_t)S; ak.b2 = (int32_t)S; ak.d2 = (int32_t)C;
+    posL = U0 * C - V0 * S;   // lower corner u = U0, v = V0
+    posH = U1 * C - V1 * S;   // upper corner u = U1, v = V1
+    ak.corner_lo = (int32_t)fdiv64(U0 * S + V0 * C, N * kF);
+    ak.corner_hi = (int32_t)-fdiv64(-(U1 * S + V1 * C), N * kF);
+  } else {
+    ak.A1 = U0; ak.A2 = -V1; ak.B1 = -U1; ak.B2 = V0;
+    ak.b1 = (int32_t)S; ak.d1 = (int32_t)C; ak.b2 = (int32_t)C; ak.d2 = (int32_t)S;
+    posL = U0 * S + V1 * C;   // lower corner u = U0, v = V1
+    posH = U1 * S + V0 * C;   // upper corner u = U1, v = V0
+    ak.corner_lo = (int32_t)fdiv64(U0 * C - V1 * S, N * kF);
+    ak.corner_hi = (int32_t)-fdiv64(-(U1 * C - V0 * S), N * kF);
+  }
+  ak.ah1 = (int32_t)(ak.A1 >> 18); ak.ah2 = (int32_t)(ak.A2 >> 18);
+  ak.bh1 = (int32_t)(ak.B1 >> 18); ak.bh2 = (int32_t)(ak.B2 >> 18);
+  ak.plo_f = fdiv64(posL, N); ak.plo_c = -fdiv64(-posL, N);
+  ak.phi_f = fdiv64(posH, N); ak.phi_c = -fdiv64(-posH, N);
+}
+
+// Lower / upper OBB bound at X = q F (fast) or X = end (clipped, 64-bit).
+TABI_HD int32_t obb_lower_at(const AxisK &ak, int32_t q, bool clipped) {
+  if (!clipped)
+    return imax32(fdiv32(ak.ah1 - q * ak.b1, ak.d1), fdiv32(ak.ah2 + q * ak.b2, ak.d2));
+  const int64_t X = ak.end;
+  return (int32_t)imax64(fdiv64(ak.A1 - X * ak.b1, (int64_t)ak.d1 * kF),
+                         fdiv64(ak.A2 + X * ak.b2, (int64_t)ak.d2 * kF));
+}
+TABI_HD int32_t obb_upper_at(const AxisK &ak, int32_t q, bool clipped) {
+  if (!clipped)
+    return imin32(-fdiv32(ak.bh1 + q * ak.b1, ak.d1), -fdiv32(ak.bh2 - q * ak.b2, ak.d2));
+  const int64_t X = ak.end;
+  return (int32_t)imin64(-fdiv64(ak.B1 + X * ak.b1, (int64_t)ak.d1 * kF),
+                         -fdiv64(ak.B2 - X * ak.b2, (int64_t)ak.d2 * kF));
+}
+
+// Raw bounds of scanline c (0 <= c < len): [lo, hi) with hi > lo.
+TABI_HD void scanline(const AxisK &ak, int32_t c, int32_t &lo_out, int32_t &hi_out) {
+  int32_t lo = 0, hi = ak.len_other;
+  if (ak.use_l) {
+    int32_t pl = kInf, ph = -kInf;
+#pragma unroll
+    for (int i = 0; i < kK; ++i)
+      if (ak.plo[i] <= c && c <= ak.phi[i]) {
+        pl = imin32(pl, ak.lo[i]);
+        ph = imax32(ph, ak.hi[i]);
+      }
+    lo = imax32(lo, pl);
+    hi = imin32(hi, ph);
+  }
+  if (ak.use_o) {
+    const int64_t a = (int64_t)c * kF;
+    const int64_t bfull = a + kF;
+    const bool clip = bfull > ak.end;
+    const int64_t b = clip ? ak.end : bfull;
+    int32_t tl, th;
+    if (a <= ak.plo_f && ak.plo_c <= b) tl = ak.corner_lo;
+    else if (ak.plo_f < a) tl = obb_lower_at(ak, c, false);
+    else tl = obb_lower_at(ak, c + 1, clip);
+    if (a <= ak.phi_f && ak.phi_c <= b) th = ak.corner_hi;
+    else if (ak.phi_f < a) th = obb_upper_at(ak, c, false);
+    else th = obb_upper_at(ak, c + 1, clip);
+    lo = imax32(lo, tl);
+    hi = imin32(hi, th);
+  }
+  lo = imax32(0, imin32(lo, ak.len_other - 1));
+  hi = imax32(lo + 1, imin32(hi, ak.len_other));
+  lo_out = lo;
+  hi_out = hi;
+}
+
+}  // namespace rmath
+}  // namespace tabi

@@ -11,9 +11,9 @@
 //      evaluated as a warp scan of 2x2 max-plus matrices.  A fold from the
 //      same first chart serves both the atlas width and the knee width.
 //      Other warps clear the offsets of the previous row;
-//   D  push: every (configuration, chart, column) item computes
-//      front[x] - TopEdge and the per-chart maxima are formed with a
-//      segmented warp reduction and one shared atomicMax per segment;
+//   D  push: one warp per chart loads its TopEdge once (both orientations)
+//      and forms, for every configuration the chart is part of, the maximum
+//      of front[x] - TopEdge over its columns;
 //   E  per configuration (one warp each) the interlock fixpoint of
 //      Algorithm 2 -- the least solution is, per chart, the maximum pushed
 //      offset over the charts chained to it, i.e. a forward and a backward
@@ -21,7 +21,8 @@
 //      maximum is max(committed maximum, max_c (y_c + max BottomEdge_c)),
 //      so configurations never copy the frontline;
 //   G  selection (Sec. 4.2) and knee detection (App. A) by warp 0;
-//   H  commit: frontline update with shared atomicMax, placements out.
+//   H  commit: one warp per chart raises the frontline (shared atomicMax,
+//      since compacted neighbours share columns); placements out.
 #include "tabi_internal.cuh"
 
 namespace tabi {
@@ -112,8 +113,7 @@ __global__ void __launch_bounds__(kNT) rowloop_kernel(Pack p, int j_lo, int maxr
   int32_t *posN = front + wp_pad;       // [maxrow] side by side
   int32_t *posH = posN + maxrow;        // [maxrow] compacted
   int32_t *yb = posH + maxrow;          // [8][maxrow]
-  int32_t *wpre = yb + 8 * maxrow;      // [maxrow + 4] prefix of widths
-  int32_t *wps = wpre + maxrow + 4;     // [maxrow] w'
+  int32_t *wps = yb + 8 * maxrow;       // [maxrow] w'
   int32_t *mbot = wps + maxrow;         // [maxrow] max BottomEdge
   int32_t *woff = mbot + maxrow;        // [maxrow] pool offset
   __shared__ Ctl ctl;
@@ -125,7 +125,6 @@ __global__ void __launch_bounds__(kNT) rowloop_kernel(Pack p, int j_lo, int maxr
   int4 *place = p.place + (int64_t)j * n;
 
   for (int x = tid; x < wp_pad; x += kNT) front[x] = 0;
-  for (int x = tid; x < 8 * maxrow; x += kNT) yb[x] = 0;
   if (tid == 0) {
     ctl.row_start = 0; ctl.row = 0; ctl.committed = 0; ctl.fail = 0;
     ctl.prev_ltr = 0; ctl.prev_maxlen = 0; ctl.knee_valid = 0;
@@ -174,7 +173,7 @@ __global__ void __launch_bounds__(kNT) rowloop_kernel(Pack p, int j_lo, int maxr
         const int32_t foldK = knee ? ctl.region_hi - ctl.region_lo : -1;
         int32_t *pos = hc ? posH : posN;
         MP carry{0, kNeg, kNeg, 0};  // identity
-        int32_t carry_x = 0, carry_wprev = kNeg, carry_wsum = 0;
+        int32_t carry_x = 0, carry_wprev = kNeg;
         bool doneF = false, doneK = !knee;
         for (int t0 = 0; !(doneF && doneK); t0 += 32) {
           const int t = t0 + lane;
@@ -219,21 +218,10 @@ __global__ void __launch_bounds__(kNT) rowloop_kernel(Pack p, int j_lo, int maxr
           if (!doneK && overK) { lenK = t0 + __ffs(overK) - 1; doneK = true; }
           else if (!doneK) lenK = t0 + 32;
           if (valid && room) pos[t] = xt;
-          if (longest) {
-            int32_t incl = w;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-              const int32_t u = __shfl_up_sync(0xffffffffu, incl, o);
-              if (lane >= o) incl += u;
-            }
-            if (valid && room) {
-              wpre[t + 1] = carry_wsum + incl;
-              wps[t] = w;
-              mbot[t] = meta[(int64_t)s * 4 + 3];
-              woff[t] = meta[(int64_t)s * 4 + 2];
-            }
-            if (t == 0) wpre[0] = 0;
-            carry_wsum += __shfl_sync(0xffffffffu, incl, 31);
+          if (longest && valid && room) {  // the row window, shared by all configurations
+            wps[t] = w;
+            mbot[t] = meta[(int64_t)s * 4 + 3];
+            woff[t] = meta[(int64_t)s * 4 + 2];
           }
           carry_x = __shfl_sync(0xffffffffu, xnext, 31);
           carry_wprev = __shfl_sync(0xffffffffu, w, 31);
@@ -252,10 +240,6 @@ __global__ void __launch_bounds__(kNT) rowloop_kernel(Pack p, int j_lo, int maxr
         ctl.len[hc] = active ? lenF : 0;
         ctl.len[2 + hc] = (active && knee) ? lenK : 0;
       }
-    } else {
-      // clear the offsets left by the previous row
-      const int clear = ctl.prev_maxlen;
-      for (int x = tid - 64; x < 8 * clear; x += kNT - 64) yb[(x / clear) * maxrow + x % clear] = 0;
     }
     __syncthreads();
     if (ctl.len[0] == 0) {  // a chart wider than the atlas: this scale fails
@@ -264,39 +248,41 @@ __global__ void __launch_bounds__(kNT) rowloop_kernel(Pack p, int j_lo, int maxr
     }
 
     // ---- D: push ----------------------------------------------------------
-    for (int cfg = 0; cfg < 8; ++cfg) {
-      const int v = cfg >> 1, dir = cfg & 1, fold = v >> 1, hc = v & 1;
-      const int len = ctl.len[v];
-      if (len == 0) continue;
-      const int32_t lo = fold ? ctl.region_lo : 0, hi = fold ? ctl.region_hi : Wp;
-      const int32_t *pos = hc ? posH : posN;
-      const int32_t total = wpre[len];
-      int32_t *y = yb + cfg * maxrow;
-      for (int base = 0; base < total; base += kNT) {
-        const int f = base + tid;
-        int32_t key = -1, val = kI32Min;
-        if (f < total) {
-          int lo_t = 0, hi_t = len - 1;  // largest t with wpre[t] <= f
-          while (lo_t < hi_t) {
-            const int mid = (lo_t + hi_t + 1) >> 1;
-            if (wpre[mid] <= f) lo_t = mid; else hi_t = mid - 1;
-          }
-          const int t = lo_t, i = f - wpre[t], w = wps[t];
-          const int32_t X = dir ? hi - pos[t] - w : lo + pos[t];
-          const int ti = dir ? w - 1 - i : i;
-          const int32_t top = (int32_t)(pool[woff[t] + ti] & 0xffffu);
-          key = t;
-          val = front[X + i] - top;
-        }
-        // per-chart maximum over consecutive lanes, one atomic per segment
+    // warp per chart: its TopEdge (and the mirrored one) is loaded once and
+    // shared by every configuration the chart takes part in
+    {
+      const int maxlen = max(max(ctl.len[0], ctl.len[1]), max(ctl.len[2], ctl.len[3]));
+      for (int t = warp; t < maxlen; t += kNW) {
+        const int w = wps[t];
+        const uint32_t *col = pool + woff[t];
+        int32_t X[8];
+        bool on[8];
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const int32_t u = __shfl_down_sync(0xffffffffu, val, o);
-          const int32_t uk = __shfl_down_sync(0xffffffffu, key, o);
-          if (lane + o < 32 && uk == key) val = max(val, u);
+        for (int cfg = 0; cfg < 8; ++cfg) {
+          const int v = cfg >> 1, dir = cfg & 1, fold = v >> 1, hc = v & 1;
+          on[cfg] = t < ctl.len[v];
+          const int32_t lo = fold ? ctl.region_lo : 0, hi = fold ? ctl.region_hi : Wp;
+          const int32_t ps = (hc ? posH : posN)[t];
+          X[cfg] = dir ? hi - ps - w : lo + ps;
         }
-        const int32_t kprev = __shfl_up_sync(0xffffffffu, key, 1);
-        if (key >= 0 && (lane == 0 || kprev != key)) atomicMax(&y[key], val);
+        int32_t acc[8];
+#pragma unroll
+        for (int cfg = 0; cfg < 8; ++cfg) acc[cfg] = 0;  // offsets start at 0 (the atlas top)
+        for (int base = 0; base < w; base += 32) {
+          const int i = base + lane;
+          if (i < w) {
+            const int32_t tf = (int32_t)(col[i] & 0xffffu);
+            const int32_t tr = (int32_t)(col[w - 1 - i] & 0xffffu);
+#pragma unroll
+            for (int cfg = 0; cfg < 8; ++cfg)
+              if (on[cfg]) acc[cfg] = max(acc[cfg], front[X[cfg] + i] - ((cfg & 1) ? tr : tf));
+          }
+        }
+#pragma unroll
+        for (int cfg = 0; cfg < 8; ++cfg) {
+          const int32_t m = warp_max(acc[cfg]);
+          if (on[cfg] && lane == 0) yb[cfg * maxrow + t] = m;
+        }
       }
     }
     __syncthreads();
@@ -421,18 +407,15 @@ __global__ void __launch_bounds__(kNT) rowloop_kernel(Pack p, int j_lo, int maxr
       const int32_t lo = fold ? ctl.region_lo : 0, hi = fold ? ctl.region_hi : Wp;
       const int32_t *pos = hc ? posH : posN;
       const int32_t *y = yb + best * maxrow;
-      const int32_t total = wpre[len];
-      for (int f = tid; f < total; f += kNT) {
-        int lo_t = 0, hi_t = len - 1;
-        while (lo_t < hi_t) {
-          const int mid = (lo_t + hi_t + 1) >> 1;
-          if (wpre[mid] <= f) lo_t = mid; else hi_t = mid - 1;
-        }
-        const int t = lo_t, i = f - wpre[t], w = wps[t];
+      for (int t = warp; t < len; t += kNW) {
+        const int w = wps[t];
+        const uint32_t *col = pool + woff[t];
         const int32_t X = dir ? hi - pos[t] - w : lo + pos[t];
-        const int ti = dir ? w - 1 - i : i;
-        const int32_t bot = (int32_t)(pool[woff[t] + ti] >> 16);
-        atomicMax(&front[X + i], y[t] + bot);
+        const int32_t yt = y[t];
+        for (int i = lane; i < w; i += 32) {
+          const int32_t bot = (int32_t)(col[dir ? w - 1 - i : i] >> 16);
+          atomicMax(&front[X + i], yt + bot);
+        }
       }
       const int row = ctl.row;
       const int bits = dir | (hc << 1) | (fold << 2);
@@ -481,14 +464,14 @@ static int rowloop_maxrow(int W, int g) {
 size_t rowloop_smem_bytes(int W, int g) {
   const int Wp = W + 2 * g;
   const int wp_pad = (Wp + 3) & ~3;
-  return sizeof(int32_t) * ((size_t)wp_pad + 14 * (size_t)rowloop_maxrow(W, g) + 4) + sizeof(Ctl);
+  return sizeof(int32_t) * ((size_t)wp_pad + 13 * (size_t)rowloop_maxrow(W, g)) + sizeof(Ctl);
 }
 
 cudaError_t launch_rowloop(const Pack &p, int j_lo, int j_hi, cudaStream_t st) {
   const int Wp = p.W + 2 * p.g;
   const int wp_pad = (Wp + 3) & ~3;
   const int maxrow = rowloop_maxrow(p.W, p.g);
-  const size_t smem = sizeof(int32_t) * ((size_t)wp_pad + 14 * (size_t)maxrow + 4);
+  const size_t smem = sizeof(int32_t) * ((size_t)wp_pad + 13 * (size_t)maxrow);
   cudaError_t e = cudaFuncSetAttribute(rowloop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   rowloop_kernel<<<j_hi - j_lo + 1, kNT, smem, st>>>(p, j_lo, maxrow, wp_pad);
