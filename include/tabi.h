@@ -55,7 +55,7 @@ typedef enum tabi_status {
                                (-2^20, 2^20), atlas side outside [1, 8192],
                                bad params, or an atlas too wide for the
                                gutter (gutter 0 supports widths up to about
-                               4,000 texels, gutter >= 1 every width)       */
+                               3,600 texels, gutter >= 1 every width)       */
   TABI_ERR_NO_FIT = 2,      /* no candidate scale packs every chart          */
   TABI_ERR_OOM = 3,         /* the context arena is too small for this input */
   TABI_ERR_CUDA = 4,        /* a CUDA call failed (see tabi_last_error)      */
@@ -147,13 +147,15 @@ tabi_status tabi_pack_device(tabi_ctx *ctx, const tabi_params *params, int32_t a
  *                        Sec. 4.1.1, App. A);
  *   TABI_INSPECT_PERM    int32[n]: input index of each sorted position;
  *   TABI_INSPECT_ENV     for candidate index `scale` (k = 16*(scale+1)):
- *                        int32[4n] meta (padded width w', padded height h',
- *                        offset, max bottom) then uint32 pool; each column
- *                        entry packs (Top' | Bot' << 16) and each row entry
- *                        (L' | R' << 16); chart s's columns start at
- *                        pool[offset] and its rows at pool[offset + wcap]
- *                        with wcap = meta of TABI_INSPECT_ENV_CAP;
- *   TABI_INSPECT_ENV_CAP int32[2n]: offset and column capacity per chart;
+ *                        int64[2] (column-pool and row-pool strides in
+ *                        entries), int32[4n] meta per sorted chart (padded
+ *                        width w', padded height h', column start, max
+ *                        bottom), the candidate's column pool (uint32,
+ *                        Top' | Bot' << 16 per padded column, chart s from
+ *                        its column start) and its row pool (uint32,
+ *                        L' | R' << 16 per padded row, chart s from its row
+ *                        offset);
+ *   TABI_INSPECT_ENV_CAP int32[2n]: row offset and row capacity per chart;
  *   TABI_INSPECT_PAIRS   int32[n] compacting distance d(s, s+1) then
  *                        uint8[n] flags (bit0 CannotMoveAbove(s, s+1),
  *                        bit1 CannotMoveAbove(s+1, s)) for `scale`;

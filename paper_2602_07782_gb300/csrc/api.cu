@@ -84,6 +84,7 @@ size_t fixed_bytes(int64_t n, int64_t nv) {
   add(4 * n);                    // hq
   add(16 * n);                   // sort ping-pong
   add(8 * n);                    // env_off
+  add((size_t)kScales * 4 * n);  // colstart
   add((size_t)kScales * 16 * n); // meta
   add((size_t)kScales * 4 * n);  // dnext
   add((size_t)kScales * n);      // pflags
@@ -215,6 +216,7 @@ tabi_status run_pack(tabi_ctx *ctx, const tabi_params *params, int32_t W, int32_
   p.hq = cv.take<int32_t>(n);
   p.sort_tmp = cv.take<uint32_t>(4 * (size_t)n);
   p.env_off = cv.take<int32_t>(2 * (size_t)n);
+  p.colstart = cv.take<int32_t>((size_t)kScales * n);
   p.meta = cv.take<int32_t>((size_t)kScales * 4 * n);
   p.dnext = cv.take<int32_t>((size_t)kScales * n);
   p.pflags = cv.take<uint8_t>((size_t)kScales * n);
@@ -224,13 +226,14 @@ tabi_status run_pack(tabi_ctx *ctx, const tabi_params *params, int32_t W, int32_
   p.result = cv.take<PackResult>(1);
   p.err = cv.take<uint32_t>(1);
   tabi_placement *d_out = host ? cv.take<tabi_placement>(n) : out;
-  if (!p.info || !p.shape || !p.place || !p.err || !d_out || (host && (!d_off || !d_verts)))
+  if (!p.info || !p.shape || !p.place || !p.err || !p.colstart || !d_out || (host && (!d_off || !d_verts)))
     return fail(ctx, TABI_ERR_OOM, "arena too small for the per-chart arrays");
   const size_t left = (cv.cap - cv.used) / sizeof(uint32_t);
-  p.pool_stride = (int64_t)(left / kScales) & ~(int64_t)63;
-  p.pool_cap = p.pool_stride;
-  p.pool = reinterpret_cast<uint32_t *>(cv.base + cv.used);
-  if (p.pool_stride < 64) return fail(ctx, TABI_ERR_OOM, "arena too small for the envelope pool");
+  // the rest: half column pools, half row pools, 64 candidates each
+  p.col_stride = p.row_stride = (int64_t)(left / (2 * kScales)) & ~(int64_t)63;
+  p.colpool = reinterpret_cast<uint32_t *>(cv.base + cv.used);
+  p.pool = p.colpool + (int64_t)kScales * p.col_stride;
+  if (p.col_stride < 64) return fail(ctx, TABI_ERR_OOM, "arena too small for the envelope pools");
   p.offsets = host ? d_off : offsets;
   p.verts = host ? d_verts : verts;
   p.out = d_out;
@@ -362,8 +365,10 @@ size_t tabi_arena_bytes(int32_t n, int32_t nv, int32_t W, int32_t H, int64_t sum
                         int32_t gutter) {
   (void)W; (void)H;
   if (n < 1) return 0;
-  const size_t pool = (size_t)kScales * 4 *
-                      ((size_t)sum_extent_texels + (size_t)n * (4 * (size_t)gutter + 2 + 3));
+  // column and row pools get the same share; each must hold the larger of
+  // sum(w') and sum(h') at k = 1024, both below sum_extent + n (2g + 4)
+  const size_t pool = (size_t)kScales * 4 * 2 *
+                      ((size_t)sum_extent_texels + (size_t)n * (2 * (size_t)gutter + 4) + 64);
   return fixed_bytes(n, nv) + pool + (size_t)kScales * 256;
 }
 
@@ -410,34 +415,41 @@ tabi_status tabi_inspect(tabi_ctx *ctx, int32_t what, int32_t scale, void *dst, 
   const Pack &p = ctx->last;
   const size_t n = (size_t)p.n;
   if (scale < 0 || scale >= kScales) return fail(ctx, TABI_ERR_INVALID_ARG, "bad scale index");
-  struct Piece { const void *src; size_t bytes; };
-  Piece pcs[2] = {{nullptr, 0}, {nullptr, 0}};
+  struct Piece { const void *src; size_t bytes; bool host; };
+  const int64_t strides[2] = {p.col_stride, p.row_stride};
+  Piece pcs[4] = {{nullptr, 0, false}, {nullptr, 0, false}, {nullptr, 0, false}, {nullptr, 0, false}};
   switch (what) {
-    case TABI_INSPECT_CHARTS: pcs[0] = {p.info, sizeof(tabi_chart_info) * n}; break;
-    case TABI_INSPECT_PERM: pcs[0] = {p.perm, 4 * n}; break;
+    case TABI_INSPECT_CHARTS: pcs[0] = {p.info, sizeof(tabi_chart_info) * n, false}; break;
+    case TABI_INSPECT_PERM: pcs[0] = {p.perm, 4 * n, false}; break;
     case TABI_INSPECT_ENV:
-      pcs[0] = {p.meta + (int64_t)scale * 4 * n, 16 * n};
-      pcs[1] = {p.pool + (int64_t)scale * p.pool_stride, 4 * (size_t)p.pool_stride};
+      pcs[0] = {strides, sizeof(strides), true};
+      pcs[1] = {p.meta + (int64_t)scale * 4 * n, 16 * n, false};
+      pcs[2] = {p.colpool + (int64_t)scale * p.col_stride, 4 * (size_t)p.col_stride, false};
+      pcs[3] = {p.pool + (int64_t)scale * p.row_stride, 4 * (size_t)p.row_stride, false};
       break;
-    case TABI_INSPECT_ENV_CAP: pcs[0] = {p.env_off, 8 * n}; break;
+    case TABI_INSPECT_ENV_CAP: pcs[0] = {p.env_off, 8 * n, false}; break;
     case TABI_INSPECT_PAIRS:
-      pcs[0] = {p.dnext + (int64_t)scale * n, 4 * n};
-      pcs[1] = {p.pflags + (int64_t)scale * n, (size_t)n};
+      pcs[0] = {p.dnext + (int64_t)scale * n, 4 * n, false};
+      pcs[1] = {p.pflags + (int64_t)scale * n, (size_t)n, false};
       break;
     case TABI_INSPECT_SCALE:
-      pcs[0] = {p.scale_out + scale, sizeof(ScaleOut)};
-      pcs[1] = {p.place + (int64_t)scale * n, 16 * n};
+      pcs[0] = {p.scale_out + scale, sizeof(ScaleOut), false};
+      pcs[1] = {p.place + (int64_t)scale * n, 16 * n, false};
       break;
     default: return fail(ctx, TABI_ERR_INVALID_ARG, "bad inspect selector");
   }
-  *needed = pcs[0].bytes + pcs[1].bytes;
+  *needed = pcs[0].bytes + pcs[1].bytes + pcs[2].bytes + pcs[3].bytes;
   if (!dst || cap < *needed) return fail(ctx, TABI_ERR_INVALID_ARG, "buffer too small");
   cudaSetDevice(ctx->device);
   char *d = (char *)dst;
   for (const Piece &pc : pcs) {
     if (!pc.bytes) continue;
-    const cudaError_t e = cudaMemcpy(d, pc.src, pc.bytes, cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "inspect copy");
+    if (pc.host) {
+      memcpy(d, pc.src, pc.bytes);
+    } else {
+      const cudaError_t e = cudaMemcpy(d, pc.src, pc.bytes, cudaMemcpyDeviceToHost);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "inspect copy");
+    }
     d += pc.bytes;
   }
   return TABI_OK;

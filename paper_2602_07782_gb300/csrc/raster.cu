@@ -5,16 +5,19 @@
 //   * per padded column i (w' = w + 2g of them): Top'(i) | Bot'(i) << 16,
 //   * per padded row r (h' = h + 2g of them):   L'(r) | R'(r) << 16,
 // packed as uint32 into that scale's envelope pool, plus the chart's padded
-// size and maximum bottom.  The warp first derives the chart's per-scale
-// constants (local-AABB piece ranges, OBB line terms and corners; see
-// raster_math.cuh) lane-parallel into shared memory; lane l of chunk t then
+// size and maximum bottom.  One warp walks one chart through a run of
+// consecutive candidates; for each it derives the chart's per-scale
+// constants (local-AABB piece ranges, OBB line terms, and the corners, which
+// are carried incrementally from candidate to candidate; see
+// raster_math.cuh) lane-parallel into shared memory, then lane l of chunk t
 // handles raw column 32t + l with 32-bit arithmetic.
 // The gutter dilation min/max over raw columns i-2g..i takes the values from
 // lanes l-o of the current chunk or, across the chunk seam, of the previous
 // chunk (kept in registers), so each raw value is computed exactly once.
 //
-// The pool layout is fixed by the sizes at k = 1024 (the largest scale), so
-// one prefix sum serves every candidate.
+// Columns go to a per-candidate column pool with the charts back to back
+// (the row loop copies a row's columns in one contiguous range); rows go to
+// a row pool laid out once by the sizes at k = 1024 (the largest scale).
 #include "raster_math.cuh"
 #include "tabi_internal.cuh"
 
@@ -59,62 +62,85 @@ __device__ __forceinline__ int32_t warp_axis(const rmath::AxisK &ak, int g, uint
   return warp_max(maxhi);
 }
 
-__global__ void __launch_bounds__(kRasterThreads, 4) raster_kernel(Pack p, int j_lo, int nj) {
+__global__ void __launch_bounds__(kRasterThreads, 4) raster_kernel(Pack p, int j_lo, int nj, int G) {
   __shared__ rmath::AxisK axk[kRasterWarps][2];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t n = p.n;
-  if (gw >= n * nj) return;
+  const int ngroups = (nj + G - 1) / G;
+  if (gw >= n * ngroups) return;
   if (*(volatile int32_t *)p.found >= 0) return;  // a larger scale already succeeded
   if (*(volatile uint32_t *)p.err) return;        // invalid input or pool overflow: write nothing
-  const int j = j_lo + (int)(gw / n);
-  const int s = (int)(gw % n);
-  const int64_t k = 16 * (j + 1);
+  const int s = (int)(gw / ngroups);
+  const int j0 = j_lo + (int)(gw % ngroups) * G;
+  const int j1 = min(j0 + G, j_lo + nj);
   const ChartShape &sh = p.shape[s];
   const bool use_l = (p.flags & TABI_F_LAABB) != 0, use_o = (p.flags & TABI_F_OBB) != 0;
-  // per-(chart, scale) constants, lane-parallel: lanes 0-9 column pieces,
-  // 10-19 row pieces, 20/21 the OBB terms of each axis
-  rmath::AxisK &a0 = axk[wib][0], &a1 = axk[wib][1];
-  if (lane < rmath::kK) {
-    rmath::setup_piece(a0, lane, sh.Wq, k, sh.tlo[lane], sh.bhi[lane]);
-  } else if (lane < 2 * rmath::kK) {
-    const int i = lane - rmath::kK;
-    rmath::setup_piece(a1, i, sh.Hq, k, sh.llo[i], sh.rhi[i]);
-  } else if (lane < 2 * rmath::kK + 2) {
-    const int m = sh.m;
-    rmath::setup_obb(lane == 2 * rmath::kK ? a0 : a1, lane - 2 * rmath::kK, sh.Wq, sh.Hq, k, m,
-                     kObbCos[m], kObbSin[m], sh.u0, sh.u1, sh.v0, sh.v1, use_l, use_o);
-  }
-  __syncwarp();
-  const int32_t off = p.env_off[2 * s], wcap = p.env_off[2 * s + 1];
+  const int m = sh.m;
+  const int64_t C = kObbCos[m], S = kObbSin[m];
+  const int32_t roff = p.env_off[2 * s];
   const int g = p.g;
-  uint32_t *base = p.pool + (int64_t)j * p.pool_stride + off;
-  const int32_t maxbot = warp_axis(a0, g, base);
-  warp_axis(a1, g, base + wcap);
-  if (lane == 0) {
-    int32_t *m = p.meta + ((int64_t)j * n + s) * 4;
-    m[0] = a0.len + 2 * g;
-    m[1] = a1.len + 2 * g;
-    m[2] = off;
-    m[3] = maxbot;
+  rmath::AxisK &a0 = axk[wib][0], &a1 = axk[wib][1];
+  // lanes 24-31 carry the eight corner quantities across the candidates
+  rmath::CornerQ cq;
+  const bool corner_lane = lane >= 24 && use_o && m > 0;
+  if (corner_lane) rmath::corner_init(cq, lane - 24, 16 * (j0 + 1), 16, C, S, sh.u0, sh.u1, sh.v0, sh.v1);
+  for (int j = j0; j < j1; ++j) {
+    const int64_t k = 16 * (j + 1);
+    // per-(chart, scale) constants, lane-parallel: lanes 0-19 the local-AABB
+    // pieces, lanes 20-21 the OBB line terms, lanes 24-31 the corners
+    if (lane < 2 * rmath::kK) {
+      const int ax = lane >= rmath::kK, i = lane - ax * rmath::kK;
+      rmath::setup_piece(ax ? a1 : a0, i, ax ? sh.Hq : sh.Wq, k, ax ? sh.llo[i] : sh.tlo[i],
+                         ax ? sh.rhi[i] : sh.bhi[i]);
+    } else if (lane < 2 * rmath::kK + 2) {
+      const int ax = lane - 2 * rmath::kK;
+      rmath::setup_obb_base(ax ? a1 : a0, ax, sh.Wq, sh.Hq, k, m, C, S, sh.u0, sh.u1, sh.v0, sh.v1, use_l,
+                            use_o);
+    } else if (corner_lane) {
+      rmath::corner_store(cq, lane - 24, (lane - 24) >> 2 ? a1 : a0);
+      rmath::corner_advance(cq);
+    }
+    __syncwarp();
+    const int32_t cstart = p.colstart[(int64_t)j * n + s];
+    const int32_t maxbot = warp_axis(a0, g, p.colpool + (int64_t)j * p.col_stride + cstart);
+    warp_axis(a1, g, p.pool + (int64_t)j * p.row_stride + roff);
+    if (lane == 0) {
+      int32_t *mt = p.meta + ((int64_t)j * n + s) * 4;
+      mt[0] = a0.len + 2 * g;
+      mt[1] = a1.len + 2 * g;
+      mt[2] = cstart;
+      mt[3] = maxbot;
+    }
+    __syncwarp();
   }
 }
 
-// Pool layout from the sizes at k = 1024 (one CTA; exclusive scan).
+// Pool layouts.  Block j < 64: column offsets of candidate j, charts back to
+// back (exclusive scan of w'(k_j)), so any run of consecutive charts has its
+// columns in one contiguous range.  Block 64: the row pool's offsets from
+// the row counts at k = 1024, rounded to 16-byte segments, shared by every
+// candidate (rows are only read per chart pair).
 __global__ void __launch_bounds__(1024) layout_kernel(Pack p) {
   __shared__ int64_t part[32];
   __shared__ int64_t carry;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int j = blockIdx.x;
+  const bool rows = j == kScales;
+  const int64_t k = 16 * (j + 1);
   if (tid == 0) carry = 0;
   __syncthreads();
   for (int base = 0; base < p.n; base += 1024) {
     const int s = base + tid;
-    int64_t sz = 0, wp = 0;
+    int64_t sz = 0, cap = 0;
     if (s < p.n) {
       const ChartShape &sh = p.shape[s];
-      wp = ((sh.Wq + 255) >> 8) + 2 * p.g;
-      const int64_t hp = ((sh.Hq + 255) >> 8) + 2 * p.g;
-      sz = (wp + hp + 3) & ~3LL;  // 16-byte aligned segments
+      if (rows) {
+        cap = ((sh.Hq + 255) >> 8) + 2 * p.g;
+        sz = (cap + 3) & ~3LL;
+      } else {
+        sz = ((sh.Wq * k + kFix - 1) >> 18) + 2 * p.g;
+      }
     }
     int64_t incl = sz;
 #pragma unroll
@@ -137,14 +163,18 @@ __global__ void __launch_bounds__(1024) layout_kernel(Pack p) {
     __syncthreads();
     const int64_t excl = carry + part[w] + incl - sz;
     if (s < p.n) {
-      p.env_off[2 * s] = (int32_t)excl;
-      p.env_off[2 * s + 1] = (int32_t)wp;
+      if (rows) {
+        p.env_off[2 * s] = (int32_t)excl;
+        p.env_off[2 * s + 1] = (int32_t)cap;
+      } else {
+        p.colstart[(int64_t)j * p.n + s] = (int32_t)excl;
+      }
     }
     __syncthreads();
     if (tid == 1023) carry = excl + sz;
     __syncthreads();
   }
-  if (tid == 0 && carry > p.pool_cap) atomicOr(p.err, kErrPool);
+  if (tid == 0 && carry > (rows ? p.row_stride : p.col_stride)) atomicOr(p.err, kErrPool);
 }
 
 // ---------------------------------------------------------------------------
@@ -182,9 +212,9 @@ __global__ void __launch_bounds__(256) hcompact_kernel(Pack p, int j_lo, int nj)
   }
   const int32_t *ma = p.meta + ps * 4, *mb = ma + 4;
   const int32_t wA = ma[0], hA = ma[1], hB = mb[1];
-  const uint32_t *pool = p.pool + (int64_t)j * p.pool_stride;
-  const uint32_t *rowA = pool + p.env_off[2 * s] + p.env_off[2 * s + 1];
-  const uint32_t *rowB = pool + p.env_off[2 * s + 2] + p.env_off[2 * s + 3];
+  const uint32_t *pool = p.pool + (int64_t)j * p.row_stride;
+  const uint32_t *rowA = pool + p.env_off[2 * s];
+  const uint32_t *rowB = pool + p.env_off[2 * s + 2];
   const int hmin = hA < hB ? hA : hB;
   int32_t M = -kBig;
   for (int r = lane; r < hmin; r += 32) {
@@ -225,13 +255,18 @@ __global__ void __launch_bounds__(256) hcompact_kernel(Pack p, int j_lo, int nj)
 
 }  // namespace
 
-void launch_layout(const Pack &p, cudaStream_t st) { layout_kernel<<<1, 1024, 0, st>>>(p); }
+void launch_layout(const Pack &p, cudaStream_t st) { layout_kernel<<<kScales + 1, 1024, 0, st>>>(p); }
 
 void launch_raster(const Pack &p, int j_lo, int j_hi, cudaStream_t st) {
   const int nj = j_hi - j_lo + 1;
-  const int64_t warps = (int64_t)p.n * nj;
-  const int64_t blocks = (warps * 32 + 255) / 256;
-  raster_kernel<<<(unsigned)blocks, 256, 0, st>>>(p, j_lo, nj);
+  // candidates per warp: enough warps to fill the GPU, as many candidates
+  // per warp as that allows (each warp walks its candidates incrementally)
+  int64_t G = ((int64_t)nj * p.n + 32767) / 32768;
+  G = G < 1 ? 1 : (G > nj ? nj : G);
+  const int64_t groups = (nj + G - 1) / G;
+  const int64_t warps = (int64_t)p.n * groups;
+  const int64_t blocks = (warps * 32 + kRasterThreads - 1) / kRasterThreads;
+  raster_kernel<<<(unsigned)blocks, kRasterThreads, 0, st>>>(p, j_lo, nj, (int)G);
 }
 
 void launch_hcompact(const Pack &p, int j_lo, int j_hi, cudaStream_t st) {

@@ -22,8 +22,19 @@
 // extreme at the box corner when the corner lies in [a, b], else at the
 // nearer end; the corner's position is kept as floor/ceil(pos / N),
 // N = C^2 + S^2, which decides both tests exactly for integer a, b.
+//
+// The 32-bit floor division by d (= C or S, 3196..16384) multiplies by a
+// float reciprocal estimate and corrects the estimate with one exact
+// remainder step: for |numerator| < 2^30 the product is within 0.1 of the
+// true quotient, so the floored estimate is off by at most one.
+//
+// Corner values and positions are linear in k: floor(k num / D).  A warp
+// that walks the candidates k, k+16, ... keeps (q, r) with k num = q D + r,
+// 0 <= r < D, and adds the precomputed (floor(16 num / D), 16 num mod D),
+// carrying one when r overflows -- no division per candidate.
 #pragma once
 
+#include <math.h>
 #include <stdint.h>
 
 #if defined(__CUDACC__)
@@ -40,11 +51,12 @@ constexpr int64_t kF = 1LL << 18;
 constexpr int32_t kInf = 0x3fffffff;
 
 struct AxisK {
-  // local-AABB pieces: scanline range [plo, phi] and scaled bounds
-  int32_t plo[kK], phi[kK], lo[kK], hi[kK];
+  // local-AABB pieces: scanline range plo | phi << 16, scaled bounds lo | hi << 16
+  uint32_t prange[kK], pval[kK];
   // OBB, fast path (X = multiple of F)
   int32_t ah1, ah2, bh1, bh2;   // floor(A1/F), floor(A2/F), floor(B1/F), floor(B2/F)
   int32_t b1, b2, d1, d2;
+  float r1, r2;                 // float reciprocal estimates of d1, d2
   int32_t corner_lo, corner_hi; // extreme values at the corners
   int32_t len, len_other, use_l, use_o;
   int64_t plo_f, plo_c, phi_f, phi_c;  // floor/ceil(corner position / N)
@@ -57,31 +69,36 @@ TABI_HD int64_t fdiv64(int64_t a, int64_t b) {  // floor, b > 0
   if ((a % b) != 0 && a < 0) --q;
   return q;
 }
-TABI_HD int32_t fdiv32(int32_t a, int32_t b) {  // floor, b > 0
-  int32_t q = a / b;
-  if ((a % b) != 0 && a < 0) --q;
-  return q;
-}
 TABI_HD int64_t imin64(int64_t a, int64_t b) { return a < b ? a : b; }
 TABI_HD int64_t imax64(int64_t a, int64_t b) { return a > b ? a : b; }
 TABI_HD int32_t imin32(int32_t a, int32_t b) { return a < b ? a : b; }
 TABI_HD int32_t imax32(int32_t a, int32_t b) { return a > b ? a : b; }
 
-// Setup item i < kK: local-AABB piece i of `axis`.  `ext` = Wq (axis 0) or
-// Hq (axis 1); `lo_q8`, `hi_q8` = the refined piece bounds (tlo/bhi or
-// llo/rhi).
-TABI_HD void setup_piece(AxisK &ak, int i, int64_t ext, int64_t k, int32_t lo_q8, int32_t hi_q8) {
-  const int64_t s0 = (int64_t)i * ext / kK * k, s1 = (int64_t)(i + 1) * ext / kK * k;
-  ak.plo[i] = (int32_t)(s0 >> 18);               // floor(s0 / F)
-  ak.phi[i] = (int32_t)((s1 + kF - 1) >> 18) - 1; // ceil(s1 / F) - 1
-  ak.lo[i] = (int32_t)(((int64_t)lo_q8 * k) >> 18);
-  ak.hi[i] = (int32_t)(((int64_t)hi_q8 * k + kF - 1) >> 18);
+// floor(a / d) for |a| < 2^30, 1 <= d < 2^15, rcp ~ 1/d (float)
+TABI_HD int32_t fdiv32(int32_t a, int32_t d, float rcp) {
+  int32_t q = (int32_t)floorf((float)a * rcp);
+  const int32_t r = a - q * d;
+  if (r < 0) --q;
+  else if (r >= d) ++q;
+  return q;
 }
 
-// Setup of the OBB constants of `axis` (C, S of the chart's angle; u0..v1
-// its strips) and of the scanline counts.
-TABI_HD void setup_obb(AxisK &ak, int axis, int64_t Wq, int64_t Hq, int64_t k, int m, int64_t C, int64_t S,
-                       int64_t u0, int64_t u1, int64_t v0, int64_t v1, bool use_l, bool use_o) {
+// Local-AABB piece i of an axis at scale k.  `ext` = Wq (axis 0) or Hq
+// (axis 1); `lo_q8`, `hi_q8` = the refined piece bounds (tlo/bhi or llo/rhi).
+TABI_HD void setup_piece(AxisK &ak, int i, int64_t ext, int64_t k, int32_t lo_q8, int32_t hi_q8) {
+  const int64_t s0 = (int64_t)i * ext / kK * k, s1 = (int64_t)(i + 1) * ext / kK * k;
+  const uint32_t plo = (uint32_t)(s0 >> 18);                // floor(s0 / F)
+  const uint32_t phi = (uint32_t)(((s1 + kF - 1) >> 18) - 1); // ceil(s1 / F) - 1
+  const uint32_t lo = (uint32_t)(((int64_t)lo_q8 * k) >> 18);
+  const uint32_t hi = (uint32_t)(((int64_t)hi_q8 * k + kF - 1) >> 18);
+  ak.prange[i] = plo | (phi << 16);
+  ak.pval[i] = lo | (hi << 16);
+}
+
+// OBB line terms and scanline counts of one axis at scale k.
+TABI_HD void setup_obb_base(AxisK &ak, int axis, int64_t Wq, int64_t Hq, int64_t k, int m, int64_t C,
+                            int64_t S, int64_t u0, int64_t u1, int64_t v0, int64_t v1, bool use_l,
+                            bool use_o) {
   const int64_t w = (Wq * k + kF - 1) >> 18, h = (Hq * k + kF - 1) >> 18;
   ak.len = (int32_t)(axis == 0 ? w : h);
   ak.len_other = (int32_t)(axis == 0 ? h : w);
@@ -89,40 +106,76 @@ TABI_HD void setup_obb(AxisK &ak, int axis, int64_t Wq, int64_t Hq, int64_t k, i
   ak.use_l = use_l;
   ak.use_o = use_o && m > 0;
   if (!ak.use_o) return;
-  const int64_t U0 = u0 * k, U1 = u1 * k, V0 = v0 * k, V1 = v1 * k, N = C * C + S * S;
-  int64_t posL, posH;
+  const int64_t U0 = u0 * k, U1 = u1 * k, V0 = v0 * k, V1 = v1 * k;
   if (axis == 0) {
     ak.A1 = U0; ak.A2 = V0; ak.B1 = -U1; ak.B2 = -V1;
     ak.b1 = (int32_t)C; ak.d1 = (int32_t)S; ak.b2 = (int32_t)S; ak.d2 = (int32_t)C;
-    posL = U0 * C - V0 * S;   // lower corner u = U0, v = V0
-    posH = U1 * C - V1 * S;   // upper corner u = U1, v = V1
-    ak.corner_lo = (int32_t)fdiv64(U0 * S + V0 * C, N * kF);
-    ak.corner_hi = (int32_t)-fdiv64(-(U1 * S + V1 * C), N * kF);
   } else {
     ak.A1 = U0; ak.A2 = -V1; ak.B1 = -U1; ak.B2 = V0;
     ak.b1 = (int32_t)S; ak.d1 = (int32_t)C; ak.b2 = (int32_t)C; ak.d2 = (int32_t)S;
-    posL = U0 * S + V1 * C;   // lower corner u = U0, v = V1
-    posH = U1 * S + V0 * C;   // upper corner u = U1, v = V0
-    ak.corner_lo = (int32_t)fdiv64(U0 * C - V1 * S, N * kF);
-    ak.corner_hi = (int32_t)-fdiv64(-(U1 * C - V0 * S), N * kF);
   }
+  ak.r1 = 1.0f / (float)ak.d1;
+  ak.r2 = 1.0f / (float)ak.d2;
   ak.ah1 = (int32_t)(ak.A1 >> 18); ak.ah2 = (int32_t)(ak.A2 >> 18);
   ak.bh1 = (int32_t)(ak.B1 >> 18); ak.bh2 = (int32_t)(ak.B2 >> 18);
-  ak.plo_f = fdiv64(posL, N); ak.plo_c = -fdiv64(-posL, N);
-  ak.phi_f = fdiv64(posH, N); ak.phi_c = -fdiv64(-posH, N);
+}
+
+// The eight corner quantities (item = axis * 4 + {0: lower value, 1: upper
+// value, 2: lower position, 3: upper position}): floor(k num / D) with
+//   lower value  num = (axis 0) u0 S + v0 C,  (axis 1) u0 C - v1 S,  D = N F
+//   upper value  num = -((axis 0) u1 S + v1 C, (axis 1) u1 C - v0 S), negated back
+//   lower position num = (axis 0) u0 C - v0 S, (axis 1) u0 S + v1 C,  D = N
+//   upper position num = (axis 0) u1 C - v1 S, (axis 1) u1 S + v0 C,  D = N
+struct CornerQ {
+  int64_t num, D, q, r, qs, rs;
+};
+
+TABI_HD void corner_init(CornerQ &cq, int item, int64_t k0, int64_t step, int64_t C, int64_t S,
+                         int64_t u0, int64_t u1, int64_t v0, int64_t v1) {
+  const int axis = item >> 2, kind = item & 3;
+  const int64_t N = C * C + S * S;
+  int64_t num;
+  switch (kind) {
+    case 0: num = axis == 0 ? u0 * S + v0 * C : u0 * C - v1 * S; break;
+    case 1: num = -(axis == 0 ? u1 * S + v1 * C : u1 * C - v0 * S); break;
+    case 2: num = axis == 0 ? u0 * C - v0 * S : u0 * S + v1 * C; break;
+    default: num = axis == 0 ? u1 * C - v1 * S : u1 * S + v0 * C; break;
+  }
+  cq.num = num;
+  cq.D = kind < 2 ? N * kF : N;
+  cq.q = fdiv64(k0 * num, cq.D);
+  cq.r = k0 * num - cq.q * cq.D;
+  cq.qs = fdiv64(step * num, cq.D);
+  cq.rs = step * num - cq.qs * cq.D;
+}
+
+TABI_HD void corner_advance(CornerQ &cq) {
+  cq.q += cq.qs;
+  cq.r += cq.rs;
+  if (cq.r >= cq.D) { cq.r -= cq.D; cq.q += 1; }
+}
+
+// Store the corner quantity into its axis' constants.
+TABI_HD void corner_store(const CornerQ &cq, int item, AxisK &ak) {
+  switch (item & 3) {
+    case 0: ak.corner_lo = (int32_t)cq.q; break;
+    case 1: ak.corner_hi = (int32_t)-cq.q; break;
+    case 2: ak.plo_f = cq.q; ak.plo_c = cq.q + (cq.r != 0); break;
+    default: ak.phi_f = cq.q; ak.phi_c = cq.q + (cq.r != 0); break;
+  }
 }
 
 // Lower / upper OBB bound at X = q F (fast) or X = end (clipped, 64-bit).
 TABI_HD int32_t obb_lower_at(const AxisK &ak, int32_t q, bool clipped) {
   if (!clipped)
-    return imax32(fdiv32(ak.ah1 - q * ak.b1, ak.d1), fdiv32(ak.ah2 + q * ak.b2, ak.d2));
+    return imax32(fdiv32(ak.ah1 - q * ak.b1, ak.d1, ak.r1), fdiv32(ak.ah2 + q * ak.b2, ak.d2, ak.r2));
   const int64_t X = ak.end;
   return (int32_t)imax64(fdiv64(ak.A1 - X * ak.b1, (int64_t)ak.d1 * kF),
                          fdiv64(ak.A2 + X * ak.b2, (int64_t)ak.d2 * kF));
 }
 TABI_HD int32_t obb_upper_at(const AxisK &ak, int32_t q, bool clipped) {
   if (!clipped)
-    return imin32(-fdiv32(ak.bh1 + q * ak.b1, ak.d1), -fdiv32(ak.bh2 - q * ak.b2, ak.d2));
+    return imin32(-fdiv32(ak.bh1 + q * ak.b1, ak.d1, ak.r1), -fdiv32(ak.bh2 - q * ak.b2, ak.d2, ak.r2));
   const int64_t X = ak.end;
   return (int32_t)imin64(-fdiv64(ak.B1 + X * ak.b1, (int64_t)ak.d1 * kF),
                          -fdiv64(ak.B2 - X * ak.b2, (int64_t)ak.d2 * kF));
@@ -134,11 +187,14 @@ TABI_HD void scanline(const AxisK &ak, int32_t c, int32_t &lo_out, int32_t &hi_o
   if (ak.use_l) {
     int32_t pl = kInf, ph = -kInf;
 #pragma unroll
-    for (int i = 0; i < kK; ++i)
-      if (ak.plo[i] <= c && c <= ak.phi[i]) {
-        pl = imin32(pl, ak.lo[i]);
-        ph = imax32(ph, ak.hi[i]);
+    for (int i = 0; i < kK; ++i) {
+      const uint32_t pr = ak.prange[i];
+      if ((int32_t)(pr & 0xffffu) <= c && c <= (int32_t)(pr >> 16)) {
+        const uint32_t pv = ak.pval[i];
+        pl = imin32(pl, (int32_t)(pv & 0xffffu));
+        ph = imax32(ph, (int32_t)(pv >> 16));
       }
+    }
     lo = imax32(lo, pl);
     hi = imin32(hi, ph);
   }

@@ -7,10 +7,13 @@
 //   A  knee refresh (Algorithm 3) and the concavity's current maximum;
 //   B  folds (Algorithm 4): warp 0 folds side by side, warp 1 with
 //      compaction.  The compacted fold x_{t+1} = max(x_t + w'_t - d_t,
-//      x_{t-1} + w'_{t-1}) is a linear recurrence in the (max,+) semiring,
-//      evaluated as a warp scan of 2x2 max-plus matrices.  A fold from the
-//      same first chart serves both the atlas width and the knee width.
-//      Other warps clear the offsets of the previous row;
+//      x_{t-1} + w'_{t-1}) is a prefix sum wherever the clamp does not
+//      bind; a chunk where it binds is redone as a warp scan of 2x2
+//      (max,+) matrices applied to the carried state (x_t, x_{t-1}).  A
+//      fold from the same first chart serves both the atlas width and the
+//      knee width.  The other warps stage the row window (widths, pool
+//      offsets, deepest bottoms, interlock bits, heights) into shared
+//      memory;
 //   D  push: one warp per chart loads its TopEdge once (both orientations)
 //      and forms, for every configuration the chart is part of, the maximum
 //      of front[x] - TopEdge over its columns;
@@ -20,7 +23,9 @@
 //      segmented max-scan -- and the score.  After the push the frontline's
 //      maximum is max(committed maximum, max_c (y_c + max BottomEdge_c)),
 //      so configurations never copy the frontline;
-//   G  selection (Sec. 4.2) and knee detection (App. A) by warp 0;
+//      Two further warps find the knee candidate (App. A) of both
+//      atlas-width rows meanwhile;
+//   G  selection (Sec. 4.2) by warp 0, which also advances the row state;
 //   H  commit: one warp per chart raises the frontline (shared atomicMax,
 //      since compacted neighbours share columns); placements out.
 #include "tabi_internal.cuh"
@@ -39,7 +44,7 @@ struct Ctl {
   int32_t row_start, row, committed, fail, prev_ltr, best, prev_maxlen;
   int32_t knee_valid, knee_ltr, knee_l, knee_r;
   int32_t region_lo, region_hi, knee_max;
-  int32_t knee_rows, knees, red[kNW];
+  int32_t knee_rows, knees, knee_t[2], stage_lo, stage_hi, red[kNW];
 };
 
 // 2x2 max-plus matrix
@@ -96,7 +101,40 @@ __device__ __forceinline__ int32_t seg_scan_max(int32_t v, bool head) {
   return v;
 }
 
-__global__ void __launch_bounds__(kNT) rowloop_kernel(Pack p, int j_lo, int maxrow, int wp_pad) {
+// Maximum over the warp of each of 8 per-lane values, by halving exchanges:
+// after the xor-16/8/4 steps lane l holds one configuration's partial max
+// (configuration ((l >> 2) & 7), bit-reversed below), finished by xor-2/1.
+// Returns that value; the configuration is reduce8_cfg(lane).
+__device__ __forceinline__ int reduce8_cfg(int lane) {
+  return (((lane >> 4) & 1) << 2) | (((lane >> 3) & 1) << 1) | ((lane >> 2) & 1);
+}
+__device__ __forceinline__ int32_t reduce8_max(const int32_t (&v)[8]) {
+  const int lane = threadIdx.x & 31;
+  int32_t a[4], b[2], c;
+  const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int32_t send = h16 ? v[i] : v[i + 4];
+    const int32_t keep = h16 ? v[i + 4] : v[i];
+    a[i] = max(keep, __shfl_xor_sync(0xffffffffu, send, 16));
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const int32_t send = h8 ? a[i] : a[i + 2];
+    const int32_t keep = h8 ? a[i + 2] : a[i];
+    b[i] = max(keep, __shfl_xor_sync(0xffffffffu, send, 8));
+  }
+  {
+    const int32_t send = h4 ? b[0] : b[1];
+    const int32_t keep = h4 ? b[1] : b[0];
+    c = max(keep, __shfl_xor_sync(0xffffffffu, send, 4));
+  }
+  c = max(c, __shfl_xor_sync(0xffffffffu, c, 2));
+  c = max(c, __shfl_xor_sync(0xffffffffu, c, 1));
+  return c;
+}
+
+__global__ void __launch_bounds__(kNT) rowloop_kernel(Pack p, int j_lo, int maxrow, int wp_pad, int scap) {
   const int j = j_lo + blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   ScaleOut *so = p.scale_out + j;
@@ -108,17 +146,20 @@ __global__ void __launch_bounds__(kNT) rowloop_kernel(Pack p, int j_lo, int maxr
   const bool use_hc = flags & TABI_F_HC;
   const bool balance = flags & TABI_F_BALANCE;
 
-  extern __shared__ int32_t sm[];
-  int32_t *front = sm;                  // [wp_pad]
+  extern __shared__ int4 sm4[];
+  uint32_t *stage = reinterpret_cast<uint32_t *>(sm4);  // [scap] the row's column words
+  int32_t *front = reinterpret_cast<int32_t *>(sm4) + scap;  // [wp_pad]
   int32_t *posN = front + wp_pad;       // [maxrow] side by side
   int32_t *posH = posN + maxrow;        // [maxrow] compacted
   int32_t *yb = posH + maxrow;          // [8][maxrow]
   int32_t *wps = yb + 8 * maxrow;       // [maxrow] w'
   int32_t *mbot = wps + maxrow;         // [maxrow] max BottomEdge
-  int32_t *woff = mbot + maxrow;        // [maxrow] pool offset
+  int32_t *woff = mbot + maxrow;        // [maxrow] column start in the column pool
+  int32_t *pflw = woff + maxrow;        // [maxrow] interlock bits of pair (t, t+1)
+  int32_t *hqw = pflw + maxrow;         // [maxrow] unscaled heights
   __shared__ Ctl ctl;
 
-  const uint32_t *pool = p.pool + (int64_t)j * p.pool_stride;
+  const uint32_t *colp = p.colpool + (int64_t)j * p.col_stride;
   const int32_t *meta = p.meta + (int64_t)j * n * 4;
   const int32_t *dnext = p.dnext + (int64_t)j * n;
   const uint8_t *pfl = p.pflags + (int64_t)j * n;
@@ -133,7 +174,7 @@ __global__ void __launch_bounds__(kNT) rowloop_kernel(Pack p, int j_lo, int maxr
   __syncthreads();
 
   while (true) {
-    const int row_start = ctl.row_start;
+    const int row_start = ctl.row_start, row = ctl.row;
     if (row_start >= n || ctl.fail) break;
 
     // ---- A: knee refresh (Algorithm 3) and the concavity's max -----------
@@ -166,50 +207,63 @@ __global__ void __launch_bounds__(kNT) rowloop_kernel(Pack p, int j_lo, int maxr
     if (warp < 2) {
       const int hc = warp;  // warp 0: side by side, warp 1: compacted
       const bool active = hc == 0 || use_hc;
-      const bool longest = hc == (use_hc ? 1 : 0);
       int32_t lenF = 0, lenK = 0;
       if (active) {
         const int32_t foldF = Wp;
         const int32_t foldK = knee ? ctl.region_hi - ctl.region_lo : -1;
         int32_t *pos = hc ? posH : posN;
-        MP carry{0, kNeg, kNeg, 0};  // identity
-        int32_t carry_x = 0, carry_wprev = kNeg;
+        // state at the chunk start: x of its first chart, x and right edge
+        // of the chart before it (none at the row start)
+        int32_t carry_x = 0, carry_xprev = kNeg, carry_re = kNeg, carry_wprev = kNeg;
         bool doneF = false, doneK = !knee;
+        int32_t w_cur = 0, d_cur = 0;
+        {
+          const int s = row_start + lane;
+          if (s < n) { w_cur = meta[(int64_t)s * 4]; d_cur = hc ? dnext[s] : 0; }
+        }
         for (int t0 = 0; !(doneF && doneK); t0 += 32) {
           const int t = t0 + lane;
           const int s = row_start + t;
           const bool valid = s < n;
           const bool room = t < maxrow;  // the last chunk may run past the row capacity
-          const int32_t w = valid ? meta[(int64_t)s * 4] : 0;
-          int32_t xt, xnext;
-          if (hc) {
-            const int32_t d = valid ? dnext[s] : 0;
-            int32_t wprev = __shfl_up_sync(0xffffffffu, w, 1);
-            if (lane == 0) wprev = carry_wprev;
-            MP m{w - d, (t == 0) ? kNeg : wprev, 0, kNeg};
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-              const MP u = mpshfl_up(m, o);
-              if (lane >= o) m = mpmul(m, u);
-            }
-            const MP full = mpmul(m, carry);
-            xnext = full.a00;  // applied to the start state (x_0, x_-1) = (0, -inf)
-            xt = __shfl_up_sync(0xffffffffu, xnext, 1);
-            if (lane == 0) xt = carry_x;
-            carry.a00 = __shfl_sync(0xffffffffu, full.a00, 31);
-            carry.a01 = __shfl_sync(0xffffffffu, full.a01, 31);
-            carry.a10 = __shfl_sync(0xffffffffu, full.a10, 31);
-            carry.a11 = __shfl_sync(0xffffffffu, full.a11, 31);
-          } else {
-            int32_t incl = w;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-              const int32_t u = __shfl_up_sync(0xffffffffu, incl, o);
-              if (lane >= o) incl += u;
-            }
-            xnext = carry_x + incl;
-            xt = xnext - w;
+          const int32_t w = w_cur, d = d_cur;
+          {  // prefetch the next chunk while this one is scanned
+            const int sn = s + 32;
+            w_cur = sn < n ? meta[(int64_t)sn * 4] : 0;
+            d_cur = (hc && sn < n) ? dnext[sn] : 0;
           }
+          const int32_t a = hc ? w - d : w;  // x_{t+1} = x_t + a_t unless the clamp binds
+          int32_t incl = a;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const int32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += u;
+          }
+          int32_t xnext = carry_x + incl, xt = xnext - a;
+          if (hc) {
+            // clamp: chart t+1 never starts left of chart t-1's right edge
+            int32_t re_prev = __shfl_up_sync(0xffffffffu, xt + w, 1);
+            if (lane == 0) re_prev = carry_re;
+            if (__any_sync(0xffffffffu, valid && xnext < re_prev)) {
+              // the clamp binds in this chunk: (max,+) matrix scan,
+              // state (x_t, x_{t-1}) -> (max(x_t + a_t, x_{t-1} + w_{t-1}), x_t)
+              int32_t wprev = __shfl_up_sync(0xffffffffu, w, 1);
+              if (lane == 0) wprev = carry_wprev;
+              MP m{a, wprev, 0, kNeg};
+#pragma unroll
+              for (int o = 1; o < 32; o <<= 1) {
+                const MP u = mpshfl_up(m, o);
+                if (lane >= o) m = mpmul(m, u);
+              }
+              xnext = max(mpadd(m.a00, carry_x), mpadd(m.a01, carry_xprev));
+              xt = __shfl_up_sync(0xffffffffu, xnext, 1);
+              if (lane == 0) xt = carry_x;
+            }
+            carry_xprev = __shfl_sync(0xffffffffu, xt, 31);
+            carry_re = __shfl_sync(0xffffffffu, xt + w, 31);
+            carry_wprev = __shfl_sync(0xffffffffu, w, 31);
+          }
+          carry_x = __shfl_sync(0xffffffffu, xnext, 31);
           // the first chart that does not fit ends the row
           const unsigned overF = __ballot_sync(0xffffffffu, !valid || xt + w > foldF);
           const unsigned overK = __ballot_sync(0xffffffffu, !valid || xt + w > foldK);
@@ -218,14 +272,7 @@ __global__ void __launch_bounds__(kNT) rowloop_kernel(Pack p, int j_lo, int maxr
           if (!doneK && overK) { lenK = t0 + __ffs(overK) - 1; doneK = true; }
           else if (!doneK) lenK = t0 + 32;
           if (valid && room) pos[t] = xt;
-          if (longest && valid && room) {  // the row window, shared by all configurations
-            wps[t] = w;
-            mbot[t] = meta[(int64_t)s * 4 + 3];
-            woff[t] = meta[(int64_t)s * 4 + 2];
-          }
-          carry_x = __shfl_sync(0xffffffffu, xnext, 31);
-          carry_wprev = __shfl_sync(0xffffffffu, w, 31);
-          if (t0 + 32 >= maxrow && !(doneF && doneK)) {  // cannot happen: rows hold <= W'/3 + 1 charts
+          if (t0 + 32 >= maxrow && !(doneF && doneK)) {  // cannot happen: rows hold <= W'/(2g+1) + 1 charts
             if (lane == 0) atomicOr(p.err, kErrRow);
             doneF = doneK = true;
           }
@@ -240,6 +287,29 @@ __global__ void __launch_bounds__(kNT) rowloop_kernel(Pack p, int j_lo, int maxr
         ctl.len[hc] = active ? lenF : 0;
         ctl.len[2 + hc] = (active && knee) ? lenK : 0;
       }
+    } else {
+      // meanwhile the other warps stage the row window into shared memory:
+      // the column words of the charts from row_start on (contiguous in the
+      // column pool; int4 loads from a 16-byte aligned start), and every
+      // chart that can be in this row's widths, column starts, deepest
+      // bottoms, interlock bits and heights
+      {
+        const int32_t c4 = meta[(int64_t)row_start * 4 + 2] & ~3;
+        const int32_t nw = (int32_t)min((int64_t)scap, p.col_stride - c4) & ~3;
+        const int4 *src = reinterpret_cast<const int4 *>(colp + c4);
+        for (int q = tid - 64; q < nw / 4; q += kNT - 64) sm4[q] = src[q];
+        if (tid == 64) { ctl.stage_lo = c4; ctl.stage_hi = c4 + nw; }
+      }
+      const int spec = min(n - row_start, maxrow);
+      for (int t = tid - 64; t < spec; t += kNT - 64) {
+        const int s = row_start + t;
+        const int4 mt = *reinterpret_cast<const int4 *>(meta + (int64_t)s * 4);
+        wps[t] = mt.x;
+        woff[t] = mt.z;
+        mbot[t] = mt.w;
+        pflw[t] = pfl[s];
+        hqw[t] = p.hq[s];
+      }
     }
     __syncthreads();
     if (ctl.len[0] == 0) {  // a chart wider than the atlas: this scale fails
@@ -249,45 +319,53 @@ __global__ void __launch_bounds__(kNT) rowloop_kernel(Pack p, int j_lo, int maxr
 
     // ---- D: push ----------------------------------------------------------
     // warp per chart: its TopEdge (and the mirrored one) is loaded once and
-    // shared by every configuration the chart takes part in
+    // shared by every configuration the chart takes part in; the per-chart
+    // maxima are warp reductions (one instruction per configuration)
     {
-      const int maxlen = max(max(ctl.len[0], ctl.len[1]), max(ctl.len[2], ctl.len[3]));
+      const int len0 = ctl.len[0], len1 = ctl.len[1], len2 = ctl.len[2], len3 = ctl.len[3];
+      const int maxlen = max(max(len0, len1), max(len2, len3));
+      const int32_t rlo = ctl.region_lo, rhi = ctl.region_hi;
+      const int32_t slo = ctl.stage_lo, shi = ctl.stage_hi;
       for (int t = warp; t < maxlen; t += kNW) {
         const int w = wps[t];
-        const uint32_t *col = pool + woff[t];
+        const int32_t cs = woff[t];
+        const uint32_t *col = (cs >= slo && cs + w <= shi) ? stage + (cs - slo) : colp + cs;
+        const int32_t pn = posN[t], ph = posH[t];
         int32_t X[8];
-        bool on[8];
-#pragma unroll
-        for (int cfg = 0; cfg < 8; ++cfg) {
-          const int v = cfg >> 1, dir = cfg & 1, fold = v >> 1, hc = v & 1;
-          on[cfg] = t < ctl.len[v];
-          const int32_t lo = fold ? ctl.region_lo : 0, hi = fold ? ctl.region_hi : Wp;
-          const int32_t ps = (hc ? posH : posN)[t];
-          X[cfg] = dir ? hi - ps - w : lo + ps;
-        }
+        X[0] = pn;                X[1] = Wp - pn - w;    // full, side by side
+        X[2] = ph;                X[3] = Wp - ph - w;    // full, compacted
+        X[4] = rlo + pn;          X[5] = rhi - pn - w;   // knee, side by side
+        X[6] = rlo + ph;          X[7] = rhi - ph - w;   // knee, compacted
+        const unsigned on = (t < len0 ? 0x03u : 0u) | (t < len1 ? 0x0cu : 0u) |
+                            (t < len2 ? 0x30u : 0u) | (t < len3 ? 0xc0u : 0u);
         int32_t acc[8];
 #pragma unroll
         for (int cfg = 0; cfg < 8; ++cfg) acc[cfg] = 0;  // offsets start at 0 (the atlas top)
         for (int base = 0; base < w; base += 32) {
           const int i = base + lane;
           if (i < w) {
-            const int32_t tf = (int32_t)(col[i] & 0xffffu);
-            const int32_t tr = (int32_t)(col[w - 1 - i] & 0xffffu);
+            const uint32_t f = col[i];
+            const uint32_t r = col[w - 1 - i];
+            const int32_t tf = (int32_t)(f & 0xffffu), tr = (int32_t)(r & 0xffffu);
 #pragma unroll
             for (int cfg = 0; cfg < 8; ++cfg)
-              if (on[cfg]) acc[cfg] = max(acc[cfg], front[X[cfg] + i] - ((cfg & 1) ? tr : tf));
+              if ((on >> cfg) & 1u) acc[cfg] = max(acc[cfg], front[X[cfg] + i] - ((cfg & 1) ? tr : tf));
           }
         }
+        int32_t mine = 0;
 #pragma unroll
         for (int cfg = 0; cfg < 8; ++cfg) {
-          const int32_t m = warp_max(acc[cfg]);
-          if (on[cfg] && lane == 0) yb[cfg * maxrow + t] = m;
+          const int32_t m = __reduce_max_sync(0xffffffffu, acc[cfg]);
+          if (lane == cfg) mine = m;
         }
+        if (lane < 8 && ((on >> lane) & 1u)) yb[lane * maxrow + t] = mine;
       }
     }
     __syncthreads();
 
     // ---- E: interlock fixpoint (Algorithm 2) and scores --------------------
+    // warps 0-7: one configuration each; warps 8-9: the knee candidate of the
+    // two atlas-width rows (App. A), so selection finds it ready
     if (warp < 8) {
       const int cfg = warp;
       const int v = cfg >> 1, hc = v & 1;
@@ -301,7 +379,7 @@ __global__ void __launch_bounds__(kNT) rowloop_kernel(Pack p, int j_lo, int maxr
             const int t = t0 + lane;
             const bool ok = t < len;
             const int32_t yv = ok ? y[t] : kI32Min;
-            const bool head = !ok || t == 0 || !(pfl[row_start + t - 1] & 2);
+            const bool head = !ok || t == 0 || !(pflw[t - 1] & 2);
             int32_t f = seg_scan_max(yv, head || lane == 0);
             // lanes before the first head of this chunk continue the carry
             const unsigned heads = __ballot_sync(0xffffffffu, head);
@@ -320,7 +398,7 @@ __global__ void __launch_bounds__(kNT) rowloop_kernel(Pack p, int j_lo, int maxr
             const int t = c * 32 + (31 - lane);  // reversed lane order
             const bool ok = t < len;
             const int32_t yv = ok ? y[t] : kI32Min;
-            const bool head = !ok || t == len - 1 || !(pfl[row_start + t] & 1);
+            const bool head = !ok || t == len - 1 || !(pflw[t] & 1);
             int32_t b = seg_scan_max(yv, head || lane == 0);
             const unsigned heads = __ballot_sync(0xffffffffu, head);
             const int first_head = heads ? __ffs(heads) - 1 : 32;
@@ -333,58 +411,58 @@ __global__ void __launch_bounds__(kNT) rowloop_kernel(Pack p, int j_lo, int maxr
         }
         int32_t mx = kI32Min;
         for (int t = lane; t < len; t += 32) mx = max(mx, y[t] + mbot[t]);
-        mx = warp_max(mx);
+        mx = __reduce_max_sync(0xffffffffu, mx);
         if (lane == 0) {
           ctl.score[cfg] = max(ctl.committed, mx);
           ctl.score_knee[cfg] = knee ? max(ctl.knee_max, mx) : 0;
         }
       }
+    } else if (warp < 10 && balance) {
+      // largest qualifying unscaled height drop among the first len charts,
+      // first on ties (key = drop << 16 | (0xffff - t))
+      const int len = ctl.len[warp - 8];
+      int64_t key = -1;
+      for (int t = lane; t + 1 < len; t += 32) {
+        const int64_t D = (int64_t)hqw[t] - hqw[t + 1];
+        if (100 * D >= (int64_t)p.knee_abs * 256 * p.H && 100 * D >= (int64_t)p.knee_rel * hqw[t]) {
+          const int64_t kk = (D << 16) | (0xffff - t);
+          key = kk > key ? kk : key;
+        }
+      }
+      key = warp_max(key);
+      if (lane == 0) ctl.knee_t[warp - 8] = key >= 0 ? 0xffff - (int)(key & 0xffff) : -1;
     }
     __syncthreads();
 
-    // ---- G: selection (Sec. 4.2) and knee detection (App. A) ---------------
+    // ---- G: selection (Sec. 4.2); the row state advances ------------------
     if (warp == 0) {
-      if (lane == 0) {
-        int choose[2] = {0, 0};
-        const int nfold = knee ? 2 : 1;
-        for (int fold = 0; fold < nfold; ++fold) {
-          const int h = (use_hc && ctl.len[fold * 2 + 1] > ctl.len[fold * 2]) ? 1 : 0;
-          const int jl = (fold * 2 + h) * 2, jr = jl + 1;
-          const int32_t kl = fold == 0 ? ctl.score[jl] : ctl.score_knee[jl];
-          const int32_t kr = fold == 0 ? ctl.score[jr] : ctl.score_knee[jr];
-          int dir;
-          if (balance) dir = kl < kr ? 0 : (kr < kl ? 1 : (ctl.prev_ltr ? 1 : 0));
-          else dir = ctl.prev_ltr ? 1 : 0;
-          choose[fold] = jl + dir;
-        }
-        int best = choose[0];
-        if (knee && ctl.len[choose[1] >> 1] > 0 &&
-            ctl.score[choose[1]] + p.knee_margin <= ctl.score[best])
-          best = choose[1];
-        ctl.best = best;
+      // lane f picks the direction for fold f (0: atlas width, 1: knee)
+      int ch = 0;
+      if (lane < 2 && (lane == 0 || knee)) {
+        const int fold = lane;
+        const int h = (use_hc && ctl.len[fold * 2 + 1] > ctl.len[fold * 2]) ? 1 : 0;
+        const int jl = (fold * 2 + h) * 2, jr = jl + 1;
+        const int32_t kl = fold == 0 ? ctl.score[jl] : ctl.score_knee[jl];
+        const int32_t kr = fold == 0 ? ctl.score[jr] : ctl.score_knee[jr];
+        int dir;
+        if (balance) dir = kl < kr ? 0 : (kr < kl ? 1 : (ctl.prev_ltr ? 1 : 0));
+        else dir = ctl.prev_ltr ? 1 : 0;
+        ch = jl + dir;
       }
-      __syncwarp();
-      const int best = ctl.best;
-      const int v = best >> 1, dir = best & 1, fold = v >> 1, hc = v & 1;
-      if (fold == 0 && balance) {
-        // largest qualifying unscaled height drop in the row, first on ties
+      const int ch1 = __shfl_sync(0xffffffffu, ch, 1);
+      if (lane == 0) {
+        int best = ch;
+        if (knee && ctl.len[ch1 >> 1] > 0 && ctl.score[ch1] + p.knee_margin <= ctl.score[best]) best = ch1;
+        const int v = best >> 1, dir = best & 1, fold = v >> 1, hc = v & 1;
         const int len = ctl.len[v];
-        int64_t key = -1;
-        for (int t = lane; t + 1 < len; t += 32) {
-          const int s = row_start + t;
-          const int64_t D = (int64_t)p.hq[s] - p.hq[s + 1];
-          if (100 * D >= (int64_t)p.knee_abs * 256 * p.H && 100 * D >= (int64_t)p.knee_rel * p.hq[s]) {
-            const int64_t kk = (D << 16) | (0xffff - t);
-            key = kk > key ? kk : key;
-          }
-        }
-        key = warp_max(key);
-        if (lane == 0) {
+        ctl.best = best;
+        if (fold == 0) {
+          // App. A: a knee in this row starts the concavity at the taller
+          // chart's padded edge; no knee if that concavity would be empty
           int valid = 0;
-          if (key >= 0) {
-            const int t = 0xffff - (int)(key & 0xffff);
-            const int32_t *pos = hc ? posH : posN;
-            const int32_t X = dir ? Wp - pos[t] - wps[t] : pos[t];
+          const int t = balance ? ctl.knee_t[hc] : -1;
+          if (t >= 0) {
+            const int32_t X = dir ? Wp - (hc ? posH : posN)[t] - wps[t] : (hc ? posH : posN)[t];
             ctl.knee_ltr = dir == 0;
             ctl.knee_l = X;
             ctl.knee_r = X + wps[t];
@@ -392,9 +470,14 @@ __global__ void __launch_bounds__(kNT) rowloop_kernel(Pack p, int j_lo, int maxr
           }
           ctl.knee_valid = valid;
           ctl.knees += valid;
+        } else {
+          ctl.knee_rows += 1;
         }
-      } else if (fold == 0 && lane == 0) {
-        ctl.knee_valid = 0;
+        ctl.committed = ctl.score[best];
+        ctl.fail = ctl.committed > Hp;
+        ctl.prev_ltr = dir == 0;
+        ctl.row_start = row_start + len;
+        ctl.row = row + 1;
       }
     }
     __syncthreads();
@@ -407,32 +490,22 @@ __global__ void __launch_bounds__(kNT) rowloop_kernel(Pack p, int j_lo, int maxr
       const int32_t lo = fold ? ctl.region_lo : 0, hi = fold ? ctl.region_hi : Wp;
       const int32_t *pos = hc ? posH : posN;
       const int32_t *y = yb + best * maxrow;
+      const int32_t slo = ctl.stage_lo, shi = ctl.stage_hi;
       for (int t = warp; t < len; t += kNW) {
         const int w = wps[t];
-        const uint32_t *col = pool + woff[t];
+        const int32_t cs = woff[t];
+        const uint32_t *col = (cs >= slo && cs + w <= shi) ? stage + (cs - slo) : colp + cs;
         const int32_t X = dir ? hi - pos[t] - w : lo + pos[t];
         const int32_t yt = y[t];
         for (int i = lane; i < w; i += 32) {
-          const int32_t bot = (int32_t)(col[dir ? w - 1 - i : i] >> 16);
-          atomicMax(&front[X + i], yt + bot);
+          const uint32_t word = col[dir ? w - 1 - i : i];
+          atomicMax(&front[X + i], yt + (int32_t)(word >> 16));
         }
       }
-      const int row = ctl.row;
       const int bits = dir | (hc << 1) | (fold << 2);
       for (int t = tid; t < len; t += kNT) {
         const int32_t X = dir ? hi - pos[t] - wps[t] : lo + pos[t];
         place[row_start + t] = make_int4(X, y[t], row, bits);
-      }
-      __syncthreads();
-      if (tid == 0) {
-        const int maxlen = max(max(ctl.len[0], ctl.len[1]), max(ctl.len[2], ctl.len[3]));
-        ctl.prev_maxlen = maxlen;
-        ctl.committed = ctl.score[best];
-        ctl.fail = ctl.committed > Hp;
-        ctl.prev_ltr = dir == 0;
-        ctl.row_start = row_start + len;
-        ctl.row = row + 1;
-        if (fold) ctl.knee_rows += 1;
       }
       __syncthreads();
     }
@@ -461,20 +534,28 @@ static int rowloop_maxrow(int W, int g) {
   return (Wp / (2 * g + 1) + 2 + 3) & ~3;
 }
 
+// Shared memory of one row-loop CTA without the column stage (the stage
+// takes what is left, up to two atlas widths of column words).
 size_t rowloop_smem_bytes(int W, int g) {
   const int Wp = W + 2 * g;
   const int wp_pad = (Wp + 3) & ~3;
-  return sizeof(int32_t) * ((size_t)wp_pad + 13 * (size_t)rowloop_maxrow(W, g)) + sizeof(Ctl);
+  return sizeof(int32_t) * ((size_t)wp_pad + 15 * (size_t)rowloop_maxrow(W, g)) + sizeof(Ctl);
 }
 
 cudaError_t launch_rowloop(const Pack &p, int j_lo, int j_hi, cudaStream_t st) {
   const int Wp = p.W + 2 * p.g;
   const int wp_pad = (Wp + 3) & ~3;
   const int maxrow = rowloop_maxrow(p.W, p.g);
-  const size_t smem = sizeof(int32_t) * ((size_t)wp_pad + 13 * (size_t)maxrow);
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  const size_t base = rowloop_smem_bytes(p.W, p.g);
+  const int64_t room = ((int64_t)optin - (int64_t)base) / 4;
+  const int scap = (int)(room < 2 * wp_pad ? (room > 0 ? room : 0) : 2 * wp_pad) & ~3;
+  const size_t smem = sizeof(int32_t) * ((size_t)scap + wp_pad + 15 * (size_t)maxrow);
   cudaError_t e = cudaFuncSetAttribute(rowloop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  rowloop_kernel<<<j_hi - j_lo + 1, kNT, smem, st>>>(p, j_lo, maxrow, wp_pad);
+  rowloop_kernel<<<j_hi - j_lo + 1, kNT, smem, st>>>(p, j_lo, maxrow, wp_pad, scap);
   return cudaGetLastError();
 }
 

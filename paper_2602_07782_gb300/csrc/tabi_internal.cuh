@@ -54,11 +54,13 @@ struct Pack {
   int32_t *perm;           // [n] sorted position -> input index
   int32_t *hq;             // [n] sorted Hq (Q.8)
   uint32_t *sort_tmp;      // [4n] radix-sort ping-pong
-  int32_t *env_off;        // [2n] pool offset, column capacity (sizes at k = 1024)
-  int64_t pool_stride;     // uint32 entries per candidate scale
-  int64_t pool_cap;        // entries available per candidate scale
-  uint32_t *pool;          // [64 * pool_stride]
-  int32_t *meta;           // [64 * 4n]: w', h', offset, max bottom
+  int32_t *env_off;        // [2n] row-pool offset and row capacity (sizes at k = 1024)
+  int32_t *colstart;       // [64 * n] column-pool offset of each chart at each candidate
+  int64_t col_stride;      // uint32 column entries per candidate scale
+  int64_t row_stride;      // uint32 row entries per candidate scale
+  uint32_t *colpool;       // [64 * col_stride] Top' | Bot' << 16, charts back to back
+  uint32_t *pool;          // [64 * row_stride] L' | R' << 16, k = 1024 capacities
+  int32_t *meta;           // [64 * 4n]: w', h', column start, max bottom
   int32_t *dnext;          // [64 * n]  compacting distance (s, s+1)
   uint8_t *pflags;         // [64 * n]  interlock bits
   int4 *place;             // [64 * n]  x, y, row, bits

@@ -212,16 +212,18 @@ class Context:
     def envelopes(self, scale: int, n: int):
         """List of (w', h', top', bot', left', right', maxbot) per sorted chart."""
         raw = self._inspect(INSPECT_ENV, scale)
-        meta = raw[:16 * n].view(np.int32).reshape(n, 4)
-        pool = raw[16 * n:].view(np.uint32)
-        cap = self._inspect(INSPECT_ENV_CAP).view(np.int32).reshape(n, 2)
+        col_stride, row_stride = (int(v) for v in raw[:16].view(np.int64))
+        meta = raw[16:16 + 16 * n].view(np.int32).reshape(n, 4)
+        cols = raw[16 + 16 * n:16 + 16 * n + 4 * col_stride].view(np.uint32)
+        rows = raw[16 + 16 * n + 4 * col_stride:].view(np.uint32)
+        roff = self._inspect(INSPECT_ENV_CAP).view(np.int32).reshape(n, 2)[:, 0]
         out = []
         for s in range(n):
-            wp, hp, off, mb = (int(v) for v in meta[s])
-            cols = pool[off:off + wp]
-            rows = pool[off + cap[s, 1]:off + cap[s, 1] + hp]
-            out.append((wp, hp, (cols & 0xffff).astype(np.int32), (cols >> 16).astype(np.int32),
-                        (rows & 0xffff).astype(np.int32), (rows >> 16).astype(np.int32), mb))
+            wp, hp, cst, mb = (int(v) for v in meta[s])
+            c = cols[cst:cst + wp]
+            r = rows[roff[s]:roff[s] + hp]
+            out.append((wp, hp, (c & 0xffff).astype(np.int32), (c >> 16).astype(np.int32),
+                        (r & 0xffff).astype(np.int32), (r >> 16).astype(np.int32), mb))
         return out
 
     def pairs(self, scale: int, n: int):
