@@ -229,10 +229,11 @@ tabi_status run_pack(tabi_ctx *ctx, const tabi_params *params, int32_t W, int32_
   if (!p.info || !p.shape || !p.place || !p.err || !p.colstart || !d_out || (host && (!d_off || !d_verts)))
     return fail(ctx, TABI_ERR_OOM, "arena too small for the per-chart arrays");
   const size_t left = (cv.cap - cv.used) / sizeof(uint32_t);
-  // the rest: half column pools, half row pools, 64 candidates each
-  p.col_stride = p.row_stride = (int64_t)(left / (2 * kScales)) & ~(int64_t)63;
+  // the rest in equal thirds: column words, their chart indices, row words
+  p.col_stride = p.row_stride = (int64_t)(left / (3 * kScales)) & ~(int64_t)63;
   p.colpool = reinterpret_cast<uint32_t *>(cv.base + cv.used);
-  p.pool = p.colpool + (int64_t)kScales * p.col_stride;
+  p.colown = reinterpret_cast<int32_t *>(p.colpool + (int64_t)kScales * p.col_stride);
+  p.pool = reinterpret_cast<uint32_t *>(p.colown + (int64_t)kScales * p.col_stride);
   if (p.col_stride < 64) return fail(ctx, TABI_ERR_OOM, "arena too small for the envelope pools");
   p.offsets = host ? d_off : offsets;
   p.verts = host ? d_verts : verts;
@@ -365,9 +366,10 @@ size_t tabi_arena_bytes(int32_t n, int32_t nv, int32_t W, int32_t H, int64_t sum
                         int32_t gutter) {
   (void)W; (void)H;
   if (n < 1) return 0;
-  // column and row pools get the same share; each must hold the larger of
-  // sum(w') and sum(h') at k = 1024, both below sum_extent + n (2g + 4)
-  const size_t pool = (size_t)kScales * 4 * 2 *
+  // column words, their chart indices and row words get equal shares; each
+  // must hold the larger of sum(w') and sum(h') at k = 1024, both below
+  // sum_extent + n (2g + 4)
+  const size_t pool = (size_t)kScales * 4 * 3 *
                       ((size_t)sum_extent_texels + (size_t)n * (2 * (size_t)gutter + 4) + 64);
   return fixed_bytes(n, nv) + pool + (size_t)kScales * 256;
 }

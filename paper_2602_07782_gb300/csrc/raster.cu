@@ -104,6 +104,10 @@ __global__ void __launch_bounds__(kRasterThreads, 4) raster_kernel(Pack p, int j
     __syncwarp();
     const int32_t cstart = p.colstart[(int64_t)j * n + s];
     const int32_t maxbot = warp_axis(a0, g, p.colpool + (int64_t)j * p.col_stride + cstart);
+    {  // each column word's chart, so a staged run of words knows its owners
+      int32_t *own = p.colown + (int64_t)j * p.col_stride + cstart;
+      for (int c = lane; c < a0.len + 2 * g; c += 32) own[c] = s;
+    }
     warp_axis(a1, g, p.pool + (int64_t)j * p.row_stride + roff);
     if (lane == 0) {
       int32_t *mt = p.meta + ((int64_t)j * n + s) * 4;

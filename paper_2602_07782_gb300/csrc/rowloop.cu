@@ -33,7 +33,7 @@
 namespace tabi {
 namespace {
 
-constexpr int kNT = 512;
+constexpr int kNT = 1024;
 constexpr int kNW = kNT / 32;
 constexpr int32_t kNeg = -(1 << 28);  // max-plus "minus infinity"
 constexpr int32_t kI32Min = -0x7fffffff - 1;
@@ -87,16 +87,15 @@ __device__ __forceinline__ int32_t block_min(int32_t v, Ctl &ctl) {
   return -block_max(-v, ctl);
 }
 
-// segmented inclusive scan (max) over lanes, segments start at head lanes
-__device__ __forceinline__ int32_t seg_scan_max(int32_t v, bool head) {
+// segmented inclusive scan (max) over lanes; `heads` has a bit per lane
+// that starts a segment (bit 0 set), each lane's start is its highest head
+__device__ __forceinline__ int32_t seg_scan_max(int32_t v, unsigned heads) {
   const int lane = threadIdx.x & 31;
-  unsigned hd = head;
+  const int start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
     const int32_t u = __shfl_up_sync(0xffffffffu, v, o);
-    const unsigned uh = __shfl_up_sync(0xffffffffu, hd, o);
-    if (lane >= o && !hd) v = max(v, u);
-    if (lane >= o) hd |= uh;
+    if (lane - o >= start) v = max(v, u);
   }
   return v;
 }
@@ -157,9 +156,11 @@ __global__ void __launch_bounds__(kNT) rowloop_kernel(Pack p, int j_lo, int maxr
   int32_t *woff = mbot + maxrow;        // [maxrow] column start in the column pool
   int32_t *pflw = woff + maxrow;        // [maxrow] interlock bits of pair (t, t+1)
   int32_t *hqw = pflw + maxrow;         // [maxrow] unscaled heights
+  int32_t *sown = hqw + maxrow;         // [scap] sorted chart index of each staged word
   __shared__ Ctl ctl;
 
   const uint32_t *colp = p.colpool + (int64_t)j * p.col_stride;
+  const int32_t *cown = p.colown + (int64_t)j * p.col_stride;
   const int32_t *meta = p.meta + (int64_t)j * n * 4;
   const int32_t *dnext = p.dnext + (int64_t)j * n;
   const uint8_t *pfl = p.pflags + (int64_t)j * n;
@@ -216,70 +217,74 @@ __global__ void __launch_bounds__(kNT) rowloop_kernel(Pack p, int j_lo, int maxr
         // of the chart before it (none at the row start)
         int32_t carry_x = 0, carry_xprev = kNeg, carry_re = kNeg, carry_wprev = kNeg;
         bool doneF = false, doneK = !knee;
-        int32_t w_cur = 0, d_cur = 0;
-        {
-          const int s = row_start + lane;
-          if (s < n) { w_cur = meta[(int64_t)s * 4]; d_cur = hc ? dnext[s] : 0; }
-        }
-        for (int t0 = 0; !(doneF && doneK); t0 += 32) {
-          const int t = t0 + lane;
-          const int s = row_start + t;
-          const bool valid = s < n;
-          const bool room = t < maxrow;  // the last chunk may run past the row capacity
-          const int32_t w = w_cur, d = d_cur;
-          {  // prefetch the next chunk while this one is scanned
-            const int sn = s + 32;
-            w_cur = sn < n ? meta[(int64_t)sn * 4] : 0;
-            d_cur = (hc && sn < n) ? dnext[sn] : 0;
-          }
-          const int32_t a = hc ? w - d : w;  // x_{t+1} = x_t + a_t unless the clamp binds
-          int32_t incl = a;
+        // widths and distances of four chunks are loaded together (one
+        // memory round trip per 128 charts), then scanned chunk by chunk
+        for (int g0 = 0; !(doneF && doneK); g0 += 128) {
+          int32_t wq[4], dq[4];
 #pragma unroll
-          for (int o = 1; o < 32; o <<= 1) {
-            const int32_t u = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += u;
+          for (int c = 0; c < 4; ++c) {
+            const int s = row_start + g0 + 32 * c + lane;
+            wq[c] = s < n ? meta[(int64_t)s * 4] : 0;
+            dq[c] = (hc && s < n) ? dnext[s] : 0;
           }
-          int32_t xnext = carry_x + incl, xt = xnext - a;
-          if (hc) {
-            // clamp: chart t+1 never starts left of chart t-1's right edge
-            int32_t re_prev = __shfl_up_sync(0xffffffffu, xt + w, 1);
-            if (lane == 0) re_prev = carry_re;
-            if (__any_sync(0xffffffffu, valid && xnext < re_prev)) {
-              // the clamp binds in this chunk: (max,+) matrix scan,
-              // state (x_t, x_{t-1}) -> (max(x_t + a_t, x_{t-1} + w_{t-1}), x_t)
-              int32_t wprev = __shfl_up_sync(0xffffffffu, w, 1);
-              if (lane == 0) wprev = carry_wprev;
-              MP m{a, wprev, 0, kNeg};
 #pragma unroll
-              for (int o = 1; o < 32; o <<= 1) {
-                const MP u = mpshfl_up(m, o);
-                if (lane >= o) m = mpmul(m, u);
-              }
-              xnext = max(mpadd(m.a00, carry_x), mpadd(m.a01, carry_xprev));
-              xt = __shfl_up_sync(0xffffffffu, xnext, 1);
-              if (lane == 0) xt = carry_x;
+          for (int c = 0; c < 4; ++c) {
+            if (doneF && doneK) break;
+            const int t0 = g0 + 32 * c;
+            const int t = t0 + lane;
+            const int s = row_start + t;
+            const bool valid = s < n;
+            const bool room = t < maxrow;  // the last chunk may run past the row capacity
+            const int32_t w = wq[c], d = dq[c];
+            const int32_t a = hc ? w - d : w;  // x_{t+1} = x_t + a_t unless the clamp binds
+            int32_t incl = a;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+              const int32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+              if (lane >= o) incl += u;
             }
-            carry_xprev = __shfl_sync(0xffffffffu, xt, 31);
-            carry_re = __shfl_sync(0xffffffffu, xt + w, 31);
-            carry_wprev = __shfl_sync(0xffffffffu, w, 31);
-          }
-          carry_x = __shfl_sync(0xffffffffu, xnext, 31);
-          // the first chart that does not fit ends the row
-          const unsigned overF = __ballot_sync(0xffffffffu, !valid || xt + w > foldF);
-          const unsigned overK = __ballot_sync(0xffffffffu, !valid || xt + w > foldK);
-          if (!doneF && overF) { lenF = t0 + __ffs(overF) - 1; doneF = true; }
-          else if (!doneF) lenF = t0 + 32;
-          if (!doneK && overK) { lenK = t0 + __ffs(overK) - 1; doneK = true; }
-          else if (!doneK) lenK = t0 + 32;
-          if (valid && room) pos[t] = xt;
-          if (t0 + 32 >= maxrow && !(doneF && doneK)) {  // cannot happen: rows hold <= W'/(2g+1) + 1 charts
-            if (lane == 0) atomicOr(p.err, kErrRow);
-            doneF = doneK = true;
-          }
-          if ((doneF && lenF >= maxrow) || (doneK && lenK >= maxrow)) {
-            if (lane == 0) atomicOr(p.err, kErrRow);
-            lenF = min(lenF, maxrow - 1);
-            lenK = min(lenK, maxrow - 1);
+            int32_t xnext = carry_x + incl, xt = xnext - a;
+            if (hc) {
+              // clamp: chart t+1 never starts left of chart t-1's right edge
+              int32_t re_prev = __shfl_up_sync(0xffffffffu, xt + w, 1);
+              if (lane == 0) re_prev = carry_re;
+              if (__any_sync(0xffffffffu, valid && xnext < re_prev)) {
+                // the clamp binds in this chunk: (max,+) matrix scan,
+                // state (x_t, x_{t-1}) -> (max(x_t + a_t, x_{t-1} + w_{t-1}), x_t)
+                int32_t wprev = __shfl_up_sync(0xffffffffu, w, 1);
+                if (lane == 0) wprev = carry_wprev;
+                MP m{a, wprev, 0, kNeg};
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                  const MP u = mpshfl_up(m, o);
+                  if (lane >= o) m = mpmul(m, u);
+                }
+                xnext = max(mpadd(m.a00, carry_x), mpadd(m.a01, carry_xprev));
+                xt = __shfl_up_sync(0xffffffffu, xnext, 1);
+                if (lane == 0) xt = carry_x;
+              }
+              carry_xprev = __shfl_sync(0xffffffffu, xt, 31);
+              carry_re = __shfl_sync(0xffffffffu, xt + w, 31);
+              carry_wprev = __shfl_sync(0xffffffffu, w, 31);
+            }
+            carry_x = __shfl_sync(0xffffffffu, xnext, 31);
+            // the first chart that does not fit ends the row
+            const unsigned overF = __ballot_sync(0xffffffffu, !valid || xt + w > foldF);
+            const unsigned overK = __ballot_sync(0xffffffffu, !valid || xt + w > foldK);
+            if (!doneF && overF) { lenF = t0 + __ffs(overF) - 1; doneF = true; }
+            else if (!doneF) lenF = t0 + 32;
+            if (!doneK && overK) { lenK = t0 + __ffs(overK) - 1; doneK = true; }
+            else if (!doneK) lenK = t0 + 32;
+            if (valid && room) pos[t] = xt;
+            if (t0 + 32 >= maxrow && !(doneF && doneK)) {  // cannot happen: rows hold <= W'/(2g+1) + 1 charts
+              if (lane == 0) atomicOr(p.err, kErrRow);
+              doneF = doneK = true;
+            }
+            if ((doneF && lenF >= maxrow) || (doneK && lenK >= maxrow)) {
+              if (lane == 0) atomicOr(p.err, kErrRow);
+              lenF = min(lenF, maxrow - 1);
+              lenK = min(lenK, maxrow - 1);
+            }
           }
         }
       }
@@ -293,13 +298,16 @@ __global__ void __launch_bounds__(kNT) rowloop_kernel(Pack p, int j_lo, int maxr
       // column pool; int4 loads from a 16-byte aligned start), and every
       // chart that can be in this row's widths, column starts, deepest
       // bottoms, interlock bits and heights
+      const int32_t c4 = meta[(int64_t)row_start * 4 + 2] & ~3;
+      const int32_t nw = (int32_t)min((int64_t)scap, p.col_stride - c4) & ~3;
       {
-        const int32_t c4 = meta[(int64_t)row_start * 4 + 2] & ~3;
-        const int32_t nw = (int32_t)min((int64_t)scap, p.col_stride - c4) & ~3;
         const int4 *src = reinterpret_cast<const int4 *>(colp + c4);
-        for (int q = tid - 64; q < nw / 4; q += kNT - 64) sm4[q] = src[q];
+        const int4 *osrc = reinterpret_cast<const int4 *>(cown + c4);
+        int4 *odst = reinterpret_cast<int4 *>(sown);
+        for (int q = tid - 64; q < nw / 4; q += kNT - 64) { sm4[q] = src[q]; odst[q] = osrc[q]; }
         if (tid == 64) { ctl.stage_lo = c4; ctl.stage_hi = c4 + nw; }
       }
+      // per chart: window entries, offsets zeroed
       const int spec = min(n - row_start, maxrow);
       for (int t = tid - 64; t < spec; t += kNT - 64) {
         const int s = row_start + t;
@@ -309,6 +317,8 @@ __global__ void __launch_bounds__(kNT) rowloop_kernel(Pack p, int j_lo, int maxr
         mbot[t] = mt.w;
         pflw[t] = pfl[s];
         hqw[t] = p.hq[s];
+#pragma unroll
+        for (int cfg = 0; cfg < 8; ++cfg) yb[cfg * maxrow + t] = 0;  // offsets start at 0
       }
     }
     __syncthreads();
@@ -348,15 +358,27 @@ __global__ void __launch_bounds__(kNT) rowloop_kernel(Pack p, int j_lo, int maxr
             const uint32_t r = col[w - 1 - i];
             const int32_t tf = (int32_t)(f & 0xffffu), tr = (int32_t)(r & 0xffffu);
 #pragma unroll
-            for (int cfg = 0; cfg < 8; ++cfg)
+            for (int cfg = 0; cfg < 4; ++cfg)
               if ((on >> cfg) & 1u) acc[cfg] = max(acc[cfg], front[X[cfg] + i] - ((cfg & 1) ? tr : tf));
+            if (knee) {
+#pragma unroll
+              for (int cfg = 4; cfg < 8; ++cfg)
+                if ((on >> cfg) & 1u) acc[cfg] = max(acc[cfg], front[X[cfg] + i] - ((cfg & 1) ? tr : tf));
+            }
           }
         }
         int32_t mine = 0;
 #pragma unroll
-        for (int cfg = 0; cfg < 8; ++cfg) {
+        for (int cfg = 0; cfg < 4; ++cfg) {
           const int32_t m = __reduce_max_sync(0xffffffffu, acc[cfg]);
           if (lane == cfg) mine = m;
+        }
+        if (knee) {  // the knee configurations exist only while a knee is live
+#pragma unroll
+          for (int cfg = 4; cfg < 8; ++cfg) {
+            const int32_t m = __reduce_max_sync(0xffffffffu, acc[cfg]);
+            if (lane == cfg) mine = m;
+          }
         }
         if (lane < 8 && ((on >> lane) & 1u)) yb[lane * maxrow + t] = mine;
       }
@@ -380,9 +402,9 @@ __global__ void __launch_bounds__(kNT) rowloop_kernel(Pack p, int j_lo, int maxr
             const bool ok = t < len;
             const int32_t yv = ok ? y[t] : kI32Min;
             const bool head = !ok || t == 0 || !(pflw[t - 1] & 2);
-            int32_t f = seg_scan_max(yv, head || lane == 0);
-            // lanes before the first head of this chunk continue the carry
             const unsigned heads = __ballot_sync(0xffffffffu, head);
+            int32_t f = seg_scan_max(yv, heads | 1u);
+            // lanes before the first head of this chunk continue the carry
             const int first_head = heads ? __ffs(heads) - 1 : 32;
             if (lane < first_head) f = max(f, carry);
             carry = __shfl_sync(0xffffffffu, f, 31);
@@ -399,8 +421,8 @@ __global__ void __launch_bounds__(kNT) rowloop_kernel(Pack p, int j_lo, int maxr
             const bool ok = t < len;
             const int32_t yv = ok ? y[t] : kI32Min;
             const bool head = !ok || t == len - 1 || !(pflw[t] & 1);
-            int32_t b = seg_scan_max(yv, head || lane == 0);
             const unsigned heads = __ballot_sync(0xffffffffu, head);
+            int32_t b = seg_scan_max(yv, heads | 1u);
             const int first_head = heads ? __ffs(heads) - 1 : 32;
             if (lane < first_head) b = max(b, carry);
             carry = __shfl_sync(0xffffffffu, b, 31);
@@ -491,6 +513,17 @@ __global__ void __launch_bounds__(kNT) rowloop_kernel(Pack p, int j_lo, int maxr
       const int32_t *pos = hc ? posH : posN;
       const int32_t *y = yb + best * maxrow;
       const int32_t slo = ctl.stage_lo, shi = ctl.stage_hi;
+      const int fA = woff[0] - slo;
+      const int fB = woff[len - 1] + wps[len - 1] - slo;
+      if (fB <= shi - slo) {
+        for (int f = fA + tid; f < fB; f += kNT) {  // lane per staged column word
+          const int t = sown[f] - row_start;
+          const int w = wps[t];
+          const int i = f - (woff[t] - slo);
+          const int32_t X = dir ? hi - pos[t] - w : lo + pos[t];
+          atomicMax(&front[X + (dir ? w - 1 - i : i)], y[t] + (int32_t)(stage[f] >> 16));
+        }
+      } else {
       for (int t = warp; t < len; t += kNW) {
         const int w = wps[t];
         const int32_t cs = woff[t];
@@ -501,6 +534,7 @@ __global__ void __launch_bounds__(kNT) rowloop_kernel(Pack p, int j_lo, int maxr
           const uint32_t word = col[dir ? w - 1 - i : i];
           atomicMax(&front[X + i], yt + (int32_t)(word >> 16));
         }
+      }
       }
       const int bits = dir | (hc << 1) | (fold << 2);
       for (int t = tid; t < len; t += kNT) {
@@ -539,7 +573,7 @@ static int rowloop_maxrow(int W, int g) {
 size_t rowloop_smem_bytes(int W, int g) {
   const int Wp = W + 2 * g;
   const int wp_pad = (Wp + 3) & ~3;
-  return sizeof(int32_t) * ((size_t)wp_pad + 15 * (size_t)rowloop_maxrow(W, g)) + sizeof(Ctl);
+  return sizeof(int32_t) * ((size_t)wp_pad + 15 * (size_t)rowloop_maxrow(W, g)) + sizeof(Ctl) + 64;
 }
 
 cudaError_t launch_rowloop(const Pack &p, int j_lo, int j_hi, cudaStream_t st) {
@@ -550,9 +584,10 @@ cudaError_t launch_rowloop(const Pack &p, int j_lo, int j_hi, cudaStream_t st) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   const size_t base = rowloop_smem_bytes(p.W, p.g);
-  const int64_t room = ((int64_t)optin - (int64_t)base) / 4;
+  // each staged column word costs 4 bytes of stage and 4 of chart index
+  const int64_t room = ((int64_t)optin - (int64_t)base) / 8;
   const int scap = (int)(room < 2 * wp_pad ? (room > 0 ? room : 0) : 2 * wp_pad) & ~3;
-  const size_t smem = sizeof(int32_t) * ((size_t)scap + wp_pad + 15 * (size_t)maxrow);
+  const size_t smem = sizeof(int32_t) * (2 * (size_t)scap + wp_pad + 15 * (size_t)maxrow);
   cudaError_t e = cudaFuncSetAttribute(rowloop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   rowloop_kernel<<<j_hi - j_lo + 1, kNT, smem, st>>>(p, j_lo, maxrow, wp_pad, scap);

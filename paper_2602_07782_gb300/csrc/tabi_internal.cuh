@@ -59,6 +59,7 @@ struct Pack {
   int64_t col_stride;      // uint32 column entries per candidate scale
   int64_t row_stride;      // uint32 row entries per candidate scale
   uint32_t *colpool;       // [64 * col_stride] Top' | Bot' << 16, charts back to back
+  int32_t *colown;         // [64 * col_stride] sorted chart index of each column word
   uint32_t *pool;          // [64 * row_stride] L' | R' << 16, k = 1024 capacities
   int32_t *meta;           // [64 * 4n]: w', h', column start, max bottom
   int32_t *dnext;          // [64 * n]  compacting distance (s, s+1)
