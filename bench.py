@@ -128,7 +128,7 @@ def algorithmic_bytes(ctx, cs, tabi, n_eval_scales):
         if not hdr[6]:
             continue
         raw = ctx._inspect(tabi.INSPECT_ENV, j)
-        meta = raw[:16 * n].view(np.int32).reshape(n, 4)
+        meta = raw[16:16 + 16 * n].view(np.int32).reshape(n, 4)
         env_cols += int(meta[:, 0].sum())
         env_rows += int(meta[:, 1].sum())
         placed += int(hdr[5])

@@ -50,7 +50,8 @@ extern "C" {
 
 typedef enum tabi_status {
   TABI_OK = 0,
-  TABI_ERR_INVALID_ARG = 1, /* n < 1, a chart with < 3 vertices, an AABB side
+  TABI_ERR_INVALID_ARG = 1, /* n < 1 or > TABI_MAX_CHARTS, a chart with < 3
+                               vertices, an AABB side
                                below one texel, a coordinate outside
                                (-2^20, 2^20), atlas side outside [1, 8192],
                                bad params, or an atlas too wide for the
@@ -74,6 +75,16 @@ typedef enum tabi_status {
 #define TABI_F_LAABB   8u /* local-AABB proxy in the envelopes, Sec. 4.1.1;
                              OBB and LAABB both off = bounding boxes only    */
 #define TABI_F_ALL     15u
+/* Inspection aid, not part of the method: every candidate's row loop runs
+ * to its end even after a larger candidate of the same atlas has succeeded
+ * (without it such a candidate is skipped or abandoned between rows).  The
+ * scale and placements are the same either way; only the per-candidate
+ * summaries of TABI_INSPECT_SCALE become complete. */
+#define TABI_F_EVAL_ALL 16u
+
+/* Largest chart count of one atlas, largest batch. */
+#define TABI_MAX_CHARTS 131072
+#define TABI_MAX_BATCH 65536
 
 typedef struct tabi_params {
   int32_t version;      /* TABI_PARAMS_VERSION                                */
@@ -87,7 +98,9 @@ typedef struct tabi_params {
   uint32_t flags;       /* TABI_F_*                                          */
   int32_t scale_fanout; /* candidate scales evaluated per wave of the
                            descending search, 1..64 (64 = all at once); the
-                           result is the same for every value               */
+                           result is the same for every value.  Waves share
+                           the envelope pools, so a smaller fan-out also
+                           needs a smaller arena                            */
 } tabi_params;
 
 /* One placed chart; see "Placement semantics" above. */
@@ -141,42 +154,88 @@ tabi_status tabi_pack_device(tabi_ctx *ctx, const tabi_params *params, int32_t a
                              const int32_t *verts, int32_t n_verts, tabi_placement *out,
                              int32_t *out_k, void *stream);
 
+/* One atlas of a batch (tabi_pack_batch, tabi_pack_batch_device): the
+ * arguments of tabi_pack in one record.  atlas_w .. out are inputs (out is
+ * the caller's placement buffer); scale_k and status are written by the
+ * call: status is this atlas's tabi_status (TABI_OK, TABI_ERR_NO_FIT,
+ * TABI_ERR_INVALID_ARG or TABI_ERR_OOM) and scale_k its k (0 unless OK). */
+typedef struct tabi_request {
+  int32_t atlas_w, atlas_h;
+  int32_t n_charts, n_verts;
+  const uint32_t *offsets; /* [n_charts + 1], offsets[0] = 0, last = n_verts */
+  const int32_t *verts;    /* [2 * n_verts] (Q.8)                            */
+  tabi_placement *out;     /* [n_charts], input order                        */
+  int32_t scale_k;         /* out                                           */
+  int32_t status;          /* out                                           */
+} tabi_request;
+
+/* Pack many independent atlases of uneven size together (the batched form:
+ * every stage runs once over all atlases, each wave of candidate scales
+ * over the atlases still searching).  Each atlas gets exactly the result
+ * tabi_pack would give it alone.  HOST pointers in the requests; the
+ * inputs are copied to the device on `stream`, the results back.
+ * 1 <= n_reqs <= TABI_MAX_BATCH.  The launch sequence is captured once per
+ * wave structure (fan-out, shared-memory class) into a CUDA graph owned by
+ * the context and replayed for every later batch.  A request that fails
+ * the host checks gets TABI_ERR_INVALID_ARG and takes no device work.
+ * Returns TABI_OK when every request has its status (which may itself be
+ * an error), else TABI_ERR_INVALID_ARG (bad params, n_reqs or pointers),
+ * TABI_ERR_OOM (the per-chart arrays do not fit the arena), TABI_ERR_CUDA
+ * or TABI_ERR_BUSY, and then no request status is meaningful.  The arena
+ * a batch needs is at most the sum of tabi_arena_bytes of its atlases. */
+tabi_status tabi_pack_batch(tabi_ctx *ctx, const tabi_params *params, tabi_request *reqs,
+                            int32_t n_reqs, void *stream);
+
+/* Same with DEVICE pointers for offsets, verts and out (reqs itself is host
+ * memory). */
+tabi_status tabi_pack_batch_device(tabi_ctx *ctx, const tabi_params *params, tabi_request *reqs,
+                                   int32_t n_reqs, void *stream);
+
 /* Intermediate results of the last pack on this context, copied to host
- * memory for inspection and step-by-step testing.  `what` selects:
+ * memory for inspection and step-by-step testing; tabi_inspect_atlas
+ * selects request `atlas` of the last batch (tabi_inspect = atlas 0).
+ * n = that atlas's chart count; `what` selects:
  *   TABI_INSPECT_CHARTS  tabi_chart_info[n], input order (prep, Sec. 3.1,
  *                        Sec. 4.1.1, App. A);
  *   TABI_INSPECT_PERM    int32[n]: input index of each sorted position;
  *   TABI_INSPECT_ENV     for candidate index `scale` (k = 16*(scale+1)):
- *                        int64[2] (column-pool and row-pool strides in
- *                        entries), int32[4n] meta per sorted chart (padded
+ *                        int64[2] (words of the atlas's column and row
+ *                        regions), int32[4n] meta per sorted chart (padded
  *                        width w', padded height h', column start, max
- *                        bottom), the candidate's column pool (uint32,
- *                        Top' | Bot' << 16 per padded column, chart s from
- *                        its column start) and its row pool (uint32,
- *                        L' | R' << 16 per padded row, chart s from its row
- *                        offset);
- *   TABI_INSPECT_ENV_CAP int32[2n]: row offset and row capacity per chart;
+ *                        bottom), int32[n] row start per sorted chart, the
+ *                        column region (uint32, Top' | Bot' << 16 per
+ *                        padded column, chart s from its column start) and
+ *                        the row region (uint32, L' | R' << 16 per padded
+ *                        row, chart s from its row start);
+ *   TABI_INSPECT_REGIONS int64[64][2] region starts in the column and row
+ *                        pools, then int64[64][2] region words, per
+ *                        candidate;
  *   TABI_INSPECT_PAIRS   int32[n] compacting distance d(s, s+1) then
  *                        uint8[n] flags (bit0 CannotMoveAbove(s, s+1),
  *                        bit1 CannotMoveAbove(s+1, s)) for `scale`;
  *   TABI_INSPECT_SCALE   int32[8]: success, rows, knee-folded rows, knees
  *                        found, final max frontline, charts placed,
- *                        evaluated, 0 -- then int32[4n] per sorted chart:
- *                        x, y, row, bits (bit0 mirror, bit1 compacting on,
- *                        bit2 knee-folded) for `scale`.
- * Only candidates evaluated by the last pack are meaningful (all of them
- * when scale_fanout = 64).  *needed receives the byte count; nothing is
- * copied if cap is too small (TABI_ERR_INVALID_ARG). */
+ *                        evaluated (0 not run, 1 ran to its end, 2
+ *                        abandoned after a larger candidate succeeded), 0
+ *                        -- then int32[4n] per sorted chart: x, y, row,
+ *                        bits (bit0 mirror, bit1 compacting on, bit2
+ *                        knee-folded) for `scale`.
+ * Only candidates the last pack ran to their end are meaningful (all of
+ * them with TABI_F_EVAL_ALL and scale_fanout 64; with a smaller fan-out a
+ * later wave reuses the envelope regions).  *needed receives the byte
+ * count; nothing is copied if cap is too small (TABI_ERR_INVALID_ARG). */
 enum {
   TABI_INSPECT_CHARTS = 1,
   TABI_INSPECT_PERM = 2,
   TABI_INSPECT_ENV = 3,
-  TABI_INSPECT_ENV_CAP = 4,
+  TABI_INSPECT_REGIONS = 4,
   TABI_INSPECT_PAIRS = 5,
   TABI_INSPECT_SCALE = 6
 };
 tabi_status tabi_inspect(tabi_ctx *ctx, int32_t what, int32_t scale, void *host_dst, size_t cap,
                          size_t *needed);
+tabi_status tabi_inspect_atlas(tabi_ctx *ctx, int32_t atlas, int32_t what, int32_t scale,
+                               void *host_dst, size_t cap, size_t *needed);
 
 /* Per-stage device time of the packs run on this context (CUDA events
  * recorded on each pack's stream around every stage).  enable = 1 starts

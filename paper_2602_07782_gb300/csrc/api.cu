@@ -1,13 +1,29 @@
 // C ABI of the packer (include/tabi.h): context, arena carving, the launch
-// sequence of one pack, result selection and inspection.
+// sequence of a batch of atlases (captured once per wave structure into a
+// CUDA graph and replayed), per-atlas results and inspection.  A single
+// pack is a batch of one.
+#include <algorithm>
 #include <atomic>
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "tabi_internal.cuh"
 
 using namespace tabi;
+
+namespace {
+
+// One captured launch sequence: the kernels of a batch for fan-out F with a
+// row-loop CTA of `smem` dynamic bytes.  Every kernel reads the batch from
+// the record at the arena's start, so the graph serves any batch.
+struct GraphEntry {
+  int F, smem;
+  cudaGraphExec_t exec;
+};
+
+}  // namespace
 
 struct tabi_ctx {
   int device = 0;
@@ -16,12 +32,20 @@ struct tabi_ctx {
   bool owned = false;
   std::atomic<int> busy{0};
   std::string last_error;
-  Pack last{};  // device layout of the last pack, for tabi_inspect
+  int sms = 0, rowloop_dyn_max = 0;
+  cudaStream_t cap_stream = nullptr;  // stream the graphs are captured on
+  std::vector<GraphEntry> graphs;
+  // pinned host staging: the batch record going up, the results coming down
+  char *hstage = nullptr;
+  size_t hstage_bytes = 0;
+  // the last batch, for tabi_inspect
+  Pack last{};
   bool has_last = false;
-  PackResult *host_result = nullptr;  // pinned
-  // optional per-stage timing
+  std::vector<AtlasDesc> last_desc;
+  std::vector<int> last_map;  // request index -> atlas index (-1: not run)
+  // optional per-stage timing (direct launches with events between stages)
   bool timing = false;
-  cudaEvent_t ev[2 + 3 * 64 * 2 + 16] = {};
+  cudaEvent_t ev[2 * (4 + 3 * kScales) + 8] = {};
   int n_ev = 0;
   double stage_ms[8] = {};
   int64_t launches[8] = {};
@@ -51,14 +75,20 @@ tabi_status cuda_fail(tabi_ctx *c, cudaError_t e, const char *where) {
   return fail(c, TABI_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
 
+size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
+
 // bump allocator over the arena (256-byte aligned pieces)
 struct Carve {
   char *base;
   size_t cap, used = 0;
+  bool ok = true;
   template <typename T>
   T *take(size_t count) {
-    const size_t bytes = (count * sizeof(T) + 255) & ~(size_t)255;
-    if (used + bytes > cap) return nullptr;
+    const size_t bytes = round256(count * sizeof(T));
+    if (used + bytes > cap) {
+      ok = false;
+      return nullptr;
+    }
     T *p = reinterpret_cast<T *>(base + used);
     used += bytes;
     return p;
@@ -69,97 +99,103 @@ bool valid_params(const tabi_params *p) {
   return p && p->version == TABI_PARAMS_VERSION && p->gutter >= 0 && p->gutter <= kMaxGutter &&
          p->knee_abs_pct >= 0 && p->knee_abs_pct <= 100 && p->knee_rel_pct >= 0 &&
          p->knee_rel_pct <= 100 && p->lr_sig_pct >= 0 && p->lr_sig_pct <= 100 &&
-         p->knee_margin >= 0 && p->knee_margin <= 1 << 20 && (p->flags & ~TABI_F_ALL) == 0 &&
-         p->scale_fanout >= 1 && p->scale_fanout <= kScales;
+         p->knee_margin >= 0 && p->knee_margin <= 1 << 20 &&
+         (p->flags & ~(TABI_F_ALL | TABI_F_EVAL_ALL)) == 0 && p->scale_fanout >= 1 &&
+         p->scale_fanout <= kScales;
 }
 
+// Arena bytes of the per-chart and per-atlas arrays of one atlas (all but
+// the envelope pools), with the host-input copies.
 size_t fixed_bytes(int64_t n, int64_t nv) {
-  size_t b = 0;
-  auto add = [&](size_t x) { b += (x + 255) & ~(size_t)255; };
-  add(4 * (n + 1));              // offsets (host variant)
-  add(8 * nv);                   // verts (host variant)
-  add(sizeof(tabi_chart_info) * n);
-  add(sizeof(ChartShape) * n * 2);
-  add(4 * n);                    // perm
-  add(4 * n);                    // hq
-  add(16 * n);                   // sort ping-pong
-  add(8 * n);                    // env_off
-  add((size_t)kScales * 4 * n);  // colstart
-  add((size_t)kScales * 16 * n); // meta
-  add((size_t)kScales * 4 * n);  // dnext
-  add((size_t)kScales * n);      // pflags
-  add((size_t)kScales * 16 * n); // place
-  add(sizeof(ScaleOut) * kScales);
-  add(4);                        // found
-  add(sizeof(PackResult));
-  add(4);                        // err
-  add(sizeof(tabi_placement) * n);
-  return b + 4096;
+  const size_t per_chart = 4 + sizeof(tabi_chart_info) + 2 * sizeof(ChartShape) + 3 * 4 + 16 +
+                           (size_t)kScales * (4 + 4 + 16 + 4 + 1 + 16) + 4 + 4 + sizeof(tabi_placement);
+  const size_t per_atlas = sizeof(AtlasDesc) + (size_t)kScales * 2 * 8 * 2 + sizeof(ScaleOut) * kScales +
+                           8 + sizeof(PackResult) + 8 + 40 * 256;
+  return (size_t)n * per_chart + 8 * (size_t)nv + per_atlas + sizeof(Pack) + 64 * 1024;
 }
 
-__global__ void init_kernel(Pack p) {
+// ---------------------------------------------------------------------------
+// per-atlas kernels of the batch record
+// ---------------------------------------------------------------------------
+__global__ void init_kernel(const Pack *__restrict__ pp) {
+  const Pack &p = *pp;
   const int t = threadIdx.x;
-  if (t < kScales) p.scale_out[t] = ScaleOut{0, 0, 0, 0, 0, 0, 0, 0};
-  if (t == 0) {
-    *p.found = -1;
-    *p.err = 0;
-    *p.result = PackResult{0, 0, 0, -1};
+  if (blockIdx.x == 0) {
+    if (t < 2 * kScales) p.jtot[t] = 0;
+    if (t < kScales) p.counter[t] = 0;
+  }
+  for (int at = blockIdx.x; at < p.A; at += gridDim.x) {
+    if (t < kScales) p.scale_out[at * kScales + t] = ScaleOut{0, 0, 0, 0, 0, 0, 0, 0};
+    if (t == 0) {
+      p.found[at] = -1;
+      p.err[at] = 0;
+      p.result[at] = PackResult{0, 0, 0, -1};
+    }
+    const int cb = p.atl[at].cb, n = p.atl[at].n;
+    for (int s = t; s < n; s += blockDim.x) p.catl[cb + s] = at;
   }
 }
 
-// Largest successful candidate (Sec. 3.1 / Sec. 5), then the placements of
-// that candidate gathered back into input order.
-__global__ void select_kernel(Pack p) {
+// Per atlas: the largest successful candidate (Sec. 3.1 / Sec. 5), then the
+// placements of that candidate gathered back into input order.
+__global__ void select_kernel(const Pack *__restrict__ pp) {
   __shared__ int best;
   __shared__ uint32_t err;
-  if (threadIdx.x == 0) {
-    int b = -1;
-    for (int j = kScales - 1; j >= 0; --j)
-      if (p.scale_out[j].success) { b = j; break; }
-    best = b;
-    err = *p.err;
-    PackResult r{0, 0, err, b};
-    if (err & kErrInvalid) r.status = TABI_ERR_INVALID_ARG;
-    else if (err & (kErrPool | kErrRow)) r.status = TABI_ERR_OOM;
-    else if (b < 0) r.status = TABI_ERR_NO_FIT;
-    else { r.status = TABI_OK; r.k = 16 * (b + 1); }
-    *p.result = r;
-  }
-  __syncthreads();
-  if (best < 0 || err) return;
-  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < p.n; s += gridDim.x * blockDim.x) {
-    const int c = p.perm[s];
-    const int4 pl = p.place[(int64_t)best * p.n + s];
-    const tabi_chart_info &inf = p.info[c];
-    tabi_placement o;
-    o.x = pl.x;
-    o.y = pl.y;
-    o.rot90 = (uint8_t)inf.rot90;
-    o.flip_x = (uint8_t)inf.flip_x;
-    o.flip_y = (uint8_t)inf.flip_y;
-    o.mirror = (uint8_t)(pl.w & 1);
-    p.out[c] = o;
+  const Pack &p = *pp;
+  for (int at = blockIdx.x; at < p.A; at += gridDim.x) {
+    if (threadIdx.x == 0) {
+      int b = -1;
+      for (int j = kScales - 1; j >= 0; --j)
+        if (p.scale_out[at * kScales + j].success) { b = j; break; }
+      best = b;
+      err = p.err[at];
+      PackResult r{0, 0, err, b};
+      if (err & kErrInvalid) r.status = TABI_ERR_INVALID_ARG;
+      else if (err & (kErrPool | kErrRow)) r.status = TABI_ERR_OOM;
+      else if (b < 0) r.status = TABI_ERR_NO_FIT;
+      else { r.status = TABI_OK; r.k = 16 * (b + 1); }
+      p.result[at] = r;
+    }
+    __syncthreads();
+    if (best >= 0 && !err) {
+      const AtlasDesc &ad = p.atl[at];
+      const int4 *place = p.place + (int64_t)best * p.N;
+      for (int s = ad.cb + threadIdx.x; s < ad.cb + ad.n; s += blockDim.x) {
+        const int c = p.perm[s];
+        const int4 pl = place[s];
+        const tabi_chart_info &inf = p.info[c];
+        tabi_placement o;
+        o.x = pl.x;
+        o.y = pl.y;
+        o.rot90 = (uint8_t)inf.rot90;
+        o.flip_x = (uint8_t)inf.flip_x;
+        o.flip_y = (uint8_t)inf.flip_y;
+        o.mirror = (uint8_t)(pl.w & 1);
+        ad.out[c - ad.cb] = o;
+      }
+    }
+    __syncthreads();
   }
 }
 
-// Event pairs around each stage of one pack: (stage, start event, end event)
+// Event pairs around each stage: (stage, start event, end event)
 struct StageMarks {
   tabi_ctx *c;
   cudaStream_t st;
   int used = 0;
-  int stage[128];
-  void mark_begin(int s) {
-    if (!c->timing || used >= 128) return;
+  int stage[4 + 3 * kScales + 4];
+  static constexpr int kMax = 4 + 3 * kScales + 4;
+  void begin(int s) {
+    if (used >= kMax) return;
     stage[used] = s;
     cudaEventRecord(c->ev[2 * used], st);
   }
-  void mark_end() {
-    if (!c->timing || used >= 128) return;
+  void end() {
+    if (used >= kMax) return;
     cudaEventRecord(c->ev[2 * used + 1], st);
     ++used;
   }
   void collect() {
-    if (!c->timing) return;
     float total = 0.f;
     for (int i = 0; i < used; ++i) {
       float ms = 0.f;
@@ -174,128 +210,287 @@ struct StageMarks {
   }
 };
 
-tabi_status run_pack(tabi_ctx *ctx, const tabi_params *params, int32_t W, int32_t H, int32_t n,
-                     const uint32_t *offsets, const int32_t *verts, int32_t nv, tabi_placement *out,
-                     int32_t *out_k, void *stream, bool host) {
-  if (!ctx) return TABI_ERR_INVALID_ARG;
-  Guard g(ctx);
-  if (!g.ok) return fail(ctx, TABI_ERR_BUSY, "context in use");
-  if (!valid_params(params)) return fail(ctx, TABI_ERR_INVALID_ARG, "bad params");
-  if (n < 1 || nv < 3 || W < 1 || H < 1 || W > kMaxAtlas || H > kMaxAtlas || !offsets || !verts ||
-      !out || !out_k)
-    return fail(ctx, TABI_ERR_INVALID_ARG, "bad sizes or null pointer");
-  if (host) {
-    if (offsets[0] != 0 || offsets[n] != (uint32_t)nv)
-      return fail(ctx, TABI_ERR_INVALID_ARG, "offsets must run from 0 to n_verts");
+// The launch sequence of a batch: prep, sort, layout, then descending waves
+// of F candidates (plan, raster, compaction, row loop), then selection.
+void enqueue(const Pack *dp, const Launch &L, int F, cudaStream_t st, StageMarks *mk) {
+  auto b = [&](int s) { if (mk) mk->begin(s); };
+  auto e = [&]() { if (mk) mk->end(); };
+  b(0);
+  launch_init(dp, L, st);
+  launch_prep(dp, L, st);
+  e();
+  b(1);
+  launch_sort(dp, L, st);
+  e();
+  b(2);
+  launch_layout(dp, L, st);
+  e();
+  int wave = 0;
+  for (int j_hi = kScales - 1; j_hi >= 0; j_hi -= F, ++wave) {
+    const int j_lo = j_hi - F + 1 < 0 ? 0 : j_hi - F + 1;
+    b(3);
+    launch_plan(dp, L, wave, st);
+    launch_raster(dp, L, j_lo, j_hi, st);
+    e();
+    b(4);
+    launch_hcompact(dp, L, j_lo, j_hi, st);
+    e();
+    b(5);
+    launch_rowloop(dp, L, wave, j_lo, j_hi, st);
+    e();
   }
-  *out_k = 0;
+  b(6);
+  launch_select(dp, L, st);
+  e();
+}
+
+int waves_of(int F) { return (kScales + F - 1) / F; }
+
+tabi_status get_graph(tabi_ctx *ctx, const Launch &L, int F, cudaGraphExec_t *out) {
+  for (const GraphEntry &g : ctx->graphs)
+    if (g.F == F && g.smem == L.rowloop_smem) { *out = g.exec; return TABI_OK; }
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamBeginCapture");
+  enqueue(reinterpret_cast<const Pack *>(ctx->arena), L, F, ctx->cap_stream, nullptr);
+  e = cudaStreamEndCapture(ctx->cap_stream, &graph);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamEndCapture");
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphInstantiate");
+  ctx->graphs.push_back(GraphEntry{F, L.rowloop_smem, exec});
+  *out = exec;
+  return TABI_OK;
+}
+
+bool ensure_hstage(tabi_ctx *ctx, size_t bytes) {
+  if (ctx->hstage_bytes >= bytes) return true;
+  if (ctx->hstage) cudaFreeHost(ctx->hstage);
+  ctx->hstage = nullptr;
+  ctx->hstage_bytes = 0;
+  const size_t want = std::max(bytes, (size_t)1 << 16);
+  if (cudaMallocHost(&ctx->hstage, want) != cudaSuccess) return false;
+  ctx->hstage_bytes = want;
+  return true;
+}
+
+// Host checks of one request; "" if it may run.
+std::string check_request(const tabi_request &r, const tabi_params *params, int smem_dyn, bool host) {
+  if (r.n_charts < 1 || r.n_charts > TABI_MAX_CHARTS) return "chart count outside [1, TABI_MAX_CHARTS]";
+  if (r.n_verts < 3) return "fewer than 3 vertices";
+  if (r.atlas_w < 1 || r.atlas_h < 1 || r.atlas_w > kMaxAtlas || r.atlas_h > kMaxAtlas)
+    return "atlas side outside [1, 8192]";
+  if (!r.offsets || !r.verts || !r.out) return "null pointer";
+  if (rowloop_smem_bytes(r.atlas_w, params->gutter) > (size_t)smem_dyn)
+    return "atlas too wide for this gutter: the row working set exceeds shared memory";
+  if (host && (r.offsets[0] != 0 || r.offsets[r.n_charts] != (uint32_t)r.n_verts))
+    return "offsets must run from 0 to n_verts";
+  return "";
+}
+
+tabi_status run_batch(tabi_ctx *ctx, const tabi_params *params, tabi_request *reqs, int32_t R, void *stream,
+                      bool host) {
+  if (!ctx) return TABI_ERR_INVALID_ARG;
+  Guard guard(ctx);
+  if (!guard.ok) return fail(ctx, TABI_ERR_BUSY, "context in use");
+  if (!valid_params(params)) return fail(ctx, TABI_ERR_INVALID_ARG, "bad params");
+  if (!reqs || R < 1 || R > TABI_MAX_BATCH) return fail(ctx, TABI_ERR_INVALID_ARG, "bad request list");
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e = cudaSetDevice(ctx->device);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
-  int smem_optin = 0;
-  cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
-  if (rowloop_smem_bytes(W, params->gutter) > (size_t)smem_optin)
-    return fail(ctx, TABI_ERR_INVALID_ARG, "atlas too wide for this gutter: the row working set exceeds shared memory");
 
+  // host checks; the atlases that run, largest first (the row-loop queue
+  // takes their tasks in this order)
+  std::vector<int> order;
+  std::string first_error;
+  for (int r = 0; r < R; ++r) {
+    reqs[r].scale_k = 0;
+    reqs[r].status = TABI_ERR_INVALID_ARG;
+    const std::string why = check_request(reqs[r], params, ctx->rowloop_dyn_max, host);
+    if (why.empty()) order.push_back(r);
+    else if (first_error.empty()) first_error = why;
+  }
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int a, int b) { return reqs[a].n_charts > reqs[b].n_charts; });
+  const int A = (int)order.size();
+  ctx->has_last = false;
+  if (A == 0) {
+    ctx->last_error = first_error;
+    return TABI_OK;
+  }
+  int64_t N = 0;
+  for (int i = 0; i < A; ++i) N += reqs[order[i]].n_charts;
+  if (N > 0x7fffffffLL) return fail(ctx, TABI_ERR_INVALID_ARG, "too many charts in one batch");
+
+  // arena: the batch record first (its address is what the graphs read)
   Carve cv{ctx->arena, ctx->arena_bytes};
   Pack p{};
-  p.n = n; p.nv = nv; p.W = W; p.H = H; p.g = params->gutter;
-  p.knee_abs = params->knee_abs_pct; p.knee_rel = params->knee_rel_pct;
-  p.lr_sig = params->lr_sig_pct; p.knee_margin = params->knee_margin;
-  p.flags = params->flags;
-  uint32_t *d_off = nullptr;
-  int32_t *d_verts = nullptr;
-  if (host) {
-    d_off = cv.take<uint32_t>(n + 1);
-    d_verts = cv.take<int32_t>(2 * (size_t)nv);
+  Pack *dpack = cv.take<Pack>(1);
+  AtlasDesc *ddesc = cv.take<AtlasDesc>(A);
+  std::vector<AtlasDesc> desc(A);
+  int64_t cb = 0;
+  for (int i = 0; i < A; ++i) {
+    const tabi_request &r = reqs[order[i]];
+    AtlasDesc &d = desc[i];
+    d.n = r.n_charts;
+    d.nv = r.n_verts;
+    d.W = r.atlas_w;
+    d.H = r.atlas_h;
+    d.cb = (int32_t)cb;
+    d.pad = 0;
+    cb += r.n_charts;
+    if (host) {
+      d.offsets = cv.take<uint32_t>((size_t)r.n_charts + 1);
+      d.verts = cv.take<int32_t>(2 * (size_t)r.n_verts);
+      d.out = cv.take<tabi_placement>((size_t)r.n_charts);
+    } else {
+      d.offsets = r.offsets;
+      d.verts = r.verts;
+      d.out = r.out;
+    }
   }
+  p.A = A;
+  p.N = (int32_t)N;
+  p.g = params->gutter;
+  p.knee_abs = params->knee_abs_pct;
+  p.knee_rel = params->knee_rel_pct;
+  p.lr_sig = params->lr_sig_pct;
+  p.knee_margin = params->knee_margin;
+  p.flags = params->flags;
+  p.F = params->scale_fanout;
+  p.nwaves = waves_of(p.F);
+  p.atl = ddesc;
+  const size_t n = (size_t)N;
+  p.catl = cv.take<int32_t>(n);
   p.info = cv.take<tabi_chart_info>(n);
   p.shape_in = cv.take<ChartShape>(n);
   p.shape = cv.take<ChartShape>(n);
   p.perm = cv.take<int32_t>(n);
   p.hq = cv.take<int32_t>(n);
-  p.sort_tmp = cv.take<uint32_t>(4 * (size_t)n);
-  p.env_off = cv.take<int32_t>(2 * (size_t)n);
-  p.colstart = cv.take<int32_t>((size_t)kScales * n);
-  p.meta = cv.take<int32_t>((size_t)kScales * 4 * n);
-  p.dnext = cv.take<int32_t>((size_t)kScales * n);
-  p.pflags = cv.take<uint8_t>((size_t)kScales * n);
-  p.place = cv.take<int4>((size_t)kScales * n);
-  p.scale_out = cv.take<ScaleOut>(kScales);
-  p.found = cv.take<int32_t>(1);
-  p.result = cv.take<PackResult>(1);
-  p.err = cv.take<uint32_t>(1);
-  tabi_placement *d_out = host ? cv.take<tabi_placement>(n) : out;
-  if (!p.info || !p.shape || !p.place || !p.err || !p.colstart || !d_out || (host && (!d_off || !d_verts)))
-    return fail(ctx, TABI_ERR_OOM, "arena too small for the per-chart arrays");
-  const size_t left = (cv.cap - cv.used) / sizeof(uint32_t);
+  p.wq = cv.take<int32_t>(n);
+  p.sort_tmp = cv.take<uint32_t>(4 * n);
+  p.colstart = cv.take<int32_t>(kScales * n);
+  p.rowstart = cv.take<int32_t>(kScales * n);
+  p.abase = cv.take<int64_t>((size_t)A * kScales * 2);
+  p.atot = cv.take<int64_t>((size_t)A * kScales * 2);
+  p.jtot = cv.take<unsigned long long>(kScales * 2);
+  p.meta = cv.take<int32_t>(kScales * 4 * n);
+  p.dnext = cv.take<int32_t>(kScales * n);
+  p.pflags = cv.take<uint8_t>(kScales * n);
+  p.place = cv.take<int4>(kScales * n);
+  p.scale_out = cv.take<ScaleOut>((size_t)A * kScales);
+  p.found = cv.take<int32_t>(A);
+  p.err = cv.take<uint32_t>(A);
+  p.result = cv.take<PackResult>(A);
+  p.act_info = cv.take<int32_t>(2);
+  p.act_atl = cv.take<int32_t>(A);
+  p.act_pre = cv.take<int32_t>(A);
+  p.act_chart = cv.take<int32_t>(n);
+  p.counter = cv.take<int32_t>(kScales);
+  if (!cv.ok) return fail(ctx, TABI_ERR_OOM, "arena too small for the per-chart arrays");
   // the rest in equal thirds: column words, their chart indices, row words
-  p.col_stride = p.row_stride = (int64_t)(left / (3 * kScales)) & ~(int64_t)63;
+  const size_t left = (cv.cap - cv.used) / sizeof(uint32_t);
+  p.col_cap = p.row_cap = (int64_t)(left / 3) & ~(int64_t)63;
+  if (p.col_cap < 64) return fail(ctx, TABI_ERR_OOM, "arena too small for the envelope pools");
   p.colpool = reinterpret_cast<uint32_t *>(cv.base + cv.used);
-  p.colown = reinterpret_cast<int32_t *>(p.colpool + (int64_t)kScales * p.col_stride);
-  p.pool = reinterpret_cast<uint32_t *>(p.colown + (int64_t)kScales * p.col_stride);
-  if (p.col_stride < 64) return fail(ctx, TABI_ERR_OOM, "arena too small for the envelope pools");
-  p.offsets = host ? d_off : offsets;
-  p.verts = host ? d_verts : verts;
-  p.out = d_out;
+  p.colown = reinterpret_cast<int32_t *>(p.colpool + p.col_cap);
+  p.pool = reinterpret_cast<uint32_t *>(p.colown + p.col_cap);
 
-  if (host) {
-    e = cudaMemcpyAsync(d_off, offsets, sizeof(uint32_t) * (n + 1), cudaMemcpyHostToDevice, st);
+  // the record and the atlas table go up in one copy
+  const size_t desc_off = round256(sizeof(Pack));
+  const size_t up = desc_off + sizeof(AtlasDesc) * (size_t)A;
+  const size_t res_off = round256(up);
+  if (!ensure_hstage(ctx, res_off + sizeof(PackResult) * (size_t)A))
+    return fail(ctx, TABI_ERR_CUDA, "pinned staging allocation failed");
+  memcpy(ctx->hstage, &p, sizeof(Pack));
+  memcpy(ctx->hstage + desc_off, desc.data(), sizeof(AtlasDesc) * (size_t)A);
+  e = cudaMemcpyAsync(dpack, ctx->hstage, up, cudaMemcpyHostToDevice, st);
+  for (int i = 0; i < A && host && e == cudaSuccess; ++i) {
+    const tabi_request &r = reqs[order[i]];
+    e = cudaMemcpyAsync((void *)desc[i].offsets, r.offsets, sizeof(uint32_t) * ((size_t)r.n_charts + 1),
+                        cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
-      e = cudaMemcpyAsync(d_verts, verts, sizeof(int32_t) * 2 * (size_t)nv, cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "input copy");
+      e = cudaMemcpyAsync((void *)desc[i].verts, r.verts, sizeof(int32_t) * 2 * (size_t)r.n_verts,
+                          cudaMemcpyHostToDevice, st);
   }
-  StageMarks mk{ctx, st};
-  mk.mark_begin(0);
-  init_kernel<<<1, 64, 0, st>>>(p);
-  launch_prep(p, st);
-  mk.mark_end();
-  mk.mark_begin(1);
-  launch_sort(p, st);
-  mk.mark_end();
-  mk.mark_begin(2);
-  launch_layout(p, st);
-  mk.mark_end();
-  // descending search in waves of `scale_fanout` candidates; once a wave
-  // has a success every later kernel returns at entry
-  const int F = params->scale_fanout;
-  for (int j_hi = kScales - 1; j_hi >= 0; j_hi -= F) {
-    const int j_lo = j_hi - F + 1 < 0 ? 0 : j_hi - F + 1;
-    mk.mark_begin(3);
-    launch_raster(p, j_lo, j_hi, st);
-    mk.mark_end();
-    mk.mark_begin(4);
-    launch_hcompact(p, j_lo, j_hi, st);
-    mk.mark_end();
-    mk.mark_begin(5);
-    e = launch_rowloop(p, j_lo, j_hi, st);
-    mk.mark_end();
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "rowloop launch");
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "input copy");
+
+  // the row-loop CTA's shared memory: what the widest atlas wants, in
+  // 16 KiB classes (fewer graphs), at most what the device allows
+  size_t want = 0;
+  for (int i = 0; i < A; ++i) want = std::max(want, rowloop_smem_wanted(desc[i].W, p.g));
+  int smem = (int)((want + 16383) & ~(size_t)16383);
+  if (smem > ctx->rowloop_dyn_max) smem = ctx->rowloop_dyn_max;
+  const Launch L{ctx->sms, smem};
+  if (ctx->timing) {
+    StageMarks mk{ctx, st};
+    enqueue(dpack, L, p.F, st, &mk);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "kernel launch");
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "pack");
+    mk.collect();
+  } else {
+    cudaGraphExec_t exec = nullptr;
+    const tabi_status gs = get_graph(ctx, L, p.F, &exec);
+    if (gs != TABI_OK) return gs;
+    e = cudaGraphLaunch(exec, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphLaunch");
   }
-  mk.mark_begin(6);
-  select_kernel<<<(n + 255) / 256 < 148 ? (n + 255) / 256 : 148, 256, 0, st>>>(p);
-  mk.mark_end();
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "kernel launch");
-  e = cudaMemcpyAsync(ctx->host_result, p.result, sizeof(PackResult), cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess && host)
-    e = cudaMemcpyAsync(out, d_out, sizeof(tabi_placement) * n, cudaMemcpyDeviceToHost, st);
+  PackResult *hres = reinterpret_cast<PackResult *>(ctx->hstage + res_off);
+  e = cudaMemcpyAsync(hres, p.result, sizeof(PackResult) * (size_t)A, cudaMemcpyDeviceToHost, st);
+  for (int i = 0; i < A && host && e == cudaSuccess; ++i) {
+    const tabi_request &r = reqs[order[i]];
+    e = cudaMemcpyAsync(r.out, desc[i].out, sizeof(tabi_placement) * (size_t)r.n_charts,
+                        cudaMemcpyDeviceToHost, st);
+  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "pack");
-  mk.collect();
   ctx->last = p;
+  ctx->last_desc = desc;
+  ctx->last_map.assign(R, -1);
+  for (int i = 0; i < A; ++i) {
+    tabi_request &r = reqs[order[i]];
+    ctx->last_map[order[i]] = i;
+    r.status = hres[i].status;
+    r.scale_k = hres[i].status == TABI_OK ? hres[i].k : 0;
+  }
   ctx->has_last = true;
-  const PackResult r = *ctx->host_result;
-  if (r.status == TABI_OK) *out_k = r.k;
+  ctx->last_error = first_error;
+  return TABI_OK;
+}
+
+tabi_status run_single(tabi_ctx *ctx, const tabi_params *params, int32_t W, int32_t H, int32_t n,
+                       const uint32_t *offsets, const int32_t *verts, int32_t nv, tabi_placement *out,
+                       int32_t *out_k, void *stream, bool host) {
+  if (!ctx) return TABI_ERR_INVALID_ARG;
+  if (!out_k) return fail(ctx, TABI_ERR_INVALID_ARG, "null out_k");
+  *out_k = 0;
+  tabi_request r{W, H, n, nv, offsets, verts, out, 0, 0};
+  const tabi_status s = run_batch(ctx, params, &r, 1, stream, host);
+  if (s != TABI_OK) return s;
+  *out_k = r.scale_k;
   switch (r.status) {
     case TABI_OK: return TABI_OK;
     case TABI_ERR_NO_FIT: return fail(ctx, TABI_ERR_NO_FIT, "no candidate scale fits every chart");
-    case TABI_ERR_INVALID_ARG: return fail(ctx, TABI_ERR_INVALID_ARG, "invalid chart (vertices, size or range)");
+    case TABI_ERR_INVALID_ARG:
+      if (ctx->has_last) return fail(ctx, TABI_ERR_INVALID_ARG, "invalid chart (vertices, size or range)");
+      return TABI_ERR_INVALID_ARG;  // host check; last_error says which
     default: return fail(ctx, TABI_ERR_OOM, "arena too small for the envelopes of this input");
   }
 }
 
 }  // namespace
+
+namespace tabi {
+void launch_init(const Pack *dp, const Launch &L, cudaStream_t st) {
+  init_kernel<<<L.sms * 2, 256, 0, st>>>(dp);
+}
+void launch_select(const Pack *dp, const Launch &L, cudaStream_t st) {
+  select_kernel<<<L.sms * 2, 256, 0, st>>>(dp);
+}
+}  // namespace tabi
 
 extern "C" {
 
@@ -323,14 +518,23 @@ tabi_status tabi_ctx_create(tabi_ctx **out, int device, void *arena, size_t aren
   tabi_ctx *c = new tabi_ctx();
   c->device = device;
   c->arena_bytes = arena_bytes;
-  if (arena) {
+  cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device);
+  int optin = 0;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+  // the row loop's dynamic shared memory may use all the opt-in space
+  // beyond its static part; raise the limit once so every graph can launch
+  const int stat = rowloop_static_smem();
+  c->rowloop_dyn_max = stat < 0 ? 0 : (optin - stat) & ~255;
+  bool ok = c->sms > 0 && c->rowloop_dyn_max > 0 && rowloop_prepare(c->rowloop_dyn_max) == cudaSuccess &&
+            cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) == cudaSuccess;
+  if (ok && arena) {
     c->arena = (char *)arena;
-  } else {
-    if (cudaMalloc(&c->arena, arena_bytes) != cudaSuccess) { delete c; return TABI_ERR_CUDA; }
-    c->owned = true;
+  } else if (ok) {
+    ok = cudaMalloc(&c->arena, arena_bytes) == cudaSuccess;
+    c->owned = ok;
   }
-  if (cudaMallocHost(&c->host_result, sizeof(PackResult)) != cudaSuccess) {
-    if (c->owned) cudaFree(c->arena);
+  if (!ok) {
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     delete c;
     return TABI_ERR_CUDA;
   }
@@ -341,9 +545,11 @@ tabi_status tabi_ctx_create(tabi_ctx **out, int device, void *arena, size_t aren
 void tabi_ctx_destroy(tabi_ctx *c) {
   if (!c) return;
   cudaSetDevice(c->device);
+  for (GraphEntry &g : c->graphs) cudaGraphExecDestroy(g.exec);
   for (int i = 0; i < c->n_ev; ++i) cudaEventDestroy(c->ev[i]);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   if (c->owned) cudaFree(c->arena);
-  if (c->host_result) cudaFreeHost(c->host_result);
+  if (c->hstage) cudaFreeHost(c->hstage);
   delete c;
 }
 
@@ -366,24 +572,35 @@ size_t tabi_arena_bytes(int32_t n, int32_t nv, int32_t W, int32_t H, int64_t sum
                         int32_t gutter) {
   (void)W; (void)H;
   if (n < 1) return 0;
-  // column words, their chart indices and row words get equal shares; each
-  // must hold the larger of sum(w') and sum(h') at k = 1024, both below
-  // sum_extent + n (2g + 4)
+  // column words, their chart indices and row words get equal shares; at
+  // candidate k each must hold the larger of sum(w') and sum(h'), both at
+  // most sum_extent * k / 1024 + n (2g + 2) (+ 3 alignment words), and the
+  // 64 candidates of one wave together at most 64 times the k = 1024 sizes
   const size_t pool = (size_t)kScales * 4 * 3 *
-                      ((size_t)sum_extent_texels + (size_t)n * (2 * (size_t)gutter + 4) + 64);
+                      ((size_t)sum_extent_texels + (size_t)n * (2 * (size_t)gutter + 2) + 4);
   return fixed_bytes(n, nv) + pool + (size_t)kScales * 256;
 }
 
 tabi_status tabi_pack(tabi_ctx *ctx, const tabi_params *params, int32_t W, int32_t H, int32_t n,
                       const uint32_t *offsets, const int32_t *verts, int32_t nv, tabi_placement *out,
                       int32_t *out_k, void *stream) {
-  return run_pack(ctx, params, W, H, n, offsets, verts, nv, out, out_k, stream, true);
+  return run_single(ctx, params, W, H, n, offsets, verts, nv, out, out_k, stream, true);
 }
 
 tabi_status tabi_pack_device(tabi_ctx *ctx, const tabi_params *params, int32_t W, int32_t H,
                              int32_t n, const uint32_t *offsets, const int32_t *verts, int32_t nv,
                              tabi_placement *out, int32_t *out_k, void *stream) {
-  return run_pack(ctx, params, W, H, n, offsets, verts, nv, out, out_k, stream, false);
+  return run_single(ctx, params, W, H, n, offsets, verts, nv, out, out_k, stream, false);
+}
+
+tabi_status tabi_pack_batch(tabi_ctx *ctx, const tabi_params *params, tabi_request *reqs, int32_t n_reqs,
+                            void *stream) {
+  return run_batch(ctx, params, reqs, n_reqs, stream, true);
+}
+
+tabi_status tabi_pack_batch_device(tabi_ctx *ctx, const tabi_params *params, tabi_request *reqs,
+                                   int32_t n_reqs, void *stream) {
+  return run_batch(ctx, params, reqs, n_reqs, stream, false);
 }
 
 tabi_status tabi_stage_times(tabi_ctx *ctx, int32_t enable, double *stage_ms, int64_t *launches,
@@ -409,52 +626,80 @@ tabi_status tabi_stage_times(tabi_ctx *ctx, int32_t enable, double *stage_ms, in
   return TABI_OK;
 }
 
-tabi_status tabi_inspect(tabi_ctx *ctx, int32_t what, int32_t scale, void *dst, size_t cap,
-                         size_t *needed) {
+tabi_status tabi_inspect_atlas(tabi_ctx *ctx, int32_t atlas, int32_t what, int32_t scale, void *dst,
+                               size_t cap, size_t *needed) {
   if (!ctx || !ctx->has_last || !needed) return TABI_ERR_INVALID_ARG;
   Guard g(ctx);
   if (!g.ok) return fail(ctx, TABI_ERR_BUSY, "context in use");
-  const Pack &p = ctx->last;
-  const size_t n = (size_t)p.n;
+  if (atlas < 0 || atlas >= (int)ctx->last_map.size() || ctx->last_map[atlas] < 0)
+    return fail(ctx, TABI_ERR_INVALID_ARG, "no such atlas in the last batch");
   if (scale < 0 || scale >= kScales) return fail(ctx, TABI_ERR_INVALID_ARG, "bad scale index");
-  struct Piece { const void *src; size_t bytes; bool host; };
-  const int64_t strides[2] = {p.col_stride, p.row_stride};
-  Piece pcs[4] = {{nullptr, 0, false}, {nullptr, 0, false}, {nullptr, 0, false}, {nullptr, 0, false}};
+  cudaSetDevice(ctx->device);
+  const Pack &p = ctx->last;
+  const int at = ctx->last_map[atlas];
+  const AtlasDesc &ad = ctx->last_desc[at];
+  const size_t n = (size_t)ad.n;
+  const int64_t js = (int64_t)scale * p.N + ad.cb;
+  // region starts and sizes of this atlas (small reads, needed to size ENV)
+  int64_t reg[2 * kScales * 2];
+  cudaError_t e = cudaMemcpy(reg, p.abase + region(at, 0, 0), sizeof(int64_t) * 2 * kScales,
+                             cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(reg + 2 * kScales, p.atot + region(at, 0, 0), sizeof(int64_t) * 2 * kScales,
+                   cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "inspect copy");
+  const int64_t words[2] = {reg[2 * kScales + 2 * scale], reg[2 * kScales + 2 * scale + 1]};
+  struct Piece {
+    const void *src;
+    size_t bytes;
+    bool host;
+  };
+  Piece pcs[5] = {};
+  bool local_perm = false;
   switch (what) {
-    case TABI_INSPECT_CHARTS: pcs[0] = {p.info, sizeof(tabi_chart_info) * n, false}; break;
-    case TABI_INSPECT_PERM: pcs[0] = {p.perm, 4 * n, false}; break;
+    case TABI_INSPECT_CHARTS: pcs[0] = {p.info + ad.cb, sizeof(tabi_chart_info) * n, false}; break;
+    case TABI_INSPECT_PERM: pcs[0] = {p.perm + ad.cb, 4 * n, false}; local_perm = true; break;
     case TABI_INSPECT_ENV:
-      pcs[0] = {strides, sizeof(strides), true};
-      pcs[1] = {p.meta + (int64_t)scale * 4 * n, 16 * n, false};
-      pcs[2] = {p.colpool + (int64_t)scale * p.col_stride, 4 * (size_t)p.col_stride, false};
-      pcs[3] = {p.pool + (int64_t)scale * p.row_stride, 4 * (size_t)p.row_stride, false};
+      pcs[0] = {words, sizeof(words), true};
+      pcs[1] = {p.meta + js * 4, 16 * n, false};
+      pcs[2] = {p.rowstart + js, 4 * n, false};
+      pcs[3] = {p.colpool + reg[2 * scale], 4 * (size_t)words[0], false};
+      pcs[4] = {p.pool + reg[2 * scale + 1], 4 * (size_t)words[1], false};
       break;
-    case TABI_INSPECT_ENV_CAP: pcs[0] = {p.env_off, 8 * n, false}; break;
+    case TABI_INSPECT_REGIONS: pcs[0] = {reg, sizeof(reg), true}; break;
     case TABI_INSPECT_PAIRS:
-      pcs[0] = {p.dnext + (int64_t)scale * n, 4 * n, false};
-      pcs[1] = {p.pflags + (int64_t)scale * n, (size_t)n, false};
+      pcs[0] = {p.dnext + js, 4 * n, false};
+      pcs[1] = {p.pflags + js, n, false};
       break;
     case TABI_INSPECT_SCALE:
-      pcs[0] = {p.scale_out + scale, sizeof(ScaleOut), false};
-      pcs[1] = {p.place + (int64_t)scale * n, 16 * n, false};
+      pcs[0] = {p.scale_out + at * kScales + scale, sizeof(ScaleOut), false};
+      pcs[1] = {p.place + js, 16 * n, false};
       break;
     default: return fail(ctx, TABI_ERR_INVALID_ARG, "bad inspect selector");
   }
-  *needed = pcs[0].bytes + pcs[1].bytes + pcs[2].bytes + pcs[3].bytes;
+  *needed = 0;
+  for (const Piece &pc : pcs) *needed += pc.bytes;
   if (!dst || cap < *needed) return fail(ctx, TABI_ERR_INVALID_ARG, "buffer too small");
-  cudaSetDevice(ctx->device);
   char *d = (char *)dst;
   for (const Piece &pc : pcs) {
     if (!pc.bytes) continue;
     if (pc.host) {
       memcpy(d, pc.src, pc.bytes);
     } else {
-      const cudaError_t e = cudaMemcpy(d, pc.src, pc.bytes, cudaMemcpyDeviceToHost);
+      e = cudaMemcpy(d, pc.src, pc.bytes, cudaMemcpyDeviceToHost);
       if (e != cudaSuccess) return cuda_fail(ctx, e, "inspect copy");
     }
     d += pc.bytes;
   }
+  if (local_perm) {  // sorted position -> input index within the atlas
+    int32_t *pm = (int32_t *)dst;
+    for (size_t s = 0; s < n; ++s) pm[s] -= ad.cb;
+  }
   return TABI_OK;
+}
+
+tabi_status tabi_inspect(tabi_ctx *ctx, int32_t what, int32_t scale, void *dst, size_t cap, size_t *needed) {
+  return tabi_inspect_atlas(ctx, 0, what, scale, dst, cap, needed);
 }
 
 }  // extern "C"

@@ -9,7 +9,7 @@
 // mirrors the other axis' slice extents exactly, so only the slices along
 // the reflected axis are recomputed (two or three slab passes, not five).
 //
-// sort_kernel: one CTA, stable LSD radix sort (three 7-bit digits of
+// sort_kernel: one CTA per atlas, stable LSD radix sort (three 7-bit digits of
 // 2^21 - 1 - Hq), so charts come out by decreasing AABB height with ties in
 // input order.  Ranking inside a warp uses __match_any_sync.
 #include "tabi_internal.cuh"
@@ -84,19 +84,21 @@ __device__ void warp_slices(const int32_t *__restrict__ v, int nv, const Xf &xf,
   }
 }
 
-__global__ void __launch_bounds__(256) prep_kernel(Pack p) {
+// One chart (global input index c) of the batch.
+__device__ __forceinline__ void prep_chart(const Pack &p, int c) {
   const int lane = threadIdx.x & 31;
-  const int c = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
-  if (c >= p.n) return;
-  const uint32_t a = p.offsets[c], b = p.offsets[c + 1];
+  const int at = p.catl[c];
+  const AtlasDesc &ad = p.atl[at];
+  const int lc = c - ad.cb;  // index within its atlas
+  const uint32_t a = ad.offsets[lc], b = ad.offsets[lc + 1];
   const int nv = (int)(b - a);
-  const int32_t *v = p.verts + 2 * (size_t)a;
+  const int32_t *v = ad.verts + 2 * (size_t)a;
   tabi_chart_info *inf = p.info + c;
   ChartShape *sh = p.shape_in + c;
 
   // Sec. 3.1: the chart's AABB (and input validation)
   int32_t mnx = 0x7fffffff, mny = 0x7fffffff, mxx = -0x7fffffff - 1, mxy = -0x7fffffff - 1;
-  int bad = (b < a) || (nv < 3) || (b > (uint32_t)p.nv);
+  int bad = (b < a) || (nv < 3) || (b > (uint32_t)ad.nv);
   if (!bad) {
     for (int i = lane; i < nv; i += 32) {
       const int32_t x = v[2 * i], y = v[2 * i + 1];
@@ -114,10 +116,10 @@ __global__ void __launch_bounds__(256) prep_kernel(Pack p) {
   if (bad || Wq < 256 || Hq < 256) {
     // rejected: keep a harmless one-texel box so later kernels stay in bounds
     if (lane == 0) {
-      inf->orig = c; inf->valid = 0; inf->Wq = 0; inf->Hq = 0;
+      inf->orig = lc; inf->valid = 0; inf->Wq = 0; inf->Hq = 0;
       sh->Wq = 256; sh->Hq = 256; sh->m = 0; sh->pad = 0;
       sh->u0 = sh->u1 = sh->v0 = sh->v1 = 0;
-      atomicOr(p.err, kErrInvalid);
+      atomicOr(p.err + at, kErrInvalid);
     }
     if (lane < kSlices) {
       sh->tlo[lane] = 0; sh->bhi[lane] = 256; sh->llo[lane] = 0; sh->rhi[lane] = 256;
@@ -248,7 +250,7 @@ __global__ void __launch_bounds__(256) prep_kernel(Pack p) {
 
   // write the records
   if (lane == 0) {
-    inf->orig = c; inf->Wq = (int32_t)Wq; inf->Hq = (int32_t)Hq;
+    inf->orig = lc; inf->Wq = (int32_t)Wq; inf->Hq = (int32_t)Hq;
     inf->rot90 = rot; inf->flip_y = xf.fy; inf->flip_x = xf.fx; inf->obb_m = best; inf->valid = 1;
     inf->u0 = bu0; inf->u1 = bu1; inf->v0 = bv0; inf->v1 = bv1;
     inf->area_top = top; inf->area_bot = bottom; inf->area_left = left; inf->area_right = right;
@@ -270,6 +272,14 @@ __global__ void __launch_bounds__(256) prep_kernel(Pack p) {
   }
 }
 
+// one warp per chart, grid-stride over the batch's charts
+__global__ void __launch_bounds__(256) prep_kernel(const Pack *__restrict__ pp) {
+  const Pack &p = *pp;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; c < p.N; c += warps)
+    prep_chart(p, (int)c);
+}
+
 // ---------------------------------------------------------------------------
 // stable radix sort by decreasing Hq (one CTA)
 // ---------------------------------------------------------------------------
@@ -277,13 +287,14 @@ constexpr int kSortThreads = 1024;
 constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kDigits = 128;  // 7-bit digits, 3 passes over 21 bits
 
-__global__ void __launch_bounds__(kSortThreads) sort_kernel(Pack p) {
+__device__ void sort_atlas(const Pack &p, int at) {
   __shared__ uint32_t hist[kDigits * kSortWarps];  // [digit][warp]
   __shared__ uint32_t part[kSortWarps];
-  const int n = p.n, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  uint32_t *kA = p.sort_tmp, *vA = kA + n, *kB = vA + n, *vB = kB + n;
+  const int cb = p.atl[at].cb;
+  const int n = p.atl[at].n, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  uint32_t *kA = p.sort_tmp + 4 * (int64_t)cb, *vA = kA + n, *kB = vA + n, *vB = kB + n;
   for (int c = tid; c < n; c += kSortThreads) {
-    kA[c] = (uint32_t)((1 << 21) - 1 - p.shape_in[c].Hq);
+    kA[c] = (uint32_t)((1 << 21) - 1 - p.shape_in[cb + c].Hq);
     vA[c] = (uint32_t)c;
   }
   const int chunk = ((n + kSortWarps - 1) / kSortWarps + 31) & ~31;
@@ -346,28 +357,36 @@ __global__ void __launch_bounds__(kSortThreads) sort_kernel(Pack p) {
     __syncthreads();
   }
   // three passes: A->B, B->A, A->B
-  for (int s = tid; s < n; s += kSortThreads) p.perm[s] = (int32_t)vB[s];
+  for (int s = tid; s < n; s += kSortThreads) p.perm[cb + s] = cb + (int32_t)vB[s];
+  __syncthreads();  // the shared histogram is reused by the next atlas
 }
 
-__global__ void gather_kernel(Pack p) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= p.n) return;
-  const int c = p.perm[s];
-  p.shape[s] = p.shape_in[c];
-  p.hq[s] = p.shape_in[c].Hq;
+// one CTA per atlas (grid-stride over the batch's atlases)
+__global__ void __launch_bounds__(kSortThreads) sort_kernel(const Pack *__restrict__ pp) {
+  const Pack &p = *pp;
+  for (int at = blockIdx.x; at < p.A; at += gridDim.x) sort_atlas(p, at);
+}
+
+__global__ void gather_kernel(const Pack *__restrict__ pp) {
+  const Pack &p = *pp;
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < p.N; s += (int64_t)gridDim.x * blockDim.x) {
+    const int c = p.perm[s];
+    const ChartShape &sh = p.shape_in[c];
+    p.shape[s] = sh;
+    p.hq[s] = sh.Hq;
+    p.wq[s] = sh.Wq;
+  }
 }
 
 }  // namespace
 
-void launch_prep(const Pack &p, cudaStream_t st) {
-  const int warps_per_block = 8;
-  const int blocks = (p.n + warps_per_block - 1) / warps_per_block;
-  prep_kernel<<<blocks, warps_per_block * 32, 0, st>>>(p);
+void launch_prep(const Pack *dp, const Launch &L, cudaStream_t st) {
+  prep_kernel<<<L.sms * 8, 256, 0, st>>>(dp);
 }
 
-void launch_sort(const Pack &p, cudaStream_t st) {
-  sort_kernel<<<1, kSortThreads, 0, st>>>(p);
-  gather_kernel<<<(p.n + 255) / 256, 256, 0, st>>>(p);
+void launch_sort(const Pack *dp, const Launch &L, cudaStream_t st) {
+  sort_kernel<<<L.sms, kSortThreads, 0, st>>>(dp);
+  gather_kernel<<<L.sms * 4, 256, 0, st>>>(dp);
 }
 
 }  // namespace tabi

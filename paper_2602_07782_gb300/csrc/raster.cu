@@ -15,9 +15,12 @@
 // lanes l-o of the current chunk or, across the chunk seam, of the previous
 // chunk (kept in registers), so each raw value is computed exactly once.
 //
-// Columns go to a per-candidate column pool with the charts back to back
-// (the row loop copies a row's columns in one contiguous range); rows go to
-// a row pool laid out once by the sizes at k = 1024 (the largest scale).
+// Columns and rows go to per-(atlas, candidate) regions of the column and
+// row pools with the charts back to back (the row loop copies a row's
+// columns in one contiguous range).  A batch runs in waves of candidates;
+// the regions of one wave tile the pools and the next wave reuses them.
+// Every kernel here is persistent: a fixed grid loops over the work the
+// wave plan left on the device (the charts of atlases still searching).
 #include "raster_math.cuh"
 #include "tabi_internal.cuh"
 
@@ -62,123 +65,216 @@ __device__ __forceinline__ int32_t warp_axis(const rmath::AxisK &ak, int g, uint
   return warp_max(maxhi);
 }
 
-__global__ void __launch_bounds__(kRasterThreads, 4) raster_kernel(Pack p, int j_lo, int nj, int G) {
+// Warp-items: (chart of an atlas still searching, run of G consecutive
+// candidates).  G is chosen so that the wave has about 32K warp-items.
+__global__ void __launch_bounds__(kRasterThreads, 4) raster_kernel(const Pack *__restrict__ pp, int j_lo, int nj) {
   __shared__ rmath::AxisK axk[kRasterWarps][2];
+  const Pack &p = *pp;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t n = p.n;
+  const int64_t total = p.act_info[1];
+  int G = (int)(((int64_t)nj * total + 32767) / 32768);
+  G = G < 1 ? 1 : (G > nj ? nj : G);
   const int ngroups = (nj + G - 1) / G;
-  if (gw >= n * ngroups) return;
-  if (*(volatile int32_t *)p.found >= 0) return;  // a larger scale already succeeded
-  if (*(volatile uint32_t *)p.err) return;        // invalid input or pool overflow: write nothing
-  const int s = (int)(gw / ngroups);
-  const int j0 = j_lo + (int)(gw % ngroups) * G;
-  const int j1 = min(j0 + G, j_lo + nj);
-  const ChartShape &sh = p.shape[s];
+  const int64_t items = total * ngroups;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t N = p.N;
   const bool use_l = (p.flags & TABI_F_LAABB) != 0, use_o = (p.flags & TABI_F_OBB) != 0;
-  const int m = sh.m;
-  const int64_t C = kObbCos[m], S = kObbSin[m];
-  const int32_t roff = p.env_off[2 * s];
   const int g = p.g;
   rmath::AxisK &a0 = axk[wib][0], &a1 = axk[wib][1];
-  // lanes 24-31 carry the eight corner quantities across the candidates
-  rmath::CornerQ cq;
-  const bool corner_lane = lane >= 24 && use_o && m > 0;
-  if (corner_lane) rmath::corner_init(cq, lane - 24, 16 * (j0 + 1), 16, C, S, sh.u0, sh.u1, sh.v0, sh.v1);
-  for (int j = j0; j < j1; ++j) {
-    const int64_t k = 16 * (j + 1);
-    // per-(chart, scale) constants, lane-parallel: lanes 0-19 the local-AABB
-    // pieces, lanes 20-21 the OBB line terms, lanes 24-31 the corners
-    if (lane < 2 * rmath::kK) {
-      const int ax = lane >= rmath::kK, i = lane - ax * rmath::kK;
-      rmath::setup_piece(ax ? a1 : a0, i, ax ? sh.Hq : sh.Wq, k, ax ? sh.llo[i] : sh.tlo[i],
-                         ax ? sh.rhi[i] : sh.bhi[i]);
-    } else if (lane < 2 * rmath::kK + 2) {
-      const int ax = lane - 2 * rmath::kK;
-      rmath::setup_obb_base(ax ? a1 : a0, ax, sh.Wq, sh.Hq, k, m, C, S, sh.u0, sh.u1, sh.v0, sh.v1, use_l,
-                            use_o);
-    } else if (corner_lane) {
-      rmath::corner_store(cq, lane - 24, (lane - 24) >> 2 ? a1 : a0);
-      rmath::corner_advance(cq);
+  for (int64_t it = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; it < items; it += nwarps) {
+    const int s = p.act_chart[it / ngroups];
+    const int at = p.catl[s];
+    const int cb = p.atl[at].cb;
+    const int j0 = j_lo + (int)(it % ngroups) * G;
+    const int j1 = min(j0 + G, j_lo + nj);
+    const ChartShape &sh = p.shape[s];
+    const int m = sh.m;
+    const int64_t C = kObbCos[m], S = kObbSin[m];
+    // lanes 24-31 carry the eight corner quantities across the candidates
+    rmath::CornerQ cq;
+    const bool corner_lane = lane >= 24 && use_o && m > 0;
+    if (corner_lane) rmath::corner_init(cq, lane - 24, 16 * (j0 + 1), 16, C, S, sh.u0, sh.u1, sh.v0, sh.v1);
+    for (int j = j0; j < j1; ++j) {
+      const int64_t k = 16 * (j + 1);
+      // per-(chart, scale) constants, lane-parallel: lanes 0-19 the local-AABB
+      // pieces, lanes 20-21 the OBB line terms, lanes 24-31 the corners
+      if (lane < 2 * rmath::kK) {
+        const int ax = lane >= rmath::kK, i = lane - ax * rmath::kK;
+        rmath::setup_piece(ax ? a1 : a0, i, ax ? sh.Hq : sh.Wq, k, ax ? sh.llo[i] : sh.tlo[i],
+                           ax ? sh.rhi[i] : sh.bhi[i]);
+      } else if (lane < 2 * rmath::kK + 2) {
+        const int ax = lane - 2 * rmath::kK;
+        rmath::setup_obb_base(ax ? a1 : a0, ax, sh.Wq, sh.Hq, k, m, C, S, sh.u0, sh.u1, sh.v0, sh.v1, use_l,
+                              use_o);
+      } else if (corner_lane) {
+        rmath::corner_store(cq, lane - 24, (lane - 24) >> 2 ? a1 : a0);
+        rmath::corner_advance(cq);
+      }
+      __syncwarp();
+      const int64_t js = (int64_t)j * N + s;
+      const int32_t cstart = p.colstart[js];
+      const int64_t cbase = p.abase[region(at, j, 0)], rbase = p.abase[region(at, j, 1)];
+      const int32_t maxbot = warp_axis(a0, g, p.colpool + cbase + cstart);
+      {  // each column word's chart, so a staged run of words knows its owners
+        int32_t *own = p.colown + cbase + cstart;
+        for (int c = lane; c < a0.len + 2 * g; c += 32) own[c] = s - cb;
+      }
+      warp_axis(a1, g, p.pool + rbase + p.rowstart[js]);
+      if (lane == 0)
+        *reinterpret_cast<int4 *>(p.meta + js * 4) = make_int4(a0.len + 2 * g, a1.len + 2 * g, cstart, maxbot);
+      __syncwarp();
     }
-    __syncwarp();
-    const int32_t cstart = p.colstart[(int64_t)j * n + s];
-    const int32_t maxbot = warp_axis(a0, g, p.colpool + (int64_t)j * p.col_stride + cstart);
-    {  // each column word's chart, so a staged run of words knows its owners
-      int32_t *own = p.colown + (int64_t)j * p.col_stride + cstart;
-      for (int c = lane; c < a0.len + 2 * g; c += 32) own[c] = s;
-    }
-    warp_axis(a1, g, p.pool + (int64_t)j * p.row_stride + roff);
-    if (lane == 0) {
-      int32_t *mt = p.meta + ((int64_t)j * n + s) * 4;
-      mt[0] = a0.len + 2 * g;
-      mt[1] = a1.len + 2 * g;
-      mt[2] = cstart;
-      mt[3] = maxbot;
-    }
-    __syncwarp();
   }
 }
 
-// Pool layouts.  Block j < 64: column offsets of candidate j, charts back to
-// back (exclusive scan of w'(k_j)), so any run of consecutive charts has its
-// columns in one contiguous range.  Block 64: the row pool's offsets from
-// the row counts at k = 1024, rounded to 16-byte segments, shared by every
-// candidate (rows are only read per chart pair).
-__global__ void __launch_bounds__(1024) layout_kernel(Pack p) {
-  __shared__ int64_t part[32];
-  __shared__ int64_t carry;
-  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  const int j = blockIdx.x;
-  const bool rows = j == kScales;
-  const int64_t k = 16 * (j + 1);
-  if (tid == 0) carry = 0;
+// Pool layouts.  For each (atlas, candidate): the padded column count
+// w'(k) = ceil(Wq k / 2^18) + 2g and row count h'(k) of every chart,
+// exclusive-scanned in sorted order, so any run of consecutive charts has
+// its columns in one contiguous range.  One CTA per (atlas, candidate);
+// each thread sums a run of consecutive charts, then a block scan.
+// Exclusive block scan of the pair (x, y); every thread also gets the
+// totals.  part: [66] shared; the caller passes a barrier before the next
+// call reuses it.
+__device__ __forceinline__ void block_scan2(int64_t &x, int64_t &y, int64_t &tx, int64_t &ty,
+                                            int64_t *part) {
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, nw = blockDim.x >> 5;
+  int64_t ix = x, iy = y;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int64_t ux = __shfl_up_sync(0xffffffffu, ix, o), uy = __shfl_up_sync(0xffffffffu, iy, o);
+    if (lane >= o) { ix += ux; iy += uy; }
+  }
+  if (lane == 31) { part[w] = ix; part[32 + w] = iy; }
   __syncthreads();
-  for (int base = 0; base < p.n; base += 1024) {
-    const int s = base + tid;
-    int64_t sz = 0, cap = 0;
-    if (s < p.n) {
-      const ChartShape &sh = p.shape[s];
-      if (rows) {
-        cap = ((sh.Hq + 255) >> 8) + 2 * p.g;
-        sz = (cap + 3) & ~3LL;
-      } else {
-        sz = ((sh.Wq * k + kFix - 1) >> 18) + 2 * p.g;
-      }
-    }
-    int64_t incl = sz;
+  if (w == 0) {
+    const int64_t px = lane < nw ? part[lane] : 0, py = lane < nw ? part[32 + lane] : 0;
+    int64_t qx = px, qy = py;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const int64_t u = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += u;
+      const int64_t ux = __shfl_up_sync(0xffffffffu, qx, o), uy = __shfl_up_sync(0xffffffffu, qy, o);
+      if (lane >= o) { qx += ux; qy += uy; }
     }
-    if (lane == 31) part[w] = incl;
-    __syncthreads();
-    if (w == 0) {
-      const int64_t x = part[lane];
-      int64_t y = x;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int64_t u = __shfl_up_sync(0xffffffffu, y, o);
-        if (lane >= o) y += u;
-      }
-      part[lane] = y - x;
+    part[lane] = qx - px;
+    part[32 + lane] = qy - py;
+    if (lane == 31) { part[64] = qx; part[65] = qy; }
+  }
+  __syncthreads();
+  x = part[w] + ix - x;
+  y = part[32 + w] + iy - y;
+  tx = part[64];
+  ty = part[65];
+}
+
+__global__ void __launch_bounds__(1024) layout_kernel(const Pack *__restrict__ pp) {
+  __shared__ int64_t part[66];
+  const Pack &p = *pp;
+  const int tid = threadIdx.x;
+  const int64_t N = p.N;
+  const int g2 = 2 * p.g;
+  for (int64_t item = blockIdx.x; item < (int64_t)p.A * kScales; item += gridDim.x) {
+    const int at = (int)(item / kScales), j = (int)(item % kScales);
+    const int n = p.atl[at].n, cb = p.atl[at].cb;
+    const int64_t k = 16 * (j + 1);
+    const int P = (n + 1023) >> 10;
+    const int s0 = min(n, tid * P), s1 = min(n, s0 + P);
+    int64_t sc = 0, sr = 0;
+    for (int s = s0; s < s1; ++s) {
+      sc += ((p.wq[cb + s] * k + kFix - 1) >> 18) + g2;
+      sr += ((p.hq[cb + s] * k + kFix - 1) >> 18) + g2;
     }
-    __syncthreads();
-    const int64_t excl = carry + part[w] + incl - sz;
-    if (s < p.n) {
-      if (rows) {
-        p.env_off[2 * s] = (int32_t)excl;
-        p.env_off[2 * s + 1] = (int32_t)cap;
-      } else {
-        p.colstart[(int64_t)j * p.n + s] = (int32_t)excl;
-      }
+    int64_t tx = 0, ty = 0;
+    block_scan2(sc, sr, tx, ty, part);
+    for (int s = s0; s < s1; ++s) {
+      const int64_t js = (int64_t)j * N + cb + s;
+      p.colstart[js] = (int32_t)sc;
+      p.rowstart[js] = (int32_t)sr;
+      sc += ((p.wq[cb + s] * k + kFix - 1) >> 18) + g2;
+      sr += ((p.hq[cb + s] * k + kFix - 1) >> 18) + g2;
     }
-    __syncthreads();
-    if (tid == 1023) carry = excl + sz;
+    if (tid == 0) {
+      // regions are whole 16-byte segments, so staged int4 loads stay aligned
+      const int64_t c4 = (tx + 3) & ~3LL, r4 = (ty + 3) & ~3LL;
+      p.atot[region(at, j, 0)] = c4;
+      p.atot[region(at, j, 1)] = r4;
+      atomicAdd(p.jtot + 2 * j, (unsigned long long)c4);
+      atomicAdd(p.jtot + 2 * j + 1, (unsigned long long)r4);
+    }
     __syncthreads();
   }
-  if (tid == 0 && carry > (rows ? p.row_stride : p.col_stride)) atomicOr(p.err, kErrPool);
+}
+
+// Region bases.  Candidates of one wave share the pools (the candidates of
+// the next wave reuse them): within a wave the larger candidates come first,
+// and within a candidate the atlases in batch order.  An atlas whose region
+// runs past a pool's end is marked out of memory (and never rasterized).
+__global__ void __launch_bounds__(1024) bases_kernel(const Pack *__restrict__ pp) {
+  __shared__ int64_t part[66];
+  __shared__ int64_t carry[2];
+  const Pack &p = *pp;
+  const int tid = threadIdx.x, j = blockIdx.x;
+  const int wv = (kScales - 1 - j) / p.F, jhi = kScales - 1 - wv * p.F;
+  int64_t offc = 0, offr = 0;
+  for (int jj = j + 1; jj <= jhi; ++jj) {
+    offc += (int64_t)p.jtot[2 * jj];
+    offr += (int64_t)p.jtot[2 * jj + 1];
+  }
+  if (tid == 0) { carry[0] = offc; carry[1] = offr; }
+  __syncthreads();
+  for (int base = 0; base < p.A; base += 1024) {
+    const int at = base + tid;
+    int64_t vc = at < p.A ? p.atot[region(at, j, 0)] : 0, vr = at < p.A ? p.atot[region(at, j, 1)] : 0;
+    int64_t ec = vc, er = vr, tx = 0, ty = 0;
+    block_scan2(ec, er, tx, ty, part);
+    if (at < p.A) {
+      const int64_t bc = carry[0] + ec, br = carry[1] + er;
+      p.abase[region(at, j, 0)] = bc;
+      p.abase[region(at, j, 1)] = br;
+      if (bc + vc > p.col_cap || br + vr > p.row_cap) atomicOr(p.err + at, kErrPool);
+    }
+    __syncthreads();
+    if (tid == 0) { carry[0] += tx; carry[1] += ty; }
+    __syncthreads();
+  }
+}
+
+// Wave plan: the atlases still searching (no success yet, no error), in
+// batch order, and a flat list of their charts.
+__global__ void __launch_bounds__(1024) plan_kernel(const Pack *__restrict__ pp, int wave) {
+  __shared__ int64_t part[66];
+  __shared__ int64_t carry[2];
+  const Pack &p = *pp;
+  const int tid = threadIdx.x;
+  if (tid == 0) { carry[0] = 0; carry[1] = 0; }
+  __syncthreads();
+  for (int base = 0; base < p.A; base += 1024) {
+    const int at = base + tid;
+    const bool live = at < p.A && *(volatile int32_t *)(p.found + at) < 0 &&
+                      *(volatile uint32_t *)(p.err + at) == 0;
+    int64_t ea = live ? 1 : 0, ec = live ? p.atl[at].n : 0, tx = 0, ty = 0;
+    block_scan2(ea, ec, tx, ty, part);
+    if (live) {
+      p.act_atl[carry[0] + ea] = at;
+      p.act_pre[carry[0] + ea] = (int32_t)(carry[1] + ec);
+    }
+    __syncthreads();
+    if (tid == 0) { carry[0] += tx; carry[1] += ty; }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    p.act_info[0] = (int32_t)carry[0];
+    p.act_info[1] = (int32_t)carry[1];
+    p.counter[wave] = 0;
+  }
+}
+
+__global__ void __launch_bounds__(256) plan_fill_kernel(const Pack *__restrict__ pp) {
+  const Pack &p = *pp;
+  const int na = p.act_info[0];
+  for (int i = blockIdx.x; i < na; i += gridDim.x) {
+    const int at = p.act_atl[i], pre = p.act_pre[i];
+    const int n = p.atl[at].n, cb = p.atl[at].cb;
+    for (int t = threadIdx.x; t < n; t += blockDim.x) p.act_chart[pre + t] = cb + t;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -200,84 +296,84 @@ __device__ __forceinline__ int32_t warp_scan_incl(int32_t v) {
 // relative to A iff every row of B stays right of all rows of A above it;
 // A may move up relative to B iff every row of A stays left of all rows of
 // B above it.
-__global__ void __launch_bounds__(256) hcompact_kernel(Pack p, int j_lo, int nj) {
+__global__ void __launch_bounds__(256) hcompact_kernel(const Pack *__restrict__ pp, int j_lo, int nj) {
+  const Pack &p = *pp;
   const int lane = threadIdx.x & 31;
-  const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t n = p.n;
-  if (gw >= n * nj) return;
-  if (*(volatile int32_t *)p.found >= 0) return;
-  if (*(volatile uint32_t *)p.err) return;
-  const int j = j_lo + (int)(gw / n);
-  const int s = (int)(gw % n);
-  const int64_t ps = (int64_t)j * n + s;
-  if (s == n - 1) {
-    if (lane == 0) { p.dnext[ps] = 0; p.pflags[ps] = 0; }
-    return;
-  }
-  const int32_t *ma = p.meta + ps * 4, *mb = ma + 4;
-  const int32_t wA = ma[0], hA = ma[1], hB = mb[1];
-  const uint32_t *pool = p.pool + (int64_t)j * p.row_stride;
-  const uint32_t *rowA = pool + p.env_off[2 * s];
-  const uint32_t *rowB = pool + p.env_off[2 * s + 2];
-  const int hmin = hA < hB ? hA : hB;
-  int32_t M = -kBig;
-  for (int r = lane; r < hmin; r += 32) {
-    const int32_t ra = (int32_t)(rowA[r] >> 16), lb = (int32_t)(rowB[r] & 0xffffu);
-    M = max(M, ra - lb);
-  }
-  M = warp_max(M);
-  int32_t d = wA - M;
-  if (d < 0) d = 0;
-  const int32_t off = wA - d;
-  int a_free = 1, b_free = 1;
-  int32_t carry_max = -kBig, carry_min = kBig;  // over rows of A / of B above the chunk
-  const int hmax = hA > hB ? hA : hB;
-  for (int base = 0; base < hmax; base += 32) {
-    const int r = base + lane;
-    const int32_t ra = r < hA ? (int32_t)(rowA[r] >> 16) : -kBig;
-    const int32_t lb = r < hB ? off + (int32_t)(rowB[r] & 0xffffu) : kBig;
-    // exclusive prefix max of R'_A and prefix min of off + L'_B
-    const int32_t imax = warp_scan_incl<true>(ra);
-    const int32_t imin = warp_scan_incl<false>(lb);
-    int32_t emax = __shfl_up_sync(0xffffffffu, imax, 1);
-    int32_t emin = __shfl_up_sync(0xffffffffu, imin, 1);
-    if (lane == 0) { emax = -kBig; emin = kBig; }
-    emax = max(emax, carry_max);
-    emin = min(emin, carry_min);
-    if (r >= 1 && r < hB && lb < emax) b_free = 0;
-    if (r >= 1 && r < hA && ra > emin) a_free = 0;
-    carry_max = max(carry_max, __shfl_sync(0xffffffffu, imax, 31));
-    carry_min = min(carry_min, __shfl_sync(0xffffffffu, imin, 31));
-  }
-  a_free = __all_sync(0xffffffffu, a_free);
-  b_free = __all_sync(0xffffffffu, b_free);
-  if (lane == 0) {
-    p.dnext[ps] = d;
-    p.pflags[ps] = (uint8_t)((a_free ? 0 : 1) | (b_free ? 0 : 2));
+  const int64_t total = p.act_info[1];
+  const int64_t items = total * nj;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t N = p.N;
+  for (int64_t it = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; it < items; it += nwarps) {
+    const int j = j_lo + (int)(it / total);
+    const int s = p.act_chart[it % total];
+    const int at = p.catl[s];
+    const int64_t ps = (int64_t)j * N + s;
+    if (s == p.atl[at].cb + p.atl[at].n - 1) {  // the atlas's last chart has no right neighbour
+      if (lane == 0) { p.dnext[ps] = 0; p.pflags[ps] = 0; }
+      continue;
+    }
+    const int32_t *ma = p.meta + ps * 4, *mb = ma + 4;
+    const int32_t wA = ma[0], hA = ma[1], hB = mb[1];
+    const uint32_t *pool = p.pool + p.abase[region(at, j, 1)];
+    const uint32_t *rowA = pool + p.rowstart[ps];
+    const uint32_t *rowB = pool + p.rowstart[ps + 1];
+    const int hmin = hA < hB ? hA : hB;
+    int32_t M = -kBig;
+    for (int r = lane; r < hmin; r += 32) {
+      const int32_t ra = (int32_t)(rowA[r] >> 16), lb = (int32_t)(rowB[r] & 0xffffu);
+      M = max(M, ra - lb);
+    }
+    M = warp_max(M);
+    int32_t d = wA - M;
+    if (d < 0) d = 0;
+    const int32_t off = wA - d;
+    int a_free = 1, b_free = 1;
+    int32_t carry_max = -kBig, carry_min = kBig;  // over rows of A / of B above the chunk
+    const int hmax = hA > hB ? hA : hB;
+    for (int base = 0; base < hmax; base += 32) {
+      const int r = base + lane;
+      const int32_t ra = r < hA ? (int32_t)(rowA[r] >> 16) : -kBig;
+      const int32_t lb = r < hB ? off + (int32_t)(rowB[r] & 0xffffu) : kBig;
+      // exclusive prefix max of R'_A and prefix min of off + L'_B
+      const int32_t imax = warp_scan_incl<true>(ra);
+      const int32_t imin = warp_scan_incl<false>(lb);
+      int32_t emax = __shfl_up_sync(0xffffffffu, imax, 1);
+      int32_t emin = __shfl_up_sync(0xffffffffu, imin, 1);
+      if (lane == 0) { emax = -kBig; emin = kBig; }
+      emax = max(emax, carry_max);
+      emin = min(emin, carry_min);
+      if (r >= 1 && r < hB && lb < emax) b_free = 0;
+      if (r >= 1 && r < hA && ra > emin) a_free = 0;
+      carry_max = max(carry_max, __shfl_sync(0xffffffffu, imax, 31));
+      carry_min = min(carry_min, __shfl_sync(0xffffffffu, imin, 31));
+    }
+    a_free = __all_sync(0xffffffffu, a_free);
+    b_free = __all_sync(0xffffffffu, b_free);
+    if (lane == 0) {
+      p.dnext[ps] = d;
+      p.pflags[ps] = (uint8_t)((a_free ? 0 : 1) | (b_free ? 0 : 2));
+    }
   }
 }
 
 }  // namespace
 
-void launch_layout(const Pack &p, cudaStream_t st) { layout_kernel<<<kScales + 1, 1024, 0, st>>>(p); }
-
-void launch_raster(const Pack &p, int j_lo, int j_hi, cudaStream_t st) {
-  const int nj = j_hi - j_lo + 1;
-  // candidates per warp: enough warps to fill the GPU, as many candidates
-  // per warp as that allows (each warp walks its candidates incrementally)
-  int64_t G = ((int64_t)nj * p.n + 32767) / 32768;
-  G = G < 1 ? 1 : (G > nj ? nj : G);
-  const int64_t groups = (nj + G - 1) / G;
-  const int64_t warps = (int64_t)p.n * groups;
-  const int64_t blocks = (warps * 32 + kRasterThreads - 1) / kRasterThreads;
-  raster_kernel<<<(unsigned)blocks, kRasterThreads, 0, st>>>(p, j_lo, nj, (int)G);
+void launch_layout(const Pack *dp, const Launch &L, cudaStream_t st) {
+  layout_kernel<<<L.sms * 2, 1024, 0, st>>>(dp);
+  bases_kernel<<<kScales, 1024, 0, st>>>(dp);
 }
 
-void launch_hcompact(const Pack &p, int j_lo, int j_hi, cudaStream_t st) {
-  const int nj = j_hi - j_lo + 1;
-  const int64_t warps = (int64_t)p.n * nj;
-  const int64_t blocks = (warps * 32 + 255) / 256;
-  hcompact_kernel<<<(unsigned)blocks, 256, 0, st>>>(p, j_lo, nj);
+void launch_plan(const Pack *dp, const Launch &L, int wave, cudaStream_t st) {
+  plan_kernel<<<1, 1024, 0, st>>>(dp, wave);
+  plan_fill_kernel<<<L.sms * 2, 256, 0, st>>>(dp);
+}
+
+void launch_raster(const Pack *dp, const Launch &L, int j_lo, int j_hi, cudaStream_t st) {
+  raster_kernel<<<L.sms * 16, kRasterThreads, 0, st>>>(dp, j_lo, j_hi - j_lo + 1);
+}
+
+void launch_hcompact(const Pack *dp, const Launch &L, int j_lo, int j_hi, cudaStream_t st) {
+  hcompact_kernel<<<L.sms * 16, 256, 0, st>>>(dp, j_lo, j_hi - j_lo + 1);
 }
 
 }  // namespace tabi

@@ -1,5 +1,7 @@
-// Row loop of one candidate scale: Algorithm 5 (with Algorithms 2, 3, 4 and
-// the hierarchical selection of Sec. 4.2), one CTA per candidate scale.
+// Row loop of one (atlas, candidate scale): Algorithm 5 (with Algorithms 2,
+// 3, 4 and the hierarchical selection of Sec. 4.2).  The kernel is
+// persistent, one CTA per multiprocessor; each CTA takes (atlas, candidate)
+// tasks of the current wave from a device counter.
 //
 // Shared memory holds the committed frontline (one int per padded atlas
 // column) and the per-row working set.  A row proceeds in barrier-separated
@@ -44,7 +46,9 @@ struct Ctl {
   int32_t row_start, row, committed, fail, prev_ltr, best, prev_maxlen;
   int32_t knee_valid, knee_ltr, knee_l, knee_r;
   int32_t region_lo, region_hi, knee_max;
-  int32_t knee_rows, knees, knee_t[2], stage_lo, stage_hi, red[kNW];
+  int32_t knee_rows, knees, knee_t[2], stage_lo, stage_hi, abort;
+  int32_t t_at, t_j, t_skip;
+  int32_t red[kNW];
 };
 
 // 2x2 max-plus matrix
@@ -100,498 +104,517 @@ __device__ __forceinline__ int32_t seg_scan_max(int32_t v, unsigned heads) {
   return v;
 }
 
-// Maximum over the warp of each of 8 per-lane values, by halving exchanges:
-// after the xor-16/8/4 steps lane l holds one configuration's partial max
-// (configuration ((l >> 2) & 7), bit-reversed below), finished by xor-2/1.
-// Returns that value; the configuration is reduce8_cfg(lane).
-__device__ __forceinline__ int reduce8_cfg(int lane) {
-  return (((lane >> 4) & 1) << 2) | (((lane >> 3) & 1) << 1) | ((lane >> 2) & 1);
-}
-__device__ __forceinline__ int32_t reduce8_max(const int32_t (&v)[8]) {
-  const int lane = threadIdx.x & 31;
-  int32_t a[4], b[2], c;
-  const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4;
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int32_t send = h16 ? v[i] : v[i + 4];
-    const int32_t keep = h16 ? v[i + 4] : v[i];
-    a[i] = max(keep, __shfl_xor_sync(0xffffffffu, send, 16));
-  }
-#pragma unroll
-  for (int i = 0; i < 2; ++i) {
-    const int32_t send = h8 ? a[i] : a[i + 2];
-    const int32_t keep = h8 ? a[i + 2] : a[i];
-    b[i] = max(keep, __shfl_xor_sync(0xffffffffu, send, 8));
-  }
-  {
-    const int32_t send = h4 ? b[0] : b[1];
-    const int32_t keep = h4 ? b[1] : b[0];
-    c = max(keep, __shfl_xor_sync(0xffffffffu, send, 4));
-  }
-  c = max(c, __shfl_xor_sync(0xffffffffu, c, 2));
-  c = max(c, __shfl_xor_sync(0xffffffffu, c, 1));
-  return c;
-}
-
-__global__ void __launch_bounds__(kNT) rowloop_kernel(Pack p, int j_lo, int maxrow, int wp_pad, int scap) {
-  const int j = j_lo + blockIdx.x;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  ScaleOut *so = p.scale_out + j;
-  if (*(volatile int32_t *)p.found >= 0) return;  // a larger scale already succeeded
-  if (*(volatile uint32_t *)p.err) return;        // invalid input or pool overflow
-  const int n = p.n;
-  const int Wp = p.W + 2 * p.g, Hp = p.H + 2 * p.g;
-  const uint32_t flags = p.flags;
-  const bool use_hc = flags & TABI_F_HC;
-  const bool balance = flags & TABI_F_BALANCE;
-
-  extern __shared__ int4 sm4[];
-  uint32_t *stage = reinterpret_cast<uint32_t *>(sm4);  // [scap] the row's column words
-  int32_t *front = reinterpret_cast<int32_t *>(sm4) + scap;  // [wp_pad]
-  int32_t *posN = front + wp_pad;       // [maxrow] side by side
-  int32_t *posH = posN + maxrow;        // [maxrow] compacted
-  int32_t *yb = posH + maxrow;          // [8][maxrow]
-  int32_t *wps = yb + 8 * maxrow;       // [maxrow] w'
-  int32_t *mbot = wps + maxrow;         // [maxrow] max BottomEdge
-  int32_t *woff = mbot + maxrow;        // [maxrow] column start in the column pool
-  int32_t *pflw = woff + maxrow;        // [maxrow] interlock bits of pair (t, t+1)
-  int32_t *hqw = pflw + maxrow;         // [maxrow] unscaled heights
-  int32_t *sown = hqw + maxrow;         // [scap] sorted chart index of each staged word
-  __shared__ Ctl ctl;
-
-  const uint32_t *colp = p.colpool + (int64_t)j * p.col_stride;
-  const int32_t *cown = p.colown + (int64_t)j * p.col_stride;
-  const int32_t *meta = p.meta + (int64_t)j * n * 4;
-  const int32_t *dnext = p.dnext + (int64_t)j * n;
-  const uint8_t *pfl = p.pflags + (int64_t)j * n;
-  int4 *place = p.place + (int64_t)j * n;
-
-  for (int x = tid; x < wp_pad; x += kNT) front[x] = 0;
-  if (tid == 0) {
-    ctl.row_start = 0; ctl.row = 0; ctl.committed = 0; ctl.fail = 0;
-    ctl.prev_ltr = 0; ctl.prev_maxlen = 0; ctl.knee_valid = 0;
-    ctl.knee_rows = 0; ctl.knees = 0;
-  }
-  __syncthreads();
-
-  while (true) {
-    const int row_start = ctl.row_start, row = ctl.row;
-    if (row_start >= n || ctl.fail) break;
-
-    // ---- A: knee refresh (Algorithm 3) and the concavity's max -----------
-    const bool knee = ctl.knee_valid;
-    if (knee) {
-      const int L = ctl.knee_l, R = ctl.knee_r;
-      if (ctl.knee_ltr) {
-        const int32_t cur = front[R];
-        int32_t best = L - 1;
-        for (int x = L + tid; x < R; x += kNT)
-          if (front[x] >= cur) best = max(best, x);
-        best = block_max(best, ctl);
-        if (tid == 0) { ctl.knee_r = best + 1; ctl.region_lo = best + 1; ctl.region_hi = Wp; }
-      } else {
-        const int32_t cur = front[L - 1];
-        int32_t best = R;
-        for (int x = L + tid; x < R; x += kNT)
-          if (front[x] >= cur) best = min(best, x);
-        best = block_min(best, ctl);
-        if (tid == 0) { ctl.knee_l = best; ctl.region_lo = 0; ctl.region_hi = best; }
-      }
-      __syncthreads();
-      int32_t mx = 0;
-      for (int x = ctl.region_lo + tid; x < ctl.region_hi; x += kNT) mx = max(mx, front[x]);
-      mx = block_max(mx, ctl);
-      if (tid == 0) ctl.knee_max = mx;
-    }
-
-    // ---- B: folds (Algorithm 4) -------------------------------------------
-    if (warp < 2) {
-      const int hc = warp;  // warp 0: side by side, warp 1: compacted
-      const bool active = hc == 0 || use_hc;
-      int32_t lenF = 0, lenK = 0;
-      if (active) {
-        const int32_t foldF = Wp;
-        const int32_t foldK = knee ? ctl.region_hi - ctl.region_lo : -1;
-        int32_t *pos = hc ? posH : posN;
-        // state at the chunk start: x of its first chart, x and right edge
-        // of the chart before it (none at the row start)
-        int32_t carry_x = 0, carry_xprev = kNeg, carry_re = kNeg, carry_wprev = kNeg;
-        bool doneF = false, doneK = !knee;
-        // widths and distances of four chunks are loaded together (one
-        // memory round trip per 128 charts), then scanned chunk by chunk
-        for (int g0 = 0; !(doneF && doneK); g0 += 128) {
-          int32_t wq[4], dq[4];
-#pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            const int s = row_start + g0 + 32 * c + lane;
-            wq[c] = s < n ? meta[(int64_t)s * 4] : 0;
-            dq[c] = (hc && s < n) ? dnext[s] : 0;
-          }
-#pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            if (doneF && doneK) break;
-            const int t0 = g0 + 32 * c;
-            const int t = t0 + lane;
-            const int s = row_start + t;
-            const bool valid = s < n;
-            const bool room = t < maxrow;  // the last chunk may run past the row capacity
-            const int32_t w = wq[c], d = dq[c];
-            const int32_t a = hc ? w - d : w;  // x_{t+1} = x_t + a_t unless the clamp binds
-            int32_t incl = a;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-              const int32_t u = __shfl_up_sync(0xffffffffu, incl, o);
-              if (lane >= o) incl += u;
-            }
-            int32_t xnext = carry_x + incl, xt = xnext - a;
-            if (hc) {
-              // clamp: chart t+1 never starts left of chart t-1's right edge
-              int32_t re_prev = __shfl_up_sync(0xffffffffu, xt + w, 1);
-              if (lane == 0) re_prev = carry_re;
-              if (__any_sync(0xffffffffu, valid && xnext < re_prev)) {
-                // the clamp binds in this chunk: (max,+) matrix scan,
-                // state (x_t, x_{t-1}) -> (max(x_t + a_t, x_{t-1} + w_{t-1}), x_t)
-                int32_t wprev = __shfl_up_sync(0xffffffffu, w, 1);
-                if (lane == 0) wprev = carry_wprev;
-                MP m{a, wprev, 0, kNeg};
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                  const MP u = mpshfl_up(m, o);
-                  if (lane >= o) m = mpmul(m, u);
-                }
-                xnext = max(mpadd(m.a00, carry_x), mpadd(m.a01, carry_xprev));
-                xt = __shfl_up_sync(0xffffffffu, xnext, 1);
-                if (lane == 0) xt = carry_x;
-              }
-              carry_xprev = __shfl_sync(0xffffffffu, xt, 31);
-              carry_re = __shfl_sync(0xffffffffu, xt + w, 31);
-              carry_wprev = __shfl_sync(0xffffffffu, w, 31);
-            }
-            carry_x = __shfl_sync(0xffffffffu, xnext, 31);
-            // the first chart that does not fit ends the row
-            const unsigned overF = __ballot_sync(0xffffffffu, !valid || xt + w > foldF);
-            const unsigned overK = __ballot_sync(0xffffffffu, !valid || xt + w > foldK);
-            if (!doneF && overF) { lenF = t0 + __ffs(overF) - 1; doneF = true; }
-            else if (!doneF) lenF = t0 + 32;
-            if (!doneK && overK) { lenK = t0 + __ffs(overK) - 1; doneK = true; }
-            else if (!doneK) lenK = t0 + 32;
-            if (valid && room) pos[t] = xt;
-            if (t0 + 32 >= maxrow && !(doneF && doneK)) {  // cannot happen: rows hold <= W'/(2g+1) + 1 charts
-              if (lane == 0) atomicOr(p.err, kErrRow);
-              doneF = doneK = true;
-            }
-            if ((doneF && lenF >= maxrow) || (doneK && lenK >= maxrow)) {
-              if (lane == 0) atomicOr(p.err, kErrRow);
-              lenF = min(lenF, maxrow - 1);
-              lenK = min(lenK, maxrow - 1);
-            }
-          }
-        }
-      }
-      if (lane == 0) {
-        ctl.len[hc] = active ? lenF : 0;
-        ctl.len[2 + hc] = (active && knee) ? lenK : 0;
-      }
-    } else {
-      // meanwhile the other warps stage the row window into shared memory:
-      // the column words of the charts from row_start on (contiguous in the
-      // column pool; int4 loads from a 16-byte aligned start), and every
-      // chart that can be in this row's widths, column starts, deepest
-      // bottoms, interlock bits and heights
-      const int32_t c4 = meta[(int64_t)row_start * 4 + 2] & ~3;
-      const int32_t nw = (int32_t)min((int64_t)scap, p.col_stride - c4) & ~3;
-      {
-        const int4 *src = reinterpret_cast<const int4 *>(colp + c4);
-        const int4 *osrc = reinterpret_cast<const int4 *>(cown + c4);
-        int4 *odst = reinterpret_cast<int4 *>(sown);
-        for (int q = tid - 64; q < nw / 4; q += kNT - 64) { sm4[q] = src[q]; odst[q] = osrc[q]; }
-        if (tid == 64) { ctl.stage_lo = c4; ctl.stage_hi = c4 + nw; }
-      }
-      // per chart: window entries, offsets zeroed
-      const int spec = min(n - row_start, maxrow);
-      for (int t = tid - 64; t < spec; t += kNT - 64) {
-        const int s = row_start + t;
-        const int4 mt = *reinterpret_cast<const int4 *>(meta + (int64_t)s * 4);
-        wps[t] = mt.x;
-        woff[t] = mt.z;
-        mbot[t] = mt.w;
-        pflw[t] = pfl[s];
-        hqw[t] = p.hq[s];
-#pragma unroll
-        for (int cfg = 0; cfg < 8; ++cfg) yb[cfg * maxrow + t] = 0;  // offsets start at 0
-      }
-    }
-    __syncthreads();
-    if (ctl.len[0] == 0) {  // a chart wider than the atlas: this scale fails
-      if (tid == 0) ctl.fail = 1;
-      break;
-    }
-
-    // ---- D: push ----------------------------------------------------------
-    // warp per chart: its TopEdge (and the mirrored one) is loaded once and
-    // shared by every configuration the chart takes part in; the per-chart
-    // maxima are warp reductions (one instruction per configuration)
-    {
-      const int len0 = ctl.len[0], len1 = ctl.len[1], len2 = ctl.len[2], len3 = ctl.len[3];
-      const int maxlen = max(max(len0, len1), max(len2, len3));
-      const int32_t rlo = ctl.region_lo, rhi = ctl.region_hi;
-      const int32_t slo = ctl.stage_lo, shi = ctl.stage_hi;
-      for (int t = warp; t < maxlen; t += kNW) {
-        const int w = wps[t];
-        const int32_t cs = woff[t];
-        const uint32_t *col = (cs >= slo && cs + w <= shi) ? stage + (cs - slo) : colp + cs;
-        const int32_t pn = posN[t], ph = posH[t];
-        int32_t X[8];
-        X[0] = pn;                X[1] = Wp - pn - w;    // full, side by side
-        X[2] = ph;                X[3] = Wp - ph - w;    // full, compacted
-        X[4] = rlo + pn;          X[5] = rhi - pn - w;   // knee, side by side
-        X[6] = rlo + ph;          X[7] = rhi - ph - w;   // knee, compacted
-        const unsigned on = (t < len0 ? 0x03u : 0u) | (t < len1 ? 0x0cu : 0u) |
-                            (t < len2 ? 0x30u : 0u) | (t < len3 ? 0xc0u : 0u);
-        int32_t acc[8];
-#pragma unroll
-        for (int cfg = 0; cfg < 8; ++cfg) acc[cfg] = 0;  // offsets start at 0 (the atlas top)
-        for (int base = 0; base < w; base += 32) {
-          const int i = base + lane;
-          if (i < w) {
-            const uint32_t f = col[i];
-            const uint32_t r = col[w - 1 - i];
-            const int32_t tf = (int32_t)(f & 0xffffu), tr = (int32_t)(r & 0xffffu);
-#pragma unroll
-            for (int cfg = 0; cfg < 4; ++cfg)
-              if ((on >> cfg) & 1u) acc[cfg] = max(acc[cfg], front[X[cfg] + i] - ((cfg & 1) ? tr : tf));
-            if (knee) {
-#pragma unroll
-              for (int cfg = 4; cfg < 8; ++cfg)
-                if ((on >> cfg) & 1u) acc[cfg] = max(acc[cfg], front[X[cfg] + i] - ((cfg & 1) ? tr : tf));
-            }
-          }
-        }
-        int32_t mine = 0;
-#pragma unroll
-        for (int cfg = 0; cfg < 4; ++cfg) {
-          const int32_t m = __reduce_max_sync(0xffffffffu, acc[cfg]);
-          if (lane == cfg) mine = m;
-        }
-        if (knee) {  // the knee configurations exist only while a knee is live
-#pragma unroll
-          for (int cfg = 4; cfg < 8; ++cfg) {
-            const int32_t m = __reduce_max_sync(0xffffffffu, acc[cfg]);
-            if (lane == cfg) mine = m;
-          }
-        }
-        if (lane < 8 && ((on >> lane) & 1u)) yb[lane * maxrow + t] = mine;
-      }
-    }
-    __syncthreads();
-
-    // ---- E: interlock fixpoint (Algorithm 2) and scores --------------------
-    // warps 0-7: one configuration each; warps 8-9: the knee candidate of the
-    // two atlas-width rows (App. A), so selection finds it ready
-    if (warp < 8) {
-      const int cfg = warp;
-      const int v = cfg >> 1, hc = v & 1;
-      const int len = ctl.len[v];
-      if (len > 0) {
-        int32_t *y = yb + cfg * maxrow;
-        if (hc) {
-          // forward: chart t takes y of t-1 when t cannot move above t-1
-          int32_t carry = kI32Min;
-          for (int t0 = 0; t0 < len; t0 += 32) {
-            const int t = t0 + lane;
-            const bool ok = t < len;
-            const int32_t yv = ok ? y[t] : kI32Min;
-            const bool head = !ok || t == 0 || !(pflw[t - 1] & 2);
-            const unsigned heads = __ballot_sync(0xffffffffu, head);
-            int32_t f = seg_scan_max(yv, heads | 1u);
-            // lanes before the first head of this chunk continue the carry
-            const int first_head = heads ? __ffs(heads) - 1 : 32;
-            if (lane < first_head) f = max(f, carry);
-            carry = __shfl_sync(0xffffffffu, f, 31);
-            // forward maxima feed the backward pass: a backward segment's
-            // maximum of forward maxima is the maximum over the whole chain
-            if (ok) y[t] = f;
-            __syncwarp();
-          }
-          // backward: chart t takes y of t+1 when t cannot move above t+1
-          carry = kI32Min;
-          const int nchunks = (len + 31) / 32;
-          for (int c = nchunks - 1; c >= 0; --c) {
-            const int t = c * 32 + (31 - lane);  // reversed lane order
-            const bool ok = t < len;
-            const int32_t yv = ok ? y[t] : kI32Min;
-            const bool head = !ok || t == len - 1 || !(pflw[t] & 1);
-            const unsigned heads = __ballot_sync(0xffffffffu, head);
-            int32_t b = seg_scan_max(yv, heads | 1u);
-            const int first_head = heads ? __ffs(heads) - 1 : 32;
-            if (lane < first_head) b = max(b, carry);
-            carry = __shfl_sync(0xffffffffu, b, 31);
-            __syncwarp();
-            if (ok) y[t] = b;
-            __syncwarp();
-          }
-        }
-        int32_t mx = kI32Min;
-        for (int t = lane; t < len; t += 32) mx = max(mx, y[t] + mbot[t]);
-        mx = __reduce_max_sync(0xffffffffu, mx);
-        if (lane == 0) {
-          ctl.score[cfg] = max(ctl.committed, mx);
-          ctl.score_knee[cfg] = knee ? max(ctl.knee_max, mx) : 0;
-        }
-      }
-    } else if (warp < 10 && balance) {
-      // largest qualifying unscaled height drop among the first len charts,
-      // first on ties (key = drop << 16 | (0xffff - t))
-      const int len = ctl.len[warp - 8];
-      int64_t key = -1;
-      for (int t = lane; t + 1 < len; t += 32) {
-        const int64_t D = (int64_t)hqw[t] - hqw[t + 1];
-        if (100 * D >= (int64_t)p.knee_abs * 256 * p.H && 100 * D >= (int64_t)p.knee_rel * hqw[t]) {
-          const int64_t kk = (D << 16) | (0xffff - t);
-          key = kk > key ? kk : key;
-        }
-      }
-      key = warp_max(key);
-      if (lane == 0) ctl.knee_t[warp - 8] = key >= 0 ? 0xffff - (int)(key & 0xffff) : -1;
-    }
-    __syncthreads();
-
-    // ---- G: selection (Sec. 4.2); the row state advances ------------------
-    if (warp == 0) {
-      // lane f picks the direction for fold f (0: atlas width, 1: knee)
-      int ch = 0;
-      if (lane < 2 && (lane == 0 || knee)) {
-        const int fold = lane;
-        const int h = (use_hc && ctl.len[fold * 2 + 1] > ctl.len[fold * 2]) ? 1 : 0;
-        const int jl = (fold * 2 + h) * 2, jr = jl + 1;
-        const int32_t kl = fold == 0 ? ctl.score[jl] : ctl.score_knee[jl];
-        const int32_t kr = fold == 0 ? ctl.score[jr] : ctl.score_knee[jr];
-        int dir;
-        if (balance) dir = kl < kr ? 0 : (kr < kl ? 1 : (ctl.prev_ltr ? 1 : 0));
-        else dir = ctl.prev_ltr ? 1 : 0;
-        ch = jl + dir;
-      }
-      const int ch1 = __shfl_sync(0xffffffffu, ch, 1);
-      if (lane == 0) {
-        int best = ch;
-        if (knee && ctl.len[ch1 >> 1] > 0 && ctl.score[ch1] + p.knee_margin <= ctl.score[best]) best = ch1;
-        const int v = best >> 1, dir = best & 1, fold = v >> 1, hc = v & 1;
-        const int len = ctl.len[v];
-        ctl.best = best;
-        if (fold == 0) {
-          // App. A: a knee in this row starts the concavity at the taller
-          // chart's padded edge; no knee if that concavity would be empty
-          int valid = 0;
-          const int t = balance ? ctl.knee_t[hc] : -1;
-          if (t >= 0) {
-            const int32_t X = dir ? Wp - (hc ? posH : posN)[t] - wps[t] : (hc ? posH : posN)[t];
-            ctl.knee_ltr = dir == 0;
-            ctl.knee_l = X;
-            ctl.knee_r = X + wps[t];
-            valid = dir == 0 ? (X + wps[t] < Wp) : (X > 0);
-          }
-          ctl.knee_valid = valid;
-          ctl.knees += valid;
-        } else {
-          ctl.knee_rows += 1;
-        }
-        ctl.committed = ctl.score[best];
-        ctl.fail = ctl.committed > Hp;
-        ctl.prev_ltr = dir == 0;
-        ctl.row_start = row_start + len;
-        ctl.row = row + 1;
-      }
-    }
-    __syncthreads();
-
-    // ---- H: commit ----------------------------------------------------------
-    {
-      const int best = ctl.best;
-      const int v = best >> 1, dir = best & 1, fold = v >> 1, hc = v & 1;
-      const int len = ctl.len[v];
-      const int32_t lo = fold ? ctl.region_lo : 0, hi = fold ? ctl.region_hi : Wp;
-      const int32_t *pos = hc ? posH : posN;
-      const int32_t *y = yb + best * maxrow;
-      const int32_t slo = ctl.stage_lo, shi = ctl.stage_hi;
-      const int fA = woff[0] - slo;
-      const int fB = woff[len - 1] + wps[len - 1] - slo;
-      if (fB <= shi - slo) {
-        for (int f = fA + tid; f < fB; f += kNT) {  // lane per staged column word
-          const int t = sown[f] - row_start;
-          const int w = wps[t];
-          const int i = f - (woff[t] - slo);
-          const int32_t X = dir ? hi - pos[t] - w : lo + pos[t];
-          atomicMax(&front[X + (dir ? w - 1 - i : i)], y[t] + (int32_t)(stage[f] >> 16));
-        }
-      } else {
-      for (int t = warp; t < len; t += kNW) {
-        const int w = wps[t];
-        const int32_t cs = woff[t];
-        const uint32_t *col = (cs >= slo && cs + w <= shi) ? stage + (cs - slo) : colp + cs;
-        const int32_t X = dir ? hi - pos[t] - w : lo + pos[t];
-        const int32_t yt = y[t];
-        for (int i = lane; i < w; i += 32) {
-          const uint32_t word = col[dir ? w - 1 - i : i];
-          atomicMax(&front[X + i], yt + (int32_t)(word >> 16));
-        }
-      }
-      }
-      const int bits = dir | (hc << 1) | (fold << 2);
-      for (int t = tid; t < len; t += kNT) {
-        const int32_t X = dir ? hi - pos[t] - wps[t] : lo + pos[t];
-        place[row_start + t] = make_int4(X, y[t], row, bits);
-      }
-      __syncthreads();
-    }
-  }
-
-  if (tid == 0) {
-    const int ok = !ctl.fail && ctl.row_start >= n;
-    so->success = ok;
-    so->rows = ctl.row;
-    so->knee_rows = ctl.knee_rows;
-    so->knees = ctl.knees;
-    so->score = ctl.committed;
-    so->placed = ctl.row_start;
-    so->evaluated = 1;
-    if (ok) atomicMax(p.found, j);
-  }
-}
-
-}  // namespace
-
 // Row capacity: charts in a row start at least 2g + 1 texels apart (each
 // padded scanline spans 2g + 1 texels or more), so a row holds at most
 // W'/(2g+1) + 1 charts.
-static int rowloop_maxrow(int W, int g) {
+__host__ __device__ __forceinline__ int rowloop_maxrow(int W, int g) {
   const int Wp = W + 2 * g;
   return (Wp / (2 * g + 1) + 2 + 3) & ~3;
 }
 
-// Shared memory of one row-loop CTA without the column stage (the stage
-// takes what is left, up to two atlas widths of column words).
+// Persistent: each CTA takes (atlas, candidate) tasks of the wave from a
+// device counter, larger candidates of an atlas first.  A task is skipped,
+// or abandoned between rows, once a larger candidate of its atlas has
+// succeeded (unless every candidate is to be evaluated).
+__global__ void __launch_bounds__(kNT) rowloop_kernel(const Pack *__restrict__ pp, int wave, int j_lo, int j_hi,
+                                                      int smem_words) {
+  const Pack &p = *pp;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nj = j_hi - j_lo + 1;
+  const uint32_t flags = p.flags;
+  const bool use_hc = flags & TABI_F_HC;
+  const bool balance = flags & TABI_F_BALANCE;
+  const bool eval_all = flags & TABI_F_EVAL_ALL;
+  const int g = p.g;
+  const int64_t N = p.N;
+  extern __shared__ int4 sm4[];
+  __shared__ Ctl ctl;
+
+  while (true) {
+    if (tid == 0) {
+      const int t = atomicAdd(p.counter + wave, 1);
+      int at = -1, j = 0, skip = 1;
+      if (t < *(volatile int32_t *)p.act_info * nj) {
+        at = p.act_atl[t / nj];
+        j = j_hi - t % nj;
+        skip = !eval_all && *(volatile int32_t *)(p.found + at) > j;
+        // the host sizes the CTA for the widest atlas; never overrun it
+        const int W = p.atl[at].W;
+        if (!skip && smem_words < ((W + 2 * g + 3) & ~3) + 15 * rowloop_maxrow(W, g)) {
+          atomicOr(p.err + at, kErrRow);
+          skip = 1;
+        }
+      }
+      ctl.t_at = at;
+      ctl.t_j = j;
+      ctl.t_skip = skip;
+    }
+    __syncthreads();
+    const int at = ctl.t_at, j = ctl.t_j;
+    if (at < 0) break;
+    if (!ctl.t_skip) {
+      const AtlasDesc &ad = p.atl[at];
+      const int n = ad.n, cb = ad.cb;
+      const int Wp = ad.W + 2 * g, Hp = ad.H + 2 * g;
+      const int wp_pad = (Wp + 3) & ~3;
+      const int maxrow = rowloop_maxrow(ad.W, g);
+      // the column stage takes what is left, up to two atlas widths of words
+      // (each staged word costs one word of stage and one of chart index)
+      const int room = (smem_words - wp_pad - 15 * maxrow) / 2;
+      const int scap = (room < 2 * wp_pad ? (room > 0 ? room : 0) : 2 * wp_pad) & ~3;
+      ScaleOut *so = p.scale_out + at * kScales + j;
+
+      uint32_t *stage = reinterpret_cast<uint32_t *>(sm4);  // [scap] the row's column words
+      int32_t *front = reinterpret_cast<int32_t *>(sm4) + scap;  // [wp_pad]
+      int32_t *posN = front + wp_pad;       // [maxrow] side by side
+      int32_t *posH = posN + maxrow;        // [maxrow] compacted
+      int32_t *yb = posH + maxrow;          // [8][maxrow]
+      int32_t *wps = yb + 8 * maxrow;       // [maxrow] w'
+      int32_t *mbot = wps + maxrow;         // [maxrow] max BottomEdge
+      int32_t *woff = mbot + maxrow;        // [maxrow] column start in the column pool
+      int32_t *pflw = woff + maxrow;        // [maxrow] interlock bits of pair (t, t+1)
+      int32_t *hqw = pflw + maxrow;         // [maxrow] unscaled heights
+      int32_t *sown = hqw + maxrow;         // [scap] sorted chart index of each staged word
+
+      const int64_t cbase = p.abase[region(at, j, 0)];
+      const int64_t ccap = p.col_cap - cbase;  // words readable from the region's start
+      const uint32_t *colp = p.colpool + cbase;
+      const int32_t *cown = p.colown + cbase;
+      const int64_t js = (int64_t)j * N + cb;
+      const int32_t *meta = p.meta + js * 4;
+      const int32_t *dnext = p.dnext + js;
+      const uint8_t *pfl = p.pflags + js;
+      const int32_t *hqa = p.hq + cb;
+      int4 *place = p.place + js;
+
+      for (int x = tid; x < wp_pad; x += kNT) front[x] = 0;
+      if (tid == 0) {
+        ctl.row_start = 0; ctl.row = 0; ctl.committed = 0; ctl.fail = 0;
+        ctl.prev_ltr = 0; ctl.prev_maxlen = 0; ctl.knee_valid = 0;
+        ctl.knee_rows = 0; ctl.knees = 0; ctl.abort = 0;
+      }
+      __syncthreads();
+
+      while (true) {
+        const int row_start = ctl.row_start, row = ctl.row;
+        if (row_start >= n || ctl.fail) break;
+
+        // ---- A: knee refresh (Algorithm 3) and the concavity's max -----------
+        const bool knee = ctl.knee_valid;
+        if (knee) {
+          const int L = ctl.knee_l, R = ctl.knee_r;
+          if (ctl.knee_ltr) {
+            const int32_t cur = front[R];
+            int32_t best = L - 1;
+            for (int x = L + tid; x < R; x += kNT)
+              if (front[x] >= cur) best = max(best, x);
+            best = block_max(best, ctl);
+            if (tid == 0) { ctl.knee_r = best + 1; ctl.region_lo = best + 1; ctl.region_hi = Wp; }
+          } else {
+            const int32_t cur = front[L - 1];
+            int32_t best = R;
+            for (int x = L + tid; x < R; x += kNT)
+              if (front[x] >= cur) best = min(best, x);
+            best = block_min(best, ctl);
+            if (tid == 0) { ctl.knee_l = best; ctl.region_lo = 0; ctl.region_hi = best; }
+          }
+          __syncthreads();
+          int32_t mx = 0;
+          for (int x = ctl.region_lo + tid; x < ctl.region_hi; x += kNT) mx = max(mx, front[x]);
+          mx = block_max(mx, ctl);
+          if (tid == 0) ctl.knee_max = mx;
+        }
+
+        // ---- B: folds (Algorithm 4) -------------------------------------------
+        if (warp < 2) {
+          const int hc = warp;  // warp 0: side by side, warp 1: compacted
+          const bool active = hc == 0 || use_hc;
+          int32_t lenF = 0, lenK = 0;
+          if (active) {
+            const int32_t foldF = Wp;
+            const int32_t foldK = knee ? ctl.region_hi - ctl.region_lo : -1;
+            int32_t *pos = hc ? posH : posN;
+            // state at the chunk start: x of its first chart, x and right edge
+            // of the chart before it (none at the row start)
+            int32_t carry_x = 0, carry_xprev = kNeg, carry_re = kNeg, carry_wprev = kNeg;
+            bool doneF = false, doneK = !knee;
+            // widths and distances of four chunks are loaded together (one
+            // memory round trip per 128 charts), then scanned chunk by chunk
+            for (int g0 = 0; !(doneF && doneK); g0 += 128) {
+              int32_t wq[4], dq[4];
+#pragma unroll
+              for (int c = 0; c < 4; ++c) {
+                const int s = row_start + g0 + 32 * c + lane;
+                wq[c] = s < n ? meta[(int64_t)s * 4] : 0;
+                dq[c] = (hc && s < n) ? dnext[s] : 0;
+              }
+#pragma unroll
+              for (int c = 0; c < 4; ++c) {
+                if (doneF && doneK) break;
+                const int t0 = g0 + 32 * c;
+                const int t = t0 + lane;
+                const int s = row_start + t;
+                const bool valid = s < n;
+                const bool room = t < maxrow;  // the last chunk may run past the row capacity
+                const int32_t w = wq[c], d = dq[c];
+                const int32_t a = hc ? w - d : w;  // x_{t+1} = x_t + a_t unless the clamp binds
+                int32_t incl = a;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                  const int32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+                  if (lane >= o) incl += u;
+                }
+                int32_t xnext = carry_x + incl, xt = xnext - a;
+                if (hc) {
+                  // clamp: chart t+1 never starts left of chart t-1's right edge
+                  int32_t re_prev = __shfl_up_sync(0xffffffffu, xt + w, 1);
+                  if (lane == 0) re_prev = carry_re;
+                  if (__any_sync(0xffffffffu, valid && xnext < re_prev)) {
+                    // the clamp binds in this chunk: (max,+) matrix scan,
+                    // state (x_t, x_{t-1}) -> (max(x_t + a_t, x_{t-1} + w_{t-1}), x_t)
+                    int32_t wprev = __shfl_up_sync(0xffffffffu, w, 1);
+                    if (lane == 0) wprev = carry_wprev;
+                    MP m{a, wprev, 0, kNeg};
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                      const MP u = mpshfl_up(m, o);
+                      if (lane >= o) m = mpmul(m, u);
+                    }
+                    xnext = max(mpadd(m.a00, carry_x), mpadd(m.a01, carry_xprev));
+                    xt = __shfl_up_sync(0xffffffffu, xnext, 1);
+                    if (lane == 0) xt = carry_x;
+                  }
+                  carry_xprev = __shfl_sync(0xffffffffu, xt, 31);
+                  carry_re = __shfl_sync(0xffffffffu, xt + w, 31);
+                  carry_wprev = __shfl_sync(0xffffffffu, w, 31);
+                }
+                carry_x = __shfl_sync(0xffffffffu, xnext, 31);
+                // the first chart that does not fit ends the row
+                const unsigned overF = __ballot_sync(0xffffffffu, !valid || xt + w > foldF);
+                const unsigned overK = __ballot_sync(0xffffffffu, !valid || xt + w > foldK);
+                if (!doneF && overF) { lenF = t0 + __ffs(overF) - 1; doneF = true; }
+                else if (!doneF) lenF = t0 + 32;
+                if (!doneK && overK) { lenK = t0 + __ffs(overK) - 1; doneK = true; }
+                else if (!doneK) lenK = t0 + 32;
+                if (valid && room) pos[t] = xt;
+                if (t0 + 32 >= maxrow && !(doneF && doneK)) {  // cannot happen: rows hold <= W'/(2g+1) + 1 charts
+                  if (lane == 0) atomicOr(p.err + at, kErrRow);
+                  doneF = doneK = true;
+                }
+                if ((doneF && lenF >= maxrow) || (doneK && lenK >= maxrow)) {
+                  if (lane == 0) atomicOr(p.err + at, kErrRow);
+                  lenF = min(lenF, maxrow - 1);
+                  lenK = min(lenK, maxrow - 1);
+                }
+              }
+            }
+          }
+          if (lane == 0) {
+            ctl.len[hc] = active ? lenF : 0;
+            ctl.len[2 + hc] = (active && knee) ? lenK : 0;
+          }
+        } else {
+          // meanwhile the other warps stage the row window into shared memory:
+          // the column words of the charts from row_start on (contiguous in the
+          // column pool; int4 loads from a 16-byte aligned start), and every
+          // chart that can be in this row's widths, column starts, deepest
+          // bottoms, interlock bits and heights
+          const int32_t c4 = meta[(int64_t)row_start * 4 + 2] & ~3;
+          const int32_t nw = (int32_t)min((int64_t)scap, ccap - c4) & ~3;
+          {
+            const int4 *src = reinterpret_cast<const int4 *>(colp + c4);
+            const int4 *osrc = reinterpret_cast<const int4 *>(cown + c4);
+            int4 *odst = reinterpret_cast<int4 *>(sown);
+            for (int q = tid - 64; q < nw / 4; q += kNT - 64) { sm4[q] = src[q]; odst[q] = osrc[q]; }
+            if (tid == 64) {
+              ctl.stage_lo = c4;
+              ctl.stage_hi = c4 + nw;
+              // a larger candidate of this atlas has succeeded: this one is moot
+              ctl.abort = !eval_all && *(volatile int32_t *)(p.found + at) > j;
+            }
+          }
+          // per chart: window entries, offsets zeroed
+          const int spec = min(n - row_start, maxrow);
+          for (int t = tid - 64; t < spec; t += kNT - 64) {
+            const int s = row_start + t;
+            const int4 mt = *reinterpret_cast<const int4 *>(meta + (int64_t)s * 4);
+            wps[t] = mt.x;
+            woff[t] = mt.z;
+            mbot[t] = mt.w;
+            pflw[t] = pfl[s];
+            hqw[t] = hqa[s];
+#pragma unroll
+            for (int cfg = 0; cfg < 8; ++cfg) yb[cfg * maxrow + t] = 0;  // offsets start at 0
+          }
+        }
+        __syncthreads();
+        if (ctl.len[0] == 0) {  // a chart wider than the atlas: this scale fails
+          if (tid == 0) ctl.fail = 1;
+          break;
+        }
+
+        // ---- D: push ----------------------------------------------------------
+        // warp per chart: its TopEdge (and the mirrored one) is loaded once and
+        // shared by every configuration the chart takes part in; the per-chart
+        // maxima are warp reductions (one instruction per configuration)
+        {
+          const int len0 = ctl.len[0], len1 = ctl.len[1], len2 = ctl.len[2], len3 = ctl.len[3];
+          const int maxlen = max(max(len0, len1), max(len2, len3));
+          const int32_t rlo = ctl.region_lo, rhi = ctl.region_hi;
+          const int32_t slo = ctl.stage_lo, shi = ctl.stage_hi;
+          for (int t = warp; t < maxlen; t += kNW) {
+            const int w = wps[t];
+            const int32_t cs = woff[t];
+            const uint32_t *col = (cs >= slo && cs + w <= shi) ? stage + (cs - slo) : colp + cs;
+            const int32_t pn = posN[t], ph = posH[t];
+            int32_t X[8];
+            X[0] = pn;                X[1] = Wp - pn - w;    // full, side by side
+            X[2] = ph;                X[3] = Wp - ph - w;    // full, compacted
+            X[4] = rlo + pn;          X[5] = rhi - pn - w;   // knee, side by side
+            X[6] = rlo + ph;          X[7] = rhi - ph - w;   // knee, compacted
+            const unsigned on = (t < len0 ? 0x03u : 0u) | (t < len1 ? 0x0cu : 0u) |
+                                (t < len2 ? 0x30u : 0u) | (t < len3 ? 0xc0u : 0u);
+            int32_t acc[8];
+#pragma unroll
+            for (int cfg = 0; cfg < 8; ++cfg) acc[cfg] = 0;  // offsets start at 0 (the atlas top)
+            for (int base = 0; base < w; base += 32) {
+              const int i = base + lane;
+              if (i < w) {
+                const uint32_t f = col[i];
+                const uint32_t r = col[w - 1 - i];
+                const int32_t tf = (int32_t)(f & 0xffffu), tr = (int32_t)(r & 0xffffu);
+#pragma unroll
+                for (int cfg = 0; cfg < 4; ++cfg)
+                  if ((on >> cfg) & 1u) acc[cfg] = max(acc[cfg], front[X[cfg] + i] - ((cfg & 1) ? tr : tf));
+                if (knee) {
+#pragma unroll
+                  for (int cfg = 4; cfg < 8; ++cfg)
+                    if ((on >> cfg) & 1u) acc[cfg] = max(acc[cfg], front[X[cfg] + i] - ((cfg & 1) ? tr : tf));
+                }
+              }
+            }
+            int32_t mine = 0;
+#pragma unroll
+            for (int cfg = 0; cfg < 4; ++cfg) {
+              const int32_t m = __reduce_max_sync(0xffffffffu, acc[cfg]);
+              if (lane == cfg) mine = m;
+            }
+            if (knee) {  // the knee configurations exist only while a knee is live
+#pragma unroll
+              for (int cfg = 4; cfg < 8; ++cfg) {
+                const int32_t m = __reduce_max_sync(0xffffffffu, acc[cfg]);
+                if (lane == cfg) mine = m;
+              }
+            }
+            if (lane < 8 && ((on >> lane) & 1u)) yb[lane * maxrow + t] = mine;
+          }
+        }
+        __syncthreads();
+
+        // ---- E: interlock fixpoint (Algorithm 2) and scores --------------------
+        // warps 0-7: one configuration each; warps 8-9: the knee candidate of the
+        // two atlas-width rows (App. A), so selection finds it ready
+        if (warp < 8) {
+          const int cfg = warp;
+          const int v = cfg >> 1, hc = v & 1;
+          const int len = ctl.len[v];
+          if (len > 0) {
+            int32_t *y = yb + cfg * maxrow;
+            if (hc) {
+              // forward: chart t takes y of t-1 when t cannot move above t-1
+              int32_t carry = kI32Min;
+              for (int t0 = 0; t0 < len; t0 += 32) {
+                const int t = t0 + lane;
+                const bool ok = t < len;
+                const int32_t yv = ok ? y[t] : kI32Min;
+                const bool head = !ok || t == 0 || !(pflw[t - 1] & 2);
+                const unsigned heads = __ballot_sync(0xffffffffu, head);
+                int32_t f = seg_scan_max(yv, heads | 1u);
+                // lanes before the first head of this chunk continue the carry
+                const int first_head = heads ? __ffs(heads) - 1 : 32;
+                if (lane < first_head) f = max(f, carry);
+                carry = __shfl_sync(0xffffffffu, f, 31);
+                // forward maxima feed the backward pass: a backward segment's
+                // maximum of forward maxima is the maximum over the whole chain
+                if (ok) y[t] = f;
+                __syncwarp();
+              }
+              // backward: chart t takes y of t+1 when t cannot move above t+1
+              carry = kI32Min;
+              const int nchunks = (len + 31) / 32;
+              for (int c = nchunks - 1; c >= 0; --c) {
+                const int t = c * 32 + (31 - lane);  // reversed lane order
+                const bool ok = t < len;
+                const int32_t yv = ok ? y[t] : kI32Min;
+                const bool head = !ok || t == len - 1 || !(pflw[t] & 1);
+                const unsigned heads = __ballot_sync(0xffffffffu, head);
+                int32_t b = seg_scan_max(yv, heads | 1u);
+                const int first_head = heads ? __ffs(heads) - 1 : 32;
+                if (lane < first_head) b = max(b, carry);
+                carry = __shfl_sync(0xffffffffu, b, 31);
+                __syncwarp();
+                if (ok) y[t] = b;
+                __syncwarp();
+              }
+            }
+            int32_t mx = kI32Min;
+            for (int t = lane; t < len; t += 32) mx = max(mx, y[t] + mbot[t]);
+            mx = __reduce_max_sync(0xffffffffu, mx);
+            if (lane == 0) {
+              ctl.score[cfg] = max(ctl.committed, mx);
+              ctl.score_knee[cfg] = knee ? max(ctl.knee_max, mx) : 0;
+            }
+          }
+        } else if (warp < 10 && balance) {
+          // largest qualifying unscaled height drop among the first len charts,
+          // first on ties (key = drop << 16 | (0xffff - t))
+          const int len = ctl.len[warp - 8];
+          int64_t key = -1;
+          for (int t = lane; t + 1 < len; t += 32) {
+            const int64_t D = (int64_t)hqw[t] - hqw[t + 1];
+            if (100 * D >= (int64_t)p.knee_abs * 256 * ad.H && 100 * D >= (int64_t)p.knee_rel * hqw[t]) {
+              const int64_t kk = (D << 16) | (0xffff - t);
+              key = kk > key ? kk : key;
+            }
+          }
+          key = warp_max(key);
+          if (lane == 0) ctl.knee_t[warp - 8] = key >= 0 ? 0xffff - (int)(key & 0xffff) : -1;
+        }
+        __syncthreads();
+
+        // ---- G: selection (Sec. 4.2); the row state advances ------------------
+        if (warp == 0) {
+          // lane f picks the direction for fold f (0: atlas width, 1: knee)
+          int ch = 0;
+          if (lane < 2 && (lane == 0 || knee)) {
+            const int fold = lane;
+            const int h = (use_hc && ctl.len[fold * 2 + 1] > ctl.len[fold * 2]) ? 1 : 0;
+            const int jl = (fold * 2 + h) * 2, jr = jl + 1;
+            const int32_t kl = fold == 0 ? ctl.score[jl] : ctl.score_knee[jl];
+            const int32_t kr = fold == 0 ? ctl.score[jr] : ctl.score_knee[jr];
+            int dir;
+            if (balance) dir = kl < kr ? 0 : (kr < kl ? 1 : (ctl.prev_ltr ? 1 : 0));
+            else dir = ctl.prev_ltr ? 1 : 0;
+            ch = jl + dir;
+          }
+          const int ch1 = __shfl_sync(0xffffffffu, ch, 1);
+          if (lane == 0) {
+            int best = ch;
+            if (knee && ctl.len[ch1 >> 1] > 0 && ctl.score[ch1] + p.knee_margin <= ctl.score[best]) best = ch1;
+            const int v = best >> 1, dir = best & 1, fold = v >> 1, hc = v & 1;
+            const int len = ctl.len[v];
+            ctl.best = best;
+            if (fold == 0) {
+              // App. A: a knee in this row starts the concavity at the taller
+              // chart's padded edge; no knee if that concavity would be empty
+              int valid = 0;
+              const int t = balance ? ctl.knee_t[hc] : -1;
+              if (t >= 0) {
+                const int32_t X = dir ? Wp - (hc ? posH : posN)[t] - wps[t] : (hc ? posH : posN)[t];
+                ctl.knee_ltr = dir == 0;
+                ctl.knee_l = X;
+                ctl.knee_r = X + wps[t];
+                valid = dir == 0 ? (X + wps[t] < Wp) : (X > 0);
+              }
+              ctl.knee_valid = valid;
+              ctl.knees += valid;
+            } else {
+              ctl.knee_rows += 1;
+            }
+            ctl.committed = ctl.score[best];
+            ctl.fail = ctl.abort ? 2 : (ctl.committed > Hp ? 1 : 0);
+            ctl.prev_ltr = dir == 0;
+            ctl.row_start = row_start + len;
+            ctl.row = row + 1;
+          }
+        }
+        __syncthreads();
+
+        // ---- H: commit ----------------------------------------------------------
+        {
+          const int best = ctl.best;
+          const int v = best >> 1, dir = best & 1, fold = v >> 1, hc = v & 1;
+          const int len = ctl.len[v];
+          const int32_t lo = fold ? ctl.region_lo : 0, hi = fold ? ctl.region_hi : Wp;
+          const int32_t *pos = hc ? posH : posN;
+          const int32_t *y = yb + best * maxrow;
+          const int32_t slo = ctl.stage_lo, shi = ctl.stage_hi;
+          const int fA = woff[0] - slo;
+          const int fB = woff[len - 1] + wps[len - 1] - slo;
+          if (fB <= shi - slo) {
+            for (int f = fA + tid; f < fB; f += kNT) {  // lane per staged column word
+              const int t = sown[f] - row_start;
+              const int w = wps[t];
+              const int i = f - (woff[t] - slo);
+              const int32_t X = dir ? hi - pos[t] - w : lo + pos[t];
+              atomicMax(&front[X + (dir ? w - 1 - i : i)], y[t] + (int32_t)(stage[f] >> 16));
+            }
+          } else {
+          for (int t = warp; t < len; t += kNW) {
+            const int w = wps[t];
+            const int32_t cs = woff[t];
+            const uint32_t *col = (cs >= slo && cs + w <= shi) ? stage + (cs - slo) : colp + cs;
+            const int32_t X = dir ? hi - pos[t] - w : lo + pos[t];
+            const int32_t yt = y[t];
+            for (int i = lane; i < w; i += 32) {
+              const uint32_t word = col[dir ? w - 1 - i : i];
+              atomicMax(&front[X + i], yt + (int32_t)(word >> 16));
+            }
+          }
+          }
+          const int bits = dir | (hc << 1) | (fold << 2);
+          for (int t = tid; t < len; t += kNT) {
+            const int32_t X = dir ? hi - pos[t] - wps[t] : lo + pos[t];
+            place[row_start + t] = make_int4(X, y[t], row, bits);
+          }
+          __syncthreads();
+        }
+      }
+
+      if (tid == 0) {
+        const int ok = !ctl.fail && ctl.row_start >= n;
+        so->success = ok;
+        so->rows = ctl.row;
+        so->knee_rows = ctl.knee_rows;
+        so->knees = ctl.knees;
+        so->score = ctl.committed;
+        so->placed = ctl.row_start;
+        so->evaluated = ctl.fail == 2 ? 2 : 1;
+        if (ok) atomicMax(p.found + at, j);
+      }
+    }  // task not skipped
+    __syncthreads();  // ctl is rewritten by the next task
+  }  // task loop
+}
+
+}  // namespace
+
+// Shared memory of one row-loop CTA without the column stage.
 size_t rowloop_smem_bytes(int W, int g) {
   const int Wp = W + 2 * g;
   const int wp_pad = (Wp + 3) & ~3;
   return sizeof(int32_t) * ((size_t)wp_pad + 15 * (size_t)rowloop_maxrow(W, g)) + sizeof(Ctl) + 64;
 }
 
-cudaError_t launch_rowloop(const Pack &p, int j_lo, int j_hi, cudaStream_t st) {
-  const int Wp = p.W + 2 * p.g;
-  const int wp_pad = (Wp + 3) & ~3;
-  const int maxrow = rowloop_maxrow(p.W, p.g);
-  int dev = 0, optin = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  const size_t base = rowloop_smem_bytes(p.W, p.g);
-  // each staged column word costs 4 bytes of stage and 4 of chart index
-  const int64_t room = ((int64_t)optin - (int64_t)base) / 8;
-  const int scap = (int)(room < 2 * wp_pad ? (room > 0 ? room : 0) : 2 * wp_pad) & ~3;
-  const size_t smem = sizeof(int32_t) * (2 * (size_t)scap + wp_pad + 15 * (size_t)maxrow);
-  cudaError_t e = cudaFuncSetAttribute(rowloop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  rowloop_kernel<<<j_hi - j_lo + 1, kNT, smem, st>>>(p, j_lo, maxrow, wp_pad, scap);
-  return cudaGetLastError();
+// ... with a stage of two atlas widths (what an atlas of width W would use).
+size_t rowloop_smem_wanted(int W, int g) {
+  const int wp_pad = (W + 2 * g + 3) & ~3;
+  return rowloop_smem_bytes(W, g) + 2 * sizeof(int32_t) * 2 * (size_t)wp_pad;
+}
+
+int rowloop_static_smem() {
+  cudaFuncAttributes a;
+  if (cudaFuncGetAttributes(&a, rowloop_kernel) != cudaSuccess) return -1;
+  return (int)a.sharedSizeBytes;
+}
+
+cudaError_t rowloop_prepare(int smem) {
+  return cudaFuncSetAttribute(rowloop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+
+void launch_rowloop(const Pack *dp, const Launch &L, int wave, int j_lo, int j_hi, cudaStream_t st) {
+  // one CTA per multiprocessor (1024 threads and most of its shared memory)
+  rowloop_kernel<<<L.sms, kNT, L.rowloop_smem, st>>>(dp, wave, j_lo, j_hi, L.rowloop_smem / 4);
 }
 
 }  // namespace tabi

@@ -17,7 +17,7 @@ constexpr int kMaxAtlas = 8192;      // atlas side limit (front fits shared memo
 constexpr int kMaxGutter = 8;
 constexpr int64_t kFix = 1LL << 18;  // scaled units per texel (Q.8 * k)
 
-// Error bits raised by kernels into Pack::err.
+// Error bits raised by kernels into Pack::err (one word per atlas).
 enum : uint32_t { kErrInvalid = 1u, kErrPool = 2u, kErrRow = 4u };
 
 // Scale-independent shape record of one chart, in sorted order (what the
@@ -28,12 +28,14 @@ struct __align__(16) ChartShape {
   int32_t tlo[kSlices], bhi[kSlices], llo[kSlices], rhi[kSlices];
 };
 
-// Per-candidate-scale summary (TABI_INSPECT_SCALE header).
+// Per-(atlas, candidate scale) summary (TABI_INSPECT_SCALE header).
+// evaluated: 0 not run, 1 ran to its end, 2 abandoned once a larger
+// candidate of the same atlas had succeeded.
 struct ScaleOut {
   int32_t success, rows, knee_rows, knees, score, placed, evaluated, pad;
 };
 
-// Result of one pack, written on the device and read once by the host.
+// Result of one atlas, written on the device and read once by the host.
 struct PackResult {
   int32_t status;  // tabi_status
   int32_t k;
@@ -41,48 +43,86 @@ struct PackResult {
   int32_t best_j;
 };
 
-// Everything one pack needs on the device; pointers into the arena.
-struct Pack {
-  int32_t n, nv, W, H, g;
-  int32_t knee_abs, knee_rel, lr_sig, knee_margin;
-  uint32_t flags;
-  const uint32_t *offsets;
-  const int32_t *verts;
-  tabi_chart_info *info;   // [n] input order
-  ChartShape *shape_in;    // [n] input order
-  ChartShape *shape;       // [n] sorted order
-  int32_t *perm;           // [n] sorted position -> input index
-  int32_t *hq;             // [n] sorted Hq (Q.8)
-  uint32_t *sort_tmp;      // [4n] radix-sort ping-pong
-  int32_t *env_off;        // [2n] row-pool offset and row capacity (sizes at k = 1024)
-  int32_t *colstart;       // [64 * n] column-pool offset of each chart at each candidate
-  int64_t col_stride;      // uint32 column entries per candidate scale
-  int64_t row_stride;      // uint32 row entries per candidate scale
-  uint32_t *colpool;       // [64 * col_stride] Top' | Bot' << 16, charts back to back
-  int32_t *colown;         // [64 * col_stride] sorted chart index of each column word
-  uint32_t *pool;          // [64 * row_stride] L' | R' << 16, k = 1024 capacities
-  int32_t *meta;           // [64 * 4n]: w', h', column start, max bottom
-  int32_t *dnext;          // [64 * n]  compacting distance (s, s+1)
-  uint8_t *pflags;         // [64 * n]  interlock bits
-  int4 *place;             // [64 * n]  x, y, row, bits
-  ScaleOut *scale_out;     // [64]
-  int32_t *found;          // highest successful candidate index so far (-1 none)
-  PackResult *result;
-  uint32_t *err;
-  tabi_placement *out;     // [n] input order
+// One atlas of a batch: its inputs and output (device pointers) and where
+// its charts sit in the batch's chart index space [cb, cb + n).
+struct AtlasDesc {
+  const uint32_t *offsets;  // [n + 1] CSR over this atlas's vertices
+  const int32_t *verts;     // [2 nv] x, y pairs, Q.8
+  tabi_placement *out;      // [n] input order
+  int32_t n, nv, W, H;
+  int32_t cb, pad;
 };
 
+// Everything a batch of packs needs on the device.  The record itself lives
+// in device memory (kernels take a pointer to it), so one captured launch
+// sequence serves every batch with the same wave structure.
+//
+// Chart indices are global over the batch: atlas a owns input and sorted
+// positions [cb_a, cb_a + n_a).  Per-candidate arrays are [64][N].
+struct Pack {
+  int32_t A, N;                 // atlases, charts over all atlases
+  int32_t g, knee_abs, knee_rel, lr_sig, knee_margin;
+  uint32_t flags;
+  int32_t F;                    // candidates per wave (scale fan-out)
+  int32_t nwaves;
+  const AtlasDesc *atl;         // [A]
+  int32_t *catl;                // [N] atlas of each chart
+  tabi_chart_info *info;        // [N] input order
+  ChartShape *shape_in;         // [N] input order
+  ChartShape *shape;            // [N] sorted order
+  int32_t *perm;                // [N] sorted position -> input index
+  int32_t *hq, *wq;             // [N] sorted Hq, Wq (Q.8)
+  uint32_t *sort_tmp;           // [4N] radix-sort ping-pong
+  int32_t *colstart;            // [64 N] column offset inside the (atlas, candidate) region
+  int32_t *rowstart;            // [64 N] row offset inside the (atlas, candidate) region
+  int64_t *abase;               // [A][64][2] column / row region start in the pools
+  int64_t *atot;                // [A][64][2] column / row region words (multiples of 4)
+  unsigned long long *jtot;     // [64][2] words of all atlases at candidate j
+  int64_t col_cap, row_cap;     // words per pool
+  uint32_t *colpool;            // Top' | Bot' << 16 per padded column
+  int32_t *colown;              // atlas-local sorted index of each column word
+  uint32_t *pool;               // L' | R' << 16 per padded row
+  int32_t *meta;                // [64 N][4]: w', h', column start, max bottom
+  int32_t *dnext;               // [64 N] compacting distance (s, s+1)
+  uint8_t *pflags;              // [64 N] interlock bits
+  int4 *place;                  // [64 N] x, y, row, bits
+  ScaleOut *scale_out;          // [A][64]
+  int32_t *found;               // [A] highest successful candidate so far (-1 none)
+  uint32_t *err;                // [A]
+  PackResult *result;           // [A]
+  int32_t *act_info;            // [2]: atlases still searching, their charts
+  int32_t *act_atl;             // [A] those atlases, in batch order
+  int32_t *act_pre;             // [A] their first position in act_chart
+  int32_t *act_chart;           // [N] their charts (global sorted index)
+  int32_t *counter;             // [64] row-loop task counter of each wave
+};
+
+// Region of (atlas a, candidate j) in the column / row pools.
+__host__ __device__ __forceinline__ int64_t region(int a, int j, int which) {
+  return ((int64_t)a * kScales + j) * 2 + which;
+}
+
 // Launch helpers (each .cu file owns its kernels).  All are asynchronous on
-// `st`; `j_hi` .. `j_lo` is a descending block of candidate indices.
-void launch_prep(const Pack &p, cudaStream_t st);
-void launch_sort(const Pack &p, cudaStream_t st);
-void launch_layout(const Pack &p, cudaStream_t st);
-void launch_raster(const Pack &p, int j_lo, int j_hi, cudaStream_t st);
-void launch_hcompact(const Pack &p, int j_lo, int j_hi, cudaStream_t st);
-cudaError_t launch_rowloop(const Pack &p, int j_lo, int j_hi, cudaStream_t st);
-size_t rowloop_smem_bytes(int W, int g);  // shared memory one row-loop CTA needs
-void launch_select(const Pack &p, cudaStream_t st);
-void launch_init(const Pack &p, cudaStream_t st);
+// `st` and capturable; grids are fixed per device (persistent kernels loop
+// over the device-side work), so they depend only on the wave structure.
+// `j_lo` .. `j_hi` is the wave's block of candidate indices.
+struct Launch {
+  int sms;          // multiprocessors
+  int rowloop_smem; // dynamic shared memory of a row-loop CTA
+};
+void launch_init(const Pack *dp, const Launch &L, cudaStream_t st);
+void launch_prep(const Pack *dp, const Launch &L, cudaStream_t st);
+void launch_sort(const Pack *dp, const Launch &L, cudaStream_t st);
+void launch_layout(const Pack *dp, const Launch &L, cudaStream_t st);
+void launch_plan(const Pack *dp, const Launch &L, int wave, cudaStream_t st);
+void launch_raster(const Pack *dp, const Launch &L, int j_lo, int j_hi, cudaStream_t st);
+void launch_hcompact(const Pack *dp, const Launch &L, int j_lo, int j_hi, cudaStream_t st);
+cudaError_t rowloop_prepare(int smem);  // raise the CTA's shared-memory limit (not capturable)
+int rowloop_static_smem();              // the row-loop kernel's static shared memory
+void launch_rowloop(const Pack *dp, const Launch &L, int wave, int j_lo, int j_hi, cudaStream_t st);
+void launch_select(const Pack *dp, const Launch &L, cudaStream_t st);
+size_t rowloop_smem_bytes(int W, int g);       // shared memory a row-loop CTA needs without the stage
+size_t rowloop_smem_wanted(int W, int g);      // ... with a stage of two atlas widths
 
 // ---------------------------------------------------------------------------
 // small device helpers

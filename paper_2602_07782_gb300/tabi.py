@@ -19,8 +19,11 @@ LIB_PATH = os.path.join(HERE, "_build", "libtabi.so")
 TABI_OK, TABI_ERR_INVALID_ARG, TABI_ERR_NO_FIT, TABI_ERR_OOM, TABI_ERR_CUDA, TABI_ERR_TIMEOUT, TABI_ERR_BUSY = range(7)
 F_HC, F_BALANCE, F_OBB, F_LAABB = 1, 2, 4, 8
 F_ALL = 15
-INSPECT_CHARTS, INSPECT_PERM, INSPECT_ENV, INSPECT_ENV_CAP, INSPECT_PAIRS, INSPECT_SCALE = 1, 2, 3, 4, 5, 6
+F_EVAL_ALL = 16  # inspection aid: every candidate's row loop runs to its end
+INSPECT_CHARTS, INSPECT_PERM, INSPECT_ENV, INSPECT_REGIONS, INSPECT_PAIRS, INSPECT_SCALE = 1, 2, 3, 4, 5, 6
 N_SCALES = 64
+MAX_CHARTS = 131072
+MAX_BATCH = 65536
 
 
 class Params(ctypes.Structure):
@@ -28,6 +31,13 @@ class Params(ctypes.Structure):
                 ("knee_abs_pct", ctypes.c_int32), ("knee_rel_pct", ctypes.c_int32),
                 ("lr_sig_pct", ctypes.c_int32), ("knee_margin", ctypes.c_int32),
                 ("flags", ctypes.c_uint32), ("scale_fanout", ctypes.c_int32)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("atlas_w", ctypes.c_int32), ("atlas_h", ctypes.c_int32),
+                ("n_charts", ctypes.c_int32), ("n_verts", ctypes.c_int32),
+                ("offsets", ctypes.c_void_p), ("verts", ctypes.c_void_p), ("out", ctypes.c_void_p),
+                ("scale_k", ctypes.c_int32), ("status", ctypes.c_int32)]
 
 
 PLACEMENT_DTYPE = np.dtype([("x", "<i4"), ("y", "<i4"), ("rot90", "u1"), ("flip_x", "u1"),
@@ -43,8 +53,8 @@ CHART_INFO_DTYPE = np.dtype([
     ("area_bl2", "<i8"), ("area_br2", "<i8")])
 
 EXPORTS = ["tabi_params_default", "tabi_ctx_create", "tabi_ctx_destroy", "tabi_last_error",
-           "tabi_status_str", "tabi_arena_bytes", "tabi_pack", "tabi_pack_device", "tabi_inspect",
-           "tabi_stage_times"]
+           "tabi_status_str", "tabi_arena_bytes", "tabi_pack", "tabi_pack_device", "tabi_pack_batch",
+           "tabi_pack_batch_device", "tabi_inspect", "tabi_inspect_atlas", "tabi_stage_times"]
 STAGES = ["prep", "sort", "layout", "raster", "hcompact", "rowloop", "select", "pack"]
 
 _lib = None
@@ -73,8 +83,13 @@ def load(path: str = LIB_PATH):
     for f in ("tabi_pack", "tabi_pack_device"):
         getattr(lib, f).argtypes = [P, P, i32, i32, i32, P, P, i32, P, P, P]
         getattr(lib, f).restype = ctypes.c_int
+    for f in ("tabi_pack_batch", "tabi_pack_batch_device"):
+        getattr(lib, f).argtypes = [P, P, P, i32, P]
+        getattr(lib, f).restype = ctypes.c_int
     lib.tabi_inspect.argtypes = [P, i32, i32, P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]
     lib.tabi_inspect.restype = ctypes.c_int
+    lib.tabi_inspect_atlas.argtypes = [P, i32, i32, i32, P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]
+    lib.tabi_inspect_atlas.restype = ctypes.c_int
     lib.tabi_stage_times.argtypes = [P, i32, P, P, P]
     lib.tabi_stage_times.restype = ctypes.c_int
     _lib = lib
@@ -108,6 +123,18 @@ def sum_extent_texels(cs) -> int:
 
 def arena_bytes(cs, gutter: int = 1) -> int:
     return int(load().tabi_arena_bytes(cs.n, cs.nv, cs.atlas_w, cs.atlas_h, sum_extent_texels(cs), gutter))
+
+
+def waves(fanout: int) -> int:
+    """Waves of the descending scale search for a fan-out."""
+    return (N_SCALES + fanout - 1) // fanout
+
+
+def kernels_per_pack(fanout: int) -> int:
+    """Kernels one (batched) pack launches: init, prep, sort + gather,
+    layout + bases, per wave plan + fill, raster, compaction, row loop;
+    selection."""
+    return 7 + 5 * waves(fanout)
 
 
 @dataclass
@@ -192,48 +219,81 @@ class Context:
             raise RuntimeError(f"tabi_stage_times failed: {self.last_error()}")
         return dict(zip(STAGES, ms)), dict(zip(STAGES, launches)), int(packs.value)
 
+    def pack_batch(self, sets, params: Params | None = None, stream=None, outs=None):
+        """tabi_pack_batch with host buffers: one ChartSet per atlas.  Returns
+        (call status, [PackResult per atlas])."""
+        params = params or params_default()
+        keep = []
+        reqs = (Request * len(sets))()
+        outs = outs or [np.zeros(cs.n, PLACEMENT_DTYPE) for cs in sets]
+        for i, cs in enumerate(sets):
+            offs = np.ascontiguousarray(cs.offsets, np.uint32)
+            verts = np.ascontiguousarray(cs.verts, np.int32)
+            keep += [offs, verts]
+            reqs[i] = Request(cs.atlas_w, cs.atlas_h, cs.n, cs.nv, offs.ctypes.data, verts.ctypes.data,
+                              outs[i].ctypes.data, 0, 0)
+        st = self.lib.tabi_pack_batch(self.h, ctypes.byref(params), reqs, len(sets),
+                                      ctypes.c_void_p(_stream_ptr(stream)))
+        return int(st), [PackResult(int(r.status), int(r.scale_k), o) for r, o in zip(reqs, outs)]
+
+    def pack_batch_requests(self, reqs, params: Params | None = None, stream=None, device: bool = True):
+        """tabi_pack_batch(_device) on a prepared ctypes Request array (raw
+        pointers, e.g. into CUDA or pinned torch tensors); statuses and k are
+        written into reqs."""
+        params = params or params_default()
+        f = self.lib.tabi_pack_batch_device if device else self.lib.tabi_pack_batch
+        return int(f(self.h, ctypes.byref(params), reqs, len(reqs), ctypes.c_void_p(_stream_ptr(stream))))
+
     # ---- inspection of the last pack ------------------------------------
-    def _inspect(self, what: int, scale: int = 0) -> bytes:
+    def _inspect(self, what: int, scale: int = 0, atlas: int = 0) -> np.ndarray:
         need = ctypes.c_size_t(0)
-        self.lib.tabi_inspect(self.h, what, scale, None, 0, ctypes.byref(need))
+        self.lib.tabi_inspect_atlas(self.h, atlas, what, scale, None, 0, ctypes.byref(need))
         buf = np.zeros(need.value, np.uint8)
-        st = self.lib.tabi_inspect(self.h, what, scale, buf.ctypes.data_as(ctypes.c_void_p), need.value,
-                                   ctypes.byref(need))
+        st = self.lib.tabi_inspect_atlas(self.h, atlas, what, scale, buf.ctypes.data_as(ctypes.c_void_p),
+                                         need.value, ctypes.byref(need))
         if st != TABI_OK:
             raise RuntimeError(f"tabi_inspect failed: {self.last_error()}")
         return buf
 
-    def charts(self) -> np.ndarray:
-        return self._inspect(INSPECT_CHARTS).view(CHART_INFO_DTYPE)
+    def charts(self, atlas: int = 0) -> np.ndarray:
+        return self._inspect(INSPECT_CHARTS, 0, atlas).view(CHART_INFO_DTYPE)
 
-    def perm(self) -> np.ndarray:
-        return self._inspect(INSPECT_PERM).view(np.int32)
+    def perm(self, atlas: int = 0) -> np.ndarray:
+        return self._inspect(INSPECT_PERM, 0, atlas).view(np.int32)
 
-    def envelopes(self, scale: int, n: int):
+    def envelopes(self, scale: int, n: int, atlas: int = 0):
         """List of (w', h', top', bot', left', right', maxbot) per sorted chart."""
-        raw = self._inspect(INSPECT_ENV, scale)
-        col_stride, row_stride = (int(v) for v in raw[:16].view(np.int64))
-        meta = raw[16:16 + 16 * n].view(np.int32).reshape(n, 4)
-        cols = raw[16 + 16 * n:16 + 16 * n + 4 * col_stride].view(np.uint32)
-        rows = raw[16 + 16 * n + 4 * col_stride:].view(np.uint32)
-        roff = self._inspect(INSPECT_ENV_CAP).view(np.int32).reshape(n, 2)[:, 0]
+        raw = self._inspect(INSPECT_ENV, scale, atlas)
+        cwords, rwords = (int(v) for v in raw[:16].view(np.int64))
+        o = 16
+        meta = raw[o:o + 16 * n].view(np.int32).reshape(n, 4)
+        o += 16 * n
+        rst = raw[o:o + 4 * n].view(np.int32)
+        o += 4 * n
+        cols = raw[o:o + 4 * cwords].view(np.uint32)
+        rows = raw[o + 4 * cwords:o + 4 * cwords + 4 * rwords].view(np.uint32)
         out = []
         for s in range(n):
             wp, hp, cst, mb = (int(v) for v in meta[s])
             c = cols[cst:cst + wp]
-            r = rows[roff[s]:roff[s] + hp]
+            r = rows[rst[s]:rst[s] + hp]
             out.append((wp, hp, (c & 0xffff).astype(np.int32), (c >> 16).astype(np.int32),
                         (r & 0xffff).astype(np.int32), (r >> 16).astype(np.int32), mb))
         return out
 
-    def pairs(self, scale: int, n: int):
-        raw = self._inspect(INSPECT_PAIRS, scale)
+    def regions(self, atlas: int = 0):
+        """(start[64, 2], words[64, 2]) of the atlas's column / row regions."""
+        raw = self._inspect(INSPECT_REGIONS, 0, atlas).view(np.int64)
+        return raw[:128].reshape(64, 2), raw[128:].reshape(64, 2)
+
+    def pairs(self, scale: int, n: int, atlas: int = 0):
+        raw = self._inspect(INSPECT_PAIRS, scale, atlas)
         d = raw[:4 * n].view(np.int32)
         fl = raw[4 * n:4 * n + n]
         return d, (fl & 1).astype(np.uint8), ((fl >> 1) & 1).astype(np.uint8)
 
-    def scale_result(self, scale: int, n: int):
-        raw = self._inspect(INSPECT_SCALE, scale)
+    def scale_result(self, scale: int, n: int, atlas: int = 0):
+        raw = self._inspect(INSPECT_SCALE, scale, atlas)
         hdr = raw[:32].view(np.int32)
         place = raw[32:32 + 16 * n].view(np.int32).reshape(n, 4)
         return hdr, place

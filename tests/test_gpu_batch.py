@@ -1,0 +1,206 @@
+"""GPU parity of the batched form: many atlases of uneven size packed by one
+launch sequence (tabi_pack_batch / tabi_pack_batch_device), each bit-exact
+with the CPU oracle and identical to the same atlas packed alone.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # the -m gpu suite runs on a GPU machine only
+    pytest.skip("CUDA not available", allow_module_level=True)
+
+from paper_2602_07782_gb300 import tabi  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = tabi.Context(arena_bytes=4 << 30)
+    yield c
+    c.close()
+
+
+def oracle_params(p):
+    return oracle.default_params(gutter=p.gutter, knee_abs=p.knee_abs_pct, knee_rel=p.knee_rel_pct,
+                                 lr_sig=p.lr_sig_pct, knee_margin=p.knee_margin, flags=p.flags & tabi.F_ALL)
+
+
+def mixed_batch():
+    """Uneven chart counts and atlas sizes, knees, a non-square atlas."""
+    sets = [synth.plain64(seed=1), synth.stars(3, 300, 512), synth.knees(1, 300, 1024),
+            synth.knees(5, 200, 512), synth.pareto20k(seed=9, n=1500, atlas=1024),
+            synth.stars(8, 40, 256), synth.rectangles([(7, 7)] * 50, 100, 60)]
+    cs = synth.knees(7, 123, 777)
+    cs.atlas_h = 333
+    sets.append(cs)
+    return sets
+
+
+def compare(cs, res, op):
+    o = oracle.pack(cs, op)
+    assert res.status == {0: 0, 2: 2, 1: 1}[o.status], cs.name
+    assert res.k == o.k, cs.name
+    if o.status == 0:
+        pl = res.place
+        for f, col in (("x", 0), ("y", 1), ("rot90", 2), ("flip_x", 3), ("flip_y", 4), ("mirror", 5)):
+            assert np.array_equal(pl[f], o.place[:, col]), (cs.name, f)
+
+
+@pytest.mark.parametrize("fanout", [64, 8, 5, 1])
+def test_batch_parity(ctx, fanout):
+    sets = mixed_batch()
+    p = tabi.params_default(scale_fanout=fanout)
+    st, res = ctx.pack_batch(sets, p)
+    assert st == tabi.TABI_OK, ctx.last_error()
+    op = oracle_params(p)
+    for cs, r in zip(sets, res):
+        compare(cs, r, op)
+
+
+def test_batch_same_as_alone(ctx):
+    sets = mixed_batch()
+    p = tabi.params_default(scale_fanout=8)
+    alone = [ctx.pack(cs, p) for cs in sets]
+    st, res = ctx.pack_batch(sets[::-1], p)  # another order, too
+    assert st == tabi.TABI_OK
+    for a, b in zip(alone, res[::-1]):
+        assert a.status == b.status and a.k == b.k
+        assert np.array_equal(a.place, b.place)
+
+
+def test_batch_steps_per_atlas(ctx):
+    """Inspection of each atlas of a batch: prep, sort, envelopes, pairs and
+    every candidate's row loop against the oracle."""
+    sets = [synth.stars(3, 120, 512), synth.knees(5, 90, 512), synth.plain64(seed=2)]
+    p = tabi.params_default(flags=tabi.F_ALL | tabi.F_EVAL_ALL)
+    op = oracle_params(p)
+    st, res = ctx.pack_batch(sets, p)
+    assert st == tabi.TABI_OK
+    for a, cs in enumerate(sets):
+        rec = oracle.prep(cs, op)
+        perm = ctx.perm(a)
+        assert np.array_equal(perm, oracle.sort(rec))
+        assert np.array_equal(ctx.charts(a)["Hq"].astype(np.int64), rec[:, oracle.R["HQ"]])
+        for j in range(0, 64, 9):
+            k = 16 * (j + 1)
+            env = ctx.envelopes(j, cs.n, a)
+            for s in range(cs.n):
+                e = oracle.envelope_padded(rec[perm[s]], k, op)
+                wp, hp, top, bot, left, right, mb = env[s]
+                assert (wp, hp) == (e.w, e.h)
+                assert np.array_equal(top, e.top) and np.array_equal(bot, e.bot)
+                assert np.array_equal(left, e.left) and np.array_equal(right, e.right)
+            d, ca, cb = ctx.pairs(j, cs.n, a)
+            od, oca, ocb, _, _ = oracle.scale_pairs(rec, perm, k, op)
+            assert np.array_equal(d[:-1], od[:-1]) and d[-1] == 0
+            assert np.array_equal(ca[:-1], oca[:-1]) and np.array_equal(cb[:-1], ocb[:-1])
+            hdr, place = ctx.scale_result(j, cs.n, a)
+            ok, opl, ost = oracle.pack_scale(rec, perm, cs.atlas_w, cs.atlas_h, k, op)
+            assert hdr[0] == int(ok) and list(hdr[1:6]) == [int(v) for v in ost[:5]]
+            assert hdr[6] == 1  # ran to its end
+            placed = int(ost[4])
+            assert np.array_equal(place[:placed, 0], opl[:placed, 0])
+            assert np.array_equal(place[:placed, 1], opl[:placed, 1])
+
+
+def test_batch_regions_tile_the_pools(ctx):
+    """Within a wave the (atlas, candidate) regions are disjoint, 16-byte
+    aligned and sized by the atlas's charts."""
+    sets = mixed_batch()
+    F = 8
+    p = tabi.params_default(scale_fanout=F)
+    st, _ = ctx.pack_batch(sets, p)
+    assert st == tabi.TABI_OK
+    starts, words = zip(*(ctx.regions(a) for a in range(len(sets))))
+    for which in (0, 1):
+        for w0 in range(0, 64, F):
+            js = [63 - w0 - i for i in range(F) if 63 - w0 - i >= 0]
+            iv = sorted((int(starts[a][j, which]), int(words[a][j, which])) for a in range(len(sets))
+                        for j in js)
+            for (s0, n0), (s1, _) in zip(iv, iv[1:]):
+                assert s0 + n0 <= s1
+            assert all(s % 4 == 0 and n % 4 == 0 for s, n in iv)
+
+
+def test_batch_rejects_bad_requests_alone(ctx):
+    """A request that fails the host checks, and one with an invalid chart,
+    fail alone; the other atlases of the batch are unaffected."""
+    good = [synth.stars(3, 300, 512), synth.plain64(seed=1)]
+    bad_host = synth.rectangles([(3, 5)], 32, 32)
+    bad_host.atlas_w = 0
+    bad_dev = synth.from_polygons([[(0, 0), (100, 0), (100, 600)]], 32, 32)
+    sets = [good[0], bad_host, bad_dev, good[1]]
+    p = tabi.params_default()
+    st, res = ctx.pack_batch(sets, p)
+    assert st == tabi.TABI_OK
+    assert res[1].status == tabi.TABI_ERR_INVALID_ARG and res[2].status == tabi.TABI_ERR_INVALID_ARG
+    op = oracle_params(p)
+    compare(good[0], res[0], op)
+    compare(good[1], res[3], op)
+
+
+def test_batch_device_entry_point(ctx):
+    sets = mixed_batch()[:5]
+    p = tabi.params_default(scale_fanout=16)
+    st, host = ctx.pack_batch(sets, p)
+    assert st == tabi.TABI_OK
+    dev = torch.device("cuda:0")
+    keep, reqs = [], (tabi.Request * len(sets))()
+    for i, cs in enumerate(sets):
+        offs = torch.from_numpy(cs.offsets.view(np.int32).copy()).to(dev)
+        verts = torch.from_numpy(cs.verts.copy()).to(dev)
+        out = torch.zeros(12 * cs.n, dtype=torch.uint8, device=dev)
+        keep.append((offs, verts, out))
+        reqs[i] = tabi.Request(cs.atlas_w, cs.atlas_h, cs.n, cs.nv, offs.data_ptr(), verts.data_ptr(),
+                               out.data_ptr(), 0, 0)
+    assert ctx.pack_batch_requests(reqs, p, device=True) == tabi.TABI_OK
+    torch.cuda.synchronize()
+    for i, h in enumerate(host):
+        assert reqs[i].status == h.status and reqs[i].scale_k == h.k
+        got = keep[i][2].cpu().numpy().view(tabi.PLACEMENT_DTYPE)
+        assert np.array_equal(got, h.place)
+
+
+def test_batch_small_arena_fails_per_atlas():
+    """An arena too small for every region: the atlases whose regions do not
+    fit report TABI_ERR_OOM, the others are still exact."""
+    sets = [synth.stars(3, 300, 512), synth.stars2k(), synth.plain64(seed=1)]
+    need = sum(tabi.arena_bytes(cs) for cs in sets)
+    c = tabi.Context(arena_bytes=need // 6)
+    try:
+        p = tabi.params_default()
+        st, res = c.pack_batch(sets, p)
+        if st == tabi.TABI_ERR_OOM:
+            return  # the per-chart arrays alone did not fit
+        assert st == tabi.TABI_OK
+        assert any(r.status == tabi.TABI_ERR_OOM for r in res)
+        op = oracle_params(p)
+        for cs, r in zip(sets, res):
+            assert r.status in (tabi.TABI_OK, tabi.TABI_ERR_OOM)
+            if r.status == tabi.TABI_OK:
+                compare(cs, r, op)
+    finally:
+        c.close()
+
+
+@pytest.mark.slow
+def test_batch_uneven_sizes_full_shapes(ctx):
+    """Sixteen atlases drawn like the 256-atlas batch workload (chart counts
+    50-5,000, atlas sides 1024/2048/4096, star charts), in the launch
+    configuration the benchmark times."""
+    sets = synth.batch256(count=16)
+    p = tabi.params_default(scale_fanout=8)
+    st, res = ctx.pack_batch(sets, p)
+    assert st == tabi.TABI_OK
+    op = oracle_params(p)
+    for cs, r in zip(sets, res):
+        assert r.status == tabi.TABI_OK
+        compare(cs, r, op)

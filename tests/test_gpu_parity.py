@@ -38,8 +38,9 @@ def gpu_params(**kw):
 
 
 def oracle_params(p):
+    # the oracle knows the method's flags only (TABI_F_EVAL_ALL is an inspection aid)
     return oracle.default_params(gutter=p.gutter, knee_abs=p.knee_abs_pct, knee_rel=p.knee_rel_pct,
-                                 lr_sig=p.lr_sig_pct, knee_margin=p.knee_margin, flags=p.flags)
+                                 lr_sig=p.lr_sig_pct, knee_margin=p.knee_margin, flags=p.flags & tabi.F_ALL)
 
 
 SMALL = {
@@ -74,7 +75,7 @@ def _check_prep(ctx, cs, op):
 def test_steps_parity(ctx, name):
     """prep, sort, envelopes, distances/flags and every candidate's row loop."""
     cs = SMALL[name]()
-    p = gpu_params()
+    p = gpu_params(flags=tabi.F_ALL | tabi.F_EVAL_ALL)  # every candidate runs to its end
     op = oracle_params(p)
     res = ctx.pack(cs, p)
     assert res.status == tabi.TABI_OK, ctx.last_error()
