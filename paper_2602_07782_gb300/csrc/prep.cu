@@ -33,47 +33,66 @@ struct Xf {
   }
 };
 
+// floor and ceil of num / d for d > 0 whose quotient is known to lie in
+// [-2^21, 2^21] (|num| < 2^43): a float estimate of the quotient is within
+// one of the floor (relative error below 2^-22), and the exact integer
+// remainder corrects it.
+__device__ __forceinline__ void floor_ceil_div(int64_t num, int32_t d, int32_t &f, int32_t &c) {
+  int32_t q = (int32_t)floorf((float)num * (1.0f / (float)d));
+  int64_t r = num - (int64_t)q * d;
+  if (r < 0) { --q; r += d; }
+  else if (r >= d) { ++q; r -= d; }
+  f = q;
+  c = q + (r != 0);
+}
+
 // Local AABBs of the K slices along one axis: for slice i = [B_i, B_{i+1}]
-// (B_i = floor(i * ext / K)), floor(min) and ceil(max) of the other
-// coordinate over the polygon's edges clipped to the slab.  Every lane ends
-// with all values.
+// (B_i = floor(i * ext / K), closed), floor(min) and ceil(max) of the other
+// coordinate over the polygon's boundary inside the slab.  That part of the
+// boundary is spanned by the vertices inside the slab and the points where
+// edges cross its bounding lines, so each lane takes its vertices (exact
+// values) and its edges' crossings of the inner lines B_1 .. B_9 strictly
+// between the edge's ends (a crossing of B_m belongs to slices m-1 and m).
+// Coordinates of the normalised chart lie in [0, 2^21], so everything but
+// the crossing numerators fits 32 bits.  Every lane ends with all values.
 __device__ void warp_slices(const int32_t *__restrict__ v, int nv, const Xf &xf, bool xaxis,
-                            int64_t ext, int64_t (&lo)[kSlices], int64_t (&hi)[kSlices]) {
+                            int64_t ext, int32_t (&lo)[kSlices], int32_t (&hi)[kSlices]) {
   const int lane = threadIdx.x & 31;
+  int32_t B[kSlices + 1];
 #pragma unroll
-  for (int i = 0; i < kSlices; ++i) { lo[i] = kI64Max; hi[i] = kI64Min; }
+  for (int i = 0; i <= kSlices; ++i) B[i] = (int32_t)((int64_t)i * ext / kSlices);
+#pragma unroll
+  for (int i = 0; i < kSlices; ++i) { lo[i] = 0x7fffffff; hi[i] = -0x7fffffff - 1; }
   for (int e = lane; e < nv; e += 32) {
     const int e1 = (e + 1 == nv) ? 0 : e + 1;
     int64_t x0, y0, x1, y1;
     xf.apply(v[2 * e], v[2 * e + 1], x0, y0);
     xf.apply(v[2 * e1], v[2 * e1 + 1], x1, y1);
-    const int64_t u0 = xaxis ? x0 : y0, w0 = xaxis ? y0 : x0;
-    const int64_t u1 = xaxis ? x1 : y1, w1 = xaxis ? y1 : x1;
-    const int64_t ul = u0 < u1 ? u0 : u1, ur = u0 < u1 ? u1 : u0;
-    int64_t den = u1 - u0;
-    const bool vert = den == 0;
-    const int64_t sgn = den < 0 ? -1 : 1;
-    den *= sgn;
+    const int32_t u0 = (int32_t)(xaxis ? x0 : y0), w0 = (int32_t)(xaxis ? y0 : x0);
+    const int32_t u1 = (int32_t)(xaxis ? x1 : y1), w1 = (int32_t)(xaxis ? y1 : x1);
+    // vertex e, in every slice that contains it
 #pragma unroll
-    for (int i = 0; i < kSlices; ++i) {
-      const int64_t a = (int64_t)i * ext / kSlices, b = (int64_t)(i + 1) * ext / kSlices;
-      if (vert) {
-        if (u0 >= a && u0 <= b) {
-          const int64_t mn = w0 < w1 ? w0 : w1, mx = w0 < w1 ? w1 : w0;
-          lo[i] = mn < lo[i] ? mn : lo[i];
-          hi[i] = mx > hi[i] ? mx : hi[i];
-        }
-        continue;
-      }
-      const int64_t ca = a > ul ? a : ul, cb = b < ur ? b : ur;
-      if (ca > cb) continue;
+    for (int i = 0; i < kSlices; ++i)
+      if (B[i] <= u0 && u0 <= B[i + 1]) { lo[i] = min(lo[i], w0); hi[i] = max(hi[i], w0); }
+    // crossings of edge (e, e+1) with the inner slab lines
+    const int32_t ul = min(u0, u1), ur = max(u0, u1);
+    unsigned mask = 0;
 #pragma unroll
-      for (int t = 0; t < 2; ++t) {
-        const int64_t u = t ? cb : ca;
-        const int64_t num = sgn * (w0 * (u1 - u0) + (u - u0) * (w1 - w0));
-        const int64_t f = floor_div(num, den), c = ceil_div(num, den);
-        lo[i] = f < lo[i] ? f : lo[i];
-        hi[i] = c > hi[i] ? c : hi[i];
+    for (int m = 1; m < kSlices; ++m)
+      if (ul < B[m] && B[m] < ur) mask |= 1u << m;
+    if (mask) {
+      const int32_t sgn = u1 > u0 ? 1 : -1;
+      const int32_t d = (u1 - u0) * sgn;
+      while (mask) {
+        const int m = __ffs(mask) - 1;
+        mask &= mask - 1;
+        const int32_t Bm = (int32_t)((int64_t)m * ext / kSlices);
+        const int64_t num = sgn * ((int64_t)w0 * (u1 - u0) + (int64_t)(Bm - u0) * (w1 - w0));
+        int32_t f, c;
+        floor_ceil_div(num, d, f, c);
+#pragma unroll
+        for (int i = 0; i < kSlices; ++i)
+          if (i == m - 1 || i == m) { lo[i] = min(lo[i], f); hi[i] = max(hi[i], c); }
       }
     }
   }
@@ -127,7 +146,7 @@ __device__ __forceinline__ void prep_chart(const Pack &p, int c) {
     return;
   }
   Xf xf{mnx, mny, W0, Wq, Hq, rot, 0, 0};
-  int64_t ylo[kSlices], yhi[kSlices], xlo[kSlices], xhi[kSlices];
+  int32_t ylo[kSlices], yhi[kSlices], xlo[kSlices], xhi[kSlices];
 
   // App. A chart orientation, vertical reflection: top vs bottom empty area
   warp_slices(v, nv, xf, true, Wq, ylo, yhi);
@@ -146,7 +165,7 @@ __device__ __forceinline__ void prep_chart(const Pack &p, int c) {
   if (xf.fy) {
 #pragma unroll
     for (int i = 0; i < kSlices; ++i) {
-      const int64_t lo = Hq - yhi[i], hi = Hq - ylo[i];
+      const int32_t lo = (int32_t)Hq - yhi[i], hi = (int32_t)Hq - ylo[i];
       ylo[i] = lo;
       yhi[i] = hi;
     }
@@ -180,7 +199,7 @@ __device__ __forceinline__ void prep_chart(const Pack &p, int c) {
   if (xf.fx) {
 #pragma unroll
     for (int j = 0; j < kSlices; ++j) {
-      const int64_t lo = Wq - xhi[j], hi = Wq - xlo[j];
+      const int32_t lo = (int32_t)Wq - xhi[j], hi = (int32_t)Wq - xlo[j];
       xlo[j] = lo;
       xhi[j] = hi;
     }

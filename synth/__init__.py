@@ -1,3 +1,4 @@
 """Seeded synthetic chart sets (inputs only; no packing arithmetic)."""
-from .charts import (ChartSet, Request, batch256, from_polygons, knees, pareto20k,  # noqa: F401
-                     plain64, rectangles, serve_stream, stars, stars2k, WORKLOADS)
+from .charts import (ChartSet, Request, batch256, batch256_specs, from_polygons, knees,  # noqa: F401
+                     pareto20k, plain64, rectangles, serve_stream, stars, stars2k, stars_many,
+                     WORKLOADS)

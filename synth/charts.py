@@ -37,6 +37,7 @@ packer's own translate step is exercised.  All coordinates stay inside
 from __future__ import annotations
 
 import math
+import os
 from dataclasses import dataclass
 
 import numpy as np
@@ -283,15 +284,39 @@ def knees(seed: int, n: int, atlas: int, n_tall: int = 6, density: float = DENSI
     return _pack([polys[i] for i in order], rng, atlas, atlas, f"knees[{n},{atlas}]")
 
 
-def batch256(seed: int = 4, count: int = 256, lo: int = 50, hi: int = 5000,
-             sides=(1024, 2048, 4096)) -> list[ChartSet]:
+def batch256_specs(seed: int = 4, count: int = 256, lo: int = 50, hi: int = 5000,
+                   sides=(1024, 2048, 4096)) -> list[tuple[int, int, int]]:
+    """(chart seed, chart count, atlas side) of each atlas of the batch."""
     rng = np.random.default_rng([seed, 4, count])
     out = []
     for i in range(count):
         n = int(rng.integers(lo, hi + 1))
         side = int(sides[int(rng.integers(0, len(sides)))])
-        out.append(stars(seed * 100003 + i, n, side))
+        out.append((seed * 100003 + i, n, side))
     return out
+
+
+def batch256(seed: int = 4, count: int = 256, lo: int = 50, hi: int = 5000,
+             sides=(1024, 2048, 4096)) -> list[ChartSet]:
+    return [stars(s, n, side) for s, n, side in batch256_specs(seed, count, lo, hi, sides)]
+
+
+def _stars_spec(spec):
+    return stars(*spec)
+
+
+def stars_many(specs, workers: int | None = None) -> list[ChartSet]:
+    """stars(*spec) for each spec, generated in a pool of spawned processes
+    (the same sets as one by one; spawn keeps the pool safe to start after
+    CUDA is initialised)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    specs = list(specs)
+    workers = workers or min(len(specs), os.cpu_count() or 1)
+    if workers <= 1 or len(specs) < 4:
+        return [stars(*sp) for sp in specs]
+    with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(_stars_spec, specs, chunksize=max(1, len(specs) // (4 * workers))))
 
 
 @dataclass
