@@ -75,11 +75,15 @@ typedef enum tabi_status {
 #define TABI_F_LAABB   8u /* local-AABB proxy in the envelopes, Sec. 4.1.1;
                              OBB and LAABB both off = bounding boxes only    */
 #define TABI_F_ALL     15u
-/* Inspection aid, not part of the method: every candidate's row loop runs
- * to its end even after a larger candidate of the same atlas has succeeded
- * (without it such a candidate is skipped or abandoned between rows).  The
- * scale and placements are the same either way; only the per-candidate
- * summaries of TABI_INSPECT_SCALE become complete. */
+/* Inspection aid, not part of the method: every candidate is evaluated and
+ * its row loop runs to its end.  Without it, candidates above the area
+ * bound are skipped (charts never overlap and stay inside the atlas, so a
+ * candidate at which the summed polygon area exceeds the atlas area cannot
+ * succeed; this holds for simple polygons, which the charts must be), and
+ * a candidate is skipped or abandoned between rows once a larger one of
+ * the same atlas has succeeded.  The scale and placements are the same
+ * either way; only the per-candidate summaries of TABI_INSPECT_SCALE become
+ * complete. */
 #define TABI_F_EVAL_ALL 16u
 
 /* Largest chart count of one atlas, largest batch. */
@@ -209,14 +213,17 @@ tabi_status tabi_pack_batch_device(tabi_ctx *ctx, const tabi_params *params, tab
  *                        row, chart s from its row start);
  *   TABI_INSPECT_REGIONS int64[64][2] region starts in the column and row
  *                        pools, then int64[64][2] region words, per
- *                        candidate;
+ *                        candidate, then int64 top candidate index (the
+ *                        largest the area bound allows, -1 if none; regions
+ *                        exist for the candidates up to it);
  *   TABI_INSPECT_PAIRS   int32[n] compacting distance d(s, s+1) then
  *                        uint8[n] flags (bit0 CannotMoveAbove(s, s+1),
  *                        bit1 CannotMoveAbove(s+1, s)) for `scale`;
  *   TABI_INSPECT_SCALE   int32[8]: success, rows, knee-folded rows, knees
  *                        found, final max frontline, charts placed,
- *                        evaluated (0 not run, 1 ran to its end, 2
- *                        abandoned after a larger candidate succeeded), 0
+ *                        evaluated (0 not run: above the area bound or
+ *                        below a success; 1 ran to its end; 2 abandoned
+ *                        after a larger candidate succeeded), 0
  *                        -- then int32[4n] per sorted chart: x, y, row,
  *                        bits (bit0 mirror, bit1 compacting on, bit2
  *                        knee-folded) for `scale`.

@@ -129,6 +129,7 @@ __global__ void init_kernel(const Pack *__restrict__ pp) {
     if (t == 0) {
       p.found[at] = -1;
       p.err[at] = 0;
+      p.area2[at] = 0;
       p.result[at] = PackResult{0, 0, 0, -1};
     }
     const int cb = p.atl[at].cb, n = p.atl[at].n;
@@ -210,8 +211,11 @@ struct StageMarks {
   }
 };
 
+int waves_of(int F) { return (kScales + F - 1) / F; }
+
 // The launch sequence of a batch: prep, sort, layout, then descending waves
-// of F candidates (plan, raster, compaction, row loop), then selection.
+// of F candidates per atlas from its top candidate (plan, raster,
+// compaction, row loop), then selection.
 void enqueue(const Pack *dp, const Launch &L, int F, cudaStream_t st, StageMarks *mk) {
   auto b = [&](int s) { if (mk) mk->begin(s); };
   auto e = [&]() { if (mk) mk->end(); };
@@ -225,26 +229,22 @@ void enqueue(const Pack *dp, const Launch &L, int F, cudaStream_t st, StageMarks
   b(2);
   launch_layout(dp, L, st);
   e();
-  int wave = 0;
-  for (int j_hi = kScales - 1; j_hi >= 0; j_hi -= F, ++wave) {
-    const int j_lo = j_hi - F + 1 < 0 ? 0 : j_hi - F + 1;
+  for (int wave = 0; wave < waves_of(F); ++wave) {
     b(3);
     launch_plan(dp, L, wave, st);
-    launch_raster(dp, L, j_lo, j_hi, st);
+    launch_raster(dp, L, wave, F, st);
     e();
     b(4);
-    launch_hcompact(dp, L, j_lo, j_hi, st);
+    launch_hcompact(dp, L, wave, F, st);
     e();
     b(5);
-    launch_rowloop(dp, L, wave, j_lo, j_hi, st);
+    launch_rowloop(dp, L, wave, F, st);
     e();
   }
   b(6);
   launch_select(dp, L, st);
   e();
 }
-
-int waves_of(int F) { return (kScales + F - 1) / F; }
 
 tabi_status get_graph(tabi_ctx *ctx, const Launch &L, int F, cudaGraphExec_t *out) {
   for (const GraphEntry &g : ctx->graphs)
@@ -380,6 +380,8 @@ tabi_status run_batch(tabi_ctx *ctx, const tabi_params *params, tabi_request *re
   p.pflags = cv.take<uint8_t>(kScales * n);
   p.place = cv.take<int4>(kScales * n);
   p.scale_out = cv.take<ScaleOut>((size_t)A * kScales);
+  p.area2 = cv.take<unsigned long long>(A);
+  p.jtop = cv.take<int32_t>(A);
   p.found = cv.take<int32_t>(A);
   p.err = cv.take<uint32_t>(A);
   p.result = cv.take<PackResult>(A);
@@ -640,14 +642,18 @@ tabi_status tabi_inspect_atlas(tabi_ctx *ctx, int32_t atlas, int32_t what, int32
   const AtlasDesc &ad = ctx->last_desc[at];
   const size_t n = (size_t)ad.n;
   const int64_t js = (int64_t)scale * p.N + ad.cb;
-  // region starts and sizes of this atlas (small reads, needed to size ENV)
-  int64_t reg[2 * kScales * 2];
+  // region starts and sizes of this atlas (small reads, needed to size ENV),
+  // then its top candidate
+  int64_t reg[2 * kScales * 2 + 1];
   cudaError_t e = cudaMemcpy(reg, p.abase + region(at, 0, 0), sizeof(int64_t) * 2 * kScales,
                              cudaMemcpyDeviceToHost);
   if (e == cudaSuccess)
     e = cudaMemcpy(reg + 2 * kScales, p.atot + region(at, 0, 0), sizeof(int64_t) * 2 * kScales,
                    cudaMemcpyDeviceToHost);
+  int32_t jt = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&jt, p.jtop + at, sizeof(int32_t), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "inspect copy");
+  reg[4 * kScales] = jt;
   const int64_t words[2] = {reg[2 * kScales + 2 * scale], reg[2 * kScales + 2 * scale + 1]};
   struct Piece {
     const void *src;

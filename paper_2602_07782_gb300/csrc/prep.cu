@@ -146,6 +146,19 @@ __device__ __forceinline__ void prep_chart(const Pack &p, int c) {
     return;
   }
   Xf xf{mnx, mny, W0, Wq, Hq, rot, 0, 0};
+
+  // twice the polygon's area (shoelace, input coordinates), summed per
+  // atlas: the area bound on the candidate scales
+  {
+    int64_t a2 = 0;
+    for (int e = lane; e < nv; e += 32) {
+      const int e1 = (e + 1 == nv) ? 0 : e + 1;
+      a2 += (int64_t)v[2 * e] * v[2 * e1 + 1] - (int64_t)v[2 * e1] * v[2 * e + 1];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+    if (lane == 0) atomicAdd(p.area2 + at, (unsigned long long)(a2 < 0 ? -a2 : a2));
+  }
   int32_t ylo[kSlices], yhi[kSlices], xlo[kSlices], xhi[kSlices];
 
   // App. A chart orientation, vertical reflection: top vs bottom empty area
@@ -377,6 +390,23 @@ __device__ void sort_atlas(const Pack &p, int at) {
   }
   // three passes: A->B, B->A, A->B
   for (int s = tid; s < n; s += kSortThreads) p.perm[cb + s] = cb + (int32_t)vB[s];
+  if (tid == 0) {
+    // Area bound: placed charts are disjoint and inside the atlas, so a
+    // candidate k can succeed only if the summed polygon area at scale
+    // k/1024 is at most W*H, i.e. area2 * k^2 <= 2 W H 2^16 2^20 (area2 is
+    // twice the area in Q.8^2 units).  Larger candidates are skipped.
+    int jt = kScales - 1;
+    if (!(p.flags & TABI_F_EVAL_ALL)) {
+      const unsigned __int128 lim = (unsigned __int128)((uint64_t)p.atl[at].W * (uint64_t)p.atl[at].H) << 37;
+      const unsigned __int128 s2 = p.area2[at];
+      jt = -1;
+      for (int j = 0; j < kScales; ++j) {
+        const uint64_t k = 16 * (uint64_t)(j + 1);
+        if (s2 * (k * k) <= lim) jt = j;
+      }
+    }
+    p.jtop[at] = jt;
+  }
   __syncthreads();  // the shared histogram is reused by the next atlas
 }
 

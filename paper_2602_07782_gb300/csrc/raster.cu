@@ -66,8 +66,9 @@ __device__ __forceinline__ int32_t warp_axis(const rmath::AxisK &ak, int g, uint
 }
 
 // Warp-items: (chart of an atlas still searching, run of G consecutive
-// candidates).  G is chosen so that the wave has about 32K warp-items.
-__global__ void __launch_bounds__(kRasterThreads, 4) raster_kernel(const Pack *__restrict__ pp, int j_lo, int nj) {
+// candidates of the atlas's wave range).  G is chosen so that the wave has
+// about 32K warp-items.
+__global__ void __launch_bounds__(kRasterThreads, 4) raster_kernel(const Pack *__restrict__ pp, int wave, int nj) {
   __shared__ rmath::AxisK axk[kRasterWarps][2];
   const Pack &p = *pp;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -85,8 +86,10 @@ __global__ void __launch_bounds__(kRasterThreads, 4) raster_kernel(const Pack *_
     const int s = p.act_chart[it / ngroups];
     const int at = p.catl[s];
     const int cb = p.atl[at].cb;
-    const int j0 = j_lo + (int)(it % ngroups) * G;
-    const int j1 = min(j0 + G, j_lo + nj);
+    const WaveRange wr = wave_range(p.jtop[at], wave, nj);
+    const int j0 = wr.lo + (int)(it % ngroups) * G;
+    const int j1 = min(j0 + G, wr.hi + 1);
+    if (j0 >= j1) continue;  // this atlas has fewer candidates left than the wave
     const ChartShape &sh = p.shape[s];
     const int m = sh.m;
     const int64_t C = kObbCos[m], S = kObbSin[m];
@@ -196,36 +199,41 @@ __global__ void __launch_bounds__(1024) layout_kernel(const Pack *__restrict__ p
       const int64_t c4 = (tx + 3) & ~3LL, r4 = (ty + 3) & ~3LL;
       p.atot[region(at, j, 0)] = c4;
       p.atot[region(at, j, 1)] = r4;
-      atomicAdd(p.jtot + 2 * j, (unsigned long long)c4);
-      atomicAdd(p.jtot + 2 * j + 1, (unsigned long long)r4);
+      const int r = p.jtop[at] - j;  // rank below the atlas's top candidate
+      if (r >= 0) {
+        atomicAdd(p.jtot + 2 * r, (unsigned long long)c4);
+        atomicAdd(p.jtot + 2 * r + 1, (unsigned long long)r4);
+      }
     }
     __syncthreads();
   }
 }
 
 // Region bases.  Candidates of one wave share the pools (the candidates of
-// the next wave reuse them): within a wave the larger candidates come first,
-// and within a candidate the atlases in batch order.  An atlas whose region
+// the next wave reuse them).  A wave holds the ranks r = wF .. wF + F - 1
+// below each atlas's top candidate; within a wave the lower ranks come
+// first, within a rank the atlases in batch order.  An atlas whose region
 // runs past a pool's end is marked out of memory (and never rasterized).
 __global__ void __launch_bounds__(1024) bases_kernel(const Pack *__restrict__ pp) {
   __shared__ int64_t part[66];
   __shared__ int64_t carry[2];
   const Pack &p = *pp;
-  const int tid = threadIdx.x, j = blockIdx.x;
-  const int wv = (kScales - 1 - j) / p.F, jhi = kScales - 1 - wv * p.F;
+  const int tid = threadIdx.x, r = blockIdx.x;
+  const int r0 = r - r % p.F;  // first rank of this wave
   int64_t offc = 0, offr = 0;
-  for (int jj = j + 1; jj <= jhi; ++jj) {
-    offc += (int64_t)p.jtot[2 * jj];
-    offr += (int64_t)p.jtot[2 * jj + 1];
+  for (int rr = r0; rr < r; ++rr) {
+    offc += (int64_t)p.jtot[2 * rr];
+    offr += (int64_t)p.jtot[2 * rr + 1];
   }
   if (tid == 0) { carry[0] = offc; carry[1] = offr; }
   __syncthreads();
   for (int base = 0; base < p.A; base += 1024) {
     const int at = base + tid;
-    int64_t vc = at < p.A ? p.atot[region(at, j, 0)] : 0, vr = at < p.A ? p.atot[region(at, j, 1)] : 0;
+    const int j = at < p.A ? p.jtop[at] - r : -1;
+    const int64_t vc = j >= 0 ? p.atot[region(at, j, 0)] : 0, vr = j >= 0 ? p.atot[region(at, j, 1)] : 0;
     int64_t ec = vc, er = vr, tx = 0, ty = 0;
     block_scan2(ec, er, tx, ty, part);
-    if (at < p.A) {
+    if (j >= 0) {
       const int64_t bc = carry[0] + ec, br = carry[1] + er;
       p.abase[region(at, j, 0)] = bc;
       p.abase[region(at, j, 1)] = br;
@@ -237,8 +245,9 @@ __global__ void __launch_bounds__(1024) bases_kernel(const Pack *__restrict__ pp
   }
 }
 
-// Wave plan: the atlases still searching (no success yet, no error), in
-// batch order, and a flat list of their charts.
+// Wave plan: the atlases still searching (no success yet, no error, and
+// candidates left for this wave), in batch order, and a flat list of their
+// charts.
 __global__ void __launch_bounds__(1024) plan_kernel(const Pack *__restrict__ pp, int wave) {
   __shared__ int64_t part[66];
   __shared__ int64_t carry[2];
@@ -249,7 +258,7 @@ __global__ void __launch_bounds__(1024) plan_kernel(const Pack *__restrict__ pp,
   for (int base = 0; base < p.A; base += 1024) {
     const int at = base + tid;
     const bool live = at < p.A && *(volatile int32_t *)(p.found + at) < 0 &&
-                      *(volatile uint32_t *)(p.err + at) == 0;
+                      *(volatile uint32_t *)(p.err + at) == 0 && p.jtop[at] - wave * p.F >= 0;
     int64_t ea = live ? 1 : 0, ec = live ? p.atl[at].n : 0, tx = 0, ty = 0;
     block_scan2(ea, ec, tx, ty, part);
     if (live) {
@@ -296,7 +305,7 @@ __device__ __forceinline__ int32_t warp_scan_incl(int32_t v) {
 // relative to A iff every row of B stays right of all rows of A above it;
 // A may move up relative to B iff every row of A stays left of all rows of
 // B above it.
-__global__ void __launch_bounds__(256) hcompact_kernel(const Pack *__restrict__ pp, int j_lo, int nj) {
+__global__ void __launch_bounds__(256) hcompact_kernel(const Pack *__restrict__ pp, int wave, int nj) {
   const Pack &p = *pp;
   const int lane = threadIdx.x & 31;
   const int64_t total = p.act_info[1];
@@ -304,9 +313,11 @@ __global__ void __launch_bounds__(256) hcompact_kernel(const Pack *__restrict__ 
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int64_t N = p.N;
   for (int64_t it = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; it < items; it += nwarps) {
-    const int j = j_lo + (int)(it / total);
     const int s = p.act_chart[it % total];
     const int at = p.catl[s];
+    const WaveRange wr = wave_range(p.jtop[at], wave, nj);
+    const int j = wr.hi - (int)(it / total);
+    if (j < wr.lo) continue;  // this atlas has fewer candidates left than the wave
     const int64_t ps = (int64_t)j * N + s;
     if (s == p.atl[at].cb + p.atl[at].n - 1) {  // the atlas's last chart has no right neighbour
       if (lane == 0) { p.dnext[ps] = 0; p.pflags[ps] = 0; }
@@ -368,12 +379,12 @@ void launch_plan(const Pack *dp, const Launch &L, int wave, cudaStream_t st) {
   plan_fill_kernel<<<L.sms * 2, 256, 0, st>>>(dp);
 }
 
-void launch_raster(const Pack *dp, const Launch &L, int j_lo, int j_hi, cudaStream_t st) {
-  raster_kernel<<<L.sms * 16, kRasterThreads, 0, st>>>(dp, j_lo, j_hi - j_lo + 1);
+void launch_raster(const Pack *dp, const Launch &L, int wave, int F, cudaStream_t st) {
+  raster_kernel<<<L.sms * 16, kRasterThreads, 0, st>>>(dp, wave, F);
 }
 
-void launch_hcompact(const Pack *dp, const Launch &L, int j_lo, int j_hi, cudaStream_t st) {
-  hcompact_kernel<<<L.sms * 16, 256, 0, st>>>(dp, j_lo, j_hi - j_lo + 1);
+void launch_hcompact(const Pack *dp, const Launch &L, int wave, int F, cudaStream_t st) {
+  hcompact_kernel<<<L.sms * 16, 256, 0, st>>>(dp, wave, F);
 }
 
 }  // namespace tabi

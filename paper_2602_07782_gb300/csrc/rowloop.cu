@@ -116,11 +116,10 @@ __host__ __device__ __forceinline__ int rowloop_maxrow(int W, int g) {
 // device counter, larger candidates of an atlas first.  A task is skipped,
 // or abandoned between rows, once a larger candidate of its atlas has
 // succeeded (unless every candidate is to be evaluated).
-__global__ void __launch_bounds__(kNT) rowloop_kernel(const Pack *__restrict__ pp, int wave, int j_lo, int j_hi,
+__global__ void __launch_bounds__(kNT) rowloop_kernel(const Pack *__restrict__ pp, int wave, int nj,
                                                       int smem_words) {
   const Pack &p = *pp;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int nj = j_hi - j_lo + 1;
   const uint32_t flags = p.flags;
   const bool use_hc = flags & TABI_F_HC;
   const bool balance = flags & TABI_F_BALANCE;
@@ -136,8 +135,9 @@ __global__ void __launch_bounds__(kNT) rowloop_kernel(const Pack *__restrict__ p
       int at = -1, j = 0, skip = 1;
       if (t < *(volatile int32_t *)p.act_info * nj) {
         at = p.act_atl[t / nj];
-        j = j_hi - t % nj;
-        skip = !eval_all && *(volatile int32_t *)(p.found + at) > j;
+        const WaveRange wr = wave_range(p.jtop[at], wave, nj);
+        j = wr.hi - t % nj;
+        skip = j < wr.lo || (!eval_all && *(volatile int32_t *)(p.found + at) > j);
         // the host sizes the CTA for the widest atlas; never overrun it
         const int W = p.atl[at].W;
         if (!skip && smem_words < ((W + 2 * g + 3) & ~3) + 15 * rowloop_maxrow(W, g)) {
@@ -612,9 +612,9 @@ cudaError_t rowloop_prepare(int smem) {
   return cudaFuncSetAttribute(rowloop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
 }
 
-void launch_rowloop(const Pack *dp, const Launch &L, int wave, int j_lo, int j_hi, cudaStream_t st) {
+void launch_rowloop(const Pack *dp, const Launch &L, int wave, int F, cudaStream_t st) {
   // one CTA per multiprocessor (1024 threads and most of its shared memory)
-  rowloop_kernel<<<L.sms, kNT, L.rowloop_smem, st>>>(dp, wave, j_lo, j_hi, L.rowloop_smem / 4);
+  rowloop_kernel<<<L.sms, kNT, L.rowloop_smem, st>>>(dp, wave, F, L.rowloop_smem / 4);
 }
 
 }  // namespace tabi

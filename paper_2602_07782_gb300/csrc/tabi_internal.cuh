@@ -77,7 +77,7 @@ struct Pack {
   int32_t *rowstart;            // [64 N] row offset inside the (atlas, candidate) region
   int64_t *abase;               // [A][64][2] column / row region start in the pools
   int64_t *atot;                // [A][64][2] column / row region words (multiples of 4)
-  unsigned long long *jtot;     // [64][2] words of all atlases at candidate j
+  unsigned long long *jtot;     // [64][2] words of all atlases at rank r (candidate jtop - r)
   int64_t col_cap, row_cap;     // words per pool
   uint32_t *colpool;            // Top' | Bot' << 16 per padded column
   int32_t *colown;              // atlas-local sorted index of each column word
@@ -87,6 +87,8 @@ struct Pack {
   uint8_t *pflags;              // [64 N] interlock bits
   int4 *place;                  // [64 N] x, y, row, bits
   ScaleOut *scale_out;          // [A][64]
+  unsigned long long *area2;    // [A] twice the summed polygon area (Q.8^2 units)
+  int32_t *jtop;                // [A] largest candidate the area bound allows (-1 none)
   int32_t *found;               // [A] highest successful candidate so far (-1 none)
   uint32_t *err;                // [A]
   PackResult *result;           // [A]
@@ -102,10 +104,20 @@ __host__ __device__ __forceinline__ int64_t region(int a, int j, int which) {
   return ((int64_t)a * kScales + j) * 2 + which;
 }
 
+// Candidates of atlas a in wave w: ranks r = w F .. w F + F - 1 below the
+// atlas's top candidate, i.e. j = jtop - r for the r with j >= 0.
+struct WaveRange {
+  int lo, hi;  // candidate indices lo .. hi (empty if hi < lo)
+};
+__host__ __device__ __forceinline__ WaveRange wave_range(int jtop, int wave, int F) {
+  const int hi = jtop - wave * F;
+  const int lo = hi - F + 1 < 0 ? 0 : hi - F + 1;
+  return WaveRange{lo, hi};
+}
+
 // Launch helpers (each .cu file owns its kernels).  All are asynchronous on
 // `st` and capturable; grids are fixed per device (persistent kernels loop
 // over the device-side work), so they depend only on the wave structure.
-// `j_lo` .. `j_hi` is the wave's block of candidate indices.
 struct Launch {
   int sms;          // multiprocessors
   int rowloop_smem; // dynamic shared memory of a row-loop CTA
@@ -115,11 +127,11 @@ void launch_prep(const Pack *dp, const Launch &L, cudaStream_t st);
 void launch_sort(const Pack *dp, const Launch &L, cudaStream_t st);
 void launch_layout(const Pack *dp, const Launch &L, cudaStream_t st);
 void launch_plan(const Pack *dp, const Launch &L, int wave, cudaStream_t st);
-void launch_raster(const Pack *dp, const Launch &L, int j_lo, int j_hi, cudaStream_t st);
-void launch_hcompact(const Pack *dp, const Launch &L, int j_lo, int j_hi, cudaStream_t st);
+void launch_raster(const Pack *dp, const Launch &L, int wave, int F, cudaStream_t st);
+void launch_hcompact(const Pack *dp, const Launch &L, int wave, int F, cudaStream_t st);
 cudaError_t rowloop_prepare(int smem);  // raise the CTA's shared-memory limit (not capturable)
 int rowloop_static_smem();              // the row-loop kernel's static shared memory
-void launch_rowloop(const Pack *dp, const Launch &L, int wave, int j_lo, int j_hi, cudaStream_t st);
+void launch_rowloop(const Pack *dp, const Launch &L, int wave, int F, cudaStream_t st);
 void launch_select(const Pack *dp, const Launch &L, cudaStream_t st);
 size_t rowloop_smem_bytes(int W, int g);       // shared memory a row-loop CTA needs without the stage
 size_t rowloop_smem_wanted(int W, int g);      // ... with a stage of two atlas widths

@@ -282,9 +282,10 @@ class Context:
         return out
 
     def regions(self, atlas: int = 0):
-        """(start[64, 2], words[64, 2]) of the atlas's column / row regions."""
+        """(start[64, 2], words[64, 2], top candidate) of the atlas's column /
+        row regions."""
         raw = self._inspect(INSPECT_REGIONS, 0, atlas).view(np.int64)
-        return raw[:128].reshape(64, 2), raw[128:].reshape(64, 2)
+        return raw[:128].reshape(64, 2), raw[128:256].reshape(64, 2), int(raw[256])
 
     def pairs(self, scale: int, n: int, atlas: int = 0):
         raw = self._inspect(INSPECT_PAIRS, scale, atlas)

@@ -112,22 +112,44 @@ def test_batch_steps_per_atlas(ctx):
 
 
 def test_batch_regions_tile_the_pools(ctx):
-    """Within a wave the (atlas, candidate) regions are disjoint, 16-byte
-    aligned and sized by the atlas's charts."""
+    """Within a wave (ranks wF .. wF+F-1 below each atlas's top candidate)
+    the (atlas, candidate) regions are disjoint, 16-byte aligned and sized
+    by the atlas's charts."""
     sets = mixed_batch()
     F = 8
     p = tabi.params_default(scale_fanout=F)
     st, _ = ctx.pack_batch(sets, p)
     assert st == tabi.TABI_OK
-    starts, words = zip(*(ctx.regions(a) for a in range(len(sets))))
+    info = [ctx.regions(a) for a in range(len(sets))]
     for which in (0, 1):
-        for w0 in range(0, 64, F):
-            js = [63 - w0 - i for i in range(F) if 63 - w0 - i >= 0]
-            iv = sorted((int(starts[a][j, which]), int(words[a][j, which])) for a in range(len(sets))
-                        for j in js)
+        for w in range(0, 64 // F):
+            iv = []
+            for starts, words, jtop in info:
+                for r in range(w * F, (w + 1) * F):
+                    if jtop - r >= 0:
+                        iv.append((int(starts[jtop - r, which]), int(words[jtop - r, which])))
+            iv.sort()
             for (s0, n0), (s1, _) in zip(iv, iv[1:]):
                 assert s0 + n0 <= s1
             assert all(s % 4 == 0 and n % 4 == 0 for s, n in iv)
+
+
+def test_area_bound_keeps_the_result(ctx):
+    """The top candidate the area bound allows is at least the chosen scale,
+    and every candidate above it fails in the oracle too."""
+    sets = mixed_batch()[:5]
+    p = tabi.params_default()
+    st, res = ctx.pack_batch(sets, p)
+    assert st == tabi.TABI_OK
+    op = oracle_params(p)
+    for a, (cs, r) in enumerate(zip(sets, res)):
+        jtop = ctx.regions(a)[2]
+        assert r.k <= 16 * (jtop + 1)
+        if jtop < 63:
+            rec = oracle.prep(cs, op)
+            perm = oracle.sort(rec)
+            ok, _, _ = oracle.pack_scale(rec, perm, cs.atlas_w, cs.atlas_h, 16 * (jtop + 2), op)
+            assert not ok
 
 
 def test_batch_rejects_bad_requests_alone(ctx):
