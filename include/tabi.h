@@ -101,10 +101,12 @@ typedef struct tabi_params {
                            by at least this many texels (1), Sec. 4.2        */
   uint32_t flags;       /* TABI_F_*                                          */
   int32_t scale_fanout; /* candidate scales evaluated per wave of the
-                           descending search, 1..64 (64 = all at once); the
-                           result is the same for every value.  Waves share
-                           the envelope pools, so a smaller fan-out also
-                           needs a smaller arena                            */
+                           descending search, 1..64 (64 = all at once), or
+                           0 = the autotuned value for this kind of batch
+                           (tabi_autotune), else 64 for one atlas and 8 for
+                           several.  The result is the same for every
+                           value.  Waves share the envelope pools, so a
+                           smaller fan-out also needs a smaller arena       */
 } tabi_params;
 
 /* One placed chart; see "Placement semantics" above. */
@@ -116,7 +118,7 @@ typedef struct tabi_placement {
 typedef struct tabi_ctx tabi_ctx;
 
 /* Fill *p with the paper's defaults: gutter 1, knee 10 % / 20 %, left/right
- * significance 10 %, knee margin 1, all features on, fan-out 64. */
+ * significance 10 %, knee margin 1, all features on; fan-out 0 (tuned). */
 void tabi_params_default(tabi_params *p);
 
 /* Create a context on CUDA device `device`.  If `arena` is non-NULL it is a
@@ -194,6 +196,31 @@ tabi_status tabi_pack_batch(tabi_ctx *ctx, const tabi_params *params, tabi_reque
  * memory). */
 tabi_status tabi_pack_batch_device(tabi_ctx *ctx, const tabi_params *params, tabi_request *reqs,
                                    int32_t n_reqs, void *stream);
+
+/* Launch shape of a batch, chosen by tabi_autotune.  None of the knobs
+ * changes a result. */
+typedef struct tabi_tuning {
+  int32_t scale_fanout;      /* candidates per wave                          */
+  int32_t raster_warp_items; /* warp-items of a raster wave (sets how many
+                                consecutive candidates one warp walks)       */
+  int32_t rowloop_threads;   /* threads per row-loop CTA: 1024 or 512        */
+  int32_t rowloop_ctas;      /* row-loop CTAs per multiprocessor: 1 or 2     */
+  float ms;                  /* device time of one batch with this shape     */
+} tabi_tuning;
+
+/* Autotuner: packs the batch (DEVICE pointers, as tabi_pack_batch_device)
+ * repeatedly under candidate launch shapes, starting from the default --
+ * fan-out 64/16/8/4, then raster warp-items 16K/64K, then 512-thread
+ * row-loop CTAs two per multiprocessor -- times each (CUDA events, second
+ * run of each), drops any shape under which some atlas ends with another
+ * status (an arena too small for a wide wave), and keeps the fastest for
+ * this kind of batch (atlas count, mean chart count and widest atlas in
+ * powers of two, gutter, flags): later batches of the kind use it when
+ * params->scale_fanout is 0.  The requests end with the results of the
+ * chosen shape, the same as one tabi_pack_batch_device call.  *out (may be
+ * NULL) receives the choice.  Returns as tabi_pack_batch_device. */
+tabi_status tabi_autotune(tabi_ctx *ctx, const tabi_params *params, tabi_request *reqs, int32_t n_reqs,
+                          void *stream, tabi_tuning *out);
 
 /* Intermediate results of the last pack on this context, copied to host
  * memory for inspection and step-by-step testing; tabi_inspect_atlas

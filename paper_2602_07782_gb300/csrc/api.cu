@@ -19,8 +19,23 @@ namespace {
 // row-loop CTA of `smem` dynamic bytes.  Every kernel reads the batch from
 // the record at the arena's start, so the graph serves any batch.
 struct GraphEntry {
-  int F, smem;
+  int F, smem, threads, ctas;
   cudaGraphExec_t exec;
+};
+
+// Launch shape of a batch: the knobs the autotuner sets.  None changes a
+// result, only how the work is cut.
+struct Tuning {
+  int F;        // candidates per wave (scale fan-out)
+  int items;    // raster warp-items per wave (sets candidates per warp)
+  int threads;  // row-loop CTA: 1024 or 512 threads
+  int ctas;     // row-loop CTAs per multiprocessor
+};
+
+struct TuneEntry {
+  uint64_t key;  // batch class
+  Tuning t;
+  float ms;
 };
 
 }  // namespace
@@ -32,9 +47,11 @@ struct tabi_ctx {
   bool owned = false;
   std::atomic<int> busy{0};
   std::string last_error;
-  int sms = 0, rowloop_dyn_max = 0;
+  int sms = 0, rowloop_dyn_max = 0, smem_per_sm = 0, smem_reserved = 0;
   cudaStream_t cap_stream = nullptr;  // stream the graphs are captured on
   std::vector<GraphEntry> graphs;
+  std::vector<TuneEntry> tuned;       // autotuner results per batch class
+  cudaEvent_t tev[2] = {};            // autotuner timing
   // pinned host staging: the batch record going up, the results coming down
   char *hstage = nullptr;
   size_t hstage_bytes = 0;
@@ -100,7 +117,7 @@ bool valid_params(const tabi_params *p) {
          p->knee_abs_pct >= 0 && p->knee_abs_pct <= 100 && p->knee_rel_pct >= 0 &&
          p->knee_rel_pct <= 100 && p->lr_sig_pct >= 0 && p->lr_sig_pct <= 100 &&
          p->knee_margin >= 0 && p->knee_margin <= 1 << 20 &&
-         (p->flags & ~(TABI_F_ALL | TABI_F_EVAL_ALL)) == 0 && p->scale_fanout >= 1 &&
+         (p->flags & ~(TABI_F_ALL | TABI_F_EVAL_ALL)) == 0 && p->scale_fanout >= 0 &&
          p->scale_fanout <= kScales;
 }
 
@@ -248,7 +265,10 @@ void enqueue(const Pack *dp, const Launch &L, int F, cudaStream_t st, StageMarks
 
 tabi_status get_graph(tabi_ctx *ctx, const Launch &L, int F, cudaGraphExec_t *out) {
   for (const GraphEntry &g : ctx->graphs)
-    if (g.F == F && g.smem == L.rowloop_smem) { *out = g.exec; return TABI_OK; }
+    if (g.F == F && g.smem == L.rowloop_smem && g.threads == L.rowloop_threads && g.ctas == L.rowloop_ctas) {
+      *out = g.exec;
+      return TABI_OK;
+    }
   cudaGraph_t graph = nullptr;
   cudaError_t e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamBeginCapture");
@@ -259,10 +279,25 @@ tabi_status get_graph(tabi_ctx *ctx, const Launch &L, int F, cudaGraphExec_t *ou
   e = cudaGraphInstantiate(&exec, graph, 0);
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphInstantiate");
-  ctx->graphs.push_back(GraphEntry{F, L.rowloop_smem, exec});
+  ctx->graphs.push_back(GraphEntry{F, L.rowloop_smem, L.rowloop_threads, L.rowloop_ctas, exec});
   *out = exec;
   return TABI_OK;
 }
+
+int ceil_log2(int64_t v) {
+  int b = 0;
+  while (((int64_t)1 << b) < v) ++b;
+  return b;
+}
+
+// Batch class for the tuning cache: atlas count, mean chart count and
+// widest atlas (powers of two), gutter and method flags.
+uint64_t batch_class(int A, int64_t N, int maxW, const tabi_params *params) {
+  return (uint64_t)ceil_log2(A) | (uint64_t)ceil_log2((N + A - 1) / A) << 8 | (uint64_t)ceil_log2(maxW) << 16 |
+         (uint64_t)params->gutter << 24 | (uint64_t)(params->flags & TABI_F_ALL) << 32;
+}
+
+Tuning default_tuning(int A) { return Tuning{A == 1 ? kScales : 8, 32768, 1024, 1}; }
 
 bool ensure_hstage(tabi_ctx *ctx, size_t bytes) {
   if (ctx->hstage_bytes >= bytes) return true;
@@ -289,11 +324,10 @@ std::string check_request(const tabi_request &r, const tabi_params *params, int 
   return "";
 }
 
-tabi_status run_batch(tabi_ctx *ctx, const tabi_params *params, tabi_request *reqs, int32_t R, void *stream,
-                      bool host) {
-  if (!ctx) return TABI_ERR_INVALID_ARG;
-  Guard guard(ctx);
-  if (!guard.ok) return fail(ctx, TABI_ERR_BUSY, "context in use");
+// One batch; the caller holds the context.
+tabi_status run_batch_locked(tabi_ctx *ctx, const tabi_params *params, tabi_request *reqs, int32_t R,
+                             void *stream, bool host, const Tuning *force = nullptr, float *ms_out = nullptr,
+                             Tuning *used = nullptr) {
   if (!valid_params(params)) return fail(ctx, TABI_ERR_INVALID_ARG, "bad params");
   if (!reqs || R < 1 || R > TABI_MAX_BATCH) return fail(ctx, TABI_ERR_INVALID_ARG, "bad request list");
   cudaStream_t st = (cudaStream_t)stream;
@@ -358,8 +392,22 @@ tabi_status run_batch(tabi_ctx *ctx, const tabi_params *params, tabi_request *re
   p.lr_sig = params->lr_sig_pct;
   p.knee_margin = params->knee_margin;
   p.flags = params->flags;
-  p.F = params->scale_fanout;
+  // launch shape: forced (autotuner), else tuned for this batch class,
+  // else the default; an explicit fan-out in params wins over both
+  int maxW = 1;
+  for (int i = 0; i < A; ++i) maxW = std::max(maxW, desc[i].W);
+  const uint64_t cls = batch_class(A, N, maxW, params);
+  Tuning tn = default_tuning(A);
+  if (force) {
+    tn = *force;
+  } else {
+    for (const TuneEntry &te : ctx->tuned)
+      if (te.key == cls) tn = te.t;
+    if (params->scale_fanout > 0) tn.F = params->scale_fanout;
+  }
+  p.F = tn.F;
   p.nwaves = waves_of(p.F);
+  p.raster_items = tn.items;
   p.atl = ddesc;
   const size_t n = (size_t)N;
   p.catl = cv.take<int32_t>(n);
@@ -424,7 +472,16 @@ tabi_status run_batch(tabi_ctx *ctx, const tabi_params *params, tabi_request *re
   for (int i = 0; i < A; ++i) want = std::max(want, rowloop_smem_wanted(desc[i].W, p.g));
   int smem = (int)((want + 16383) & ~(size_t)16383);
   if (smem > ctx->rowloop_dyn_max) smem = ctx->rowloop_dyn_max;
-  const Launch L{ctx->sms, smem};
+  Launch L{ctx->sms, smem, tn.threads == 512 ? 512 : 1024, 1};
+  if (L.rowloop_threads == 512 && tn.ctas == 2) {
+    // two CTAs per multiprocessor if both fit its shared memory
+    const int two = (ctx->smem_per_sm - 2 * (ctx->smem_reserved + rowloop_static_smem())) / 2 & ~255;
+    if ((int)want <= two) {
+      L.rowloop_smem = std::min(smem, two);
+      L.rowloop_ctas = 2;
+    }
+  }
+  if (used) *used = Tuning{tn.F, tn.items, L.rowloop_threads, L.rowloop_ctas};
   if (ctx->timing) {
     StageMarks mk{ctx, st};
     enqueue(dpack, L, p.F, st, &mk);
@@ -437,7 +494,9 @@ tabi_status run_batch(tabi_ctx *ctx, const tabi_params *params, tabi_request *re
     cudaGraphExec_t exec = nullptr;
     const tabi_status gs = get_graph(ctx, L, p.F, &exec);
     if (gs != TABI_OK) return gs;
+    if (ms_out) cudaEventRecord(ctx->tev[0], st);
     e = cudaGraphLaunch(exec, st);
+    if (ms_out) cudaEventRecord(ctx->tev[1], st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphLaunch");
   }
   PackResult *hres = reinterpret_cast<PackResult *>(ctx->hstage + res_off);
@@ -449,6 +508,7 @@ tabi_status run_batch(tabi_ctx *ctx, const tabi_params *params, tabi_request *re
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "pack");
+  if (ms_out && !ctx->timing) cudaEventElapsedTime(ms_out, ctx->tev[0], ctx->tev[1]);
   ctx->last = p;
   ctx->last_desc = desc;
   ctx->last_map.assign(R, -1);
@@ -461,6 +521,14 @@ tabi_status run_batch(tabi_ctx *ctx, const tabi_params *params, tabi_request *re
   ctx->has_last = true;
   ctx->last_error = first_error;
   return TABI_OK;
+}
+
+tabi_status run_batch(tabi_ctx *ctx, const tabi_params *params, tabi_request *reqs, int32_t R, void *stream,
+                      bool host) {
+  if (!ctx) return TABI_ERR_INVALID_ARG;
+  Guard guard(ctx);
+  if (!guard.ok) return fail(ctx, TABI_ERR_BUSY, "context in use");
+  return run_batch_locked(ctx, params, reqs, R, stream, host);
 }
 
 tabi_status run_single(tabi_ctx *ctx, const tabi_params *params, int32_t W, int32_t H, int32_t n,
@@ -505,7 +573,7 @@ void tabi_params_default(tabi_params *p) {
   p->lr_sig_pct = 10;
   p->knee_margin = 1;
   p->flags = TABI_F_ALL;
-  p->scale_fanout = kScales;
+  p->scale_fanout = 0;  // tuned, else 64 for one atlas and 8 for a batch
 }
 
 tabi_status tabi_ctx_create(tabi_ctx **out, int device, void *arena, size_t arena_bytes) {
@@ -525,10 +593,13 @@ tabi_status tabi_ctx_create(tabi_ctx **out, int device, void *arena, size_t aren
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
   // the row loop's dynamic shared memory may use all the opt-in space
   // beyond its static part; raise the limit once so every graph can launch
+  cudaDeviceGetAttribute(&c->smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device);
+  cudaDeviceGetAttribute(&c->smem_reserved, cudaDevAttrReservedSharedMemoryPerBlock, device);
   const int stat = rowloop_static_smem();
   c->rowloop_dyn_max = stat < 0 ? 0 : (optin - stat) & ~255;
   bool ok = c->sms > 0 && c->rowloop_dyn_max > 0 && rowloop_prepare(c->rowloop_dyn_max) == cudaSuccess &&
-            cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) == cudaSuccess;
+            cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreate(&c->tev[0]) == cudaSuccess && cudaEventCreate(&c->tev[1]) == cudaSuccess;
   if (ok && arena) {
     c->arena = (char *)arena;
   } else if (ok) {
@@ -537,6 +608,8 @@ tabi_status tabi_ctx_create(tabi_ctx **out, int device, void *arena, size_t aren
   }
   if (!ok) {
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    for (cudaEvent_t ev : c->tev)
+      if (ev) cudaEventDestroy(ev);
     delete c;
     return TABI_ERR_CUDA;
   }
@@ -549,6 +622,8 @@ void tabi_ctx_destroy(tabi_ctx *c) {
   cudaSetDevice(c->device);
   for (GraphEntry &g : c->graphs) cudaGraphExecDestroy(g.exec);
   for (int i = 0; i < c->n_ev; ++i) cudaEventDestroy(c->ev[i]);
+  for (cudaEvent_t ev : c->tev)
+    if (ev) cudaEventDestroy(ev);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   if (c->owned) cudaFree(c->arena);
   if (c->hstage) cudaFreeHost(c->hstage);
@@ -603,6 +678,85 @@ tabi_status tabi_pack_batch(tabi_ctx *ctx, const tabi_params *params, tabi_reque
 tabi_status tabi_pack_batch_device(tabi_ctx *ctx, const tabi_params *params, tabi_request *reqs,
                                    int32_t n_reqs, void *stream) {
   return run_batch(ctx, params, reqs, n_reqs, stream, false);
+}
+
+tabi_status tabi_autotune(tabi_ctx *ctx, const tabi_params *params, tabi_request *reqs, int32_t n_reqs,
+                          void *stream, tabi_tuning *out) {
+  if (!ctx) return TABI_ERR_INVALID_ARG;
+  Guard guard(ctx);
+  if (!guard.ok) return fail(ctx, TABI_ERR_BUSY, "context in use");
+  if (ctx->timing) return fail(ctx, TABI_ERR_INVALID_ARG, "stage timing is on");
+  // coordinate search from the default shape: fan-out, then raster
+  // warp-items, then the row-loop CTA shape; each candidate timed on its
+  // second run (the first captures its graph).  A shape under which some
+  // atlas ends differently (an arena too small for a wide wave) is out.
+  Tuning best = default_tuning(n_reqs);
+  float best_ms = -1.f;
+  std::vector<int32_t> ref;
+  auto trial = [&](const Tuning &t) -> tabi_status {
+    float ms = 0.f, ms2 = 0.f;
+    Tuning used{};
+    tabi_status s = run_batch_locked(ctx, params, reqs, n_reqs, stream, false, &t, &ms, &used);
+    if (s == TABI_OK) s = run_batch_locked(ctx, params, reqs, n_reqs, stream, false, &t, &ms2, &used);
+    if (s != TABI_OK) return s;
+    if (!ctx->has_last) return fail(ctx, TABI_ERR_INVALID_ARG, "no request passed the host checks");
+    std::vector<int32_t> got(n_reqs);
+    for (int i = 0; i < n_reqs; ++i) got[i] = reqs[i].status;
+    if (ref.empty()) ref = got;
+    if (got != ref) return TABI_OK;
+    if (best_ms < 0.f || ms2 < best_ms) { best_ms = ms2; best = used; }
+    return TABI_OK;
+  };
+  {
+    const tabi_status s = trial(best);
+    if (s != TABI_OK) return s;
+  }
+  const int fanouts[] = {kScales, 16, 8, 4};
+  const Tuning start = best;
+  for (int F : fanouts) {
+    if (F == start.F) continue;
+    Tuning t = start;
+    t.F = F;
+    const tabi_status s = trial(t);
+    if (s != TABI_OK) return s;
+  }
+  const int items[] = {16384, 65536};
+  const Tuning base = best;
+  for (int it : items) {
+    Tuning t = base;
+    t.items = it;
+    const tabi_status s = trial(t);
+    if (s != TABI_OK) return s;
+  }
+  {
+    Tuning t = best;
+    t.threads = 512;
+    t.ctas = 2;
+    const tabi_status s = trial(t);
+    if (s != TABI_OK) return s;
+  }
+  {  // leave the requests with the chosen shape's results
+    float ms = 0.f;
+    const tabi_status s = run_batch_locked(ctx, params, reqs, n_reqs, stream, false, &best, &ms, nullptr);
+    if (s != TABI_OK) return s;
+  }
+  // remember it for this batch class (tabi_params.scale_fanout = 0 uses it)
+  const Pack &p = ctx->last;
+  int maxW = 1;
+  for (const AtlasDesc &d : ctx->last_desc) maxW = std::max(maxW, d.W);
+  const uint64_t cls = batch_class(p.A, p.N, maxW, params);
+  bool found = false;
+  for (TuneEntry &te : ctx->tuned)
+    if (te.key == cls) { te.t = best; te.ms = best_ms; found = true; }
+  if (!found) ctx->tuned.push_back(TuneEntry{cls, best, best_ms});
+  if (out) {
+    out->scale_fanout = best.F;
+    out->raster_warp_items = best.items;
+    out->rowloop_threads = best.threads;
+    out->rowloop_ctas = best.ctas;
+    out->ms = best_ms;
+  }
+  return TABI_OK;
 }
 
 tabi_status tabi_stage_times(tabi_ctx *ctx, int32_t enable, double *stage_ms, int64_t *launches,

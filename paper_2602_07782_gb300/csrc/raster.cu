@@ -67,13 +67,14 @@ __device__ __forceinline__ int32_t warp_axis(const rmath::AxisK &ak, int g, uint
 
 // Warp-items: (chart of an atlas still searching, run of G consecutive
 // candidates of the atlas's wave range).  G is chosen so that the wave has
-// about 32K warp-items.
+// about raster_items warp-items (a tuned launch shape).
 __global__ void __launch_bounds__(kRasterThreads, 4) raster_kernel(const Pack *__restrict__ pp, int wave, int nj) {
   __shared__ rmath::AxisK axk[kRasterWarps][2];
   const Pack &p = *pp;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int64_t total = p.act_info[1];
-  int G = (int)(((int64_t)nj * total + 32767) / 32768);
+  const int64_t target = p.raster_items;
+  int G = (int)(((int64_t)nj * total + target - 1) / target);
   G = G < 1 ? 1 : (G > nj ? nj : G);
   const int ngroups = (nj + G - 1) / G;
   const int64_t items = total * ngroups;

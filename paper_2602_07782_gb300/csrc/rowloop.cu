@@ -35,8 +35,7 @@
 namespace tabi {
 namespace {
 
-constexpr int kNT = 1024;
-constexpr int kNW = kNT / 32;
+constexpr int kMaxWarps = 32;
 constexpr int32_t kNeg = -(1 << 28);  // max-plus "minus infinity"
 constexpr int32_t kI32Min = -0x7fffffff - 1;
 
@@ -48,7 +47,7 @@ struct Ctl {
   int32_t region_lo, region_hi, knee_max;
   int32_t knee_rows, knees, knee_t[2], stage_lo, stage_hi, abort;
   int32_t t_at, t_j, t_skip;
-  int32_t red[kNW];
+  int32_t red[kMaxWarps];
 };
 
 // 2x2 max-plus matrix
@@ -77,18 +76,20 @@ __device__ __forceinline__ MP mpshfl_up(const MP &m, int o) {
   return r;
 }
 
+template <int NW>
 __device__ __forceinline__ int32_t block_max(int32_t v, Ctl &ctl) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   v = warp_max(v);
   if (lane == 0) ctl.red[w] = v;
   __syncthreads();
-  int32_t r = lane < kNW ? ctl.red[lane] : kI32Min;
+  int32_t r = lane < NW ? ctl.red[lane] : kI32Min;
   r = warp_max(r);
   __syncthreads();
   return r;
 }
+template <int NW>
 __device__ __forceinline__ int32_t block_min(int32_t v, Ctl &ctl) {
-  return -block_max(-v, ctl);
+  return -block_max<NW>(-v, ctl);
 }
 
 // segmented inclusive scan (max) over lanes; `heads` has a bit per lane
@@ -116,8 +117,10 @@ __host__ __device__ __forceinline__ int rowloop_maxrow(int W, int g) {
 // device counter, larger candidates of an atlas first.  A task is skipped,
 // or abandoned between rows, once a larger candidate of its atlas has
 // succeeded (unless every candidate is to be evaluated).
-__global__ void __launch_bounds__(kNT) rowloop_kernel(const Pack *__restrict__ pp, int wave, int nj,
-                                                      int smem_words) {
+// NT threads per CTA (1024: one CTA per multiprocessor; 512: two).
+template <int NT>
+__global__ void __launch_bounds__(NT) rowloop_kernel(const Pack *__restrict__ pp, int wave, int nj, int smem_words) {
+  constexpr int kNT = NT, kNW = NT / 32;
   const Pack &p = *pp;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t flags = p.flags;
@@ -208,20 +211,20 @@ __global__ void __launch_bounds__(kNT) rowloop_kernel(const Pack *__restrict__ p
             int32_t best = L - 1;
             for (int x = L + tid; x < R; x += kNT)
               if (front[x] >= cur) best = max(best, x);
-            best = block_max(best, ctl);
+            best = block_max<kNW>(best, ctl);
             if (tid == 0) { ctl.knee_r = best + 1; ctl.region_lo = best + 1; ctl.region_hi = Wp; }
           } else {
             const int32_t cur = front[L - 1];
             int32_t best = R;
             for (int x = L + tid; x < R; x += kNT)
               if (front[x] >= cur) best = min(best, x);
-            best = block_min(best, ctl);
+            best = block_min<kNW>(best, ctl);
             if (tid == 0) { ctl.knee_l = best; ctl.region_lo = 0; ctl.region_hi = best; }
           }
           __syncthreads();
           int32_t mx = 0;
           for (int x = ctl.region_lo + tid; x < ctl.region_hi; x += kNT) mx = max(mx, front[x]);
-          mx = block_max(mx, ctl);
+          mx = block_max<kNW>(mx, ctl);
           if (tid == 0) ctl.knee_max = mx;
         }
 
@@ -604,17 +607,27 @@ size_t rowloop_smem_wanted(int W, int g) {
 
 int rowloop_static_smem() {
   cudaFuncAttributes a;
-  if (cudaFuncGetAttributes(&a, rowloop_kernel) != cudaSuccess) return -1;
-  return (int)a.sharedSizeBytes;
+  int m = 0;
+  for (const void *f : {(const void *)rowloop_kernel<1024>, (const void *)rowloop_kernel<512>}) {
+    if (cudaFuncGetAttributes(&a, f) != cudaSuccess) return -1;
+    m = (int)a.sharedSizeBytes > m ? (int)a.sharedSizeBytes : m;
+  }
+  return m;
 }
 
 cudaError_t rowloop_prepare(int smem) {
-  return cudaFuncSetAttribute(rowloop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaError_t e = cudaFuncSetAttribute(rowloop_kernel<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(rowloop_kernel<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  return e;
 }
 
 void launch_rowloop(const Pack *dp, const Launch &L, int wave, int F, cudaStream_t st) {
-  // one CTA per multiprocessor (1024 threads and most of its shared memory)
-  rowloop_kernel<<<L.sms, kNT, L.rowloop_smem, st>>>(dp, wave, F, L.rowloop_smem / 4);
+  // persistent: as many CTAs as fit on the multiprocessors at once
+  if (L.rowloop_threads == 512)
+    rowloop_kernel<512><<<L.sms * L.rowloop_ctas, 512, L.rowloop_smem, st>>>(dp, wave, F, L.rowloop_smem / 4);
+  else
+    rowloop_kernel<1024><<<L.sms, 1024, L.rowloop_smem, st>>>(dp, wave, F, L.rowloop_smem / 4);
 }
 
 }  // namespace tabi

@@ -65,6 +65,8 @@ struct Pack {
   uint32_t flags;
   int32_t F;                    // candidates per wave (scale fan-out)
   int32_t nwaves;
+  int32_t raster_items;         // target warp-items of a raster wave
+  int32_t pad_;
   const AtlasDesc *atl;         // [A]
   int32_t *catl;                // [N] atlas of each chart
   tabi_chart_info *info;        // [N] input order
@@ -119,8 +121,10 @@ __host__ __device__ __forceinline__ WaveRange wave_range(int jtop, int wave, int
 // `st` and capturable; grids are fixed per device (persistent kernels loop
 // over the device-side work), so they depend only on the wave structure.
 struct Launch {
-  int sms;          // multiprocessors
-  int rowloop_smem; // dynamic shared memory of a row-loop CTA
+  int sms;             // multiprocessors
+  int rowloop_smem;    // dynamic shared memory of a row-loop CTA
+  int rowloop_threads; // 1024 or 512 threads per row-loop CTA
+  int rowloop_ctas;    // row-loop CTAs per multiprocessor (512 threads: 1 or 2)
 };
 void launch_init(const Pack *dp, const Launch &L, cudaStream_t st);
 void launch_prep(const Pack *dp, const Launch &L, cudaStream_t st);

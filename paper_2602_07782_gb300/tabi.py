@@ -40,6 +40,11 @@ class Request(ctypes.Structure):
                 ("scale_k", ctypes.c_int32), ("status", ctypes.c_int32)]
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("scale_fanout", ctypes.c_int32), ("raster_warp_items", ctypes.c_int32),
+                ("rowloop_threads", ctypes.c_int32), ("rowloop_ctas", ctypes.c_int32), ("ms", ctypes.c_float)]
+
+
 PLACEMENT_DTYPE = np.dtype([("x", "<i4"), ("y", "<i4"), ("rot90", "u1"), ("flip_x", "u1"),
                             ("flip_y", "u1"), ("mirror", "u1")])
 
@@ -54,7 +59,8 @@ CHART_INFO_DTYPE = np.dtype([
 
 EXPORTS = ["tabi_params_default", "tabi_ctx_create", "tabi_ctx_destroy", "tabi_last_error",
            "tabi_status_str", "tabi_arena_bytes", "tabi_pack", "tabi_pack_device", "tabi_pack_batch",
-           "tabi_pack_batch_device", "tabi_inspect", "tabi_inspect_atlas", "tabi_stage_times"]
+           "tabi_pack_batch_device", "tabi_autotune", "tabi_inspect", "tabi_inspect_atlas",
+           "tabi_stage_times"]
 STAGES = ["prep", "sort", "layout", "raster", "hcompact", "rowloop", "select", "pack"]
 
 _lib = None
@@ -86,6 +92,8 @@ def load(path: str = LIB_PATH):
     for f in ("tabi_pack_batch", "tabi_pack_batch_device"):
         getattr(lib, f).argtypes = [P, P, P, i32, P]
         getattr(lib, f).restype = ctypes.c_int
+    lib.tabi_autotune.argtypes = [P, P, P, i32, P, P]
+    lib.tabi_autotune.restype = ctypes.c_int
     lib.tabi_inspect.argtypes = [P, i32, i32, P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]
     lib.tabi_inspect.restype = ctypes.c_int
     lib.tabi_inspect_atlas.argtypes = [P, i32, i32, i32, P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]
@@ -243,6 +251,15 @@ class Context:
         params = params or params_default()
         f = self.lib.tabi_pack_batch_device if device else self.lib.tabi_pack_batch
         return int(f(self.h, ctypes.byref(params), reqs, len(reqs), ctypes.c_void_p(_stream_ptr(stream))))
+
+    def autotune(self, reqs, params: Params | None = None, stream=None):
+        """tabi_autotune on a prepared ctypes Request array (device pointers).
+        Returns (status, Tuning)."""
+        params = params or params_default()
+        t = Tuning()
+        st = self.lib.tabi_autotune(self.h, ctypes.byref(params), reqs, len(reqs),
+                                    ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(t))
+        return int(st), t
 
     # ---- inspection of the last pack ------------------------------------
     def _inspect(self, what: int, scale: int = 0, atlas: int = 0) -> np.ndarray:

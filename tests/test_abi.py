@@ -36,7 +36,7 @@ def test_param_defaults_follow_the_paper(lib):
     from paper_2602_07782_gb300 import tabi
     p = tabi.params_default()
     assert (p.gutter, p.knee_abs_pct, p.knee_rel_pct, p.lr_sig_pct) == (1, 10, 20, 10)
-    assert p.flags == tabi.F_ALL and p.scale_fanout == 64
+    assert p.flags == tabi.F_ALL and p.scale_fanout == 0  # 0: tuned / default launch shape
     assert tabi.status_str(tabi.TABI_ERR_NO_FIT) == "no candidate scale fits"
 
 

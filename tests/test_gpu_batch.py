@@ -80,7 +80,8 @@ def test_batch_steps_per_atlas(ctx):
     """Inspection of each atlas of a batch: prep, sort, envelopes, pairs and
     every candidate's row loop against the oracle."""
     sets = [synth.stars(3, 120, 512), synth.knees(5, 90, 512), synth.plain64(seed=2)]
-    p = tabi.params_default(flags=tabi.F_ALL | tabi.F_EVAL_ALL)
+    # one wave of all 64 candidates: no later wave reuses their regions
+    p = tabi.params_default(flags=tabi.F_ALL | tabi.F_EVAL_ALL, scale_fanout=64)
     op = oracle_params(p)
     st, res = ctx.pack_batch(sets, p)
     assert st == tabi.TABI_OK
@@ -191,26 +192,68 @@ def test_batch_device_entry_point(ctx):
         assert np.array_equal(got, h.place)
 
 
+def _device_requests(sets):
+    dev = torch.device("cuda:0")
+    keep, reqs = [], (tabi.Request * len(sets))()
+    for i, cs in enumerate(sets):
+        offs = torch.from_numpy(cs.offsets.view(np.int32).copy()).to(dev)
+        verts = torch.from_numpy(cs.verts.copy()).to(dev)
+        out = torch.zeros(12 * cs.n, dtype=torch.uint8, device=dev)
+        keep.append((offs, verts, out))
+        reqs[i] = tabi.Request(cs.atlas_w, cs.atlas_h, cs.n, cs.nv, offs.data_ptr(), verts.data_ptr(),
+                               out.data_ptr(), 0, 0)
+    return keep, reqs
+
+
+def test_autotune_keeps_results_exact(ctx):
+    """After the autotuner's trial launches (fan-outs, raster warp-items,
+    512-thread row-loop CTAs two per multiprocessor) the requests hold the
+    chosen shape's results, identical to the oracle's; the tuned shape is
+    then used for fan-out 0."""
+    sets = mixed_batch()
+    keep, reqs = _device_requests(sets)
+    p = tabi.params_default()
+    st, t = ctx.autotune(reqs, p)
+    assert st == tabi.TABI_OK, ctx.last_error()
+    assert t.scale_fanout in (64, 16, 8, 4) and t.raster_warp_items in (16384, 32768, 65536)
+    assert (t.rowloop_threads, t.rowloop_ctas) in ((1024, 1), (512, 2), (512, 1))
+    assert t.ms > 0
+    torch.cuda.synchronize()
+    op = oracle_params(p)
+    for i, cs in enumerate(sets):
+        place = keep[i][2].cpu().numpy().view(tabi.PLACEMENT_DTYPE)
+        compare(cs, tabi.PackResult(reqs[i].status, reqs[i].scale_k, place), op)
+    # fan-out 0 takes the tuned shape; same results again
+    st2, res = ctx.pack_batch(sets, p)
+    assert st2 == tabi.TABI_OK
+    for i, r in enumerate(res):
+        assert r.status == reqs[i].status and r.k == reqs[i].scale_k
+
+
 def test_batch_small_arena_fails_per_atlas():
-    """An arena too small for every region: the atlases whose regions do not
+    """Arenas too small for every region: the atlases whose regions do not
     fit report TABI_ERR_OOM, the others are still exact."""
     sets = [synth.stars(3, 300, 512), synth.stars2k(), synth.plain64(seed=1)]
     need = sum(tabi.arena_bytes(cs) for cs in sets)
-    c = tabi.Context(arena_bytes=need // 6)
-    try:
-        p = tabi.params_default()
-        st, res = c.pack_batch(sets, p)
-        if st == tabi.TABI_ERR_OOM:
-            return  # the per-chart arrays alone did not fit
-        assert st == tabi.TABI_OK
-        assert any(r.status == tabi.TABI_ERR_OOM for r in res)
-        op = oracle_params(p)
-        for cs, r in zip(sets, res):
-            assert r.status in (tabi.TABI_OK, tabi.TABI_ERR_OOM)
-            if r.status == tabi.TABI_OK:
-                compare(cs, r, op)
-    finally:
-        c.close()
+    p = tabi.params_default(scale_fanout=64)
+    op = oracle_params(p)
+    saw_oom = False
+    for div in (4, 8, 16, 32, 64):
+        c = tabi.Context(arena_bytes=max(need // div, 2 << 20))
+        try:
+            st, res = c.pack_batch(sets, p)
+            if st == tabi.TABI_ERR_OOM:
+                break  # the per-chart arrays alone no longer fit
+            assert st == tabi.TABI_OK
+            for cs, r in zip(sets, res):
+                assert r.status in (tabi.TABI_OK, tabi.TABI_ERR_OOM)
+                if r.status == tabi.TABI_OK:
+                    compare(cs, r, op)
+                else:
+                    saw_oom = True
+        finally:
+            c.close()
+    assert saw_oom
 
 
 @pytest.mark.slow
