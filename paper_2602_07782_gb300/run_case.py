@@ -1,0 +1,60 @@
+"""Pack one named synthetic workload a few times through the C ABI.
+
+A fixed, small driver for profilers (ncu) and quick checks:
+
+    python -m paper_2602_07782_gb300.run_case stars2k --reps 2
+    python -m paper_2602_07782_gb300.run_case batch --atlases 16 --reps 2
+
+Exits non-zero if a pack fails.  Builds the library first if needed.
+"""
+from __future__ import annotations
+
+import argparse
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def main(argv=None) -> int:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("case", choices=["plain64", "stars2k", "pareto20k", "batch"])
+    ap.add_argument("--reps", type=int, default=2)
+    ap.add_argument("--atlases", type=int, default=16)
+    ap.add_argument("--fanout", type=int, default=0)
+    args = ap.parse_args(argv)
+
+    import synth
+    if args.case == "batch":
+        sets = synth.stars_many(synth.batch256_specs(count=args.atlases))
+    else:
+        sets = [synth.WORKLOADS[args.case]()]
+
+    from . import build, tabi
+    build.build()
+    need = sum(tabi.arena_bytes(cs) for cs in sets)
+    ctx = tabi.Context(arena_bytes=min(need, 32 << 30) + (64 << 20))
+    params = tabi.params_default(scale_fanout=args.fanout)
+    ks = None
+    for _ in range(args.reps):
+        if len(sets) == 1:
+            r = ctx.pack(sets[0], params)
+            res = [r]
+        else:
+            st, res = ctx.pack_batch(sets, params)
+            if st != tabi.TABI_OK:
+                print("batch failed:", tabi.status_str(st), ctx.last_error())
+                return 1
+        if any(r.status != tabi.TABI_OK for r in res):
+            print("pack failed:", [tabi.status_str(r.status) for r in res], ctx.last_error())
+            return 1
+        ks = [r.k for r in res]
+    print(args.case, "atlases", len(sets), "k", ks[:8], "..." if len(ks) > 8 else "")
+    ctx.close()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
