@@ -61,7 +61,10 @@ typedef enum tabi_status {
   TABI_ERR_OOM = 3,         /* the context arena is too small for this input */
   TABI_ERR_CUDA = 4,        /* a CUDA call failed (see tabi_last_error)      */
   TABI_ERR_TIMEOUT = 5,     /* a bounded wait ran out (serving)              */
-  TABI_ERR_BUSY = 6         /* the context is in use by another call         */
+  TABI_ERR_BUSY = 6,        /* the context is in use by another call; or a
+                               server is shutting down                       */
+  TABI_PENDING = 7          /* not an error: the request is still in flight
+                               (tabi_poll)                                    */
 } tabi_status;
 
 #define TABI_PARAMS_VERSION 1
@@ -221,6 +224,68 @@ typedef struct tabi_tuning {
  * NULL) receives the choice.  Returns as tabi_pack_batch_device. */
 tabi_status tabi_autotune(tabi_ctx *ctx, const tabi_params *params, tabi_request *reqs, int32_t n_reqs,
                           void *stream, tabi_tuning *out);
+
+/* ---------------------------------------------------------------------
+ * Serving: continuous batching of requests as they arrive.
+ *
+ * A server owns a device-memory budget (arena_bytes, one allocation) split
+ * evenly into `lanes`; each lane is a packing context with its own stream.
+ * Submitted requests queue in arrival order; whenever a lane is idle a
+ * worker thread takes requests from the head of the queue -- as many as the
+ * lane's arena admits (the request's arena estimate at the server's
+ * fan-out), at most max_batch -- stages them in pinned memory and launches
+ * them as one batch.  Batches of different lanes overlap on the GPU, so
+ * requests arriving while others run start as soon as a lane frees up.
+ * Every request gets exactly the result tabi_pack would give it alone.
+ * A request whose estimate exceeds a lane's arena fails with TABI_ERR_OOM.
+ * -------------------------------------------------------------------- */
+typedef struct tabi_server tabi_server;
+
+typedef struct tabi_server_config {
+  int32_t device;      /* CUDA device                                        */
+  int32_t lanes;       /* batches in flight at once, 1..64 (4)               */
+  int32_t max_batch;   /* requests per batch, 1..TABI_MAX_BATCH (64)         */
+  int32_t pad;
+  size_t arena_bytes;  /* device memory budget, split over the lanes (8 GiB) */
+  tabi_params params;  /* for every request; scale_fanout 1..64 (8)          */
+} tabi_server_config;
+
+/* Completion record of one request; times in ns on the host's steady
+ * clock, from the server's creation: submitted, batch launched, result
+ * handed over. */
+typedef struct tabi_result {
+  int32_t status;  /* tabi_status of the request (as in tabi_request)        */
+  int32_t scale_k;
+  int64_t t_submit_ns, t_start_ns, t_done_ns;
+} tabi_result;
+
+typedef struct tabi_server_stats {
+  int64_t submitted, launched, completed; /* requests                        */
+  int64_t batches, max_batch;             /* batches launched, largest       */
+  int64_t queued, busy_lanes;             /* now                             */
+} tabi_server_stats;
+
+void tabi_server_config_default(tabi_server_config *cfg);
+/* TABI_ERR_INVALID_ARG (bad config), TABI_ERR_CUDA (allocation). */
+tabi_status tabi_server_create(tabi_server **out, const tabi_server_config *cfg);
+/* Stops taking batches, fails queued requests with TABI_ERR_BUSY, waits
+ * (at most 60 s) for the batches in flight, frees everything. */
+void tabi_server_destroy(tabi_server *srv);
+/* Queue a request (HOST pointers; offsets, verts and out must stay valid
+ * until the request completes; out is written when it completes with
+ * TABI_OK).  *ticket identifies it.  Returns TABI_OK (also for a request
+ * that fails its checks: the ticket then completes at once with its
+ * status), TABI_ERR_INVALID_ARG for NULL arguments, TABI_ERR_BUSY while
+ * shutting down.  Thread-safe. */
+tabi_status tabi_submit(tabi_server *srv, const tabi_request *req, uint64_t *ticket);
+/* TABI_OK and *res filled (the ticket is released) if the request has
+ * completed, TABI_PENDING if not, TABI_ERR_INVALID_ARG for an unknown
+ * ticket.  Never blocks on the device. */
+tabi_status tabi_poll(tabi_server *srv, uint64_t ticket, tabi_result *res);
+/* As tabi_poll, waiting at most timeout_ms: TABI_ERR_TIMEOUT if the request
+ * has not completed by then (the ticket stays valid). */
+tabi_status tabi_wait(tabi_server *srv, uint64_t ticket, int32_t timeout_ms, tabi_result *res);
+tabi_status tabi_server_get_stats(tabi_server *srv, tabi_server_stats *out);
 
 /* Intermediate results of the last pack on this context, copied to host
  * memory for inspection and step-by-step testing; tabi_inspect_atlas

@@ -9,65 +9,9 @@
 #include <string>
 #include <vector>
 
-#include "tabi_internal.cuh"
+#include "context.h"
 
 using namespace tabi;
-
-namespace {
-
-// One captured launch sequence: the kernels of a batch for fan-out F with a
-// row-loop CTA of `smem` dynamic bytes.  Every kernel reads the batch from
-// the record at the arena's start, so the graph serves any batch.
-struct GraphEntry {
-  int F, smem, threads, ctas;
-  cudaGraphExec_t exec;
-};
-
-// Launch shape of a batch: the knobs the autotuner sets.  None changes a
-// result, only how the work is cut.
-struct Tuning {
-  int F;        // candidates per wave (scale fan-out)
-  int items;    // raster warp-items per wave (sets candidates per warp)
-  int threads;  // row-loop CTA: 1024 or 512 threads
-  int ctas;     // row-loop CTAs per multiprocessor
-};
-
-struct TuneEntry {
-  uint64_t key;  // batch class
-  Tuning t;
-  float ms;
-};
-
-}  // namespace
-
-struct tabi_ctx {
-  int device = 0;
-  char *arena = nullptr;
-  size_t arena_bytes = 0;
-  bool owned = false;
-  std::atomic<int> busy{0};
-  std::string last_error;
-  int sms = 0, rowloop_dyn_max = 0, smem_per_sm = 0, smem_reserved = 0;
-  cudaStream_t cap_stream = nullptr;  // stream the graphs are captured on
-  std::vector<GraphEntry> graphs;
-  std::vector<TuneEntry> tuned;       // autotuner results per batch class
-  cudaEvent_t tev[2] = {};            // autotuner timing
-  // pinned host staging: the batch record going up, the results coming down
-  char *hstage = nullptr;
-  size_t hstage_bytes = 0;
-  // the last batch, for tabi_inspect
-  Pack last{};
-  bool has_last = false;
-  std::vector<AtlasDesc> last_desc;
-  std::vector<int> last_map;  // request index -> atlas index (-1: not run)
-  // optional per-stage timing (direct launches with events between stages)
-  bool timing = false;
-  cudaEvent_t ev[2 * (4 + 3 * kScales) + 8] = {};
-  int n_ev = 0;
-  double stage_ms[8] = {};
-  int64_t launches[8] = {};
-  int64_t packs = 0;
-};
 
 namespace {
 
@@ -324,10 +268,16 @@ std::string check_request(const tabi_request &r, const tabi_params *params, int 
   return "";
 }
 
-// One batch; the caller holds the context.
-tabi_status run_batch_locked(tabi_ctx *ctx, const tabi_params *params, tabi_request *reqs, int32_t R,
-                             void *stream, bool host, const Tuning *force = nullptr, float *ms_out = nullptr,
-                             Tuning *used = nullptr) {
+}  // namespace
+
+// First half of a batch: host checks, arena carving, input copies, the
+// launch sequence (graph replay) and the copies of the results into pinned
+// staging, all enqueued on `stream`.  Nothing waits for the device (except
+// with stage timing on).  The caller holds the context and calls
+// batch_finish once the stream has reached this point.
+tabi_status batch_launch(tabi_ctx *ctx, const tabi_params *params, tabi_request *reqs, int32_t R, void *stream,
+                         bool host, const Tuning *force, Tuning *used, InFlight &fl) {
+  fl = InFlight{};
   if (!valid_params(params)) return fail(ctx, TABI_ERR_INVALID_ARG, "bad params");
   if (!reqs || R < 1 || R > TABI_MAX_BATCH) return fail(ctx, TABI_ERR_INVALID_ARG, "bad request list");
   cudaStream_t st = (cudaStream_t)stream;
@@ -336,8 +286,8 @@ tabi_status run_batch_locked(tabi_ctx *ctx, const tabi_params *params, tabi_requ
 
   // host checks; the atlases that run, largest first (the row-loop queue
   // takes their tasks in this order)
-  std::vector<int> order;
-  std::string first_error;
+  std::vector<int> &order = fl.order;
+  std::string &first_error = fl.first_error;
   for (int r = 0; r < R; ++r) {
     reqs[r].scale_k = 0;
     reqs[r].status = TABI_ERR_INVALID_ARG;
@@ -348,11 +298,9 @@ tabi_status run_batch_locked(tabi_ctx *ctx, const tabi_params *params, tabi_requ
   std::stable_sort(order.begin(), order.end(),
                    [&](int a, int b) { return reqs[a].n_charts > reqs[b].n_charts; });
   const int A = (int)order.size();
+  fl.A = A;
   ctx->has_last = false;
-  if (A == 0) {
-    ctx->last_error = first_error;
-    return TABI_OK;
-  }
+  if (A == 0) return TABI_OK;
   int64_t N = 0;
   for (int i = 0; i < A; ++i) N += reqs[order[i]].n_charts;
   if (N > 0x7fffffffLL) return fail(ctx, TABI_ERR_INVALID_ARG, "too many charts in one batch");
@@ -362,7 +310,8 @@ tabi_status run_batch_locked(tabi_ctx *ctx, const tabi_params *params, tabi_requ
   Pack p{};
   Pack *dpack = cv.take<Pack>(1);
   AtlasDesc *ddesc = cv.take<AtlasDesc>(A);
-  std::vector<AtlasDesc> desc(A);
+  std::vector<AtlasDesc> &desc = fl.desc;
+  desc.assign(A, AtlasDesc{});
   int64_t cb = 0;
   for (int i = 0; i < A; ++i) {
     const tabi_request &r = reqs[order[i]];
@@ -494,9 +443,10 @@ tabi_status run_batch_locked(tabi_ctx *ctx, const tabi_params *params, tabi_requ
     cudaGraphExec_t exec = nullptr;
     const tabi_status gs = get_graph(ctx, L, p.F, &exec);
     if (gs != TABI_OK) return gs;
-    if (ms_out) cudaEventRecord(ctx->tev[0], st);
+    cudaEventRecord(ctx->tev[0], st);
     e = cudaGraphLaunch(exec, st);
-    if (ms_out) cudaEventRecord(ctx->tev[1], st);
+    cudaEventRecord(ctx->tev[1], st);
+    fl.timed = true;
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphLaunch");
   }
   PackResult *hres = reinterpret_cast<PackResult *>(ctx->hstage + res_off);
@@ -506,21 +456,50 @@ tabi_status run_batch_locked(tabi_ctx *ctx, const tabi_params *params, tabi_requ
     e = cudaMemcpyAsync(r.out, desc[i].out, sizeof(tabi_placement) * (size_t)r.n_charts,
                         cudaMemcpyDeviceToHost, st);
   }
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "pack");
-  if (ms_out && !ctx->timing) cudaEventElapsedTime(ms_out, ctx->tev[0], ctx->tev[1]);
-  ctx->last = p;
-  ctx->last_desc = desc;
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "result copy");
+  fl.p = p;
+  fl.res_off = res_off;
+  return TABI_OK;
+}
+
+// Second half: after the stream has passed batch_launch's work, the
+// per-request statuses and the inspection state.
+tabi_status batch_finish(tabi_ctx *ctx, tabi_request *reqs, int32_t R, InFlight &fl, float *ms_out) {
+  if (fl.A == 0) {
+    ctx->last_error = fl.first_error;
+    return TABI_OK;
+  }
+  if (ms_out && fl.timed) cudaEventElapsedTime(ms_out, ctx->tev[0], ctx->tev[1]);
+  const PackResult *hres = reinterpret_cast<const PackResult *>(ctx->hstage + fl.res_off);
+  ctx->last = fl.p;
+  ctx->last_desc = fl.desc;
   ctx->last_map.assign(R, -1);
-  for (int i = 0; i < A; ++i) {
-    tabi_request &r = reqs[order[i]];
-    ctx->last_map[order[i]] = i;
+  for (int i = 0; i < fl.A; ++i) {
+    tabi_request &r = reqs[fl.order[i]];
+    ctx->last_map[fl.order[i]] = i;
     r.status = hres[i].status;
     r.scale_k = hres[i].status == TABI_OK ? hres[i].k : 0;
   }
   ctx->has_last = true;
-  ctx->last_error = first_error;
+  ctx->last_error = fl.first_error;
   return TABI_OK;
+}
+
+namespace {
+
+// One batch, synchronously; the caller holds the context.
+tabi_status run_batch_locked(tabi_ctx *ctx, const tabi_params *params, tabi_request *reqs, int32_t R,
+                             void *stream, bool host, const Tuning *force = nullptr, float *ms_out = nullptr,
+                             Tuning *used = nullptr) {
+  InFlight fl;
+  tabi_status s = batch_launch(ctx, params, reqs, R, stream, host, force, used, fl);
+  if (s != TABI_OK || fl.A == 0) {
+    if (s == TABI_OK) batch_finish(ctx, reqs, R, fl, nullptr);
+    return s;
+  }
+  const cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "pack");
+  return batch_finish(ctx, reqs, R, fl, ms_out);
 }
 
 tabi_status run_batch(tabi_ctx *ctx, const tabi_params *params, tabi_request *reqs, int32_t R, void *stream,
@@ -641,6 +620,7 @@ const char *tabi_status_str(tabi_status s) {
     case TABI_ERR_CUDA: return "CUDA error";
     case TABI_ERR_TIMEOUT: return "timeout";
     case TABI_ERR_BUSY: return "context busy";
+    case TABI_PENDING: return "pending";
   }
   return "unknown status";
 }

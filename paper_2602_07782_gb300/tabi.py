@@ -16,7 +16,8 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libtabi.so")
 
-TABI_OK, TABI_ERR_INVALID_ARG, TABI_ERR_NO_FIT, TABI_ERR_OOM, TABI_ERR_CUDA, TABI_ERR_TIMEOUT, TABI_ERR_BUSY = range(7)
+(TABI_OK, TABI_ERR_INVALID_ARG, TABI_ERR_NO_FIT, TABI_ERR_OOM, TABI_ERR_CUDA, TABI_ERR_TIMEOUT, TABI_ERR_BUSY,
+ TABI_PENDING) = range(8)
 F_HC, F_BALANCE, F_OBB, F_LAABB = 1, 2, 4, 8
 F_ALL = 15
 F_EVAL_ALL = 16  # inspection aid: every candidate's row loop runs to its end
@@ -45,6 +46,21 @@ class Tuning(ctypes.Structure):
                 ("rowloop_threads", ctypes.c_int32), ("rowloop_ctas", ctypes.c_int32), ("ms", ctypes.c_float)]
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("lanes", ctypes.c_int32), ("max_batch", ctypes.c_int32),
+                ("pad", ctypes.c_int32), ("arena_bytes", ctypes.c_size_t), ("params", Params)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("scale_k", ctypes.c_int32), ("t_submit_ns", ctypes.c_int64),
+                ("t_start_ns", ctypes.c_int64), ("t_done_ns", ctypes.c_int64)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_int64) for f in ("submitted", "launched", "completed", "batches", "max_batch",
+                                              "queued", "busy_lanes")]
+
+
 PLACEMENT_DTYPE = np.dtype([("x", "<i4"), ("y", "<i4"), ("rot90", "u1"), ("flip_x", "u1"),
                             ("flip_y", "u1"), ("mirror", "u1")])
 
@@ -60,7 +76,8 @@ CHART_INFO_DTYPE = np.dtype([
 EXPORTS = ["tabi_params_default", "tabi_ctx_create", "tabi_ctx_destroy", "tabi_last_error",
            "tabi_status_str", "tabi_arena_bytes", "tabi_pack", "tabi_pack_device", "tabi_pack_batch",
            "tabi_pack_batch_device", "tabi_autotune", "tabi_inspect", "tabi_inspect_atlas",
-           "tabi_stage_times"]
+           "tabi_stage_times", "tabi_server_config_default", "tabi_server_create", "tabi_server_destroy",
+           "tabi_submit", "tabi_poll", "tabi_wait", "tabi_server_get_stats"]
 STAGES = ["prep", "sort", "layout", "raster", "hcompact", "rowloop", "select", "pack"]
 
 _lib = None
@@ -94,6 +111,18 @@ def load(path: str = LIB_PATH):
         getattr(lib, f).restype = ctypes.c_int
     lib.tabi_autotune.argtypes = [P, P, P, i32, P, P]
     lib.tabi_autotune.restype = ctypes.c_int
+    lib.tabi_server_config_default.argtypes = [P]
+    lib.tabi_server_create.argtypes = [ctypes.POINTER(P), P]
+    lib.tabi_server_create.restype = ctypes.c_int
+    lib.tabi_server_destroy.argtypes = [P]
+    lib.tabi_submit.argtypes = [P, P, ctypes.POINTER(ctypes.c_uint64)]
+    lib.tabi_submit.restype = ctypes.c_int
+    lib.tabi_poll.argtypes = [P, ctypes.c_uint64, P]
+    lib.tabi_poll.restype = ctypes.c_int
+    lib.tabi_wait.argtypes = [P, ctypes.c_uint64, i32, P]
+    lib.tabi_wait.restype = ctypes.c_int
+    lib.tabi_server_get_stats.argtypes = [P, P]
+    lib.tabi_server_get_stats.restype = ctypes.c_int
     lib.tabi_inspect.argtypes = [P, i32, i32, P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]
     lib.tabi_inspect.restype = ctypes.c_int
     lib.tabi_inspect_atlas.argtypes = [P, i32, i32, i32, P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]
@@ -315,6 +344,79 @@ class Context:
         hdr = raw[:32].view(np.int32)
         place = raw[32:32 + 16 * n].view(np.int32).reshape(n, 4)
         return hdr, place
+
+
+def server_config_default(**kw) -> ServerConfig:
+    c = ServerConfig()
+    load().tabi_server_config_default(ctypes.byref(c))
+    for k, v in kw.items():
+        if k == "params":
+            c.params = v
+        else:
+            setattr(c, k, v)
+    return c
+
+
+class Server:
+    """Serving loop (continuous batching) on one device: tabi_server_*."""
+
+    def __init__(self, cfg: ServerConfig | None = None, **kw):
+        self.lib = load()
+        cfg = cfg or server_config_default(**kw)
+        h = ctypes.c_void_p()
+        st = self.lib.tabi_server_create(ctypes.byref(h), ctypes.byref(cfg))
+        if st != TABI_OK:
+            raise RuntimeError(f"tabi_server_create failed: {status_str(st)}")
+        self.h = h
+        self._held = {}  # ticket -> buffers that must outlive the request
+
+    def submit(self, cs, out: np.ndarray | None = None):
+        """Queue one ChartSet (host buffers).  Returns (status, ticket, out)."""
+        offs = np.ascontiguousarray(cs.offsets, np.uint32)
+        verts = np.ascontiguousarray(cs.verts, np.int32)
+        if out is None:
+            out = np.zeros(cs.n, PLACEMENT_DTYPE)
+        return self.submit_ptrs(cs.n, cs.nv, cs.atlas_w, cs.atlas_h, offs, verts, out)
+
+    def submit_ptrs(self, n, nv, W, H, offs: np.ndarray, verts: np.ndarray, out: np.ndarray):
+        req = Request(W, H, n, nv, offs.ctypes.data, verts.ctypes.data, out.ctypes.data, 0, 0)
+        t = ctypes.c_uint64(0)
+        st = self.lib.tabi_submit(self.h, ctypes.byref(req), ctypes.byref(t))
+        if st == TABI_OK:
+            self._held[int(t.value)] = (offs, verts, out)
+        return int(st), int(t.value), out
+
+    def _done(self, ticket, st, r):
+        if st == TABI_OK:
+            self._held.pop(ticket, None)
+        return st, r
+
+    def poll(self, ticket: int):
+        r = Result()
+        st = self.lib.tabi_poll(self.h, ticket, ctypes.byref(r))
+        return self._done(ticket, int(st), r)
+
+    def wait(self, ticket: int, timeout_ms: int = 60000):
+        r = Result()
+        st = self.lib.tabi_wait(self.h, ticket, int(timeout_ms), ctypes.byref(r))
+        return self._done(ticket, int(st), r)
+
+    def stats(self) -> dict:
+        s = ServerStats()
+        self.lib.tabi_server_get_stats(self.h, ctypes.byref(s))
+        return {f: int(getattr(s, f)) for f, _ in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.tabi_server_destroy(self.h)
+            self.h = None
+            self._held.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def _stream_ptr(stream) -> int:
