@@ -14,7 +14,11 @@ HBM, L2 flushed (256 MiB write) before every step, each step bracketed by
 CUDA events on the packing stream.  e2e: the same batch through the
 host-buffer entry point (tabi_pack_batch) from pinned host memory, the
 host<->device copies inside the timed region.  plain: the same atlases
-through the single-atlas entry point, one call each.  The roofline stage
+through the single-atlas entry point, one call each.  served: the serving
+loop (tabi_server, continuous batching, 8 GiB arena) under a Poisson
+stream of 2,000 requests/s for 10 s (chart counts log-uniform 16..20,000,
+sides 512..4096), p50/p99 latency against the 15 ms interactive budget,
+beside the plain packer serving the same stream one request at a time.  The roofline stage
 times come from CUDA events the library records on the packing stream
 around every stage, over K further steps of the same workload.
 --impl reference times the CPU oracle on the same atlases.
@@ -52,6 +56,12 @@ def parse():
     ap.add_argument("--atlases", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--serve-rate", type=float, default=2000.0)
+    ap.add_argument("--serve-bodies", type=int, default=256)
+    ap.add_argument("--serve-lanes", type=int, default=4)
+    ap.add_argument("--serve-fanout", type=int, default=8)
     return ap.parse_args()
 
 
@@ -374,6 +384,125 @@ def run_ours(args, rank, world, local, sets):
     return res
 
 
+def serve_workload(args):
+    """Arrival times and request bodies of the served workload: Poisson
+    arrivals at --serve-rate for --serve-seconds, chart counts log-uniform
+    in 16..20,000, sides 512..4096, star charts; the arrivals draw their
+    bodies from the first --serve-bodies distinct requests of the stream
+    (generating all 20,000 bodies would take an hour of host time)."""
+    import synth
+    specs = synth.serve_specs(rate=args.serve_rate, duration=args.serve_seconds)
+    P = min(args.serve_bodies, len(specs))
+    bodies = synth.stars_many([sp[1:] for sp in specs[:P]])
+    return [sp[0] for sp in specs], [i % P for i in range(len(specs))], bodies
+
+
+def run_served(args, local, arrivals, body_of, bodies):
+    """The serving loop under the Poisson stream: submit each request at its
+    arrival time from one host thread, collect completions on another.
+    Latency = result handed over - submitted (library host clock)."""
+    import ctypes
+
+    import torch
+
+    from paper_2602_07782_gb300 import tabi
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+    # each body alone through the plain single-atlas packer: its result and
+    # its service time (stream-synchronous call, wall clock, median of 3)
+    ctx = tabi.Context(arena_bytes=8 << 30, device=local)
+    params = tabi.params_default()
+    ref_k, service = [], []
+    for cs in bodies:
+        offs = torch.from_numpy(cs.offsets.view(np.int32).copy()).to(dev)
+        verts = torch.from_numpy(cs.verts.copy()).to(dev)
+        out = torch.zeros(12 * cs.n, dtype=torch.uint8, device=dev)
+        ts = []
+        for _ in range(3):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st, k = ctx.pack_device(cs.n, cs.nv, cs.atlas_w, cs.atlas_h, offs, verts, out, params)
+            ts.append(time.perf_counter() - t0)
+            assert st == 0, ctx.last_error()
+        ref_k.append(k)
+        service.append(float(np.median(ts)))
+    ctx.close()
+    # the plain packer serving the same stream: one pack at a time, FIFO
+    done = 0.0
+    plain_lat = []
+    for t, b in zip(arrivals, body_of):
+        done = max(done, t) + service[b]
+        plain_lat.append(done - t)
+    plain_lat = np.array(plain_lat) * 1e3
+    plain_span = done - arrivals[0]
+
+    sp = tabi.params_default(scale_fanout=args.serve_fanout)
+    srv = tabi.Server(lanes=args.serve_lanes, max_batch=64, arena_bytes=8 << 30, params=sp)
+    host = [(np.ascontiguousarray(cs.offsets, np.uint32), np.ascontiguousarray(cs.verts, np.int32)) for cs in bodies]
+    for b, cs in enumerate(bodies):  # warm-up: every body once (graphs, caches)
+        st, t, _ = srv.submit_ptrs(cs.n, cs.nv, cs.atlas_w, cs.atlas_h, host[b][0], host[b][1],
+                                   np.zeros(cs.n, tabi.PLACEMENT_DTYPE))
+        assert st == 0
+    while srv.stats()["completed"] < len(bodies):
+        time.sleep(0.01)
+    base = srv.stats()
+    tickets = [None] * len(arrivals)
+    results = [None] * len(arrivals)
+    ready = threading.Semaphore(0)
+
+    def submitter():
+        t0 = time.perf_counter()
+        for i, (ta, b) in enumerate(zip(arrivals, body_of)):
+            while True:
+                dt = t0 + ta - time.perf_counter()
+                if dt <= 0:
+                    break
+                time.sleep(dt - 0.0002 if dt > 0.0005 else 0)
+            cs = bodies[b]
+            st, t, _ = srv.submit_ptrs(cs.n, cs.nv, cs.atlas_w, cs.atlas_h, host[b][0], host[b][1],
+                                       np.empty(cs.n, tabi.PLACEMENT_DTYPE))
+            assert st == 0
+            tickets[i] = t
+            ready.release()
+
+    def collector():
+        for i in range(len(arrivals)):
+            ready.acquire()
+            st, r = srv.wait(tickets[i], 120000)
+            assert st == 0
+            results[i] = (r.status, r.scale_k, r.t_submit_ns, r.t_start_ns, r.t_done_ns)
+
+    ths = [threading.Thread(target=submitter), threading.Thread(target=collector)]
+    for th in ths:
+        th.start()
+    for th in ths:
+        th.join()
+    stats = srv.stats()
+    srv.close()
+    ok = all(r[0] == 0 and r[1] == ref_k[b] for r, b in zip(results, body_of))
+    lat = np.array([(r[4] - r[2]) * 1e-6 for r in results])
+    span = (max(r[4] for r in results) - min(r[2] for r in results)) * 1e-9
+    nb = stats["batches"] - base["batches"]
+    return {
+        "value": len(arrivals) / span, "unit": "packs/s",
+        "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+        "within_15ms": float(np.mean(lat <= 15.0)), "budget_ms": 15.0,
+        "requests": len(arrivals), "rate_per_s": args.serve_rate, "seconds": args.serve_seconds,
+        "distinct_bodies": len(bodies), "charts_mean": float(np.mean([bodies[b].n for b in body_of])),
+        "lanes": args.serve_lanes, "scale_fanout": args.serve_fanout, "arena_bytes": 8 << 30,
+        "batches": nb, "mean_batch": (stats["launched"] - base["launched"]) / max(1, nb),
+        "max_batch": stats["max_batch"], "results_equal_alone": ok,
+        "plain_fifo": {"value": len(arrivals) / plain_span, "unit": "packs/s",
+                       "p50_ms": float(np.percentile(plain_lat, 50)),
+                       "p99_ms": float(np.percentile(plain_lat, 99)),
+                       "within_15ms": float(np.mean(plain_lat <= 15.0)),
+                       "how": "the single-atlas packer serving the same arrivals one at a time (FIFO), "
+                              "from each body's measured tabi_pack_device time"},
+        "how": "tabi_server: 8 GiB arena over the lanes, continuous batching; one submitting thread at the "
+               "arrival times, one collecting thread; latency = result handed over - submitted",
+    }
+
+
 def run_reference(args, rank, world):
     """The CPU oracle on the same atlases: one atlas per step, in batch order."""
     import oracle
@@ -415,12 +544,15 @@ def main():
             print(json.dumps(res))
         return
     sets = workload(args.atlases)  # spawned generator pool, before any CUDA work
+    served_inputs = None if args.no_serve or rank != 0 else serve_workload(args)
     if world > 1:
         import torch
         torch.distributed.init_process_group("nccl")
     import __graft_entry__
     __graft_entry__.build()
     res = run_ours(args, rank, world, local, sets)
+    if served_inputs is not None:
+        res["served"] = run_served(args, local, *served_inputs)
     if rank == 0:
         if not args.no_cpu_baseline:
             res["cpu_baseline"] = cpu_baseline(sets)

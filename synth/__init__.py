@@ -1,4 +1,4 @@
 """Seeded synthetic chart sets (inputs only; no packing arithmetic)."""
 from .charts import (ChartSet, Request, batch256, batch256_specs, from_polygons, knees,  # noqa: F401
-                     pareto20k, plain64, rectangles, serve_stream, stars, stars2k, stars_many,
+                     pareto20k, plain64, rectangles, serve_specs, serve_stream, stars, stars2k, stars_many,
                      WORKLOADS)

@@ -325,13 +325,14 @@ class Request:
     charts: ChartSet
 
 
-def serve_stream(seed: int = 5, rate: float = 2000.0, duration: float = 10.0,
-                 lo: int = 16, hi: int = 20000, sides=(512, 1024, 2048, 4096),
-                 limit: int | None = None) -> list[Request]:
-    """Poisson arrivals; chart counts log-uniform in [lo, hi]."""
+def serve_specs(seed: int = 5, rate: float = 2000.0, duration: float = 10.0,
+                lo: int = 16, hi: int = 20000, sides=(512, 1024, 2048, 4096),
+                limit: int | None = None) -> list[tuple[float, int, int, int]]:
+    """(arrival time s, chart seed, chart count, atlas side) of each request
+    of serve_stream, without generating the charts."""
     rng = np.random.default_rng([seed, 5])
     t = 0.0
-    reqs = []
+    out = []
     i = 0
     while True:
         t += rng.exponential(1.0 / rate)
@@ -339,9 +340,17 @@ def serve_stream(seed: int = 5, rate: float = 2000.0, duration: float = 10.0,
             break
         n = int(round(math.exp(rng.uniform(math.log(lo), math.log(hi)))))
         side = int(sides[int(rng.integers(0, len(sides)))])
-        reqs.append(Request(t, stars(seed * 1000003 + i, n, side)))
+        out.append((t, seed * 1000003 + i, n, side))
         i += 1
-    return reqs
+    return out
+
+
+def serve_stream(seed: int = 5, rate: float = 2000.0, duration: float = 10.0,
+                 lo: int = 16, hi: int = 20000, sides=(512, 1024, 2048, 4096),
+                 limit: int | None = None) -> list[Request]:
+    """Poisson arrivals; chart counts log-uniform in [lo, hi]."""
+    return [Request(t, stars(sd, n, side)) for t, sd, n, side in
+            serve_specs(seed, rate, duration, lo, hi, sides, limit)]
 
 
 def rectangles(sizes_tx, atlas_w: int, atlas_h: int, seed: int = 0) -> ChartSet:
