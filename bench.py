@@ -156,6 +156,17 @@ def raster_sources_digest() -> str:
     return h.hexdigest()[:16]
 
 
+def max_over_ranks(total_ms: float, world: int, device=None) -> float:
+    """The timed region of the slowest replica (whole-job time): a MAX
+    all-reduce over the ranks (NCCL on the GPUs, gloo in the CPU tests)."""
+    if world <= 1:
+        return total_ms
+    import torch
+    t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
 def wave_ranges(jtop: int, k_best: int, F: int):
     """(wave, candidates) the batch evaluates for one atlas: waves of F
     candidates below its top candidate, down to the wave of its result."""
@@ -272,9 +283,7 @@ def run_ours(args, rank, world, local, sets):
     per = np.array([a.elapsed_time(b) for a, b in evs])
     total_ms = float(per.sum())
     if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+        total_ms = max_over_ranks(total_ms, world, dev)
         torch.distributed.barrier()
     assert [r.scale_k for r in reqs] == ks
 
