@@ -111,7 +111,8 @@ __global__ void __launch_bounds__(kRasterThreads, 4) raster_kernel(const Pack *_
         rmath::setup_obb_base(ax ? a1 : a0, ax, sh.Wq, sh.Hq, k, m, C, S, sh.u0, sh.u1, sh.v0, sh.v1, use_l,
                               use_o);
       } else if (corner_lane) {
-        rmath::corner_store(cq, lane - 24, (lane - 24) >> 2 ? a1 : a0);
+        const int ax = (lane - 24) >> 2;
+        rmath::corner_store(cq, lane - 24, ax ? a1 : a0, (ax ? sh.Hq : sh.Wq) * k);
         rmath::corner_advance(cq);
       }
       __syncwarp();

@@ -21,7 +21,8 @@
 // Lower is convex and upper concave in X, so over [a, b] each reaches its
 // extreme at the box corner when the corner lies in [a, b], else at the
 // nearer end; the corner's position is kept as floor/ceil(pos / N),
-// N = C^2 + S^2, which decides both tests exactly for integer a, b.
+// N = C^2 + S^2, which decides both tests exactly for integer a, b, and is
+// turned into a range of scanline indices once per candidate.
 //
 // The 32-bit floor division by d (= C or S, 3196..16384) multiplies by a
 // float reciprocal estimate and corrects the estimate with one exact
@@ -59,7 +60,11 @@ struct AxisK {
   float r1, r2;                 // float reciprocal estimates of d1, d2
   int32_t corner_lo, corner_hi; // extreme values at the corners
   int32_t len, len_other, use_l, use_o;
-  int64_t plo_f, plo_c, phi_f, phi_c;  // floor/ceil(corner position / N)
+  // corner tests in scanline units (see corner_store): the corner value
+  // applies on scanlines [c0, c1]; scanlines c > f lie wholly past the
+  // corner (the bound's extreme over them is at their start)
+  int32_t lo_c0, lo_c1, lo_f, hi_c0, hi_c1, hi_f;
+  int32_t clip_c;                      // the scanline cut by the chart's end (-1: none)
   int64_t end;                         // ext * k
   int64_t A1, A2, B1, B2;              // 64-bit form for the clipped scanline
 };
@@ -103,6 +108,7 @@ TABI_HD void setup_obb_base(AxisK &ak, int axis, int64_t Wq, int64_t Hq, int64_t
   ak.len = (int32_t)(axis == 0 ? w : h);
   ak.len_other = (int32_t)(axis == 0 ? h : w);
   ak.end = (axis == 0 ? Wq : Hq) * k;
+  ak.clip_c = (ak.end & (kF - 1)) ? ak.len - 1 : -1;
   ak.use_l = use_l;
   ak.use_o = use_o && m > 0;
   if (!ak.use_o) return;
@@ -155,13 +161,31 @@ TABI_HD void corner_advance(CornerQ &cq) {
   if (cq.r >= cq.D) { cq.r -= cq.D; cq.q += 1; }
 }
 
-// Store the corner quantity into its axis' constants.
-TABI_HD void corner_store(const CornerQ &cq, int item, AxisK &ak) {
+// Corner position pos (scaled units) as scanline tests.  Over scanline c,
+// X in [a, b] = [cF, min((c+1)F, end)], the corner value applies iff
+// a <= floor(pos) and ceil(pos) <= b, i.e. iff c0 <= c <= c1 with
+// c0 = ceil(ceil(pos)/F) - 1, c1 = floor(floor(pos)/F) when 0 <= pos and
+// ceil(pos) <= end, and never otherwise; the scanline lies wholly past the
+// corner (floor(pos) < a) iff c > f = floor(floor(pos)/F).
+TABI_HD void corner_range(int64_t pf, int64_t pc, int64_t end, int32_t &c0, int32_t &c1, int32_t &f) {
+  f = (int32_t)(pf >> 18);
+  if (pf < 0 || pc > end) {
+    c0 = 1;
+    c1 = 0;
+  } else {
+    c0 = (int32_t)(((pc + kF - 1) >> 18) - 1);
+    c1 = f;
+  }
+}
+
+// Store the corner quantity into its axis' constants.  `end` = ext * k of
+// the item's axis.
+TABI_HD void corner_store(const CornerQ &cq, int item, AxisK &ak, int64_t end) {
   switch (item & 3) {
     case 0: ak.corner_lo = (int32_t)cq.q; break;
     case 1: ak.corner_hi = (int32_t)-cq.q; break;
-    case 2: ak.plo_f = cq.q; ak.plo_c = cq.q + (cq.r != 0); break;
-    default: ak.phi_f = cq.q; ak.phi_c = cq.q + (cq.r != 0); break;
+    case 2: corner_range(cq.q, cq.q + (cq.r != 0), end, ak.lo_c0, ak.lo_c1, ak.lo_f); break;
+    default: corner_range(cq.q, cq.q + (cq.r != 0), end, ak.hi_c0, ak.hi_c1, ak.hi_f); break;
   }
 }
 
@@ -181,34 +205,23 @@ TABI_HD int32_t obb_upper_at(const AxisK &ak, int32_t q, bool clipped) {
                          -fdiv64(ak.B2 - X * ak.b2, (int64_t)ak.d2 * kF));
 }
 
-// Raw bounds of scanline c (0 <= c < len): [lo, hi) with hi > lo.
-TABI_HD void scanline(const AxisK &ak, int32_t c, int32_t &lo_out, int32_t &hi_out) {
+// Raw bounds of scanline c (0 <= c < len): [lo, hi) with hi > lo, given
+// the local-AABB bounds pl, ph of the pieces that meet the scanline.
+TABI_HD void scanline_from(const AxisK &ak, int32_t c, int32_t pl, int32_t ph, int32_t &lo_out,
+                           int32_t &hi_out) {
   int32_t lo = 0, hi = ak.len_other;
   if (ak.use_l) {
-    int32_t pl = kInf, ph = -kInf;
-#pragma unroll
-    for (int i = 0; i < kK; ++i) {
-      const uint32_t pr = ak.prange[i];
-      if ((int32_t)(pr & 0xffffu) <= c && c <= (int32_t)(pr >> 16)) {
-        const uint32_t pv = ak.pval[i];
-        pl = imin32(pl, (int32_t)(pv & 0xffffu));
-        ph = imax32(ph, (int32_t)(pv >> 16));
-      }
-    }
     lo = imax32(lo, pl);
     hi = imin32(hi, ph);
   }
   if (ak.use_o) {
-    const int64_t a = (int64_t)c * kF;
-    const int64_t bfull = a + kF;
-    const bool clip = bfull > ak.end;
-    const int64_t b = clip ? ak.end : bfull;
+    const bool clip = c == ak.clip_c;
     int32_t tl, th;
-    if (a <= ak.plo_f && ak.plo_c <= b) tl = ak.corner_lo;
-    else if (ak.plo_f < a) tl = obb_lower_at(ak, c, false);
+    if (ak.lo_c0 <= c && c <= ak.lo_c1) tl = ak.corner_lo;
+    else if (c > ak.lo_f) tl = obb_lower_at(ak, c, false);
     else tl = obb_lower_at(ak, c + 1, clip);
-    if (a <= ak.phi_f && ak.phi_c <= b) th = ak.corner_hi;
-    else if (ak.phi_f < a) th = obb_upper_at(ak, c, false);
+    if (ak.hi_c0 <= c && c <= ak.hi_c1) th = ak.corner_hi;
+    else if (c > ak.hi_f) th = obb_upper_at(ak, c, false);
     else th = obb_upper_at(ak, c + 1, clip);
     lo = imax32(lo, tl);
     hi = imin32(hi, th);
@@ -217,6 +230,21 @@ TABI_HD void scanline(const AxisK &ak, int32_t c, int32_t &lo_out, int32_t &hi_o
   hi = imax32(lo + 1, imin32(hi, ak.len_other));
   lo_out = lo;
   hi_out = hi;
+}
+
+// The same with the pieces tested here (all ten per scanline).
+TABI_HD void scanline(const AxisK &ak, int32_t c, int32_t &lo_out, int32_t &hi_out) {
+  int32_t pl = kInf, ph = -kInf;
+#pragma unroll
+  for (int i = 0; i < kK; ++i) {
+    const uint32_t pr = ak.prange[i];
+    if ((int32_t)(pr & 0xffffu) <= c && c <= (int32_t)(pr >> 16)) {
+      const uint32_t pv = ak.pval[i];
+      pl = imin32(pl, (int32_t)(pv & 0xffffu));
+      ph = imax32(ph, (int32_t)(pv >> 16));
+    }
+  }
+  scanline_from(ak, c, pl, ph, lo_out, hi_out);
 }
 
 }  // namespace rmath
