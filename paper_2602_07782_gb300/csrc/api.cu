@@ -83,7 +83,7 @@ __global__ void init_kernel(const Pack *__restrict__ pp) {
   const int t = threadIdx.x;
   if (blockIdx.x == 0) {
     if (t < 2 * kScales) p.jtot[t] = 0;
-    if (t < kScales) p.counter[t] = 0;
+    for (int i = t; i < kScales * kMaxChunks; i += blockDim.x) p.counter[i] = 0;
   }
   for (int at = blockIdx.x; at < p.A; at += gridDim.x) {
     if (t < kScales) p.scale_out[at * kScales + t] = ScaleOut{0, 0, 0, 0, 0, 0, 0, 0};
@@ -175,8 +175,8 @@ struct StageMarks {
 int waves_of(int F) { return (kScales + F - 1) / F; }
 
 // The launch sequence of a batch: prep, sort, layout, then descending waves
-// of F candidates per atlas from its top candidate (plan, raster,
-// compaction, row loop), then selection.
+// of F candidates per atlas from its top candidate, each in Q chunks of the
+// sorted charts (plan, raster, compaction, row loop), then selection.
 void enqueue(const Pack *dp, const Launch &L, int F, cudaStream_t st, StageMarks *mk) {
   auto b = [&](int s) { if (mk) mk->begin(s); };
   auto e = [&]() { if (mk) mk->end(); };
@@ -190,18 +190,19 @@ void enqueue(const Pack *dp, const Launch &L, int F, cudaStream_t st, StageMarks
   b(2);
   launch_layout(dp, L, st);
   e();
-  for (int wave = 0; wave < waves_of(F); ++wave) {
-    b(3);
-    launch_plan(dp, L, wave, st);
-    launch_raster(dp, L, wave, F, st);
-    e();
-    b(4);
-    launch_hcompact(dp, L, wave, F, st);
-    e();
-    b(5);
-    launch_rowloop(dp, L, wave, F, st);
-    e();
-  }
+  for (int wave = 0; wave < waves_of(F); ++wave)
+    for (int q = 0; q < L.Q; ++q) {  // chart chunks of the wave (lazy evaluation)
+      b(3);
+      launch_plan(dp, L, wave, q, st);
+      launch_raster(dp, L, wave, q, F, st);
+      e();
+      b(4);
+      launch_hcompact(dp, L, wave, q, F, st);
+      e();
+      b(5);
+      launch_rowloop(dp, L, wave, q, F, st);
+      e();
+    }
   b(6);
   launch_select(dp, L, st);
   e();
@@ -209,7 +210,8 @@ void enqueue(const Pack *dp, const Launch &L, int F, cudaStream_t st, StageMarks
 
 tabi_status get_graph(tabi_ctx *ctx, const Launch &L, int F, cudaGraphExec_t *out) {
   for (const GraphEntry &g : ctx->graphs)
-    if (g.F == F && g.smem == L.rowloop_smem && g.threads == L.rowloop_threads && g.ctas == L.rowloop_ctas) {
+    if (g.F == F && g.smem == L.rowloop_smem && g.threads == L.rowloop_threads && g.ctas == L.rowloop_ctas &&
+        g.Q == L.Q) {
       *out = g.exec;
       return TABI_OK;
     }
@@ -223,7 +225,7 @@ tabi_status get_graph(tabi_ctx *ctx, const Launch &L, int F, cudaGraphExec_t *ou
   e = cudaGraphInstantiate(&exec, graph, 0);
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphInstantiate");
-  ctx->graphs.push_back(GraphEntry{F, L.rowloop_smem, L.rowloop_threads, L.rowloop_ctas, exec});
+  ctx->graphs.push_back(GraphEntry{F, L.rowloop_smem, L.rowloop_threads, L.rowloop_ctas, L.Q, exec});
   *out = exec;
   return TABI_OK;
 }
@@ -241,7 +243,9 @@ uint64_t batch_class(int A, int64_t N, int maxW, const tabi_params *params) {
          (uint64_t)params->gutter << 24 | (uint64_t)(params->flags & TABI_F_ALL) << 32;
 }
 
-Tuning default_tuning(int A) { return Tuning{A == 1 ? kScales : 8, 32768, 1024, 1}; }
+// One atlas: every candidate at once, no chunks (its row loops are the
+// critical path); a batch: waves of eight candidates in four chunks.
+Tuning default_tuning(int A) { return A == 1 ? Tuning{kScales, 32768, 1024, 1, 1} : Tuning{8, 32768, 1024, 1, 4}; }
 
 bool ensure_hstage(tabi_ctx *ctx, size_t bytes) {
   if (ctx->hstage_bytes >= bytes) return true;
@@ -357,6 +361,9 @@ tabi_status batch_launch(tabi_ctx *ctx, const tabi_params *params, tabi_request 
   p.F = tn.F;
   p.nwaves = waves_of(p.F);
   p.raster_items = tn.items;
+  p.Q = tn.Q < 1 ? 1 : (tn.Q > kMaxChunks ? kMaxChunks : tn.Q);
+  p.wps_stride = 4;
+  for (int i = 0; i < A; ++i) p.wps_stride = std::max(p.wps_stride, (desc[i].W + 2 * p.g + 3) & ~3);
   p.atl = ddesc;
   const size_t n = (size_t)N;
   p.catl = cv.take<int32_t>(n);
@@ -386,7 +393,10 @@ tabi_status batch_launch(tabi_ctx *ctx, const tabi_params *params, tabi_request 
   p.act_atl = cv.take<int32_t>(A);
   p.act_pre = cv.take<int32_t>(A);
   p.act_chart = cv.take<int32_t>(n);
-  p.counter = cv.take<int32_t>(kScales);
+  p.counter = cv.take<int32_t>(kScales * kMaxChunks);
+  p.tstate = cv.take<int32_t>((size_t)A * kScales);
+  p.front_save = cv.take<int32_t>((size_t)A * p.F * p.wps_stride);
+  p.ctl_save = cv.take<int32_t>((size_t)A * p.F * 16);
   if (!cv.ok) return fail(ctx, TABI_ERR_OOM, "arena too small for the per-chart arrays");
   // the rest in equal thirds: column words, their chart indices, row words
   const size_t left = (cv.cap - cv.used) / sizeof(uint32_t);
@@ -421,7 +431,7 @@ tabi_status batch_launch(tabi_ctx *ctx, const tabi_params *params, tabi_request 
   for (int i = 0; i < A; ++i) want = std::max(want, rowloop_smem_wanted(desc[i].W, p.g));
   int smem = (int)((want + 16383) & ~(size_t)16383);
   if (smem > ctx->rowloop_dyn_max) smem = ctx->rowloop_dyn_max;
-  Launch L{ctx->sms, smem, tn.threads == 512 ? 512 : 1024, 1};
+  Launch L{ctx->sms, smem, tn.threads == 512 ? 512 : 1024, 1, p.Q};
   if (L.rowloop_threads == 512 && tn.ctas == 2) {
     // two CTAs per multiprocessor if both fit its shared memory
     const int two = (ctx->smem_per_sm - 2 * (ctx->smem_reserved + rowloop_static_smem())) / 2 & ~255;
@@ -430,7 +440,7 @@ tabi_status batch_launch(tabi_ctx *ctx, const tabi_params *params, tabi_request 
       L.rowloop_ctas = 2;
     }
   }
-  if (used) *used = Tuning{tn.F, tn.items, L.rowloop_threads, L.rowloop_ctas};
+  if (used) *used = Tuning{tn.F, tn.items, L.rowloop_threads, L.rowloop_ctas, p.Q};
   if (ctx->timing) {
     StageMarks mk{ctx, st};
     enqueue(dpack, L, p.F, st, &mk);
@@ -715,6 +725,12 @@ tabi_status tabi_autotune(tabi_ctx *ctx, const tabi_params *params, tabi_request
     const tabi_status s = trial(t);
     if (s != TABI_OK) return s;
   }
+  {  // the other chunking: all charts at once, or lazily in four chunks
+    Tuning t = best;
+    t.Q = best.Q == 1 ? 4 : 1;
+    const tabi_status s = trial(t);
+    if (s != TABI_OK) return s;
+  }
   {  // leave the requests with the chosen shape's results
     float ms = 0.f;
     const tabi_status s = run_batch_locked(ctx, params, reqs, n_reqs, stream, false, &best, &ms, nullptr);
@@ -734,6 +750,7 @@ tabi_status tabi_autotune(tabi_ctx *ctx, const tabi_params *params, tabi_request
     out->raster_warp_items = best.items;
     out->rowloop_threads = best.threads;
     out->rowloop_ctas = best.ctas;
+    out->chunks = best.Q;
     out->ms = best_ms;
   }
   return TABI_OK;

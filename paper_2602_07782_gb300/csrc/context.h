@@ -15,7 +15,7 @@ namespace tabi {
 // row-loop CTA of `smem` dynamic bytes.  Every kernel reads the batch from
 // the record at the arena's start, so the graph serves any batch.
 struct GraphEntry {
-  int F, smem, threads, ctas;
+  int F, smem, threads, ctas, Q;
   cudaGraphExec_t exec;
 };
 
@@ -26,6 +26,7 @@ struct Tuning {
   int items;    // raster warp-items per wave (sets candidates per warp)
   int threads;  // row-loop CTA: 1024 or 512 threads
   int ctas;     // row-loop CTAs per multiprocessor
+  int Q;        // chart chunks per wave (lazy evaluation; 1 = all at once)
 };
 
 struct TuneEntry {

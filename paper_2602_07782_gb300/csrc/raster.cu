@@ -68,7 +68,8 @@ __device__ __forceinline__ int32_t warp_axis(const rmath::AxisK &ak, int g, uint
 // Warp-items: (chart of an atlas still searching, run of G consecutive
 // candidates of the atlas's wave range).  G is chosen so that the wave has
 // about raster_items warp-items (a tuned launch shape).
-__global__ void __launch_bounds__(kRasterThreads, 4) raster_kernel(const Pack *__restrict__ pp, int wave, int nj) {
+__global__ void __launch_bounds__(kRasterThreads, 4) raster_kernel(const Pack *__restrict__ pp, int wave, int q,
+                                                                  int nj) {
   __shared__ rmath::AxisK axk[kRasterWarps][2];
   const Pack &p = *pp;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -81,6 +82,7 @@ __global__ void __launch_bounds__(kRasterThreads, 4) raster_kernel(const Pack *_
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int64_t N = p.N;
   const bool use_l = (p.flags & TABI_F_LAABB) != 0, use_o = (p.flags & TABI_F_OBB) != 0;
+  const bool all = q == 0 || (p.flags & TABI_F_EVAL_ALL);  // later chunks: running candidates only
   const int g = p.g;
   rmath::AxisK &a0 = axk[wib][0], &a1 = axk[wib][1];
   for (int64_t it = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; it < items; it += nwarps) {
@@ -116,17 +118,18 @@ __global__ void __launch_bounds__(kRasterThreads, 4) raster_kernel(const Pack *_
         rmath::corner_advance(cq);
       }
       __syncwarp();
-      const int64_t js = (int64_t)j * N + s;
-      const int32_t cstart = p.colstart[js];
-      const int64_t cbase = p.abase[region(at, j, 0)], rbase = p.abase[region(at, j, 1)];
-      const int32_t maxbot = warp_axis(a0, g, p.colpool + cbase + cstart);
-      {  // each column word's chart, so a staged run of words knows its owners
-        int32_t *own = p.colown + cbase + cstart;
-        for (int c = lane; c < a0.len + 2 * g; c += 32) own[c] = s - cb;
+      if (all || (p.tstate[at * kScales + j] == 0 && *(volatile int32_t *)(p.found + at) < j)) {
+        const int64_t js = (int64_t)j * N + s;
+        const int32_t cstart = p.colstart[js];
+        const int64_t cbase = p.abase[region(at, j, 0)], rbase = p.abase[region(at, j, 1)];
+        const int32_t maxbot = warp_axis(a0, g, p.colpool + cbase + cstart);
+        {  // each column word's chart, so a staged run of words knows its owners
+          int32_t *own = p.colown + cbase + cstart;
+          for (int c = lane; c < a0.len + 2 * g; c += 32) own[c] = s - cb;
+        }
+        warp_axis(a1, g, p.pool + rbase + p.rowstart[js]);
+        if (lane == 0) p.meta[js * 4 + 3] = maxbot;  // w', h' and the column start come from the layout
       }
-      warp_axis(a1, g, p.pool + rbase + p.rowstart[js]);
-      if (lane == 0)
-        *reinterpret_cast<int4 *>(p.meta + js * 4) = make_int4(a0.len + 2 * g, a1.len + 2 * g, cstart, maxbot);
       __syncwarp();
     }
   }
@@ -135,8 +138,9 @@ __global__ void __launch_bounds__(kRasterThreads, 4) raster_kernel(const Pack *_
 // Pool layouts.  For each (atlas, candidate): the padded column count
 // w'(k) = ceil(Wq k / 2^18) + 2g and row count h'(k) of every chart,
 // exclusive-scanned in sorted order, so any run of consecutive charts has
-// its columns in one contiguous range.  One CTA per (atlas, candidate);
-// each thread sums a run of consecutive charts, then a block scan.
+// its columns in one contiguous range; the sizes and column starts also go
+// to the meta record.  One CTA per (atlas, candidate); each thread sums a
+// run of consecutive charts, then a block scan.
 // Exclusive block scan of the pair (x, y); every thread also gets the
 // totals.  part: [66] shared; the caller passes a barrier before the next
 // call reuses it.
@@ -189,12 +193,18 @@ __global__ void __launch_bounds__(1024) layout_kernel(const Pack *__restrict__ p
     }
     int64_t tx = 0, ty = 0;
     block_scan2(sc, sr, tx, ty, part);
+    const bool meta = j <= p.jtop[at];  // candidates the search may evaluate
     for (int s = s0; s < s1; ++s) {
       const int64_t js = (int64_t)j * N + cb + s;
+      const int32_t wp = (int32_t)(((p.wq[cb + s] * k + kFix - 1) >> 18) + g2);
+      const int32_t hp = (int32_t)(((p.hq[cb + s] * k + kFix - 1) >> 18) + g2);
       p.colstart[js] = (int32_t)sc;
       p.rowstart[js] = (int32_t)sr;
-      sc += ((p.wq[cb + s] * k + kFix - 1) >> 18) + g2;
-      sr += ((p.hq[cb + s] * k + kFix - 1) >> 18) + g2;
+      // w', h' and the column start of every chart are known before any
+      // envelope is drawn (the row loop folds rows of charts not yet drawn)
+      if (meta) *reinterpret_cast<int4 *>(p.meta + js * 4) = make_int4(wp, hp, (int32_t)sc, 0);
+      sc += wp;
+      sr += hp;
     }
     if (tid == 0) {
       // regions are whole 16-byte segments, so staged int4 loads stay aligned
@@ -249,8 +259,8 @@ __global__ void __launch_bounds__(1024) bases_kernel(const Pack *__restrict__ pp
 
 // Wave plan: the atlases still searching (no success yet, no error, and
 // candidates left for this wave), in batch order, and a flat list of their
-// charts.
-__global__ void __launch_bounds__(1024) plan_kernel(const Pack *__restrict__ pp, int wave) {
+// charts in chunk q.
+__global__ void __launch_bounds__(1024) plan_kernel(const Pack *__restrict__ pp, int wave, int q) {
   __shared__ int64_t part[66];
   __shared__ int64_t carry[2];
   const Pack &p = *pp;
@@ -259,9 +269,15 @@ __global__ void __launch_bounds__(1024) plan_kernel(const Pack *__restrict__ pp,
   __syncthreads();
   for (int base = 0; base < p.A; base += 1024) {
     const int at = base + tid;
-    const bool live = at < p.A && *(volatile int32_t *)(p.found + at) < 0 &&
-                      *(volatile uint32_t *)(p.err + at) == 0 && p.jtop[at] - wave * p.F >= 0;
-    int64_t ea = live ? 1 : 0, ec = live ? p.atl[at].n : 0, tx = 0, ty = 0;
+    // a success in an earlier wave ends the atlas's search; within this
+    // wave only the candidates above the success still matter
+    const int top = at < p.A ? p.jtop[at] - wave * p.F : -1;
+    const int fnd = at < p.A ? *(volatile int32_t *)(p.found + at) : 0;
+    const bool live = at < p.A && *(volatile uint32_t *)(p.err + at) == 0 && top >= 0 &&
+                      (fnd < 0 || (q > 0 && fnd < top));
+    const int n = live ? p.atl[at].n : 0;
+    int64_t ea = live ? 1 : 0, ec = live ? chunk_end(n, q, p.Q) - (q ? chunk_end(n, q - 1, p.Q) : 0) : 0;
+    int64_t tx = 0, ty = 0;
     block_scan2(ea, ec, tx, ty, part);
     if (live) {
       p.act_atl[carry[0] + ea] = at;
@@ -274,17 +290,18 @@ __global__ void __launch_bounds__(1024) plan_kernel(const Pack *__restrict__ pp,
   if (tid == 0) {
     p.act_info[0] = (int32_t)carry[0];
     p.act_info[1] = (int32_t)carry[1];
-    p.counter[wave] = 0;
+    p.counter[wave * kMaxChunks + q] = 0;
   }
 }
 
-__global__ void __launch_bounds__(256) plan_fill_kernel(const Pack *__restrict__ pp) {
+__global__ void __launch_bounds__(256) plan_fill_kernel(const Pack *__restrict__ pp, int q) {
   const Pack &p = *pp;
   const int na = p.act_info[0];
   for (int i = blockIdx.x; i < na; i += gridDim.x) {
     const int at = p.act_atl[i], pre = p.act_pre[i];
     const int n = p.atl[at].n, cb = p.atl[at].cb;
-    for (int t = threadIdx.x; t < n; t += blockDim.x) p.act_chart[pre + t] = cb + t;
+    const int c0 = q ? chunk_end(n, q - 1, p.Q) : 0, c1 = chunk_end(n, q, p.Q);
+    for (int t = threadIdx.x; t < c1 - c0; t += blockDim.x) p.act_chart[pre + t] = cb + c0 + t;
   }
 }
 
@@ -307,24 +324,32 @@ __device__ __forceinline__ int32_t warp_scan_incl(int32_t v) {
 // relative to A iff every row of B stays right of all rows of A above it;
 // A may move up relative to B iff every row of A stays left of all rows of
 // B above it.
-__global__ void __launch_bounds__(256) hcompact_kernel(const Pack *__restrict__ pp, int wave, int nj) {
+// Items are the charts c of chunk q: the pair (c - 1, c) (both charts are
+// drawn by the end of the chunk), and the atlas's last chart's empty pair.
+__global__ void __launch_bounds__(256) hcompact_kernel(const Pack *__restrict__ pp, int wave, int q, int nj) {
   const Pack &p = *pp;
   const int lane = threadIdx.x & 31;
   const int64_t total = p.act_info[1];
   const int64_t items = total * nj;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int64_t N = p.N;
+  const bool all = q == 0 || (p.flags & TABI_F_EVAL_ALL);
   for (int64_t it = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; it < items; it += nwarps) {
-    const int s = p.act_chart[it % total];
-    const int at = p.catl[s];
+    const int c = p.act_chart[it % total];
+    const int at = p.catl[c];
     const WaveRange wr = wave_range(p.jtop[at], wave, nj);
     const int j = wr.hi - (int)(it / total);
     if (j < wr.lo) continue;  // this atlas has fewer candidates left than the wave
-    const int64_t ps = (int64_t)j * N + s;
-    if (s == p.atl[at].cb + p.atl[at].n - 1) {  // the atlas's last chart has no right neighbour
-      if (lane == 0) { p.dnext[ps] = 0; p.pflags[ps] = 0; }
-      continue;
+    if (!all && (p.tstate[at * kScales + j] || *(volatile int32_t *)(p.found + at) > j))
+      continue;  // the candidate has finished, or a larger one has succeeded
+    const int cb = p.atl[at].cb;
+    if (c == cb + p.atl[at].n - 1 && lane == 0) {  // no right neighbour
+      p.dnext[(int64_t)j * N + c] = 0;
+      p.pflags[(int64_t)j * N + c] = 0;
     }
+    if (c == cb) continue;
+    const int s = c - 1;
+    const int64_t ps = (int64_t)j * N + s;
     const int32_t *ma = p.meta + ps * 4, *mb = ma + 4;
     const int32_t wA = ma[0], hA = ma[1], hB = mb[1];
     const uint32_t *pool = p.pool + p.abase[region(at, j, 1)];
@@ -376,17 +401,17 @@ void launch_layout(const Pack *dp, const Launch &L, cudaStream_t st) {
   bases_kernel<<<kScales, 1024, 0, st>>>(dp);
 }
 
-void launch_plan(const Pack *dp, const Launch &L, int wave, cudaStream_t st) {
-  plan_kernel<<<1, 1024, 0, st>>>(dp, wave);
-  plan_fill_kernel<<<L.sms * 2, 256, 0, st>>>(dp);
+void launch_plan(const Pack *dp, const Launch &L, int wave, int q, cudaStream_t st) {
+  plan_kernel<<<1, 1024, 0, st>>>(dp, wave, q);
+  plan_fill_kernel<<<L.sms * 2, 256, 0, st>>>(dp, q);
 }
 
-void launch_raster(const Pack *dp, const Launch &L, int wave, int F, cudaStream_t st) {
-  raster_kernel<<<L.sms * 16, kRasterThreads, 0, st>>>(dp, wave, F);
+void launch_raster(const Pack *dp, const Launch &L, int wave, int q, int F, cudaStream_t st) {
+  raster_kernel<<<L.sms * 16, kRasterThreads, 0, st>>>(dp, wave, q, F);
 }
 
-void launch_hcompact(const Pack *dp, const Launch &L, int wave, int F, cudaStream_t st) {
-  hcompact_kernel<<<L.sms * 16, 256, 0, st>>>(dp, wave, F);
+void launch_hcompact(const Pack *dp, const Launch &L, int wave, int q, int F, cudaStream_t st) {
+  hcompact_kernel<<<L.sms * 16, 256, 0, st>>>(dp, wave, q, F);
 }
 
 }  // namespace tabi

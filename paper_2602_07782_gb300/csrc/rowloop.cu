@@ -3,6 +3,15 @@
 // persistent, one CTA per multiprocessor; each CTA takes (atlas, candidate)
 // tasks of the current wave from a device counter.
 //
+// Lazy evaluation: a wave draws the envelopes chunk by chunk of the sorted
+// charts (first 1/8, next 1/8, 1/4, 1/2), and after each chunk the row loop
+// of every candidate still running commits the rows it can decide with the
+// charts drawn so far, then parks its frontline and row state until the
+// next chunk.  A candidate that fails (most candidates above the answer
+// fail after a fraction of their charts) gets no further envelopes.  A row
+// is decided only if the first chart that does not fit in any fold is drawn,
+// so every decision is the one the whole-atlas loop would make.
+//
 // Shared memory holds the committed frontline (one int per padded atlas
 // column) and the per-row working set.  A row proceeds in barrier-separated
 // phases:
@@ -119,7 +128,8 @@ __host__ __device__ __forceinline__ int rowloop_maxrow(int W, int g) {
 // succeeded (unless every candidate is to be evaluated).
 // NT threads per CTA (1024: one CTA per multiprocessor; 512: two).
 template <int NT>
-__global__ void __launch_bounds__(NT) rowloop_kernel(const Pack *__restrict__ pp, int wave, int nj, int smem_words) {
+__global__ void __launch_bounds__(NT) rowloop_kernel(const Pack *__restrict__ pp, int wave, int q, int nj,
+                                                     int smem_words) {
   constexpr int kNT = NT, kNW = NT / 32;
   const Pack &p = *pp;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -134,13 +144,19 @@ __global__ void __launch_bounds__(NT) rowloop_kernel(const Pack *__restrict__ pp
 
   while (true) {
     if (tid == 0) {
-      const int t = atomicAdd(p.counter + wave, 1);
+      const int t = atomicAdd(p.counter + wave * kMaxChunks + q, 1);
       int at = -1, j = 0, skip = 1;
       if (t < *(volatile int32_t *)p.act_info * nj) {
         at = p.act_atl[t / nj];
         const WaveRange wr = wave_range(p.jtop[at], wave, nj);
         j = wr.hi - t % nj;
-        skip = j < wr.lo || (!eval_all && *(volatile int32_t *)(p.found + at) > j);
+        skip = j < wr.lo || (q > 0 && p.tstate[at * kScales + j] != 0);  // outside the wave, or finished
+        if (!skip && !eval_all && *(volatile int32_t *)(p.found + at) > j) {
+          // a larger candidate has succeeded: this one is moot
+          skip = 1;
+          if (q > 0) p.scale_out[at * kScales + j].evaluated = 2;  // it ran in an earlier chunk
+          p.tstate[at * kScales + j] = 1;                         // no later chunk runs it
+        }
         // the host sizes the CTA for the widest atlas; never overrun it
         const int W = p.atl[at].W;
         if (!skip && smem_words < ((W + 2 * g + 3) & ~3) + 15 * rowloop_maxrow(W, g)) {
@@ -190,13 +206,29 @@ __global__ void __launch_bounds__(NT) rowloop_kernel(const Pack *__restrict__ pp
       const int32_t *hqa = p.hq + cb;
       int4 *place = p.place + js;
 
-      for (int x = tid; x < wp_pad; x += kNT) front[x] = 0;
-      if (tid == 0) {
-        ctl.row_start = 0; ctl.row = 0; ctl.committed = 0; ctl.fail = 0;
-        ctl.prev_ltr = 0; ctl.prev_maxlen = 0; ctl.knee_valid = 0;
-        ctl.knee_rows = 0; ctl.knees = 0; ctl.abort = 0;
+      // charts drawn so far (chunks 0..q); rows are decided on them only
+      const int avail = q == p.Q - 1 ? n : chunk_end(n, q, p.Q);
+      const int64_t slot = (int64_t)at * p.F + (wave_range(p.jtop[at], wave, nj).hi - j);
+      int32_t *fsave = p.front_save + slot * p.wps_stride;
+      int32_t *csave = p.ctl_save + slot * 16;
+      if (q == 0) {
+        for (int x = tid; x < wp_pad; x += kNT) front[x] = 0;
+        if (tid == 0) {
+          ctl.row_start = 0; ctl.row = 0; ctl.committed = 0; ctl.prev_ltr = 0;
+          ctl.knee_valid = 0; ctl.knee_ltr = 0; ctl.knee_l = 0; ctl.knee_r = 0;
+          ctl.knee_rows = 0; ctl.knees = 0;
+        }
+      } else {  // resume where the previous chunk stopped
+        for (int x = tid; x < wp_pad; x += kNT) front[x] = fsave[x];
+        if (tid == 0) {
+          ctl.row_start = csave[0]; ctl.row = csave[1]; ctl.committed = csave[2]; ctl.prev_ltr = csave[3];
+          ctl.knee_valid = csave[4]; ctl.knee_ltr = csave[5]; ctl.knee_l = csave[6]; ctl.knee_r = csave[7];
+          ctl.knee_rows = csave[8]; ctl.knees = csave[9];
+        }
       }
+      if (tid == 0) { ctl.fail = 0; ctl.prev_maxlen = 0; ctl.abort = 0; }
       __syncthreads();
+      bool deferred = false;
 
       while (true) {
         const int row_start = ctl.row_start, row = ctl.row;
@@ -242,14 +274,16 @@ __global__ void __launch_bounds__(NT) rowloop_kernel(const Pack *__restrict__ pp
             int32_t carry_x = 0, carry_xprev = kNeg, carry_re = kNeg, carry_wprev = kNeg;
             bool doneF = false, doneK = !knee;
             // widths and distances of four chunks are loaded together (one
-            // memory round trip per 128 charts), then scanned chunk by chunk
+            // memory round trip per 128 charts), then scanned chunk by chunk;
+            // a fold stops at the first chart not drawn yet (the row then
+            // waits for the next chunk)
             for (int g0 = 0; !(doneF && doneK); g0 += 128) {
               int32_t wq[4], dq[4];
 #pragma unroll
               for (int c = 0; c < 4; ++c) {
                 const int s = row_start + g0 + 32 * c + lane;
                 wq[c] = s < n ? meta[(int64_t)s * 4] : 0;
-                dq[c] = (hc && s < n) ? dnext[s] : 0;
+                dq[c] = (hc && s < avail) ? dnext[s] : 0;
               }
 #pragma unroll
               for (int c = 0; c < 4; ++c) {
@@ -257,7 +291,7 @@ __global__ void __launch_bounds__(NT) rowloop_kernel(const Pack *__restrict__ pp
                 const int t0 = g0 + 32 * c;
                 const int t = t0 + lane;
                 const int s = row_start + t;
-                const bool valid = s < n;
+                const bool valid = s < avail;  // undrawn charts end every fold
                 const bool room = t < maxrow;  // the last chunk may run past the row capacity
                 const int32_t w = wq[c], d = dq[c];
                 const int32_t a = hc ? w - d : w;  // x_{t+1} = x_t + a_t unless the clamp binds
@@ -351,6 +385,16 @@ __global__ void __launch_bounds__(NT) rowloop_kernel(const Pack *__restrict__ pp
           }
         }
         __syncthreads();
+        // The folds examined charts up to the first that does not fit; its
+        // position depends on the compaction distance of the pair before it.
+        // If that chart is not drawn yet the row waits for the next chunk.
+        if (avail < n) {
+          const int mx = max(max(ctl.len[0], ctl.len[1]), max(ctl.len[2], ctl.len[3]));
+          if (row_start + mx >= avail) {
+            deferred = true;
+            break;
+          }
+        }
         if (ctl.len[0] == 0) {  // a chart wider than the atlas: this scale fails
           if (tid == 0) ctl.fail = 1;
           break;
@@ -574,7 +618,15 @@ __global__ void __launch_bounds__(NT) rowloop_kernel(const Pack *__restrict__ pp
         }
       }
 
-      if (tid == 0) {
+      if (deferred) {  // keep the state for the next chunk
+        for (int x = tid; x < wp_pad; x += kNT) fsave[x] = front[x];
+        if (tid == 0) {
+          csave[0] = ctl.row_start; csave[1] = ctl.row; csave[2] = ctl.committed; csave[3] = ctl.prev_ltr;
+          csave[4] = ctl.knee_valid; csave[5] = ctl.knee_ltr; csave[6] = ctl.knee_l; csave[7] = ctl.knee_r;
+          csave[8] = ctl.knee_rows; csave[9] = ctl.knees;
+          p.tstate[at * kScales + j] = 0;
+        }
+      } else if (tid == 0) {
         const int ok = !ctl.fail && ctl.row_start >= n;
         so->success = ok;
         so->rows = ctl.row;
@@ -583,6 +635,7 @@ __global__ void __launch_bounds__(NT) rowloop_kernel(const Pack *__restrict__ pp
         so->score = ctl.committed;
         so->placed = ctl.row_start;
         so->evaluated = ctl.fail == 2 ? 2 : 1;
+        p.tstate[at * kScales + j] = 1;
         if (ok) atomicMax(p.found + at, j);
       }
     }  // task not skipped
@@ -622,12 +675,12 @@ cudaError_t rowloop_prepare(int smem) {
   return e;
 }
 
-void launch_rowloop(const Pack *dp, const Launch &L, int wave, int F, cudaStream_t st) {
+void launch_rowloop(const Pack *dp, const Launch &L, int wave, int q, int F, cudaStream_t st) {
   // persistent: as many CTAs as fit on the multiprocessors at once
   if (L.rowloop_threads == 512)
-    rowloop_kernel<512><<<L.sms * L.rowloop_ctas, 512, L.rowloop_smem, st>>>(dp, wave, F, L.rowloop_smem / 4);
+    rowloop_kernel<512><<<L.sms * L.rowloop_ctas, 512, L.rowloop_smem, st>>>(dp, wave, q, F, L.rowloop_smem / 4);
   else
-    rowloop_kernel<1024><<<L.sms, 1024, L.rowloop_smem, st>>>(dp, wave, F, L.rowloop_smem / 4);
+    rowloop_kernel<1024><<<L.sms, 1024, L.rowloop_smem, st>>>(dp, wave, q, F, L.rowloop_smem / 4);
 }
 
 }  // namespace tabi

@@ -66,6 +66,8 @@ struct Pack {
   int32_t F;                    // candidates per wave (scale fan-out)
   int32_t nwaves;
   int32_t raster_items;         // target warp-items of a raster wave
+  int32_t Q;                    // chart chunks per wave (1: all charts at once)
+  int32_t wps_stride;           // ints per saved frontline (widest atlas, padded)
   int32_t pad_;
   const AtlasDesc *atl;         // [A]
   int32_t *catl;                // [N] atlas of each chart
@@ -98,12 +100,33 @@ struct Pack {
   int32_t *act_atl;             // [A] those atlases, in batch order
   int32_t *act_pre;             // [A] their first position in act_chart
   int32_t *act_chart;           // [N] their charts (global sorted index)
-  int32_t *counter;             // [64] row-loop task counter of each wave
+  int32_t *counter;             // [64][kMaxChunks] row-loop task counter of each (wave, chunk)
+  int32_t *tstate;              // [A][64] row-loop task: 0 running (or not begun), 1 finished
+  int32_t *front_save;          // [A][F][wps_stride] frontline of a task between chunks
+  int32_t *ctl_save;            // [A][F][16] row state of a task between chunks
 };
 
 // Region of (atlas a, candidate j) in the column / row pools.
 __host__ __device__ __forceinline__ int64_t region(int a, int j, int which) {
   return ((int64_t)a * kScales + j) * 2 + which;
+}
+
+// Chart chunks of a wave (lazy evaluation, see the row loop): chunk q of an
+// atlas of n sorted charts ends at ceil(n e_q / 16) with
+//   Q = 1: e = 16;  Q = 2: e = 4, 16;  Q = 4: e = 2, 4, 8, 16;
+//   Q = 6: e = 2, 4, 6, 8, 12, 16;  Q = 8: e = 2, 4, ..., 16
+// (the first chunks are short: most candidates above the answer fail early).
+constexpr int kMaxChunks = 8;
+__host__ __device__ __forceinline__ int chunk_end(int n, int q, int Q) {
+  int e;
+  switch (Q) {
+    case 1: e = 16; break;
+    case 2: e = q ? 16 : 4; break;
+    case 4: e = 2 << q; break;
+    case 6: e = q < 4 ? 2 * (q + 1) : (q == 4 ? 12 : 16); break;
+    default: e = 2 * (q + 1); break;
+  }
+  return q == Q - 1 ? n : (int)(((int64_t)n * e + 15) >> 4);
 }
 
 // Candidates of atlas a in wave w: ranks r = w F .. w F + F - 1 below the
@@ -125,17 +148,18 @@ struct Launch {
   int rowloop_smem;    // dynamic shared memory of a row-loop CTA
   int rowloop_threads; // 1024 or 512 threads per row-loop CTA
   int rowloop_ctas;    // row-loop CTAs per multiprocessor (512 threads: 1 or 2)
+  int Q;               // chart chunks per wave
 };
 void launch_init(const Pack *dp, const Launch &L, cudaStream_t st);
 void launch_prep(const Pack *dp, const Launch &L, cudaStream_t st);
 void launch_sort(const Pack *dp, const Launch &L, cudaStream_t st);
 void launch_layout(const Pack *dp, const Launch &L, cudaStream_t st);
-void launch_plan(const Pack *dp, const Launch &L, int wave, cudaStream_t st);
-void launch_raster(const Pack *dp, const Launch &L, int wave, int F, cudaStream_t st);
-void launch_hcompact(const Pack *dp, const Launch &L, int wave, int F, cudaStream_t st);
+void launch_plan(const Pack *dp, const Launch &L, int wave, int q, cudaStream_t st);
+void launch_raster(const Pack *dp, const Launch &L, int wave, int q, int F, cudaStream_t st);
+void launch_hcompact(const Pack *dp, const Launch &L, int wave, int q, int F, cudaStream_t st);
 cudaError_t rowloop_prepare(int smem);  // raise the CTA's shared-memory limit (not capturable)
 int rowloop_static_smem();              // the row-loop kernel's static shared memory
-void launch_rowloop(const Pack *dp, const Launch &L, int wave, int F, cudaStream_t st);
+void launch_rowloop(const Pack *dp, const Launch &L, int wave, int q, int F, cudaStream_t st);
 void launch_select(const Pack *dp, const Launch &L, cudaStream_t st);
 size_t rowloop_smem_bytes(int W, int g);       // shared memory a row-loop CTA needs without the stage
 size_t rowloop_smem_wanted(int W, int g);      // ... with a stage of two atlas widths

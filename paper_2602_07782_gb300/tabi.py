@@ -43,7 +43,8 @@ class Request(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("scale_fanout", ctypes.c_int32), ("raster_warp_items", ctypes.c_int32),
-                ("rowloop_threads", ctypes.c_int32), ("rowloop_ctas", ctypes.c_int32), ("ms", ctypes.c_float)]
+                ("rowloop_threads", ctypes.c_int32), ("rowloop_ctas", ctypes.c_int32), ("chunks", ctypes.c_int32),
+                ("ms", ctypes.c_float)]
 
 
 class ServerConfig(ctypes.Structure):
@@ -167,11 +168,11 @@ def waves(fanout: int) -> int:
     return (N_SCALES + fanout - 1) // fanout
 
 
-def kernels_per_pack(fanout: int) -> int:
+def kernels_per_pack(fanout: int, chunks: int = 4) -> int:
     """Kernels one (batched) pack launches: init, prep, sort + gather,
-    layout + bases, per wave plan + fill, raster, compaction, row loop;
-    selection."""
-    return 7 + 5 * waves(fanout)
+    layout + bases, per wave and chart chunk plan + fill, raster,
+    compaction, row loop; selection."""
+    return 7 + 5 * waves(fanout) * chunks
 
 
 @dataclass
