@@ -256,28 +256,47 @@ __device__ __forceinline__ void prep_chart(const Pack &p, int c) {
     r1 = min(xh, r2);
   }
 
-  // App. A OBB: 8 angles, extents of u = xC + yS, v = -xS + yC
+  // App. A OBB: 8 angles, extents of u = xC + yS, v = -xS + yC.  Lane l
+  // takes angle l % 8 over every fourth vertex from l / 8; the four lanes
+  // of an angle combine by two exchanges; then every lane picks the angle
+  // of least area / (C^2 + S^2) in angle order, exactly as a sequential
+  // scan over m would (ties to the smaller m).
   int64_t bu0 = 0, bu1 = 0, bv0 = 0, bv1 = 0;
   int best = 0;
-  __int128 best_area = 0, best_n = 1;
-  for (int m = 0; m < kAngles; ++m) {
-    const int64_t C = kObbCos[m], S = kObbSin[m];
+  {
+    const int am = lane & 7;
+    const int64_t C = kObbCos[am], S = kObbSin[am];
     int64_t u0 = kI64Max, u1 = kI64Min, v0 = kI64Max, v1 = kI64Min;
-    for (int i = lane; i < nv; i += 32) {
+    for (int i = lane >> 3; i < nv; i += 4) {
       int64_t x, y;
       xf.apply(v[2 * i], v[2 * i + 1], x, y);
       const int64_t uu = x * C + y * S, vv = -x * S + y * C;
       u0 = min(u0, uu); u1 = max(u1, uu);
       v0 = min(v0, vv); v1 = max(v1, vv);
     }
-    u0 = warp_min(u0); u1 = warp_max(u1);
-    v0 = warp_min(v0); v1 = warp_max(v1);
-    const __int128 area = (__int128)(u1 - u0) * (v1 - v0);
-    const __int128 nrm = (__int128)(C * C + S * S);
-    if (m == 0 || area * best_n < best_area * nrm) {
-      best = m; best_area = area; best_n = nrm;
-      bu0 = u0; bu1 = u1; bv0 = v0; bv1 = v1;
+#pragma unroll
+    for (int o = 8; o < 32; o <<= 1) {
+      u0 = min(u0, (int64_t)__shfl_xor_sync(0xffffffffu, u0, o));
+      u1 = max(u1, (int64_t)__shfl_xor_sync(0xffffffffu, u1, o));
+      v0 = min(v0, (int64_t)__shfl_xor_sync(0xffffffffu, v0, o));
+      v1 = max(v1, (int64_t)__shfl_xor_sync(0xffffffffu, v1, o));
     }
+    const int64_t du = u1 - u0, dv = v1 - v0;
+    __int128 best_area = 0, best_n = 1;
+#pragma unroll
+    for (int m = 0; m < kAngles; ++m) {
+      const int64_t dum = __shfl_sync(0xffffffffu, du, m), dvm = __shfl_sync(0xffffffffu, dv, m);
+      const int64_t Cm = kObbCos[m], Sm = kObbSin[m];
+      const __int128 area = (__int128)dum * dvm;
+      const __int128 nrm = (__int128)(Cm * Cm + Sm * Sm);
+      if (m == 0 || area * best_n < best_area * nrm) {
+        best = m; best_area = area; best_n = nrm;
+      }
+    }
+    bu0 = __shfl_sync(0xffffffffu, u0, best);
+    bu1 = __shfl_sync(0xffffffffu, u1, best);
+    bv0 = __shfl_sync(0xffffffffu, v0, best);
+    bv1 = __shfl_sync(0xffffffffu, v1, best);
   }
 
   // write the records
@@ -305,7 +324,7 @@ __device__ __forceinline__ void prep_chart(const Pack &p, int c) {
 }
 
 // one warp per chart, grid-stride over the batch's charts
-__global__ void __launch_bounds__(256) prep_kernel(const Pack *__restrict__ pp) {
+__global__ void __launch_bounds__(256, 2) prep_kernel(const Pack *__restrict__ pp) {
   const Pack &p = *pp;
   const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; c < p.N; c += warps)
