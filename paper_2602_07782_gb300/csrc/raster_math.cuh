@@ -16,8 +16,10 @@
 // floor((floor(A / F) - c b) / d), because adding the remainder (a fraction
 // in [0, 1)) to an integer numerator never changes a floor by a positive
 // integer d.  All such numerators fit 32 bits (|A|/F < 2^28, c b < 2^27), so
-// the per-scanline work is 32-bit; only a scanline clipped by the chart's
-// end (X = ext * k, not a multiple of F) uses the 64-bit form.
+// the per-scanline work is 32-bit; a scanline clipped by the chart's end
+// (X = ext * k, not a multiple of F) forms its numerator in 64 bits once per
+// candidate and shifts it down first (floor(N / (d F)) = floor(floor(N / F)
+// / d)).
 // Lower is convex and upper concave in X, so over [a, b] each reaches its
 // extreme at the box corner when the corner lies in [a, b], else at the
 // nearer end; the corner's position is kept as floor/ceil(pos / N),
@@ -65,6 +67,7 @@ struct AxisK {
   // corner (the bound's extreme over them is at their start)
   int32_t lo_c0, lo_c1, lo_f, hi_c0, hi_c1, hi_f;
   int32_t clip_c;                      // the scanline cut by the chart's end (-1: none)
+  int32_t cl_n1, cl_n2, cu_n1, cu_n2;  // shifted numerators at X = end (lower, upper)
   int64_t end;                         // ext * k
   int64_t A1, A2, B1, B2;              // 64-bit form for the clipped scanline
 };
@@ -124,6 +127,11 @@ TABI_HD void setup_obb_base(AxisK &ak, int axis, int64_t Wq, int64_t Hq, int64_t
   ak.r2 = 1.0f / (float)ak.d2;
   ak.ah1 = (int32_t)(ak.A1 >> 18); ak.ah2 = (int32_t)(ak.A2 >> 18);
   ak.bh1 = (int32_t)(ak.B1 >> 18); ak.bh2 = (int32_t)(ak.B2 >> 18);
+  // at X = end: floor(N / (d F)) = floor(floor(N / F) / d), |N| < 2^47
+  ak.cl_n1 = (int32_t)((ak.A1 - ak.end * ak.b1) >> 18);
+  ak.cl_n2 = (int32_t)((ak.A2 + ak.end * ak.b2) >> 18);
+  ak.cu_n1 = (int32_t)((ak.B1 + ak.end * ak.b1) >> 18);
+  ak.cu_n2 = (int32_t)((ak.B2 - ak.end * ak.b2) >> 18);
 }
 
 // The eight corner quantities (item = axis * 4 + {0: lower value, 1: upper
@@ -189,20 +197,18 @@ TABI_HD void corner_store(const CornerQ &cq, int item, AxisK &ak, int64_t end) {
   }
 }
 
-// Lower / upper OBB bound at X = q F (fast) or X = end (clipped, 64-bit).
+// Lower / upper OBB bound at X = q F or, for the scanline cut by the
+// chart's end, X = end (the precomputed shifted numerators; both cases take
+// the 32-bit division, the shifted numerators being below 2^29).
 TABI_HD int32_t obb_lower_at(const AxisK &ak, int32_t q, bool clipped) {
-  if (!clipped)
-    return imax32(fdiv32(ak.ah1 - q * ak.b1, ak.d1, ak.r1), fdiv32(ak.ah2 + q * ak.b2, ak.d2, ak.r2));
-  const int64_t X = ak.end;
-  return (int32_t)imax64(fdiv64(ak.A1 - X * ak.b1, (int64_t)ak.d1 * kF),
-                         fdiv64(ak.A2 + X * ak.b2, (int64_t)ak.d2 * kF));
+  const int32_t n1 = clipped ? ak.cl_n1 : ak.ah1 - q * ak.b1;
+  const int32_t n2 = clipped ? ak.cl_n2 : ak.ah2 + q * ak.b2;
+  return imax32(fdiv32(n1, ak.d1, ak.r1), fdiv32(n2, ak.d2, ak.r2));
 }
 TABI_HD int32_t obb_upper_at(const AxisK &ak, int32_t q, bool clipped) {
-  if (!clipped)
-    return imin32(-fdiv32(ak.bh1 + q * ak.b1, ak.d1, ak.r1), -fdiv32(ak.bh2 - q * ak.b2, ak.d2, ak.r2));
-  const int64_t X = ak.end;
-  return (int32_t)imin64(-fdiv64(ak.B1 + X * ak.b1, (int64_t)ak.d1 * kF),
-                         -fdiv64(ak.B2 - X * ak.b2, (int64_t)ak.d2 * kF));
+  const int32_t n1 = clipped ? ak.cu_n1 : ak.bh1 + q * ak.b1;
+  const int32_t n2 = clipped ? ak.cu_n2 : ak.bh2 - q * ak.b2;
+  return imin32(-fdiv32(n1, ak.d1, ak.r1), -fdiv32(n2, ak.d2, ak.r2));
 }
 
 // Raw bounds of scanline c (0 <= c < len): [lo, hi) with hi > lo, given
@@ -215,14 +221,15 @@ TABI_HD void scanline_from(const AxisK &ak, int32_t c, int32_t pl, int32_t ph, i
     hi = imin32(hi, ph);
   }
   if (ak.use_o) {
+    // without branches (the lanes of a chunk straddle the corners): the
+    // extreme over the scanline is at its start if the corner lies before
+    // it, else at its end (X = end if cut); the corner value if inside
     const bool clip = c == ak.clip_c;
-    int32_t tl, th;
-    if (ak.lo_c0 <= c && c <= ak.lo_c1) tl = ak.corner_lo;
-    else if (c > ak.lo_f) tl = obb_lower_at(ak, c, false);
-    else tl = obb_lower_at(ak, c + 1, clip);
-    if (ak.hi_c0 <= c && c <= ak.hi_c1) th = ak.corner_hi;
-    else if (c > ak.hi_f) th = obb_upper_at(ak, c, false);
-    else th = obb_upper_at(ak, c + 1, clip);
+    const bool past_l = c > ak.lo_f, past_h = c > ak.hi_f;
+    int32_t tl = obb_lower_at(ak, past_l ? c : c + 1, !past_l && clip);
+    int32_t th = obb_upper_at(ak, past_h ? c : c + 1, !past_h && clip);
+    tl = (ak.lo_c0 <= c && c <= ak.lo_c1) ? ak.corner_lo : tl;
+    th = (ak.hi_c0 <= c && c <= ak.hi_c1) ? ak.corner_hi : th;
     lo = imax32(lo, tl);
     hi = imin32(hi, th);
   }
