@@ -77,6 +77,16 @@ TABI_HD int64_t fdiv64(int64_t a, int64_t b) {  // floor, b > 0
   if ((a % b) != 0 && a < 0) --q;
   return q;
 }
+// floor(a / d) for d > 0, |a| < 2^62, |a / d| < 2^40: the double quotient
+// is within 2^-11 of the true one, so its floor is off by at most one and
+// the exact remainder a - q d fixes it.
+TABI_HD int64_t fdiv64_est(int64_t a, int64_t d) {
+  int64_t q = (int64_t)floor((double)a / (double)d);
+  const int64_t r = a - q * d;
+  if (r < 0) --q;
+  else if (r >= d) ++q;
+  return q;
+}
 TABI_HD int64_t imin64(int64_t a, int64_t b) { return a < b ? a : b; }
 TABI_HD int64_t imax64(int64_t a, int64_t b) { return a > b ? a : b; }
 TABI_HD int32_t imin32(int32_t a, int32_t b) { return a < b ? a : b; }
@@ -105,8 +115,8 @@ TABI_HD void setup_piece(AxisK &ak, int i, int64_t ext, int64_t k, int32_t lo_q8
 
 // OBB line terms and scanline counts of one axis at scale k.
 TABI_HD void setup_obb_base(AxisK &ak, int axis, int64_t Wq, int64_t Hq, int64_t k, int m, int64_t C,
-                            int64_t S, int64_t u0, int64_t u1, int64_t v0, int64_t v1, bool use_l,
-                            bool use_o) {
+                            int64_t S, float rC, float rS, int64_t u0, int64_t u1, int64_t v0, int64_t v1,
+                            bool use_l, bool use_o) {
   const int64_t w = (Wq * k + kF - 1) >> 18, h = (Hq * k + kF - 1) >> 18;
   ak.len = (int32_t)(axis == 0 ? w : h);
   ak.len_other = (int32_t)(axis == 0 ? h : w);
@@ -123,8 +133,8 @@ TABI_HD void setup_obb_base(AxisK &ak, int axis, int64_t Wq, int64_t Hq, int64_t
     ak.A1 = U0; ak.A2 = -V1; ak.B1 = -U1; ak.B2 = V0;
     ak.b1 = (int32_t)S; ak.d1 = (int32_t)C; ak.b2 = (int32_t)C; ak.d2 = (int32_t)S;
   }
-  ak.r1 = 1.0f / (float)ak.d1;
-  ak.r2 = 1.0f / (float)ak.d2;
+  ak.r1 = axis == 0 ? rS : rC;  // reciprocal estimates of d1, d2
+  ak.r2 = axis == 0 ? rC : rS;
   ak.ah1 = (int32_t)(ak.A1 >> 18); ak.ah2 = (int32_t)(ak.A2 >> 18);
   ak.bh1 = (int32_t)(ak.B1 >> 18); ak.bh2 = (int32_t)(ak.B2 >> 18);
   // at X = end: floor(N / (d F)) = floor(floor(N / F) / d), |N| < 2^47
@@ -157,9 +167,10 @@ TABI_HD void corner_init(CornerQ &cq, int item, int64_t k0, int64_t step, int64_
   }
   cq.num = num;
   cq.D = kind < 2 ? N * kF : N;
-  cq.q = fdiv64(k0 * num, cq.D);
+  // |num| < 2^51, k0 <= 1024, D >= N > 2^23: the quotients are below 2^38
+  cq.q = fdiv64_est(k0 * num, cq.D);
   cq.r = k0 * num - cq.q * cq.D;
-  cq.qs = fdiv64(step * num, cq.D);
+  cq.qs = fdiv64_est(step * num, cq.D);
   cq.rs = step * num - cq.qs * cq.D;
 }
 
