@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(kRasterThreads, 4) raster_kernel(const Pack *_
                            ax ? sh.rhi[i] : sh.bhi[i]);
       } else if (lane < 2 * rmath::kK + 2) {
         const int ax = lane - 2 * rmath::kK;
-        rmath::setup_obb_base(ax ? a1 : a0, ax, sh.Wq, sh.Hq, k, m, C, S, kObbRcpCos[m], kObbRcpSin[m], sh.u0,
+        rmath::setup_obb_base(ax ? a1 : a0, ax, sh.Wq, sh.Hq, k, m, C, S, kObbDivCos[m], kObbDivSin[m], sh.u0,
                               sh.u1, sh.v0, sh.v1, use_l,
                               use_o);
       } else if (corner_lane) {

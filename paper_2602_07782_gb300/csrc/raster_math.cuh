@@ -26,10 +26,10 @@
 // N = C^2 + S^2, which decides both tests exactly for integer a, b, and is
 // turned into a range of scanline indices once per candidate.
 //
-// The 32-bit floor division by d (= C or S, 3196..16384) multiplies by a
-// float reciprocal estimate and corrects the estimate with one exact
-// remainder step: for |numerator| < 2^30 the product is within 0.1 of the
-// true quotient, so the floored estimate is off by at most one.
+// The 32-bit floor division by d (= C or S, 3196..16384, fixed per angle)
+// is a multiply-high by d's magic number and a shift (division by an
+// invariant integer, see fdiv_magic), exact for the numerators here
+// (|numerator| < 2^29).
 //
 // Corner values and positions are linear in k: floor(k num / D).  A warp
 // that walks the candidates k, k+16, ... keeps (q, r) with k num = q D + r,
@@ -53,13 +53,44 @@ constexpr int kK = 10;
 constexpr int64_t kF = 1LL << 18;
 constexpr int32_t kInf = 0x3fffffff;
 
+// Division by an invariant integer d by multiplication (Granlund and
+// Montgomery, "Division by invariant integers using multiplication", 1994,
+// Thm. 4.2 with N = 31): for 2^(l-1) < d <= 2^l and M = ceil(2^(31+l) / d),
+// floor(x / d) = floor(M x / 2^(31+l)) for every 0 <= x < 2^31, and
+// M < 2^32.  A numerator |a| < 2^29 is shifted into that range by adding
+// B d with B = ceil(2^29 / d), and B is taken off the quotient.
+struct Magic {
+  uint32_t M;
+  int32_t shift;  // l - 1 (the multiply-high already drops 32 bits)
+  int32_t bd;     // B d
+  int32_t B;
+};
+constexpr Magic magic_div(uint32_t d) {
+  int l = 0;
+  while ((1u << l) < d) ++l;
+  const uint64_t M = ((1ull << (31 + l)) + d - 1) / d;
+  const uint32_t B = ((1u << 29) + d - 1) / d;
+  return Magic{(uint32_t)M, l - 1, (int32_t)(B * d), (int32_t)B};
+}
+TABI_HD uint32_t umulhi32(uint32_t a, uint32_t b) {
+#if defined(__CUDA_ARCH__)
+  return __umulhi(a, b);
+#else
+  return (uint32_t)(((uint64_t)a * b) >> 32);
+#endif
+}
+// floor(a / d) for |a| < 2^29 and the magic numbers of d (d >= 2)
+TABI_HD int32_t fdiv_magic(int32_t a, const Magic &mg) {
+  return (int32_t)(umulhi32(mg.M, (uint32_t)(a + mg.bd)) >> mg.shift) - mg.B;
+}
+
 struct AxisK {
   // local-AABB pieces: scanline range plo | phi << 16, scaled bounds lo | hi << 16
   uint32_t prange[kK], pval[kK];
   // OBB, fast path (X = multiple of F)
   int32_t ah1, ah2, bh1, bh2;   // floor(A1/F), floor(A2/F), floor(B1/F), floor(B2/F)
   int32_t b1, b2, d1, d2;
-  float r1, r2;                 // float reciprocal estimates of d1, d2
+  Magic q1, q2;                 // exact division by d1, d2 (multiply-high)
   int32_t corner_lo, corner_hi; // extreme values at the corners
   int32_t len, len_other, use_l, use_o;
   // corner tests in scanline units (see corner_store): the corner value
@@ -115,8 +146,8 @@ TABI_HD void setup_piece(AxisK &ak, int i, int64_t ext, int64_t k, int32_t lo_q8
 
 // OBB line terms and scanline counts of one axis at scale k.
 TABI_HD void setup_obb_base(AxisK &ak, int axis, int64_t Wq, int64_t Hq, int64_t k, int m, int64_t C,
-                            int64_t S, float rC, float rS, int64_t u0, int64_t u1, int64_t v0, int64_t v1,
-                            bool use_l, bool use_o) {
+                            int64_t S, const Magic &qC, const Magic &qS, int64_t u0, int64_t u1, int64_t v0,
+                            int64_t v1, bool use_l, bool use_o) {
   const int64_t w = (Wq * k + kF - 1) >> 18, h = (Hq * k + kF - 1) >> 18;
   ak.len = (int32_t)(axis == 0 ? w : h);
   ak.len_other = (int32_t)(axis == 0 ? h : w);
@@ -133,8 +164,8 @@ TABI_HD void setup_obb_base(AxisK &ak, int axis, int64_t Wq, int64_t Hq, int64_t
     ak.A1 = U0; ak.A2 = -V1; ak.B1 = -U1; ak.B2 = V0;
     ak.b1 = (int32_t)S; ak.d1 = (int32_t)C; ak.b2 = (int32_t)C; ak.d2 = (int32_t)S;
   }
-  ak.r1 = axis == 0 ? rS : rC;  // reciprocal estimates of d1, d2
-  ak.r2 = axis == 0 ? rC : rS;
+  ak.q1 = axis == 0 ? qS : qC;  // division by d1, d2
+  ak.q2 = axis == 0 ? qC : qS;
   ak.ah1 = (int32_t)(ak.A1 >> 18); ak.ah2 = (int32_t)(ak.A2 >> 18);
   ak.bh1 = (int32_t)(ak.B1 >> 18); ak.bh2 = (int32_t)(ak.B2 >> 18);
   // at X = end: floor(N / (d F)) = floor(floor(N / F) / d), |N| < 2^47
@@ -214,12 +245,12 @@ TABI_HD void corner_store(const CornerQ &cq, int item, AxisK &ak, int64_t end) {
 TABI_HD int32_t obb_lower_at(const AxisK &ak, int32_t q, bool clipped) {
   const int32_t n1 = clipped ? ak.cl_n1 : ak.ah1 - q * ak.b1;
   const int32_t n2 = clipped ? ak.cl_n2 : ak.ah2 + q * ak.b2;
-  return imax32(fdiv32(n1, ak.d1, ak.r1), fdiv32(n2, ak.d2, ak.r2));
+  return imax32(fdiv_magic(n1, ak.q1), fdiv_magic(n2, ak.q2));
 }
 TABI_HD int32_t obb_upper_at(const AxisK &ak, int32_t q, bool clipped) {
   const int32_t n1 = clipped ? ak.cu_n1 : ak.bh1 + q * ak.b1;
   const int32_t n2 = clipped ? ak.cu_n2 : ak.bh2 - q * ak.b2;
-  return imin32(-fdiv32(n1, ak.d1, ak.r1), -fdiv32(n2, ak.d2, ak.r2));
+  return imin32(-fdiv_magic(n1, ak.q1), -fdiv_magic(n2, ak.q2));
 }
 
 // Raw bounds of scanline c (0 <= c < len): [lo, hi) with hi > lo, given

@@ -7,6 +7,7 @@
 #include <stdint.h>
 
 #include "../../include/tabi.h"
+#include "raster_math.cuh"
 
 namespace tabi {
 
@@ -204,12 +205,13 @@ __device__ __forceinline__ T warp_max(T v) {
 // C_m = round-half-away(2^14 * cos(m*pi/16)), S_m likewise with sin.
 static __constant__ int32_t kObbCos[kAngles] = {16384, 16069, 15137, 13623, 11585, 9102, 6270, 3196};
 static __constant__ int32_t kObbSin[kAngles] = {0, 3196, 6270, 9102, 11585, 13623, 15137, 16069};
-// Float reciprocal estimates of the table entries (the rasterizer's 32-bit
-// floor division corrects any estimate this close); sin 0 is never a
-// divisor (m = 0 has no OBB constraint).
-static __constant__ float kObbRcpCos[kAngles] = {1.0f / 16384, 1.0f / 16069, 1.0f / 15137, 1.0f / 13623,
-                                                 1.0f / 11585, 1.0f / 9102,  1.0f / 6270,  1.0f / 3196};
-static __constant__ float kObbRcpSin[kAngles] = {0.0f,         1.0f / 3196,  1.0f / 6270, 1.0f / 9102,
-                                                 1.0f / 11585, 1.0f / 13623, 1.0f / 15137, 1.0f / 16069};
+// Magic numbers for exact division by the table entries (raster_math.cuh,
+// fdiv_magic); sin 0 is never a divisor (m = 0 has no OBB constraint).
+static __constant__ rmath::Magic kObbDivCos[kAngles] = {
+    rmath::magic_div(16384), rmath::magic_div(16069), rmath::magic_div(15137), rmath::magic_div(13623),
+    rmath::magic_div(11585), rmath::magic_div(9102),  rmath::magic_div(6270),  rmath::magic_div(3196)};
+static __constant__ rmath::Magic kObbDivSin[kAngles] = {
+    rmath::magic_div(2),     rmath::magic_div(3196),  rmath::magic_div(6270),  rmath::magic_div(9102),
+    rmath::magic_div(11585), rmath::magic_div(13623), rmath::magic_div(15137), rmath::magic_div(16069)};
 
 }  // namespace tabi

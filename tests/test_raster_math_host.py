@@ -1,0 +1,81 @@
+"""Host checks of the rasterizer's integer division helpers
+(paper_2602_07782_gb300/csrc/raster_math.cuh compiled with g++): the
+multiply-high division by the OBB table's divisors and the estimated 64-bit
+floor division equal exact floor division.  The GPU parity tests check the
+envelopes they produce against the oracle."""
+from __future__ import annotations
+
+import os
+import subprocess
+import tempfile
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+PROGRAM = r"""
+#include <cstdio>
+#include <cstdint>
+#include <random>
+#include "raster_math.cuh"
+using namespace tabi::rmath;
+
+static int64_t floor_div(int64_t a, int64_t d) {
+  int64_t q = a / d;
+  if ((a % d) != 0 && a < 0) --q;
+  return q;
+}
+
+int main() {
+  const uint32_t divisors[] = {16384, 16069, 15137, 13623, 11585, 9102, 6270, 3196, 2, 3, 7, 1000, 32767};
+  std::mt19937_64 rng(12345);
+  long bad = 0, checked = 0;
+  const int32_t lim = 1 << 29;
+  for (uint32_t d : divisors) {
+    const Magic mg = magic_div(d);
+    auto check = [&](int32_t a) {
+      if (a <= -lim || a >= lim) return;
+      ++checked;
+      if (fdiv_magic(a, mg) != floor_div(a, d)) {
+        if (bad < 5) std::printf("magic d=%u a=%d got %d want %lld\n", d, a, fdiv_magic(a, mg), (long long)floor_div(a, d));
+        ++bad;
+      }
+    };
+    for (int i = 0; i < 200000; ++i) check((int32_t)(rng() % (2u * lim)) - lim);
+    // around multiples of d, across the whole range
+    for (int64_t m = -(int64_t)lim / d - 1; m <= (int64_t)lim / d + 1; m += 1 + (int64_t)(lim / d) / 4096)
+      for (int o = -2; o <= 2; ++o) check((int32_t)(m * (int64_t)d + o));
+    for (int o = 0; o < 4096; ++o) { check(-lim + 1 + o); check(lim - 1 - o); check(o); check(-o); }
+  }
+  // 64-bit estimate: quotients below 2^40, numerators below 2^62
+  for (int i = 0; i < 400000; ++i) {
+    const int64_t d = (int64_t)(rng() % ((1ull << 46) - (1ull << 23))) + (1ll << 23);
+    const int64_t a = (int64_t)(rng() % (1ull << 62)) - (1ll << 61);
+    ++checked;
+    if (fdiv64_est(a, d) != floor_div(a, d)) ++bad;
+    const int64_t q = (int64_t)(rng() % (1ull << 38)) - (1ll << 37);
+    for (int o = -1; o <= 1; ++o) {
+      const int64_t b = q * d + o;
+      if (b > -(1ll << 62) && b < (1ll << 62)) { ++checked; if (fdiv64_est(b, d) != floor_div(b, d)) ++bad; }
+    }
+  }
+  std::printf("checked %ld bad %ld\n", checked, bad);
+  return bad ? 1 : 0;
+}
+"""
+
+
+def test_division_helpers_are_exact():
+    gxx = "g++"
+    with tempfile.TemporaryDirectory() as td:
+        src = os.path.join(td, "t.cpp")
+        exe = os.path.join(td, "t")
+        with open(src, "w") as f:
+            f.write(PROGRAM)
+        inc = os.path.join(ROOT, "paper_2602_07782_gb300", "csrc")
+        r = subprocess.run([gxx, "-O2", "-std=c++17", "-I", inc, src, "-o", exe], capture_output=True, text=True)
+        if r.returncode != 0:
+            pytest.fail(r.stderr[-3000:])
+        r = subprocess.run([exe], capture_output=True, text=True, timeout=300)
+        assert r.returncode == 0, r.stdout[-2000:]
+        assert "bad 0" in r.stdout
