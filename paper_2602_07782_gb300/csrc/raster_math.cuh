@@ -44,6 +44,11 @@
 #define TABI_HD __host__ __device__ __forceinline__
 #else
 #define TABI_HD inline
+// host builds (the division tests) get CUDA's 4-int vector by hand
+struct int4 {
+  int x, y, z, w;
+};
+inline int4 make_int4(int x, int y, int z, int w) { return int4{x, y, z, w}; }
 #endif
 
 namespace tabi {
@@ -85,8 +90,10 @@ TABI_HD int32_t fdiv_magic(int32_t a, const Magic &mg) {
 }
 
 struct AxisK {
-  // local-AABB pieces: scanline range plo | phi << 16, scaled bounds lo | hi << 16
-  uint32_t prange[kK], pval[kK];
+  // local-AABB pieces: first scanline, span (last - first), scaled bounds
+  // lo, hi -- one 16-byte record each, so a scanline tests a piece with one
+  // broadcast vector load, one unsigned compare and two min/max
+  int4 piece[kK];
   // OBB, fast path (X = multiple of F)
   int32_t ah1, ah2, bh1, bh2;   // floor(A1/F), floor(A2/F), floor(B1/F), floor(B2/F)
   int32_t b1, b2, d1, d2;
@@ -136,12 +143,11 @@ TABI_HD int32_t fdiv32(int32_t a, int32_t d, float rcp) {
 // (axis 1); `lo_q8`, `hi_q8` = the refined piece bounds (tlo/bhi or llo/rhi).
 TABI_HD void setup_piece(AxisK &ak, int i, int64_t ext, int64_t k, int32_t lo_q8, int32_t hi_q8) {
   const int64_t s0 = (int64_t)i * ext / kK * k, s1 = (int64_t)(i + 1) * ext / kK * k;
-  const uint32_t plo = (uint32_t)(s0 >> 18);                // floor(s0 / F)
-  const uint32_t phi = (uint32_t)(((s1 + kF - 1) >> 18) - 1); // ceil(s1 / F) - 1
-  const uint32_t lo = (uint32_t)(((int64_t)lo_q8 * k) >> 18);
-  const uint32_t hi = (uint32_t)(((int64_t)hi_q8 * k + kF - 1) >> 18);
-  ak.prange[i] = plo | (phi << 16);
-  ak.pval[i] = lo | (hi << 16);
+  const int32_t plo = (int32_t)(s0 >> 18);                // floor(s0 / F)
+  const int32_t phi = (int32_t)(((s1 + kF - 1) >> 18) - 1); // ceil(s1 / F) - 1 (>= plo: s1 > s0)
+  const int32_t lo = (int32_t)(((int64_t)lo_q8 * k) >> 18);
+  const int32_t hi = (int32_t)(((int64_t)hi_q8 * k + kF - 1) >> 18);
+  ak.piece[i] = make_int4(plo, phi - plo, lo, hi);
 }
 
 // OBB line terms and scanline counts of one axis at scale k.
@@ -286,11 +292,10 @@ TABI_HD void scanline(const AxisK &ak, int32_t c, int32_t &lo_out, int32_t &hi_o
   int32_t pl = kInf, ph = -kInf;
 #pragma unroll
   for (int i = 0; i < kK; ++i) {
-    const uint32_t pr = ak.prange[i];
-    if ((int32_t)(pr & 0xffffu) <= c && c <= (int32_t)(pr >> 16)) {
-      const uint32_t pv = ak.pval[i];
-      pl = imin32(pl, (int32_t)(pv & 0xffffu));
-      ph = imax32(ph, (int32_t)(pv >> 16));
+    const int4 pc = ak.piece[i];
+    if ((uint32_t)(c - pc.x) <= (uint32_t)pc.y) {  // plo <= c <= plo + span
+      pl = imin32(pl, pc.z);
+      ph = imax32(ph, pc.w);
     }
   }
   scanline_from(ak, c, pl, ph, lo_out, hi_out);

@@ -590,9 +590,13 @@ __global__ void __launch_bounds__(NT) rowloop_kernel(const Pack *__restrict__ pp
           const int fB = woff[len - 1] + wps[len - 1] - slo;
           if (fB <= shi - slo) {
             for (int f = fA + tid; f < fB; f += kNT) {  // lane per staged column word
+              // the word's chart and column, from its staged owner index
+              // (checked: a wrong owner raises an error, never a stray access)
               const int t = sown[f] - row_start;
+              if ((unsigned)t >= (unsigned)len) { atomicOr(p.err + at, kErrRow); continue; }
               const int w = wps[t];
               const int i = f - (woff[t] - slo);
+              if ((unsigned)i >= (unsigned)w) { atomicOr(p.err + at, kErrRow); continue; }
               const int32_t X = dir ? hi - pos[t] - w : lo + pos[t];
               atomicMax(&front[X + (dir ? w - 1 - i : i)], y[t] + (int32_t)(stage[f] >> 16));
             }
