@@ -80,11 +80,12 @@ typedef enum tabi_status {
 #define TABI_F_ALL     15u
 /* Inspection aid, not part of the method: every candidate is evaluated and
  * its row loop runs to its end.  Without it, candidates above the area
- * bound are skipped (charts never overlap and stay inside the atlas, so a
- * candidate at which the summed polygon area exceeds the atlas area cannot
- * succeed; this holds for simple polygons, which the charts must be), and
- * a candidate is skipped or abandoned between rows once a larger one of
- * the same atlas has succeeded.  The scale and placements are the same
+ * bound are skipped (the charts' covers dilated by the gutter never overlap
+ * and stay inside the padded atlas, and a simple polygon of area A and
+ * larger side E dilated by g covers at least A + 2gE + 4g^2, so a candidate
+ * at which these areas exceed (W + 2g)(H + 2g) cannot succeed; charts must
+ * be simple polygons), and a candidate is skipped or abandoned between rows
+ * once a larger one of the same atlas has succeeded.  The scale and placements are the same
  * either way; only the per-candidate summaries of TABI_INSPECT_SCALE become
  * complete. */
 #define TABI_F_EVAL_ALL 16u

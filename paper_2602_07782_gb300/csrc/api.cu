@@ -91,6 +91,7 @@ __global__ void init_kernel(const Pack *__restrict__ pp) {
       p.found[at] = -1;
       p.err[at] = 0;
       p.area2[at] = 0;
+      p.ext_sum[at] = 0;
       p.result[at] = PackResult{0, 0, 0, -1};
     }
     const int cb = p.atl[at].cb, n = p.atl[at].n;
@@ -385,6 +386,7 @@ tabi_status batch_launch(tabi_ctx *ctx, const tabi_params *params, tabi_request 
   p.place = cv.take<int4>(kScales * n);
   p.scale_out = cv.take<ScaleOut>((size_t)A * kScales);
   p.area2 = cv.take<unsigned long long>(A);
+  p.ext_sum = cv.take<unsigned long long>(A);
   p.jtop = cv.take<int32_t>(A);
   p.found = cv.take<int32_t>(A);
   p.err = cv.take<uint32_t>(A);

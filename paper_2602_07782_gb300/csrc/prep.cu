@@ -157,7 +157,10 @@ __device__ __forceinline__ void prep_chart(const Pack &p, int c) {
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) a2 += __shfl_xor_sync(0xffffffffu, a2, o);
-    if (lane == 0) atomicAdd(p.area2 + at, (unsigned long long)(a2 < 0 ? -a2 : a2));
+    if (lane == 0) {
+      atomicAdd(p.area2 + at, (unsigned long long)(a2 < 0 ? -a2 : a2));
+      atomicAdd(p.ext_sum + at, (unsigned long long)Hq);  // Hq >= Wq after the rotation
+    }
   }
   int32_t ylo[kSlices], yhi[kSlices], xlo[kSlices], xhi[kSlices];
 
@@ -410,18 +413,26 @@ __device__ void sort_atlas(const Pack &p, int at) {
   // three passes: A->B, B->A, A->B
   for (int s = tid; s < n; s += kSortThreads) p.perm[cb + s] = cb + (int32_t)vB[s];
   if (tid == 0) {
-    // Area bound: placed charts are disjoint and inside the atlas, so a
-    // candidate k can succeed only if the summed polygon area at scale
-    // k/1024 is at most W*H, i.e. area2 * k^2 <= 2 W H 2^16 2^20 (area2 is
-    // twice the area in Q.8^2 units).  Larger candidates are skipped.
+    // Area bound: placed charts' covers, each dilated by the gutter g, are
+    // disjoint and lie in the padded atlas (W + 2g) x (H + 2g).  A connected
+    // polygon of area A and larger extent E dilated by g covers at least
+    // A + 2 g E + 4 g^2 (every line across it gains 2g).  At scale k/1024 the
+    // area is area2 k^2 / 2^37 and the extent E k / 2^18 texels (area2 =
+    // twice the area in Q.8^2, E in Q.8), so candidate k can succeed only if
+    //   area2 k^2 + 2g 2^19 k sum(E) + 4 g^2 2^37 n <= (W + 2g)(H + 2g) 2^37.
+    // Larger candidates are skipped.
     int jt = kScales - 1;
     if (!(p.flags & TABI_F_EVAL_ALL)) {
-      const unsigned __int128 lim = (unsigned __int128)((uint64_t)p.atl[at].W * (uint64_t)p.atl[at].H) << 37;
-      const unsigned __int128 s2 = p.area2[at];
+      const uint64_t g = (uint64_t)p.g;
+      const unsigned __int128 lim =
+          (unsigned __int128)(((uint64_t)p.atl[at].W + 2 * g) * ((uint64_t)p.atl[at].H + 2 * g)) << 37;
+      const unsigned __int128 s2 = p.area2[at], ex = p.ext_sum[at];
+      const unsigned __int128 fixed = (unsigned __int128)(4 * g * g * (uint64_t)n) << 37;
       jt = -1;
       for (int j = 0; j < kScales; ++j) {
         const uint64_t k = 16 * (uint64_t)(j + 1);
-        if (s2 * (k * k) <= lim) jt = j;
+        const unsigned __int128 need = s2 * (k * k) + ((ex * (2 * g * k)) << 19) + fixed;
+        if (need <= lim) jt = j;
       }
     }
     p.jtop[at] = jt;

@@ -93,6 +93,7 @@ struct Pack {
   int4 *place;                  // [64 N] x, y, row, bits
   ScaleOut *scale_out;          // [A][64]
   unsigned long long *area2;    // [A] twice the summed polygon area (Q.8^2 units)
+  unsigned long long *ext_sum;  // [A] summed larger AABB side of the charts (Q.8)
   int32_t *jtop;                // [A] largest candidate the area bound allows (-1 none)
   int32_t *found;               // [A] highest successful candidate so far (-1 none)
   uint32_t *err;                // [A]

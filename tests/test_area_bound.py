@@ -1,11 +1,12 @@
 """The area bound on the candidate scales (CPU, against the oracle).
 
-Placed charts never overlap and lie inside the atlas (Sec. 5 packs without
-overlap; the envelopes are conservative covers), so a candidate k can only
-succeed if the summed polygon area at scale k/1024 is at most W * H.  The
-GPU path skips the candidates above that bound.  These tests check, with
-the oracle, that every skipped candidate indeed fails and that the chosen
-scale is never above the bound.
+Placed charts never overlap (Sec. 5: gutters of g texels between charts;
+the envelopes are conservative covers): the covers dilated by g are
+disjoint inside the padded atlas (W + 2g) x (H + 2g), so a candidate k can
+only succeed if the charts' dilated areas at scale k/1024 sum to at most
+that.  The GPU path skips the candidates above the bound.  These tests
+check, with the oracle, that every skipped candidate indeed fails and that
+the chosen scale is never above the bound, and the dilation lemma itself.
 """
 from __future__ import annotations
 
@@ -26,14 +27,29 @@ def twice_area_q8(cs) -> int:
     return total
 
 
-def top_candidate(cs) -> int:
-    """Largest j with area2 * k^2 <= W H 2^37 (k = 16 (j + 1)); -1 if none."""
+def larger_extents_q8(cs) -> int:
+    """Summed larger AABB side of the charts (Q.8)."""
+    total = 0
+    for i in range(cs.n):
+        p = cs.polygon(i).astype(np.int64)
+        ext = p.max(axis=0) - p.min(axis=0)
+        total += int(ext.max())
+    return total
+
+
+def top_candidate(cs, gutter: int = 1) -> int:
+    """Largest j (k = 16 (j + 1)) whose dilated-area bound holds; -1 if none.
+    The covers dilated by g are disjoint inside (W + 2g) x (H + 2g), and a
+    connected polygon of area A and larger extent E dilated by g covers at
+    least A + 2 g E + 4 g^2 (texels, at scale k/1024)."""
     s2 = twice_area_q8(cs)
-    lim = cs.atlas_w * cs.atlas_h << 37
+    ext = larger_extents_q8(cs)
+    g = gutter
+    lim = ((cs.atlas_w + 2 * g) * (cs.atlas_h + 2 * g)) << 37
     jt = -1
     for j in range(64):
         k = 16 * (j + 1)
-        if s2 * k * k <= lim:
+        if s2 * k * k + ((2 * g * k * ext) << 19) + ((4 * g * g * cs.n) << 37) <= lim:
             jt = j
     return jt
 
@@ -61,9 +77,49 @@ def test_candidates_above_the_area_bound_fail(name):
 
 
 def test_area_bound_is_tight_for_exact_tiling():
-    """64 squares of 8x8 texels tile a 64x64 atlas exactly at k = 1024 with
-    no gutter; the bound allows k = 1024 and nothing less is forced."""
+    """Without a gutter the bound is the plain area bound: 64 squares of 8x8
+    texels tile a 64x64 atlas exactly at k = 1024; 65 do not fit above
+    k = 1016.  With gutter 1 a square of side 8x dilates to at least
+    64x^2 + 16x + 4 texels (x = k/1024), and 64 of them must fit 66 x 66."""
     cs = synth.rectangles([(8, 8)] * 64, 64, 64)
-    assert top_candidate(cs) == 63
+    assert top_candidate(cs, gutter=0) == 63
     cs2 = synth.rectangles([(8, 8)] * 65, 64, 64)
-    assert top_candidate(cs2) == 62  # (k/1024)^2 * 65 * 64 <= 4096  <=>  k <= 1016
+    assert top_candidate(cs2, gutter=0) == 62  # (k/1024)^2 * 65 * 64 <= 4096  <=>  k <= 1016
+    # gutter 1: 64 (64 x^2 + 16 x + 4) <= 66^2  <=>  x <= 0.8833  <=>  k <= 904.5
+    assert top_candidate(cs, gutter=1) == 55  # k = 896
+
+
+def test_dilation_lemma_on_rasterised_polygons():
+    """The dilated area of a connected polygon is at least A + 2 g E + 4 g^2:
+    checked on fine rasterisations of the workload's chart shapes."""
+    cs = synth.plain64(seed=3)
+    g = 1.0
+    for i in range(0, cs.n, 8):
+        p = cs.polygon(i).astype(np.float64) / 256.0
+        p -= p.min(axis=0)
+        w, h = p.max(axis=0)
+        step = 0.05
+        xs = np.arange(-g, w + g, step) + step / 2
+        ys = np.arange(-g, h + g, step) + step / 2
+        X, Y = np.meshgrid(xs, ys)
+        inside = _points_in_polygon(X.ravel(), Y.ravel(), p).reshape(X.shape)
+        # dilate by g with a square structuring element on the fine grid
+        r = int(round(g / step))
+        from scipy.ndimage import binary_dilation
+        dil = binary_dilation(inside, structure=np.ones((2 * r + 1, 2 * r + 1), bool))
+        area_dil = dil.sum() * step * step
+        area = 0.5 * abs(np.sum(p[:, 0] * np.roll(p[:, 1], -1) - np.roll(p[:, 0], -1) * p[:, 1]))
+        assert area_dil >= area + 2 * g * max(w, h) + 4 * g * g - 0.5  # grid error margin
+
+
+def _points_in_polygon(x, y, poly):
+    inside = np.zeros(x.shape, bool)
+    n = len(poly)
+    for a in range(n):
+        x0, y0 = poly[a]
+        x1, y1 = poly[(a + 1) % n]
+        cond = (y0 > y) != (y1 > y)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            xc = x0 + (y - y0) * (x1 - x0) / (y1 - y0)
+        inside ^= cond & (x < xc)
+    return inside
