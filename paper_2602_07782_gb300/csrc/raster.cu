@@ -102,6 +102,12 @@ __global__ void __launch_bounds__(kRasterThreads, 4) raster_kernel(const Pack *_
     if (corner_lane) rmath::corner_init(cq, lane - 24, 16 * (j0 + 1), 16, C, S, sh.u0, sh.u1, sh.v0, sh.v1);
     for (int j = j0; j < j1; ++j) {
       const int64_t k = 16 * (j + 1);
+      // a finished candidate (later chunks): nothing to draw; the corner
+      // quantities still step to the next candidate
+      if (!all && (p.tstate[at * kScales + j] != 0 || *(volatile int32_t *)(p.found + at) >= j)) {
+        if (corner_lane) rmath::corner_advance(cq);
+        continue;
+      }
       // per-(chart, scale) constants, lane-parallel: lanes 0-19 the local-AABB
       // pieces, lanes 20-21 the OBB line terms, lanes 24-31 the corners
       if (lane < 2 * rmath::kK) {
@@ -119,29 +125,21 @@ __global__ void __launch_bounds__(kRasterThreads, 4) raster_kernel(const Pack *_
         rmath::corner_advance(cq);
       }
       __syncwarp();
-      if (all || (p.tstate[at * kScales + j] == 0 && *(volatile int32_t *)(p.found + at) < j)) {
-        const int64_t js = (int64_t)j * N + s;
-        const int32_t cstart = p.colstart[js];
-        const int64_t cbase = p.abase[region(at, j, 0)], rbase = p.abase[region(at, j, 1)];
-        const int32_t maxbot = warp_axis(a0, g, p.colpool + cbase + cstart);
-        {  // each column word's chart, so a staged run of words knows its owners
-          int32_t *own = p.colown + cbase + cstart;
-          for (int c = lane; c < a0.len + 2 * g; c += 32) own[c] = s - cb;
-        }
-        warp_axis(a1, g, p.pool + rbase + p.rowstart[js]);
-        if (lane == 0) p.meta[js * 4 + 3] = maxbot;  // w', h' and the column start come from the layout
+      const int64_t js = (int64_t)j * N + s;
+      const int32_t cstart = p.colstart[js];
+      const int64_t cbase = p.abase[region(at, j, 0)], rbase = p.abase[region(at, j, 1)];
+      const int32_t maxbot = warp_axis(a0, g, p.colpool + cbase + cstart);
+      {  // each column word's chart, so a staged run of words knows its owners
+        int32_t *own = p.colown + cbase + cstart;
+        for (int c = lane; c < a0.len + 2 * g; c += 32) own[c] = s - cb;
       }
+      warp_axis(a1, g, p.pool + rbase + p.rowstart[js]);
+      if (lane == 0) p.meta[js * 4 + 3] = maxbot;  // w', h' and the column start come from the layout
       __syncwarp();
     }
   }
 }
 
-// Pool layouts.  For each (atlas, candidate): the padded column count
-// w'(k) = ceil(Wq k / 2^18) + 2g and row count h'(k) of every chart,
-// exclusive-scanned in sorted order, so any run of consecutive charts has
-// its columns in one contiguous range; the sizes and column starts also go
-// to the meta record.  One CTA per (atlas, candidate); each thread sums a
-// run of consecutive charts, then a block scan.
 // Exclusive block scan of the pair (x, y); every thread also gets the
 // totals.  part: [66] shared; the caller passes a barrier before the next
 // call reuses it.
@@ -175,6 +173,12 @@ __device__ __forceinline__ void block_scan2(int64_t &x, int64_t &y, int64_t &tx,
   ty = part[65];
 }
 
+// Pool layouts.  For each (atlas, candidate): the padded column count
+// w'(k) = ceil(Wq k / 2^18) + 2g and row count h'(k) of every chart,
+// exclusive-scanned in sorted order, so any run of consecutive charts has
+// its columns in one contiguous range; the sizes and column starts also go
+// to the meta record.  One CTA per (atlas, candidate); each thread sums a
+// run of consecutive charts, then a block scan.
 __global__ void __launch_bounds__(1024) layout_kernel(const Pack *__restrict__ pp) {
   __shared__ int64_t part[66];
   const Pack &p = *pp;
