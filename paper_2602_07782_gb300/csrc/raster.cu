@@ -278,8 +278,15 @@ __global__ void __launch_bounds__(1024) plan_kernel(const Pack *__restrict__ pp,
     // wave only the candidates above the success still matter
     const int top = at < p.A ? p.jtop[at] - wave * p.F : -1;
     const int fnd = at < p.A ? *(volatile int32_t *)(p.found + at) : 0;
-    const bool live = at < p.A && *(volatile uint32_t *)(p.err + at) == 0 && top >= 0 &&
-                      (fnd < 0 || (q > 0 && fnd < top));
+    bool live = at < p.A && *(volatile uint32_t *)(p.err + at) == 0 && top >= 0 &&
+                (fnd < 0 || (q > 0 && fnd < top));
+    if (live && q > 0 && !(p.flags & TABI_F_EVAL_ALL)) {
+      // a later chunk only for atlases with a candidate of the wave still running
+      const WaveRange wr = wave_range(p.jtop[at], wave, p.F);
+      bool running = false;
+      for (int j = max(wr.lo, fnd + 1); j <= wr.hi && !running; ++j) running = p.tstate[at * kScales + j] == 0;
+      live = running;
+    }
     const int n = live ? p.atl[at].n : 0;
     int64_t ea = live ? 1 : 0, ec = live ? chunk_end(n, q, p.Q) - (q ? chunk_end(n, q - 1, p.Q) : 0) : 0;
     int64_t tx = 0, ty = 0;
