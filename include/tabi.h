@@ -185,8 +185,10 @@ typedef struct tabi_request {
  * tabi_pack would give it alone.  HOST pointers in the requests; the
  * inputs are copied to the device on `stream`, the results back.
  * 1 <= n_reqs <= TABI_MAX_BATCH.  The launch sequence is captured once per
- * wave structure (fan-out, shared-memory class) into a CUDA graph owned by
- * the context and replayed for every later batch.  A request that fails
+ * launch shape (fan-out, chunks, shared-memory class) into a CUDA graph
+ * owned by the context and replayed for every later batch; its waves run
+ * in a device-side loop (a conditional WHILE node) that stops as soon as
+ * no atlas has a candidate left to try, so later waves cost nothing.  A request that fails
  * the host checks gets TABI_ERR_INVALID_ARG and takes no device work.
  * Returns TABI_OK when every request has its status (which may itself be
  * an error), else TABI_ERR_INVALID_ARG (bad params, n_reqs or pointers),
@@ -218,7 +220,7 @@ typedef struct tabi_tuning {
 
 /* Autotuner: packs the batch (DEVICE pointers, as tabi_pack_batch_device)
  * repeatedly under candidate launch shapes, starting from the default --
- * fan-out 64/16/8/4, then raster warp-items 16K/64K, then 512-thread
+ * fan-out 64/16/8/4/2/1, then raster warp-items 16K/64K, then 512-thread
  * row-loop CTAs two per multiprocessor, then the other chunking (one chart
  * chunk per wave or four) -- times each (CUDA events, second
  * run of each), drops any shape under which some atlas ends with another

@@ -84,6 +84,7 @@ __global__ void init_kernel(const Pack *__restrict__ pp) {
   if (blockIdx.x == 0) {
     if (t < 2 * kScales) p.jtot[t] = 0;
     for (int i = t; i < kScales * kMaxChunks; i += blockDim.x) p.counter[i] = 0;
+    if (t == 0) *p.cur_wave = 0;
   }
   for (int at = blockIdx.x; at < p.A; at += gridDim.x) {
     if (t < kScales) p.scale_out[at * kScales + t] = ScaleOut{0, 0, 0, 0, 0, 0, 0, 0};
@@ -177,36 +178,113 @@ int waves_of(int F) { return (kScales + F - 1) / F; }
 
 // The launch sequence of a batch: prep, sort, layout, then descending waves
 // of F candidates per atlas from its top candidate, each in Q chunks of the
-// sorted charts (plan, raster, compaction, row loop), then selection.
-void enqueue(const Pack *dp, const Launch &L, int F, cudaStream_t st, StageMarks *mk) {
-  auto b = [&](int s) { if (mk) mk->begin(s); };
-  auto e = [&]() { if (mk) mk->end(); };
-  b(0);
+// sorted charts (plan, raster, compaction, row loop), then selection.  The
+// wave index lives in device memory; each wave ends with wave_end.
+void enqueue_prologue(const Pack *dp, const Launch &L, cudaStream_t st, StageMarks *mk) {
+  if (mk) mk->begin(0);
   launch_init(dp, L, st);
   launch_prep(dp, L, st);
-  e();
-  b(1);
+  if (mk) { mk->end(); mk->begin(1); }
   launch_sort(dp, L, st);
-  e();
-  b(2);
+  if (mk) { mk->end(); mk->begin(2); }
   launch_layout(dp, L, st);
-  e();
-  for (int wave = 0; wave < waves_of(F); ++wave)
-    for (int q = 0; q < L.Q; ++q) {  // chart chunks of the wave (lazy evaluation)
-      b(3);
-      launch_plan(dp, L, wave, q, st);
-      launch_raster(dp, L, wave, q, F, st);
-      e();
-      b(4);
-      launch_hcompact(dp, L, wave, q, F, st);
-      e();
-      b(5);
-      launch_rowloop(dp, L, wave, q, F, st);
-      e();
-    }
-  b(6);
+  if (mk) mk->end();
+}
+
+void enqueue_wave(const Pack *dp, const Launch &L, int F, cudaStream_t st, StageMarks *mk,
+                  cudaGraphConditionalHandle h, bool in_graph) {
+  auto b = [&](int s) { if (mk) mk->begin(s); };
+  auto e = [&]() { if (mk) mk->end(); };
+  for (int q = 0; q < L.Q; ++q) {  // chart chunks of the wave (lazy evaluation)
+    b(3);
+    launch_plan(dp, L, q, st);
+    launch_raster(dp, L, q, F, st);
+    e();
+    b(4);
+    launch_hcompact(dp, L, q, F, st);
+    e();
+    b(5);
+    launch_rowloop(dp, L, q, F, st);
+    e();
+  }
+  launch_wave_end(dp, h, in_graph, st);
+}
+
+void enqueue_select(const Pack *dp, const Launch &L, cudaStream_t st, StageMarks *mk) {
+  if (mk) mk->begin(6);
   launch_select(dp, L, st);
-  e();
+  if (mk) mk->end();
+}
+
+// Direct launches (per-stage timing): every wave from the host.
+void enqueue(const Pack *dp, const Launch &L, int F, cudaStream_t st, StageMarks *mk) {
+  enqueue_prologue(dp, L, st, mk);
+  for (int wave = 0; wave < waves_of(F); ++wave) enqueue_wave(dp, L, F, st, mk, 0, false);
+  enqueue_select(dp, L, st, mk);
+}
+
+// The graph of a launch shape: prologue, a WHILE node whose body is one wave
+// (wave_end decides on the device whether another wave runs, so waves in
+// which no atlas searches cost nothing), then selection.
+tabi_status capture_graph(tabi_ctx *ctx, const Launch &L, int F, cudaGraph_t *out) {
+  const Pack *dp = reinterpret_cast<const Pack *>(ctx->arena);
+  cudaStream_t s0 = ctx->cap_stream, s1 = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&s1, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamCreate");
+  cudaGraph_t graph = nullptr, body = nullptr;
+  cudaGraphNode_t node = nullptr;
+  cudaGraphConditionalHandle h = 0;
+  bool capturing = false;
+  const char *what = "cudaStreamBeginCapture";
+  do {
+    if ((e = cudaStreamBeginCapture(s0, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) break;
+    capturing = true;
+    enqueue_prologue(dp, L, s0, nullptr);
+    cudaStreamCaptureStatus cs;
+    const cudaGraphNode_t *deps = nullptr;
+    const cudaGraphEdgeData *edges = nullptr;
+    size_t ndeps = 0;
+    what = "cudaStreamGetCaptureInfo";
+    if ((e = cudaStreamGetCaptureInfo(s0, &cs, nullptr, &graph, &deps, &edges, &ndeps)) != cudaSuccess) break;
+    what = "cudaGraphConditionalHandleCreate";
+    if ((e = cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault)) != cudaSuccess) break;
+    cudaGraphNodeParams np{};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    what = "cudaGraphAddNode";
+    if ((e = cudaGraphAddNode(&node, graph, deps, edges, ndeps, &np)) != cudaSuccess) break;
+    body = np.conditional.phGraph_out[0];
+    what = "cudaStreamUpdateCaptureDependencies";
+    if ((e = cudaStreamUpdateCaptureDependencies(s0, &node, nullptr, 1, cudaStreamSetCaptureDependencies)) !=
+        cudaSuccess)
+      break;
+    what = "body capture";
+    if ((e = cudaStreamBeginCaptureToGraph(s1, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) !=
+        cudaSuccess)
+      break;
+    enqueue_wave(dp, L, F, s1, nullptr, h, true);
+    cudaGraph_t body_out = nullptr;
+    if ((e = cudaStreamEndCapture(s1, &body_out)) != cudaSuccess) break;
+    enqueue_select(dp, L, s0, nullptr);
+    what = "cudaStreamEndCapture";
+    capturing = false;
+    e = cudaStreamEndCapture(s0, &graph);
+  } while (false);
+  if (capturing) {
+    cudaGraph_t junk = nullptr;
+    cudaStreamEndCapture(s0, &junk);
+    if (junk) cudaGraphDestroy(junk);
+    graph = nullptr;
+  }
+  cudaStreamDestroy(s1);
+  if (e != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return cuda_fail(ctx, e, what);
+  }
+  *out = graph;
+  return TABI_OK;
 }
 
 tabi_status get_graph(tabi_ctx *ctx, const Launch &L, int F, cudaGraphExec_t *out) {
@@ -217,13 +295,10 @@ tabi_status get_graph(tabi_ctx *ctx, const Launch &L, int F, cudaGraphExec_t *ou
       return TABI_OK;
     }
   cudaGraph_t graph = nullptr;
-  cudaError_t e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamBeginCapture");
-  enqueue(reinterpret_cast<const Pack *>(ctx->arena), L, F, ctx->cap_stream, nullptr);
-  e = cudaStreamEndCapture(ctx->cap_stream, &graph);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamEndCapture");
+  const tabi_status cs = capture_graph(ctx, L, F, &graph);
+  if (cs != TABI_OK) return cs;
   cudaGraphExec_t exec = nullptr;
-  e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphInstantiate");
   ctx->graphs.push_back(GraphEntry{F, L.rowloop_smem, L.rowloop_threads, L.rowloop_ctas, L.Q, exec});
@@ -396,6 +471,7 @@ tabi_status batch_launch(tabi_ctx *ctx, const tabi_params *params, tabi_request 
   p.act_pre = cv.take<int32_t>(A);
   p.act_chart = cv.take<int32_t>(n);
   p.counter = cv.take<int32_t>(kScales * kMaxChunks);
+  p.cur_wave = cv.take<int32_t>(1);
   p.tstate = cv.take<int32_t>((size_t)A * kScales);
   p.front_save = cv.take<int32_t>((size_t)A * p.F * p.wps_stride);
   p.ctl_save = cv.take<int32_t>((size_t)A * p.F * 16);
@@ -703,7 +779,7 @@ tabi_status tabi_autotune(tabi_ctx *ctx, const tabi_params *params, tabi_request
     const tabi_status s = trial(best);
     if (s != TABI_OK) return s;
   }
-  const int fanouts[] = {kScales, 16, 8, 4};
+  const int fanouts[] = {kScales, 16, 8, 4, 2, 1};
   const Tuning start = best;
   for (int F : fanouts) {
     if (F == start.F) continue;

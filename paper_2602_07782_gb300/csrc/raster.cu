@@ -68,10 +68,10 @@ __device__ __forceinline__ int32_t warp_axis(const rmath::AxisK &ak, int g, uint
 // Warp-items: (chart of an atlas still searching, run of G consecutive
 // candidates of the atlas's wave range).  G is chosen so that the wave has
 // about raster_items warp-items (a tuned launch shape).
-__global__ void __launch_bounds__(kRasterThreads, 4) raster_kernel(const Pack *__restrict__ pp, int wave, int q,
-                                                                  int nj) {
+__global__ void __launch_bounds__(kRasterThreads, 4) raster_kernel(const Pack *__restrict__ pp, int q, int nj) {
   __shared__ rmath::AxisK axk[kRasterWarps][2];
   const Pack &p = *pp;
+  const int wave = *(volatile const int32_t *)p.cur_wave;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int64_t total = p.act_info[1];
   const int64_t target = p.raster_items;
@@ -265,10 +265,11 @@ __global__ void __launch_bounds__(1024) bases_kernel(const Pack *__restrict__ pp
 // Wave plan: the atlases still searching (no success yet, no error, and
 // candidates left for this wave), in batch order, and a flat list of their
 // charts in chunk q.
-__global__ void __launch_bounds__(1024) plan_kernel(const Pack *__restrict__ pp, int wave, int q) {
+__global__ void __launch_bounds__(1024) plan_kernel(const Pack *__restrict__ pp, int q) {
   __shared__ int64_t part[66];
   __shared__ int64_t carry[2];
   const Pack &p = *pp;
+  const int wave = *(volatile const int32_t *)p.cur_wave;
   const int tid = threadIdx.x;
   if (tid == 0) { carry[0] = 0; carry[1] = 0; }
   __syncthreads();
@@ -338,8 +339,9 @@ __device__ __forceinline__ int32_t warp_scan_incl(int32_t v) {
 // B above it.
 // Items are the charts c of chunk q: the pair (c - 1, c) (both charts are
 // drawn by the end of the chunk), and the atlas's last chart's empty pair.
-__global__ void __launch_bounds__(256) hcompact_kernel(const Pack *__restrict__ pp, int wave, int q, int nj) {
+__global__ void __launch_bounds__(256) hcompact_kernel(const Pack *__restrict__ pp, int q, int nj) {
   const Pack &p = *pp;
+  const int wave = *(volatile const int32_t *)p.cur_wave;
   const int lane = threadIdx.x & 31;
   const int64_t total = p.act_info[1];
   const int64_t items = total * nj;
@@ -406,6 +408,25 @@ __global__ void __launch_bounds__(256) hcompact_kernel(const Pack *__restrict__ 
   }
 }
 
+// After a wave: the next wave index, and whether any atlas can still search
+// in it (no success, no error, candidates left below its top); inside a
+// captured graph that decides whether the wave loop runs again.
+__global__ void __launch_bounds__(1024) wave_end_kernel(const Pack *__restrict__ pp, cudaGraphConditionalHandle h,
+                                                        int in_graph) {
+  __shared__ int any;
+  const Pack &p = *pp;
+  const int w = *(volatile const int32_t *)p.cur_wave + 1;
+  if (threadIdx.x == 0) any = 0;
+  __syncthreads();
+  for (int at = threadIdx.x; at < p.A; at += blockDim.x)
+    if (p.found[at] < 0 && p.err[at] == 0 && p.jtop[at] - w * p.F >= 0) any = 1;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    *p.cur_wave = w;
+    if (in_graph) cudaGraphSetConditional(h, (any && w < p.nwaves) ? 1u : 0u);
+  }
+}
+
 }  // namespace
 
 void launch_layout(const Pack *dp, const Launch &L, cudaStream_t st) {
@@ -413,17 +434,21 @@ void launch_layout(const Pack *dp, const Launch &L, cudaStream_t st) {
   bases_kernel<<<kScales, 1024, 0, st>>>(dp);
 }
 
-void launch_plan(const Pack *dp, const Launch &L, int wave, int q, cudaStream_t st) {
-  plan_kernel<<<1, 1024, 0, st>>>(dp, wave, q);
+void launch_plan(const Pack *dp, const Launch &L, int q, cudaStream_t st) {
+  plan_kernel<<<1, 1024, 0, st>>>(dp, q);
   plan_fill_kernel<<<L.sms * 2, 256, 0, st>>>(dp, q);
 }
 
-void launch_raster(const Pack *dp, const Launch &L, int wave, int q, int F, cudaStream_t st) {
-  raster_kernel<<<L.sms * 16, kRasterThreads, 0, st>>>(dp, wave, q, F);
+void launch_raster(const Pack *dp, const Launch &L, int q, int F, cudaStream_t st) {
+  raster_kernel<<<L.sms * 16, kRasterThreads, 0, st>>>(dp, q, F);
 }
 
-void launch_hcompact(const Pack *dp, const Launch &L, int wave, int q, int F, cudaStream_t st) {
-  hcompact_kernel<<<L.sms * 16, 256, 0, st>>>(dp, wave, q, F);
+void launch_hcompact(const Pack *dp, const Launch &L, int q, int F, cudaStream_t st) {
+  hcompact_kernel<<<L.sms * 16, 256, 0, st>>>(dp, q, F);
+}
+
+void launch_wave_end(const Pack *dp, cudaGraphConditionalHandle h, bool in_graph, cudaStream_t st) {
+  wave_end_kernel<<<1, 1024, 0, st>>>(dp, h, in_graph ? 1 : 0);
 }
 
 }  // namespace tabi

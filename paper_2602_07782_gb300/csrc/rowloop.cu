@@ -128,10 +128,10 @@ __host__ __device__ __forceinline__ int rowloop_maxrow(int W, int g) {
 // succeeded (unless every candidate is to be evaluated).
 // NT threads per CTA (1024: one CTA per multiprocessor; 512: two).
 template <int NT>
-__global__ void __launch_bounds__(NT) rowloop_kernel(const Pack *__restrict__ pp, int wave, int q, int nj,
-                                                     int smem_words) {
+__global__ void __launch_bounds__(NT) rowloop_kernel(const Pack *__restrict__ pp, int q, int nj, int smem_words) {
   constexpr int kNT = NT, kNW = NT / 32;
   const Pack &p = *pp;
+  const int wave = *(volatile const int32_t *)p.cur_wave;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t flags = p.flags;
   const bool use_hc = flags & TABI_F_HC;
@@ -679,12 +679,12 @@ cudaError_t rowloop_prepare(int smem) {
   return e;
 }
 
-void launch_rowloop(const Pack *dp, const Launch &L, int wave, int q, int F, cudaStream_t st) {
+void launch_rowloop(const Pack *dp, const Launch &L, int q, int F, cudaStream_t st) {
   // persistent: as many CTAs as fit on the multiprocessors at once
   if (L.rowloop_threads == 512)
-    rowloop_kernel<512><<<L.sms * L.rowloop_ctas, 512, L.rowloop_smem, st>>>(dp, wave, q, F, L.rowloop_smem / 4);
+    rowloop_kernel<512><<<L.sms * L.rowloop_ctas, 512, L.rowloop_smem, st>>>(dp, q, F, L.rowloop_smem / 4);
   else
-    rowloop_kernel<1024><<<L.sms, 1024, L.rowloop_smem, st>>>(dp, wave, q, F, L.rowloop_smem / 4);
+    rowloop_kernel<1024><<<L.sms, 1024, L.rowloop_smem, st>>>(dp, q, F, L.rowloop_smem / 4);
 }
 
 }  // namespace tabi

@@ -103,6 +103,7 @@ struct Pack {
   int32_t *act_pre;             // [A] their first position in act_chart
   int32_t *act_chart;           // [N] their charts (global sorted index)
   int32_t *counter;             // [64][kMaxChunks] row-loop task counter of each (wave, chunk)
+  int32_t *cur_wave;            // the wave the kernels work on (advanced by wave_end)
   int32_t *tstate;              // [A][64] row-loop task: 0 running (or not begun), 1 finished
   int32_t *front_save;          // [A][F][wps_stride] frontline of a task between chunks
   int32_t *ctl_save;            // [A][F][16] row state of a task between chunks
@@ -156,12 +157,15 @@ void launch_init(const Pack *dp, const Launch &L, cudaStream_t st);
 void launch_prep(const Pack *dp, const Launch &L, cudaStream_t st);
 void launch_sort(const Pack *dp, const Launch &L, cudaStream_t st);
 void launch_layout(const Pack *dp, const Launch &L, cudaStream_t st);
-void launch_plan(const Pack *dp, const Launch &L, int wave, int q, cudaStream_t st);
-void launch_raster(const Pack *dp, const Launch &L, int wave, int q, int F, cudaStream_t st);
-void launch_hcompact(const Pack *dp, const Launch &L, int wave, int q, int F, cudaStream_t st);
+void launch_plan(const Pack *dp, const Launch &L, int q, cudaStream_t st);
+void launch_raster(const Pack *dp, const Launch &L, int q, int F, cudaStream_t st);
+void launch_hcompact(const Pack *dp, const Launch &L, int q, int F, cudaStream_t st);
+// Ends a wave: advances the wave index and, inside a captured graph, sets
+// the loop condition (another wave iff an atlas can still search).
+void launch_wave_end(const Pack *dp, cudaGraphConditionalHandle h, bool in_graph, cudaStream_t st);
 cudaError_t rowloop_prepare(int smem);  // raise the CTA's shared-memory limit (not capturable)
 int rowloop_static_smem();              // the row-loop kernel's static shared memory
-void launch_rowloop(const Pack *dp, const Launch &L, int wave, int q, int F, cudaStream_t st);
+void launch_rowloop(const Pack *dp, const Launch &L, int q, int F, cudaStream_t st);
 void launch_select(const Pack *dp, const Launch &L, cudaStream_t st);
 size_t rowloop_smem_bytes(int W, int g);       // shared memory a row-loop CTA needs without the stage
 size_t rowloop_smem_wanted(int W, int g);      // ... with a stage of two atlas widths
