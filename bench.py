@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--atlases", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--fanout", type=int, default=0,
+                    help="with --no-autotune: candidates per wave (0: the library default)")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--serve-rate", type=float, default=2000.0)
@@ -239,14 +241,17 @@ def run_ours(args, rank, world, local, sets):
     keep, reqs = device_requests(tabi, torch, dev, sets)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     params = tabi.params_default()  # fan-out 0: the tuned launch shape
-    tuning = None
     if not args.no_autotune:
         st, t = ctx.autotune(reqs, params, stream=stream)
         assert st == 0, ctx.last_error()
         tuning = {"scale_fanout": t.scale_fanout, "raster_warp_items": t.raster_warp_items,
                   "rowloop_threads": t.rowloop_threads, "rowloop_ctas": t.rowloop_ctas,
-                  "tuned_batch_ms": round(t.ms, 3)}
-    F = tuning["scale_fanout"] if tuning else 8
+                  "chunks": t.chunks, "tuned_batch_ms": round(t.ms, 3)}
+    else:  # the library's default shape for a batch, or the given fan-out
+        params.scale_fanout = args.fanout
+        tuning = {"scale_fanout": args.fanout or 8, "raster_warp_items": 32768, "rowloop_threads": 1024,
+                  "rowloop_ctas": 1, "chunks": 4, "autotuned": False}
+    F, Q = tuning["scale_fanout"], tuning["chunks"]
 
     def step(ev=None):
         flush.fill_(1)  # evict L2 (129 MB) before the step
@@ -282,6 +287,7 @@ def run_ours(args, rank, world, local, sets):
         torch.cuda.synchronize()
         t_wall = time.perf_counter() - t_wall
     per = np.array([a.elapsed_time(b) for a, b in evs])
+    waves_run = ctx.waves_run()  # waves of the graph's device-side loop in the last timed batch
     total_ms = float(per.sum())
     if world > 1:
         total_ms = max_over_ranks(total_ms, world, dev)
@@ -371,7 +377,7 @@ def run_ours(args, rank, world, local, sets):
         "data": "synthetic (seeded star charts; the paper's chart sets are not available)",
         "config": {"workload": WORKLOAD, "atlases": A, "charts": int(sum(cs.n for cs in sets)),
                    "vertices": int(sum(cs.nv for cs in sets)), "candidates": 64, "gutter": 1,
-                   "tuning": tuning, "k_mean": float(np.mean(ks)),
+                   "tuning": tuning, "waves_per_step": waves_run, "k_mean": float(np.mean(ks)),
                    "l2": "flushed before every step (256 MiB write), outside the timed events",
                    "parallelism": f"replicas x{world}"},
         "plain": {"value": A / (plain_ms.sum() * 1e-3), "unit": "packs/s",
@@ -379,7 +385,7 @@ def run_ours(args, rank, world, local, sets):
                   "how": "the same atlases, one tabi_pack_device call each (stream-synchronous), wall clock"},
         "e2e": {"value": world * A * args.steps / e2e_s, "unit": "packs/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": int(args.steps * tabi.kernels_per_pack(F)),
+        "gpu_launches": int(args.steps * tabi.kernels_per_pack(F, Q, waves_run)),
         "stages_ms_per_step": {s: round(stage_ms[s] / max(1, npacks), 4) for s in stage_ms},
         "roofline": {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 2), "peak": hbm_peak,
                      "unit": "GB/s", "frac": round(achieved / hbm_peak, 5), "traffic": traffic,

@@ -211,18 +211,19 @@ typedef struct tabi_tuning {
                                 consecutive candidates one warp walks)       */
   int32_t rowloop_threads;   /* threads per row-loop CTA: 1024 or 512        */
   int32_t rowloop_ctas;      /* row-loop CTAs per multiprocessor: 1 or 2     */
-  int32_t chunks;            /* chart chunks per wave: 4 (lazy: a candidate
-                                that fails gets no envelopes for the charts
-                                after its failing row; the default for a
-                                batch) or 1 (the default for one atlas)      */
+  int32_t chunks;            /* chart chunks per wave: 4 or 8 (lazy: a
+                                candidate that fails gets no envelopes for
+                                the charts after its failing row's chunk; 4
+                                is the default for a batch) or 1 (the
+                                default for one atlas)                       */
   float ms;                  /* device time of one batch with this shape     */
 } tabi_tuning;
 
 /* Autotuner: packs the batch (DEVICE pointers, as tabi_pack_batch_device)
  * repeatedly under candidate launch shapes, starting from the default --
  * fan-out 64/16/8/4/2/1, then raster warp-items 16K/64K, then 512-thread
- * row-loop CTAs two per multiprocessor, then the other chunking (one chart
- * chunk per wave or four) -- times each (CUDA events, second
+ * row-loop CTAs two per multiprocessor, then the other chunkings (one,
+ * four or eight chart chunks per wave) -- times each (CUDA events, second
  * run of each), drops any shape under which some atlas ends with another
  * status (an arena too small for a wide wave), and keeps the fastest for
  * this kind of batch (atlas count, mean chart count and widest atlas in
@@ -315,7 +316,9 @@ tabi_status tabi_server_get_stats(tabi_server *srv, tabi_server_stats *out);
  *                        pools, then int64[64][2] region words, per
  *                        candidate, then int64 top candidate index (the
  *                        largest the area bound allows, -1 if none; regions
- *                        exist for the candidates up to it);
+ *                        exist for the candidates up to it), then int64
+ *                        waves the last pack ran (the same for every atlas
+ *                        of its batch);
  *   TABI_INSPECT_PAIRS   int32[n] compacting distance d(s, s+1) then
  *                        uint8[n] flags (bit0 CannotMoveAbove(s, s+1),
  *                        bit1 CannotMoveAbove(s+1, s)) for `scale`;

@@ -803,11 +803,15 @@ tabi_status tabi_autotune(tabi_ctx *ctx, const tabi_params *params, tabi_request
     const tabi_status s = trial(t);
     if (s != TABI_OK) return s;
   }
-  {  // the other chunking: all charts at once, or lazily in four chunks
-    Tuning t = best;
-    t.Q = best.Q == 1 ? 4 : 1;
-    const tabi_status s = trial(t);
-    if (s != TABI_OK) return s;
+  {  // the other chunkings: all charts at once, or lazily in four or eight chunks
+    const Tuning base_q = best;
+    for (int Q : {1, 4, 8}) {
+      if (Q == base_q.Q) continue;
+      Tuning t = base_q;
+      t.Q = Q;
+      const tabi_status s = trial(t);
+      if (s != TABI_OK) return s;
+    }
   }
   {  // leave the requests with the chosen shape's results
     float ms = 0.f;
@@ -873,16 +877,18 @@ tabi_status tabi_inspect_atlas(tabi_ctx *ctx, int32_t atlas, int32_t what, int32
   const int64_t js = (int64_t)scale * p.N + ad.cb;
   // region starts and sizes of this atlas (small reads, needed to size ENV),
   // then its top candidate
-  int64_t reg[2 * kScales * 2 + 1];
+  int64_t reg[2 * kScales * 2 + 2];
   cudaError_t e = cudaMemcpy(reg, p.abase + region(at, 0, 0), sizeof(int64_t) * 2 * kScales,
                              cudaMemcpyDeviceToHost);
   if (e == cudaSuccess)
     e = cudaMemcpy(reg + 2 * kScales, p.atot + region(at, 0, 0), sizeof(int64_t) * 2 * kScales,
                    cudaMemcpyDeviceToHost);
-  int32_t jt = 0;
+  int32_t jt = 0, waves = 0;
   if (e == cudaSuccess) e = cudaMemcpy(&jt, p.jtop + at, sizeof(int32_t), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(&waves, p.cur_wave, sizeof(int32_t), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "inspect copy");
   reg[4 * kScales] = jt;
+  reg[4 * kScales + 1] = waves;
   const int64_t words[2] = {reg[2 * kScales + 2 * scale], reg[2 * kScales + 2 * scale + 1]};
   struct Piece {
     const void *src;

@@ -1,8 +1,10 @@
 // Chart preparation (Sec. 3.1, Sec. 4.1.1, App. A) and the height sort.
 //
-// prep_kernel: one warp per chart.  Lanes stride over the chart's edges; the
-// per-slice extrema and the per-angle OBB extents are combined with warp
-// shuffles, so no atomics are needed.  Three slice passes mirror the
+// prep_kernel: a group of G lanes per chart (G = 8: four charts per warp,
+// which keeps four times as many charts in flight as one per warp -- the
+// kernel is bound by latency, not issue).  Lanes stride over the chart's edges; the per-slice
+// extrema and the per-angle OBB extents are combined with shuffles inside
+// the group (its own lane mask), so no atomics are needed.  Three slice passes mirror the
 // orientation logic: slices of the rotated chart decide the vertical
 // reflection, slices of the vertically reflected chart decide the horizontal
 // one, slices of the final chart are the local-AABB proxy.  A reflection
@@ -33,6 +35,30 @@ struct Xf {
   }
 };
 
+// Reductions and shuffles inside a group of G lanes (mask gm).
+template <int G, typename T>
+__device__ __forceinline__ T gmin(T v, unsigned gm) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) {
+    const T u = __shfl_xor_sync(gm, v, o);
+    v = u < v ? u : v;
+  }
+  return v;
+}
+template <int G, typename T>
+__device__ __forceinline__ T gmax(T v, unsigned gm) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) {
+    const T u = __shfl_xor_sync(gm, v, o);
+    v = u > v ? u : v;
+  }
+  return v;
+}
+template <int G>
+__device__ __forceinline__ unsigned group_mask() {
+  return G == 32 ? 0xffffffffu : (((1u << G) - 1) << (threadIdx.x & (32 - G)));
+}
+
 // floor and ceil of num / d for d > 0 whose quotient is known to lie in
 // [-2^21, 2^21] (|num| < 2^43): a float estimate of the quotient is within
 // one of the floor (relative error below 2^-22), and the exact integer
@@ -54,16 +80,19 @@ __device__ __forceinline__ void floor_ceil_div(int64_t num, int32_t d, int32_t &
 // values) and its edges' crossings of the inner lines B_1 .. B_9 strictly
 // between the edge's ends (a crossing of B_m belongs to slices m-1 and m).
 // Coordinates of the normalised chart lie in [0, 2^21], so everything but
-// the crossing numerators fits 32 bits.  Every lane ends with all values.
-__device__ void warp_slices(const int32_t *__restrict__ v, int nv, const Xf &xf, bool xaxis,
-                            int64_t ext, int32_t (&lo)[kSlices], int32_t (&hi)[kSlices]) {
-  const int lane = threadIdx.x & 31;
+// the crossing numerators fits 32 bits.  Every lane of the group ends with
+// all values.
+template <int G>
+__device__ void group_slices(const int32_t *__restrict__ v, int nv, const Xf &xf, bool xaxis,
+                             int64_t ext, int32_t (&lo)[kSlices], int32_t (&hi)[kSlices]) {
+  const int lane = threadIdx.x & (G - 1);
+  const unsigned gm = group_mask<G>();
   int32_t B[kSlices + 1];
 #pragma unroll
   for (int i = 0; i <= kSlices; ++i) B[i] = (int32_t)((int64_t)i * ext / kSlices);
 #pragma unroll
   for (int i = 0; i < kSlices; ++i) { lo[i] = 0x7fffffff; hi[i] = -0x7fffffff - 1; }
-  for (int e = lane; e < nv; e += 32) {
+  for (int e = lane; e < nv; e += G) {
     const int e1 = (e + 1 == nv) ? 0 : e + 1;
     int64_t x0, y0, x1, y1;
     xf.apply(v[2 * e], v[2 * e + 1], x0, y0);
@@ -98,14 +127,16 @@ __device__ void warp_slices(const int32_t *__restrict__ v, int nv, const Xf &xf,
   }
 #pragma unroll
   for (int i = 0; i < kSlices; ++i) {
-    lo[i] = warp_min(lo[i]);
-    hi[i] = warp_max(hi[i]);
+    lo[i] = gmin<G>(lo[i], gm);
+    hi[i] = gmax<G>(hi[i], gm);
   }
 }
 
-// One chart (global input index c) of the batch.
+// One chart (global input index c) of the batch, by a group of G lanes.
+template <int G>
 __device__ __forceinline__ void prep_chart(const Pack &p, int c) {
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & (G - 1);
+  const unsigned gm = group_mask<G>();
   const int at = p.catl[c];
   const AtlasDesc &ad = p.atl[at];
   const int lc = c - ad.cb;  // index within its atlas
@@ -119,16 +150,16 @@ __device__ __forceinline__ void prep_chart(const Pack &p, int c) {
   int32_t mnx = 0x7fffffff, mny = 0x7fffffff, mxx = -0x7fffffff - 1, mxy = -0x7fffffff - 1;
   int bad = (b < a) || (nv < 3) || (b > (uint32_t)ad.nv);
   if (!bad) {
-    for (int i = lane; i < nv; i += 32) {
+    for (int i = lane; i < nv; i += G) {
       const int32_t x = v[2 * i], y = v[2 * i + 1];
       bad |= (x <= -(1 << 20)) | (x >= (1 << 20)) | (y <= -(1 << 20)) | (y >= (1 << 20));
       mnx = min(mnx, x); mxx = max(mxx, x);
       mny = min(mny, y); mxy = max(mxy, y);
     }
   }
-  bad = __any_sync(0xffffffffu, bad);
-  mnx = warp_min(mnx); mxx = warp_max(mxx);
-  mny = warp_min(mny); mxy = warp_max(mxy);
+  bad = __any_sync(gm, bad);
+  mnx = gmin<G>(mnx, gm); mxx = gmax<G>(mxx, gm);
+  mny = gmin<G>(mny, gm); mxy = gmax<G>(mxy, gm);
   const int64_t W0 = (int64_t)mxx - mnx, H0 = (int64_t)mxy - mny;
   const int rot = W0 > H0;  // rotate to be taller than wide (strictly wider)
   const int64_t Wq = rot ? H0 : W0, Hq = rot ? W0 : H0;
@@ -140,8 +171,8 @@ __device__ __forceinline__ void prep_chart(const Pack &p, int c) {
       sh->u0 = sh->u1 = sh->v0 = sh->v1 = 0;
       atomicOr(p.err + at, kErrInvalid);
     }
-    if (lane < kSlices) {
-      sh->tlo[lane] = 0; sh->bhi[lane] = 256; sh->llo[lane] = 0; sh->rhi[lane] = 256;
+    for (int i = lane; i < kSlices; i += G) {
+      sh->tlo[i] = 0; sh->bhi[i] = 256; sh->llo[i] = 0; sh->rhi[i] = 256;
     }
     return;
   }
@@ -151,12 +182,12 @@ __device__ __forceinline__ void prep_chart(const Pack &p, int c) {
   // atlas: the area bound on the candidate scales
   {
     int64_t a2 = 0;
-    for (int e = lane; e < nv; e += 32) {
+    for (int e = lane; e < nv; e += G) {
       const int e1 = (e + 1 == nv) ? 0 : e + 1;
       a2 += (int64_t)v[2 * e] * v[2 * e1 + 1] - (int64_t)v[2 * e1] * v[2 * e + 1];
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+    for (int o = G / 2; o > 0; o >>= 1) a2 += __shfl_xor_sync(gm, a2, o);
     if (lane == 0) {
       atomicAdd(p.area2 + at, (unsigned long long)(a2 < 0 ? -a2 : a2));
       atomicAdd(p.ext_sum + at, (unsigned long long)Hq);  // Hq >= Wq after the rotation
@@ -165,7 +196,7 @@ __device__ __forceinline__ void prep_chart(const Pack &p, int c) {
   int32_t ylo[kSlices], yhi[kSlices], xlo[kSlices], xhi[kSlices];
 
   // App. A chart orientation, vertical reflection: top vs bottom empty area
-  warp_slices(v, nv, xf, true, Wq, ylo, yhi);
+  group_slices<G>(v, nv, xf, true, Wq, ylo, yhi);
   int64_t top = 0, bottom = 0;
 #pragma unroll
   for (int i = 0; i < kSlices; ++i) {
@@ -189,7 +220,7 @@ __device__ __forceinline__ void prep_chart(const Pack &p, int c) {
 
   // horizontal reflection: left vs right empty area, else bottom-left vs
   // bottom-right of the midline (doubled coordinates)
-  warp_slices(v, nv, xf, false, Hq, xlo, xhi);
+  group_slices<G>(v, nv, xf, false, Hq, xlo, xhi);
   int64_t left = 0, right = 0, bl2 = 0, br2 = 0;
 #pragma unroll
   for (int j = 0; j < kSlices; ++j) {
@@ -219,58 +250,62 @@ __device__ __forceinline__ void prep_chart(const Pack &p, int c) {
       xlo[j] = lo;
       xhi[j] = hi;
     }
-    warp_slices(v, nv, xf, true, Wq, ylo, yhi);
+    group_slices<G>(v, nv, xf, true, Wq, ylo, yhi);
   }
 
-  // Sec. 4.1.1 merge: tighten each slice by the other axis' slices
-  // (lanes 0..9: x-slices, lanes 16..25: y-slices)
-  int64_t r0 = 0, r1 = 0;
-  if (lane < kSlices) {
-    const int i = lane;
-    const int64_t Xi = (int64_t)i * Wq / kSlices, Xi1 = (int64_t)(i + 1) * Wq / kSlices;
-    int64_t t2 = kI64Max, b2v = kI64Min;
+  // Sec. 4.1.1 merge: tighten each slice by the other axis' slices (task
+  // t of the group's lanes: x-slice t for t < 10, y-slice t - 16 for
+  // 16 <= t < 26), written out at once
+  for (int t = lane; t < 32; t += G) {
+    if (t < kSlices) {
+      const int i = t;
+      const int64_t Xi = (int64_t)i * Wq / kSlices, Xi1 = (int64_t)(i + 1) * Wq / kSlices;
+      int64_t t2 = kI64Max, b2v = kI64Min;
 #pragma unroll
-    for (int j = 0; j < kSlices; ++j)
-      if (xlo[j] <= Xi1 && xhi[j] >= Xi) {
-        const int64_t Yj = (int64_t)j * Hq / kSlices, Yj1 = (int64_t)(j + 1) * Hq / kSlices;
-        t2 = min(t2, Yj);
-        b2v = max(b2v, Yj1);
-      }
-    int64_t yl = 0, yh = 0;
+      for (int j = 0; j < kSlices; ++j)
+        if (xlo[j] <= Xi1 && xhi[j] >= Xi) {
+          const int64_t Yj = (int64_t)j * Hq / kSlices, Yj1 = (int64_t)(j + 1) * Hq / kSlices;
+          t2 = min(t2, Yj);
+          b2v = max(b2v, Yj1);
+        }
+      int64_t yl = 0, yh = 0;
 #pragma unroll
-    for (int q = 0; q < kSlices; ++q) if (q == i) { yl = ylo[q]; yh = yhi[q]; }
-    r0 = max(yl, t2);
-    r1 = min(yh, b2v);
-  } else if (lane >= 16 && lane < 16 + kSlices) {
-    const int j = lane - 16;
-    const int64_t Yj = (int64_t)j * Hq / kSlices, Yj1 = (int64_t)(j + 1) * Hq / kSlices;
-    int64_t l2 = kI64Max, r2 = kI64Min;
+      for (int q = 0; q < kSlices; ++q) if (q == i) { yl = ylo[q]; yh = yhi[q]; }
+      const int32_t r0 = (int32_t)max(yl, t2), r1 = (int32_t)min(yh, b2v);
+      inf->tlo[i] = r0; inf->bhi[i] = r1;
+      sh->tlo[i] = r0; sh->bhi[i] = r1;
+    } else if (t >= 16 && t < 16 + kSlices) {
+      const int j = t - 16;
+      const int64_t Yj = (int64_t)j * Hq / kSlices, Yj1 = (int64_t)(j + 1) * Hq / kSlices;
+      int64_t l2 = kI64Max, r2 = kI64Min;
 #pragma unroll
-    for (int i = 0; i < kSlices; ++i)
-      if (ylo[i] <= Yj1 && yhi[i] >= Yj) {
-        const int64_t Xi = (int64_t)i * Wq / kSlices, Xi1 = (int64_t)(i + 1) * Wq / kSlices;
-        l2 = min(l2, Xi);
-        r2 = max(r2, Xi1);
-      }
-    int64_t xl = 0, xh = 0;
+      for (int i = 0; i < kSlices; ++i)
+        if (ylo[i] <= Yj1 && yhi[i] >= Yj) {
+          const int64_t Xi = (int64_t)i * Wq / kSlices, Xi1 = (int64_t)(i + 1) * Wq / kSlices;
+          l2 = min(l2, Xi);
+          r2 = max(r2, Xi1);
+        }
+      int64_t xl = 0, xh = 0;
 #pragma unroll
-    for (int q = 0; q < kSlices; ++q) if (q == j) { xl = xlo[q]; xh = xhi[q]; }
-    r0 = max(xl, l2);
-    r1 = min(xh, r2);
+      for (int q = 0; q < kSlices; ++q) if (q == j) { xl = xlo[q]; xh = xhi[q]; }
+      const int32_t r0 = (int32_t)max(xl, l2), r1 = (int32_t)min(xh, r2);
+      inf->llo[j] = r0; inf->rhi[j] = r1;
+      sh->llo[j] = r0; sh->rhi[j] = r1;
+    }
   }
 
   // App. A OBB: 8 angles, extents of u = xC + yS, v = -xS + yC.  Lane l
-  // takes angle l % 8 over every fourth vertex from l / 8; the four lanes
-  // of an angle combine by two exchanges; then every lane picks the angle
-  // of least area / (C^2 + S^2) in angle order, exactly as a sequential
-  // scan over m would (ties to the smaller m).
+  // takes angle l % 8 over every (G/8)-th vertex from l / 8; the lanes of
+  // an angle combine by exchanges; then every lane picks the angle of least
+  // area / (C^2 + S^2) in angle order, exactly as a sequential scan over m
+  // would (ties to the smaller m).
   int64_t bu0 = 0, bu1 = 0, bv0 = 0, bv1 = 0;
   int best = 0;
   {
     const int am = lane & 7;
     const int64_t C = kObbCos[am], S = kObbSin[am];
     int64_t u0 = kI64Max, u1 = kI64Min, v0 = kI64Max, v1 = kI64Min;
-    for (int i = lane >> 3; i < nv; i += 4) {
+    for (int i = lane >> 3; i < nv; i += G / 8) {
       int64_t x, y;
       xf.apply(v[2 * i], v[2 * i + 1], x, y);
       const int64_t uu = x * C + y * S, vv = -x * S + y * C;
@@ -278,17 +313,17 @@ __device__ __forceinline__ void prep_chart(const Pack &p, int c) {
       v0 = min(v0, vv); v1 = max(v1, vv);
     }
 #pragma unroll
-    for (int o = 8; o < 32; o <<= 1) {
-      u0 = min(u0, (int64_t)__shfl_xor_sync(0xffffffffu, u0, o));
-      u1 = max(u1, (int64_t)__shfl_xor_sync(0xffffffffu, u1, o));
-      v0 = min(v0, (int64_t)__shfl_xor_sync(0xffffffffu, v0, o));
-      v1 = max(v1, (int64_t)__shfl_xor_sync(0xffffffffu, v1, o));
+    for (int o = 8; o < G; o <<= 1) {
+      u0 = min(u0, (int64_t)__shfl_xor_sync(gm, u0, o));
+      u1 = max(u1, (int64_t)__shfl_xor_sync(gm, u1, o));
+      v0 = min(v0, (int64_t)__shfl_xor_sync(gm, v0, o));
+      v1 = max(v1, (int64_t)__shfl_xor_sync(gm, v1, o));
     }
     const int64_t du = u1 - u0, dv = v1 - v0;
     __int128 best_area = 0, best_n = 1;
 #pragma unroll
     for (int m = 0; m < kAngles; ++m) {
-      const int64_t dum = __shfl_sync(0xffffffffu, du, m), dvm = __shfl_sync(0xffffffffu, dv, m);
+      const int64_t dum = __shfl_sync(gm, du, m, G), dvm = __shfl_sync(gm, dv, m, G);
       const int64_t Cm = kObbCos[m], Sm = kObbSin[m];
       const __int128 area = (__int128)dum * dvm;
       const __int128 nrm = (__int128)(Cm * Cm + Sm * Sm);
@@ -296,10 +331,10 @@ __device__ __forceinline__ void prep_chart(const Pack &p, int c) {
         best = m; best_area = area; best_n = nrm;
       }
     }
-    bu0 = __shfl_sync(0xffffffffu, u0, best);
-    bu1 = __shfl_sync(0xffffffffu, u1, best);
-    bv0 = __shfl_sync(0xffffffffu, v0, best);
-    bv1 = __shfl_sync(0xffffffffu, v1, best);
+    bu0 = __shfl_sync(gm, u0, best, G);
+    bu1 = __shfl_sync(gm, u1, best, G);
+    bv0 = __shfl_sync(gm, v0, best, G);
+    bv1 = __shfl_sync(gm, v1, best, G);
   }
 
   // write the records
@@ -317,21 +352,15 @@ __device__ __forceinline__ void prep_chart(const Pack &p, int c) {
     sh->Wq = (int32_t)Wq; sh->Hq = (int32_t)Hq; sh->m = best; sh->pad = 0;
     sh->u0 = bu0; sh->u1 = bu1; sh->v0 = bv0; sh->v1 = bv1;
   }
-  if (lane < kSlices) {
-    inf->tlo[lane] = (int32_t)r0; inf->bhi[lane] = (int32_t)r1;
-    sh->tlo[lane] = (int32_t)r0; sh->bhi[lane] = (int32_t)r1;
-  } else if (lane >= 16 && lane < 16 + kSlices) {
-    inf->llo[lane - 16] = (int32_t)r0; inf->rhi[lane - 16] = (int32_t)r1;
-    sh->llo[lane - 16] = (int32_t)r0; sh->rhi[lane - 16] = (int32_t)r1;
-  }
 }
 
-// one warp per chart, grid-stride over the batch's charts
+// one group of kPrepGroup lanes per chart, grid-stride over the batch's charts
+constexpr int kPrepGroup = 8;
 __global__ void __launch_bounds__(256, 2) prep_kernel(const Pack *__restrict__ pp) {
   const Pack &p = *pp;
-  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; c < p.N; c += warps)
-    prep_chart(p, (int)c);
+  const int64_t groups = ((int64_t)gridDim.x * blockDim.x) / kPrepGroup;
+  for (int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / kPrepGroup; c < p.N; c += groups)
+    prep_chart<kPrepGroup>(p, (int)c);
 }
 
 // ---------------------------------------------------------------------------

@@ -99,7 +99,11 @@ __global__ void __launch_bounds__(kRasterThreads, 4) raster_kernel(const Pack *_
     // lanes 24-31 carry the eight corner quantities across the candidates
     rmath::CornerQ cq;
     const bool corner_lane = lane >= 24 && use_o && m > 0;
-    if (corner_lane) rmath::corner_init(cq, lane - 24, 16 * (j0 + 1), 16, C, S, sh.u0, sh.u1, sh.v0, sh.v1);
+    if (corner_lane) {
+      int64_t qs, rs;
+      rmath::corner_step(lane - 24, C, S, sh.u0, sh.u1, sh.v0, sh.v1, qs, rs);
+      rmath::corner_init(cq, lane - 24, j0, C, S, qs, rs);
+    }
     for (int j = j0; j < j1; ++j) {
       const int64_t k = 16 * (j + 1);
       // a finished candidate (later chunks): nothing to draw; the corner

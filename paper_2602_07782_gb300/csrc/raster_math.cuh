@@ -187,28 +187,70 @@ TABI_HD void setup_obb_base(AxisK &ak, int axis, int64_t Wq, int64_t Hq, int64_t
 //   upper value  num = -((axis 0) u1 S + v1 C, (axis 1) u1 C - v0 S), negated back
 //   lower position num = (axis 0) u0 C - v0 S, (axis 1) u0 S + v1 C,  D = N
 //   upper position num = (axis 0) u1 C - v1 S, (axis 1) u1 S + v0 C,  D = N
+// over the candidates k = 16 (j + 1): from the quotient and remainder of
+// one step (16 num = qs D + rs, 0 <= rs < D) a run of candidates starts
+// with a small division and then advances by one step per candidate.
 struct CornerQ {
-  int64_t num, D, q, r, qs, rs;
+  int64_t D, q, r, qs, rs;
 };
 
-TABI_HD void corner_init(CornerQ &cq, int item, int64_t k0, int64_t step, int64_t C, int64_t S,
-                         int64_t u0, int64_t u1, int64_t v0, int64_t v1) {
-  const int axis = item >> 2, kind = item & 3;
-  const int64_t N = C * C + S * S;
-  int64_t num;
-  switch (kind) {
-    case 0: num = axis == 0 ? u0 * S + v0 * C : u0 * C - v1 * S; break;
-    case 1: num = -(axis == 0 ? u1 * S + v1 * C : u1 * C - v0 * S); break;
-    case 2: num = axis == 0 ? u0 * C - v0 * S : u0 * S + v1 * C; break;
-    default: num = axis == 0 ? u1 * C - v1 * S : u1 * S + v0 * C; break;
+TABI_HD int64_t corner_num(int item, int64_t C, int64_t S, int64_t u0, int64_t u1, int64_t v0, int64_t v1) {
+  const int axis = item >> 2;
+  switch (item & 3) {
+    case 0: return axis == 0 ? u0 * S + v0 * C : u0 * C - v1 * S;
+    case 1: return -(axis == 0 ? u1 * S + v1 * C : u1 * C - v0 * S);
+    case 2: return axis == 0 ? u0 * C - v0 * S : u0 * S + v1 * C;
+    default: return axis == 0 ? u1 * C - v1 * S : u1 * S + v0 * C;
   }
-  cq.num = num;
-  cq.D = kind < 2 ? N * kF : N;
-  // |num| < 2^51, k0 <= 1024, D >= N > 2^23: the quotients are below 2^38
-  cq.q = fdiv64_est(k0 * num, cq.D);
-  cq.r = k0 * num - cq.q * cq.D;
-  cq.qs = fdiv64_est(step * num, cq.D);
-  cq.rs = step * num - cq.qs * cq.D;
+}
+TABI_HD int64_t corner_den(int item, int64_t C, int64_t S) {
+  const int64_t N = C * C + S * S;
+  return (item & 3) < 2 ? N * kF : N;
+}
+
+// floor(a / N) for |a| < 2^62 and 2^23 < N < 2^30 in single precision and
+// exact integer corrections.  A float quotient has relative error below
+// 2^-22 (three roundings of 2^-24), so the first estimate q1 (|a / N| <
+// 2^39) is within 2^17 + 1 of a / N; the remainder a - q1 N is then below
+// 2^48 in size, and the estimate of its quotient (below 2^17 + 1) is within
+// 2^-5 of the true one, so the sum is off by at most one, which the exact
+// remainder fixes.
+TABI_HD int64_t fdiv_n(int64_t a, int64_t N) {
+  const float rn = 1.0f / (float)N;
+  int64_t q = (int64_t)((float)a * rn);
+  q += (int64_t)floorf((float)(a - q * N) * rn);
+  const int64_t r = a - q * N;
+  if (r < 0) --q;
+  else if (r >= N) ++q;
+  return q;
+}
+
+// One step's quotient and remainder.  D = N F or N with N = C^2 + S^2 in
+// (2^23, 2^29] and |16 num| < 2^55; floor(a / (N F)) = floor(floor(a / F) / N).
+TABI_HD void corner_step(int item, int64_t C, int64_t S, int64_t u0, int64_t u1, int64_t v0, int64_t v1,
+                         int64_t &qs, int64_t &rs) {
+  const int64_t num = 16 * corner_num(item, C, S, u0, u1, v0, v1);
+  const int64_t N = C * C + S * S;
+  qs = fdiv_n((item & 3) < 2 ? (num >> 18) : num, N);
+  rs = num - qs * corner_den(item, C, S);
+}
+
+// Candidate j0 from the step: k0 num = (j0 + 1)(qs D + rs), so
+// q = (j0 + 1) qs + floor(t / D) with t = (j0 + 1) rs in [0, 64 D).  The
+// float quotient of t / D is below 64 and within 2^-16 of the true one
+// (three roundings of relative size 2^-24), so its floor is off by at most
+// one and the exact remainder fixes it.
+TABI_HD void corner_init(CornerQ &cq, int item, int j0, int64_t C, int64_t S, int64_t qs, int64_t rs) {
+  cq.D = corner_den(item, C, S);
+  cq.qs = qs;
+  cq.rs = rs;
+  const int64_t t = (int64_t)(j0 + 1) * rs;
+  int64_t qq = (int64_t)floorf((float)t / (float)cq.D);
+  int64_t r = t - qq * cq.D;
+  if (r < 0) { --qq; r += cq.D; }
+  else if (r >= cq.D) { ++qq; r -= cq.D; }
+  cq.q = (int64_t)(j0 + 1) * qs + qq;
+  cq.r = r;
 }
 
 TABI_HD void corner_advance(CornerQ &cq) {

@@ -168,11 +168,15 @@ def waves(fanout: int) -> int:
     return (N_SCALES + fanout - 1) // fanout
 
 
-def kernels_per_pack(fanout: int, chunks: int = 4) -> int:
+def kernels_per_pack(fanout: int, chunks: int = 4, waves_run: int | None = None) -> int:
     """Kernels one (batched) pack launches: init, prep, sort + gather,
-    layout + bases, per wave and chart chunk plan + fill, raster,
-    compaction, row loop; selection."""
-    return 7 + 5 * waves(fanout) * chunks
+    layout + bases; per wave, for each chart chunk plan + fill, raster,
+    compaction, row loop, then the wave's end; selection.  The graph runs
+    waves only while some atlas still searches (`waves_run` of them: the
+    most any atlas of the batch needs, at least one); direct launches
+    (stage timing) run every wave."""
+    w = waves(fanout) if waves_run is None else max(1, waves_run)
+    return 7 + (5 * chunks + 1) * w
 
 
 @dataclass
@@ -333,6 +337,11 @@ class Context:
         row regions."""
         raw = self._inspect(INSPECT_REGIONS, 0, atlas).view(np.int64)
         return raw[:128].reshape(64, 2), raw[128:256].reshape(64, 2), int(raw[256])
+
+    def waves_run(self) -> int:
+        """Waves of candidates the last pack ran (its device-side loop stops
+        once no atlas of the batch searches)."""
+        return int(self._inspect(INSPECT_REGIONS, 0, 0).view(np.int64)[257])
 
     def pairs(self, scale: int, n: int, atlas: int = 0):
         raw = self._inspect(INSPECT_PAIRS, scale, atlas)

@@ -135,6 +135,32 @@ def test_batch_regions_tile_the_pools(ctx):
             assert all(s % 4 == 0 and n % 4 == 0 for s, n in iv)
 
 
+@pytest.mark.parametrize("fanout", [2, 5])
+def test_wave_loop_stops_when_no_atlas_searches(ctx, fanout):
+    """The graph's device-side wave loop runs exactly the waves the slowest
+    atlas needs (down to the wave holding its result, or through its last
+    candidate when nothing fits); direct launches run every wave."""
+    sets = mixed_batch()
+    p = tabi.params_default(scale_fanout=fanout)
+    st, res = ctx.pack_batch(sets, p)
+    assert st == tabi.TABI_OK
+    need = 0
+    for a, r in enumerate(res):
+        jt = ctx.regions(a)[2]
+        if r.status == tabi.TABI_OK:
+            need = max(need, (jt - (r.k // 16 - 1)) // fanout + 1)
+        elif r.status == tabi.TABI_ERR_NO_FIT and jt >= 0:
+            need = max(need, jt // fanout + 1)
+    assert ctx.waves_run() == max(1, need)
+    ctx.stage_times(True)
+    try:
+        st, res2 = ctx.pack_batch(sets, p)
+    finally:
+        ctx.stage_times(False)
+    assert st == tabi.TABI_OK and [r.k for r in res2] == [r.k for r in res]
+    assert ctx.waves_run() == (64 + fanout - 1) // fanout
+
+
 def test_area_bound_keeps_the_result(ctx):
     """The top candidate the area bound allows is at least the chosen scale,
     and every candidate above it fails in the oracle too."""

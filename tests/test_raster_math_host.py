@@ -1,7 +1,9 @@
 """Host checks of the rasterizer's integer division helpers
 (paper_2602_07782_gb300/csrc/raster_math.cuh compiled with g++): the
-multiply-high division by the OBB table's divisors and the estimated 64-bit
-floor division equal exact floor division.  The GPU parity tests check the
+multiply-high division by the OBB table's divisors, the estimated 64-bit
+floor division, the single-precision division by the OBB norms and the OBB
+corner runs (started from one step's quotient, then advanced per
+candidate) equal exact floor division.  The GPU parity tests check the
 envelopes they produce against the oracle."""
 from __future__ import annotations
 
@@ -57,6 +59,47 @@ int main() {
     for (int o = -1; o <= 1; ++o) {
       const int64_t b = q * d + o;
       if (b > -(1ll << 62) && b < (1ll << 62)) { ++checked; if (fdiv64_est(b, d) != floor_div(b, d)) ++bad; }
+    }
+  }
+  // single-precision exact division by N in (2^23, 2^30), |a| < 2^62
+  for (int i = 0; i < 400000; ++i) {
+    const int64_t N = (int64_t)(rng() % ((1ull << 30) - (1ull << 23) - 1)) + (1ll << 23) + 1;
+    const int64_t a = (int64_t)(rng() % (1ull << 63)) - (1ll << 62) + 1;
+    ++checked;
+    if (fdiv_n(a, N) != floor_div(a, N)) {
+      if (bad < 5) std::printf("fdiv_n a=%lld N=%lld\n", (long long)a, (long long)N);
+      ++bad;
+    }
+    const int64_t q = (int64_t)(rng() % (1ull << 39)) - (1ll << 38);
+    for (int o = -2; o <= 2; ++o) {
+      const int64_t b = q * N + o;
+      if (b > -(1ll << 62) && b < (1ll << 62)) { ++checked; if (fdiv_n(b, N) != floor_div(b, N)) ++bad; }
+    }
+  }
+  // OBB corner runs: a run started at candidate j0 from the per-chart step
+  // (16 num = qs D + rs), then advanced one candidate at a time, gives
+  // floor(k num / D) and its remainder at every k = 16 (j + 1)
+  for (int t = 0; t < 3000; ++t) {
+    int64_t C, S;
+    do { C = (int64_t)(rng() % 16385); S = (int64_t)(rng() % 16385); } while (C * C + S * S <= (1ll << 23));
+    auto r36 = [&]() { return (int64_t)(rng() % (1ull << 37)) - (1ll << 36); };
+    const int64_t u0 = r36(), u1 = r36(), v0 = r36(), v1 = r36();
+    const int item = (int)(rng() % 8);
+    int64_t qs, rs;
+    corner_step(item, C, S, u0, u1, v0, v1, qs, rs);
+    const int64_t num = corner_num(item, C, S, u0, u1, v0, v1), D = corner_den(item, C, S);
+    const int j0 = (int)(rng() % 64);
+    CornerQ cq;
+    corner_init(cq, item, j0, C, S, qs, rs);
+    for (int j = j0; j < 64; ++j) {
+      const int64_t kn = 16 * (int64_t)(j + 1) * num;
+      const int64_t q = floor_div(kn, D);
+      ++checked;
+      if (cq.q != q || cq.r != kn - q * D) {
+        if (bad < 5) std::printf("corner item %d j0 %d j %d got %lld want %lld\n", item, j0, j, (long long)cq.q, (long long)q);
+        ++bad;
+      }
+      corner_advance(cq);
     }
   }
   std::printf("checked %ld bad %ld\n", checked, bad);
