@@ -317,8 +317,9 @@ tabi_status tabi_server_get_stats(tabi_server *srv, tabi_server_stats *out);
  *                        candidate, then int64 top candidate index (the
  *                        largest the area bound allows, -1 if none; regions
  *                        exist for the candidates up to it), then int64
- *                        waves the last pack ran (the same for every atlas
- *                        of its batch);
+ *                        waves the last pack ran and int64 prep lanes per
+ *                        chart it used (both the same for every atlas of
+ *                        its batch);
  *   TABI_INSPECT_PAIRS   int32[n] compacting distance d(s, s+1) then
  *                        uint8[n] flags (bit0 CannotMoveAbove(s, s+1),
  *                        bit1 CannotMoveAbove(s+1, s)) for `scale`;

@@ -290,7 +290,7 @@ tabi_status capture_graph(tabi_ctx *ctx, const Launch &L, int F, cudaGraph_t *ou
 tabi_status get_graph(tabi_ctx *ctx, const Launch &L, int F, cudaGraphExec_t *out) {
   for (const GraphEntry &g : ctx->graphs)
     if (g.F == F && g.smem == L.rowloop_smem && g.threads == L.rowloop_threads && g.ctas == L.rowloop_ctas &&
-        g.Q == L.Q) {
+        g.Q == L.Q && g.prep_group == L.prep_group) {
       *out = g.exec;
       return TABI_OK;
     }
@@ -301,7 +301,7 @@ tabi_status get_graph(tabi_ctx *ctx, const Launch &L, int F, cudaGraphExec_t *ou
   cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphInstantiate");
-  ctx->graphs.push_back(GraphEntry{F, L.rowloop_smem, L.rowloop_threads, L.rowloop_ctas, L.Q, exec});
+  ctx->graphs.push_back(GraphEntry{F, L.rowloop_smem, L.rowloop_threads, L.rowloop_ctas, L.Q, L.prep_group, exec});
   *out = exec;
   return TABI_OK;
 }
@@ -439,6 +439,7 @@ tabi_status batch_launch(tabi_ctx *ctx, const tabi_params *params, tabi_request 
   p.raster_items = tn.items;
   p.Q = tn.Q < 1 ? 1 : (tn.Q > kMaxChunks ? kMaxChunks : tn.Q);
   p.wps_stride = 4;
+  p.prep_group = prep_group_for(p.N, ctx->sms);
   for (int i = 0; i < A; ++i) p.wps_stride = std::max(p.wps_stride, (desc[i].W + 2 * p.g + 3) & ~3);
   p.atl = ddesc;
   const size_t n = (size_t)N;
@@ -509,7 +510,7 @@ tabi_status batch_launch(tabi_ctx *ctx, const tabi_params *params, tabi_request 
   for (int i = 0; i < A; ++i) want = std::max(want, rowloop_smem_wanted(desc[i].W, p.g));
   int smem = (int)((want + 16383) & ~(size_t)16383);
   if (smem > ctx->rowloop_dyn_max) smem = ctx->rowloop_dyn_max;
-  Launch L{ctx->sms, smem, tn.threads == 512 ? 512 : 1024, 1, p.Q};
+  Launch L{ctx->sms, smem, tn.threads == 512 ? 512 : 1024, 1, p.Q, p.prep_group};
   if (L.rowloop_threads == 512 && tn.ctas == 2) {
     // two CTAs per multiprocessor if both fit its shared memory
     const int two = (ctx->smem_per_sm - 2 * (ctx->smem_reserved + rowloop_static_smem())) / 2 & ~255;
@@ -877,7 +878,7 @@ tabi_status tabi_inspect_atlas(tabi_ctx *ctx, int32_t atlas, int32_t what, int32
   const int64_t js = (int64_t)scale * p.N + ad.cb;
   // region starts and sizes of this atlas (small reads, needed to size ENV),
   // then its top candidate
-  int64_t reg[2 * kScales * 2 + 2];
+  int64_t reg[2 * kScales * 2 + 3];
   cudaError_t e = cudaMemcpy(reg, p.abase + region(at, 0, 0), sizeof(int64_t) * 2 * kScales,
                              cudaMemcpyDeviceToHost);
   if (e == cudaSuccess)
@@ -889,6 +890,7 @@ tabi_status tabi_inspect_atlas(tabi_ctx *ctx, int32_t atlas, int32_t what, int32
   if (e != cudaSuccess) return cuda_fail(ctx, e, "inspect copy");
   reg[4 * kScales] = jt;
   reg[4 * kScales + 1] = waves;
+  reg[4 * kScales + 2] = p.prep_group;
   const int64_t words[2] = {reg[2 * kScales + 2 * scale], reg[2 * kScales + 2 * scale + 1]};
   struct Piece {
     const void *src;

@@ -15,7 +15,7 @@ namespace tabi {
 // row-loop CTA of `smem` dynamic bytes.  Every kernel reads the batch from
 // the record at the arena's start, so the graph serves any batch.
 struct GraphEntry {
-  int F, smem, threads, ctas, Q;
+  int F, smem, threads, ctas, Q, prep_group;
   cudaGraphExec_t exec;
 };
 

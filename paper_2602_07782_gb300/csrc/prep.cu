@@ -1,8 +1,8 @@
 // Chart preparation (Sec. 3.1, Sec. 4.1.1, App. A) and the height sort.
 //
-// prep_kernel: a group of G lanes per chart (G = 8: four charts per warp,
-// which keeps four times as many charts in flight as one per warp -- the
-// kernel is bound by latency, not issue).  Lanes stride over the chart's edges; the per-slice
+// prep_kernel: a group of G lanes per chart (G = 32, 16, 8 or 4, chosen by
+// the batch's chart count: narrow groups keep more charts in flight -- the
+// kernel is bound by latency, not issue -- once there are enough of them).  Lanes stride over the chart's edges; the per-slice
 // extrema and the per-angle OBB extents are combined with shuffles inside
 // the group (its own lane mask), so no atomics are needed.  Three slice passes mirror the
 // orientation logic: slices of the rotated chart decide the vertical
@@ -302,28 +302,35 @@ __device__ __forceinline__ void prep_chart(const Pack &p, int c) {
   int64_t bu0 = 0, bu1 = 0, bv0 = 0, bv1 = 0;
   int best = 0;
   {
-    const int am = lane & 7;
-    const int64_t C = kObbCos[am], S = kObbSin[am];
-    int64_t u0 = kI64Max, u1 = kI64Min, v0 = kI64Max, v1 = kI64Min;
-    for (int i = lane >> 3; i < nv; i += G / 8) {
-      int64_t x, y;
-      xf.apply(v[2 * i], v[2 * i + 1], x, y);
-      const int64_t uu = x * C + y * S, vv = -x * S + y * C;
-      u0 = min(u0, uu); u1 = max(u1, uu);
-      v0 = min(v0, vv); v1 = max(v1, vv);
-    }
+    // groups narrower than 8 lanes: lane l takes angles l, l + G, ...
+    constexpr int R = G >= 8 ? 1 : 8 / G;
+    int64_t u0[R], u1[R], v0[R], v1[R];
 #pragma unroll
-    for (int o = 8; o < G; o <<= 1) {
-      u0 = min(u0, (int64_t)__shfl_xor_sync(gm, u0, o));
-      u1 = max(u1, (int64_t)__shfl_xor_sync(gm, u1, o));
-      v0 = min(v0, (int64_t)__shfl_xor_sync(gm, v0, o));
-      v1 = max(v1, (int64_t)__shfl_xor_sync(gm, v1, o));
+    for (int r = 0; r < R; ++r) {
+      const int am = (lane & 7) + G * r;
+      const int64_t C = kObbCos[am], S = kObbSin[am];
+      u0[r] = kI64Max; u1[r] = kI64Min; v0[r] = kI64Max; v1[r] = kI64Min;
+      for (int i = G >= 8 ? lane >> 3 : 0; i < nv; i += G >= 8 ? G / 8 : 1) {
+        int64_t x, y;
+        xf.apply(v[2 * i], v[2 * i + 1], x, y);
+        const int64_t uu = x * C + y * S, vv = -x * S + y * C;
+        u0[r] = min(u0[r], uu); u1[r] = max(u1[r], uu);
+        v0[r] = min(v0[r], vv); v1[r] = max(v1[r], vv);
+      }
+#pragma unroll
+      for (int o = 8; o < G; o <<= 1) {
+        u0[r] = min(u0[r], (int64_t)__shfl_xor_sync(gm, u0[r], o));
+        u1[r] = max(u1[r], (int64_t)__shfl_xor_sync(gm, u1[r], o));
+        v0[r] = min(v0[r], (int64_t)__shfl_xor_sync(gm, v0[r], o));
+        v1[r] = max(v1[r], (int64_t)__shfl_xor_sync(gm, v1[r], o));
+      }
     }
-    const int64_t du = u1 - u0, dv = v1 - v0;
     __int128 best_area = 0, best_n = 1;
 #pragma unroll
     for (int m = 0; m < kAngles; ++m) {
-      const int64_t dum = __shfl_sync(gm, du, m, G), dvm = __shfl_sync(gm, dv, m, G);
+      const int r = m / G < R ? m / G : 0;  // angle m: lane m % G, slot m / G
+      const int64_t dum = __shfl_sync(gm, u1[r] - u0[r], m % G, G);
+      const int64_t dvm = __shfl_sync(gm, v1[r] - v0[r], m % G, G);
       const int64_t Cm = kObbCos[m], Sm = kObbSin[m];
       const __int128 area = (__int128)dum * dvm;
       const __int128 nrm = (__int128)(Cm * Cm + Sm * Sm);
@@ -331,10 +338,14 @@ __device__ __forceinline__ void prep_chart(const Pack &p, int c) {
         best = m; best_area = area; best_n = nrm;
       }
     }
-    bu0 = __shfl_sync(gm, u0, best, G);
-    bu1 = __shfl_sync(gm, u1, best, G);
-    bv0 = __shfl_sync(gm, v0, best, G);
-    bv1 = __shfl_sync(gm, v1, best, G);
+    int64_t su0 = u0[0], su1 = u1[0], sv0 = v0[0], sv1 = v1[0];
+#pragma unroll
+    for (int r = 1; r < R; ++r)
+      if (best / G == r) { su0 = u0[r]; su1 = u1[r]; sv0 = v0[r]; sv1 = v1[r]; }
+    bu0 = __shfl_sync(gm, su0, best % G, G);
+    bu1 = __shfl_sync(gm, su1, best % G, G);
+    bv0 = __shfl_sync(gm, sv0, best % G, G);
+    bv1 = __shfl_sync(gm, sv1, best % G, G);
   }
 
   // write the records
@@ -354,13 +365,13 @@ __device__ __forceinline__ void prep_chart(const Pack &p, int c) {
   }
 }
 
-// one group of kPrepGroup lanes per chart, grid-stride over the batch's charts
-constexpr int kPrepGroup = 8;
+// one group of G lanes per chart, grid-stride over the batch's charts
+template <int G>
 __global__ void __launch_bounds__(256, 2) prep_kernel(const Pack *__restrict__ pp) {
   const Pack &p = *pp;
-  const int64_t groups = ((int64_t)gridDim.x * blockDim.x) / kPrepGroup;
-  for (int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / kPrepGroup; c < p.N; c += groups)
-    prep_chart<kPrepGroup>(p, (int)c);
+  const int64_t groups = ((int64_t)gridDim.x * blockDim.x) / G;
+  for (int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G; c < p.N; c += groups)
+    prep_chart<G>(p, (int)c);
 }
 
 // ---------------------------------------------------------------------------
@@ -489,7 +500,20 @@ __global__ void gather_kernel(const Pack *__restrict__ pp) {
 }  // namespace
 
 void launch_prep(const Pack *dp, const Launch &L, cudaStream_t st) {
-  prep_kernel<<<L.sms * 8, 256, 0, st>>>(dp);
+  switch (L.prep_group) {
+    case 32: prep_kernel<32><<<L.sms * 8, 256, 0, st>>>(dp); break;
+    case 16: prep_kernel<16><<<L.sms * 8, 256, 0, st>>>(dp); break;
+    case 8: prep_kernel<8><<<L.sms * 8, 256, 0, st>>>(dp); break;
+    default: prep_kernel<4><<<L.sms * 8, 256, 0, st>>>(dp); break;
+  }
+}
+
+// Lanes per chart: wide groups while the charts leave the multiprocessors'
+// resident warps (two 256-thread CTAs each) idle -- the latency of one
+// chart is the prep time then -- narrow ones once they are all busy.
+int prep_group_for(int64_t charts, int sms) {
+  const int64_t warps = (int64_t)sms * 16;
+  return charts <= warps ? 32 : charts <= 2 * warps ? 16 : charts <= 4 * warps ? 8 : 4;
 }
 
 void launch_sort(const Pack *dp, const Launch &L, cudaStream_t st) {

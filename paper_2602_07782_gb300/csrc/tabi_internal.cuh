@@ -69,6 +69,7 @@ struct Pack {
   int32_t raster_items;         // target warp-items of a raster wave
   int32_t Q;                    // chart chunks per wave (1: all charts at once)
   int32_t wps_stride;           // ints per saved frontline (widest atlas, padded)
+  int32_t prep_group;           // prep lanes per chart (host record of the launch)
   int32_t pad_;
   const AtlasDesc *atl;         // [A]
   int32_t *catl;                // [N] atlas of each chart
@@ -152,9 +153,11 @@ struct Launch {
   int rowloop_threads; // 1024 or 512 threads per row-loop CTA
   int rowloop_ctas;    // row-loop CTAs per multiprocessor (512 threads: 1 or 2)
   int Q;               // chart chunks per wave
+  int prep_group;      // prep lanes per chart: 32, 16, 8 or 4
 };
 void launch_init(const Pack *dp, const Launch &L, cudaStream_t st);
 void launch_prep(const Pack *dp, const Launch &L, cudaStream_t st);
+int prep_group_for(int64_t charts, int sms);
 void launch_sort(const Pack *dp, const Launch &L, cudaStream_t st);
 void launch_layout(const Pack *dp, const Launch &L, cudaStream_t st);
 void launch_plan(const Pack *dp, const Launch &L, int q, cudaStream_t st);

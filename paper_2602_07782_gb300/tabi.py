@@ -343,6 +343,11 @@ class Context:
         once no atlas of the batch searches)."""
         return int(self._inspect(INSPECT_REGIONS, 0, 0).view(np.int64)[257])
 
+    def prep_group(self) -> int:
+        """Lanes per chart the last pack's prep used (32, 16, 8 or 4: wider
+        while its charts leave the GPU's resident warps idle)."""
+        return int(self._inspect(INSPECT_REGIONS, 0, 0).view(np.int64)[258])
+
     def pairs(self, scale: int, n: int, atlas: int = 0):
         raw = self._inspect(INSPECT_PAIRS, scale, atlas)
         d = raw[:4 * n].view(np.int32)

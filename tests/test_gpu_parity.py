@@ -71,6 +71,21 @@ def _check_prep(ctx, cs, op):
     return rec, perm
 
 
+def test_prep_group_widths(ctx):
+    """Prep runs 32, 16, 8 or 4 lanes per chart, by the chart count against
+    the multiprocessors' resident warps; every width gives the oracle's
+    chart records and sorted order."""
+    warps = 16 * torch.cuda.get_device_properties(0).multi_processor_count
+    seen = set()
+    for i, n in enumerate([warps // 2, warps * 3 // 2, warps * 3, warps * 5]):
+        cs = synth.stars(40 + i, n, 4096)
+        p = gpu_params()
+        ctx.pack(cs, p)
+        seen.add(ctx.prep_group())
+        _check_prep(ctx, cs, oracle_params(p))
+    assert seen == {32, 16, 8, 4}
+
+
 @pytest.mark.parametrize("name", list(SMALL))
 def test_steps_parity(ctx, name):
     """prep, sort, envelopes, distances/flags and every candidate's row loop."""
