@@ -35,30 +35,6 @@ struct Xf {
   }
 };
 
-// Reductions and shuffles inside a group of G lanes (mask gm).
-template <int G, typename T>
-__device__ __forceinline__ T gmin(T v, unsigned gm) {
-#pragma unroll
-  for (int o = G / 2; o > 0; o >>= 1) {
-    const T u = __shfl_xor_sync(gm, v, o);
-    v = u < v ? u : v;
-  }
-  return v;
-}
-template <int G, typename T>
-__device__ __forceinline__ T gmax(T v, unsigned gm) {
-#pragma unroll
-  for (int o = G / 2; o > 0; o >>= 1) {
-    const T u = __shfl_xor_sync(gm, v, o);
-    v = u > v ? u : v;
-  }
-  return v;
-}
-template <int G>
-__device__ __forceinline__ unsigned group_mask() {
-  return G == 32 ? 0xffffffffu : (((1u << G) - 1) << (threadIdx.x & (32 - G)));
-}
-
 // floor and ceil of num / d for d > 0 whose quotient is known to lie in
 // [-2^21, 2^21] (|num| < 2^43): a float estimate of the quotient is within
 // one of the floor (relative error below 2^-22), and the exact integer
@@ -127,8 +103,8 @@ __device__ void group_slices(const int32_t *__restrict__ v, int nv, const Xf &xf
   }
 #pragma unroll
   for (int i = 0; i < kSlices; ++i) {
-    lo[i] = gmin<G>(lo[i], gm);
-    hi[i] = gmax<G>(hi[i], gm);
+    lo[i] = group_min<G>(lo[i], gm);
+    hi[i] = group_max<G>(hi[i], gm);
   }
 }
 
@@ -158,8 +134,8 @@ __device__ __forceinline__ void prep_chart(const Pack &p, int c) {
     }
   }
   bad = __any_sync(gm, bad);
-  mnx = gmin<G>(mnx, gm); mxx = gmax<G>(mxx, gm);
-  mny = gmin<G>(mny, gm); mxy = gmax<G>(mxy, gm);
+  mnx = group_min<G>(mnx, gm); mxx = group_max<G>(mxx, gm);
+  mny = group_min<G>(mny, gm); mxy = group_max<G>(mxy, gm);
   const int64_t W0 = (int64_t)mxx - mnx, H0 = (int64_t)mxy - mny;
   const int rot = W0 > H0;  // rotate to be taller than wide (strictly wider)
   const int64_t Wq = rot ? H0 : W0, Hq = rot ? W0 : H0;

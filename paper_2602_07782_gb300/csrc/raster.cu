@@ -325,34 +325,38 @@ __global__ void __launch_bounds__(256) plan_fill_kernel(const Pack *__restrict__
 // ---------------------------------------------------------------------------
 // horizontal compactor (Sec. 4.1.2, App. A interlock)
 // ---------------------------------------------------------------------------
-template <bool kMax>
-__device__ __forceinline__ int32_t warp_scan_incl(int32_t v) {
-  const int lane = threadIdx.x & 31;
+// Inclusive max / min scan over an aligned group of G lanes.
+template <int G, bool kMax>
+__device__ __forceinline__ int32_t group_scan_incl(int32_t v, unsigned gm) {
+  const int lane = threadIdx.x & (G - 1);
 #pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int32_t u = __shfl_up_sync(0xffffffffu, v, o);
+  for (int o = 1; o < G; o <<= 1) {
+    const int32_t u = __shfl_up_sync(gm, v, o, G);
     if (lane >= o) v = kMax ? (u > v ? u : v) : (u < v ? u : v);
   }
   return v;
 }
 
-// One warp per (scale, sorted pair (s, s+1)), A = s left of B = s+1,
-// top-aligned:  d = w'_A - max_r (R'_A(r) - L'_B(r));  B may move up
-// relative to A iff every row of B stays right of all rows of A above it;
-// A may move up relative to B iff every row of A stays left of all rows of
-// B above it.
+// One group of G lanes per (scale, sorted pair (s, s+1)), A = s left of
+// B = s+1, top-aligned:  d = w'_A - max_r (R'_A(r) - L'_B(r));  B may move
+// up relative to A iff every row of B stays right of all rows of A above
+// it; A may move up relative to B iff every row of A stays left of all rows
+// of B above it.  Groups narrower than a warp keep more pairs' chains of
+// dependent loads in flight (the kernel waits on memory, not on issue).
 // Items are the charts c of chunk q: the pair (c - 1, c) (both charts are
 // drawn by the end of the chunk), and the atlas's last chart's empty pair.
+template <int G>
 __global__ void __launch_bounds__(256) hcompact_kernel(const Pack *__restrict__ pp, int q, int nj) {
   const Pack &p = *pp;
   const int wave = *(volatile const int32_t *)p.cur_wave;
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & (G - 1);
+  const unsigned gm = group_mask<G>();
   const int64_t total = p.act_info[1];
   const int64_t items = total * nj;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t ngroups = ((int64_t)gridDim.x * blockDim.x) / G;
   const int64_t N = p.N;
   const bool all = q == 0 || (p.flags & TABI_F_EVAL_ALL);
-  for (int64_t it = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; it < items; it += nwarps) {
+  for (int64_t it = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G; it < items; it += ngroups) {
     const int c = p.act_chart[it % total];
     const int at = p.catl[c];
     const WaveRange wr = wave_range(p.jtop[at], wave, nj);
@@ -375,36 +379,36 @@ __global__ void __launch_bounds__(256) hcompact_kernel(const Pack *__restrict__ 
     const uint32_t *rowB = pool + p.rowstart[ps + 1];
     const int hmin = hA < hB ? hA : hB;
     int32_t M = -kBig;
-    for (int r = lane; r < hmin; r += 32) {
+    for (int r = lane; r < hmin; r += G) {
       const int32_t ra = (int32_t)(rowA[r] >> 16), lb = (int32_t)(rowB[r] & 0xffffu);
       M = max(M, ra - lb);
     }
-    M = warp_max(M);
+    M = group_max<G>(M, gm);
     int32_t d = wA - M;
     if (d < 0) d = 0;
     const int32_t off = wA - d;
     int a_free = 1, b_free = 1;
     int32_t carry_max = -kBig, carry_min = kBig;  // over rows of A / of B above the chunk
     const int hmax = hA > hB ? hA : hB;
-    for (int base = 0; base < hmax; base += 32) {
+    for (int base = 0; base < hmax; base += G) {
       const int r = base + lane;
       const int32_t ra = r < hA ? (int32_t)(rowA[r] >> 16) : -kBig;
       const int32_t lb = r < hB ? off + (int32_t)(rowB[r] & 0xffffu) : kBig;
       // exclusive prefix max of R'_A and prefix min of off + L'_B
-      const int32_t imax = warp_scan_incl<true>(ra);
-      const int32_t imin = warp_scan_incl<false>(lb);
-      int32_t emax = __shfl_up_sync(0xffffffffu, imax, 1);
-      int32_t emin = __shfl_up_sync(0xffffffffu, imin, 1);
+      const int32_t imax = group_scan_incl<G, true>(ra, gm);
+      const int32_t imin = group_scan_incl<G, false>(lb, gm);
+      int32_t emax = __shfl_up_sync(gm, imax, 1, G);
+      int32_t emin = __shfl_up_sync(gm, imin, 1, G);
       if (lane == 0) { emax = -kBig; emin = kBig; }
       emax = max(emax, carry_max);
       emin = min(emin, carry_min);
       if (r >= 1 && r < hB && lb < emax) b_free = 0;
       if (r >= 1 && r < hA && ra > emin) a_free = 0;
-      carry_max = max(carry_max, __shfl_sync(0xffffffffu, imax, 31));
-      carry_min = min(carry_min, __shfl_sync(0xffffffffu, imin, 31));
+      carry_max = max(carry_max, __shfl_sync(gm, imax, G - 1, G));
+      carry_min = min(carry_min, __shfl_sync(gm, imin, G - 1, G));
     }
-    a_free = __all_sync(0xffffffffu, a_free);
-    b_free = __all_sync(0xffffffffu, b_free);
+    a_free = __all_sync(gm, a_free);
+    b_free = __all_sync(gm, b_free);
     if (lane == 0) {
       p.dnext[ps] = d;
       p.pflags[ps] = (uint8_t)((a_free ? 0 : 1) | (b_free ? 0 : 2));
@@ -447,8 +451,9 @@ void launch_raster(const Pack *dp, const Launch &L, int q, int F, cudaStream_t s
   raster_kernel<<<L.sms * 16, kRasterThreads, 0, st>>>(dp, q, F);
 }
 
+constexpr int kHcGroup = 16;
 void launch_hcompact(const Pack *dp, const Launch &L, int q, int F, cudaStream_t st) {
-  hcompact_kernel<<<L.sms * 16, 256, 0, st>>>(dp, q, F);
+  hcompact_kernel<kHcGroup><<<L.sms * 16, 256, 0, st>>>(dp, q, F);
 }
 
 void launch_wave_end(const Pack *dp, cudaGraphConditionalHandle h, bool in_graph, cudaStream_t st) {

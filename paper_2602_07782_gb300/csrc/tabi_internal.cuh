@@ -209,6 +209,31 @@ __device__ __forceinline__ T warp_max(T v) {
   return v;
 }
 
+// Reductions inside an aligned group of G lanes of a warp (G a power of two,
+// mask gm from group_mask<G>()).
+template <int G, typename T>
+__device__ __forceinline__ T group_min(T v, unsigned gm) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) {
+    const T u = __shfl_xor_sync(gm, v, o);
+    v = u < v ? u : v;
+  }
+  return v;
+}
+template <int G, typename T>
+__device__ __forceinline__ T group_max(T v, unsigned gm) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) {
+    const T u = __shfl_xor_sync(gm, v, o);
+    v = u > v ? u : v;
+  }
+  return v;
+}
+template <int G>
+__device__ __forceinline__ unsigned group_mask() {
+  return G == 32 ? 0xffffffffu : (((1u << G) - 1) << (threadIdx.x & (32 - G)));
+}
+
 // OBB angle table (App. A: 8 rotations evenly spaced in [0, 7*pi/16]):
 // C_m = round-half-away(2^14 * cos(m*pi/16)), S_m likewise with sin.
 static __constant__ int32_t kObbCos[kAngles] = {16384, 16069, 15137, 13623, 11585, 9102, 6270, 3196};
