@@ -159,6 +159,22 @@ def raster_sources_digest() -> str:
     return h.hexdigest()[:16]
 
 
+SMS = 152  # multiprocessors of a GB300
+
+
+def raster_ops_per_word(g: int) -> int:
+    """Integer operations one padded scanline word of an envelope needs by
+    its definition (App. A proxies, Sec. 5 gutter): ten local-AABB pieces,
+    each a subtract, an unsigned range compare, a min and a max (40); two
+    OBB bounds, each the extreme of two lines (a multiply-add and an exact
+    division by multiply-high, shift and subtract per line, then a max or
+    min: 9) and the corner override (two compares and a select: 3) (24);
+    the combination with the pieces and the clamps to the chart box (6);
+    the gutter dilation, a min and a max per neighbour over 2g neighbours
+    (4g); packing the word and the deepest bottom (3)."""
+    return 40 + 24 + 6 + 4 * g + 3
+
+
 def max_over_ranks(total_ms: float, world: int, device=None) -> float:
     """The timed region of the slowest replica (whole-job time): a MAX
     all-reduce over the ranks (NCCL on the GPUs, gloo in the CPU tests)."""
@@ -246,11 +262,12 @@ def run_ours(args, rank, world, local, sets):
         assert st == 0, ctx.last_error()
         tuning = {"scale_fanout": t.scale_fanout, "raster_warp_items": t.raster_warp_items,
                   "rowloop_threads": t.rowloop_threads, "rowloop_ctas": t.rowloop_ctas,
-                  "chunks": t.chunks, "tuned_batch_ms": round(t.ms, 3)}
+                  "chunks": t.chunks, "progressive_bound": t.progressive_bound,
+                  "tuned_batch_ms": round(t.ms, 3)}
     else:  # the library's default shape for a batch, or the given fan-out
         params.scale_fanout = args.fanout
         tuning = {"scale_fanout": args.fanout or 8, "raster_warp_items": 32768, "rowloop_threads": 1024,
-                  "rowloop_ctas": 1, "chunks": 4, "autotuned": False}
+                  "rowloop_ctas": 1, "chunks": 4, "progressive_bound": 1, "autotuned": False}
     F, Q = tuning["scale_fanout"], tuning["chunks"]
 
     def step(ev=None):
@@ -337,9 +354,10 @@ def run_ours(args, rank, world, local, sets):
     h2d = int(sum(4 * (cs.n + 1) + 8 * cs.nv for cs in sets))
     d2h = int(sum(12 * cs.n for cs in sets)) + 16 * A
 
-    # roofline of the dominant stage (algorithmic bytes / its average launch)
+    # roofline of the dominant stage
     jtops = [ctx.regions(a)[2] for a in range(A)]
     alg = algorithmic_bytes(sets, ks, jtops, F)
+    raster_words = ctx.raster_words()  # padded scanline words the (last, stage-timed) batch rasterized
     kernels = {s: stage_ms[s] for s in ("prep", "sort", "layout", "raster", "hcompact", "rowloop", "select")}
     dom = max(kernels, key=kernels.get)
     peaks = {}
@@ -352,12 +370,36 @@ def run_ours(args, rank, world, local, sets):
     launches_dom = max(1, stage_launches[dom] // max(1, npacks))
     dom_ms = stage_ms[dom] / max(1, stage_launches[dom])
     dom_bytes = alg.get(dom, 0) / launches_dom
-    achieved = dom_bytes / (dom_ms * 1e-3) / 1e9 if dom_ms > 0 and dom in alg else 0.0
+    achieved_gbs = dom_bytes / (dom_ms * 1e-3) / 1e9 if dom_ms > 0 and dom in alg else 0.0
     # traffic per launch: the captured launch's DRAM / algorithmic ratio
     # times this launch's algorithmic bytes, while the kernel is unchanged
     traffic = None
     if dom == "raster" and RASTER_NCU and raster_sources_digest() == RASTER_NCU["sources_sha256_16"]:
         traffic = int(dom_bytes * RASTER_NCU["dram_bytes"] / RASTER_NCU["algorithmic_bytes"])
+    hbm_view = {"kernel": dom, "bound": "hbm", "achieved": round(achieved_gbs, 2), "peak": hbm_peak,
+                "unit": "GB/s", "frac": round(achieved_gbs / hbm_peak, 5), "traffic": traffic,
+                "traffic_source": ("ncu capture scaled by algorithmic bytes" if traffic else
+                                   "null: no capture of the current kernel with an envelope set larger than L2"),
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.8 TB/s",
+                "algorithmic_bytes_per_launch": int(dom_bytes), "avg_launch_ms": round(dom_ms, 4),
+                "launches_per_step": int(launches_dom)}
+    roofline = hbm_view
+    if dom == "raster":
+        # the raster is bound by integer issue (ncu: ALU pipe and issue slots
+        # busiest, DRAM far from peak): algorithmic integer operations per
+        # launch over its average event-timed launch, against the issue
+        # rate of the multiprocessors at their maximum clock
+        sm_max = (clk.summary().get("sm_max_mhz") or 2070.0)
+        alu_peak = SMS * 4 * 32 * sm_max * 1e6 / 1e12  # tera lane-operations per second
+        ops_launch = raster_words * raster_ops_per_word(1) / launches_dom
+        achieved_t = ops_launch / (dom_ms * 1e-3) / 1e12 if dom_ms > 0 else 0.0
+        roofline = {"kernel": "raster", "bound": "alu", "achieved": round(achieved_t, 4), "peak": round(alu_peak, 3),
+                    "unit": "Tops/s", "frac": round(achieved_t / alu_peak, 5), "traffic": traffic,
+                    "traffic_source": hbm_view["traffic_source"],
+                    "peak_source": f"{SMS} SMs x 4 schedulers x 32 lanes x {sm_max:.0f} MHz (maximum SM clock)",
+                    "ops_per_word": raster_ops_per_word(1), "words_per_step": int(raster_words),
+                    "algorithmic_ops_per_launch": int(ops_launch), "avg_launch_ms": round(dom_ms, 4),
+                    "launches_per_step": int(launches_dom), "hbm_view": hbm_view}
 
     res = {
         "metric": METRIC,
@@ -387,13 +429,7 @@ def run_ours(args, rank, world, local, sets):
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(args.steps * tabi.kernels_per_pack(F, Q, waves_run)),
         "stages_ms_per_step": {s: round(stage_ms[s] / max(1, npacks), 4) for s in stage_ms},
-        "roofline": {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 2), "peak": hbm_peak,
-                     "unit": "GB/s", "frac": round(achieved / hbm_peak, 5), "traffic": traffic,
-                     "traffic_source": ("ncu capture scaled by algorithmic bytes" if traffic else
-                                        "null: no capture of the current kernel with an envelope set larger than L2"),
-                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.8 TB/s",
-                     "algorithmic_bytes_per_launch": int(dom_bytes), "avg_launch_ms": round(dom_ms, 4),
-                     "launches_per_step": int(launches_dom)},
+        "roofline": roofline,
         "clocks": clk.summary(),
         "wall_s_timed_region": t_wall,
     }

@@ -216,6 +216,11 @@ typedef struct tabi_tuning {
                                 the charts after its failing row's chunk; 4
                                 is the default for a batch) or 1 (the
                                 default for one atlas)                       */
+  int32_t progressive_bound; /* 1: a candidate stops as soon as the charts
+                                not yet placed cannot fit under its
+                                frontline by area (an exact test; the
+                                default for a batch), 0: only when its rows
+                                overflow (the default for one atlas)         */
   float ms;                  /* device time of one batch with this shape     */
 } tabi_tuning;
 
@@ -223,7 +228,8 @@ typedef struct tabi_tuning {
  * repeatedly under candidate launch shapes, starting from the default --
  * fan-out 64/16/8/4/2/1, then raster warp-items 16K/64K, then 512-thread
  * row-loop CTAs two per multiprocessor, then the other chunkings (one,
- * four or eight chart chunks per wave) -- times each (CUDA events, second
+ * four or eight chart chunks per wave), then the progressive area bound
+ * switched the other way -- times each (CUDA events, second
  * run of each), drops any shape under which some atlas ends with another
  * status (an arena too small for a wide wave), and keeps the fastest for
  * this kind of batch (atlas count, mean chart count and widest atlas in
@@ -317,9 +323,10 @@ tabi_status tabi_server_get_stats(tabi_server *srv, tabi_server_stats *out);
  *                        candidate, then int64 top candidate index (the
  *                        largest the area bound allows, -1 if none; regions
  *                        exist for the candidates up to it), then int64
- *                        waves the last pack ran and int64 prep lanes per
- *                        chart it used (both the same for every atlas of
- *                        its batch);
+ *                        waves the last pack ran, int64 prep lanes per
+ *                        chart it used and int64 padded scanline words
+ *                        (columns + rows over every chart and candidate)
+ *                        its raster evaluated (all three batch-wide);
  *   TABI_INSPECT_PAIRS   int32[n] compacting distance d(s, s+1) then
  *                        uint8[n] flags (bit0 CannotMoveAbove(s, s+1),
  *                        bit1 CannotMoveAbove(s+1, s)) for `scale`;
@@ -352,8 +359,9 @@ tabi_status tabi_inspect_atlas(tabi_ctx *ctx, int32_t atlas, int32_t what, int32
  * recorded on each pack's stream around every stage).  enable = 1 starts
  * collection (and clears the totals), 0 stops it; with a non-NULL stage_ms
  * the accumulated milliseconds are copied out before the state changes:
- *   stage_ms[0..7] = prep, sort, layout, raster, hcompact, rowloop, select,
- *                    whole pack;  launches[0..7] = launches of each;
+ *   stage_ms[0..7] = prep, sort, layout (with the waves' plans), raster,
+ *                    hcompact, rowloop, select, whole pack;
+ *   launches[0..7] = event-timed launches of each;
  *   *packs = packs timed.
  * Timing adds event records between kernels; leave it off otherwise. */
 tabi_status tabi_stage_times(tabi_ctx *ctx, int32_t enable, double *stage_ms, int64_t *launches,

@@ -68,7 +68,7 @@ bool valid_params(const tabi_params *p) {
 // Arena bytes of the per-chart and per-atlas arrays of one atlas (all but
 // the envelope pools), with the host-input copies.
 size_t fixed_bytes(int64_t n, int64_t nv) {
-  const size_t per_chart = 4 + sizeof(tabi_chart_info) + 2 * sizeof(ChartShape) + 3 * 4 + 16 +
+  const size_t per_chart = 4 + sizeof(tabi_chart_info) + 2 * sizeof(ChartShape) + 3 * 4 + 16 + 24 +
                            (size_t)kScales * (4 + 4 + 16 + 4 + 1 + 16) + 4 + 4 + sizeof(tabi_placement);
   const size_t per_atlas = sizeof(AtlasDesc) + (size_t)kScales * 2 * 8 * 2 + sizeof(ScaleOut) * kScales +
                            8 + sizeof(PackResult) + 8 + 40 * 256;
@@ -84,7 +84,10 @@ __global__ void init_kernel(const Pack *__restrict__ pp) {
   if (blockIdx.x == 0) {
     if (t < 2 * kScales) p.jtot[t] = 0;
     for (int i = t; i < kScales * kMaxChunks; i += blockDim.x) p.counter[i] = 0;
-    if (t == 0) *p.cur_wave = 0;
+    if (t == 0) {
+      *p.cur_wave = 0;
+      *p.raster_words = 0;
+    }
   }
   for (int at = blockIdx.x; at < p.A; at += gridDim.x) {
     if (t < kScales) p.scale_out[at * kScales + t] = ScaleOut{0, 0, 0, 0, 0, 0, 0, 0};
@@ -147,8 +150,8 @@ struct StageMarks {
   tabi_ctx *c;
   cudaStream_t st;
   int used = 0;
-  int stage[4 + 3 * kScales + 4];
-  static constexpr int kMax = 4 + 3 * kScales + 4;
+  static constexpr int kMax = tabi_ctx::kStageMarks;
+  int stage[kMax];
   void begin(int s) {
     if (used >= kMax) return;
     stage[used] = s;
@@ -196,8 +199,10 @@ void enqueue_wave(const Pack *dp, const Launch &L, int F, cudaStream_t st, Stage
   auto b = [&](int s) { if (mk) mk->begin(s); };
   auto e = [&]() { if (mk) mk->end(); };
   for (int q = 0; q < L.Q; ++q) {  // chart chunks of the wave (lazy evaluation)
-    b(3);
+    b(2);  // the wave plan counts with the layout
     launch_plan(dp, L, q, st);
+    e();
+    b(3);
     launch_raster(dp, L, q, F, st);
     e();
     b(4);
@@ -319,9 +324,13 @@ uint64_t batch_class(int A, int64_t N, int maxW, const tabi_params *params) {
          (uint64_t)params->gutter << 24 | (uint64_t)(params->flags & TABI_F_ALL) << 32;
 }
 
-// One atlas: every candidate at once, no chunks (its row loops are the
-// critical path); a batch: waves of eight candidates in four chunks.
-Tuning default_tuning(int A) { return A == 1 ? Tuning{kScales, 32768, 1024, 1, 1} : Tuning{8, 32768, 1024, 1, 4}; }
+// One atlas: every candidate at once, no chunks and no progressive area
+// bound (its successful candidate's row loop is the critical path, which
+// stopping the failing ones early does not shorten); a batch: waves of
+// eight candidates in four chunks, failing candidates stopped early.
+Tuning default_tuning(int A) {
+  return A == 1 ? Tuning{kScales, 32768, 1024, 1, 1, 0} : Tuning{8, 32768, 1024, 1, 4, 1};
+}
 
 bool ensure_hstage(tabi_ctx *ctx, size_t bytes) {
   if (ctx->hstage_bytes >= bytes) return true;
@@ -438,6 +447,7 @@ tabi_status batch_launch(tabi_ctx *ctx, const tabi_params *params, tabi_request 
   p.nwaves = waves_of(p.F);
   p.raster_items = tn.items;
   p.Q = tn.Q < 1 ? 1 : (tn.Q > kMaxChunks ? kMaxChunks : tn.Q);
+  p.prog_bound = tn.B ? 1 : 0;
   p.wps_stride = 4;
   p.prep_group = prep_group_for(p.N, ctx->sms);
   for (int i = 0; i < A; ++i) p.wps_stride = std::max(p.wps_stride, (desc[i].W + 2 * p.g + 3) & ~3);
@@ -473,6 +483,10 @@ tabi_status batch_launch(tabi_ctx *ctx, const tabi_params *params, tabi_request 
   p.act_chart = cv.take<int32_t>(n);
   p.counter = cv.take<int32_t>(kScales * kMaxChunks);
   p.cur_wave = cv.take<int32_t>(1);
+  p.raster_words = cv.take<unsigned long long>(1);
+  p.carea = cv.take<unsigned long long>(n);
+  p.pre2 = cv.take<unsigned long long>(n);
+  p.preE = cv.take<unsigned long long>(n);
   p.tstate = cv.take<int32_t>((size_t)A * kScales);
   p.front_save = cv.take<int32_t>((size_t)A * p.F * p.wps_stride);
   p.ctl_save = cv.take<int32_t>((size_t)A * p.F * 16);
@@ -519,7 +533,7 @@ tabi_status batch_launch(tabi_ctx *ctx, const tabi_params *params, tabi_request 
       L.rowloop_ctas = 2;
     }
   }
-  if (used) *used = Tuning{tn.F, tn.items, L.rowloop_threads, L.rowloop_ctas, p.Q};
+  if (used) *used = Tuning{tn.F, tn.items, L.rowloop_threads, L.rowloop_ctas, p.Q, p.prog_bound};
   if (ctx->timing) {
     StageMarks mk{ctx, st};
     enqueue(dpack, L, p.F, st, &mk);
@@ -814,6 +828,12 @@ tabi_status tabi_autotune(tabi_ctx *ctx, const tabi_params *params, tabi_request
       if (s != TABI_OK) return s;
     }
   }
+  {  // the progressive area bound on or off
+    Tuning t = best;
+    t.B = !best.B;
+    const tabi_status s = trial(t);
+    if (s != TABI_OK) return s;
+  }
   {  // leave the requests with the chosen shape's results
     float ms = 0.f;
     const tabi_status s = run_batch_locked(ctx, params, reqs, n_reqs, stream, false, &best, &ms, nullptr);
@@ -834,6 +854,7 @@ tabi_status tabi_autotune(tabi_ctx *ctx, const tabi_params *params, tabi_request
     out->rowloop_threads = best.threads;
     out->rowloop_ctas = best.ctas;
     out->chunks = best.Q;
+    out->progressive_bound = best.B;
     out->ms = best_ms;
   }
   return TABI_OK;
@@ -878,19 +899,23 @@ tabi_status tabi_inspect_atlas(tabi_ctx *ctx, int32_t atlas, int32_t what, int32
   const int64_t js = (int64_t)scale * p.N + ad.cb;
   // region starts and sizes of this atlas (small reads, needed to size ENV),
   // then its top candidate
-  int64_t reg[2 * kScales * 2 + 3];
+  int64_t reg[2 * kScales * 2 + 4];
   cudaError_t e = cudaMemcpy(reg, p.abase + region(at, 0, 0), sizeof(int64_t) * 2 * kScales,
                              cudaMemcpyDeviceToHost);
   if (e == cudaSuccess)
     e = cudaMemcpy(reg + 2 * kScales, p.atot + region(at, 0, 0), sizeof(int64_t) * 2 * kScales,
                    cudaMemcpyDeviceToHost);
   int32_t jt = 0, waves = 0;
+  unsigned long long rwords = 0;
   if (e == cudaSuccess) e = cudaMemcpy(&jt, p.jtop + at, sizeof(int32_t), cudaMemcpyDeviceToHost);
   if (e == cudaSuccess) e = cudaMemcpy(&waves, p.cur_wave, sizeof(int32_t), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(&rwords, p.raster_words, sizeof(rwords), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "inspect copy");
   reg[4 * kScales] = jt;
   reg[4 * kScales + 1] = waves;
   reg[4 * kScales + 2] = p.prep_group;
+  reg[4 * kScales + 3] = (int64_t)rwords;
   const int64_t words[2] = {reg[2 * kScales + 2 * scale], reg[2 * kScales + 2 * scale + 1]};
   struct Piece {
     const void *src;

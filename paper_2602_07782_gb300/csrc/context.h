@@ -15,7 +15,7 @@ namespace tabi {
 // row-loop CTA of `smem` dynamic bytes.  Every kernel reads the batch from
 // the record at the arena's start, so the graph serves any batch.
 struct GraphEntry {
-  int F, smem, threads, ctas, Q, prep_group;
+  int F, smem, threads, ctas, Q, prep_group;  // (the progressive bound is read from the record)
   cudaGraphExec_t exec;
 };
 
@@ -27,6 +27,7 @@ struct Tuning {
   int threads;  // row-loop CTA: 1024 or 512 threads
   int ctas;     // row-loop CTAs per multiprocessor
   int Q;        // chart chunks per wave (lazy evaluation; 1 = all at once)
+  int B;        // row loop checks the progressive area bound (1) or not (0)
 };
 
 struct TuneEntry {
@@ -59,7 +60,10 @@ struct tabi_ctx {
   std::vector<int> last_map;  // request index -> atlas index (-1: not run)
   // optional per-stage timing (direct launches with events between stages)
   bool timing = false;
-  cudaEvent_t ev[2 * (4 + 3 * tabi::kScales) + 8] = {};
+  // event pairs around the stages of one pack: prologue (3), per wave and
+  // chart chunk plan, raster, compaction, row loop (4), selection
+  static constexpr int kStageMarks = 4 + 4 * tabi::kScales * tabi::kMaxChunks + 4;
+  cudaEvent_t ev[2 * kStageMarks] = {};
   int n_ev = 0;
   double stage_ms[8] = {};
   int64_t launches[8] = {};

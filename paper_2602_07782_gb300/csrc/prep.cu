@@ -143,6 +143,7 @@ __device__ __forceinline__ void prep_chart(const Pack &p, int c) {
     // rejected: keep a harmless one-texel box so later kernels stay in bounds
     if (lane == 0) {
       inf->orig = lc; inf->valid = 0; inf->Wq = 0; inf->Hq = 0;
+      p.carea[c] = 0;
       sh->Wq = 256; sh->Hq = 256; sh->m = 0; sh->pad = 0;
       sh->u0 = sh->u1 = sh->v0 = sh->v1 = 0;
       atomicOr(p.err + at, kErrInvalid);
@@ -165,6 +166,7 @@ __device__ __forceinline__ void prep_chart(const Pack &p, int c) {
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1) a2 += __shfl_xor_sync(gm, a2, o);
     if (lane == 0) {
+      p.carea[c] = (unsigned long long)(a2 < 0 ? -a2 : a2);
       atomicAdd(p.area2 + at, (unsigned long long)(a2 < 0 ? -a2 : a2));
       atomicAdd(p.ext_sum + at, (unsigned long long)Hq);  // Hq >= Wq after the rotation
     }

@@ -85,6 +85,10 @@ __global__ void __launch_bounds__(kRasterThreads, 4) raster_kernel(const Pack *_
   const bool all = q == 0 || (p.flags & TABI_F_EVAL_ALL);  // later chunks: running candidates only
   const int g = p.g;
   rmath::AxisK &a0 = axk[wib][0], &a1 = axk[wib][1];
+  __shared__ unsigned long long cta_words;  // scanline words of this CTA (one counter add per CTA)
+  if (threadIdx.x == 0) cta_words = 0;
+  __syncthreads();
+  unsigned long long words = 0;
   for (int64_t it = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; it < items; it += nwarps) {
     const int s = p.act_chart[it / ngroups];
     const int at = p.catl[s];
@@ -139,9 +143,13 @@ __global__ void __launch_bounds__(kRasterThreads, 4) raster_kernel(const Pack *_
       }
       warp_axis(a1, g, p.pool + rbase + p.rowstart[js]);
       if (lane == 0) p.meta[js * 4 + 3] = maxbot;  // w', h' and the column start come from the layout
+      words += (unsigned long long)(a0.len + a1.len + 4 * g);
       __syncwarp();
     }
   }
+  if (lane == 0 && words) atomicAdd(&cta_words, words);
+  __syncthreads();
+  if (threadIdx.x == 0 && cta_words) atomicAdd(p.raster_words, cta_words);
 }
 
 // Exclusive block scan of the pair (x, y); every thread also gets the
@@ -201,6 +209,23 @@ __global__ void __launch_bounds__(1024) layout_kernel(const Pack *__restrict__ p
       sr += ((p.hq[cb + s] * k + kFix - 1) >> 18) + g2;
     }
     int64_t tx = 0, ty = 0;
+    if (j == 0 && p.prog_bound) {
+      // once per atlas: prefix sums, in sorted order, of the charts' doubled
+      // areas and larger extents (the row loop's progressive area bound)
+      int64_t sa = 0, se = 0, ta = 0, te = 0;
+      for (int s = s0; s < s1; ++s) {
+        sa += (int64_t)p.carea[p.perm[cb + s]];
+        se += p.hq[cb + s];
+      }
+      block_scan2(sa, se, ta, te, part);
+      for (int s = s0; s < s1; ++s) {
+        p.pre2[cb + s] = (unsigned long long)sa;
+        p.preE[cb + s] = (unsigned long long)se;
+        sa += (int64_t)p.carea[p.perm[cb + s]];
+        se += p.hq[cb + s];
+      }
+      __syncthreads();  // part is reused by the next scan
+    }
     block_scan2(sc, sr, tx, ty, part);
     const bool meta = j <= p.jtop[at];  // candidates the search may evaluate
     for (int s = s0; s < s1; ++s) {

@@ -100,6 +100,19 @@ template <int NW>
 __device__ __forceinline__ int32_t block_min(int32_t v, Ctl &ctl) {
   return -block_max<NW>(-v, ctl);
 }
+template <int NW>
+__device__ __forceinline__ int32_t block_sum(int32_t v, Ctl &ctl) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (lane == 0) ctl.red[w] = v;
+  __syncthreads();
+  int32_t r = lane < NW ? ctl.red[lane] : 0;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+  __syncthreads();
+  return r;
+}
 
 // segmented inclusive scan (max) over lanes; `heads` has a bit per lane
 // that starts a segment (bit 0 set), each lane's start is its highest head
@@ -137,6 +150,7 @@ __global__ void __launch_bounds__(NT) rowloop_kernel(const Pack *__restrict__ pp
   const bool use_hc = flags & TABI_F_HC;
   const bool balance = flags & TABI_F_BALANCE;
   const bool eval_all = flags & TABI_F_EVAL_ALL;
+  const bool area_bound = !eval_all && p.prog_bound;  // phase I
   const int g = p.g;
   const int64_t N = p.N;
   extern __shared__ int4 sm4[];
@@ -617,6 +631,29 @@ __global__ void __launch_bounds__(NT) rowloop_kernel(const Pack *__restrict__ pp
           for (int t = tid; t < len; t += kNT) {
             const int32_t X = dir ? hi - pos[t] - wps[t] : lo + pos[t];
             place[row_start + t] = make_int4(X, y[t], row, bits);
+          }
+          __syncthreads();
+        }
+
+        // ---- I: progressive area bound (exact; an addition to the paper) -----
+        // Every later chart is dropped onto the frontline, so its padded
+        // envelope lies between front[x] and the padded atlas bottom Hp (or
+        // the candidate fails), and padded envelopes are disjoint; a
+        // connected polygon of area A and larger extent E dilated by g covers
+        // at least A + 2gE + 4g^2.  Once the charts not yet placed cannot
+        // fit that way into the area under the frontline, the candidate
+        // fails now instead of rows later.
+        if (area_bound && !ctl.fail && ctl.row_start < n) {
+          int32_t fr = 0;  // free texels under the frontline (front[x] <= Hp here; sides <= 8192)
+          for (int x = tid; x < Wp; x += kNT) fr += Hp - front[x];
+          fr = block_sum<kNW>(fr, ctl);
+          if (tid == 0) {
+            const int s = ctl.row_start;
+            const uint64_t kk = 16 * (uint64_t)(j + 1), gg = (uint64_t)g;
+            const unsigned __int128 S2 = p.area2[at] - p.pre2[cb + s], SE = p.ext_sum[at] - p.preE[cb + s];
+            const unsigned __int128 need = S2 * (kk * kk) + ((SE * (2 * gg * kk)) << 19) +
+                                           ((unsigned __int128)(4 * gg * gg * (uint64_t)(n - s)) << 37);
+            if (need > ((unsigned __int128)(uint32_t)fr << 37)) ctl.fail = 1;
           }
           __syncthreads();
         }

@@ -70,6 +70,7 @@ struct Pack {
   int32_t Q;                    // chart chunks per wave (1: all charts at once)
   int32_t wps_stride;           // ints per saved frontline (widest atlas, padded)
   int32_t prep_group;           // prep lanes per chart (host record of the launch)
+  int32_t prog_bound;           // row loop checks the progressive area bound after each row
   int32_t pad_;
   const AtlasDesc *atl;         // [A]
   int32_t *catl;                // [N] atlas of each chart
@@ -105,6 +106,10 @@ struct Pack {
   int32_t *act_chart;           // [N] their charts (global sorted index)
   int32_t *counter;             // [64][kMaxChunks] row-loop task counter of each (wave, chunk)
   int32_t *cur_wave;            // the wave the kernels work on (advanced by wave_end)
+  unsigned long long *raster_words;  // padded scanline words the raster evaluated (a counter)
+  unsigned long long *carea;    // [N] twice each chart's polygon area (Q.8^2), input order
+  unsigned long long *pre2;     // [N] sorted order: carea summed over the atlas's earlier charts
+  unsigned long long *preE;     // [N] sorted order: Hq summed over the atlas's earlier charts
   int32_t *tstate;              // [A][64] row-loop task: 0 running (or not begun), 1 finished
   int32_t *front_save;          // [A][F][wps_stride] frontline of a task between chunks
   int32_t *ctl_save;            // [A][F][16] row state of a task between chunks

@@ -44,7 +44,7 @@ class Request(ctypes.Structure):
 class Tuning(ctypes.Structure):
     _fields_ = [("scale_fanout", ctypes.c_int32), ("raster_warp_items", ctypes.c_int32),
                 ("rowloop_threads", ctypes.c_int32), ("rowloop_ctas", ctypes.c_int32), ("chunks", ctypes.c_int32),
-                ("ms", ctypes.c_float)]
+                ("progressive_bound", ctypes.c_int32), ("ms", ctypes.c_float)]
 
 
 class ServerConfig(ctypes.Structure):
@@ -347,6 +347,11 @@ class Context:
         """Lanes per chart the last pack's prep used (32, 16, 8 or 4: wider
         while its charts leave the GPU's resident warps idle)."""
         return int(self._inspect(INSPECT_REGIONS, 0, 0).view(np.int64)[258])
+
+    def raster_words(self) -> int:
+        """Padded scanline words (columns + rows, every chart and candidate)
+        the last pack's raster evaluated."""
+        return int(self._inspect(INSPECT_REGIONS, 0, 0).view(np.int64)[259])
 
     def pairs(self, scale: int, n: int, atlas: int = 0):
         raw = self._inspect(INSPECT_PAIRS, scale, atlas)

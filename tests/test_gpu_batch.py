@@ -179,6 +179,32 @@ def test_area_bound_keeps_the_result(ctx):
             assert not ok
 
 
+def test_progressive_area_bound_stops_only_failing_candidates(ctx):
+    """Every candidate up to the area bound's top in one wave: each one that
+    ends without success -- some stopped by the progressive area bound
+    before their rows overflow -- fails in the oracle too, and the bound
+    does stop some of them early."""
+    sets = mixed_batch()[:5] + [synth.stars(21, 600, 1024), synth.stars(22, 900, 1024)]
+    p = tabi.params_default(scale_fanout=64)
+    st, res = ctx.pack_batch(sets, p)
+    assert st == tabi.TABI_OK
+    op = oracle_params(p)
+    early = 0
+    for a, (cs, r) in enumerate(zip(sets, res)):
+        compare(cs, r, op)
+        jtop = ctx.regions(a)[2]
+        rec = oracle.prep(cs, op)
+        perm = oracle.sort(rec)
+        for j in range(jtop, -1, -1):
+            hdr, _ = ctx.scale_result(j, cs.n, a)
+            if hdr[6] != 1 or hdr[0]:
+                continue  # abandoned, or successful
+            ok, _, ost = oracle.pack_scale(rec, perm, cs.atlas_w, cs.atlas_h, 16 * (j + 1), op)
+            assert not ok, (cs.name, j)
+            early += int(hdr[5] < int(ost[4]))  # stopped with fewer charts placed than at the overflow
+    assert early > 0
+
+
 def test_batch_rejects_bad_requests_alone(ctx):
     """A request that fails the host checks, and one with an invalid chart,
     fail alone; the other atlases of the batch are unaffected."""
