@@ -636,13 +636,14 @@ __global__ void __launch_bounds__(NT) rowloop_kernel(const Pack *__restrict__ pp
         }
 
         // ---- I: progressive area bound (exact; an addition to the paper) -----
-        // Every later chart is dropped onto the frontline, so its padded
-        // envelope lies between front[x] and the padded atlas bottom Hp (or
-        // the candidate fails), and padded envelopes are disjoint; a
-        // connected polygon of area A and larger extent E dilated by g covers
-        // at least A + 2gE + 4g^2.  Once the charts not yet placed cannot
-        // fit that way into the area under the frontline, the candidate
-        // fails now instead of rows later.
+        // Every later chart is dropped onto the frontline: in column x its
+        // cover dilated by g lies inside its padded envelope, at or below
+        // front[x], and above the padded atlas bottom Hp (or the candidate
+        // fails).  Placed charts' dilated covers are pairwise disjoint (the
+        // gutter), and a connected polygon of area A and larger extent E
+        // dilated by g covers at least A + 2gE + 4g^2.  Once the charts not
+        // yet placed cannot fit that way into the area under the frontline,
+        // the candidate fails now instead of rows later.
         if (area_bound && !ctl.fail && ctl.row_start < n) {
           int32_t fr = 0;  // free texels under the frontline (front[x] <= Hp here; sides <= 8192)
           for (int x = tid; x < Wp; x += kNT) fr += Hp - front[x];
