@@ -24,6 +24,9 @@ def main(argv=None) -> int:
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--atlases", type=int, default=16)
     ap.add_argument("--fanout", type=int, default=0)
+    ap.add_argument("--direct", action="store_true",
+                    help="launch the kernels directly (stage timing) instead of replaying the graph, whose "
+                         "device-side wave loop profilers cannot enter")
     args = ap.parse_args(argv)
 
     import synth
@@ -37,6 +40,8 @@ def main(argv=None) -> int:
     need = sum(tabi.arena_bytes(cs) for cs in sets)
     ctx = tabi.Context(arena_bytes=min(need, 32 << 30) + (64 << 20))
     params = tabi.params_default(scale_fanout=args.fanout)
+    if args.direct:
+        ctx.stage_times(True)
     ks = None
     for _ in range(args.reps):
         if len(sets) == 1:
