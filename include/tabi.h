@@ -211,7 +211,7 @@ typedef struct tabi_tuning {
                                 consecutive candidates one warp walks)       */
   int32_t rowloop_threads;   /* threads per row-loop CTA: 1024 or 512        */
   int32_t rowloop_ctas;      /* row-loop CTAs per multiprocessor: 1 or 2     */
-  int32_t chunks;            /* chart chunks per wave: 4 or 8 (lazy: a
+  int32_t chunks;            /* chart chunks per wave: 4, 6 or 8 (lazy: a
                                 candidate that fails gets no envelopes for
                                 the charts after its failing row's chunk; 4
                                 is the default for a batch) or 1 (the
@@ -228,7 +228,7 @@ typedef struct tabi_tuning {
  * repeatedly under candidate launch shapes, starting from the default --
  * fan-out 64/16/8/4/2/1, then raster warp-items 16K/64K, then 512-thread
  * row-loop CTAs two per multiprocessor, then the other chunkings (one,
- * four or eight chart chunks per wave), then the progressive area bound
+ * four, six or eight chart chunks per wave), then the progressive area bound
  * switched the other way -- times each (CUDA events, second
  * run of each), drops any shape under which some atlas ends with another
  * status (an arena too small for a wide wave), and keeps the fastest for
@@ -239,6 +239,18 @@ typedef struct tabi_tuning {
  * NULL) receives the choice.  Returns as tabi_pack_batch_device. */
 tabi_status tabi_autotune(tabi_ctx *ctx, const tabi_params *params, tabi_request *reqs, int32_t n_reqs,
                           void *stream, tabi_tuning *out);
+
+/* tabi_pack_batch (device_pointers = 0) or tabi_pack_batch_device
+ * (device_pointers = 1) under an explicit launch shape instead of the
+ * tuned or default one (params->scale_fanout is ignored; shape->ms too):
+ * for reproducible timing and for tests, since no shape changes a result.
+ * scale_fanout 1..64, raster_warp_items >= 1, rowloop_threads 512 or 1024,
+ * rowloop_ctas 1 or 2 (2 only with 512 threads and only if two CTAs fit a
+ * multiprocessor; else 1), chunks 1..8, progressive_bound 0 or 1; anything
+ * else is TABI_ERR_INVALID_ARG.  Returns as tabi_pack_batch. */
+tabi_status tabi_pack_batch_shaped(tabi_ctx *ctx, const tabi_params *params, tabi_request *reqs,
+                                   int32_t n_reqs, void *stream, int32_t device_pointers,
+                                   const tabi_tuning *shape);
 
 /* ---------------------------------------------------------------------
  * Serving: continuous batching of requests as they arrive.

@@ -763,6 +763,23 @@ tabi_status tabi_pack_batch_device(tabi_ctx *ctx, const tabi_params *params, tab
   return run_batch(ctx, params, reqs, n_reqs, stream, false);
 }
 
+tabi_status tabi_pack_batch_shaped(tabi_ctx *ctx, const tabi_params *params, tabi_request *reqs,
+                                   int32_t n_reqs, void *stream, int32_t device_pointers,
+                                   const tabi_tuning *shape) {
+  if (!ctx) return TABI_ERR_INVALID_ARG;
+  if (!shape) return fail(ctx, TABI_ERR_INVALID_ARG, "null shape");
+  if (shape->scale_fanout < 1 || shape->scale_fanout > kScales || shape->raster_warp_items < 1 ||
+      (shape->rowloop_threads != 512 && shape->rowloop_threads != 1024) || shape->rowloop_ctas < 1 ||
+      shape->rowloop_ctas > 2 || shape->chunks < 1 || shape->chunks > kMaxChunks ||
+      (shape->progressive_bound != 0 && shape->progressive_bound != 1))
+    return fail(ctx, TABI_ERR_INVALID_ARG, "bad launch shape");
+  Guard guard(ctx);
+  if (!guard.ok) return fail(ctx, TABI_ERR_BUSY, "context in use");
+  const Tuning t{shape->scale_fanout, shape->raster_warp_items, shape->rowloop_threads, shape->rowloop_ctas,
+                 shape->chunks, shape->progressive_bound};
+  return run_batch_locked(ctx, params, reqs, n_reqs, stream, device_pointers == 0, &t);
+}
+
 tabi_status tabi_autotune(tabi_ctx *ctx, const tabi_params *params, tabi_request *reqs, int32_t n_reqs,
                           void *stream, tabi_tuning *out) {
   if (!ctx) return TABI_ERR_INVALID_ARG;
@@ -818,9 +835,9 @@ tabi_status tabi_autotune(tabi_ctx *ctx, const tabi_params *params, tabi_request
     const tabi_status s = trial(t);
     if (s != TABI_OK) return s;
   }
-  {  // the other chunkings: all charts at once, or lazily in four or eight chunks
+  {  // the other chunkings: all charts at once, or lazily in four, six or eight chunks
     const Tuning base_q = best;
-    for (int Q : {1, 4, 8}) {
+    for (int Q : {1, 4, 6, 8}) {
       if (Q == base_q.Q) continue;
       Tuning t = base_q;
       t.Q = Q;

@@ -4,7 +4,8 @@
 // tasks of the current wave from a device counter.
 //
 // Lazy evaluation: a wave draws the envelopes chunk by chunk of the sorted
-// charts (first 1/8, next 1/8, 1/4, 1/2), and after each chunk the row loop
+// charts (e.g. first 1/8, next 1/8, 1/4, 1/2; see chunk_end), and after
+// each chunk the row loop
 // of every candidate still running commits the rows it can decide with the
 // charts drawn so far, then parks its frontline and row state until the
 // next chunk.  A candidate that fails (most candidates above the answer

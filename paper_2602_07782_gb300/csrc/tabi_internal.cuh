@@ -121,21 +121,22 @@ __host__ __device__ __forceinline__ int64_t region(int a, int j, int which) {
 }
 
 // Chart chunks of a wave (lazy evaluation, see the row loop): chunk q of an
-// atlas of n sorted charts ends at ceil(n e_q / 16) with
-//   Q = 1: e = 16;  Q = 2: e = 4, 16;  Q = 4: e = 2, 4, 8, 16;
-//   Q = 6: e = 2, 4, 6, 8, 12, 16;  Q = 8: e = 2, 4, ..., 16
-// (the first chunks are short: most candidates above the answer fail early).
+// atlas of n sorted charts ends at ceil(n e_q / 64) with
+//   Q = 1: e = 64;  Q = 2: e = 16, 64;  Q = 4: e = 8, 16, 32, 64;
+//   Q = 6: e = 2, 8, 16, 24, 40, 64;  Q = 8: e = 1, 2, 4, 8, 16, 24, 40, 64
+// (the first chunks are short -- the sorted charts come tallest first, and
+// a candidate far above the answer fails within its first rows).
 constexpr int kMaxChunks = 8;
 __host__ __device__ __forceinline__ int chunk_end(int n, int q, int Q) {
   int e;
   switch (Q) {
-    case 1: e = 16; break;
-    case 2: e = q ? 16 : 4; break;
-    case 4: e = 2 << q; break;
-    case 6: e = q < 4 ? 2 * (q + 1) : (q == 4 ? 12 : 16); break;
-    default: e = 2 * (q + 1); break;
+    case 1: e = 64; break;
+    case 2: e = q ? 64 : 16; break;
+    case 4: e = 8 << q; break;
+    case 6: { constexpr int t[6] = {2, 8, 16, 24, 40, 64}; e = t[q]; break; }
+    default: { constexpr int t[8] = {1, 2, 4, 8, 16, 24, 40, 64}; e = t[q]; break; }
   }
-  return q == Q - 1 ? n : (int)(((int64_t)n * e + 15) >> 4);
+  return q == Q - 1 ? n : (int)(((int64_t)n * e + 63) >> 6);
 }
 
 // Candidates of atlas a in wave w: ranks r = w F .. w F + F - 1 below the

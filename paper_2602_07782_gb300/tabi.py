@@ -76,7 +76,7 @@ CHART_INFO_DTYPE = np.dtype([
 
 EXPORTS = ["tabi_params_default", "tabi_ctx_create", "tabi_ctx_destroy", "tabi_last_error",
            "tabi_status_str", "tabi_arena_bytes", "tabi_pack", "tabi_pack_device", "tabi_pack_batch",
-           "tabi_pack_batch_device", "tabi_autotune", "tabi_inspect", "tabi_inspect_atlas",
+           "tabi_pack_batch_device", "tabi_pack_batch_shaped", "tabi_autotune", "tabi_inspect", "tabi_inspect_atlas",
            "tabi_stage_times", "tabi_server_config_default", "tabi_server_create", "tabi_server_destroy",
            "tabi_submit", "tabi_poll", "tabi_wait", "tabi_server_get_stats"]
 STAGES = ["prep", "sort", "layout", "raster", "hcompact", "rowloop", "select", "pack"]
@@ -112,6 +112,8 @@ def load(path: str = LIB_PATH):
         getattr(lib, f).restype = ctypes.c_int
     lib.tabi_autotune.argtypes = [P, P, P, i32, P, P]
     lib.tabi_autotune.restype = ctypes.c_int
+    lib.tabi_pack_batch_shaped.argtypes = [P, P, P, i32, P, i32, P]
+    lib.tabi_pack_batch_shaped.restype = ctypes.c_int
     lib.tabi_server_config_default.argtypes = [P]
     lib.tabi_server_create.argtypes = [ctypes.POINTER(P), P]
     lib.tabi_server_create.restype = ctypes.c_int
@@ -261,9 +263,10 @@ class Context:
             raise RuntimeError(f"tabi_stage_times failed: {self.last_error()}")
         return dict(zip(STAGES, ms)), dict(zip(STAGES, launches)), int(packs.value)
 
-    def pack_batch(self, sets, params: Params | None = None, stream=None, outs=None):
-        """tabi_pack_batch with host buffers: one ChartSet per atlas.  Returns
-        (call status, [PackResult per atlas])."""
+    def pack_batch(self, sets, params: Params | None = None, stream=None, outs=None, shape: Tuning | None = None):
+        """tabi_pack_batch with host buffers: one ChartSet per atlas (with an
+        explicit launch shape: tabi_pack_batch_shaped).  Returns (call status,
+        [PackResult per atlas])."""
         params = params or params_default()
         keep = []
         reqs = (Request * len(sets))()
@@ -274,8 +277,12 @@ class Context:
             keep += [offs, verts]
             reqs[i] = Request(cs.atlas_w, cs.atlas_h, cs.n, cs.nv, offs.ctypes.data, verts.ctypes.data,
                               outs[i].ctypes.data, 0, 0)
-        st = self.lib.tabi_pack_batch(self.h, ctypes.byref(params), reqs, len(sets),
-                                      ctypes.c_void_p(_stream_ptr(stream)))
+        if shape is None:
+            st = self.lib.tabi_pack_batch(self.h, ctypes.byref(params), reqs, len(sets),
+                                          ctypes.c_void_p(_stream_ptr(stream)))
+        else:
+            st = self.lib.tabi_pack_batch_shaped(self.h, ctypes.byref(params), reqs, len(sets),
+                                                 ctypes.c_void_p(_stream_ptr(stream)), 0, ctypes.byref(shape))
         return int(st), [PackResult(int(r.status), int(r.scale_k), o) for r, o in zip(reqs, outs)]
 
     def pack_batch_requests(self, reqs, params: Params | None = None, stream=None, device: bool = True):

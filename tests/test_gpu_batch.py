@@ -65,6 +65,36 @@ def test_batch_parity(ctx, fanout):
         compare(cs, r, op)
 
 
+SHAPES = [  # (fan-out, raster warp-items, row-loop threads, CTAs per SM, chunks, progressive bound)
+    (2, 32768, 1024, 1, 4, 1), (2, 65536, 1024, 1, 6, 1), (1, 16384, 1024, 1, 8, 1), (3, 32768, 512, 2, 2, 1),
+    (8, 4096, 512, 1, 1, 0), (64, 32768, 1024, 1, 8, 0), (5, 100, 1024, 1, 3, 1), (16, 32768, 512, 2, 7, 0),
+]
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=[",".join(map(str, s)) for s in SHAPES])
+def test_every_launch_shape_gives_the_oracle_result(ctx, shape):
+    """No launch shape changes a result: each one, forced through
+    tabi_pack_batch_shaped, packs every atlas of a batch exactly as the
+    oracle does."""
+    sets = mixed_batch()
+    t = tabi.Tuning(*shape, 0.0)
+    p = tabi.params_default()
+    st, res = ctx.pack_batch(sets, p, shape=t)
+    assert st == tabi.TABI_OK, ctx.last_error()
+    op = oracle_params(p)
+    for cs, r in zip(sets, res):
+        compare(cs, r, op)
+
+
+def test_bad_launch_shapes_are_refused(ctx):
+    sets = mixed_batch()[:2]
+    p = tabi.params_default()
+    for bad in [(0, 32768, 1024, 1, 4, 1), (2, 0, 1024, 1, 4, 1), (2, 32768, 256, 1, 4, 1),
+                (2, 32768, 1024, 3, 4, 1), (2, 32768, 1024, 1, 9, 1), (2, 32768, 1024, 1, 4, 2)]:
+        st, _ = ctx.pack_batch(sets, p, shape=tabi.Tuning(*bad, 0.0))
+        assert st == tabi.TABI_ERR_INVALID_ARG, bad
+
+
 def test_batch_same_as_alone(ctx):
     sets = mixed_batch()
     p = tabi.params_default(scale_fanout=8)
