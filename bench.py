@@ -143,10 +143,10 @@ def cpu_baseline(sets, budget_s: float = 15.0):
             "sample": f"the first {packs} atlases of the batch ({charts} charts), {dt:.1f} s on one host core"}
 
 
-# DRAM traffic of raster_kernel from one ncu capture of a launch whose
-# envelopes exceed L2, with a digest of the kernel's sources at capture
-# time; None while no such capture of the current kernel exists (the
-# chunked launches of the batch mostly stay in L2).
+# DRAM read + write of every raster_kernel launch of one batch of this
+# workload (ncu, direct launches, the launch shape below), with a digest of
+# the kernel's sources at capture time; the bench reports it per launch
+# while the sources and the shape match, else null.
 RASTER_NCU = None
 
 
@@ -358,6 +358,10 @@ def run_ours(args, rank, world, local, sets):
     jtops = [ctx.regions(a)[2] for a in range(A)]
     alg = algorithmic_bytes(sets, ks, jtops, F)
     raster_words = ctx.raster_words()  # padded scanline words the (last, stage-timed) batch rasterized
+    raster_cols = ctx.raster_column_words()
+    # the raster's bytes from the words it evaluated: 8 B per column word
+    # (word + owner index), 4 B per row word
+    alg["raster"] = 8 * raster_cols + 4 * (raster_words - raster_cols)
     kernels = {s: stage_ms[s] for s in ("prep", "sort", "layout", "raster", "hcompact", "rowloop", "select")}
     dom = max(kernels, key=kernels.get)
     peaks = {}
@@ -374,12 +378,13 @@ def run_ours(args, rank, world, local, sets):
     # traffic per launch: the captured launch's DRAM / algorithmic ratio
     # times this launch's algorithmic bytes, while the kernel is unchanged
     traffic = None
-    if dom == "raster" and RASTER_NCU and raster_sources_digest() == RASTER_NCU["sources_sha256_16"]:
-        traffic = int(dom_bytes * RASTER_NCU["dram_bytes"] / RASTER_NCU["algorithmic_bytes"])
+    if (dom == "raster" and RASTER_NCU and raster_sources_digest() == RASTER_NCU["sources_sha256_16"]
+            and all(tuning.get(k) == v for k, v in RASTER_NCU["shape"].items())):
+        traffic = int(RASTER_NCU["dram_bytes_per_step"] / launches_dom)
     hbm_view = {"kernel": dom, "bound": "hbm", "achieved": round(achieved_gbs, 2), "peak": hbm_peak,
                 "unit": "GB/s", "frac": round(achieved_gbs / hbm_peak, 5), "traffic": traffic,
-                "traffic_source": ("ncu capture scaled by algorithmic bytes" if traffic else
-                                   "null: no capture of the current kernel with an envelope set larger than L2"),
+                "traffic_source": ("ncu capture of this workload's raster launches (profiles/raster_kernel_batch256.md)"
+                                   if traffic else "null: no ncu capture of the current kernel at this launch shape"),
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.8 TB/s",
                 "algorithmic_bytes_per_launch": int(dom_bytes), "avg_launch_ms": round(dom_ms, 4),
                 "launches_per_step": int(launches_dom)}

@@ -336,9 +336,10 @@ tabi_status tabi_server_get_stats(tabi_server *srv, tabi_server_stats *out);
  *                        largest the area bound allows, -1 if none; regions
  *                        exist for the candidates up to it), then int64
  *                        waves the last pack ran, int64 prep lanes per
- *                        chart it used and int64 padded scanline words
+ *                        chart it used, int64 padded scanline words
  *                        (columns + rows over every chart and candidate)
- *                        its raster evaluated (all three batch-wide);
+ *                        its raster evaluated and int64 the column words
+ *                        among them (all four batch-wide);
  *   TABI_INSPECT_PAIRS   int32[n] compacting distance d(s, s+1) then
  *                        uint8[n] flags (bit0 CannotMoveAbove(s, s+1),
  *                        bit1 CannotMoveAbove(s+1, s)) for `scale`;

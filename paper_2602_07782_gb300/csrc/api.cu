@@ -86,7 +86,7 @@ __global__ void init_kernel(const Pack *__restrict__ pp) {
     for (int i = t; i < kScales * kMaxChunks; i += blockDim.x) p.counter[i] = 0;
     if (t == 0) {
       *p.cur_wave = 0;
-      *p.raster_words = 0;
+      p.raster_words[0] = p.raster_words[1] = 0;
     }
   }
   for (int at = blockIdx.x; at < p.A; at += gridDim.x) {
@@ -483,7 +483,7 @@ tabi_status batch_launch(tabi_ctx *ctx, const tabi_params *params, tabi_request 
   p.act_chart = cv.take<int32_t>(n);
   p.counter = cv.take<int32_t>(kScales * kMaxChunks);
   p.cur_wave = cv.take<int32_t>(1);
-  p.raster_words = cv.take<unsigned long long>(1);
+  p.raster_words = cv.take<unsigned long long>(2);
   p.carea = cv.take<unsigned long long>(n);
   p.pre2 = cv.take<unsigned long long>(n);
   p.preE = cv.take<unsigned long long>(n);
@@ -916,23 +916,24 @@ tabi_status tabi_inspect_atlas(tabi_ctx *ctx, int32_t atlas, int32_t what, int32
   const int64_t js = (int64_t)scale * p.N + ad.cb;
   // region starts and sizes of this atlas (small reads, needed to size ENV),
   // then its top candidate
-  int64_t reg[2 * kScales * 2 + 4];
+  int64_t reg[2 * kScales * 2 + 5];
   cudaError_t e = cudaMemcpy(reg, p.abase + region(at, 0, 0), sizeof(int64_t) * 2 * kScales,
                              cudaMemcpyDeviceToHost);
   if (e == cudaSuccess)
     e = cudaMemcpy(reg + 2 * kScales, p.atot + region(at, 0, 0), sizeof(int64_t) * 2 * kScales,
                    cudaMemcpyDeviceToHost);
   int32_t jt = 0, waves = 0;
-  unsigned long long rwords = 0;
+  unsigned long long rwords[2] = {0, 0};
   if (e == cudaSuccess) e = cudaMemcpy(&jt, p.jtop + at, sizeof(int32_t), cudaMemcpyDeviceToHost);
   if (e == cudaSuccess) e = cudaMemcpy(&waves, p.cur_wave, sizeof(int32_t), cudaMemcpyDeviceToHost);
   if (e == cudaSuccess)
-    e = cudaMemcpy(&rwords, p.raster_words, sizeof(rwords), cudaMemcpyDeviceToHost);
+    e = cudaMemcpy(rwords, p.raster_words, sizeof(rwords), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "inspect copy");
   reg[4 * kScales] = jt;
   reg[4 * kScales + 1] = waves;
   reg[4 * kScales + 2] = p.prep_group;
-  reg[4 * kScales + 3] = (int64_t)rwords;
+  reg[4 * kScales + 3] = (int64_t)rwords[0];
+  reg[4 * kScales + 4] = (int64_t)rwords[1];
   const int64_t words[2] = {reg[2 * kScales + 2 * scale], reg[2 * kScales + 2 * scale + 1]};
   struct Piece {
     const void *src;

@@ -85,10 +85,10 @@ __global__ void __launch_bounds__(kRasterThreads, 4) raster_kernel(const Pack *_
   const bool all = q == 0 || (p.flags & TABI_F_EVAL_ALL);  // later chunks: running candidates only
   const int g = p.g;
   rmath::AxisK &a0 = axk[wib][0], &a1 = axk[wib][1];
-  __shared__ unsigned long long cta_words;  // scanline words of this CTA (one counter add per CTA)
-  if (threadIdx.x == 0) cta_words = 0;
+  __shared__ unsigned long long cta_words[2];  // scanline and column words of this CTA (one add per CTA)
+  if (threadIdx.x < 2) cta_words[threadIdx.x] = 0;
   __syncthreads();
-  unsigned long long words = 0;
+  unsigned long long words = 0, cols = 0;
   for (int64_t it = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; it < items; it += nwarps) {
     const int s = p.act_chart[it / ngroups];
     const int at = p.catl[s];
@@ -144,12 +144,16 @@ __global__ void __launch_bounds__(kRasterThreads, 4) raster_kernel(const Pack *_
       warp_axis(a1, g, p.pool + rbase + p.rowstart[js]);
       if (lane == 0) p.meta[js * 4 + 3] = maxbot;  // w', h' and the column start come from the layout
       words += (unsigned long long)(a0.len + a1.len + 4 * g);
+      cols += (unsigned long long)(a0.len + 2 * g);
       __syncwarp();
     }
   }
-  if (lane == 0 && words) atomicAdd(&cta_words, words);
+  if (lane == 0 && words) {
+    atomicAdd(&cta_words[0], words);
+    atomicAdd(&cta_words[1], cols);
+  }
   __syncthreads();
-  if (threadIdx.x == 0 && cta_words) atomicAdd(p.raster_words, cta_words);
+  if (threadIdx.x < 2 && cta_words[threadIdx.x]) atomicAdd(p.raster_words + threadIdx.x, cta_words[threadIdx.x]);
 }
 
 // Exclusive block scan of the pair (x, y); every thread also gets the

@@ -106,7 +106,7 @@ struct Pack {
   int32_t *act_chart;           // [N] their charts (global sorted index)
   int32_t *counter;             // [64][kMaxChunks] row-loop task counter of each (wave, chunk)
   int32_t *cur_wave;            // the wave the kernels work on (advanced by wave_end)
-  unsigned long long *raster_words;  // padded scanline words the raster evaluated (a counter)
+  unsigned long long *raster_words;  // [2] padded scanline words / column words the raster evaluated
   unsigned long long *carea;    // [N] twice each chart's polygon area (Q.8^2), input order
   unsigned long long *pre2;     // [N] sorted order: carea summed over the atlas's earlier charts
   unsigned long long *preE;     // [N] sorted order: Hq summed over the atlas's earlier charts

@@ -360,6 +360,10 @@ class Context:
         the last pack's raster evaluated."""
         return int(self._inspect(INSPECT_REGIONS, 0, 0).view(np.int64)[259])
 
+    def raster_column_words(self) -> int:
+        """Padded column words among them (the rest are row words)."""
+        return int(self._inspect(INSPECT_REGIONS, 0, 0).view(np.int64)[260])
+
     def pairs(self, scale: int, n: int, atlas: int = 0):
         raw = self._inspect(INSPECT_PAIRS, scale, atlas)
         d = raw[:4 * n].view(np.int32)
