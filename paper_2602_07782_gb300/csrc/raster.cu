@@ -68,7 +68,7 @@ __device__ __forceinline__ int32_t warp_axis(const rmath::AxisK &ak, int g, uint
 // Warp-items: (chart of an atlas still searching, run of G consecutive
 // candidates of the atlas's wave range).  G is chosen so that the wave has
 // about raster_items warp-items (a tuned launch shape).
-__global__ void __launch_bounds__(kRasterThreads, 4) raster_kernel(const Pack *__restrict__ pp, int q, int nj) {
+__global__ void __launch_bounds__(kRasterThreads, 3) raster_kernel(const Pack *__restrict__ pp, int q, int nj) {
   __shared__ rmath::AxisK axk[kRasterWarps][2];
   const Pack &p = *pp;
   const int wave = *(volatile const int32_t *)p.cur_wave;
@@ -477,7 +477,8 @@ void launch_plan(const Pack *dp, const Launch &L, int q, cudaStream_t st) {
 }
 
 void launch_raster(const Pack *dp, const Launch &L, int q, int F, cudaStream_t st) {
-  raster_kernel<<<L.sms * 16, kRasterThreads, 0, st>>>(dp, q, F);
+  // persistent: the three 256-thread CTAs that fit a multiprocessor at 80 registers
+  raster_kernel<<<L.sms * 3, kRasterThreads, 0, st>>>(dp, q, F);
 }
 
 constexpr int kHcGroup = 16;
