@@ -343,13 +343,61 @@ __device__ __forceinline__ void prep_chart(const Pack &p, int c) {
   }
 }
 
-// one group of G lanes per chart, grid-stride over the batch's charts
+// One group of G lanes per chart.  Groups narrower than a warp run loops
+// as long as their chart's vertex count, so a CTA takes tiles of charts and
+// orders each tile by vertex count (a counting sort in shared memory)
+// before its groups take them: the charts of one warp then have similar
+// loop lengths.  The order does not matter otherwise (charts are
+// independent).
+constexpr int kPrepThreads = 256, kPrepTile = 512, kPrepKeys = 128;
 template <int G>
-__global__ void __launch_bounds__(256, 2) prep_kernel(const Pack *__restrict__ pp) {
+__global__ void __launch_bounds__(kPrepThreads, 2) prep_kernel(const Pack *__restrict__ pp) {
   const Pack &p = *pp;
-  const int64_t groups = ((int64_t)gridDim.x * blockDim.x) / G;
-  for (int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G; c < p.N; c += groups)
-    prep_chart<G>(p, (int)c);
+  if constexpr (G == 32) {
+    const int64_t groups = ((int64_t)gridDim.x * blockDim.x) / G;
+    for (int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G; c < p.N; c += groups)
+      prep_chart<G>(p, (int)c);
+  } else {
+    __shared__ int32_t order[kPrepTile];
+    __shared__ uint8_t key[kPrepTile];
+    __shared__ int32_t cnt[kPrepKeys];
+    constexpr int kGroups = kPrepThreads / G;
+    const int tid = threadIdx.x;
+    for (int64_t base = (int64_t)blockIdx.x * kPrepTile; base < p.N; base += (int64_t)gridDim.x * kPrepTile) {
+      const int m = (int)min((int64_t)kPrepTile, p.N - base);
+      for (int i = tid; i < kPrepKeys; i += kPrepThreads) cnt[i] = 0;
+      __syncthreads();
+      for (int i = tid; i < m; i += kPrepThreads) {
+        const int c = (int)(base + i);
+        const AtlasDesc &ad = p.atl[p.catl[c]];
+        const int lc = c - ad.cb;
+        const int64_t nv = (int64_t)ad.offsets[lc + 1] - ad.offsets[lc];  // checked in prep_chart
+        const int k = nv < 0 ? 0 : (nv >= kPrepKeys ? kPrepKeys - 1 : (int)nv);
+        key[i] = (uint8_t)k;
+        atomicAdd(&cnt[k], 1);
+      }
+      __syncthreads();
+      if (tid < 32) {  // exclusive scan of the key counts (four per lane)
+        int v[4], sum = 0;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) { v[r] = cnt[4 * tid + r]; sum += v[r]; }
+        int incl = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int u = __shfl_up_sync(0xffffffffu, incl, o);
+          if (tid >= o) incl += u;
+        }
+        int run = incl - sum;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) { cnt[4 * tid + r] = run; run += v[r]; }
+      }
+      __syncthreads();
+      for (int i = tid; i < m; i += kPrepThreads) order[atomicAdd(&cnt[key[i]], 1)] = (int)(base + i);
+      __syncthreads();
+      for (int i = tid / G; i < m; i += kGroups) prep_chart<G>(p, order[i]);
+      __syncthreads();  // the tile's arrays are refilled next
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -479,10 +527,10 @@ __global__ void gather_kernel(const Pack *__restrict__ pp) {
 
 void launch_prep(const Pack *dp, const Launch &L, cudaStream_t st) {
   switch (L.prep_group) {
-    case 32: prep_kernel<32><<<L.sms * 8, 256, 0, st>>>(dp); break;
-    case 16: prep_kernel<16><<<L.sms * 8, 256, 0, st>>>(dp); break;
-    case 8: prep_kernel<8><<<L.sms * 8, 256, 0, st>>>(dp); break;
-    default: prep_kernel<4><<<L.sms * 8, 256, 0, st>>>(dp); break;
+    case 32: prep_kernel<32><<<L.sms * 8, kPrepThreads, 0, st>>>(dp); break;
+    case 16: prep_kernel<16><<<L.sms * 8, kPrepThreads, 0, st>>>(dp); break;
+    case 8: prep_kernel<8><<<L.sms * 8, kPrepThreads, 0, st>>>(dp); break;
+    default: prep_kernel<4><<<L.sms * 8, kPrepThreads, 0, st>>>(dp); break;
   }
 }
 
