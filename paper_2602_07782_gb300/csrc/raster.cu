@@ -375,7 +375,7 @@ __device__ __forceinline__ int32_t group_scan_incl(int32_t v, unsigned gm) {
 // Items are the charts c of chunk q: the pair (c - 1, c) (both charts are
 // drawn by the end of the chunk), and the atlas's last chart's empty pair.
 template <int G>
-__global__ void __launch_bounds__(256) hcompact_kernel(const Pack *__restrict__ pp, int q, int nj) {
+__global__ void __launch_bounds__(256, 8) hcompact_kernel(const Pack *__restrict__ pp, int q, int nj) {
   const Pack &p = *pp;
   const int wave = *(volatile const int32_t *)p.cur_wave;
   const int lane = threadIdx.x & (G - 1);
@@ -483,7 +483,9 @@ void launch_raster(const Pack *dp, const Launch &L, int q, int F, cudaStream_t s
 
 constexpr int kHcGroup = 16;
 void launch_hcompact(const Pack *dp, const Launch &L, int q, int F, cudaStream_t st) {
-  hcompact_kernel<kHcGroup><<<L.sms * 16, 256, 0, st>>>(dp, q, F);
+  // persistent: eight 256-thread CTAs per multiprocessor (full occupancy for a
+  // kernel that waits on its loads)
+  hcompact_kernel<kHcGroup><<<L.sms * 8, 256, 0, st>>>(dp, q, F);
 }
 
 void launch_wave_end(const Pack *dp, cudaGraphConditionalHandle h, bool in_graph, cudaStream_t st) {
