@@ -321,7 +321,9 @@ tabi_status tabi_server_get_stats(tabi_server *srv, tabi_server_stats *out);
  *   TABI_INSPECT_CHARTS  tabi_chart_info[n], input order (prep, Sec. 3.1,
  *                        Sec. 4.1.1, App. A);
  *   TABI_INSPECT_PERM    int32[n]: input index of each sorted position;
- *   TABI_INSPECT_ENV     for candidate index `scale` (k = 16*(scale+1)):
+ *   TABI_INSPECT_ENV     for candidate index `scale` (k = 16*(scale+1);
+ *                        at most the top candidate of REGIONS, else
+ *                        TABI_ERR_INVALID_ARG):
  *                        int64[2] (words of the atlas's column and row
  *                        regions), int32[4n] meta per sorted chart (padded
  *                        width w', padded height h', column start, max

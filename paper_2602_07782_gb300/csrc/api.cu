@@ -946,6 +946,7 @@ tabi_status tabi_inspect_atlas(tabi_ctx *ctx, int32_t atlas, int32_t what, int32
     case TABI_INSPECT_CHARTS: pcs[0] = {p.info + ad.cb, sizeof(tabi_chart_info) * n, false}; break;
     case TABI_INSPECT_PERM: pcs[0] = {p.perm + ad.cb, 4 * n, false}; local_perm = true; break;
     case TABI_INSPECT_ENV:
+      if (scale > jt) return fail(ctx, TABI_ERR_INVALID_ARG, "candidate above the area bound's top: no envelopes");
       pcs[0] = {words, sizeof(words), true};
       pcs[1] = {p.meta + js * 4, 16 * n, false};
       pcs[2] = {p.rowstart + js, 4 * n, false};

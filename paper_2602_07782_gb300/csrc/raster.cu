@@ -103,6 +103,20 @@ __global__ void __launch_bounds__(kRasterThreads, 3) raster_kernel(const Pack *_
     // lanes 24-31 carry the eight corner quantities across the candidates
     rmath::CornerQ cq;
     const bool corner_lane = lane >= 24 && use_o && m > 0;
+    // per chart, kept across the run of candidates: the piece lanes' slice
+    // bounds (registers) and the OBB lanes' scale-free terms (shared)
+    uint32_t pb0 = 0, pb1 = 0, plq = 0, phq = 0;
+    if (lane < 2 * rmath::kK) {
+      const int ax = lane >= rmath::kK, i = lane - ax * rmath::kK;
+      const uint32_t ext = (uint32_t)(ax ? sh.Hq : sh.Wq);
+      pb0 = i * ext / rmath::kK;
+      pb1 = (i + 1) * ext / rmath::kK;
+      plq = (uint32_t)(ax ? sh.llo[i] : sh.tlo[i]);
+      phq = (uint32_t)(ax ? sh.rhi[i] : sh.bhi[i]);
+    } else if (lane < 2 * rmath::kK + 2) {
+      const int ax = lane - 2 * rmath::kK;
+      rmath::setup_obb_fixed(ax ? a1 : a0, ax, m, C, S, kObbDivCos[m], kObbDivSin[m], use_l, use_o);
+    }
     if (corner_lane) {
       int64_t qs, rs;
       rmath::corner_step(lane - 24, C, S, sh.u0, sh.u1, sh.v0, sh.v1, qs, rs);
@@ -120,13 +134,10 @@ __global__ void __launch_bounds__(kRasterThreads, 3) raster_kernel(const Pack *_
       // pieces, lanes 20-21 the OBB line terms, lanes 24-31 the corners
       if (lane < 2 * rmath::kK) {
         const int ax = lane >= rmath::kK, i = lane - ax * rmath::kK;
-        rmath::setup_piece(ax ? a1 : a0, i, ax ? sh.Hq : sh.Wq, k, ax ? sh.llo[i] : sh.tlo[i],
-                           ax ? sh.rhi[i] : sh.bhi[i]);
+        rmath::setup_piece(ax ? a1 : a0, i, pb0, pb1, (uint32_t)k, plq, phq);
       } else if (lane < 2 * rmath::kK + 2) {
         const int ax = lane - 2 * rmath::kK;
-        rmath::setup_obb_base(ax ? a1 : a0, ax, sh.Wq, sh.Hq, k, m, C, S, kObbDivCos[m], kObbDivSin[m], sh.u0,
-                              sh.u1, sh.v0, sh.v1, use_l,
-                              use_o);
+        rmath::setup_obb_k(ax ? a1 : a0, ax, sh.Wq, sh.Hq, k, C, S, sh.u0, sh.u1, sh.v0, sh.v1);
       } else if (corner_lane) {
         const int ax = (lane - 24) >> 2;
         rmath::corner_store(cq, lane - 24, ax ? a1 : a0, (ax ? sh.Hq : sh.Wq) * k);
@@ -203,6 +214,9 @@ __global__ void __launch_bounds__(1024) layout_kernel(const Pack *__restrict__ p
   const int g2 = 2 * p.g;
   for (int64_t item = blockIdx.x; item < (int64_t)p.A * kScales; item += gridDim.x) {
     const int at = (int)(item / kScales), j = (int)(item % kScales);
+    // candidates above the area bound's top are never evaluated (the first
+    // item still builds the atlas's prefix sums)
+    if (j > p.jtop[at] && j != 0) continue;
     const int n = p.atl[at].n, cb = p.atl[at].cb;
     const int64_t k = 16 * (j + 1);
     const int P = (n + 1023) >> 10;

@@ -139,46 +139,56 @@ TABI_HD int32_t fdiv32(int32_t a, int32_t d, float rcp) {
   return q;
 }
 
-// Local-AABB piece i of an axis at scale k.  `ext` = Wq (axis 0) or Hq
-// (axis 1); `lo_q8`, `hi_q8` = the refined piece bounds (tlo/bhi or llo/rhi).
-TABI_HD void setup_piece(AxisK &ak, int i, int64_t ext, int64_t k, int32_t lo_q8, int32_t hi_q8) {
-  const int64_t s0 = (int64_t)i * ext / kK * k, s1 = (int64_t)(i + 1) * ext / kK * k;
-  const int32_t plo = (int32_t)(s0 >> 18);                // floor(s0 / F)
-  const int32_t phi = (int32_t)(((s1 + kF - 1) >> 18) - 1); // ceil(s1 / F) - 1 (>= plo: s1 > s0)
-  const int32_t lo = (int32_t)(((int64_t)lo_q8 * k) >> 18);
-  const int32_t hi = (int32_t)(((int64_t)hi_q8 * k + kF - 1) >> 18);
+// Local-AABB piece i of an axis at scale k, from its slice bounds
+// b0 = floor(i ext / K), b1 = floor((i + 1) ext / K) (ext = Wq or Hq) and
+// the refined piece bounds lo_q8, hi_q8 (tlo/bhi or llo/rhi), all in
+// [0, 2^21): the scaled values stay below 2^31 (k <= 1024), so 32-bit
+// unsigned arithmetic is exact.
+TABI_HD void setup_piece(AxisK &ak, int i, uint32_t b0, uint32_t b1, uint32_t k, uint32_t lo_q8, uint32_t hi_q8) {
+  const uint32_t s0 = b0 * k, s1 = b1 * k;
+  const int32_t plo = (int32_t)(s0 >> 18);                 // floor(s0 / F)
+  const int32_t phi = (int32_t)((s1 + kF - 1) >> 18) - 1;   // ceil(s1 / F) - 1 (>= plo: s1 > s0)
+  const int32_t lo = (int32_t)((lo_q8 * k) >> 18);
+  const int32_t hi = (int32_t)((hi_q8 * k + kF - 1) >> 18);
   ak.piece[i] = make_int4(plo, phi - plo, lo, hi);
 }
 
-// OBB line terms and scanline counts of one axis at scale k.
-TABI_HD void setup_obb_base(AxisK &ak, int axis, int64_t Wq, int64_t Hq, int64_t k, int m, int64_t C,
-                            int64_t S, const Magic &qC, const Magic &qS, int64_t u0, int64_t u1, int64_t v0,
-                            int64_t v1, bool use_l, bool use_o) {
-  const int64_t w = (Wq * k + kF - 1) >> 18, h = (Hq * k + kF - 1) >> 18;
-  ak.len = (int32_t)(axis == 0 ? w : h);
-  ak.len_other = (int32_t)(axis == 0 ? h : w);
-  ak.end = (axis == 0 ? Wq : Hq) * k;
-  ak.clip_c = (ak.end & (kF - 1)) ? ak.len - 1 : -1;
+// OBB terms of one axis that do not depend on the scale (once per chart).
+TABI_HD void setup_obb_fixed(AxisK &ak, int axis, int m, int64_t C, int64_t S, const Magic &qC,
+                             const Magic &qS, bool use_l, bool use_o) {
   ak.use_l = use_l;
   ak.use_o = use_o && m > 0;
-  if (!ak.use_o) return;
-  const int64_t U0 = u0 * k, U1 = u1 * k, V0 = v0 * k, V1 = v1 * k;
   if (axis == 0) {
-    ak.A1 = U0; ak.A2 = V0; ak.B1 = -U1; ak.B2 = -V1;
     ak.b1 = (int32_t)C; ak.d1 = (int32_t)S; ak.b2 = (int32_t)S; ak.d2 = (int32_t)C;
   } else {
-    ak.A1 = U0; ak.A2 = -V1; ak.B1 = -U1; ak.B2 = V0;
     ak.b1 = (int32_t)S; ak.d1 = (int32_t)C; ak.b2 = (int32_t)C; ak.d2 = (int32_t)S;
   }
   ak.q1 = axis == 0 ? qS : qC;  // division by d1, d2
   ak.q2 = axis == 0 ? qC : qS;
-  ak.ah1 = (int32_t)(ak.A1 >> 18); ak.ah2 = (int32_t)(ak.A2 >> 18);
-  ak.bh1 = (int32_t)(ak.B1 >> 18); ak.bh2 = (int32_t)(ak.B2 >> 18);
+}
+
+// OBB line terms and scanline counts of one axis at scale k (after
+// setup_obb_fixed for the same axis and chart).
+TABI_HD void setup_obb_k(AxisK &ak, int axis, int64_t Wq, int64_t Hq, int64_t k, int64_t C, int64_t S,
+                         int64_t u0, int64_t u1, int64_t v0, int64_t v1) {
+  const int64_t w = (Wq * k + kF - 1) >> 18, h = (Hq * k + kF - 1) >> 18;
+  ak.len = (int32_t)(axis == 0 ? w : h);
+  ak.len_other = (int32_t)(axis == 0 ? h : w);
+  const int64_t end = (axis == 0 ? Wq : Hq) * k;
+  ak.end = end;
+  ak.clip_c = (end & (kF - 1)) ? ak.len - 1 : -1;
+  if (!ak.use_o) return;
+  const int64_t U0 = u0 * k, U1 = u1 * k, V0 = v0 * k, V1 = v1 * k;
+  const int64_t A1 = U0, A2 = axis == 0 ? V0 : -V1, B1 = -U1, B2 = axis == 0 ? -V1 : V0;
+  const int64_t b1 = axis == 0 ? C : S, b2 = axis == 0 ? S : C;
+  ak.A1 = A1; ak.A2 = A2; ak.B1 = B1; ak.B2 = B2;
+  ak.ah1 = (int32_t)(A1 >> 18); ak.ah2 = (int32_t)(A2 >> 18);
+  ak.bh1 = (int32_t)(B1 >> 18); ak.bh2 = (int32_t)(B2 >> 18);
   // at X = end: floor(N / (d F)) = floor(floor(N / F) / d), |N| < 2^47
-  ak.cl_n1 = (int32_t)((ak.A1 - ak.end * ak.b1) >> 18);
-  ak.cl_n2 = (int32_t)((ak.A2 + ak.end * ak.b2) >> 18);
-  ak.cu_n1 = (int32_t)((ak.B1 + ak.end * ak.b1) >> 18);
-  ak.cu_n2 = (int32_t)((ak.B2 - ak.end * ak.b2) >> 18);
+  ak.cl_n1 = (int32_t)((A1 - end * b1) >> 18);
+  ak.cl_n2 = (int32_t)((A2 + end * b2) >> 18);
+  ak.cu_n1 = (int32_t)((B1 + end * b1) >> 18);
+  ak.cu_n2 = (int32_t)((B2 - end * b2) >> 18);
 }
 
 // The eight corner quantities (item = axis * 4 + {0: lower value, 1: upper

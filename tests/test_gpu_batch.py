@@ -191,6 +191,19 @@ def test_wave_loop_stops_when_no_atlas_searches(ctx, fanout):
     assert ctx.waves_run() == (64 + fanout - 1) // fanout
 
 
+def test_envelopes_exist_up_to_the_top_candidate_only(ctx):
+    """Candidates above the area bound's top are never evaluated: their
+    envelopes are refused by inspection, the top candidate's are not."""
+    cs = synth.stars(3, 300, 512)
+    st, _ = ctx.pack_batch([cs, synth.plain64(seed=1)], tabi.params_default())
+    assert st == tabi.TABI_OK
+    jt = ctx.regions(0)[2]
+    assert 0 <= jt < 63
+    ctx.envelopes(jt, cs.n, 0)
+    with pytest.raises(RuntimeError):
+        ctx.envelopes(jt + 1, cs.n, 0)
+
+
 def test_area_bound_keeps_the_result(ctx):
     """The top candidate the area bound allows is at least the chosen scale,
     and every candidate above it fails in the oracle too."""
