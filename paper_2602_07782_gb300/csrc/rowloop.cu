@@ -57,6 +57,7 @@ struct Ctl {
   int32_t region_lo, region_hi, knee_max;
   int32_t knee_rows, knees, knee_t[2], stage_lo, stage_hi, abort;
   int32_t t_at, t_j, t_skip;
+  int32_t front_sum;     // the committed frontline summed over the padded columns
   int32_t red[kMaxWarps];
 };
 
@@ -241,9 +242,20 @@ __global__ void __launch_bounds__(NT) rowloop_kernel(const Pack *__restrict__ pp
           ctl.knee_rows = csave[8]; ctl.knees = csave[9];
         }
       }
-      if (tid == 0) { ctl.fail = 0; ctl.prev_maxlen = 0; ctl.abort = 0; }
+      {  // the frontline's sum (atlas sides <= 8192: below 2^31), kept up to date by the commits
+        int32_t fs = 0;
+        if (q > 0 && area_bound)
+          for (int x = tid; x < Wp; x += kNT) fs += front[x];
+        if (area_bound) fs = block_sum<kNW>(fs, ctl);
+        if (tid == 0) { ctl.fail = 0; ctl.prev_maxlen = 0; ctl.abort = 0; ctl.front_sum = fs; }
+      }
       __syncthreads();
       bool deferred = false;
+      // progressive area bound: the atlas's totals (per task) and, loaded in
+      // the selection phase by thread 0, the sums before the next row's first
+      // chart (used after the commit, which hides the loads' latency)
+      const unsigned long long tot2 = area_bound ? p.area2[at] : 0, totE = area_bound ? p.ext_sum[at] : 0;
+      unsigned long long nxt2 = 0, nxtE = 0;
 
       while (true) {
         const int row_start = ctl.row_start, row = ctl.row;
@@ -588,6 +600,10 @@ __global__ void __launch_bounds__(NT) rowloop_kernel(const Pack *__restrict__ pp
             ctl.prev_ltr = dir == 0;
             ctl.row_start = row_start + len;
             ctl.row = row + 1;
+            if (area_bound && row_start + len < n) {
+              nxt2 = p.pre2[cb + row_start + len];
+              nxtE = p.preE[cb + row_start + len];
+            }
           }
         }
         __syncthreads();
@@ -603,6 +619,7 @@ __global__ void __launch_bounds__(NT) rowloop_kernel(const Pack *__restrict__ pp
           const int32_t slo = ctl.stage_lo, shi = ctl.stage_hi;
           const int fA = woff[0] - slo;
           const int fB = woff[len - 1] + wps[len - 1] - slo;
+          int32_t grow = 0;  // this thread's rise of the frontline (telescoping: atomicMax returns the old value)
           if (fB <= shi - slo) {
             for (int f = fA + tid; f < fB; f += kNT) {  // lane per staged column word
               // the word's chart and column, from its staged owner index
@@ -613,7 +630,13 @@ __global__ void __launch_bounds__(NT) rowloop_kernel(const Pack *__restrict__ pp
               const int i = f - (woff[t] - slo);
               if ((unsigned)i >= (unsigned)w) { atomicOr(p.err + at, kErrRow); continue; }
               const int32_t X = dir ? hi - pos[t] - w : lo + pos[t];
-              atomicMax(&front[X + (dir ? w - 1 - i : i)], y[t] + (int32_t)(stage[f] >> 16));
+              const int32_t v = y[t] + (int32_t)(stage[f] >> 16);
+              if (area_bound) {
+                const int32_t old = atomicMax(&front[X + (dir ? w - 1 - i : i)], v);
+                grow += v > old ? v - old : 0;
+              } else {
+                atomicMax(&front[X + (dir ? w - 1 - i : i)], v);
+              }
             }
           } else {
           for (int t = warp; t < len; t += kNW) {
@@ -624,9 +647,16 @@ __global__ void __launch_bounds__(NT) rowloop_kernel(const Pack *__restrict__ pp
             const int32_t yt = y[t];
             for (int i = lane; i < w; i += 32) {
               const uint32_t word = col[dir ? w - 1 - i : i];
-              atomicMax(&front[X + i], yt + (int32_t)(word >> 16));
+              const int32_t v = yt + (int32_t)(word >> 16);
+              const int32_t old = atomicMax(&front[X + i], v);
+              grow += v > old ? v - old : 0;
             }
           }
+          }
+          if (area_bound) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) grow += __shfl_xor_sync(0xffffffffu, grow, o);
+            if (lane == 0 && grow) atomicAdd(&ctl.front_sum, grow);
           }
           const int bits = dir | (hc << 1) | (fold << 2);
           for (int t = tid; t < len; t += kNT) {
@@ -646,13 +676,11 @@ __global__ void __launch_bounds__(NT) rowloop_kernel(const Pack *__restrict__ pp
         // yet placed cannot fit that way into the area under the frontline,
         // the candidate fails now instead of rows later.
         if (area_bound && !ctl.fail && ctl.row_start < n) {
-          int32_t fr = 0;  // free texels under the frontline (front[x] <= Hp here; sides <= 8192)
-          for (int x = tid; x < Wp; x += kNT) fr += Hp - front[x];
-          fr = block_sum<kNW>(fr, ctl);
           if (tid == 0) {
             const int s = ctl.row_start;
+            const int32_t fr = Wp * Hp - ctl.front_sum;  // free texels under the frontline (sides <= 8192)
             const uint64_t kk = 16 * (uint64_t)(j + 1), gg = (uint64_t)g;
-            const unsigned __int128 S2 = p.area2[at] - p.pre2[cb + s], SE = p.ext_sum[at] - p.preE[cb + s];
+            const unsigned __int128 S2 = tot2 - nxt2, SE = totE - nxtE;
             const unsigned __int128 need = S2 * (kk * kk) + ((SE * (2 * gg * kk)) << 19) +
                                            ((unsigned __int128)(4 * gg * gg * (uint64_t)(n - s)) << 37);
             if (need > ((unsigned __int128)(uint32_t)fr << 37)) ctl.fail = 1;
