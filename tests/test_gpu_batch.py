@@ -86,6 +86,19 @@ def test_every_launch_shape_gives_the_oracle_result(ctx, shape):
         compare(cs, r, op)
 
 
+@pytest.mark.parametrize("gutter", [0, 2, 3])
+def test_batch_gutters_with_the_progressive_bound(ctx, gutter):
+    """The area bounds at other gutters (their g terms): a batch with the
+    progressive bound on, every atlas as the oracle packs it."""
+    sets = mixed_batch()
+    p = tabi.params_default(gutter=gutter)
+    st, res = ctx.pack_batch(sets, p, shape=tabi.Tuning(2, 32768, 1024, 1, 4, 1, 0.0))
+    assert st == tabi.TABI_OK, ctx.last_error()
+    op = oracle_params(p)
+    for cs, r in zip(sets, res):
+        compare(cs, r, op)
+
+
 def test_bad_launch_shapes_are_refused(ctx):
     sets = mixed_batch()[:2]
     p = tabi.params_default()
