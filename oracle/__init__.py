@@ -25,22 +25,24 @@ _SRC = os.path.join(_HERE, "tabi_oracle.c")
 _LIBDIR = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_LIBDIR, "libtabi_oracle.so")
 
-K = 10
+K = 10  # local AABBs per axis by default (App. A); the slots of a record hold up to 10
 REC = 128
 # record field offsets (mirror of the enum in tabi_oracle.c)
 R = dict(ORIG=0, MINX=1, MINY=2, W0=3, H0=4, WQ=5, HQ=6, ROT=7, FLIPY=8, FLIPX=9,
          OBBM=10, U0=11, U1=12, V0=13, V1=14, X=15, Y=26, YLO=37, YHI=47, XLO=57,
          XHI=67, TLO=77, BHI=87, LLO=97, RHI=107, ATOP=117, ABOT=118, ALEFT=119,
-         ARIGHT=120, ABL2=121, ABR2=122)
+         ARIGHT=120, ABL2=121, ABR2=122, LK=123)
 
 F_HC, F_BALANCE, F_OBB, F_LAABB = 1, 2, 4, 8
 F_ALL = F_HC | F_BALANCE | F_OBB | F_LAABB
 
 
-def default_params(gutter=1, knee_abs=10, knee_rel=20, lr_sig=10, knee_margin=1, flags=F_ALL):
+def default_params(gutter=1, knee_abs=10, knee_rel=20, lr_sig=10, knee_margin=1, flags=F_ALL, laabb_k=K):
     """Paper defaults: 1-px gutter (Sec. 5), knee thresholds 10 % / 20 % and
-    the 10 % left/right significance (App. A), knee margin 1 texel."""
-    return np.array([gutter, knee_abs, knee_rel, lr_sig, knee_margin, flags], np.int32)
+    the 10 % left/right significance (App. A), knee margin 1 texel, K = 10
+    local AABBs per axis (App. A; Tab. 13 ablates 2 and 5, the oracle takes
+    any K in 1..10)."""
+    return np.array([gutter, knee_abs, knee_rel, lr_sig, knee_margin, flags, laabb_k], np.int32)
 
 
 def build(force: bool = False) -> str:

@@ -11,7 +11,8 @@
  * to check by eye, with no blocking, fusion or reordering:
  *
  *   prep      Sec. 3.1 + Sec. 4.3: AABB, rotate to taller-than-wide;
- *             Sec. 4.1.1 + App. A "Computing Local AABBs": K=10 slices/axis;
+ *             Sec. 4.1.1 + App. A "Computing Local AABBs": K slices/axis
+ *             (K = 10, App. A; 2 and 5 are the Tab. 13 ablation);
  *             App. A "Computing Chart Orientations": vertical then horizontal
  *             reflection from the slice areas;
  *             Sec. 4.1.1 "merge ... tighter bound": slice refinement;
@@ -44,7 +45,8 @@
 #include <stdlib.h>
 #include <string.h>
 
-#define OR_K 10          /* local AABBs per axis (App. A / Tab. 13 default) */
+#define OR_K 10          /* most local AABBs per axis (App. A default; Tab. 13
+                            ablates 2 and 5); the count K is a parameter    */
 #define OR_ANGLES 8      /* OBB rotations m*pi/16, m = 0..7 (App. A)          */
 #define OR_REC 128       /* int64 fields per chart record                    */
 #define OR_FIX 262144LL  /* 2^18: scaled units per texel                     */
@@ -59,11 +61,12 @@ enum {
   R_Y = 26,            /* Y[0..K]   y-slice boundaries          */
   R_YLO = 37, R_YHI = 47, R_XLO = 57, R_XHI = 67,  /* raw final slices      */
   R_TLO = 77, R_BHI = 87, R_LLO = 97, R_RHI = 107, /* refined pieces        */
-  R_ATOP = 117, R_ABOT, R_ALEFT, R_ARIGHT, R_ABL2, R_ABR2
+  R_ATOP = 117, R_ABOT, R_ALEFT, R_ARIGHT, R_ABL2, R_ABR2,
+  R_LK = 123           /* K: local AABBs per axis of this record         */
 };
 
 /* ---- params (int32 array) ------------------------------------------------ */
-enum { P_GUTTER = 0, P_KNEE_ABS, P_KNEE_REL, P_LR_SIG, P_KNEE_MARGIN, P_FLAGS, P_COUNT };
+enum { P_GUTTER = 0, P_KNEE_ABS, P_KNEE_REL, P_LR_SIG, P_KNEE_MARGIN, P_FLAGS, P_LAABB_K, P_COUNT };
 #define F_HC      1  /* horizontal compacting configurations (Sec. 4.1.2)       */
 #define F_BALANCE 2  /* direction choice + knees (Sec. 4.2); else alternation   */
 #define F_OBB     4  /* OBB proxy in the envelope (Sec. 4.1.1)                  */
@@ -128,17 +131,17 @@ static int slab_extent(int nv, const int64_t *u, const int64_t *v,
 
 /* K equal intervals per axis: boundaries floor(i*extent/K); slice i is the  */
 /* closed interval [X_i, X_{i+1}].  READING: equal widths up to flooring.    */
-static int local_aabbs(int nv, const int64_t *x, const int64_t *y, int64_t Wq, int64_t Hq,
+static int local_aabbs(int K, int nv, const int64_t *x, const int64_t *y, int64_t Wq, int64_t Hq,
                        int64_t *X, int64_t *Y, int64_t *ylo, int64_t *yhi,
                        int64_t *xlo, int64_t *xhi) {
-  for (int i = 0; i <= OR_K; ++i) {
-    X[i] = (int64_t)i * Wq / OR_K;
-    Y[i] = (int64_t)i * Hq / OR_K;
+  for (int i = 0; i <= K; ++i) {
+    X[i] = (int64_t)i * Wq / K;
+    Y[i] = (int64_t)i * Hq / K;
   }
   int ok = 1;
-  for (int i = 0; i < OR_K; ++i)
+  for (int i = 0; i < K; ++i)
     ok &= slab_extent(nv, x, y, X[i], X[i + 1], &ylo[i], &yhi[i]);
-  for (int j = 0; j < OR_K; ++j)
+  for (int j = 0; j < K; ++j)
     ok &= slab_extent(nv, y, x, Y[j], Y[j + 1], &xlo[j], &xhi[j]);
   return ok;
 }
@@ -161,7 +164,9 @@ void oracle_obb_table(int64_t *out /* 16 */) {
 /* ------------------------------------------------------------------------ */
 static int prep_one(int nv, const int32_t *v, const int32_t *params, int64_t *r) {
   memset(r, 0, sizeof(int64_t) * OR_REC);
-  if (nv < 3) return 1;
+  const int K = params[P_LAABB_K];
+  if (nv < 3 || K < 1 || K > OR_K) return 1;
+  r[R_LK] = K;
   int64_t *x = (int64_t *)malloc(sizeof(int64_t) * nv);
   int64_t *y = (int64_t *)malloc(sizeof(int64_t) * nv);
 
@@ -190,9 +195,9 @@ static int prep_one(int nv, const int32_t *v, const int32_t *params, int64_t *r)
 
   /* App. A "Computing Chart Orientations": top and bottom empty areas between */
   /* the x-slices' bounds and the AABB; reflect vertically if top > bottom.    */
-  local_aabbs(nv, x, y, Wq, Hq, X, Y, ylo, yhi, xlo, xhi);
+  local_aabbs(K, nv, x, y, Wq, Hq, X, Y, ylo, yhi, xlo, xhi);
   int64_t top = 0, bottom = 0;
-  for (int i = 0; i < OR_K; ++i) {
+  for (int i = 0; i < K; ++i) {
     top += (X[i + 1] - X[i]) * ylo[i];
     bottom += (X[i + 1] - X[i]) * (Hq - yhi[i]);
   }
@@ -207,13 +212,13 @@ static int prep_one(int nv, const int32_t *v, const int32_t *params, int64_t *r)
   /* significantly larger, reflect when the bottom area left of the midline  */
   /* exceeds the bottom area right of it (READING: strict; the midline split */
   /* is exact in doubled coordinates).                                        */
-  local_aabbs(nv, x, y, Wq, Hq, X, Y, ylo, yhi, xlo, xhi);
+  local_aabbs(K, nv, x, y, Wq, Hq, X, Y, ylo, yhi, xlo, xhi);
   int64_t left = 0, right = 0, bl2 = 0, br2 = 0;
-  for (int j = 0; j < OR_K; ++j) {
+  for (int j = 0; j < K; ++j) {
     left += (Y[j + 1] - Y[j]) * xlo[j];
     right += (Y[j + 1] - Y[j]) * (Wq - xhi[j]);
   }
-  for (int i = 0; i < OR_K; ++i) {
+  for (int i = 0; i < K; ++i) {
     int64_t e = Hq - yhi[i];
     int64_t a2 = 2 * X[i], b2 = 2 * X[i + 1];
     int64_t lenL = mx64(0, mn64(b2, Wq) - mx64(a2, 0));
@@ -232,9 +237,9 @@ static int prep_one(int nv, const int32_t *v, const int32_t *params, int64_t *r)
   r[R_FLIPX] = flip_x;
 
   /* final local AABBs on the reflected chart */
-  local_aabbs(nv, x, y, Wq, Hq, X, Y, ylo, yhi, xlo, xhi);
-  for (int i = 0; i <= OR_K; ++i) { r[R_X + i] = X[i]; r[R_Y + i] = Y[i]; }
-  for (int i = 0; i < OR_K; ++i) {
+  local_aabbs(K, nv, x, y, Wq, Hq, X, Y, ylo, yhi, xlo, xhi);
+  for (int i = 0; i <= K; ++i) { r[R_X + i] = X[i]; r[R_Y + i] = Y[i]; }
+  for (int i = 0; i < K; ++i) {
     r[R_YLO + i] = ylo[i]; r[R_YHI + i] = yhi[i];
     r[R_XLO + i] = xlo[i]; r[R_XHI + i] = xhi[i];
   }
@@ -243,9 +248,9 @@ static int prep_one(int nv, const int32_t *v, const int32_t *params, int64_t *r)
   /* (last) y-slice whose x-range meets it; each y-slice's left (right) by   */
   /* the first (last) x-slice whose y-range meets it.  READING: the merge is */
   /* a per-slice refinement, closed-interval intersection tests.             */
-  for (int i = 0; i < OR_K; ++i) {
+  for (int i = 0; i < K; ++i) {
     int64_t t2 = INT64_MAX, b2v = INT64_MIN;
-    for (int j = 0; j < OR_K; ++j)
+    for (int j = 0; j < K; ++j)
       if (xlo[j] <= X[i + 1] && xhi[j] >= X[i]) {
         t2 = mn64(t2, Y[j]);
         b2v = mx64(b2v, Y[j + 1]);
@@ -253,9 +258,9 @@ static int prep_one(int nv, const int32_t *v, const int32_t *params, int64_t *r)
     r[R_TLO + i] = mx64(ylo[i], t2);
     r[R_BHI + i] = mn64(yhi[i], b2v);
   }
-  for (int j = 0; j < OR_K; ++j) {
+  for (int j = 0; j < K; ++j) {
     int64_t l2 = INT64_MAX, r2 = INT64_MIN;
-    for (int i = 0; i < OR_K; ++i)
+    for (int i = 0; i < K; ++i)
       if (ylo[i] <= Y[j + 1] && yhi[i] >= Y[j]) {
         l2 = mn64(l2, X[i]);
         r2 = mx64(r2, X[i + 1]);
@@ -360,6 +365,7 @@ int oracle_envelope(const int64_t *r, int32_t k, const int32_t *params, int32_t 
   if (w > cap || h > cap) return 1;
   int flags = params[P_FLAGS];
   int use_l = (flags & F_LAABB) != 0, use_o = (flags & F_OBB) != 0;
+  const int K = (int)r[R_LK];
   int64_t C[OR_ANGLES], S[OR_ANGLES];
   obb_table(C, S);
   int m = (int)r[R_OBBM];
@@ -372,7 +378,7 @@ int oracle_envelope(const int64_t *r, int32_t k, const int32_t *params, int32_t 
     int64_t T = 0, B = h;
     if (use_l) {
       int64_t tl = INT64_MAX, bl = INT64_MIN;
-      for (int i = 0; i < OR_K; ++i)
+      for (int i = 0; i < K; ++i)
         if (r[R_X + i] * k < b && r[R_X + i + 1] * k > a) {
           tl = mn64(tl, r[R_TLO + i]);
           bl = mx64(bl, r[R_BHI + i]);
@@ -414,7 +420,7 @@ int oracle_envelope(const int64_t *r, int32_t k, const int32_t *params, int32_t 
     int64_t L = 0, R = w;
     if (use_l) {
       int64_t ll = INT64_MAX, rl = INT64_MIN;
-      for (int j = 0; j < OR_K; ++j)
+      for (int j = 0; j < K; ++j)
         if (r[R_Y + j] * k < b && r[R_Y + j + 1] * k > a) {
           ll = mn64(ll, r[R_LLO + j]);
           rl = mx64(rl, r[R_RHI + j]);
