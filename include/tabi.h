@@ -67,7 +67,7 @@ typedef enum tabi_status {
                                (tabi_poll)                                    */
 } tabi_status;
 
-#define TABI_PARAMS_VERSION 1
+#define TABI_PARAMS_VERSION 2
 
 /* Feature flags (all on = the paper's method; the others are the ablations
  * of Tab. 3 and the boxes-only Chameleon baseline). */
@@ -111,6 +111,13 @@ typedef struct tabi_params {
                            several.  The result is the same for every
                            value.  Waves share the envelope pools, so a
                            smaller fan-out also needs a smaller arena       */
+  int32_t laabb_count;  /* local AABBs per axis K: 10 (App. A), or 2 or 5 (the
+                           Tab. 13 ablation: fewer slices, looser envelopes,
+                           usually a smaller scale); other values return
+                           TABI_ERR_INVALID_ARG.  Slice s of an extent E is
+                           [floor(s E / K), floor((s + 1) E / K)]; the ten
+                           slots per axis of tabi_chart_info hold slice
+                           floor(t K / 10) in slot t                        */
 } tabi_params;
 
 /* One placed chart; see "Placement semantics" above. */

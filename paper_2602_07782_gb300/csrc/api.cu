@@ -62,7 +62,8 @@ bool valid_params(const tabi_params *p) {
          p->knee_rel_pct <= 100 && p->lr_sig_pct >= 0 && p->lr_sig_pct <= 100 &&
          p->knee_margin >= 0 && p->knee_margin <= 1 << 20 &&
          (p->flags & ~(TABI_F_ALL | TABI_F_EVAL_ALL)) == 0 && p->scale_fanout >= 0 &&
-         p->scale_fanout <= kScales;
+         p->scale_fanout <= kScales &&
+         (p->laabb_count == 2 || p->laabb_count == 5 || p->laabb_count == kSlices);
 }
 
 // Arena bytes of the per-chart and per-atlas arrays of one atlas (all but
@@ -295,7 +296,7 @@ tabi_status capture_graph(tabi_ctx *ctx, const Launch &L, int F, cudaGraph_t *ou
 tabi_status get_graph(tabi_ctx *ctx, const Launch &L, int F, cudaGraphExec_t *out) {
   for (const GraphEntry &g : ctx->graphs)
     if (g.F == F && g.smem == L.rowloop_smem && g.threads == L.rowloop_threads && g.ctas == L.rowloop_ctas &&
-        g.Q == L.Q && g.prep_group == L.prep_group) {
+        g.Q == L.Q && g.prep_group == L.prep_group && g.laabb_k == L.laabb_k) {
       *out = g.exec;
       return TABI_OK;
     }
@@ -306,7 +307,8 @@ tabi_status get_graph(tabi_ctx *ctx, const Launch &L, int F, cudaGraphExec_t *ou
   cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphInstantiate");
-  ctx->graphs.push_back(GraphEntry{F, L.rowloop_smem, L.rowloop_threads, L.rowloop_ctas, L.Q, L.prep_group, exec});
+  ctx->graphs.push_back(
+      GraphEntry{F, L.rowloop_smem, L.rowloop_threads, L.rowloop_ctas, L.Q, L.prep_group, L.laabb_k, exec});
   *out = exec;
   return TABI_OK;
 }
@@ -318,10 +320,11 @@ int ceil_log2(int64_t v) {
 }
 
 // Batch class for the tuning cache: atlas count, mean chart count and
-// widest atlas (powers of two), gutter and method flags.
+// widest atlas (powers of two), gutter, method flags and local-AABB count.
 uint64_t batch_class(int A, int64_t N, int maxW, const tabi_params *params) {
   return (uint64_t)ceil_log2(A) | (uint64_t)ceil_log2((N + A - 1) / A) << 8 | (uint64_t)ceil_log2(maxW) << 16 |
-         (uint64_t)params->gutter << 24 | (uint64_t)(params->flags & TABI_F_ALL) << 32;
+         (uint64_t)params->gutter << 24 | (uint64_t)(params->flags & TABI_F_ALL) << 32 |
+         (uint64_t)params->laabb_count << 40;
 }
 
 // One atlas: every candidate at once, no chunks and no progressive area
@@ -430,6 +433,7 @@ tabi_status batch_launch(tabi_ctx *ctx, const tabi_params *params, tabi_request 
   p.lr_sig = params->lr_sig_pct;
   p.knee_margin = params->knee_margin;
   p.flags = params->flags;
+  p.laabb_k = params->laabb_count;
   // launch shape: forced (autotuner), else tuned for this batch class,
   // else the default; an explicit fan-out in params wins over both
   int maxW = 1;
@@ -524,7 +528,7 @@ tabi_status batch_launch(tabi_ctx *ctx, const tabi_params *params, tabi_request 
   for (int i = 0; i < A; ++i) want = std::max(want, rowloop_smem_wanted(desc[i].W, p.g));
   int smem = (int)((want + 16383) & ~(size_t)16383);
   if (smem > ctx->rowloop_dyn_max) smem = ctx->rowloop_dyn_max;
-  Launch L{ctx->sms, smem, tn.threads == 512 ? 512 : 1024, 1, p.Q, p.prep_group};
+  Launch L{ctx->sms, smem, tn.threads == 512 ? 512 : 1024, 1, p.Q, p.prep_group, p.laabb_k};
   if (L.rowloop_threads == 512 && tn.ctas == 2) {
     // two CTAs per multiprocessor if both fit its shared memory
     const int two = (ctx->smem_per_sm - 2 * (ctx->smem_reserved + rowloop_static_smem())) / 2 & ~255;
@@ -655,6 +659,7 @@ void tabi_params_default(tabi_params *p) {
   p->lr_sig_pct = 10;
   p->knee_margin = 1;
   p->flags = TABI_F_ALL;
+  p->laabb_count = kSlices;
   p->scale_fanout = 0;  // tuned, else 64 for one atlas and 8 for a batch
 }
 

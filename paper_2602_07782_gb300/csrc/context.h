@@ -15,7 +15,7 @@ namespace tabi {
 // row-loop CTA of `smem` dynamic bytes.  Every kernel reads the batch from
 // the record at the arena's start, so the graph serves any batch.
 struct GraphEntry {
-  int F, smem, threads, ctas, Q, prep_group;  // (the progressive bound is read from the record)
+  int F, smem, threads, ctas, Q, prep_group, laabb_k;  // (the progressive bound is read from the record)
   cudaGraphExec_t exec;
 };
 

@@ -53,21 +53,22 @@ __device__ __forceinline__ void floor_ceil_div(int64_t num, int32_t d, int32_t &
 // coordinate over the polygon's boundary inside the slab.  That part of the
 // boundary is spanned by the vertices inside the slab and the points where
 // edges cross its bounding lines, so each lane takes its vertices (exact
-// values) and its edges' crossings of the inner lines B_1 .. B_9 strictly
-// between the edge's ends (a crossing of B_m belongs to slices m-1 and m).
+// values) and its edges' crossings of the inner lines B_1 .. B_{K-1}
+// strictly between the edge's ends (a crossing of B_m belongs to slices
+// m-1 and m).  K is 10 (App. A) or 2 or 5 (the Tab. 13 ablation).
 // Coordinates of the normalised chart lie in [0, 2^21], so everything but
 // the crossing numerators fits 32 bits.  Every lane of the group ends with
 // all values.
-template <int G>
+template <int G, int K>
 __device__ void group_slices(const int32_t *__restrict__ v, int nv, const Xf &xf, bool xaxis,
-                             int64_t ext, int32_t (&lo)[kSlices], int32_t (&hi)[kSlices]) {
+                             int64_t ext, int32_t (&lo)[K], int32_t (&hi)[K]) {
   const int lane = threadIdx.x & (G - 1);
   const unsigned gm = group_mask<G>();
-  int32_t B[kSlices + 1];
+  int32_t B[K + 1];
 #pragma unroll
-  for (int i = 0; i <= kSlices; ++i) B[i] = (int32_t)((int64_t)i * ext / kSlices);
+  for (int i = 0; i <= K; ++i) B[i] = (int32_t)((int64_t)i * ext / K);
 #pragma unroll
-  for (int i = 0; i < kSlices; ++i) { lo[i] = 0x7fffffff; hi[i] = -0x7fffffff - 1; }
+  for (int i = 0; i < K; ++i) { lo[i] = 0x7fffffff; hi[i] = -0x7fffffff - 1; }
   for (int e = lane; e < nv; e += G) {
     const int e1 = (e + 1 == nv) ? 0 : e + 1;
     int64_t x0, y0, x1, y1;
@@ -77,13 +78,13 @@ __device__ void group_slices(const int32_t *__restrict__ v, int nv, const Xf &xf
     const int32_t u1 = (int32_t)(xaxis ? x1 : y1), w1 = (int32_t)(xaxis ? y1 : x1);
     // vertex e, in every slice that contains it
 #pragma unroll
-    for (int i = 0; i < kSlices; ++i)
+    for (int i = 0; i < K; ++i)
       if (B[i] <= u0 && u0 <= B[i + 1]) { lo[i] = min(lo[i], w0); hi[i] = max(hi[i], w0); }
     // crossings of edge (e, e+1) with the inner slab lines
     const int32_t ul = min(u0, u1), ur = max(u0, u1);
     unsigned mask = 0;
 #pragma unroll
-    for (int m = 1; m < kSlices; ++m)
+    for (int m = 1; m < K; ++m)
       if (ul < B[m] && B[m] < ur) mask |= 1u << m;
     if (mask) {
       const int32_t sgn = u1 > u0 ? 1 : -1;
@@ -91,25 +92,31 @@ __device__ void group_slices(const int32_t *__restrict__ v, int nv, const Xf &xf
       while (mask) {
         const int m = __ffs(mask) - 1;
         mask &= mask - 1;
-        const int32_t Bm = (int32_t)((int64_t)m * ext / kSlices);
+        const int32_t Bm = (int32_t)((int64_t)m * ext / K);
         const int64_t num = sgn * ((int64_t)w0 * (u1 - u0) + (int64_t)(Bm - u0) * (w1 - w0));
         int32_t f, c;
         floor_ceil_div(num, d, f, c);
 #pragma unroll
-        for (int i = 0; i < kSlices; ++i)
+        for (int i = 0; i < K; ++i)
           if (i == m - 1 || i == m) { lo[i] = min(lo[i], f); hi[i] = max(hi[i], c); }
       }
     }
   }
 #pragma unroll
-  for (int i = 0; i < kSlices; ++i) {
+  for (int i = 0; i < K; ++i) {
     lo[i] = group_min<G>(lo[i], gm);
     hi[i] = group_max<G>(hi[i], gm);
   }
 }
 
-// One chart (global input index c) of the batch, by a group of G lanes.
-template <int G>
+// One chart (global input index c) of the batch, by a group of G lanes,
+// with K local AABBs per axis, K dividing 10.  The records keep ten slots
+// per axis: slot t holds slice floor(t K / 10).  Slice s of K spans the
+// ten-slice boundaries floor(i E / 10) for i = 10 s / K .. 10 (s + 1) / K
+// (floor(s E / K) = floor((10 s / K) E / 10)), so its slots' open intervals
+// tile its own and an envelope over the ten slots equals one over the K
+// slices: the rasterizer needs no count.
+template <int G, int K>
 __device__ __forceinline__ void prep_chart(const Pack &p, int c) {
   const int lane = threadIdx.x & (G - 1);
   const unsigned gm = group_mask<G>();
@@ -171,14 +178,14 @@ __device__ __forceinline__ void prep_chart(const Pack &p, int c) {
       atomicAdd(p.ext_sum + at, (unsigned long long)Hq);  // Hq >= Wq after the rotation
     }
   }
-  int32_t ylo[kSlices], yhi[kSlices], xlo[kSlices], xhi[kSlices];
+  int32_t ylo[K], yhi[K], xlo[K], xhi[K];
 
   // App. A chart orientation, vertical reflection: top vs bottom empty area
-  group_slices<G>(v, nv, xf, true, Wq, ylo, yhi);
+  group_slices<G, K>(v, nv, xf, true, Wq, ylo, yhi);
   int64_t top = 0, bottom = 0;
 #pragma unroll
-  for (int i = 0; i < kSlices; ++i) {
-    const int64_t wi = (int64_t)(i + 1) * Wq / kSlices - (int64_t)i * Wq / kSlices;
+  for (int i = 0; i < K; ++i) {
+    const int64_t wi = (int64_t)(i + 1) * Wq / K - (int64_t)i * Wq / K;
     top += wi * ylo[i];
     bottom += wi * (Hq - yhi[i]);
   }
@@ -189,7 +196,7 @@ __device__ __forceinline__ void prep_chart(const Pack &p, int c) {
   // reflected axis must be recomputed, their boundaries do not mirror.
   if (xf.fy) {
 #pragma unroll
-    for (int i = 0; i < kSlices; ++i) {
+    for (int i = 0; i < K; ++i) {
       const int32_t lo = (int32_t)Hq - yhi[i], hi = (int32_t)Hq - ylo[i];
       ylo[i] = lo;
       yhi[i] = hi;
@@ -198,18 +205,18 @@ __device__ __forceinline__ void prep_chart(const Pack &p, int c) {
 
   // horizontal reflection: left vs right empty area, else bottom-left vs
   // bottom-right of the midline (doubled coordinates)
-  group_slices<G>(v, nv, xf, false, Hq, xlo, xhi);
+  group_slices<G, K>(v, nv, xf, false, Hq, xlo, xhi);
   int64_t left = 0, right = 0, bl2 = 0, br2 = 0;
 #pragma unroll
-  for (int j = 0; j < kSlices; ++j) {
-    const int64_t hj = (int64_t)(j + 1) * Hq / kSlices - (int64_t)j * Hq / kSlices;
+  for (int j = 0; j < K; ++j) {
+    const int64_t hj = (int64_t)(j + 1) * Hq / K - (int64_t)j * Hq / K;
     left += hj * xlo[j];
     right += hj * (Wq - xhi[j]);
   }
 #pragma unroll
-  for (int i = 0; i < kSlices; ++i) {
+  for (int i = 0; i < K; ++i) {
     const int64_t e = Hq - yhi[i];
-    const int64_t a2 = 2 * ((int64_t)i * Wq / kSlices), b2 = 2 * ((int64_t)(i + 1) * Wq / kSlices);
+    const int64_t a2 = 2 * ((int64_t)i * Wq / K), b2 = 2 * ((int64_t)(i + 1) * Wq / K);
     const int64_t lenL = max((int64_t)0, min(b2, Wq) - max(a2, (int64_t)0));
     const int64_t lenR = max((int64_t)0, min(b2, 2 * Wq) - max(a2, Wq));
     bl2 += e * lenL;
@@ -223,52 +230,52 @@ __device__ __forceinline__ void prep_chart(const Pack &p, int c) {
   // final local AABBs
   if (xf.fx) {
 #pragma unroll
-    for (int j = 0; j < kSlices; ++j) {
+    for (int j = 0; j < K; ++j) {
       const int32_t lo = (int32_t)Wq - xhi[j], hi = (int32_t)Wq - xlo[j];
       xlo[j] = lo;
       xhi[j] = hi;
     }
-    group_slices<G>(v, nv, xf, true, Wq, ylo, yhi);
+    group_slices<G, K>(v, nv, xf, true, Wq, ylo, yhi);
   }
 
   // Sec. 4.1.1 merge: tighten each slice by the other axis' slices (task
-  // t of the group's lanes: x-slice t for t < 10, y-slice t - 16 for
-  // 16 <= t < 26), written out at once
+  // t of the group's lanes: record slot t of the x-slices for t < 10, slot
+  // t - 16 of the y-slices for 16 <= t < 26), written out at once
   for (int t = lane; t < 32; t += G) {
     if (t < kSlices) {
-      const int i = t;
-      const int64_t Xi = (int64_t)i * Wq / kSlices, Xi1 = (int64_t)(i + 1) * Wq / kSlices;
+      const int i = t * K / kSlices;
+      const int64_t Xi = (int64_t)i * Wq / K, Xi1 = (int64_t)(i + 1) * Wq / K;
       int64_t t2 = kI64Max, b2v = kI64Min;
 #pragma unroll
-      for (int j = 0; j < kSlices; ++j)
+      for (int j = 0; j < K; ++j)
         if (xlo[j] <= Xi1 && xhi[j] >= Xi) {
-          const int64_t Yj = (int64_t)j * Hq / kSlices, Yj1 = (int64_t)(j + 1) * Hq / kSlices;
+          const int64_t Yj = (int64_t)j * Hq / K, Yj1 = (int64_t)(j + 1) * Hq / K;
           t2 = min(t2, Yj);
           b2v = max(b2v, Yj1);
         }
       int64_t yl = 0, yh = 0;
 #pragma unroll
-      for (int q = 0; q < kSlices; ++q) if (q == i) { yl = ylo[q]; yh = yhi[q]; }
+      for (int q = 0; q < K; ++q) if (q == i) { yl = ylo[q]; yh = yhi[q]; }
       const int32_t r0 = (int32_t)max(yl, t2), r1 = (int32_t)min(yh, b2v);
-      inf->tlo[i] = r0; inf->bhi[i] = r1;
-      sh->tlo[i] = r0; sh->bhi[i] = r1;
+      inf->tlo[t] = r0; inf->bhi[t] = r1;
+      sh->tlo[t] = r0; sh->bhi[t] = r1;
     } else if (t >= 16 && t < 16 + kSlices) {
-      const int j = t - 16;
-      const int64_t Yj = (int64_t)j * Hq / kSlices, Yj1 = (int64_t)(j + 1) * Hq / kSlices;
+      const int j = (t - 16) * K / kSlices;
+      const int64_t Yj = (int64_t)j * Hq / K, Yj1 = (int64_t)(j + 1) * Hq / K;
       int64_t l2 = kI64Max, r2 = kI64Min;
 #pragma unroll
-      for (int i = 0; i < kSlices; ++i)
+      for (int i = 0; i < K; ++i)
         if (ylo[i] <= Yj1 && yhi[i] >= Yj) {
-          const int64_t Xi = (int64_t)i * Wq / kSlices, Xi1 = (int64_t)(i + 1) * Wq / kSlices;
+          const int64_t Xi = (int64_t)i * Wq / K, Xi1 = (int64_t)(i + 1) * Wq / K;
           l2 = min(l2, Xi);
           r2 = max(r2, Xi1);
         }
       int64_t xl = 0, xh = 0;
 #pragma unroll
-      for (int q = 0; q < kSlices; ++q) if (q == j) { xl = xlo[q]; xh = xhi[q]; }
+      for (int q = 0; q < K; ++q) if (q == j) { xl = xlo[q]; xh = xhi[q]; }
       const int32_t r0 = (int32_t)max(xl, l2), r1 = (int32_t)min(xh, r2);
-      inf->llo[j] = r0; inf->rhi[j] = r1;
-      sh->llo[j] = r0; sh->rhi[j] = r1;
+      inf->llo[t - 16] = r0; inf->rhi[t - 16] = r1;
+      sh->llo[t - 16] = r0; sh->rhi[t - 16] = r1;
     }
   }
 
@@ -335,8 +342,9 @@ __device__ __forceinline__ void prep_chart(const Pack &p, int c) {
     inf->area_bl2 = bl2; inf->area_br2 = br2;
 #pragma unroll
     for (int i = 0; i < kSlices; ++i) {
-      inf->ylo[i] = (int32_t)ylo[i]; inf->yhi[i] = (int32_t)yhi[i];
-      inf->xlo[i] = (int32_t)xlo[i]; inf->xhi[i] = (int32_t)xhi[i];
+      const int q = i * K / kSlices;
+      inf->ylo[i] = (int32_t)ylo[q]; inf->yhi[i] = (int32_t)yhi[q];
+      inf->xlo[i] = (int32_t)xlo[q]; inf->xhi[i] = (int32_t)xhi[q];
     }
     sh->Wq = (int32_t)Wq; sh->Hq = (int32_t)Hq; sh->m = best; sh->pad = 0;
     sh->u0 = bu0; sh->u1 = bu1; sh->v0 = bv0; sh->v1 = bv1;
@@ -350,13 +358,13 @@ __device__ __forceinline__ void prep_chart(const Pack &p, int c) {
 // loop lengths.  The order does not matter otherwise (charts are
 // independent).
 constexpr int kPrepThreads = 256, kPrepTile = 512, kPrepKeys = 128;
-template <int G>
+template <int G, int K>
 __global__ void __launch_bounds__(kPrepThreads, 2) prep_kernel(const Pack *__restrict__ pp) {
   const Pack &p = *pp;
   if constexpr (G == 32) {
     const int64_t groups = ((int64_t)gridDim.x * blockDim.x) / G;
     for (int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G; c < p.N; c += groups)
-      prep_chart<G>(p, (int)c);
+      prep_chart<G, K>(p, (int)c);
   } else {
     __shared__ int32_t order[kPrepTile];
     __shared__ uint8_t key[kPrepTile];
@@ -394,7 +402,7 @@ __global__ void __launch_bounds__(kPrepThreads, 2) prep_kernel(const Pack *__res
       __syncthreads();
       for (int i = tid; i < m; i += kPrepThreads) order[atomicAdd(&cnt[key[i]], 1)] = (int)(base + i);
       __syncthreads();
-      for (int i = tid / G; i < m; i += kGroups) prep_chart<G>(p, order[i]);
+      for (int i = tid / G; i < m; i += kGroups) prep_chart<G, K>(p, order[i]);
       __syncthreads();  // the tile's arrays are refilled next
     }
   }
@@ -525,12 +533,21 @@ __global__ void gather_kernel(const Pack *__restrict__ pp) {
 
 }  // namespace
 
-void launch_prep(const Pack *dp, const Launch &L, cudaStream_t st) {
+template <int K>
+void launch_prep_k(const Pack *dp, const Launch &L, cudaStream_t st) {
   switch (L.prep_group) {
-    case 32: prep_kernel<32><<<L.sms * 8, kPrepThreads, 0, st>>>(dp); break;
-    case 16: prep_kernel<16><<<L.sms * 8, kPrepThreads, 0, st>>>(dp); break;
-    case 8: prep_kernel<8><<<L.sms * 8, kPrepThreads, 0, st>>>(dp); break;
-    default: prep_kernel<4><<<L.sms * 8, kPrepThreads, 0, st>>>(dp); break;
+    case 32: prep_kernel<32, K><<<L.sms * 8, kPrepThreads, 0, st>>>(dp); break;
+    case 16: prep_kernel<16, K><<<L.sms * 8, kPrepThreads, 0, st>>>(dp); break;
+    case 8: prep_kernel<8, K><<<L.sms * 8, kPrepThreads, 0, st>>>(dp); break;
+    default: prep_kernel<4, K><<<L.sms * 8, kPrepThreads, 0, st>>>(dp); break;
+  }
+}
+
+void launch_prep(const Pack *dp, const Launch &L, cudaStream_t st) {
+  switch (L.laabb_k) {
+    case 2: launch_prep_k<2>(dp, L, st); break;
+    case 5: launch_prep_k<5>(dp, L, st); break;
+    default: launch_prep_k<kSlices>(dp, L, st); break;
   }
 }
 

@@ -11,7 +11,7 @@
 
 namespace tabi {
 
-constexpr int kSlices = 10;          // local AABBs per axis (App. A; Tab. 13 default)
+constexpr int kSlices = 10;          // most local AABBs per axis (App. A default; Tab. 13 also 2, 5)
 constexpr int kAngles = 8;           // OBB rotations m*pi/16, m = 0..7 (App. A)
 constexpr int kScales = 64;          // candidates k = 16*(j+1), j = 0..63 (Sec. 5)
 constexpr int kMaxAtlas = 8192;      // atlas side limit (front fits shared memory)
@@ -71,7 +71,7 @@ struct Pack {
   int32_t wps_stride;           // ints per saved frontline (widest atlas, padded)
   int32_t prep_group;           // prep lanes per chart (host record of the launch)
   int32_t prog_bound;           // row loop checks the progressive area bound after each row
-  int32_t pad_;
+  int32_t laabb_k;              // local AABBs per axis (2, 5 or 10; record slot t holds slice t K / 10)
   const AtlasDesc *atl;         // [A]
   int32_t *catl;                // [N] atlas of each chart
   tabi_chart_info *info;        // [N] input order
@@ -160,6 +160,7 @@ struct Launch {
   int rowloop_ctas;    // row-loop CTAs per multiprocessor (512 threads: 1 or 2)
   int Q;               // chart chunks per wave
   int prep_group;      // prep lanes per chart: 32, 16, 8 or 4
+  int laabb_k;         // local AABBs per axis: 2, 5 or 10 (selects the prep kernel)
 };
 void launch_init(const Pack *dp, const Launch &L, cudaStream_t st);
 void launch_prep(const Pack *dp, const Launch &L, cudaStream_t st);

@@ -31,7 +31,8 @@ class Params(ctypes.Structure):
     _fields_ = [("version", ctypes.c_int32), ("gutter", ctypes.c_int32),
                 ("knee_abs_pct", ctypes.c_int32), ("knee_rel_pct", ctypes.c_int32),
                 ("lr_sig_pct", ctypes.c_int32), ("knee_margin", ctypes.c_int32),
-                ("flags", ctypes.c_uint32), ("scale_fanout", ctypes.c_int32)]
+                ("flags", ctypes.c_uint32), ("scale_fanout", ctypes.c_int32),
+                ("laabb_count", ctypes.c_int32)]
 
 
 class Request(ctypes.Structure):

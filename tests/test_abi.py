@@ -3,6 +3,7 @@ entry point include/tabi.h declares; parameter defaults match the paper.
 No compute calls (no GPU here)."""
 from __future__ import annotations
 
+import ctypes
 import os
 import re
 
@@ -37,6 +38,8 @@ def test_param_defaults_follow_the_paper(lib):
     p = tabi.params_default()
     assert (p.gutter, p.knee_abs_pct, p.knee_rel_pct, p.lr_sig_pct) == (1, 10, 20, 10)
     assert p.flags == tabi.F_ALL and p.scale_fanout == 0  # 0: tuned / default launch shape
+    assert p.laabb_count == 10  # local AABBs per axis (App. A)
+    assert ctypes.sizeof(tabi.Params) == 36 and p.version == 2
     assert tabi.status_str(tabi.TABI_ERR_NO_FIT) == "no candidate scale fits"
 
 

@@ -30,7 +30,8 @@ def ctx():
 
 def oracle_params(p):
     return oracle.default_params(gutter=p.gutter, knee_abs=p.knee_abs_pct, knee_rel=p.knee_rel_pct,
-                                 lr_sig=p.lr_sig_pct, knee_margin=p.knee_margin, flags=p.flags & tabi.F_ALL)
+                                 lr_sig=p.lr_sig_pct, knee_margin=p.knee_margin, flags=p.flags & tabi.F_ALL,
+                                 laabb_k=p.laabb_count)
 
 
 def mixed_batch():
@@ -84,6 +85,21 @@ def test_every_launch_shape_gives_the_oracle_result(ctx, shape):
     op = oracle_params(p)
     for cs, r in zip(sets, res):
         compare(cs, r, op)
+
+
+@pytest.mark.parametrize("count", [2, 5])
+def test_batch_laabb_counts(ctx, count):
+    """Tab. 13's local-AABB counts through the captured batch graph (the
+    count picks its prep kernel): every atlas as the oracle packs it at that
+    count, then at the default count again (a graph of its own)."""
+    sets = mixed_batch()
+    for c in (count, 10):
+        p = tabi.params_default(laabb_count=c)
+        st, res = ctx.pack_batch(sets, p)
+        assert st == tabi.TABI_OK, ctx.last_error()
+        op = oracle_params(p)
+        for cs, r in zip(sets, res):
+            compare(cs, r, op)
 
 
 @pytest.mark.parametrize("gutter", [0, 2, 3])

@@ -40,7 +40,8 @@ def gpu_params(**kw):
 def oracle_params(p):
     # the oracle knows the method's flags only (TABI_F_EVAL_ALL is an inspection aid)
     return oracle.default_params(gutter=p.gutter, knee_abs=p.knee_abs_pct, knee_rel=p.knee_rel_pct,
-                                 lr_sig=p.lr_sig_pct, knee_margin=p.knee_margin, flags=p.flags & tabi.F_ALL)
+                                 lr_sig=p.lr_sig_pct, knee_margin=p.knee_margin, flags=p.flags & tabi.F_ALL,
+                                 laabb_k=p.laabb_count)
 
 
 SMALL = {
@@ -56,6 +57,8 @@ SMALL = {
 def _check_prep(ctx, cs, op):
     info = ctx.charts()
     rec = oracle.prep(cs, op)
+    nk = int(op[6])  # local AABBs per axis; record slot t holds slice t * nk // 10
+    slot = np.arange(10) * nk // 10
     assert np.all(info["valid"] == 1)
     for f, col in (("Wq", "WQ"), ("Hq", "HQ"), ("rot90", "ROT"), ("flip_y", "FLIPY"),
                    ("flip_x", "FLIPX"), ("obb_m", "OBBM"), ("u0", "U0"), ("u1", "U1"),
@@ -65,7 +68,7 @@ def _check_prep(ctx, cs, op):
         assert np.array_equal(info[f].astype(np.int64), rec[:, R[col]]), f
     for f, col in (("ylo", "YLO"), ("yhi", "YHI"), ("xlo", "XLO"), ("xhi", "XHI"),
                    ("tlo", "TLO"), ("bhi", "BHI"), ("llo", "LLO"), ("rhi", "RHI")):
-        assert np.array_equal(info[f].astype(np.int64), rec[:, R[col]:R[col] + K]), f
+        assert np.array_equal(info[f].astype(np.int64), rec[:, R[col] + slot]), f
     perm = ctx.perm()
     assert np.array_equal(perm, oracle.sort(rec))
     return rec, perm
@@ -163,6 +166,37 @@ def test_ablation_parity(ctx, flags):
     cs = synth.knees(2, 250, 1024)
     p = gpu_params(flags=flags)
     _compare_pack(cs, ctx.pack(cs, p), oracle_params(p))
+
+
+@pytest.mark.parametrize("count", [2, 5])
+def test_laabb_count_parity(ctx, count):
+    """Tab. 13's local-AABB counts: chart records, envelopes at a spread of
+    candidates and the packing, each against the oracle at that count."""
+    cs = synth.knees(8, 220, 1024)
+    p = gpu_params(flags=tabi.F_ALL | tabi.F_EVAL_ALL, laabb_count=count)
+    op = oracle_params(p)
+    res = ctx.pack(cs, p)
+    assert res.status == tabi.TABI_OK, ctx.last_error()
+    rec, perm = _check_prep(ctx, cs, op)
+    for j in (3, 20, 37, 63):
+        env = ctx.envelopes(j, cs.n)
+        for s in range(cs.n):
+            e = oracle.envelope_padded(rec[perm[s]], 16 * (j + 1), op)
+            wp, hp, top, bot, left, right, mb = env[s]
+            assert (wp, hp) == (e.w, e.h), (j, s)
+            assert np.array_equal(top, e.top) and np.array_equal(bot, e.bot), (j, s)
+            assert np.array_equal(left, e.left) and np.array_equal(right, e.right), (j, s)
+    _compare_pack(cs, res, op)
+    for flags in (tabi.F_ALL & ~tabi.F_OBB, tabi.F_ALL):
+        p = gpu_params(flags=flags, laabb_count=count, scale_fanout=8)
+        _compare_pack(cs, ctx.pack(cs, p), oracle_params(p))
+
+
+def test_laabb_count_rejected(ctx):
+    cs = synth.stars(6, 20, 256)
+    for count in (0, 1, 3, 11):
+        assert ctx.pack(cs, gpu_params(laabb_count=count)).status == tabi.TABI_ERR_INVALID_ARG
+    assert ctx.pack(cs, gpu_params()).status == tabi.TABI_OK
 
 
 @pytest.mark.parametrize("gutter", [0, 2, 3])
