@@ -37,12 +37,16 @@ F_HC, F_BALANCE, F_OBB, F_LAABB = 1, 2, 4, 8
 F_ALL = F_HC | F_BALANCE | F_OBB | F_LAABB
 
 
-def default_params(gutter=1, knee_abs=10, knee_rel=20, lr_sig=10, knee_margin=1, flags=F_ALL, laabb_k=K):
+def default_params(gutter=1, knee_abs=10, knee_rel=20, lr_sig=10, knee_margin=1, flags=F_ALL, laabb_k=K,
+                   topt=10, hybrid_min=10000):
     """Paper defaults: 1-px gutter (Sec. 5), knee thresholds 10 % / 20 % and
     the 10 % left/right significance (App. A), knee margin 1 texel, K = 10
     local AABBs per axis (App. A; Tab. 13 ablates 2 and 5, the oracle takes
-    any K in 1..10)."""
-    return np.array([gutter, knee_abs, knee_rel, lr_sig, knee_margin, flags, laabb_k], np.int32)
+    any K in 1..10), prefix-sum folding past t_opt = 1 % of the atlas height
+    (``topt`` in permille; 0 = off) for atlases of more than 10,000 charts
+    (Sec. 4.4, Tab. 4)."""
+    return np.array([gutter, knee_abs, knee_rel, lr_sig, knee_margin, flags, laabb_k, topt, hybrid_min],
+                    np.int32)
 
 
 def build(force: bool = False) -> str:
@@ -170,12 +174,13 @@ def scale_pairs(rec, perm, k, params=None):
 
 def pack_scale(rec, perm, W, H, k, params=None):
     """Algorithm 5 at one scale.  Returns (success, place[n,6] in sorted order
-    (x, y, mirror, row, compacting on, knee-folded), stats[5]: rows, knee-folded
-    rows, knees found, final max frontline, charts placed)."""
+    (x, y, mirror, row, compacting on, fold: 0 atlas width, 1 knee, 2 prefix-sum
+    tail), stats[6]: rows, knee-folded rows, knees found, final max frontline,
+    charts placed, tail rows)."""
     params = default_params() if params is None else params
     n = rec.shape[0]
     place = np.full((n, 6), -1, np.int32)
-    stats = np.zeros(5, np.int32)
+    stats = np.zeros(6, np.int32)
     ok = lib().oracle_pack_scale(n, _p(np.ascontiguousarray(rec)), _p(np.ascontiguousarray(perm, np.int32)),
                                  int(W), int(H), int(k), _p(params), _p(place), _p(stats))
     if ok < 0:
@@ -187,7 +192,7 @@ def pack_scale(rec, perm, W, H, k, params=None):
 class PackResult:
     status: int  # 0 ok, 1 invalid, 2 no fit
     k: int
-    place: np.ndarray  # int32[n, 10]: x, y, rot90, flip_x, flip_y, mirror, row, sorted pos, hc, knee
+    place: np.ndarray  # int32[n, 10]: x, y, rot90, flip_x, flip_y, mirror, row, sorted pos, hc, fold
     success: np.ndarray | None  # int32[64] per candidate j=1..64 (k=16j) if all_scales
     stats: np.ndarray
 
@@ -199,7 +204,7 @@ def pack(cs, params=None, all_scales=False):
     out_k = np.zeros(1, np.int32)
     place = np.full((cs.n, 10), -1, np.int32)
     succ = np.zeros(64, np.int32)
-    stats = np.zeros(5, np.int32)
+    stats = np.zeros(6, np.int32)
     st = lib().oracle_pack(cs.n, _p(offs), _p(verts), int(cs.atlas_w), int(cs.atlas_h), _p(params),
                            1 if all_scales else 0, _p(out_k), _p(place), _p(succ), _p(stats))
     return PackResult(int(st), int(out_k[0]), place, succ if all_scales else None, stats)

@@ -29,6 +29,9 @@
  *             (CorrectYOffsets, the literal do-while), Algorithm 3
  *             (UpdateKneeLocation), knee detection (App. A "Knee Detection
  *             Parameters") and the hierarchical selection of Sec. 4.2.
+ *   hybrid    Sec. 4.4: past the rows with knees and tall charts, the rest
+ *             of the charts are folded by a prefix sum of their offsets and
+ *             pushed row by row in a fixed direction pattern.
  *   search    Sec. 3.1 / Sec. 5: 64 candidate scales, largest success wins.
  *
  * Integer conventions (the paper fixes no precision):
@@ -66,7 +69,8 @@ enum {
 };
 
 /* ---- params (int32 array) ------------------------------------------------ */
-enum { P_GUTTER = 0, P_KNEE_ABS, P_KNEE_REL, P_LR_SIG, P_KNEE_MARGIN, P_FLAGS, P_LAABB_K, P_COUNT };
+enum { P_GUTTER = 0, P_KNEE_ABS, P_KNEE_REL, P_LR_SIG, P_KNEE_MARGIN, P_FLAGS, P_LAABB_K,
+       P_TOPT, P_HYBRID_MIN, P_COUNT };
 #define F_HC      1  /* horizontal compacting configurations (Sec. 4.1.2)       */
 #define F_BALANCE 2  /* direction choice + knees (Sec. 4.2); else alternation   */
 #define F_OBB     4  /* OBB proxy in the envelope (Sec. 4.1.1)                  */
@@ -642,12 +646,89 @@ static Knee find_knee(int s0, int s1, int ltr, const int64_t *X, const Env *env,
   return kd;
 }
 
+/* Sec. 4.4 "Performance Optimization": the remaining charts folded by a   */
+/* prefix sum, then pushed row by row.  The prefix runs over the offsets    */
+/* between consecutive charts (padded width minus the compacting distance   */
+/* to the next chart; with compaction off, the width), as a recurrence so   */
+/* the compacted fold keeps its rule that chart s+1 never starts left of    */
+/* chart s-1's right edge.  READING of the row break and the "intermediate */
+/* downscaling": a chart whose unwrapped prefix P lies in [rL, (r+1)L)      */
+/* starts tail row r at x = P - rL, with L = W' - wmax + 1 (wmax the widest */
+/* remaining padded chart), so every chart ends inside the padded atlas     */
+/* (x + w' <= L - 1 + wmax = W').  The rows are thus folded to a width      */
+/* shortened by the widest chart instead of overflowing and being scaled    */
+/* down afterwards: every chart keeps the candidate scale, so the scales of */
+/* all charts stay equal and the area-weighted selection of the final scale */
+/* reduces to the largest successful candidate.  READING of FastAtlas's      */
+/* fixed alternation: one left-to-right row, then two right-to-left rows,   */
+/* starting with the first tail row.  Each row is pushed onto the frontline */
+/* exactly like a committed row of Algorithm 5 (mirrored charts in a        */
+/* right-to-left row, Algorithm 2 when compacting).                          */
+typedef struct {
+  int on;
+  int64_t L;        /* fold width of the tail rows                    */
+  int64_t P;        /* unwrapped prefix of the next row's first chart */
+  int64_t Pprev;    /* ... of the chart before it                      */
+  int64_t Wprev;    /* padded width of the chart before it             */
+  int have_prev;    /* a chart precedes the next row in the tail       */
+  int rows;         /* tail rows committed                             */
+} Tail;
+
+/* One tail row from rowStart: fold, push, commit.  Returns the last chart */
+/* of the row; the frontline, placements and the tail state advance.      */
+static int tail_row(int n, int rowStart, int row, Tail *t, int hc, const Env *env,
+                    const int32_t *dnext, const uint8_t *cannotA, const uint8_t *cannotB,
+                    int64_t Wp, int64_t *front, int64_t *X, int64_t *y, int32_t *place) {
+  int64_t B = (t->P / t->L) * t->L; /* the row's start in the unwrapped prefix */
+  int64_t P = t->P, Pp = t->Pprev, Wpv = t->Wprev;
+  int have = t->have_prev;
+  int s = rowStart;
+  for (; s < n && P < B + t->L; ++s) {
+    X[s] = P - B;
+    int64_t nx = P + env[s].wp - (hc ? dnext[s] : 0);
+    if (hc && have && nx < Pp + Wpv) nx = Pp + Wpv;
+    Pp = P;
+    Wpv = env[s].wp;
+    have = 1;
+    P = nx;
+  }
+  int e = s - 1;
+  t->P = P; t->Pprev = Pp; t->Wprev = Wpv; t->have_prev = have;
+  int dir = (t->rows % 3 == 0) ? 0 : 1;
+  for (int c = rowStart; c <= e; ++c)
+    if (dir == 1) X[c] = Wp - X[c] - env[c].wp;
+  for (int c = rowStart; c <= e; ++c) {
+    y[c] = 0;
+    for (int i = 0; i < env[c].wp; ++i) {
+      int ti = dir == 0 ? i : env[c].wp - 1 - i;
+      y[c] = mx64(y[c], front[X[c] + i] - env[c].top[ti]);
+    }
+  }
+  if (hc) correct_y_offsets(rowStart, e, cannotA, cannotB, y);
+  for (int c = rowStart; c <= e; ++c) {
+    for (int i = 0; i < env[c].wp; ++i) {
+      int ti = dir == 0 ? i : env[c].wp - 1 - i;
+      front[X[c] + i] = mx64(front[X[c] + i], y[c] + env[c].bot[ti]);
+    }
+    place[6 * c + 0] = (int32_t)X[c];
+    place[6 * c + 1] = (int32_t)y[c];
+    place[6 * c + 2] = dir;
+    place[6 * c + 3] = row;
+    place[6 * c + 4] = hc;
+    place[6 * c + 5] = 2; /* folded by the prefix sum */
+  }
+  t->rows += 1;
+  return e;
+}
+
 enum { CFG_FULL = 0, CFG_KNEE = 1 };
 
 /* Placements in sorted order, 6 int32 per chart: x, y, mirror (right-to-left   */
-/* row), row index, compacting on in that row, row folded into a knee.           */
+/* row), row index, compacting on in that row, fold (0 atlas width, 1 knee,       */
+/* 2 prefix-sum tail).                                                            */
 /* stats[0] = rows committed, [1] = knee-folded rows, [2] = knees found,          */
-/* [3] = final committed score (max frontline), [4] = charts placed.             */
+/* [3] = final committed score (max frontline), [4] = charts placed,              */
+/* [5] = tail rows (Sec. 4.4).                                                    */
 static int pack_scale_env(int n, const Env *env, const int64_t *hq, const int32_t *dnext,
                           const uint8_t *cannotA, const uint8_t *cannotB,
                           int32_t W, int32_t H, const int32_t *params,
@@ -664,13 +745,41 @@ static int pack_scale_env(int n, const Env *env, const int64_t *hq, const int32_
   }
   for (int f = 0; f < 2; ++f)
     for (int h = 0; h < 2; ++h) pos[f][h] = (int64_t *)malloc(sizeof(int64_t) * n);
-  memset(stats, 0, sizeof(int32_t) * 5);
+  memset(stats, 0, sizeof(int32_t) * 6);
+  /* Sec. 4.4: the hybrid applies to atlases of more than hybrid_min charts */
+  /* (the paper: t_opt = 1 % above 10,000 charts, none below).             */
+  const int hybrid = params[P_TOPT] > 0 && n > params[P_HYBRID_MIN];
+  Tail tail = {0, 1, 0, 0, 0, 0, 0};
 
   int rowStart = 0, overflow = 0, row = 0;
   int prev_ltr = 0; /* READING: direction ties alternate, the first row left-to-right */
   int64_t committed = 0;
   Knee kd = {0, 1, 0, 0};
   while (rowStart < n && !overflow) {
+    /* Sec. 4.4: switch to prefix-sum folding once no knee is live and the  */
+    /* row's tallest chart (its first) is below t_opt of the atlas height   */
+    /* (READING: its scaled height, without gutters; t_opt in permille).    */
+    if (hybrid && !tail.on && !kd.valid &&
+        1000 * ((int64_t)env[rowStart].hp - 2 * g) < (int64_t)params[P_TOPT] * H) {
+      int64_t wmax = 0;
+      for (int s = rowStart; s < n; ++s) wmax = mx64(wmax, env[s].wp);
+      if (wmax > Wp) { overflow = 1; break; } /* a chart wider than the atlas */
+      tail.on = 1;
+      tail.L = Wp - wmax + 1;
+    }
+    if (tail.on) {
+      int hc = (flags & F_HC) != 0;
+      int e = tail_row(n, rowStart, row, &tail, hc, env, dnext, cannotA, cannotB, Wp, front, X[0], y[0], place);
+      committed = 0;
+      for (int64_t xx = 0; xx < Wp; ++xx) committed = mx64(committed, front[xx]);
+      overflow = committed > Hp;
+      prev_ltr = place[6 * e + 2] == 0;
+      stats[4] = e + 1;
+      stats[5] = tail.rows;
+      rowStart = e + 1;
+      ++row;
+      continue;
+    }
     if (kd.valid) update_knee(&kd, front);
     int nfold = kd.valid ? 2 : 1;
     int rowEnd[2][2];
@@ -887,7 +996,7 @@ int oracle_pack(int32_t n, const uint32_t *offsets, const int32_t *verts, int32_
   oracle_sort(n, rec, perm);
   int32_t *place = (int32_t *)malloc(sizeof(int32_t) * 6 * n);
   int32_t *best_place = (int32_t *)malloc(sizeof(int32_t) * 6 * n);
-  int32_t stats[5], best_stats[5] = {0, 0, 0, 0, 0};
+  int32_t stats[6], best_stats[6] = {0, 0, 0, 0, 0, 0};
   int best_k = 0;
   for (int j = 64; j >= 1; --j) {
     int32_t k = 16 * j;
