@@ -118,6 +118,25 @@ typedef struct tabi_params {
                            [floor(s E / K), floor((s + 1) E / K)]; the ten
                            slots per axis of tabi_chart_info hold slice
                            floor(t K / 10) in slot t                        */
+  int32_t topt_permille;     /* t_opt of Sec. 4.4 in permille of the atlas
+                                height (10 = the paper's 1 %; 0 = rows are
+                                always folded one by one, Tab. 4's t_opt = 0):
+                                once no knee is live and a row's tallest
+                                chart is shorter than t_opt H at the
+                                candidate scale, the remaining charts are
+                                folded by a prefix sum of their offsets
+                                (padded width minus the compacting distance
+                                to the next chart; chart s+1 never left of
+                                chart s-1's right edge) into rows of width
+                                W + 2g - w'max + 1 (w'max the widest
+                                remaining padded chart: every chart ends
+                                inside the atlas without the intermediate
+                                downscaling of the paper, so all charts keep
+                                one scale), laid left-to-right, right-to-
+                                left, right-to-left in turn and dropped
+                                onto the skyline; 0..1000                   */
+  int32_t hybrid_min_charts; /* the prefix folding applies to atlases of more
+                                than this many charts (the paper: 10,000)   */
 } tabi_params;
 
 /* One placed chart; see "Placement semantics" above. */
@@ -356,10 +375,12 @@ tabi_status tabi_server_get_stats(tabi_server *srv, tabi_server_stats *out);
  *                        found, final max frontline, charts placed,
  *                        evaluated (0 not run: above the area bound or
  *                        below a success; 1 ran to its end; 2 abandoned
- *                        after a larger candidate succeeded), 0
+ *                        after a larger candidate succeeded), rows folded
+ *                        by the prefix sum (topt_permille)
  *                        -- then int32[4n] per sorted chart: x, y, row,
  *                        bits (bit0 mirror, bit1 compacting on, bit2
- *                        knee-folded) for `scale`.
+ *                        knee-folded, bit3 folded by the prefix sum) for
+ *                        `scale`.
  * Only candidates the last pack ran to their end are meaningful (all of
  * them with TABI_F_EVAL_ALL and scale_fanout 64; with a smaller fan-out a
  * later wave reuses the envelope regions).  *needed receives the byte

@@ -63,7 +63,8 @@ bool valid_params(const tabi_params *p) {
          p->knee_margin >= 0 && p->knee_margin <= 1 << 20 &&
          (p->flags & ~(TABI_F_ALL | TABI_F_EVAL_ALL)) == 0 && p->scale_fanout >= 0 &&
          p->scale_fanout <= kScales &&
-         (p->laabb_count == 2 || p->laabb_count == 5 || p->laabb_count == kSlices);
+         (p->laabb_count == 2 || p->laabb_count == 5 || p->laabb_count == kSlices) &&
+         p->topt_permille >= 0 && p->topt_permille <= 1000 && p->hybrid_min_charts >= 0;
 }
 
 // Arena bytes of the per-chart and per-atlas arrays of one atlas (all but
@@ -324,7 +325,7 @@ int ceil_log2(int64_t v) {
 uint64_t batch_class(int A, int64_t N, int maxW, const tabi_params *params) {
   return (uint64_t)ceil_log2(A) | (uint64_t)ceil_log2((N + A - 1) / A) << 8 | (uint64_t)ceil_log2(maxW) << 16 |
          (uint64_t)params->gutter << 24 | (uint64_t)(params->flags & TABI_F_ALL) << 32 |
-         (uint64_t)params->laabb_count << 40;
+         (uint64_t)params->laabb_count << 40 | (uint64_t)(params->topt_permille > 0) << 44;
 }
 
 // One atlas: every candidate at once, no chunks and no progressive area
@@ -434,6 +435,8 @@ tabi_status batch_launch(tabi_ctx *ctx, const tabi_params *params, tabi_request 
   p.knee_margin = params->knee_margin;
   p.flags = params->flags;
   p.laabb_k = params->laabb_count;
+  p.topt = params->topt_permille;
+  p.hyb_min = params->hybrid_min_charts;
   // launch shape: forced (autotuner), else tuned for this batch class,
   // else the default; an explicit fan-out in params wins over both
   int maxW = 1;
@@ -660,6 +663,8 @@ void tabi_params_default(tabi_params *p) {
   p->knee_margin = 1;
   p->flags = TABI_F_ALL;
   p->laabb_count = kSlices;
+  p->topt_permille = 10;        // Sec. 4.4: t_opt = 1 % ...
+  p->hybrid_min_charts = 10000;  // ... for atlases of more than 10,000 charts
   p->scale_fanout = 0;  // tuned, else 64 for one atlas and 8 for a batch
 }
 

@@ -40,6 +40,15 @@
 //   G  selection (Sec. 4.2) by warp 0, which also advances the row state;
 //   H  commit: one warp per chart raises the frontline (shared atomicMax,
 //      since compacted neighbours share columns); placements out.
+//
+// Prefix-sum tail (Sec. 4.4): once no knee is live and a row's first
+// (tallest) chart is below t_opt of the atlas height (atlases of more than
+// hybrid_min charts), phase T switches the task to the tail for good.  A
+// tail row is the same fold, continued from the carried unwrapped prefix
+// (the offsets' running sum, clamp included) and cut where the prefix
+// passes the next multiple of L = W' - w'max + 1; its direction follows
+// the fixed pattern left-to-right, right-to-left, right-to-left; phases D,
+// E and H run it as the one configuration of the row.
 #include "tabi_internal.cuh"
 
 namespace tabi {
@@ -58,6 +67,10 @@ struct Ctl {
   int32_t knee_rows, knees, knee_t[2], stage_lo, stage_hi, abort;
   int32_t t_at, t_j, t_skip;
   int32_t front_sum;     // the committed frontline summed over the padded columns
+  // prefix-sum tail (Sec. 4.4): on, fold width L, unwrapped prefix of the
+  // next row's first chart and of the chart before it (have_prev: one
+  // exists) with that chart's width, tail rows committed
+  int32_t tail, tL, tP, tPrev, tWprev, tHave, trows;
   int32_t red[kMaxWarps];
 };
 
@@ -153,6 +166,7 @@ __global__ void __launch_bounds__(NT) rowloop_kernel(const Pack *__restrict__ pp
   const bool balance = flags & TABI_F_BALANCE;
   const bool eval_all = flags & TABI_F_EVAL_ALL;
   const bool area_bound = !eval_all && p.prog_bound;  // phase I
+  const int vt = use_hc ? 1 : 0;                      // the fold a tail row uses
   const int g = p.g;
   const int64_t N = p.N;
   extern __shared__ int4 sm4[];
@@ -193,6 +207,7 @@ __global__ void __launch_bounds__(NT) rowloop_kernel(const Pack *__restrict__ pp
       const int Wp = ad.W + 2 * g, Hp = ad.H + 2 * g;
       const int wp_pad = (Wp + 3) & ~3;
       const int maxrow = rowloop_maxrow(ad.W, g);
+      const bool hybrid = p.topt > 0 && n > p.hyb_min;  // Sec. 4.4
       // the column stage takes what is left, up to two atlas widths of words
       // (each staged word costs one word of stage and one of chart index)
       const int room = (smem_words - wp_pad - 15 * maxrow) / 2;
@@ -233,6 +248,7 @@ __global__ void __launch_bounds__(NT) rowloop_kernel(const Pack *__restrict__ pp
           ctl.row_start = 0; ctl.row = 0; ctl.committed = 0; ctl.prev_ltr = 0;
           ctl.knee_valid = 0; ctl.knee_ltr = 0; ctl.knee_l = 0; ctl.knee_r = 0;
           ctl.knee_rows = 0; ctl.knees = 0;
+          ctl.tail = 0; ctl.tL = 1; ctl.tP = 0; ctl.tPrev = 0; ctl.tWprev = 0; ctl.tHave = 0; ctl.trows = 0;
         }
       } else {  // resume where the previous chunk stopped
         for (int x = tid; x < wp_pad; x += kNT) front[x] = fsave[x];
@@ -240,6 +256,8 @@ __global__ void __launch_bounds__(NT) rowloop_kernel(const Pack *__restrict__ pp
           ctl.row_start = csave[0]; ctl.row = csave[1]; ctl.committed = csave[2]; ctl.prev_ltr = csave[3];
           ctl.knee_valid = csave[4]; ctl.knee_ltr = csave[5]; ctl.knee_l = csave[6]; ctl.knee_r = csave[7];
           ctl.knee_rows = csave[8]; ctl.knees = csave[9];
+          ctl.tail = csave[10] & 1; ctl.tHave = (csave[10] >> 1) & 1; ctl.trows = csave[10] >> 2;
+          ctl.tL = csave[11]; ctl.tP = csave[12]; ctl.tPrev = csave[13]; ctl.tWprev = csave[14];
         }
       }
       {  // the frontline's sum (atlas sides <= 8192: below 2^31), kept up to date by the commits
@@ -260,6 +278,27 @@ __global__ void __launch_bounds__(NT) rowloop_kernel(const Pack *__restrict__ pp
       while (true) {
         const int row_start = ctl.row_start, row = ctl.row;
         if (row_start >= n || ctl.fail) break;
+
+        // ---- T: switch to the prefix-sum tail (Sec. 4.4) ----------------------
+        // once no knee is live and the row's first (tallest) chart is shorter
+        // than t_opt H at this scale; the rows are then folded to the width
+        // L = W' - w'max + 1 (w'max over the remaining charts, known from the
+        // layout before any is drawn), so every chart ends inside the atlas
+        if (hybrid && !ctl.tail && !ctl.knee_valid &&
+            1000 * (int64_t)(meta[(int64_t)row_start * 4 + 1] - 2 * g) < (int64_t)p.topt * ad.H) {
+          int32_t wm = 0;
+          for (int s = row_start + tid; s < n; s += kNT) wm = max(wm, meta[(int64_t)s * 4]);
+          wm = block_max<kNW>(wm, ctl);
+          if (tid == 0) {
+            if (wm > Wp) ctl.fail = 1;  // a chart wider than the atlas
+            ctl.tail = 1; ctl.tL = Wp - wm + 1; ctl.tP = 0; ctl.tHave = 0;
+          }
+          __syncthreads();
+          if (ctl.fail) break;
+        }
+        const bool tail = ctl.tail;
+        // a tail row's start in the unwrapped prefix, and its fold width
+        const int32_t tB = tail ? (ctl.tP / ctl.tL) * ctl.tL : 0, tL = ctl.tL;
 
         // ---- A: knee refresh (Algorithm 3) and the concavity's max -----------
         const bool knee = ctl.knee_valid;
@@ -290,7 +329,7 @@ __global__ void __launch_bounds__(NT) rowloop_kernel(const Pack *__restrict__ pp
         // ---- B: folds (Algorithm 4) -------------------------------------------
         if (warp < 2) {
           const int hc = warp;  // warp 0: side by side, warp 1: compacted
-          const bool active = hc == 0 || use_hc;
+          const bool active = tail ? hc == vt : (hc == 0 || use_hc);
           int32_t lenF = 0, lenK = 0;
           if (active) {
             const int32_t foldF = Wp;
@@ -299,6 +338,14 @@ __global__ void __launch_bounds__(NT) rowloop_kernel(const Pack *__restrict__ pp
             // state at the chunk start: x of its first chart, x and right edge
             // of the chart before it (none at the row start)
             int32_t carry_x = 0, carry_xprev = kNeg, carry_re = kNeg, carry_wprev = kNeg;
+            if (tail) {  // continue the prefix, relative to this row's start
+              carry_x = ctl.tP - tB;
+              if (ctl.tHave) {
+                carry_xprev = ctl.tPrev - tB;
+                carry_re = carry_xprev + ctl.tWprev;
+                carry_wprev = ctl.tWprev;
+              }
+            }
             bool doneF = false, doneK = !knee;
             // widths and distances of four chunks are loaded together (one
             // memory round trip per 128 charts), then scanned chunk by chunk;
@@ -354,7 +401,8 @@ __global__ void __launch_bounds__(NT) rowloop_kernel(const Pack *__restrict__ pp
                 }
                 carry_x = __shfl_sync(0xffffffffu, xnext, 31);
                 // the first chart that does not fit ends the row
-                const unsigned overF = __ballot_sync(0xffffffffu, !valid || xt + w > foldF);
+                // (a tail row: the first chart starting at or past L)
+                const unsigned overF = __ballot_sync(0xffffffffu, !valid || (tail ? xt >= tL : xt + w > foldF));
                 const unsigned overK = __ballot_sync(0xffffffffu, !valid || xt + w > foldK);
                 if (!doneF && overF) { lenF = t0 + __ffs(overF) - 1; doneF = true; }
                 else if (!doneF) lenF = t0 + 32;
@@ -422,7 +470,7 @@ __global__ void __launch_bounds__(NT) rowloop_kernel(const Pack *__restrict__ pp
             break;
           }
         }
-        if (ctl.len[0] == 0) {  // a chart wider than the atlas: this scale fails
+        if (ctl.len[tail ? vt : 0] == 0) {  // a chart wider than the atlas: this scale fails
           if (tid == 0) ctl.fail = 1;
           break;
         }
@@ -557,7 +605,32 @@ __global__ void __launch_bounds__(NT) rowloop_kernel(const Pack *__restrict__ pp
         __syncthreads();
 
         // ---- G: selection (Sec. 4.2); the row state advances ------------------
-        if (warp == 0) {
+        if (warp == 0 && tail) {
+          // a tail row: its fold, the direction of FastAtlas's pattern
+          if (lane == 0) {
+            const int dir = ctl.trows % 3 == 0 ? 0 : 1;
+            const int best = vt * 2 + dir;
+            const int len = ctl.len[vt];
+            const int32_t *pos = vt ? posH : posN;
+            ctl.best = best;
+            if (row_start + len < n) {  // the next row continues the prefix from here
+              ctl.tP = tB + pos[len];
+              ctl.tPrev = tB + pos[len - 1];
+              ctl.tWprev = wps[len - 1];
+              ctl.tHave = 1;
+            }
+            ctl.trows += 1;
+            ctl.committed = ctl.score[best];
+            ctl.fail = ctl.abort ? 2 : (ctl.committed > Hp ? 1 : 0);
+            ctl.prev_ltr = dir == 0;
+            ctl.row_start = row_start + len;
+            ctl.row = row + 1;
+            if (area_bound && row_start + len < n) {
+              nxt2 = p.pre2[cb + row_start + len];
+              nxtE = p.preE[cb + row_start + len];
+            }
+          }
+        } else if (warp == 0) {
           // lane f picks the direction for fold f (0: atlas width, 1: knee)
           int ch = 0;
           if (lane < 2 && (lane == 0 || knee)) {
@@ -658,7 +731,7 @@ __global__ void __launch_bounds__(NT) rowloop_kernel(const Pack *__restrict__ pp
             for (int o = 16; o > 0; o >>= 1) grow += __shfl_xor_sync(0xffffffffu, grow, o);
             if (lane == 0 && grow) atomicAdd(&ctl.front_sum, grow);
           }
-          const int bits = dir | (hc << 1) | (fold << 2);
+          const int bits = dir | (hc << 1) | (fold << 2) | ((int)tail << 3);
           for (int t = tid; t < len; t += kNT) {
             const int32_t X = dir ? hi - pos[t] - wps[t] : lo + pos[t];
             place[row_start + t] = make_int4(X, y[t], row, bits);
@@ -695,6 +768,8 @@ __global__ void __launch_bounds__(NT) rowloop_kernel(const Pack *__restrict__ pp
           csave[0] = ctl.row_start; csave[1] = ctl.row; csave[2] = ctl.committed; csave[3] = ctl.prev_ltr;
           csave[4] = ctl.knee_valid; csave[5] = ctl.knee_ltr; csave[6] = ctl.knee_l; csave[7] = ctl.knee_r;
           csave[8] = ctl.knee_rows; csave[9] = ctl.knees;
+          csave[10] = ctl.tail | (ctl.tHave << 1) | (ctl.trows << 2);
+          csave[11] = ctl.tL; csave[12] = ctl.tP; csave[13] = ctl.tPrev; csave[14] = ctl.tWprev;
           p.tstate[at * kScales + j] = 0;
         }
       } else if (tid == 0) {
@@ -706,6 +781,7 @@ __global__ void __launch_bounds__(NT) rowloop_kernel(const Pack *__restrict__ pp
         so->score = ctl.committed;
         so->placed = ctl.row_start;
         so->evaluated = ctl.fail == 2 ? 2 : 1;
+        so->tail_rows = ctl.trows;
         p.tstate[at * kScales + j] = 1;
         if (ok) atomicMax(p.found + at, j);
       }

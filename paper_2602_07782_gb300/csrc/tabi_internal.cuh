@@ -33,7 +33,7 @@ struct __align__(16) ChartShape {
 // evaluated: 0 not run, 1 ran to its end, 2 abandoned once a larger
 // candidate of the same atlas had succeeded.
 struct ScaleOut {
-  int32_t success, rows, knee_rows, knees, score, placed, evaluated, pad;
+  int32_t success, rows, knee_rows, knees, score, placed, evaluated, tail_rows;
 };
 
 // Result of one atlas, written on the device and read once by the host.
@@ -72,6 +72,8 @@ struct Pack {
   int32_t prep_group;           // prep lanes per chart (host record of the launch)
   int32_t prog_bound;           // row loop checks the progressive area bound after each row
   int32_t laabb_k;              // local AABBs per axis (2, 5 or 10; record slot t holds slice t K / 10)
+  int32_t topt;                 // t_opt of the prefix-sum tail, permille of the atlas height (0: off)
+  int32_t hyb_min;              // the tail applies to atlases of more charts than this
   const AtlasDesc *atl;         // [A]
   int32_t *catl;                // [N] atlas of each chart
   tabi_chart_info *info;        // [N] input order

@@ -32,7 +32,8 @@ class Params(ctypes.Structure):
                 ("knee_abs_pct", ctypes.c_int32), ("knee_rel_pct", ctypes.c_int32),
                 ("lr_sig_pct", ctypes.c_int32), ("knee_margin", ctypes.c_int32),
                 ("flags", ctypes.c_uint32), ("scale_fanout", ctypes.c_int32),
-                ("laabb_count", ctypes.c_int32)]
+                ("laabb_count", ctypes.c_int32), ("topt_permille", ctypes.c_int32),
+                ("hybrid_min_charts", ctypes.c_int32)]
 
 
 class Request(ctypes.Structure):

@@ -39,7 +39,8 @@ def test_param_defaults_follow_the_paper(lib):
     assert (p.gutter, p.knee_abs_pct, p.knee_rel_pct, p.lr_sig_pct) == (1, 10, 20, 10)
     assert p.flags == tabi.F_ALL and p.scale_fanout == 0  # 0: tuned / default launch shape
     assert p.laabb_count == 10  # local AABBs per axis (App. A)
-    assert ctypes.sizeof(tabi.Params) == 36 and p.version == 2
+    assert (p.topt_permille, p.hybrid_min_charts) == (10, 10000)  # Sec. 4.4: 1 % above 10,000 charts
+    assert ctypes.sizeof(tabi.Params) == 44 and p.version == 2
     assert tabi.status_str(tabi.TABI_ERR_NO_FIT) == "no candidate scale fits"
 
 

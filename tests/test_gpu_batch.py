@@ -31,7 +31,7 @@ def ctx():
 def oracle_params(p):
     return oracle.default_params(gutter=p.gutter, knee_abs=p.knee_abs_pct, knee_rel=p.knee_rel_pct,
                                  lr_sig=p.lr_sig_pct, knee_margin=p.knee_margin, flags=p.flags & tabi.F_ALL,
-                                 laabb_k=p.laabb_count)
+                                 laabb_k=p.laabb_count, topt=p.topt_permille, hybrid_min=p.hybrid_min_charts)
 
 
 def mixed_batch():
@@ -81,6 +81,20 @@ def test_every_launch_shape_gives_the_oracle_result(ctx, shape):
     t = tabi.Tuning(*shape, 0.0)
     p = tabi.params_default()
     st, res = ctx.pack_batch(sets, p, shape=t)
+    assert st == tabi.TABI_OK, ctx.last_error()
+    op = oracle_params(p)
+    for cs, r in zip(sets, res):
+        compare(cs, r, op)
+
+
+@pytest.mark.parametrize("shape", SHAPES[:4], ids=[",".join(map(str, s)) for s in SHAPES[:4]])
+def test_batch_tail_in_chunks(ctx, shape):
+    """The prefix-sum tail (Sec. 4.4) under lazy chunks: a task parks its
+    tail state between chunks and resumes it; every atlas as the oracle
+    packs it."""
+    sets = mixed_batch()
+    p = tabi.params_default(topt_permille=40, hybrid_min_charts=100)
+    st, res = ctx.pack_batch(sets, p, shape=tabi.Tuning(*shape, 0.0))
     assert st == tabi.TABI_OK, ctx.last_error()
     op = oracle_params(p)
     for cs, r in zip(sets, res):

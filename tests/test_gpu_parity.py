@@ -41,7 +41,7 @@ def oracle_params(p):
     # the oracle knows the method's flags only (TABI_F_EVAL_ALL is an inspection aid)
     return oracle.default_params(gutter=p.gutter, knee_abs=p.knee_abs_pct, knee_rel=p.knee_rel_pct,
                                  lr_sig=p.lr_sig_pct, knee_margin=p.knee_margin, flags=p.flags & tabi.F_ALL,
-                                 laabb_k=p.laabb_count)
+                                 laabb_k=p.laabb_count, topt=p.topt_permille, hybrid_min=p.hybrid_min_charts)
 
 
 SMALL = {
@@ -90,10 +90,14 @@ def test_prep_group_widths(ctx):
 
 
 @pytest.mark.parametrize("name", list(SMALL))
-def test_steps_parity(ctx, name):
-    """prep, sort, envelopes, distances/flags and every candidate's row loop."""
+@pytest.mark.parametrize("topt", [0, 60])
+def test_steps_parity(ctx, name, topt):
+    """prep, sort, envelopes, distances/flags and every candidate's row loop
+    (topt 60: rows past 6 % of the atlas height folded by the prefix sum of
+    Sec. 4.4, whatever the chart count)."""
     cs = SMALL[name]()
-    p = gpu_params(flags=tabi.F_ALL | tabi.F_EVAL_ALL)  # every candidate runs to its end
+    p = gpu_params(flags=tabi.F_ALL | tabi.F_EVAL_ALL,  # every candidate runs to its end
+                   topt_permille=topt, hybrid_min_charts=0)
     op = oracle_params(p)
     res = ctx.pack(cs, p)
     assert res.status == tabi.TABI_OK, ctx.last_error()
@@ -116,6 +120,7 @@ def test_steps_parity(ctx, name):
         ok, opl, ost = oracle.pack_scale(rec, perm, cs.atlas_w, cs.atlas_h, k, op)
         assert hdr[0] == int(ok), j
         assert list(hdr[1:6]) == [ost[0], ost[1], ost[2], ost[3], ost[4]], j
+        assert hdr[7] == ost[5], j  # rows folded by the prefix sum (Sec. 4.4)
         placed = int(ost[4])
         bits = opl[:placed, 2] | (opl[:placed, 4] << 1) | (opl[:placed, 5] << 2)
         assert np.array_equal(place[:placed, 0], opl[:placed, 0]), j
@@ -166,6 +171,32 @@ def test_ablation_parity(ctx, flags):
     cs = synth.knees(2, 250, 1024)
     p = gpu_params(flags=flags)
     _compare_pack(cs, ctx.pack(cs, p), oracle_params(p))
+
+
+@pytest.mark.parametrize("name", list(SMALL))
+@pytest.mark.parametrize("fanout", [64, 8, 1])
+@pytest.mark.parametrize("topt", [20, 150])
+def test_tail_pack_parity(ctx, name, fanout, topt):
+    """The prefix-sum tail (Sec. 4.4) in every candidate, whole packs."""
+    cs = SMALL[name]()
+    p = gpu_params(scale_fanout=fanout, topt_permille=topt, hybrid_min_charts=0)
+    _compare_pack(cs, ctx.pack(cs, p), oracle_params(p))
+
+
+@pytest.mark.parametrize("flags", [tabi.F_ALL & ~tabi.F_HC, tabi.F_ALL & ~tabi.F_BALANCE, 0])
+def test_tail_ablation_parity(ctx, flags):
+    cs = synth.knees(2, 250, 1024)
+    p = gpu_params(flags=flags, topt_permille=100, hybrid_min_charts=0)
+    _compare_pack(cs, ctx.pack(cs, p), oracle_params(p))
+
+
+def test_tail_threshold_by_chart_count(ctx):
+    """The tail applies above hybrid_min_charts only (the paper: 10,000)."""
+    cs = synth.stars(6, 400, 512)
+    for hmin in (399, 400):
+        p = gpu_params(topt_permille=100, hybrid_min_charts=hmin)
+        o = _compare_pack(cs, ctx.pack(cs, p), oracle_params(p))
+        assert (o.stats[5] > 0) == (hmin < 400)
 
 
 @pytest.mark.parametrize("count", [2, 5])
