@@ -147,7 +147,7 @@ def cpu_baseline(sets, budget_s: float = 15.0):
 # workload (ncu, direct launches, the launch shape below), with a digest of
 # the kernel's sources at capture time; the bench reports it per launch
 # while the sources and the shape match, else null.
-RASTER_NCU = {"dram_bytes_per_step": 2655321088, "sources_sha256_16": "0adc9213561ebaa2",
+RASTER_NCU = {"dram_bytes_per_step": 2676225280, "sources_sha256_16": "769f1f70cd681781",
               "shape": {"scale_fanout": 2, "chunks": 4, "progressive_bound": 1}}
 
 

@@ -85,7 +85,10 @@ __global__ void init_kernel(const Pack *__restrict__ pp) {
   const int t = threadIdx.x;
   if (blockIdx.x == 0) {
     if (t < 2 * kScales) p.jtot[t] = 0;
-    for (int i = t; i < kScales * kMaxChunks; i += blockDim.x) p.counter[i] = 0;
+    for (int i = t; i < kScales * kMaxChunks; i += blockDim.x) {
+      p.counter[i] = 0;
+      p.rcounter[i] = 0;
+    }
     if (t == 0) {
       *p.cur_wave = 0;
       p.raster_words[0] = p.raster_words[1] = 0;
@@ -489,6 +492,7 @@ tabi_status batch_launch(tabi_ctx *ctx, const tabi_params *params, tabi_request 
   p.act_pre = cv.take<int32_t>(A);
   p.act_chart = cv.take<int32_t>(n);
   p.counter = cv.take<int32_t>(kScales * kMaxChunks);
+  p.rcounter = cv.take<uint32_t>(kScales * kMaxChunks);
   p.cur_wave = cv.take<int32_t>(1);
   p.raster_words = cv.take<unsigned long long>(2);
   p.carea = cv.take<unsigned long long>(n);

@@ -78,23 +78,30 @@ __global__ void __launch_bounds__(kRasterThreads, 3) raster_kernel(const Pack *_
   int G = (int)(((int64_t)nj * total + target - 1) / target);
   G = G < 1 ? 1 : (G > nj ? nj : G);
   const int ngroups = (nj + G - 1) / G;
-  const int64_t items = total * ngroups;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const uint32_t items = (uint32_t)(total * ngroups);  // about raster_items, or one per chart: below 2^31
   const int64_t N = p.N;
   const bool use_l = (p.flags & TABI_F_LAABB) != 0, use_o = (p.flags & TABI_F_OBB) != 0;
   const bool all = q == 0 || (p.flags & TABI_F_EVAL_ALL);  // later chunks: running candidates only
   const int g = p.g;
   rmath::AxisK &a0 = axk[wib][0], &a1 = axk[wib][1];
-  __shared__ unsigned long long cta_words[2];  // scanline and column words of this CTA (one add per CTA)
+  __shared__ unsigned long long cta_words[2];  // scanline and column words of this CTA (one global add)
   if (threadIdx.x < 2) cta_words[threadIdx.x] = 0;
   __syncthreads();
-  unsigned long long words = 0, cols = 0;
-  for (int64_t it = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; it < items; it += nwarps) {
-    const int s = p.act_chart[it / ngroups];
+  // items go to warps as they free up (a device counter per (wave, chunk)):
+  // an item's cost follows its chart's size, which spans orders of
+  // magnitude, so a fixed assignment leaves most warps idle behind the few
+  // that drew the largest charts
+  uint32_t *next_item = p.rcounter + wave * kMaxChunks + q;
+  while (true) {
+    uint32_t grab = 0;
+    if (lane == 0) grab = atomicAdd(next_item, 1u);
+    const uint32_t it = __shfl_sync(0xffffffffu, grab, 0);
+    if (it >= items) break;
+    const int s = p.act_chart[it / (uint32_t)ngroups];
     const int at = p.catl[s];
     const int cb = p.atl[at].cb;
     const WaveRange wr = wave_range(p.jtop[at], wave, nj);
-    const int j0 = wr.lo + (int)(it % ngroups) * G;
+    const int j0 = wr.lo + (int)(it % (uint32_t)ngroups) * G;
     const int j1 = min(j0 + G, wr.hi + 1);
     if (j0 >= j1) continue;  // this atlas has fewer candidates left than the wave
     const ChartShape &sh = p.shape[s];
@@ -153,15 +160,13 @@ __global__ void __launch_bounds__(kRasterThreads, 3) raster_kernel(const Pack *_
         for (int c = lane; c < a0.len + 2 * g; c += 32) own[c] = s - cb;
       }
       warp_axis(a1, g, p.pool + rbase + p.rowstart[js]);
-      if (lane == 0) p.meta[js * 4 + 3] = maxbot;  // w', h' and the column start come from the layout
-      words += (unsigned long long)(a0.len + a1.len + 4 * g);
-      cols += (unsigned long long)(a0.len + 2 * g);
+      if (lane == 0) {
+        p.meta[js * 4 + 3] = maxbot;  // w', h' and the column start come from the layout
+        atomicAdd(&cta_words[0], (unsigned long long)(a0.len + a1.len + 4 * g));
+        atomicAdd(&cta_words[1], (unsigned long long)(a0.len + 2 * g));
+      }
       __syncwarp();
     }
-  }
-  if (lane == 0 && words) {
-    atomicAdd(&cta_words[0], words);
-    atomicAdd(&cta_words[1], cols);
   }
   __syncthreads();
   if (threadIdx.x < 2 && cta_words[threadIdx.x]) atomicAdd(p.raster_words + threadIdx.x, cta_words[threadIdx.x]);

@@ -107,6 +107,7 @@ struct Pack {
   int32_t *act_pre;             // [A] their first position in act_chart
   int32_t *act_chart;           // [N] their charts (global sorted index)
   int32_t *counter;             // [64][kMaxChunks] row-loop task counter of each (wave, chunk)
+  uint32_t *rcounter;           // [64][kMaxChunks] raster warp-item counter of each (wave, chunk)
   int32_t *cur_wave;            // the wave the kernels work on (advanced by wave_end)
   unsigned long long *raster_words;  // [2] padded scanline words / column words the raster evaluated
   unsigned long long *carea;    // [N] twice each chart's polygon area (Q.8^2), input order
