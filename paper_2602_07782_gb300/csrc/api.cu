@@ -67,6 +67,61 @@ bool valid_params(const tabi_params *p) {
          p->topt_permille >= 0 && p->topt_permille <= 1000 && p->hybrid_min_charts >= 0;
 }
 
+// Host <-> device copies of a batch's request arrays.  When the caller's
+// host buffers are pinned (or registered), one kernel reads them (and,
+// after the pack, writes the placements back) directly over the host link,
+// instead of two copy calls per request in and one out; each copy is cut
+// into pieces of at most kPieceBytes so that the CTAs share the large
+// ones.  Buffers that the device cannot address (pageable memory) keep the
+// copy calls.
+constexpr uint64_t kPieceBytes = 64 * 1024;
+struct CopyPiece {
+  const uint8_t *src;
+  uint8_t *dst;
+  uint64_t bytes;
+};
+
+size_t pieces_of(uint64_t bytes) { return (size_t)((bytes + kPieceBytes - 1) / kPieceBytes); }
+
+// Every piece starts kPieceBytes (a multiple of 16) into its copy, so a
+// piece is 16-byte aligned at both ends iff its copy is; request arrays
+// are 4-byte aligned (checked on the host).
+__global__ void __launch_bounds__(256) copy_pieces_kernel(const CopyPiece *__restrict__ pcs, int n) {
+  for (int i = blockIdx.x; i < n; i += gridDim.x) {
+    const CopyPiece pc = pcs[i];
+    if ((((uintptr_t)pc.src | (uintptr_t)pc.dst) & 15) == 0) {
+      const uint64_t n16 = pc.bytes >> 4;
+      const uint4 *s = reinterpret_cast<const uint4 *>(pc.src);
+      uint4 *d = reinterpret_cast<uint4 *>(pc.dst);
+      for (uint64_t k = threadIdx.x; k < n16; k += blockDim.x) d[k] = s[k];
+      for (uint64_t k = (n16 << 4) + threadIdx.x * 4; k < pc.bytes; k += blockDim.x * 4)
+        *reinterpret_cast<uint32_t *>(pc.dst + k) = *reinterpret_cast<const uint32_t *>(pc.src + k);
+    } else {
+      for (uint64_t k = threadIdx.x * 4; k < pc.bytes; k += blockDim.x * 4)
+        *reinterpret_cast<uint32_t *>(pc.dst + k) = *reinterpret_cast<const uint32_t *>(pc.src + k);
+    }
+  }
+}
+
+// `host` itself when the device can address that host buffer at the same
+// address (pinned or registered memory under unified addressing) and it is
+// 4-byte aligned; else null (the buffer then takes a copy call).
+const void *device_view(const void *host) {
+  if (((uintptr_t)host & 3) != 0) return nullptr;
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, host) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost && a.devicePointer == host ? host : nullptr;
+}
+
+void add_pieces(std::vector<CopyPiece> &v, const void *src, void *dst, uint64_t bytes) {
+  for (uint64_t o = 0; o < bytes; o += kPieceBytes)
+    v.push_back(CopyPiece{static_cast<const uint8_t *>(src) + o, static_cast<uint8_t *>(dst) + o,
+                          bytes - o < kPieceBytes ? bytes - o : kPieceBytes});
+}
+
 // Arena bytes of the per-chart and per-atlas arrays of one atlas (all but
 // the envelope pools), with the host-input copies.
 size_t fixed_bytes(int64_t n, int64_t nv) {
@@ -74,7 +129,10 @@ size_t fixed_bytes(int64_t n, int64_t nv) {
                            (size_t)kScales * (4 + 4 + 16 + 4 + 1 + 16) + 4 + 4 + sizeof(tabi_placement);
   const size_t per_atlas = sizeof(AtlasDesc) + (size_t)kScales * 2 * 8 * 2 + sizeof(ScaleOut) * kScales +
                            8 + sizeof(PackResult) + 8 + 40 * 256;
-  return (size_t)n * per_chart + 8 * (size_t)nv + per_atlas + sizeof(Pack) + 64 * 1024;
+  const size_t pieces = pieces_of(4 * (uint64_t)(n + 1)) + pieces_of(8 * (uint64_t)nv) +
+                        pieces_of(sizeof(tabi_placement) * (uint64_t)n);
+  return (size_t)n * per_chart + 8 * (size_t)nv + per_atlas + sizeof(CopyPiece) * pieces + 256 + sizeof(Pack) +
+         64 * 1024;
 }
 
 // ---------------------------------------------------------------------------
@@ -406,6 +464,16 @@ tabi_status batch_launch(tabi_ctx *ctx, const tabi_params *params, tabi_request 
   Pack p{};
   Pack *dpack = cv.take<Pack>(1);
   AtlasDesc *ddesc = cv.take<AtlasDesc>(A);
+  // copy pieces of the host buffers the device can address, in then out
+  // (uploaded with the record: they follow the atlas table)
+  size_t max_pieces = 0;
+  if (host)
+    for (int i = 0; i < A; ++i) {
+      const tabi_request &r = reqs[order[i]];
+      max_pieces += pieces_of(4 * ((uint64_t)r.n_charts + 1)) + pieces_of(8 * (uint64_t)r.n_verts) +
+                    pieces_of(sizeof(tabi_placement) * (uint64_t)r.n_charts);
+    }
+  CopyPiece *dpieces = max_pieces ? cv.take<CopyPiece>(max_pieces) : nullptr;
   std::vector<AtlasDesc> &desc = fl.desc;
   desc.assign(A, AtlasDesc{});
   int64_t cb = 0;
@@ -510,16 +578,49 @@ tabi_status batch_launch(tabi_ctx *ctx, const tabi_params *params, tabi_request 
   p.colown = reinterpret_cast<int32_t *>(p.colpool + p.col_cap);
   p.pool = reinterpret_cast<uint32_t *>(p.colown + p.col_cap);
 
-  // the record and the atlas table go up in one copy
+  // host buffers: pieces for those the device addresses, copy calls for
+  // the rest (outputs: `out_call` marks the requests that need one)
+  std::vector<CopyPiece> pin, pout;
+  std::vector<char> in_call(host ? A : 0, 0), out_call(host ? A : 0, 0);
+  for (int i = 0; i < A && host; ++i) {
+    const tabi_request &r = reqs[order[i]];
+    const uint64_t bo = 4 * ((uint64_t)r.n_charts + 1), bv = 8 * (uint64_t)r.n_verts;
+    const void *so = device_view(r.offsets), *sv = device_view(r.verts);
+    if (so && sv) {
+      add_pieces(pin, so, (void *)desc[i].offsets, bo);
+      add_pieces(pin, sv, (void *)desc[i].verts, bv);
+    } else {
+      in_call[i] = 1;
+    }
+    void *dout = const_cast<void *>(device_view(r.out));
+    if (dout) add_pieces(pout, desc[i].out, dout, sizeof(tabi_placement) * (uint64_t)r.n_charts);
+    else out_call[i] = 1;
+  }
+
+  // the record, the atlas table and the copy pieces go up in one copy
   const size_t desc_off = round256(sizeof(Pack));
-  const size_t up = desc_off + sizeof(AtlasDesc) * (size_t)A;
+  const size_t pcs_off = desc_off + round256(sizeof(AtlasDesc) * (size_t)A);
+  const size_t npcs = pin.size() + pout.size();
+  const size_t up = npcs ? pcs_off + sizeof(CopyPiece) * npcs : desc_off + sizeof(AtlasDesc) * (size_t)A;
   const size_t res_off = round256(up);
+  if (npcs && (!dpieces || reinterpret_cast<char *>(dpieces) != reinterpret_cast<char *>(dpack) + pcs_off ||
+               npcs > max_pieces))
+    return fail(ctx, TABI_ERR_CUDA, "copy pieces misplaced");  // cannot happen: the carve is contiguous
   if (!ensure_hstage(ctx, res_off + sizeof(PackResult) * (size_t)A))
     return fail(ctx, TABI_ERR_CUDA, "pinned staging allocation failed");
   memcpy(ctx->hstage, &p, sizeof(Pack));
   memcpy(ctx->hstage + desc_off, desc.data(), sizeof(AtlasDesc) * (size_t)A);
+  if (npcs) {
+    memcpy(ctx->hstage + pcs_off, pin.data(), sizeof(CopyPiece) * pin.size());
+    memcpy(ctx->hstage + pcs_off + sizeof(CopyPiece) * pin.size(), pout.data(), sizeof(CopyPiece) * pout.size());
+  }
   e = cudaMemcpyAsync(dpack, ctx->hstage, up, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && !pin.empty()) {
+    copy_pieces_kernel<<<ctx->sms * 4, 256, 0, st>>>(dpieces, (int)pin.size());
+    e = cudaGetLastError();
+  }
   for (int i = 0; i < A && host && e == cudaSuccess; ++i) {
+    if (!in_call[i]) continue;
     const tabi_request &r = reqs[order[i]];
     e = cudaMemcpyAsync((void *)desc[i].offsets, r.offsets, sizeof(uint32_t) * ((size_t)r.n_charts + 1),
                         cudaMemcpyHostToDevice, st);
@@ -565,7 +666,12 @@ tabi_status batch_launch(tabi_ctx *ctx, const tabi_params *params, tabi_request 
   }
   PackResult *hres = reinterpret_cast<PackResult *>(ctx->hstage + res_off);
   e = cudaMemcpyAsync(hres, p.result, sizeof(PackResult) * (size_t)A, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && !pout.empty()) {
+    copy_pieces_kernel<<<ctx->sms * 4, 256, 0, st>>>(dpieces + pin.size(), (int)pout.size());
+    e = cudaGetLastError();
+  }
   for (int i = 0; i < A && host && e == cudaSuccess; ++i) {
+    if (!out_call[i]) continue;
     const tabi_request &r = reqs[order[i]];
     e = cudaMemcpyAsync(r.out, desc[i].out, sizeof(tabi_placement) * (size_t)r.n_charts,
                         cudaMemcpyDeviceToHost, st);

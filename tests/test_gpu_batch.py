@@ -407,3 +407,46 @@ def test_batch_uneven_sizes_full_shapes(ctx):
     for cs, r in zip(sets, res):
         assert r.status == tabi.TABI_OK
         compare(cs, r, op)
+
+
+def test_pinned_host_buffers_match(ctx):
+    """tabi_pack_batch with pinned host buffers (the device reads and writes
+    them directly) and with pageable ones (copy calls), mixed in one batch,
+    and the same batch from device buffers: identical results.  The pinned
+    arrays start at offsets 0, 4 and 8 bytes into their allocations, so the
+    copy kernel meets unaligned starts too."""
+    sets = mixed_batch()
+    p = tabi.params_default()
+    st, ref = ctx.pack_batch(sets, p)
+    assert st == tabi.TABI_OK, ctx.last_error()
+    hold = []
+    reqs = (tabi.Request * len(sets))()
+    outs = []
+    for i, cs in enumerate(sets):
+        pinned = i % 3 != 2  # every third request stays pageable
+        sh = 4 * (i % 3)  # byte offset of the arrays in their allocations
+        if pinned:
+            ob = torch.zeros(4 * (cs.n + 1) + 16, dtype=torch.uint8).pin_memory()
+            vb = torch.zeros(8 * cs.nv + 16, dtype=torch.uint8).pin_memory()
+            out_b = torch.zeros(12 * cs.n + 16, dtype=torch.uint8).pin_memory()
+            ob.numpy()[sh:sh + 4 * (cs.n + 1)] = cs.offsets.view(np.uint8)
+            vb.numpy()[sh:sh + 8 * cs.nv] = cs.verts.view(np.uint8)
+            hold.append((ob, vb, out_b))
+            optr, vptr, outp = ob.data_ptr() + sh, vb.data_ptr() + sh, out_b.data_ptr() + sh
+            outs.append(out_b.numpy()[sh:sh + 12 * cs.n])
+        else:
+            o, v = np.ascontiguousarray(cs.offsets, np.uint32), np.ascontiguousarray(cs.verts, np.int32)
+            out_np = np.zeros(12 * cs.n, np.uint8)
+            hold.append((o, v, out_np))
+            optr, vptr, outp = o.ctypes.data, v.ctypes.data, out_np.ctypes.data
+            outs.append(out_np)
+        reqs[i] = tabi.Request(cs.atlas_w, cs.atlas_h, cs.n, cs.nv, optr, vptr, outp, 0, 0)
+    for _ in range(2):  # twice: the second batch reuses the context's arena
+        assert ctx.pack_batch_requests(reqs, p, device=False) == tabi.TABI_OK, ctx.last_error()
+        for i, (cs, r) in enumerate(zip(sets, ref)):
+            assert reqs[i].status == r.status and reqs[i].scale_k == r.k, cs.name
+            got = outs[i].view(tabi.PLACEMENT_DTYPE)
+            for f in ("x", "y", "rot90", "flip_x", "flip_y", "mirror"):
+                assert np.array_equal(got[f], r.place[f]), (cs.name, f)
+        for o in outs:
+            o[:] = 0
