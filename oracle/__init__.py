@@ -210,6 +210,26 @@ def pack(cs, params=None, all_scales=False):
     return PackResult(int(st), int(out_k[0]), place, succ if all_scales else None, stats)
 
 
+def _pack_one(args):
+    cs, params = args
+    r = pack(cs, params)
+    return r.status, r.k, r.place
+
+
+def pack_many(sets, params=None, workers=None):
+    """pack() of each chart set, in a pool of spawned processes (spawn keeps
+    the pool safe to start after CUDA is initialised).  Returns
+    [(status, k, place)]."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    params = default_params() if params is None else params
+    workers = workers or min(len(sets), os.cpu_count() or 1)
+    if workers <= 1:
+        return [_pack_one((cs, params)) for cs in sets]
+    with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(_pack_one, [(cs, params) for cs in sets]))
+
+
 def correct_y(y, cannotA, cannotB, s0=0, s1=None):
     """Literal Algorithm 2 on int64 offsets y (in place copy returned)."""
     y = np.array(y, np.int64)

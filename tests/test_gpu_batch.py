@@ -450,3 +450,30 @@ def test_pinned_host_buffers_match(ctx):
                 assert np.array_equal(got[f], r.place[f]), (cs.name, f)
         for o in outs:
             o[:] = 0
+
+
+@pytest.mark.slow
+def test_full_batch_in_the_benchmark_shape_sampled():
+    """The whole 256-atlas workload (614,480 charts) in the launch shape the
+    benchmark's autotuner picks (fan-out 2, 64K raster warp-items, 1024-thread
+    row-loop CTAs, four chunks, progressive area bound): every atlas's scale
+    and placements against the oracle for a sample of 32 atlases spread over
+    the batch (largest, smallest and evenly spaced by chart count)."""
+    sets = synth.stars_many(synth.batch256_specs())
+    need = sum(tabi.arena_bytes(cs) for cs in sets)
+    c = tabi.Context(arena_bytes=min(need, 32 << 30) + (64 << 20))
+    try:
+        p = tabi.params_default()
+        st, res = c.pack_batch(sets, p, shape=tabi.Tuning(2, 65536, 1024, 1, 4, 1, 0.0))
+        assert st == tabi.TABI_OK, c.last_error()
+    finally:
+        c.close()
+    assert all(r.status == tabi.TABI_OK for r in res)
+    by_n = sorted(range(len(sets)), key=lambda i: sets[i].n)
+    pick = sorted({by_n[0], by_n[-1], *by_n[::8]})
+    out = oracle.pack_many([sets[i] for i in pick], oracle_params(p))
+    for i, (ost, ok, opl) in zip(pick, out):
+        assert ost == 0 and res[i].k == ok, i
+        pl = res[i].place
+        for f, col in (("x", 0), ("y", 1), ("rot90", 2), ("flip_x", 3), ("flip_y", 4), ("mirror", 5)):
+            assert np.array_equal(pl[f], opl[:, col]), (i, f)
