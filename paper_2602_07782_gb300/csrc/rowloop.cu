@@ -37,9 +37,13 @@
 //      so configurations never copy the frontline;
 //      Two further warps find the knee candidate (App. A) of both
 //      atlas-width rows meanwhile;
-//   G  selection (Sec. 4.2) by warp 0, which also advances the row state;
+//   G  selection (Sec. 4.2): every thread derives the same choice from the
+//      scores (so no barrier separates it from the commit); thread 0 also
+//      advances the row state;
 //   H  commit: one warp per chart raises the frontline (shared atomicMax,
 //      since compacted neighbours share columns); placements out.
+// The progressive area bound after a commit is checked by one thread of
+// the next row's staging (phase B), so a row costs four barriers.
 //
 // Prefix-sum tail (Sec. 4.4): once no knee is live and a row's first
 // (tallest) chart is below t_opt of the atlas height (atlases of more than
@@ -61,7 +65,7 @@ constexpr int32_t kI32Min = -0x7fffffff - 1;
 struct Ctl {
   int32_t len[4];        // fold variants v = fold * 2 + hc: charts in the row
   int32_t score[8], score_knee[8];
-  int32_t row_start, row, committed, fail, prev_ltr, best, prev_maxlen;
+  int32_t row_start, row, committed, fail, prev_ltr, bound_fail, prev_maxlen;
   int32_t knee_valid, knee_ltr, knee_l, knee_r;
   int32_t region_lo, region_hi, knee_max;
   int32_t knee_rows, knees, knee_t[2], stage_lo, stage_hi, abort;
@@ -265,19 +269,18 @@ __global__ void __launch_bounds__(NT) rowloop_kernel(const Pack *__restrict__ pp
         if (q > 0 && area_bound)
           for (int x = tid; x < Wp; x += kNT) fs += front[x];
         if (area_bound) fs = block_sum<kNW>(fs, ctl);
-        if (tid == 0) { ctl.fail = 0; ctl.prev_maxlen = 0; ctl.abort = 0; ctl.front_sum = fs; }
+        if (tid == 0) { ctl.fail = 0; ctl.bound_fail = 0; ctl.prev_maxlen = 0; ctl.abort = 0; ctl.front_sum = fs; }
       }
       __syncthreads();
       bool deferred = false;
-      // progressive area bound: the atlas's totals (per task) and, loaded in
-      // the selection phase by thread 0, the sums before the next row's first
-      // chart (used after the commit, which hides the loads' latency)
+      // progressive area bound: the atlas's totals (per task)
       const unsigned long long tot2 = area_bound ? p.area2[at] : 0, totE = area_bound ? p.ext_sum[at] : 0;
-      unsigned long long nxt2 = 0, nxtE = 0;
 
       while (true) {
         const int row_start = ctl.row_start, row = ctl.row;
         if (row_start >= n || ctl.fail) break;
+        // row state the selection reads while thread 0 advances it
+        const int prev_ltr = ctl.prev_ltr, trows = ctl.trows;
 
         // ---- T: switch to the prefix-sum tail (Sec. 4.4) ----------------------
         // once no knee is live and the row's first (tallest) chart is shorter
@@ -443,6 +446,25 @@ __global__ void __launch_bounds__(NT) rowloop_kernel(const Pack *__restrict__ pp
               ctl.stage_hi = c4 + nw;
               // a larger candidate of this atlas has succeeded: this one is moot
               ctl.abort = !eval_all && *(volatile int32_t *)(p.found + at) > j;
+              // ---- progressive area bound (exact; an addition to the paper) ----
+              // Every later chart is dropped onto the frontline: in column x
+              // its cover dilated by g lies inside its padded envelope, at or
+              // below front[x], and above the padded atlas bottom Hp (or the
+              // candidate fails).  Placed charts' dilated covers are pairwise
+              // disjoint (the gutter), and a connected polygon of area A and
+              // larger extent E dilated by g covers at least A + 2gE + 4g^2.
+              // Once the charts not yet placed cannot fit that way into the
+              // area under the frontline, the candidate fails now instead of
+              // rows later (checked after every committed row).
+              if (area_bound && row > 0) {
+                const unsigned long long nxt2 = p.pre2[cb + row_start], nxtE = p.preE[cb + row_start];
+                const int32_t fr = Wp * Hp - ctl.front_sum;  // free texels under the frontline (sides <= 8192)
+                const uint64_t kk = 16 * (uint64_t)(j + 1), gg = (uint64_t)g;
+                const unsigned __int128 S2 = tot2 - nxt2, SE = totE - nxtE;
+                const unsigned __int128 need = S2 * (kk * kk) + ((SE * (2 * gg * kk)) << 19) +
+                                               ((unsigned __int128)(4 * gg * gg * (uint64_t)(n - row_start)) << 37);
+                if (need > ((unsigned __int128)(uint32_t)fr << 37)) ctl.bound_fail = 1;
+              }
             }
           }
           // per chart: window entries, offsets zeroed
@@ -460,6 +482,10 @@ __global__ void __launch_bounds__(NT) rowloop_kernel(const Pack *__restrict__ pp
           }
         }
         __syncthreads();
+        if (ctl.bound_fail) {  // the progressive area bound: the candidate fails
+          if (tid == 0) ctl.fail = 1;
+          break;
+        }
         // The folds examined charts up to the first that does not fit; its
         // position depends on the compaction distance of the pair before it.
         // If that chart is not drawn yet the row waits for the next chunk.
@@ -605,85 +631,69 @@ __global__ void __launch_bounds__(NT) rowloop_kernel(const Pack *__restrict__ pp
         __syncthreads();
 
         // ---- G: selection (Sec. 4.2); the row state advances ------------------
-        if (warp == 0 && tail) {
-          // a tail row: its fold, the direction of FastAtlas's pattern
-          if (lane == 0) {
-            const int dir = ctl.trows % 3 == 0 ? 0 : 1;
-            const int best = vt * 2 + dir;
-            const int len = ctl.len[vt];
+        // Every thread derives the same choice from the scores (fixed since the
+        // last barrier) and the row state it read at the row's start; thread 0
+        // alone writes the next row's state, which no thread reads before the
+        // commit's barrier.
+        int best;
+        if (tail) {
+          best = vt * 2 + (trows % 3 == 0 ? 0 : 1);  // a tail row: FastAtlas's direction pattern
+        } else {
+          // per fold (0: atlas width, 1: knee): compaction iff it fits more
+          // charts, then the direction with the smaller maximum frontline
+          int ch[2];
+#pragma unroll
+          for (int fold = 0; fold < 2; ++fold) {
+            const int h = (use_hc && ctl.len[fold * 2 + 1] > ctl.len[fold * 2]) ? 1 : 0;
+            const int jl = (fold * 2 + h) * 2, jr = jl + 1;
+            const int32_t kl = fold == 0 ? ctl.score[jl] : ctl.score_knee[jl];
+            const int32_t kr = fold == 0 ? ctl.score[jr] : ctl.score_knee[jr];
+            int dir;
+            if (balance) dir = kl < kr ? 0 : (kr < kl ? 1 : (prev_ltr ? 1 : 0));
+            else dir = prev_ltr ? 1 : 0;
+            ch[fold] = jl + dir;
+          }
+          best = ch[0];
+          if (knee && ctl.len[ch[1] >> 1] > 0 && ctl.score[ch[1]] + p.knee_margin <= ctl.score[best]) best = ch[1];
+        }
+        if (tid == 0) {
+          const int v = best >> 1, dir = best & 1, fold = v >> 1, hc = v & 1;
+          const int len = ctl.len[v];
+          if (tail) {
             const int32_t *pos = vt ? posH : posN;
-            ctl.best = best;
             if (row_start + len < n) {  // the next row continues the prefix from here
               ctl.tP = tB + pos[len];
               ctl.tPrev = tB + pos[len - 1];
               ctl.tWprev = wps[len - 1];
               ctl.tHave = 1;
             }
-            ctl.trows += 1;
-            ctl.committed = ctl.score[best];
-            ctl.fail = ctl.abort ? 2 : (ctl.committed > Hp ? 1 : 0);
-            ctl.prev_ltr = dir == 0;
-            ctl.row_start = row_start + len;
-            ctl.row = row + 1;
-            if (area_bound && row_start + len < n) {
-              nxt2 = p.pre2[cb + row_start + len];
-              nxtE = p.preE[cb + row_start + len];
+            ctl.trows = trows + 1;
+          } else if (fold == 0) {
+            // App. A: a knee in this row starts the concavity at the taller
+            // chart's padded edge; no knee if that concavity would be empty
+            int valid = 0;
+            const int t = balance ? ctl.knee_t[hc] : -1;
+            if (t >= 0) {
+              const int32_t X = dir ? Wp - (hc ? posH : posN)[t] - wps[t] : (hc ? posH : posN)[t];
+              ctl.knee_ltr = dir == 0;
+              ctl.knee_l = X;
+              ctl.knee_r = X + wps[t];
+              valid = dir == 0 ? (X + wps[t] < Wp) : (X > 0);
             }
+            ctl.knee_valid = valid;
+            ctl.knees += valid;
+          } else {
+            ctl.knee_rows += 1;
           }
-        } else if (warp == 0) {
-          // lane f picks the direction for fold f (0: atlas width, 1: knee)
-          int ch = 0;
-          if (lane < 2 && (lane == 0 || knee)) {
-            const int fold = lane;
-            const int h = (use_hc && ctl.len[fold * 2 + 1] > ctl.len[fold * 2]) ? 1 : 0;
-            const int jl = (fold * 2 + h) * 2, jr = jl + 1;
-            const int32_t kl = fold == 0 ? ctl.score[jl] : ctl.score_knee[jl];
-            const int32_t kr = fold == 0 ? ctl.score[jr] : ctl.score_knee[jr];
-            int dir;
-            if (balance) dir = kl < kr ? 0 : (kr < kl ? 1 : (ctl.prev_ltr ? 1 : 0));
-            else dir = ctl.prev_ltr ? 1 : 0;
-            ch = jl + dir;
-          }
-          const int ch1 = __shfl_sync(0xffffffffu, ch, 1);
-          if (lane == 0) {
-            int best = ch;
-            if (knee && ctl.len[ch1 >> 1] > 0 && ctl.score[ch1] + p.knee_margin <= ctl.score[best]) best = ch1;
-            const int v = best >> 1, dir = best & 1, fold = v >> 1, hc = v & 1;
-            const int len = ctl.len[v];
-            ctl.best = best;
-            if (fold == 0) {
-              // App. A: a knee in this row starts the concavity at the taller
-              // chart's padded edge; no knee if that concavity would be empty
-              int valid = 0;
-              const int t = balance ? ctl.knee_t[hc] : -1;
-              if (t >= 0) {
-                const int32_t X = dir ? Wp - (hc ? posH : posN)[t] - wps[t] : (hc ? posH : posN)[t];
-                ctl.knee_ltr = dir == 0;
-                ctl.knee_l = X;
-                ctl.knee_r = X + wps[t];
-                valid = dir == 0 ? (X + wps[t] < Wp) : (X > 0);
-              }
-              ctl.knee_valid = valid;
-              ctl.knees += valid;
-            } else {
-              ctl.knee_rows += 1;
-            }
-            ctl.committed = ctl.score[best];
-            ctl.fail = ctl.abort ? 2 : (ctl.committed > Hp ? 1 : 0);
-            ctl.prev_ltr = dir == 0;
-            ctl.row_start = row_start + len;
-            ctl.row = row + 1;
-            if (area_bound && row_start + len < n) {
-              nxt2 = p.pre2[cb + row_start + len];
-              nxtE = p.preE[cb + row_start + len];
-            }
-          }
+          ctl.committed = ctl.score[best];
+          ctl.fail = ctl.abort ? 2 : (ctl.committed > Hp ? 1 : 0);
+          ctl.prev_ltr = dir == 0;
+          ctl.row_start = row_start + len;
+          ctl.row = row + 1;
         }
-        __syncthreads();
 
         // ---- H: commit ----------------------------------------------------------
         {
-          const int best = ctl.best;
           const int v = best >> 1, dir = best & 1, fold = v >> 1, hc = v & 1;
           const int len = ctl.len[v];
           const int32_t lo = fold ? ctl.region_lo : 0, hi = fold ? ctl.region_hi : Wp;
@@ -739,27 +749,6 @@ __global__ void __launch_bounds__(NT) rowloop_kernel(const Pack *__restrict__ pp
           __syncthreads();
         }
 
-        // ---- I: progressive area bound (exact; an addition to the paper) -----
-        // Every later chart is dropped onto the frontline: in column x its
-        // cover dilated by g lies inside its padded envelope, at or below
-        // front[x], and above the padded atlas bottom Hp (or the candidate
-        // fails).  Placed charts' dilated covers are pairwise disjoint (the
-        // gutter), and a connected polygon of area A and larger extent E
-        // dilated by g covers at least A + 2gE + 4g^2.  Once the charts not
-        // yet placed cannot fit that way into the area under the frontline,
-        // the candidate fails now instead of rows later.
-        if (area_bound && !ctl.fail && ctl.row_start < n) {
-          if (tid == 0) {
-            const int s = ctl.row_start;
-            const int32_t fr = Wp * Hp - ctl.front_sum;  // free texels under the frontline (sides <= 8192)
-            const uint64_t kk = 16 * (uint64_t)(j + 1), gg = (uint64_t)g;
-            const unsigned __int128 S2 = tot2 - nxt2, SE = totE - nxtE;
-            const unsigned __int128 need = S2 * (kk * kk) + ((SE * (2 * gg * kk)) << 19) +
-                                           ((unsigned __int128)(4 * gg * gg * (uint64_t)(n - s)) << 37);
-            if (need > ((unsigned __int128)(uint32_t)fr << 37)) ctl.fail = 1;
-          }
-          __syncthreads();
-        }
       }
 
       if (deferred) {  // keep the state for the next chunk
