@@ -148,7 +148,9 @@ typedef struct tabi_placement {
 typedef struct tabi_ctx tabi_ctx;
 
 /* Fill *p with the paper's defaults: gutter 1, knee 10 % / 20 %, left/right
- * significance 10 %, knee margin 1, all features on; fan-out 0 (tuned). */
+ * significance 10 %, knee margin 1, all features on, 10 local AABBs per
+ * axis, prefix-sum folding past t_opt = 1 % for atlases of more than 10,000
+ * charts; fan-out 0 (tuned). */
 void tabi_params_default(tabi_params *p);
 
 /* Create a context on CUDA device `device`.  If `arena` is non-NULL it is a
@@ -176,7 +178,12 @@ size_t tabi_arena_bytes(int32_t n_charts, int32_t n_verts, int32_t atlas_w, int3
  *                          chart;
  *   out[n_charts]          placements, input order (written on TABI_OK);
  *   out_k                  the chosen k (scale k/1024); 0 on NO_FIT.
- * The inputs are copied to the device on `stream`, the result back.
+ * The inputs are copied to the device on `stream`, the result back:
+ * buffers in pinned (cudaHostAlloc / cudaHostRegister) memory, 4-byte
+ * aligned, are read and written by a copy kernel over the host link (one
+ * launch each way for the whole batch); other host buffers take one
+ * cudaMemcpyAsync each.  Either way the buffers are only touched before the
+ * call returns.
  * Returns TABI_OK, TABI_ERR_NO_FIT, TABI_ERR_INVALID_ARG, TABI_ERR_OOM,
  * TABI_ERR_CUDA or TABI_ERR_BUSY. */
 tabi_status tabi_pack(tabi_ctx *ctx, const tabi_params *params, int32_t atlas_w, int32_t atlas_h,
@@ -209,7 +216,8 @@ typedef struct tabi_request {
  * every stage runs once over all atlases, each wave of candidate scales
  * over the atlases still searching).  Each atlas gets exactly the result
  * tabi_pack would give it alone.  HOST pointers in the requests; the
- * inputs are copied to the device on `stream`, the results back.
+ * inputs are copied to the device on `stream`, the results back (pinned
+ * buffers by the copy kernel, as for tabi_pack).
  * 1 <= n_reqs <= TABI_MAX_BATCH.  The launch sequence is captured once per
  * launch shape (fan-out, chunks, shared-memory class) into a CUDA graph
  * owned by the context and replayed for every later batch; its waves run
