@@ -23,12 +23,14 @@ constexpr int64_t kI64Max = 0x7fffffffffffffffLL;
 constexpr int64_t kI64Min = -kI64Max - 1;
 
 // Chart-local transform: translate the AABB min to the origin, rotate
-// (x, y) -> (y, W0 - x) when wider than tall, then the reflections.
+// (x, y) -> (y, W0 - x) when wider than tall, then the reflections.  Input
+// coordinates lie in (-2^20, 2^20), so every intermediate is in [0, 2^21]
+// and 32-bit arithmetic is exact.
 struct Xf {
-  int64_t minx, miny, W0, Wq, Hq;
+  int32_t minx, miny, W0, Wq, Hq;
   int rot, fy, fx;
-  __device__ __forceinline__ void apply(int32_t vx, int32_t vy, int64_t &x, int64_t &y) const {
-    const int64_t tx = (int64_t)vx - minx, ty = (int64_t)vy - miny;
+  __device__ __forceinline__ void apply(int32_t vx, int32_t vy, int32_t &x, int32_t &y) const {
+    const int32_t tx = vx - minx, ty = vy - miny;
     if (rot) { x = ty; y = W0 - tx; } else { x = tx; y = ty; }
     if (fy) y = Hq - y;
     if (fx) x = Wq - x;
@@ -71,11 +73,11 @@ __device__ void group_slices(const int32_t *__restrict__ v, int nv, const Xf &xf
   for (int i = 0; i < K; ++i) { lo[i] = 0x7fffffff; hi[i] = -0x7fffffff - 1; }
   for (int e = lane; e < nv; e += G) {
     const int e1 = (e + 1 == nv) ? 0 : e + 1;
-    int64_t x0, y0, x1, y1;
+    int32_t x0, y0, x1, y1;
     xf.apply(v[2 * e], v[2 * e + 1], x0, y0);
     xf.apply(v[2 * e1], v[2 * e1 + 1], x1, y1);
-    const int32_t u0 = (int32_t)(xaxis ? x0 : y0), w0 = (int32_t)(xaxis ? y0 : x0);
-    const int32_t u1 = (int32_t)(xaxis ? x1 : y1), w1 = (int32_t)(xaxis ? y1 : x1);
+    const int32_t u0 = xaxis ? x0 : y0, w0 = xaxis ? y0 : x0;
+    const int32_t u1 = xaxis ? x1 : y1, w1 = xaxis ? y1 : x1;
     // vertex e, in every slice that contains it
 #pragma unroll
     for (int i = 0; i < K; ++i)
@@ -160,7 +162,7 @@ __device__ __forceinline__ void prep_chart(const Pack &p, int c) {
     }
     return;
   }
-  Xf xf{mnx, mny, W0, Wq, Hq, rot, 0, 0};
+  Xf xf{mnx, mny, (int32_t)W0, (int32_t)Wq, (int32_t)Hq, rot, 0, 0};
 
   // twice the polygon's area (shoelace, input coordinates), summed per
   // atlas: the area bound on the candidate scales
@@ -293,12 +295,13 @@ __device__ __forceinline__ void prep_chart(const Pack &p, int c) {
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int am = (lane & 7) + G * r;
-      const int64_t C = kObbCos[am], S = kObbSin[am];
+      const int32_t C = kObbCos[am], S = kObbSin[am];
       u0[r] = kI64Max; u1[r] = kI64Min; v0[r] = kI64Max; v1[r] = kI64Min;
       for (int i = G >= 8 ? lane >> 3 : 0; i < nv; i += G >= 8 ? G / 8 : 1) {
-        int64_t x, y;
+        int32_t x, y;
         xf.apply(v[2 * i], v[2 * i + 1], x, y);
-        const int64_t uu = x * C + y * S, vv = -x * S + y * C;
+        // |x|, |y| <= 2^21 and C, S <= 2^14: 32 x 32 -> 64-bit products
+        const int64_t uu = (int64_t)x * C + (int64_t)y * S, vv = (int64_t)y * C - (int64_t)x * S;
         u0[r] = min(u0[r], uu); u1[r] = max(u1[r], uu);
         v0[r] = min(v0[r], vv); v1[r] = max(v1[r], vv);
       }
