@@ -50,7 +50,7 @@ METRIC = "packs/sec and p50/p99 ms per atlas, batched/served vs plain GPU packer
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--atlases", type=int, default=256)
