@@ -60,15 +60,16 @@ BOXES = [[(3, 5), (2, 2), (4, 6), (1, 3), (5, 5), (2, 4), (3, 3), (1, 1), (2, 6)
 
 @pytest.mark.parametrize("case", range(len(BOXES)))
 @pytest.mark.parametrize("k", [256, 512, 768, 1024])
-def test_boxes_match_skyline_brute_force(case, k):
+@pytest.mark.parametrize("g", [1, 0, 2])
+def test_boxes_match_skyline_brute_force(case, k, g):
     sizes = BOXES[case]
     W, H = 17, 40
     cs = synth.rectangles(sizes, W, H)
-    params = oracle.default_params(topt=1000, hybrid_min=0)  # every row is a tail row
+    params = oracle.default_params(topt=1000, hybrid_min=0, gutter=g)  # every row is a tail row
     rec = oracle.prep(cs, params)
     perm = oracle.sort(rec)
     ok, place, stats = oracle.pack_scale(rec, perm, W, H, k, params)
-    bok, exp = skyline_tail(sizes, W, H, k)
+    bok, exp = skyline_tail(sizes, W, H, k, g)
     assert ok == bok
     placed = int(stats[4])
     assert stats[5] == stats[0]  # all rows are tail rows
