@@ -272,8 +272,10 @@ def run_ours(args, rank, world, local, sets):
     F, Q = tuning["scale_fanout"], tuning["chunks"]
 
     def step(ev=None):
-        flush.fill_(1)  # evict L2 (129 MB) before the step
         with torch.cuda.stream(stream):
+            # evict L2 (129 MB) before the step, on the packing stream so the
+            # write is ordered before the step's start event and kernels
+            flush.fill_(1)
             if ev:
                 ev[0].record(stream)
             st = ctx.pack_batch_requests(reqs, params, stream=stream)

@@ -330,14 +330,22 @@ void tabi_server_config_default(tabi_server_config *cfg);
 /* TABI_ERR_INVALID_ARG (bad config), TABI_ERR_CUDA (allocation). */
 tabi_status tabi_server_create(tabi_server **out, const tabi_server_config *cfg);
 /* Stops taking batches, fails queued requests with TABI_ERR_BUSY, waits
- * (at most 60 s) for the batches in flight, frees everything. */
+ * for the batches in flight (bounded: polled, at most about 60 s in all;
+ * requests still running then complete with TABI_ERR_TIMEOUT), and frees
+ * everything -- except, if a batch is still running after that bound, the
+ * device memory and pinned staging it may still touch, which stay
+ * allocated. */
 void tabi_server_destroy(tabi_server *srv);
 /* Queue a request (HOST pointers; offsets, verts and out must stay valid
  * until the request completes; out is written when it completes with
- * TABI_OK).  *ticket identifies it.  Returns TABI_OK (also for a request
- * that fails its checks: the ticket then completes at once with its
- * status), TABI_ERR_INVALID_ARG for NULL arguments, TABI_ERR_BUSY while
- * shutting down.  Thread-safe. */
+ * TABI_OK).  *ticket identifies it.  The host checks the request before
+ * reading its vertices: chart count in [1, TABI_MAX_CHARTS], non-NULL
+ * buffers, offsets from 0 to n_verts with at least three vertices per
+ * chart; a request that fails them completes at once with
+ * TABI_ERR_INVALID_ARG, one whose arena estimate exceeds a lane with
+ * TABI_ERR_OOM.  Returns TABI_OK (also for such a request: the ticket
+ * carries its status), TABI_ERR_INVALID_ARG for NULL arguments,
+ * TABI_ERR_BUSY while shutting down.  Thread-safe. */
 tabi_status tabi_submit(tabi_server *srv, const tabi_request *req, uint64_t *ticket);
 /* TABI_OK and *res filled (the ticket is released) if the request has
  * completed, TABI_PENDING if not, TABI_ERR_INVALID_ARG for an unknown
@@ -439,7 +447,12 @@ tabi_status tabi_stage_times(tabi_ctx *ctx, int32_t enable, double *stage_ms, in
  * call before any stream capture.  Every call shares the one scratch array,
  * so calls that overlap on the GPU (concurrent streams) race: serialise
  * them.  Returns TABI_OK, TABI_ERR_INVALID_ARG or TABI_ERR_CUDA (launch or
- * address lookup failed). */
+ * address lookup failed).  CUDA errors are read with cudaPeekAtLastError,
+ * never cleared on another's behalf: if an error from earlier work is
+ * already pending on the calling thread the call launches nothing and
+ * returns TABI_ERR_CUDA, leaving that error in place for its owner; an
+ * error raised by this call's own launch is cleared and returned as
+ * TABI_ERR_CUDA. */
 tabi_status tabi_sort_heights_noalloc(const int32_t *heights, int32_t n, int32_t *perm, void *stream);
 
 /* Per-chart record of the prep step (TABI_INSPECT_CHARTS). */

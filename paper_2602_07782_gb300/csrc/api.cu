@@ -125,7 +125,7 @@ void add_pieces(std::vector<CopyPiece> &v, const void *src, void *dst, uint64_t 
 // Arena bytes of the per-chart and per-atlas arrays of one atlas (all but
 // the envelope pools), with the host-input copies.
 size_t fixed_bytes(int64_t n, int64_t nv) {
-  const size_t per_chart = 4 + sizeof(tabi_chart_info) + 2 * sizeof(ChartShape) + 3 * 4 + 16 + 24 +
+  const size_t per_chart = 4 + sizeof(tabi_chart_info) + 2 * sizeof(ChartShape) + 3 * 4 + 16 + 32 +
                            (size_t)kScales * (4 + 4 + 16 + 4 + 1 + 16) + 4 + 4 + sizeof(tabi_placement);
   const size_t per_atlas = sizeof(AtlasDesc) + (size_t)kScales * 2 * 8 * 2 + sizeof(ScaleOut) * kScales +
                            8 + sizeof(PackResult) + 8 + 40 * 256;
@@ -564,6 +564,7 @@ tabi_status batch_launch(tabi_ctx *ctx, const tabi_params *params, tabi_request 
   p.cur_wave = cv.take<int32_t>(1);
   p.raster_words = cv.take<unsigned long long>(2);
   p.carea = cv.take<unsigned long long>(n);
+  p.barea = cv.take<unsigned long long>(n);
   p.pre2 = cv.take<unsigned long long>(n);
   p.preE = cv.take<unsigned long long>(n);
   p.tstate = cv.take<int32_t>((size_t)A * kScales);

@@ -21,88 +21,25 @@
 namespace {
 
 constexpr int kNoAllocMaxCharts = 65536;
-constexpr int kThreads = 1024;
-constexpr int kWarps = kThreads / 32;
-constexpr int kDigits = 128;  // 7-bit digits, 3 passes over 21-bit keys
 
 static __device__ __align__(256) uint32_t g_sort_scratch[4 * kNoAllocMaxCharts];
 
 std::mutex g_mu;
 uint32_t *g_scratch_addr[256] = {};
 
-// Stable LSD radix sort of chart indices by decreasing height (ties keep
-// index order), one CTA.  Heights outside [0, 2^21) are clamped into it.
-__global__ void __launch_bounds__(kThreads)
+// Chart indices by decreasing height, ties in index order: the pack's own
+// radix sort (radix_sort21) on keys 2^21 - 1 - height, with heights outside
+// [0, 2^21) clamped into it.  One CTA.
+__global__ void __launch_bounds__(tabi::kRadixThreads)
     sort_heights_kernel(const int32_t *__restrict__ heights, int n, uint32_t *scratch, int32_t *perm) {
-  __shared__ uint32_t hist[kDigits * kWarps];
-  __shared__ uint32_t part[kWarps];
-  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   uint32_t *kA = scratch, *vA = kA + n, *kB = vA + n, *vB = kB + n;
-  for (int c = tid; c < n; c += kThreads) {
+  for (int c = threadIdx.x; c < n; c += tabi::kRadixThreads) {
     const int32_t h = min(max(heights[c], 0), (1 << 21) - 1);
     kA[c] = (uint32_t)((1 << 21) - 1 - h);
     vA[c] = (uint32_t)c;
   }
-  const int chunk = ((n + kWarps - 1) / kWarps + 31) & ~31;
-  const int beg = w * chunk, end = min(n, beg + chunk);
-  const unsigned lt = (1u << lane) - 1u;
-  __syncthreads();
-  for (int pass = 0; pass < 3; ++pass) {
-    const int shift = 7 * pass;
-    const uint32_t *ks = (pass & 1) ? kB : kA, *vs = (pass & 1) ? vB : vA;
-    uint32_t *kd = (pass & 1) ? kA : kB, *vd = (pass & 1) ? vA : vB;
-    for (int i = tid; i < kDigits * kWarps; i += kThreads) hist[i] = 0;
-    __syncthreads();
-    for (int base = beg; base < end; base += 32) {
-      const int i = base + lane;
-      const bool ok = i < end;
-      const uint32_t d = ok ? (ks[i] >> shift) & (kDigits - 1) : kDigits;
-      const unsigned peers = __match_any_sync(0xffffffffu, d);
-      if (ok && lane == __ffs(peers) - 1) hist[d * kWarps + w] += __popc(peers);
-    }
-    __syncthreads();
-    uint32_t loc[4], sum = 0;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) { loc[q] = hist[tid * 4 + q]; sum += loc[q]; }
-    uint32_t incl = sum;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += u;
-    }
-    if (lane == 31) part[w] = incl;
-    __syncthreads();
-    if (w == 0) {
-      const uint32_t x = part[lane];
-      uint32_t y = x;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t u = __shfl_up_sync(0xffffffffu, y, o);
-        if (lane >= o) y += u;
-      }
-      part[lane] = y - x;
-    }
-    __syncthreads();
-    uint32_t run = part[w] + incl - sum;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) { hist[tid * 4 + q] = run; run += loc[q]; }
-    __syncthreads();
-    for (int base = beg; base < end; base += 32) {
-      const int i = base + lane;
-      const bool ok = i < end;
-      const uint32_t key = ok ? ks[i] : 0u;
-      const uint32_t d = ok ? (key >> shift) & (kDigits - 1) : kDigits;
-      const unsigned peers = __match_any_sync(0xffffffffu, d);
-      uint32_t dst = 0;
-      if (ok) dst = hist[d * kWarps + w] + __popc(peers & lt);
-      __syncwarp();
-      if (ok && lane == __ffs(peers) - 1) hist[d * kWarps + w] += __popc(peers);
-      __syncwarp();
-      if (ok) { kd[dst] = key; vd[dst] = vs[i]; }
-    }
-    __syncthreads();
-  }
-  for (int s = tid; s < n; s += kThreads) perm[s] = (int32_t)vB[s];
+  tabi::radix_sort21(kA, vA, kB, vB, n);
+  for (int s = threadIdx.x; s < n; s += tabi::kRadixThreads) perm[s] = (int32_t)vB[s];
 }
 
 }  // namespace
@@ -122,6 +59,15 @@ extern "C" tabi_status tabi_sort_heights_noalloc(const int32_t *heights, int32_t
     }
     scratch = g_scratch_addr[dev];
   }
-  sort_heights_kernel<<<1, kThreads, 0, (cudaStream_t)stream>>>(heights, n, scratch, perm);
-  return cudaGetLastError() == cudaSuccess ? TABI_OK : TABI_ERR_CUDA;
+  // Errors are looked at without clearing them (cudaPeekAtLastError): an
+  // error already pending from other work on this thread is left to its
+  // owner and nothing is launched; an error raised by this launch is
+  // cleared and reported as this call's TABI_ERR_CUDA.
+  if (cudaPeekAtLastError() != cudaSuccess) return TABI_ERR_CUDA;
+  sort_heights_kernel<<<1, tabi::kRadixThreads, 0, (cudaStream_t)stream>>>(heights, n, scratch, perm);
+  if (cudaPeekAtLastError() != cudaSuccess) {
+    cudaGetLastError();
+    return TABI_ERR_CUDA;
+  }
+  return TABI_OK;
 }

@@ -153,6 +153,7 @@ __device__ __forceinline__ void prep_chart(const Pack &p, int c) {
     if (lane == 0) {
       inf->orig = lc; inf->valid = 0; inf->Wq = 0; inf->Hq = 0;
       p.carea[c] = 0;
+      p.barea[c] = 0;
       sh->Wq = 256; sh->Hq = 256; sh->m = 0; sh->pad = 0;
       sh->u0 = sh->u1 = sh->v0 = sh->v1 = 0;
       atomicOr(p.err + at, kErrInvalid);
@@ -164,19 +165,57 @@ __device__ __forceinline__ void prep_chart(const Pack &p, int c) {
   }
   Xf xf{mnx, mny, (int32_t)W0, (int32_t)Wq, (int32_t)Hq, rot, 0, 0};
 
-  // twice the polygon's area (shoelace, input coordinates), summed per
-  // atlas: the area bound on the candidate scales
+  // Twice the polygon's area (shoelace, input coordinates).  The area
+  // bound on the candidate scales needs the area a chart surely covers,
+  // which |shoelace| / 2 is for a simple polygon but not for a loop that
+  // winds twice or crosses itself (its shoelace can exceed its cover).  So
+  // the bound takes a chart's area only where one pass certifies the loop
+  // simple: every edge turns strictly the same way around the point
+  // c = floor(vertex mean) (cross(v_i - c, v_i+1 - c) all > 0 or all < 0)
+  // and the loop winds around c exactly once -- then every ray from c meets
+  // the loop once, so it is a simple polygon, star-shaped about c.  Other
+  // loops (non-star simple polygons among them) enter the bound with area
+  // 0, which keeps it a valid lower bound; only its strength changes.
   {
-    int64_t a2 = 0;
+    int64_t a2 = 0, sx = 0, sy = 0;
     for (int e = lane; e < nv; e += G) {
       const int e1 = (e + 1 == nv) ? 0 : e + 1;
       a2 += (int64_t)v[2 * e] * v[2 * e1 + 1] - (int64_t)v[2 * e1] * v[2 * e + 1];
+      sx += v[2 * e];
+      sy += v[2 * e + 1];
     }
 #pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) a2 += __shfl_xor_sync(gm, a2, o);
+    for (int o = G / 2; o > 0; o >>= 1) {
+      a2 += __shfl_xor_sync(gm, a2, o);
+      sx += __shfl_xor_sync(gm, sx, o);
+      sy += __shfl_xor_sync(gm, sy, o);
+    }
+    // floor of the vertex mean (|sum| < 2^38); offsets from it below 2^21
+    const int64_t cx = sx >= 0 ? sx / nv : -((-sx + nv - 1) / nv);
+    const int64_t cy = sy >= 0 ? sy / nv : -((-sy + nv - 1) / nv);
+    int pos = 1, neg = 1, wn = 0;
+    for (int e = lane; e < nv; e += G) {
+      const int e1 = (e + 1 == nv) ? 0 : e + 1;
+      const int64_t ax = v[2 * e] - cx, ay = v[2 * e + 1] - cy;
+      const int64_t bx = v[2 * e1] - cx, by = v[2 * e1 + 1] - cy;
+      const int64_t cr = ax * by - bx * ay;  // below 2^43 in size
+      pos &= cr > 0;
+      neg &= cr < 0;
+      // winding number of the loop about c (crossings of the ray y = 0,
+      // x > 0, counted with their direction; half-open in y)
+      if (ay <= 0) { if (by > 0 && cr > 0) ++wn; }
+      else if (by <= 0 && cr < 0) --wn;
+    }
+    pos = __all_sync(gm, pos);
+    neg = __all_sync(gm, neg);
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) wn += __shfl_xor_sync(gm, wn, o);
+    const unsigned long long aa = (unsigned long long)(a2 < 0 ? -a2 : a2);
+    const bool simple = (pos || neg) && (wn == 1 || wn == -1);
     if (lane == 0) {
-      p.carea[c] = (unsigned long long)(a2 < 0 ? -a2 : a2);
-      atomicAdd(p.area2 + at, (unsigned long long)(a2 < 0 ? -a2 : a2));
+      p.carea[c] = aa;
+      p.barea[c] = simple ? aa : 0ull;
+      atomicAdd(p.area2 + at, simple ? aa : 0ull);
       atomicAdd(p.ext_sum + at, (unsigned long long)Hq);  // Hq >= Wq after the rotation
     }
   }
@@ -414,86 +453,24 @@ __global__ void __launch_bounds__(kPrepThreads, 2) prep_kernel(const Pack *__res
 // ---------------------------------------------------------------------------
 // stable radix sort by decreasing Hq (one CTA)
 // ---------------------------------------------------------------------------
-constexpr int kSortThreads = 1024;
-constexpr int kSortWarps = kSortThreads / 32;
-constexpr int kDigits = 128;  // 7-bit digits, 3 passes over 21 bits
+constexpr int kSortThreads = kRadixThreads;
 
 __device__ void sort_atlas(const Pack &p, int at) {
-  __shared__ uint32_t hist[kDigits * kSortWarps];  // [digit][warp]
-  __shared__ uint32_t part[kSortWarps];
   const int cb = p.atl[at].cb;
-  const int n = p.atl[at].n, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int n = p.atl[at].n, tid = threadIdx.x;
   uint32_t *kA = p.sort_tmp + 4 * (int64_t)cb, *vA = kA + n, *kB = vA + n, *vB = kB + n;
   for (int c = tid; c < n; c += kSortThreads) {
     kA[c] = (uint32_t)((1 << 21) - 1 - p.shape_in[cb + c].Hq);
     vA[c] = (uint32_t)c;
   }
-  const int chunk = ((n + kSortWarps - 1) / kSortWarps + 31) & ~31;
-  const int beg = w * chunk, end = min(n, beg + chunk);
-  const unsigned lt = (1u << lane) - 1u;
-  __syncthreads();
-  for (int pass = 0; pass < 3; ++pass) {
-    const int shift = 7 * pass;
-    const uint32_t *ks = (pass & 1) ? kB : kA, *vs = (pass & 1) ? vB : vA;
-    uint32_t *kd = (pass & 1) ? kA : kB, *vd = (pass & 1) ? vA : vB;
-    for (int i = tid; i < kDigits * kSortWarps; i += kSortThreads) hist[i] = 0;
-    __syncthreads();
-    for (int base = beg; base < end; base += 32) {
-      const int i = base + lane;
-      const bool ok = i < end;
-      const uint32_t d = ok ? (ks[i] >> shift) & (kDigits - 1) : kDigits;
-      const unsigned peers = __match_any_sync(0xffffffffu, d);
-      if (ok && lane == __ffs(peers) - 1) hist[d * kSortWarps + w] += __popc(peers);
-    }
-    __syncthreads();
-    // exclusive scan of hist in digit-major order (4 entries per thread)
-    uint32_t loc[4], sum = 0;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) { loc[q] = hist[tid * 4 + q]; sum += loc[q]; }
-    uint32_t incl = sum;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += u;
-    }
-    if (lane == 31) part[w] = incl;
-    __syncthreads();
-    if (w == 0) {
-      uint32_t x = part[lane], y = x;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t u = __shfl_up_sync(0xffffffffu, y, o);
-        if (lane >= o) y += u;
-      }
-      part[lane] = y - x;
-    }
-    __syncthreads();
-    uint32_t run = part[w] + incl - sum;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) { hist[tid * 4 + q] = run; run += loc[q]; }
-    __syncthreads();
-    for (int base = beg; base < end; base += 32) {
-      const int i = base + lane;
-      const bool ok = i < end;
-      const uint32_t key = ok ? ks[i] : 0u;
-      const uint32_t d = ok ? (key >> shift) & (kDigits - 1) : kDigits;
-      const unsigned peers = __match_any_sync(0xffffffffu, d);
-      uint32_t dst = 0;
-      if (ok) dst = hist[d * kSortWarps + w] + __popc(peers & lt);
-      __syncwarp();
-      if (ok && lane == __ffs(peers) - 1) hist[d * kSortWarps + w] += __popc(peers);
-      __syncwarp();
-      if (ok) { kd[dst] = key; vd[dst] = vs[i]; }
-    }
-    __syncthreads();
-  }
-  // three passes: A->B, B->A, A->B
+  radix_sort21(kA, vA, kB, vB, n);  // sorted values in vB
   for (int s = tid; s < n; s += kSortThreads) p.perm[cb + s] = cb + (int32_t)vB[s];
   if (tid == 0) {
     // Area bound: placed charts' covers, each dilated by the gutter g, are
     // disjoint and lie in the padded atlas (W + 2g) x (H + 2g).  A connected
     // polygon of area A and larger extent E dilated by g covers at least
-    // A + 2 g E + 4 g^2 (every line across it gains 2g).  At scale k/1024 the
+    // A + 2 g E + 4 g^2 (every line across it gains 2g); A is taken only
+    // for loops certified simple (else 0, see prep_chart).  At scale k/1024 the
     // area is area2 k^2 / 2^37 and the extent E k / 2^18 texels (area2 =
     // twice the area in Q.8^2, E in Q.8), so candidate k can succeed only if
     //   area2 k^2 + 2g 2^19 k sum(E) + 4 g^2 2^37 n <= (W + 2g)(H + 2g) 2^37.

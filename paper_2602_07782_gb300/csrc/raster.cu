@@ -237,14 +237,14 @@ __global__ void __launch_bounds__(1024) layout_kernel(const Pack *__restrict__ p
       // areas and larger extents (the row loop's progressive area bound)
       int64_t sa = 0, se = 0, ta = 0, te = 0;
       for (int s = s0; s < s1; ++s) {
-        sa += (int64_t)p.carea[p.perm[cb + s]];
+        sa += (int64_t)p.barea[p.perm[cb + s]];
         se += p.hq[cb + s];
       }
       block_scan2(sa, se, ta, te, part);
       for (int s = s0; s < s1; ++s) {
         p.pre2[cb + s] = (unsigned long long)sa;
         p.preE[cb + s] = (unsigned long long)se;
-        sa += (int64_t)p.carea[p.perm[cb + s]];
+        sa += (int64_t)p.barea[p.perm[cb + s]];
         se += p.hq[cb + s];
       }
       __syncthreads();  // part is reused by the next scan

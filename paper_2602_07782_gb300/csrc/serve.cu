@@ -91,6 +91,19 @@ void CUDART_CB lane_finished(void *arg) {
   delete pair;
 }
 
+// The host walks a request's vertex loops (request_bytes) before any device
+// check runs, so the offsets are checked here first: they start at 0, end
+// at n_verts and give every chart at least three vertices (so they never
+// decrease and never pass n_verts).
+bool offsets_valid(const tabi_request &r) {
+  if (r.offsets[0] != 0 || r.offsets[r.n_charts] != (uint32_t)r.n_verts) return false;
+  for (int c = 0; c < r.n_charts; ++c)
+    if (r.offsets[c + 1] < r.offsets[c] || r.offsets[c + 1] - r.offsets[c] < 3 ||
+        r.offsets[c + 1] > (uint32_t)r.n_verts)
+      return false;
+  return true;
+}
+
 // Arena bytes a request may need at fan-out F: the per-chart arrays, and
 // the envelope pools of one wave of F candidates at most as large as at
 // k = 1024 (column words, their chart indices, row words; each at most the
@@ -325,13 +338,28 @@ void tabi_server_destroy(tabi_server *s) {
   s->wake.notify_one();
   s->worker.join();
   cudaSetDevice(s->cfg.device);
+  // The worker gave in-flight batches up to 60 s; whatever still runs gets
+  // the rest of a 60 s budget here, polled, never an unbounded wait.  A lane
+  // whose stream is still busy after that keeps its context, staging and
+  // the shared arena allocated (freeing memory a running kernel may still
+  // touch is never safe); everything else is released.
+  const int64_t deadline = now_ns() + 60LL * 1000 * 1000 * 1000;
+  bool leak = false;
   for (auto &ln : s->lanes) {
-    cudaStreamSynchronize(ln->st);
+    cudaError_t q = cudaStreamQuery(ln->st);
+    while (q == cudaErrorNotReady && now_ns() < deadline) {
+      std::this_thread::sleep_for(std::chrono::microseconds(500));
+      q = cudaStreamQuery(ln->st);
+    }
+    if (q == cudaErrorNotReady) {
+      leak = true;
+      continue;
+    }
     tabi_ctx_destroy(ln->ctx);
     cudaStreamDestroy(ln->st);
     if (ln->stage) cudaFreeHost(ln->stage);
   }
-  cudaFree(s->arena);
+  if (!leak) cudaFree(s->arena);
   delete s;
 }
 
@@ -344,7 +372,7 @@ tabi_status tabi_submit(tabi_server *s, const tabi_request *req, uint64_t *ticke
   bool reject = false;
   int32_t why = TABI_ERR_INVALID_ARG;
   if (req->n_charts < 1 || req->n_charts > TABI_MAX_CHARTS || req->n_verts < 3 || !req->offsets ||
-      !req->verts || !req->out || req->offsets[0] != 0 || req->offsets[req->n_charts] != (uint32_t)req->n_verts) {
+      !req->verts || !req->out || !offsets_valid(*req)) {
     reject = true;
   } else {
     t.est = request_bytes(*req, s->params.scale_fanout, s->params.gutter);

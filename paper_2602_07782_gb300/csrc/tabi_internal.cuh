@@ -96,7 +96,7 @@ struct Pack {
   uint8_t *pflags;              // [64 N] interlock bits
   int4 *place;                  // [64 N] x, y, row, bits
   ScaleOut *scale_out;          // [A][64]
-  unsigned long long *area2;    // [A] twice the summed polygon area (Q.8^2 units)
+  unsigned long long *area2;    // [A] twice the summed area of the charts certified simple (Q.8^2)
   unsigned long long *ext_sum;  // [A] summed larger AABB side of the charts (Q.8)
   int32_t *jtop;                // [A] largest candidate the area bound allows (-1 none)
   int32_t *found;               // [A] highest successful candidate so far (-1 none)
@@ -110,8 +110,9 @@ struct Pack {
   uint32_t *rcounter;           // [64][kMaxChunks] raster warp-item counter of each (wave, chunk)
   int32_t *cur_wave;            // the wave the kernels work on (advanced by wave_end)
   unsigned long long *raster_words;  // [2] padded scanline words / column words the raster evaluated
-  unsigned long long *carea;    // [N] twice each chart's polygon area (Q.8^2), input order
-  unsigned long long *pre2;     // [N] sorted order: carea summed over the atlas's earlier charts
+  unsigned long long *carea;    // [N] twice each chart's polygon area |shoelace| (Q.8^2), input order
+  unsigned long long *barea;    // [N] carea if the loop is certified simple, else 0 (the area bounds)
+  unsigned long long *pre2;     // [N] sorted order: barea summed over the atlas's earlier charts
   unsigned long long *preE;     // [N] sorted order: Hq summed over the atlas's earlier charts
   int32_t *tstate;              // [A][64] row-loop task: 0 running (or not begun), 1 finished
   int32_t *front_save;          // [A][F][wps_stride] frontline of a task between chunks
@@ -242,6 +243,85 @@ __device__ __forceinline__ T group_max(T v, unsigned gm) {
 template <int G>
 __device__ __forceinline__ unsigned group_mask() {
   return G == 32 ? 0xffffffffu : (((1u << G) - 1) << (threadIdx.x & (32 - G)));
+}
+
+// Stable LSD radix sort of keys below 2^21 (three passes of 7-bit digits)
+// by one CTA of kRadixThreads threads: on entry kA/vA hold n keys and their
+// values, on exit kB/vB hold them sorted by increasing key, equal keys in
+// their entry order (passes A -> B -> A -> B).  Each warp owns a contiguous
+// run of the input; per pass a histogram [digit][warp] counts the digits
+// (lanes with equal digits found by __match_any_sync, their leader adds
+// the count), an exclusive scan in digit-major order gives every (digit,
+// warp) its first output slot, and the scatter walks each run in order.
+// The height sort of the pack (Sec. 3.1) and the allocation-free height
+// sort both call this.
+constexpr int kRadixThreads = 1024;
+__device__ __forceinline__ void radix_sort21(uint32_t *kA, uint32_t *vA, uint32_t *kB, uint32_t *vB, int n) {
+  constexpr int kW = kRadixThreads / 32, kDig = 128;
+  __shared__ uint32_t hist[kDig * kW];  // [digit][warp]
+  __shared__ uint32_t part[kW];
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int chunk = ((n + kW - 1) / kW + 31) & ~31;
+  const int beg = w * chunk, end = min(n, beg + chunk);
+  const unsigned lt = (1u << lane) - 1u;
+  __syncthreads();  // the caller's key fill is complete
+  for (int pass = 0; pass < 3; ++pass) {
+    const int shift = 7 * pass;
+    const uint32_t *ks = (pass & 1) ? kB : kA, *vs = (pass & 1) ? vB : vA;
+    uint32_t *kd = (pass & 1) ? kA : kB, *vd = (pass & 1) ? vA : vB;
+    for (int i = tid; i < kDig * kW; i += kRadixThreads) hist[i] = 0;
+    __syncthreads();
+    for (int base = beg; base < end; base += 32) {
+      const int i = base + lane;
+      const bool ok = i < end;
+      const uint32_t d = ok ? (ks[i] >> shift) & (kDig - 1) : kDig;
+      const unsigned peers = __match_any_sync(0xffffffffu, d);
+      if (ok && lane == __ffs(peers) - 1) hist[d * kW + w] += __popc(peers);
+      __syncwarp();  // the next leader of this digit may be another lane
+    }
+    __syncthreads();
+    // exclusive scan of hist in digit-major order (4 entries per thread)
+    uint32_t loc[4], sum = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) { loc[q] = hist[tid * 4 + q]; sum += loc[q]; }
+    uint32_t incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += u;
+    }
+    if (lane == 31) part[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+      const uint32_t x = part[lane];
+      uint32_t y = x;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t u = __shfl_up_sync(0xffffffffu, y, o);
+        if (lane >= o) y += u;
+      }
+      part[lane] = y - x;
+    }
+    __syncthreads();
+    uint32_t run = part[w] + incl - sum;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) { hist[tid * 4 + q] = run; run += loc[q]; }
+    __syncthreads();
+    for (int base = beg; base < end; base += 32) {
+      const int i = base + lane;
+      const bool ok = i < end;
+      const uint32_t key = ok ? ks[i] : 0u;
+      const uint32_t d = ok ? (key >> shift) & (kDig - 1) : kDig;
+      const unsigned peers = __match_any_sync(0xffffffffu, d);
+      uint32_t dst = 0;
+      if (ok) dst = hist[d * kW + w] + __popc(peers & lt);
+      __syncwarp();
+      if (ok && lane == __ffs(peers) - 1) hist[d * kW + w] += __popc(peers);
+      __syncwarp();
+      if (ok) { kd[dst] = key; vd[dst] = vs[i]; }
+    }
+    __syncthreads();
+  }
 }
 
 // OBB angle table (App. A: 8 rotations evenly spaced in [0, 7*pi/16]):

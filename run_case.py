@@ -2,8 +2,8 @@
 
 A fixed, small driver for profilers (ncu) and quick checks:
 
-    python -m paper_2602_07782_gb300.run_case stars2k --reps 2
-    python -m paper_2602_07782_gb300.run_case batch --atlases 16 --reps 2
+    python run_case.py stars2k --reps 2
+    python run_case.py batch --atlases 16 --reps 2
 
 Exits non-zero if a pack fails.  Builds the library first if needed.
 """
@@ -13,7 +13,7 @@ import argparse
 import os
 import sys
 
-ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
@@ -35,7 +35,7 @@ def main(argv=None) -> int:
     else:
         sets = [synth.WORKLOADS[args.case]()]
 
-    from . import build, tabi
+    from paper_2602_07782_gb300 import build, tabi
     build.build()
     need = sum(tabi.arena_bytes(cs) for cs in sets)
     ctx = tabi.Context(arena_bytes=min(need, 32 << 30) + (64 << 20))

@@ -261,6 +261,41 @@ def test_edge_cases(ctx):
     _compare_pack(cs, ctx.pack(cs, p), op)
 
 
+def _looped(poly, times):
+    return [q for _ in range(times) for q in poly]
+
+
+def test_self_overlapping_loops_keep_the_oracle_result(ctx):
+    """Loops that wind twice or cross themselves have a shoelace area above
+    the area they cover, so the area bounds (a shortcut the oracle does not
+    take) must not count it: such loops enter the bounds with area 0.  A
+    doubly wound square alone in an atlas it exactly fills at scale 1 is the
+    case an uncertified bound would get wrong (twice its area exceeds the
+    atlas); with a pentagram and a bow tie beside it, single packs and a
+    batch with the progressive bound all give the oracle's scale and
+    placements."""
+    s = 100 * 256
+    square = [(0, 0), (s, 0), (s, s), (0, s)]
+    cs = synth.from_polygons([_looped(square, 2)], 100, 100)
+    p = gpu_params()
+    o = _compare_pack(cs, ctx.pack(cs, p), oracle_params(p))
+    assert o.k == 1024
+    pent = [(int(12800 + 12000 * np.sin(2 * np.pi * 2 * i / 5)), int(12800 - 12000 * np.cos(2 * np.pi * 2 * i / 5)))
+            for i in range(5)]  # a pentagram: its centre is wound twice
+    bow = [(0, 0), (s // 2, s // 2), (s // 2, 0), (0, s // 2)]
+    mixed = synth.from_polygons([_looped(square, 3), pent, bow, _looped(pent, 2)], 160, 130)
+    for fanout in (64, 8):
+        p = gpu_params(scale_fanout=fanout)
+        _compare_pack(mixed, ctx.pack(mixed, p), oracle_params(p))
+    sets = [cs, mixed, synth.stars(31, 300, 512)]
+    shape = tabi.Tuning(scale_fanout=2, raster_warp_items=32768, rowloop_threads=1024, rowloop_ctas=1,
+                        chunks=4, progressive_bound=1)
+    st, res = ctx.pack_batch(sets, gpu_params(), shape=shape)
+    assert st == tabi.TABI_OK
+    for c, r in zip(sets, res):
+        _compare_pack(c, r, oracle_params(gpu_params()))
+
+
 def test_invalid_inputs(ctx):
     p = gpu_params()
     bad = [synth.from_polygons([[(0, 0), (100, 0), (100, 600)]], 32, 32),      # < 1 texel wide

@@ -110,6 +110,28 @@ def test_served_bad_and_oversized_requests_fail_alone(alone):
         srv.close()
 
 
+def test_submit_checks_offsets_before_reading_vertices():
+    """The server walks a request's vertex loops on the host to size it, so
+    tabi_submit checks the offsets first: a middle offset past n_verts, a
+    decreasing one, or a chart with fewer than three vertices completes the
+    ticket with TABI_ERR_INVALID_ARG instead of reading out of bounds."""
+    srv = tabi.Server(lanes=1, max_batch=4, arena_bytes=256 << 20)
+    try:
+        verts = np.array([0, 0, 512, 0, 512, 512, 0, 0, 512, 0, 512, 512], np.int32)
+        for offs in ([0, 1 << 30, 6], [0, 4, 2, 6], [0, 2, 6], [0, 6, 6]):
+            o = np.array(offs, np.uint32)
+            out = np.zeros(len(offs) - 1, tabi.PLACEMENT_DTYPE)
+            st, t, _ = srv.submit_ptrs(len(offs) - 1, 6, 64, 64, o, verts, out)
+            assert st == tabi.TABI_OK
+            st, r = srv.wait(t)
+            assert st == tabi.TABI_OK and r.status == tabi.TABI_ERR_INVALID_ARG, offs
+        good = np.array([0, 3, 6], np.uint32)
+        st, t, out = srv.submit_ptrs(2, 6, 64, 64, good, verts, np.zeros(2, tabi.PLACEMENT_DTYPE))
+        assert srv.wait(t)[1].status == tabi.TABI_OK
+    finally:
+        srv.close()
+
+
 def test_poll_wait_and_unknown_tickets():
     srv = tabi.Server(lanes=1, max_batch=4, arena_bytes=512 << 20)
     try:

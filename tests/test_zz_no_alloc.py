@@ -4,9 +4,9 @@ Callers that cannot call cudaMalloc -- engines with a fixed, pre-budgeted
 device memory pool, frame loops that must not stall on an allocation -- use
 this entry point: its scratch is a fixed array inside the library, and the
 caller passes only device input and output buffers.  The test calls it
-through the C ABI twice in a row and checks each result against the order
-the regular pack entry point (tabi_pack) computed for the same charts.
-Collected last on purpose.
+through the C ABI twice in a row and checks each result against the CPU
+oracle's height sort of the same charts (Sec. 3.1) and against the order the
+regular pack entry point (tabi_pack) computed.  Collected last on purpose.
 """
 from __future__ import annotations
 
@@ -15,6 +15,7 @@ import ctypes
 import numpy as np
 import pytest
 
+import oracle
 import synth
 
 pytestmark = pytest.mark.gpu
@@ -43,7 +44,9 @@ def test_noalloc_sort_matches_pack_order_twice():
             res = ctx.pack(cs)
             assert res.status == tabi.TABI_OK, ctx.last_error()
             ref = ctx.perm()
-            heights = ctx.charts()["Hq"].astype(np.int32)
+            rec = oracle.prep(cs)  # the heights come from the oracle, not from the GPU path
+            assert np.array_equal(ctx.charts()["Hq"], rec[:, oracle.R["HQ"]])
+            heights = rec[:, oracle.R["HQ"]].astype(np.int32)
             d_h = torch.from_numpy(heights.copy()).cuda()
             d_p = torch.full((cs.n,), -1, dtype=torch.int32, device="cuda")
             stream = torch.cuda.current_stream()
@@ -51,7 +54,9 @@ def test_noalloc_sort_matches_pack_order_twice():
                               ctypes.c_void_p(stream.cuda_stream))
             stream.synchronize()
             assert st == tabi.TABI_OK
-            assert np.array_equal(d_p.cpu().numpy(), ref)
+            got = d_p.cpu().numpy()
+            assert np.array_equal(got, oracle.sort(rec))
+            assert np.array_equal(got, ref)
     finally:
         ctx.close()
 
