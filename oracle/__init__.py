@@ -8,8 +8,10 @@ CUDA path except the seeded inputs from ``synth``.
 Functions follow the paper's steps (Gu, Vining, Sheffer, arXiv 2602.07782):
 ``prep`` (Sec. 3.1, Sec. 4.1.1, App. A), ``sort`` (Sec. 3.1),
 ``envelope``/``envelope_padded`` (App. A "Parallel Pushing Algorithm",
-Sec. 5 gutters), ``hcompact`` (Sec. 4.1.2, App. A interlock), ``pack_scale``
-(Algorithms 2-5, Sec. 4.2) and ``pack`` (the scale search, Sec. 3.1 / Sec. 5).
+Sec. 4.1.1 merge, Sec. 5 gutters), ``hcompact`` (Sec. 4.1.2, App. A
+interlock), ``pack_scale`` (Algorithms 2-5, Sec. 4.2, the prefix-sum tail of
+Sec. 4.4) and ``pack`` (the scale search, Sec. 3.1 / Sec. 5, with Sec. 4.4's
+area-weighted choice).
 """
 from __future__ import annotations
 
@@ -30,8 +32,7 @@ REC = 128
 # record field offsets (mirror of the enum in tabi_oracle.c)
 R = dict(ORIG=0, MINX=1, MINY=2, W0=3, H0=4, WQ=5, HQ=6, ROT=7, FLIPY=8, FLIPX=9,
          OBBM=10, U0=11, U1=12, V0=13, V1=14, X=15, Y=26, YLO=37, YHI=47, XLO=57,
-         XHI=67, TLO=77, BHI=87, LLO=97, RHI=107, ATOP=117, ABOT=118, ALEFT=119,
-         ARIGHT=120, ABL2=121, ABR2=122, LK=123)
+         XHI=67, ATOP=77, ABOT=78, ALEFT=79, ARIGHT=80, ABL2=81, ABR2=82, LK=83)
 
 F_HC, F_BALANCE, F_OBB, F_LAABB = 1, 2, 4, 8
 F_ALL = F_HC | F_BALANCE | F_OBB | F_LAABB
@@ -173,14 +174,15 @@ def scale_pairs(rec, perm, k, params=None):
 
 
 def pack_scale(rec, perm, W, H, k, params=None):
-    """Algorithm 5 at one scale.  Returns (success, place[n,6] in sorted order
+    """Algorithm 5 at one scale.  Returns (success, place[n,7] in sorted order
     (x, y, mirror, row, compacting on, fold: 0 atlas width, 1 knee, 2 prefix-sum
-    tail), stats[6]: rows, knee-folded rows, knees found, final max frontline,
-    charts placed, tail rows)."""
+    tail, the chart's scale: k, or the tail's k'), stats[8]: rows, knee-folded
+    rows, knees found, final max frontline, charts placed, tail rows, the
+    tail's scale k' (0: none), first tail chart (n: none))."""
     params = default_params() if params is None else params
     n = rec.shape[0]
-    place = np.full((n, 6), -1, np.int32)
-    stats = np.zeros(6, np.int32)
+    place = np.full((n, 7), -1, np.int32)
+    stats = np.zeros(8, np.int32)
     ok = lib().oracle_pack_scale(n, _p(np.ascontiguousarray(rec)), _p(np.ascontiguousarray(perm, np.int32)),
                                  int(W), int(H), int(k), _p(params), _p(place), _p(stats))
     if ok < 0:
@@ -191,23 +193,28 @@ def pack_scale(rec, perm, W, H, k, params=None):
 @dataclass
 class PackResult:
     status: int  # 0 ok, 1 invalid, 2 no fit
-    k: int
-    place: np.ndarray  # int32[n, 10]: x, y, rot90, flip_x, flip_y, mirror, row, sorted pos, hc, fold
+    k: int       # the chosen candidate S
+    place: np.ndarray  # int32[n, 11]: x, y, rot90, flip_x, flip_y, mirror, row, sorted pos, hc, fold, k
     success: np.ndarray | None  # int32[64] per candidate j=1..64 (k=16j) if all_scales
-    stats: np.ndarray
+    stats: np.ndarray  # int32[8] of the chosen candidate (see pack_scale)
+    score: int = 0     # sum over charts of twice the area (Q.8^2) x the chart's scale
 
 
 def pack(cs, params=None, all_scales=False):
+    """The scale search (Sec. 3.1, Sec. 5) with Sec. 4.4's area-weighted
+    choice among the successful candidates."""
     params = default_params() if params is None else params
     offs = np.ascontiguousarray(cs.offsets, np.uint32)
     verts = np.ascontiguousarray(cs.verts, np.int32)
     out_k = np.zeros(1, np.int32)
-    place = np.full((cs.n, 10), -1, np.int32)
+    place = np.full((cs.n, 11), -1, np.int32)
     succ = np.zeros(64, np.int32)
-    stats = np.zeros(6, np.int32)
+    stats = np.zeros(12, np.int32)
     st = lib().oracle_pack(cs.n, _p(offs), _p(verts), int(cs.atlas_w), int(cs.atlas_h), _p(params),
                            1 if all_scales else 0, _p(out_k), _p(place), _p(succ), _p(stats))
-    return PackResult(int(st), int(out_k[0]), place, succ if all_scales else None, stats)
+    lo, hi = (int(v) for v in stats[8:12].view(np.int64))
+    score = (hi << 64) + (lo & ((1 << 64) - 1))
+    return PackResult(int(st), int(out_k[0]), place, succ if all_scales else None, stats[:8].copy(), score)
 
 
 def _pack_one(args):

@@ -15,14 +15,16 @@
  *             (K = 10, App. A; 2 and 5 are the Tab. 13 ablation);
  *             App. A "Computing Chart Orientations": vertical then horizontal
  *             reflection from the slice areas;
- *             Sec. 4.1.1 "merge ... tighter bound": slice refinement;
  *             App. A "Computing Oriented Bounding Boxes": 8 angles in
  *             [0, 7pi/16], minimum-area box.
  *   sort      Sec. 3.1: decreasing AABB height.
  *   envelope  App. A "Parallel Pushing Algorithm": TopEdge/BottomEdge per
  *             texel column as the tighter of the two proxies, top rounded
  *             outward, bottom rounded outward; the same per texel row
- *             (left/right extents) for horizontal compaction; Sec. 5 gutters.
+ *             (left/right extents) for horizontal compaction; Sec. 4.1.1
+ *             "merge ... taking the tighter bound": the local-AABB proxy's
+ *             bound in a column is the tighter of the x-slices' and the
+ *             y-slices' bounds there; Sec. 5 gutters.
  *   hcompact  Sec. 4.1.2 compacting distance; App. A "Detecting Interlocking
  *             Charts" (CannotMoveAbove).
  *   row loop  Algorithm 5 with Algorithm 4 (FoldRow), Algorithm 2
@@ -30,9 +32,12 @@
  *             (UpdateKneeLocation), knee detection (App. A "Knee Detection
  *             Parameters") and the hierarchical selection of Sec. 4.2.
  *   hybrid    Sec. 4.4: past the rows with knees and tall charts, the rest
- *             of the charts are folded by a prefix sum of their offsets and
- *             pushed row by row in a fixed direction pattern.
- *   search    Sec. 3.1 / Sec. 5: 64 candidate scales, largest success wins.
+ *             of the charts are folded by a prefix sum of their offsets,
+ *             downscaled until the overflowing rows fit, and pushed row by
+ *             row in a fixed direction pattern.
+ *   search    Sec. 3.1 / Sec. 5: 64 candidate scales; Sec. 4.4: the success
+ *             with the largest area-weighted mean final scale wins (without
+ *             a tail: the largest successful scale).
  *
  * Integer conventions (the paper fixes no precision):
  *   vertices are int32 in 1/256 texel ("Q.8"); a candidate scale is k/1024
@@ -62,10 +67,9 @@ enum {
   R_OBBM = 10, R_U0, R_U1, R_V0, R_V1,
   R_X = 15,            /* X[0..K]   x-slice boundaries          */
   R_Y = 26,            /* Y[0..K]   y-slice boundaries          */
-  R_YLO = 37, R_YHI = 47, R_XLO = 57, R_XHI = 67,  /* raw final slices      */
-  R_TLO = 77, R_BHI = 87, R_LLO = 97, R_RHI = 107, /* refined pieces        */
-  R_ATOP = 117, R_ABOT, R_ALEFT, R_ARIGHT, R_ABL2, R_ABR2,
-  R_LK = 123           /* K: local AABBs per axis of this record         */
+  R_YLO = 37, R_YHI = 47, R_XLO = 57, R_XHI = 67,  /* final slices          */
+  R_ATOP = 77, R_ABOT, R_ALEFT, R_ARIGHT, R_ABL2, R_ABR2,
+  R_LK = 83            /* K: local AABBs per axis of this record         */
 };
 
 /* ---- params (int32 array) ------------------------------------------------ */
@@ -248,31 +252,6 @@ static int prep_one(int nv, const int32_t *v, const int32_t *params, int64_t *r)
     r[R_XLO + i] = xlo[i]; r[R_XHI + i] = xhi[i];
   }
 
-  /* Sec. 4.1.1 merge: each x-slice's top (bottom) is tightened by the first */
-  /* (last) y-slice whose x-range meets it; each y-slice's left (right) by   */
-  /* the first (last) x-slice whose y-range meets it.  READING: the merge is */
-  /* a per-slice refinement, closed-interval intersection tests.             */
-  for (int i = 0; i < K; ++i) {
-    int64_t t2 = INT64_MAX, b2v = INT64_MIN;
-    for (int j = 0; j < K; ++j)
-      if (xlo[j] <= X[i + 1] && xhi[j] >= X[i]) {
-        t2 = mn64(t2, Y[j]);
-        b2v = mx64(b2v, Y[j + 1]);
-      }
-    r[R_TLO + i] = mx64(ylo[i], t2);
-    r[R_BHI + i] = mn64(yhi[i], b2v);
-  }
-  for (int j = 0; j < K; ++j) {
-    int64_t l2 = INT64_MAX, r2 = INT64_MIN;
-    for (int i = 0; i < K; ++i)
-      if (ylo[i] <= Y[j + 1] && yhi[i] >= Y[j]) {
-        l2 = mn64(l2, X[i]);
-        r2 = mx64(r2, X[i + 1]);
-      }
-    r[R_LLO + j] = mx64(xlo[j], l2);
-    r[R_RHI + j] = mn64(xhi[j], r2);
-  }
-
   /* App. A "Computing Oriented Bounding Boxes": for each of 8 angles the    */
   /* box is the intersection of the strips u in [u0,u1], v in [v0,v1] with   */
   /* u = xC + yS, v = -xS + yC over the vertices; keep the minimum area      */
@@ -353,14 +332,21 @@ static int64_t scaled_len(int64_t q, int64_t k) { return ceil_div((i128)q * k, O
 /* interval (c, c+1), clipped to the chart's x-range) TopEdge is the floor of */
 /* the least y of the tighter proxy and BottomEdge the ceiling of the        */
 /* greatest y ("rounded" outward so separation stays strict).  The local-    */
-/* AABB proxy contributes the refined pieces whose open x-interval meets the */
-/* column; the OBB contributes the minimum (maximum) of its top (bottom)     */
+/* AABB proxy bounds the column by the x-slices whose open x-interval meets  */
+/* it, merged (Sec. 4.1.1, READING: per column, the tighter of the two) with */
+/* the bound of the y-slices whose x-range meets it: a chart point in the    */
+/* column lies in some y-slice j, so it is no higher than Y_j and no lower   */
+/* than Y_j+1 (a per-slice merge instead would change nothing: the slice     */
+/* holding an x-slice's topmost point always meets that x-slice).  The OBB   */
+/* contributes the minimum (maximum) of its top (bottom)                     */
 /* boundary over the column, reached at the box corner when the corner lies  */
 /* inside the column and at the nearer column end otherwise (each boundary   */
 /* is the max (min) of two lines).  The per-row left/right extents are the   */
 /* same construction with the axes swapped.                                  */
-int oracle_envelope(const int64_t *r, int32_t k, const int32_t *params, int32_t *wh,
-                    int32_t *top, int32_t *bot, int32_t *left, int32_t *right, int32_t cap) {
+/* cols = 0 skips the columns (TopEdge/BottomEdge): the tail's trial scales */
+/* need widths and per-row extents only.                                     */
+static int envelope_impl(const int64_t *r, int32_t k, const int32_t *params, int32_t *wh,
+                         int32_t *top, int32_t *bot, int32_t *left, int32_t *right, int32_t cap, int cols) {
   const int64_t F = OR_FIX;
   int64_t Wq = r[R_WQ], Hq = r[R_HQ];
   int64_t w = scaled_len(Wq, k), h = scaled_len(Hq, k);
@@ -377,16 +363,27 @@ int oracle_envelope(const int64_t *r, int32_t k, const int32_t *params, int32_t 
   i128 U0 = (i128)r[R_U0] * k, U1 = (i128)r[R_U1] * k;
   i128 V0 = (i128)r[R_V0] * k, V1 = (i128)r[R_V1] * k;
 
-  for (int64_t c = 0; c < w; ++c) {
+  for (int64_t c = 0; c < w && cols; ++c) {
     int64_t a = c * F, b = mn64((c + 1) * F, Wq * k);
     int64_t T = 0, B = h;
     if (use_l) {
-      int64_t tl = INT64_MAX, bl = INT64_MIN;
+      /* the x-slices meeting the column bound its top and bottom by their */
+      /* extremes; the y-slices bound them by their own extent: the chart's */
+      /* top in the column is no higher than the first y-slice whose        */
+      /* x-range meets the column, its bottom no lower than the last one.   */
+      /* Sec. 4.1.1's merge keeps the tighter of the two.                   */
+      int64_t tl = INT64_MAX, bl = INT64_MIN, t2 = INT64_MAX, b2 = INT64_MIN;
       for (int i = 0; i < K; ++i)
         if (r[R_X + i] * k < b && r[R_X + i + 1] * k > a) {
-          tl = mn64(tl, r[R_TLO + i]);
-          bl = mx64(bl, r[R_BHI + i]);
+          tl = mn64(tl, r[R_YLO + i]);
+          bl = mx64(bl, r[R_YHI + i]);
         }
+      for (int j = 0; j < K; ++j)
+        if (r[R_XLO + j] * k < b && r[R_XHI + j] * k > a) {
+          t2 = mn64(t2, r[R_Y + j]);
+          b2 = mx64(b2, r[R_Y + j + 1]);
+        }
+      if (t2 != INT64_MAX) { tl = mx64(tl, t2); bl = mn64(bl, b2); }
       T = mx64(T, floor_div((i128)tl * k, F));
       B = mn64(B, ceil_div((i128)bl * k, F));
     }
@@ -423,12 +420,20 @@ int oracle_envelope(const int64_t *r, int32_t k, const int32_t *params, int32_t 
     int64_t a = rr * F, b = mn64((rr + 1) * F, Hq * k);
     int64_t L = 0, R = w;
     if (use_l) {
-      int64_t ll = INT64_MAX, rl = INT64_MIN;
+      /* the same with the axes swapped: y-slices bound the row by their   */
+      /* extremes, x-slices whose y-range meets the row by their extent    */
+      int64_t ll = INT64_MAX, rl = INT64_MIN, l2 = INT64_MAX, r2 = INT64_MIN;
       for (int j = 0; j < K; ++j)
         if (r[R_Y + j] * k < b && r[R_Y + j + 1] * k > a) {
-          ll = mn64(ll, r[R_LLO + j]);
-          rl = mx64(rl, r[R_RHI + j]);
+          ll = mn64(ll, r[R_XLO + j]);
+          rl = mx64(rl, r[R_XHI + j]);
         }
+      for (int i = 0; i < K; ++i)
+        if (r[R_YLO + i] * k < b && r[R_YHI + i] * k > a) {
+          l2 = mn64(l2, r[R_X + i]);
+          r2 = mx64(r2, r[R_X + i + 1]);
+        }
+      if (l2 != INT64_MAX) { ll = mx64(ll, l2); rl = mn64(rl, r2); }
       L = mx64(L, floor_div((i128)ll * k, F));
       R = mn64(R, ceil_div((i128)rl * k, F));
     }
@@ -462,14 +467,19 @@ int oracle_envelope(const int64_t *r, int32_t k, const int32_t *params, int32_t 
   return 0;
 }
 
+int oracle_envelope(const int64_t *r, int32_t k, const int32_t *params, int32_t *wh,
+                    int32_t *top, int32_t *bot, int32_t *left, int32_t *right, int32_t cap) {
+  return envelope_impl(r, k, params, wh, top, bot, left, right, cap, 1);
+}
+
 /* Sec. 5 gutters (g texels around each chart, none at the atlas edges).     */
 /* READING: each envelope is dilated by g in the Chebyshev sense into padded */
 /* coordinates (width w+2g, height h+2g); padded footprints must be disjoint */
 /* inside the padded atlas (W+2g) x (H+2g).  A chart whose padded footprint  */
 /* starts at padded (X, Y) has its texels at atlas (X, Y) onward.            */
-int oracle_envelope_padded(const int64_t *r, int32_t k, const int32_t *params, int32_t *wh,
-                           int32_t *topP, int32_t *botP, int32_t *leftP, int32_t *rightP,
-                           int32_t cap) {
+static int envelope_padded_impl(const int64_t *r, int32_t k, const int32_t *params, int32_t *wh,
+                                int32_t *topP, int32_t *botP, int32_t *leftP, int32_t *rightP,
+                                int32_t cap, int cols) {
   int g = params[P_GUTTER];
   int64_t w = scaled_len(r[R_WQ], k), h = scaled_len(r[R_HQ], k);
   if (w > cap || h > cap) { wh[0] = (int32_t)w; wh[1] = (int32_t)h; return 1; }
@@ -478,12 +488,12 @@ int oracle_envelope_padded(const int64_t *r, int32_t k, const int32_t *params, i
   int32_t *l = (int32_t *)malloc(sizeof(int32_t) * (h + 1));
   int32_t *ri = (int32_t *)malloc(sizeof(int32_t) * (h + 1));
   int32_t whr[2];
-  oracle_envelope(r, k, params, whr, t, bo, l, ri, cap);
+  envelope_impl(r, k, params, whr, t, bo, l, ri, cap, cols);
   int64_t wp = w + 2 * g, hp = h + 2 * g;
   wh[0] = (int32_t)wp;
   wh[1] = (int32_t)hp;
   if (wp > cap || hp > cap) { free(t); free(bo); free(l); free(ri); return 1; }
-  for (int64_t i = 0; i < wp; ++i) {
+  for (int64_t i = 0; i < wp && cols; ++i) {
     int64_t mnv = INT64_MAX, mxv = INT64_MIN;
     for (int64_t c = i - 2 * g; c <= i; ++c)
       if (c >= 0 && c < w) { mnv = mn64(mnv, t[c]); mxv = mx64(mxv, bo[c]); }
@@ -499,6 +509,12 @@ int oracle_envelope_padded(const int64_t *r, int32_t k, const int32_t *params, i
   }
   free(t); free(bo); free(l); free(ri);
   return 0;
+}
+
+int oracle_envelope_padded(const int64_t *r, int32_t k, const int32_t *params, int32_t *wh,
+                           int32_t *topP, int32_t *botP, int32_t *leftP, int32_t *rightP,
+                           int32_t cap) {
+  return envelope_padded_impl(r, k, params, wh, topP, botP, leftP, rightP, cap, 1);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -646,93 +662,189 @@ static Knee find_knee(int s0, int s1, int ltr, const int64_t *X, const Env *env,
   return kd;
 }
 
-/* Sec. 4.4 "Performance Optimization": the remaining charts folded by a   */
-/* prefix sum, then pushed row by row.  The prefix runs over the offsets    */
-/* between consecutive charts (padded width minus the compacting distance   */
-/* to the next chart; with compaction off, the width), as a recurrence so   */
-/* the compacted fold keeps its rule that chart s+1 never starts left of    */
-/* chart s-1's right edge.  READING of the row break and the "intermediate */
-/* downscaling": a chart whose unwrapped prefix P lies in [rL, (r+1)L)      */
-/* starts tail row r at x = P - rL, with L = W' - wmax + 1 (wmax the widest */
-/* remaining padded chart), so every chart ends inside the padded atlas     */
-/* (x + w' <= L - 1 + wmax = W').  The rows are thus folded to a width      */
-/* shortened by the widest chart instead of overflowing and being scaled    */
-/* down afterwards: every chart keeps the candidate scale, so the scales of */
-/* all charts stay equal and the area-weighted selection of the final scale */
-/* reduces to the largest successful candidate.  READING of FastAtlas's      */
-/* fixed alternation: one left-to-right row, then two right-to-left rows,   */
-/* starting with the first tail row.  Each row is pushed onto the frontline */
-/* exactly like a committed row of Algorithm 5 (mirrored charts in a        */
-/* right-to-left row, Algorithm 2 when compacting).                          */
+/* Envelopes, distances and flags of sorted charts at scale k. */
 typedef struct {
-  int on;
-  int64_t L;        /* fold width of the tail rows                    */
-  int64_t P;        /* unwrapped prefix of the next row's first chart */
-  int64_t Pprev;    /* ... of the chart before it                      */
-  int64_t Wprev;    /* padded width of the chart before it             */
-  int have_prev;    /* a chart precedes the next row in the tail       */
-  int rows;         /* tail rows committed                             */
-} Tail;
+  int n;
+  Env *env;
+  int32_t *pool;
+  int64_t *hq;
+  int32_t *dnext;
+  uint8_t *cannotA, *cannotB;
+} ScaleData;
 
-/* One tail row from rowStart: fold, push, commit.  Returns the last chart */
-/* of the row; the frontline, placements and the tail state advance.      */
-static int tail_row(int n, int rowStart, int row, Tail *t, int hc, const Env *env,
-                    const int32_t *dnext, const uint8_t *cannotA, const uint8_t *cannotB,
-                    int64_t Wp, int64_t *front, int64_t *X, int64_t *y, int32_t *place) {
-  int64_t B = (t->P / t->L) * t->L; /* the row's start in the unwrapped prefix */
-  int64_t P = t->P, Pp = t->Pprev, Wpv = t->Wprev;
-  int have = t->have_prev;
-  int s = rowStart;
-  for (; s < n && P < B + t->L; ++s) {
-    X[s] = P - B;
-    int64_t nx = P + env[s].wp - (hc ? dnext[s] : 0);
-    if (hc && have && nx < Pp + Wpv) nx = Pp + Wpv;
-    Pp = P;
-    Wpv = env[s].wp;
-    have = 1;
-    P = nx;
+static int build_scale(int n, const int64_t *rec, const int32_t *perm, int32_t k,
+                       const int32_t *params, ScaleData *sd, int cols);
+static void free_scale(ScaleData *sd);
+
+/* x offsets of the charts of one row laid from its near end: Algorithm 4's */
+/* recurrence (x of the next chart = x + w' - d with compacting, x + w'     */
+/* without; with compacting never left of the right edge of the chart two  */
+/* places before, READING 11 of the sequential fold).  x[0..m-1] relative  */
+/* to the row's first chart; returns the row's extent max(x + w').          */
+static int64_t lay_row(int m, const Env *env, const int32_t *dnext, int hc, int64_t *x) {
+  int64_t ext = 0;
+  for (int t = 0; t < m; ++t) {
+    if (t == 0) x[t] = 0;
+    else {
+      x[t] = x[t - 1] + env[t - 1].wp - (hc ? dnext[t - 1] : 0);
+      if (hc && t >= 2 && x[t] < x[t - 2] + env[t - 2].wp) x[t] = x[t - 2] + env[t - 2].wp;
+    }
+    ext = mx64(ext, x[t] + env[t].wp);
   }
-  int e = s - 1;
-  t->P = P; t->Pprev = Pp; t->Wprev = Wpv; t->have_prev = have;
-  int dir = (t->rows % 3 == 0) ? 0 : 1;
-  for (int c = rowStart; c <= e; ++c)
-    if (dir == 1) X[c] = Wp - X[c] - env[c].wp;
-  for (int c = rowStart; c <= e; ++c) {
-    y[c] = 0;
-    for (int i = 0; i < env[c].wp; ++i) {
-      int ti = dir == 0 ? i : env[c].wp - 1 - i;
-      y[c] = mx64(y[c], front[X[c] + i] - env[c].top[ti]);
+  return ext;
+}
+
+/* Sec. 4.4 "Performance Optimization": once the rows no longer hold knees   */
+/* or tall charts, the remaining charts (sorted positions c0..n-1) are laid */
+/* out in one pass instead of row by row:                                    */
+/*  1. prefix-sum folding at the candidate scale S: the prefix of the        */
+/*     offsets between consecutive charts (padded width minus the compacting */
+/*     distance to the next chart; the padded width without compacting;     */
+/*     READING: the compacted fold keeps its rule that a chart never starts  */
+/*     left of the right edge of the chart two places before) puts chart s   */
+/*     at P_s, and the rows are cut modulo the padded atlas width: chart s   */
+/*     belongs to tail row floor(P_s / W'), so a row's last chart may        */
+/*     overflow the width;                                                   */
+/*  2. intermediate downscaling: READING (on the k/1024 grid, integer): the  */
+/*     tail charts take one scale k' <= S at which every tail row, re-laid   */
+/*     from its near end with the envelopes, widths and compacting distances */
+/*     at k', fits the padded width W'.  k' is found by a 16-way search:     */
+/*     with lo = 0 and hi = S + 1, each round tries the 15 scales            */
+/*     lo + floor(i (hi - lo) / 16), i = 1..15, sets lo to the largest that  */
+/*     fits (if any does) and hi to the smallest tried above the new lo, and */
+/*     three rounds end with hi = lo + 1; k' = lo, and the candidate fails   */
+/*     if lo = 0.  Where "every row fits" is monotone in the scale, this is  */
+/*     the largest k' <= S that fits;                                        */
+/*  3. the rows, drawn at k', go into the atlas in FastAtlas's fixed         */
+/*     alternation (READING: one left-to-right row, then two right-to-left   */
+/*     rows, starting with the first tail row) and are pushed up onto the    */
+/*     frontline like committed rows of Algorithm 5 (mirrored charts in a    */
+/*     right-to-left row, Algorithm 2 when compacting).                      */
+/* The tail charts' final scale is k', the others' S; the search then keeps */
+/* the candidate whose area-weighted mean final scale is largest.           */
+/* Returns 1 if every row fits below the padded height, else 0; the tail    */
+/* placements go to place (sorted positions), the rows it committed and its */
+/* scale to stats.                                                           */
+/* Whether every tail row, re-laid at scale k2, fits the padded width. */
+static int tail_rows_fit(int m, int nr, const int32_t *rstart, const int64_t *rec, const int32_t *perm,
+                         int32_t k2, const int32_t *params, int hc, int64_t Wp, int64_t *x) {
+  ScaleData sd;
+  int fits = !build_scale(m, rec, perm, k2, params, &sd, 0);
+  for (int r = 0; r < nr && fits; ++r) {
+    const int a = rstart[r], b = rstart[r + 1];
+    fits = lay_row(b - a, sd.env + a, sd.dnext + a, hc, x + a) <= Wp;
+  }
+  free_scale(&sd);
+  return fits;
+}
+
+static int tail_pack(int n, int c0, int row, const Env *env, const int32_t *dnext,
+                     const int64_t *rec, const int32_t *perm, int32_t S, const int32_t *params,
+                     int64_t Wp, int64_t Hp, int64_t *front, int32_t *place, int32_t *stats,
+                     int64_t *committed) {
+  const int hc = (params[P_FLAGS] & F_HC) != 0;
+  const int m = n - c0;
+  int64_t *P = (int64_t *)malloc(sizeof(int64_t) * m);
+  int32_t *rstart = (int32_t *)malloc(sizeof(int32_t) * (m + 1));
+  int64_t *x = (int64_t *)malloc(sizeof(int64_t) * m);
+  int64_t *y = (int64_t *)malloc(sizeof(int64_t) * m);
+
+  /* 1. prefix-sum folding at S, rows cut modulo W' */
+  for (int t = 0; t < m; ++t) {
+    const int s = c0 + t;
+    if (t == 0) P[t] = 0;
+    else {
+      P[t] = P[t - 1] + env[s - 1].wp - (hc ? dnext[s - 1] : 0);
+      if (hc && t >= 2 && P[t] < P[t - 2] + env[s - 2].wp) P[t] = P[t - 2] + env[s - 2].wp;
     }
   }
-  if (hc) correct_y_offsets(rowStart, e, cannotA, cannotB, y);
-  for (int c = rowStart; c <= e; ++c) {
-    for (int i = 0; i < env[c].wp; ++i) {
-      int ti = dir == 0 ? i : env[c].wp - 1 - i;
-      front[X[c] + i] = mx64(front[X[c] + i], y[c] + env[c].bot[ti]);
+  int nr = 0;
+  for (int t = 0; t < m; ++t)
+    if (t == 0 || P[t] / Wp != P[t - 1] / Wp) rstart[nr++] = t;
+  rstart[nr] = m;
+
+  /* 2. intermediate scale k': the 16-way search */
+  int32_t lo = 0, hi = S + 1;
+  for (int round = 0; round < 3; ++round) {
+    int32_t tried[15];
+    int32_t best = lo;
+    for (int i = 1; i <= 15; ++i) {
+      tried[i - 1] = lo + (int32_t)(((int64_t)i * (hi - lo)) / 16);
+      if (tried[i - 1] > lo && tried[i - 1] < hi &&
+          tail_rows_fit(m, nr, rstart, rec, perm + c0, tried[i - 1], params, hc, Wp, x))
+        best = tried[i - 1] > best ? tried[i - 1] : best;
     }
-    place[6 * c + 0] = (int32_t)X[c];
-    place[6 * c + 1] = (int32_t)y[c];
-    place[6 * c + 2] = dir;
-    place[6 * c + 3] = row;
-    place[6 * c + 4] = hc;
-    place[6 * c + 5] = 2; /* folded by the prefix sum */
+    int32_t nhi = hi;
+    for (int i = 0; i < 15; ++i)
+      if (tried[i] > best && tried[i] < nhi) nhi = tried[i];
+    lo = best;
+    hi = nhi;
   }
-  t->rows += 1;
-  return e;
+  const int32_t kt = lo;
+  stats[6] = kt;
+  stats[7] = c0;
+  int ok = kt > 0;
+  ScaleData sd;
+  if (kt) {
+    ok = !build_scale(m, rec, perm + c0, kt, params, &sd, 1);
+    for (int r = 0; r < nr && ok; ++r) lay_row(rstart[r + 1] - rstart[r], sd.env + rstart[r],
+                                               sd.dnext + rstart[r], hc, x + rstart[r]);
+  }
+
+  /* 3. the rows at k', FastAtlas's directions, pushed onto the frontline */
+  for (int r = 0; r < nr && ok; ++r) {
+    const int a = rstart[r], b = rstart[r + 1];
+    const int dir = (r % 3 == 0) ? 0 : 1;
+    const Env *e = sd.env;
+    for (int t = a; t < b; ++t) {
+      const int64_t X = dir ? Wp - x[t] - e[t].wp : x[t];
+      y[t] = 0;
+      for (int i = 0; i < e[t].wp; ++i) {
+        const int ti = dir == 0 ? i : e[t].wp - 1 - i;
+        y[t] = mx64(y[t], front[X + i] - e[t].top[ti]);
+      }
+      x[t] = X;
+    }
+    if (hc) correct_y_offsets(a, b - 1, sd.cannotA, sd.cannotB, y);
+    for (int t = a; t < b; ++t) {
+      for (int i = 0; i < e[t].wp; ++i) {
+        const int ti = dir == 0 ? i : e[t].wp - 1 - i;
+        front[x[t] + i] = mx64(front[x[t] + i], y[t] + e[t].bot[ti]);
+      }
+      int32_t *pl = place + 7 * (c0 + t);
+      pl[0] = (int32_t)x[t];
+      pl[1] = (int32_t)y[t];
+      pl[2] = dir;
+      pl[3] = row + r;
+      pl[4] = hc;
+      pl[5] = 2; /* folded by the prefix sum */
+      pl[6] = kt;
+    }
+    *committed = 0;
+    for (int64_t xx = 0; xx < Wp; ++xx) *committed = mx64(*committed, front[xx]);
+    ok = *committed <= Hp;
+    stats[0] = row + r + 1;
+    stats[4] = c0 + b;
+    stats[5] = r + 1;
+  }
+  if (kt) free_scale(&sd);
+  free(P); free(rstart); free(x); free(y);
+  return ok;
 }
 
 enum { CFG_FULL = 0, CFG_KNEE = 1 };
 
-/* Placements in sorted order, 6 int32 per chart: x, y, mirror (right-to-left   */
+/* Placements in sorted order, 7 int32 per chart: x, y, mirror (right-to-left   */
 /* row), row index, compacting on in that row, fold (0 atlas width, 1 knee,       */
-/* 2 prefix-sum tail).                                                            */
+/* 2 prefix-sum tail), the chart's scale (S, or the tail's k').                   */
 /* stats[0] = rows committed, [1] = knee-folded rows, [2] = knees found,          */
 /* [3] = final committed score (max frontline), [4] = charts placed,              */
-/* [5] = tail rows (Sec. 4.4).                                                    */
+/* [5] = tail rows, [6] = the tail's scale k' (0: no tail, or none fitted),       */
+/* [7] = first tail chart (n: no tail) (Sec. 4.4).                                */
 static int pack_scale_env(int n, const Env *env, const int64_t *hq, const int32_t *dnext,
                           const uint8_t *cannotA, const uint8_t *cannotB,
-                          int32_t W, int32_t H, const int32_t *params,
-                          int32_t *place, int32_t *stats) {
+                          int32_t W, int32_t H, const int64_t *rec, const int32_t *perm,
+                          int32_t S, const int32_t *params, int32_t *place, int32_t *stats) {
   int g = params[P_GUTTER];
   int flags = params[P_FLAGS];
   int64_t Wp = (int64_t)W + 2 * g, Hp = (int64_t)H + 2 * g;
@@ -745,11 +857,12 @@ static int pack_scale_env(int n, const Env *env, const int64_t *hq, const int32_
   }
   for (int f = 0; f < 2; ++f)
     for (int h = 0; h < 2; ++h) pos[f][h] = (int64_t *)malloc(sizeof(int64_t) * n);
-  memset(stats, 0, sizeof(int32_t) * 6);
+  memset(stats, 0, sizeof(int32_t) * 8);
+  stats[7] = n;
   /* Sec. 4.4: the hybrid applies to atlases of more than hybrid_min charts */
   /* (the paper: t_opt = 1 % above 10,000 charts, none below).             */
   const int hybrid = params[P_TOPT] > 0 && n > params[P_HYBRID_MIN];
-  Tail tail = {0, 1, 0, 0, 0, 0, 0};
+  int tail_ok = -1; /* -1: no tail */
 
   int rowStart = 0, overflow = 0, row = 0;
   int prev_ltr = 0; /* READING: direction ties alternate, the first row left-to-right */
@@ -759,26 +872,14 @@ static int pack_scale_env(int n, const Env *env, const int64_t *hq, const int32_
     /* Sec. 4.4: switch to prefix-sum folding once no knee is live and the  */
     /* row's tallest chart (its first) is below t_opt of the atlas height   */
     /* (READING: its scaled height, without gutters; t_opt in permille).    */
-    if (hybrid && !tail.on && !kd.valid &&
+    if (hybrid && !kd.valid &&
         1000 * ((int64_t)env[rowStart].hp - 2 * g) < (int64_t)params[P_TOPT] * H) {
-      int64_t wmax = 0;
-      for (int s = rowStart; s < n; ++s) wmax = mx64(wmax, env[s].wp);
-      if (wmax > Wp) { overflow = 1; break; } /* a chart wider than the atlas */
-      tail.on = 1;
-      tail.L = Wp - wmax + 1;
-    }
-    if (tail.on) {
-      int hc = (flags & F_HC) != 0;
-      int e = tail_row(n, rowStart, row, &tail, hc, env, dnext, cannotA, cannotB, Wp, front, X[0], y[0], place);
-      committed = 0;
-      for (int64_t xx = 0; xx < Wp; ++xx) committed = mx64(committed, front[xx]);
-      overflow = committed > Hp;
-      prev_ltr = place[6 * e + 2] == 0;
-      stats[4] = e + 1;
-      stats[5] = tail.rows;
-      rowStart = e + 1;
-      ++row;
-      continue;
+      stats[0] = row;
+      tail_ok = tail_pack(n, rowStart, row, env, dnext, rec, perm, S, params, Wp, Hp, front, place, stats,
+                          &committed);
+      row = stats[0];
+      rowStart = stats[4];
+      break;
     }
     if (kd.valid) update_knee(&kd, front);
     int nfold = kd.valid ? 2 : 1;
@@ -865,12 +966,13 @@ static int pack_scale_env(int n, const Env *env, const int64_t *hq, const int32_
     /* commit the best configuration */
     memcpy(front, local[best], sizeof(int64_t) * Wp);
     for (int s = rowStart; s <= e; ++s) {
-      place[6 * s + 0] = (int32_t)X[best][s];
-      place[6 * s + 1] = (int32_t)y[best][s];
-      place[6 * s + 2] = bdir;
-      place[6 * s + 3] = row;
-      place[6 * s + 4] = bh;
-      place[6 * s + 5] = bf;
+      place[7 * s + 0] = (int32_t)X[best][s];
+      place[7 * s + 1] = (int32_t)y[best][s];
+      place[7 * s + 2] = bdir;
+      place[7 * s + 3] = row;
+      place[7 * s + 4] = bh;
+      place[7 * s + 5] = bf;
+      place[7 * s + 6] = S;
     }
     if (bf == CFG_FULL) {
       kd = (flags & F_BALANCE) ? find_knee(rowStart, e, bdir == 0, X[best], env, hq, H, (int32_t)Wp, params)
@@ -888,6 +990,7 @@ static int pack_scale_env(int n, const Env *env, const int64_t *hq, const int32_
   }
   stats[0] = row;
   stats[3] = (int32_t)committed;
+  if (tail_ok == 0) overflow = 1;
   free(front);
   for (int j = 0; j < 8; ++j) { free(local[j]); free(X[j]); free(y[j]); }
   for (int f = 0; f < 2; ++f)
@@ -895,18 +998,10 @@ static int pack_scale_env(int n, const Env *env, const int64_t *hq, const int32_
   return !overflow && rowStart >= n;
 }
 
-/* Envelopes, distances and flags of all sorted charts at scale k. */
-typedef struct {
-  int n;
-  Env *env;
-  int32_t *pool;
-  int64_t *hq;
-  int32_t *dnext;
-  uint8_t *cannotA, *cannotB;
-} ScaleData;
-
+/* Envelopes, distances and flags of the sorted charts perm[0..n-1] at */
+/* scale k.                                                              */
 static int build_scale(int n, const int64_t *rec, const int32_t *perm, int32_t k,
-                       const int32_t *params, ScaleData *sd) {
+                       const int32_t *params, ScaleData *sd, int cols) {
   int g = params[P_GUTTER];
   sd->n = n;
   sd->env = (Env *)calloc(n, sizeof(Env));
@@ -928,7 +1023,7 @@ static int build_scale(int n, const int64_t *rec, const int32_t *perm, int32_t k
     e->top = p; e->bot = p + wp; e->left = p + 2 * wp; e->right = p + 2 * wp + hp;
     p += 2 * wp + 2 * hp;
     int32_t wh[2];
-    if (oracle_envelope_padded(r, k, params, wh, e->top, e->bot, e->left, e->right, 1 << 30)) return 1;
+    if (envelope_padded_impl(r, k, params, wh, e->top, e->bot, e->left, e->right, 1 << 30, cols)) return 1;
     e->wp = wh[0];
     e->hp = wh[1];
     sd->hq[s] = r[R_HQ];
@@ -953,7 +1048,7 @@ int oracle_scale_pairs(int32_t n, const int64_t *rec, const int32_t *perm, int32
                        const int32_t *params, int32_t *d, uint8_t *cannotA, uint8_t *cannotB,
                        int32_t *wp, int32_t *hp) {
   ScaleData sd;
-  if (build_scale(n, rec, perm, k, params, &sd)) { free_scale(&sd); return 1; }
+  if (build_scale(n, rec, perm, k, params, &sd, 1)) { free_scale(&sd); return 1; }
   for (int s = 0; s < n; ++s) {
     d[s] = sd.dnext[s]; cannotA[s] = sd.cannotA[s]; cannotB[s] = sd.cannotB[s];
     wp[s] = sd.env[s].wp; hp[s] = sd.env[s].hp;
@@ -965,8 +1060,9 @@ int oracle_scale_pairs(int32_t n, const int64_t *rec, const int32_t *perm, int32
 int oracle_pack_scale(int32_t n, const int64_t *rec, const int32_t *perm, int32_t W, int32_t H,
                       int32_t k, const int32_t *params, int32_t *place, int32_t *stats) {
   ScaleData sd;
-  if (build_scale(n, rec, perm, k, params, &sd)) { free_scale(&sd); return -1; }
-  int ok = pack_scale_env(n, sd.env, sd.hq, sd.dnext, sd.cannotA, sd.cannotB, W, H, params, place, stats);
+  if (build_scale(n, rec, perm, k, params, &sd, 1)) { free_scale(&sd); return -1; }
+  int ok = pack_scale_env(n, sd.env, sd.hq, sd.dnext, sd.cannotA, sd.cannotB, W, H, rec, perm, k, params,
+                          place, stats);
   free_scale(&sd);
   return ok;
 }
@@ -977,13 +1073,34 @@ void oracle_correct_y(int32_t s0, int32_t s1, const uint8_t *cannotA, const uint
   correct_y_offsets(s0, s1, cannotA, cannotB, y);
 }
 
+/* Twice the area of a chart's vertex loop (shoelace), in Q.8^2 units, as */
+/* a magnitude: the weight of the chart in the area-weighted mean scale.   */
+static int64_t loop_area2(int nv, const int32_t *v) {
+  int64_t a2 = 0;
+  for (int i = 0; i < nv; ++i) {
+    int j = (i + 1) % nv;
+    a2 += (int64_t)v[2 * i] * v[2 * j + 1] - (int64_t)v[2 * j] * v[2 * i + 1];
+  }
+  return a2 < 0 ? -a2 : a2;
+}
+
 /* ------------------------------------------------------------------------ */
-/* Sec. 3.1 / Sec. 5 scale search: candidates k = 16j, j = 1..64; the      */
-/* largest k whose packing succeeds.  all_scales=1 evaluates every          */
-/* candidate (success_per_k[j-1]); otherwise the search runs from the top   */
-/* and stops at the first success (same result).                            */
-/* place_out (input order, 10 int32 per chart): x, y, rot90, flip_x, flip_y, */
-/* mirror, row, sorted position, compacting on, knee-folded.                 */
+/* Sec. 3.1 / Sec. 5 scale search over the candidates S = 16j, j = 1..64,   */
+/* with Sec. 4.4's choice: the successful candidate whose mean final scale, */
+/* weighted by chart area, is largest -- i.e. the largest                   */
+/* sum_c area_c * scale_c (scale_c = S, or k' for the prefix-sum tail's     */
+/* charts), compared exactly; READING: ties keep the larger S.  Without a   */
+/* tail every chart has scale S and this is the largest successful S.  The */
+/* candidates are tried from the top; once one has succeeded, a smaller S   */
+/* can only win if S * sum_c area_c exceeds the best sum (no chart's scale  */
+/* exceeds its candidate), so the search stops at the first S where it     */
+/* does not (all_scales = 1 evaluates every candidate instead, with the     */
+/* same result; success_per_k[j-1] records each).                           */
+/* place_out (input order, 11 int32 per chart): x, y, rot90, flip_x,         */
+/* flip_y, mirror, row, sorted position, compacting on, fold (0 atlas       */
+/* width, 1 knee, 2 prefix-sum tail), the chart's scale k.                  */
+/* stats_out: the chosen candidate's stats (8, see pack_scale_env), then    */
+/* its area-weighted scale sum as two int64 halves (low, high).             */
 /* Returns 0 ok, 1 invalid input, 2 no fit.                                  */
 /* ------------------------------------------------------------------------ */
 int oracle_pack(int32_t n, const uint32_t *offsets, const int32_t *verts, int32_t W, int32_t H,
@@ -994,41 +1111,59 @@ int oracle_pack(int32_t n, const uint32_t *offsets, const int32_t *verts, int32_
   if (oracle_prep(n, offsets, verts, params, rec)) { free(rec); return 1; }
   int32_t *perm = (int32_t *)malloc(sizeof(int32_t) * n);
   oracle_sort(n, rec, perm);
-  int32_t *place = (int32_t *)malloc(sizeof(int32_t) * 6 * n);
-  int32_t *best_place = (int32_t *)malloc(sizeof(int32_t) * 6 * n);
-  int32_t stats[6], best_stats[6] = {0, 0, 0, 0, 0, 0};
+  int64_t *area = (int64_t *)malloc(sizeof(int64_t) * n); /* sorted order */
+  i128 area_total = 0;
+  for (int s = 0; s < n; ++s) {
+    int c = perm[s];
+    area[s] = loop_area2((int)(offsets[c + 1] - offsets[c]), verts + 2 * offsets[c]);
+    area_total += area[s];
+  }
+  int32_t *place = (int32_t *)malloc(sizeof(int32_t) * 7 * n);
+  int32_t *best_place = (int32_t *)malloc(sizeof(int32_t) * 7 * n);
+  int32_t stats[8], best_stats[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   int best_k = 0;
+  i128 best_score = 0;
   for (int j = 64; j >= 1; --j) {
     int32_t k = 16 * j;
-    if (!all_scales && best_k) break;
+    if (!all_scales && best_k && (i128)k * area_total <= best_score) break;
     int ok = oracle_pack_scale(n, rec, perm, W, H, k, params, place, stats);
     if (success_per_k) success_per_k[j - 1] = ok == 1;
-    if (ok == 1 && !best_k) {
+    if (ok != 1) continue;
+    i128 score = 0;
+    for (int s = 0; s < n; ++s) score += (i128)area[s] * place[7 * s + 6];
+    if (!best_k || score > best_score) {
       best_k = k;
-      memcpy(best_place, place, sizeof(int32_t) * 6 * n);
+      best_score = score;
+      memcpy(best_place, place, sizeof(int32_t) * 7 * n);
       memcpy(best_stats, stats, sizeof(best_stats));
     }
   }
   *out_k = best_k;
-  if (stats_out) memcpy(stats_out, best_stats, sizeof(best_stats));
+  if (stats_out) {
+    memcpy(stats_out, best_stats, sizeof(best_stats));
+    int64_t lo = (int64_t)(uint64_t)best_score, hi = (int64_t)(best_score >> 64);
+    memcpy(stats_out + 8, &lo, 8);
+    memcpy(stats_out + 10, &hi, 8);
+  }
   if (best_k) {
     for (int s = 0; s < n; ++s) {
       int c = perm[s];
       const int64_t *r = rec + (int64_t)c * OR_REC;
-      int32_t *o = place_out + 10 * c;
-      o[0] = best_place[6 * s + 0];
-      o[1] = best_place[6 * s + 1];
+      int32_t *o = place_out + 11 * c;
+      o[0] = best_place[7 * s + 0];
+      o[1] = best_place[7 * s + 1];
       o[2] = (int32_t)r[R_ROT];
       o[3] = (int32_t)r[R_FLIPX];
       o[4] = (int32_t)r[R_FLIPY];
-      o[5] = best_place[6 * s + 2];
-      o[6] = best_place[6 * s + 3];
+      o[5] = best_place[7 * s + 2];
+      o[6] = best_place[7 * s + 3];
       o[7] = s;
-      o[8] = best_place[6 * s + 4];
-      o[9] = best_place[6 * s + 5];
+      o[8] = best_place[7 * s + 4];
+      o[9] = best_place[7 * s + 5];
+      o[10] = best_place[7 * s + 6];
     }
   }
-  free(rec); free(perm); free(place); free(best_place);
+  free(rec); free(perm); free(area); free(place); free(best_place);
   return best_k ? 0 : 2;
 }
 

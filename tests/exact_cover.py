@@ -103,23 +103,26 @@ def dilate(mask: np.ndarray, g: int) -> np.ndarray:
     return out
 
 
-def check_packing(cs, k: int, place: np.ndarray, gutter: int = 1, envelope_fn=None):
+def check_packing(cs, k, place: np.ndarray, gutter: int = 1, envelope_fn=None):
     """Validate a full packing.  `place` is int32[n, >=6] in input order
-    (x, y, rot90, flip_x, flip_y, mirror).  Returns a dict of violation
+    (x, y, rot90, flip_x, flip_y, mirror); `k` is the scale of every chart,
+    or an array of each chart's scale (the prefix-sum tail of Sec. 4.4 draws
+    its charts at a scale of their own).  Returns a dict of violation
     counts: out-of-atlas texels, texels where dilated covers overlap, texels
-    where plain covers overlap, and (if envelope_fn is given) cover texels
-    outside the chart's own envelope."""
+    where plain covers overlap, and (if envelope_fn(chart, k) is given) cover
+    texels outside the chart's own envelope."""
     W, H = cs.atlas_w, cs.atlas_h
+    ks = np.broadcast_to(np.asarray(k, np.int64), (cs.n,))
     count = np.zeros((H + 2 * gutter, W + 2 * gutter), np.int16)
     plain = np.zeros((H, W), np.int16)
     out_of_atlas = 0
     outside_env = 0
     for i in range(cs.n):
         x, y, rot, fx, fy, mir = (int(v) for v in place[i, :6])
-        poly, w, h = placed_polygon(cs.polygon(i), k, rot, fx, fy, mir)
+        poly, w, h = placed_polygon(cs.polygon(i), int(ks[i]), rot, fx, fy, mir)
         cv = cover(poly, w, h)
         if envelope_fn is not None:
-            env = envelope_fn(i)
+            env = envelope_fn(i, int(ks[i]))
             top, bot = env.top, env.bot
             if mir:
                 top, bot = top[::-1], bot[::-1]

@@ -20,42 +20,74 @@ def _ceil_div(a, b):
     return -(-a // b)
 
 
-def skyline_tail(sizes, W, H, k, g=1):
-    """Independent brute force for boxes folded entirely by the tail: sorted
-    by height, padded sizes at scale k, prefix offsets = padded widths,
-    rows broken at multiples of L = W' - wmax + 1, FastAtlas directions, each
-    box dropped onto the skyline.  Returns (success, {sorted pos: (X, y,
-    mirror, tail row)})."""
+def _rows_modulo(P, Wp):
+    """Tail rows of the prefix fold: maximal runs of charts with the same
+    floor(P / W')."""
+    rows = []
+    for s, p in enumerate(P):
+        if not rows or p // Wp != P[rows[-1][-1]] // Wp:
+            rows.append([])
+        rows[-1].append(s)
+    return rows
+
+
+def skyline_tail(sizes, W, H, S, g=1):
+    """Independent brute force for boxes folded entirely by the tail
+    (Sec. 4.4): sorted by height, padded widths at the candidate S, the
+    prefix of the widths (boxes have compacting distance 0) cut into rows
+    modulo W'; the intermediate scale is the largest k' <= S at which every
+    row's widths sum to at most W' (for boxes the widths, hence the fit,
+    are monotone in the scale, where the oracle's 16-way search finds the
+    largest fit); rows in FastAtlas's
+    directions (left, right, right, ...) from their near end, each box
+    dropped onto the skyline.  Returns (success, k', {sorted pos: (X, y,
+    mirror, tail row)}).  Boxes wider than tall are turned upright first
+    (Sec. 3.1)."""
+    sizes = [(min(w, h), max(w, h)) for w, h in sizes]
     order = sorted(range(len(sizes)), key=lambda i: -sizes[i][1])  # stable
     Wp, Hp = W + 2 * g, H + 2 * g
-    wp = [_ceil_div(sizes[i][0] * k, 1024) + 2 * g for i in order]
-    hp = [_ceil_div(sizes[i][1] * k, 1024) + 2 * g for i in order]
-    if max(wp) > Wp:
-        return False, {}
-    L = Wp - max(wp) + 1
-    P = np.concatenate([[0], np.cumsum(wp)[:-1]])
-    groups = {}
-    for s, p in enumerate(P):
-        groups.setdefault(int(p) // L, []).append(s)
+
+    def wp(k):
+        return [_ceil_div(sizes[i][0] * k, 1024) + 2 * g for i in order]
+
+    def hp(k):
+        return [_ceil_div(sizes[i][1] * k, 1024) + 2 * g for i in order]
+
+    w = wp(S)
+    P = np.concatenate([[0], np.cumsum(w)[:-1]]).astype(int)
+    rows = _rows_modulo(P, Wp)
+    kt = 0
+    for k2 in range(S, 0, -1):
+        if all(sum(wp(k2)[s] for s in row) <= Wp for row in rows):
+            kt = k2
+            break
+    if not kt:
+        return False, 0, {}
+    w2, h2 = wp(kt), hp(kt)
     front = np.zeros(Wp, np.int64)
     out = {}
-    for t, r in enumerate(sorted(groups)):
+    for t, row in enumerate(rows):
         mirror = t % 3 != 0
-        ys = {}
-        for s in groups[r]:
-            x = int(P[s]) - r * L
-            X = Wp - x - wp[s] if mirror else x
-            ys[s] = (X, int(front[X:X + wp[s]].max()))
-        for s, (X, y) in ys.items():
-            front[X:X + wp[s]] = np.maximum(front[X:X + wp[s]], y + hp[s])
+        x, drops = 0, []
+        for s in row:
+            X = Wp - x - w2[s] if mirror else x
+            drops.append((s, X, int(front[X:X + w2[s]].max())))
+            x += w2[s]
+        for s, X, y in drops:
+            front[X:X + w2[s]] = np.maximum(front[X:X + w2[s]], y + h2[s])
             out[s] = (X, y, int(mirror), t)
         if front.max() > Hp:
-            return False, out
-    return True, out
+            return False, kt, out
+    return True, kt, out
+
+
+def _area2(sizes):
+    return [2 * (w * 256) * (h * 256) for w, h in sizes]
 
 
 BOXES = [[(3, 5), (2, 2), (4, 6), (1, 3), (5, 5), (2, 4), (3, 3), (1, 1), (2, 6), (4, 4)] * 3,
-         [(1, 2), (2, 3), (3, 3), (1, 1)] * 9 + [(6, 7), (5, 8)]]
+         [(1, 2), (2, 3), (3, 3), (1, 1)] * 9 + [(6, 7), (5, 8)],
+         [(9, 11), (7, 9), (8, 8), (6, 10), (5, 7), (9, 6), (4, 9), (8, 5)] * 4]
 
 
 @pytest.mark.parametrize("case", range(len(BOXES)))
@@ -63,32 +95,79 @@ BOXES = [[(3, 5), (2, 2), (4, 6), (1, 3), (5, 5), (2, 4), (3, 3), (1, 1), (2, 6)
 @pytest.mark.parametrize("g", [1, 0, 2])
 def test_boxes_match_skyline_brute_force(case, k, g):
     sizes = BOXES[case]
-    W, H = 17, 40
+    W, H = 17 if case < 2 else 41, 40
     cs = synth.rectangles(sizes, W, H)
     params = oracle.default_params(topt=1000, hybrid_min=0, gutter=g)  # every row is a tail row
     rec = oracle.prep(cs, params)
     perm = oracle.sort(rec)
     ok, place, stats = oracle.pack_scale(rec, perm, W, H, k, params)
-    bok, exp = skyline_tail(sizes, W, H, k, g)
+    bok, kt, exp = skyline_tail(sizes, W, H, k, g)
     assert ok == bok
+    assert stats[6] == kt and stats[7] == 0
     placed = int(stats[4])
     assert stats[5] == stats[0]  # all rows are tail rows
+    assert placed == len(exp)
     for s in range(placed):
         X, y, mirror, t = exp[s]
         assert tuple(place[s, :4]) == (X, y, mirror, t), s
-        assert place[s, 5] == 2 and place[s, 4] == 1
+        assert place[s, 5] == 2 and place[s, 4] == 1 and place[s, 6] == kt
 
 
-def test_boxes_search_matches_brute_force():
-    sizes = BOXES[0]
-    W, H = 17, 40
+def test_three_rows_downscaled_by_hand():
+    """Nine boxes 100 texels wide and 130 down to 122 tall, in a 300 x 400
+    atlas with 1-px gutters (W' = 302): at S = 1024 their padded widths are
+    102, the prefix 0, 102, ..., 816 puts three boxes in each of rows 0, 1,
+    2 (floor(P / 302)), and each row overflows (306 > 302).  At k the padded
+    width is ceil(100 k / 1024) + 2, so three fit iff ceil(100 k / 1024) <=
+    98, i.e. k <= 1003: k' = 1003 (padded widths 100, padded heights
+    ceil(h 1003 / 1024) + 2 = 130, 129, ..., 122).  Row 0 runs left to
+    right at x = 0, 100, 200; rows 1 and 2 run right to left at x = 202,
+    102, 2 and drop onto the skyline: row 1 lands at 128, 129, 130 and
+    levels it at 255, row 2 lands at 255 and tops out at 379.  S = 1008
+    gives the same k' and so the same weighted scale; the tie keeps the
+    larger candidate, and 992 (whose rows need k' = 747) cannot beat 1003."""
+    sizes = [(100, h) for h in range(130, 121, -1)]
+    cs = synth.rectangles(sizes, 300, 400)
+    params = oracle.default_params(topt=1000, hybrid_min=0)
+    rec = oracle.prep(cs, params)
+    perm = oracle.sort(rec)
+    assert list(perm) == list(range(9)) and not rec[:, R["ROT"]].any()
+    ok, place, stats = oracle.pack_scale(rec, perm, 300, 400, 1024, params)
+    assert ok and stats[6] == 1003 and stats[5] == 3 and stats[3] == 379
+    assert list(place[:, 3]) == [0, 0, 0, 1, 1, 1, 2, 2, 2]
+    assert list(place[:, 2]) == [0, 0, 0, 1, 1, 1, 1, 1, 1]
+    assert list(place[:, 0]) == [0, 100, 200, 202, 102, 2, 202, 102, 2]
+    assert list(place[:, 1]) == [0, 0, 0, 128, 129, 130, 255, 255, 255]
+    assert list(place[:, 6]) == [1003] * 9
+    ok2, _, st2 = oracle.pack_scale(rec, perm, 300, 400, 1008, params)
+    assert ok2 and st2[6] == 1003
+    # at 992 the padded widths are 99: the prefix puts four boxes in row 0,
+    # which fit only at ceil(100 k / 1024) <= 73, i.e. k' = 747
+    ok3, _, st3 = oracle.pack_scale(rec, perm, 300, 400, 992, params)
+    assert ok3 and st3[6] == 747
+    r = oracle.pack(cs, params)
+    assert r.status == 0 and r.k == 1024 and list(r.place[:, 10]) == [1003] * 9
+    assert r.score == 1003 * sum(_area2(sizes))
+
+
+@pytest.mark.parametrize("case", range(len(BOXES)))
+def test_boxes_search_matches_brute_force(case):
+    """The search keeps the successful candidate with the largest
+    area-weighted scale, ties to the larger candidate (Sec. 4.4)."""
+    sizes = BOXES[case]
+    W, H = 17 if case < 2 else 41, 40
     cs = synth.rectangles(sizes, W, H)
     params = oracle.default_params(topt=1000, hybrid_min=0)
     r = oracle.pack(cs, params, all_scales=True)
-    for j in range(1, 65):
-        assert bool(r.success[j - 1]) == skyline_tail(sizes, W, H, 16 * j)[0], j
-    best = max(16 * j for j in range(1, 65) if skyline_tail(sizes, W, H, 16 * j)[0])
-    assert r.k == best
+    area = sum(_area2(sizes))
+    best, best_score = 0, -1
+    for j in range(64, 0, -1):
+        ok, kt, _ = skyline_tail(sizes, W, H, 16 * j)
+        assert bool(r.success[j - 1]) == ok, j
+        if ok and kt * area > best_score:
+            best, best_score = 16 * j, kt * area
+    assert r.k == best and r.score == best_score
+    assert r.status == 0 and np.all(r.place[:, 10] == best_score // area)
 
 
 def _tall_then_small():
@@ -120,34 +199,78 @@ def test_switch_point():
         assert tail_rows == [r >= first_tail for r in range(len(firsts))]
         assert stats[5] == len(firsts) - first_tail
         assert stats[5] > 0 and first_tail > 0
+        assert stats[7] == firsts[first_tail]
+        # the head keeps the candidate scale, the tail its own
+        assert np.all(place[:firsts[first_tail], 6] == k)
+        assert np.all(place[firsts[first_tail]:placed, 6] == stats[6]) and 0 < stats[6] <= k
         # FastAtlas's alternation: one left-to-right row, then two right-to-left
         mirrors = [int(place[s, 2]) for s in firsts[first_tail:]]
         assert mirrors == [int(t % 3 != 0) for t in range(len(mirrors))]
 
 
-def test_compacted_prefix_is_tight():
+def test_compacted_rows_are_tight_at_the_tail_scale():
     """In a left-to-right tail row each chart sits at the compacting distance
-    from its predecessor, unless the clamp (chart s+1 never left of chart
-    s-1's right edge) binds, in which case it touches that right edge."""
+    (at the tail's scale k') from its predecessor, unless the clamp (chart
+    s+1 never left of chart s-1's right edge) binds, in which case it
+    touches that right edge; each row starts at the atlas's left edge."""
     cs = synth.stars(17, 400, 512)
     params = oracle.default_params(topt=200, hybrid_min=0)
     rec = oracle.prep(cs, params)
     perm = oracle.sort(rec)
     k = 448
     ok, place, stats = oracle.pack_scale(rec, perm, cs.atlas_w, cs.atlas_h, k, params)
-    d, _, _, wp, _ = oracle.scale_pairs(rec, perm, k, params)
+    kt = int(stats[6])
+    assert 0 < kt <= k
+    d, _, _, wp, _ = oracle.scale_pairs(rec, perm, kt, params)
     placed = int(stats[4])
-    checked = 0
-    for s in range(1, placed - 1):
-        same = place[s, 3] == place[s + 1, 3] and place[s, 5] == 2
-        if not same or place[s, 2] != 0:
+    checked = starts = 0
+    for s in range(int(stats[7]), placed):
+        if place[s, 2] != 0:
+            continue
+        if s == stats[7] or place[s - 1, 3] != place[s, 3]:
+            assert place[s, 0] == 0
+            starts += 1
+        if s + 1 >= placed or place[s, 3] != place[s + 1, 3]:
             continue
         gap_ok = place[s + 1, 0] - place[s, 0] == wp[s] - d[s]
         clamp = place[s - 1, 3] == place[s, 3] and place[s + 1, 0] == place[s - 1, 0] + wp[s - 1]
         assert gap_ok or clamp, s
         assert place[s + 1, 0] - place[s, 0] >= wp[s] - d[s]
         checked += 1
-    assert checked > 50
+    assert checked > 50 and starts > 2
+
+
+def test_rows_follow_the_prefix_modulo_the_width():
+    """The tail's rows are the prefix fold at the candidate scale cut modulo
+    W' (each row's last chart may overflow it), recomputed here from the
+    oracle's own widths and distances at S; every row fits W' at k'."""
+    cs = synth.stars(19, 600, 512)
+    params = oracle.default_params(topt=200, hybrid_min=0)
+    rec = oracle.prep(cs, params)
+    perm = oracle.sort(rec)
+    S = 480
+    ok, place, stats = oracle.pack_scale(rec, perm, cs.atlas_w, cs.atlas_h, S, params)
+    c0, placed = int(stats[7]), int(stats[4])
+    d, _, _, wp, _ = oracle.scale_pairs(rec, perm, S, params)
+    P = [0]
+    for s in range(c0, cs.n - 1):
+        nx = P[-1] + wp[s] - d[s]
+        if len(P) >= 2:
+            nx = max(nx, P[-2] + wp[s - 1])
+        P.append(nx)
+    Wp = cs.atlas_w + 2
+    rows = _rows_modulo(P, Wp)
+    overflowing = sum(P[row[-1]] + wp[c0 + row[-1]] > (P[row[0]] // Wp + 1) * Wp for row in rows)
+    assert overflowing > 0
+    got = place[c0:placed, 3] - place[c0, 3]
+    want = np.concatenate([[t] * len(row) for t, row in enumerate(rows)])[:placed - c0]
+    assert np.array_equal(got, want)
+    _, _, _, wpt, _ = oracle.scale_pairs(rec, perm, int(stats[6]), params)
+    for row in rows[:int(stats[5])]:
+        xs = [c0 + t for t in row]
+        lo = min(place[s, 0] for s in xs)
+        hi = max(place[s, 0] + wpt[s] for s in xs)
+        assert lo >= 0 and hi <= Wp
 
 
 @pytest.mark.parametrize("make", [lambda: synth.stars(23, 600, 512), lambda: synth.knees(3, 500, 1024),
@@ -162,10 +285,17 @@ def test_invariants_with_the_tail(make, flags):
     assert r.status == 0
     assert r.stats[5] > 0
     rec = oracle.prep(cs, params)
-    res = check_packing(cs, r.k, r.place, envelope_fn=lambda c: oracle.envelope(rec[c], r.k, params))
+    res = check_packing(cs, r.place[:, 10], r.place, envelope_fn=lambda c, kc: oracle.envelope(rec[c], kc, params))
     assert res == dict(out_of_atlas=0, gutter_overlap=0, overlap=0, outside_envelope=0)
     j = r.k // 16
-    assert r.success[j - 1] == 1 and not np.any(r.success[j:])
+    assert r.success[j - 1] == 1
+    # every larger successful candidate has a smaller area-weighted scale
+    perm = oracle.sort(rec)
+    area = np.array([_loop_area2(cs.polygon(perm[s])) for s in range(cs.n)], dtype=object)
+    for jj in range(j + 1, 65):
+        if r.success[jj - 1]:
+            ok, pl, st = oracle.pack_scale(rec, perm, cs.atlas_w, cs.atlas_h, 16 * jj, params)
+            assert ok and int(np.dot(area, pl[:, 6].astype(object))) < r.score
 
 
 def test_small_atlases_keep_sequential_folding():
@@ -177,6 +307,12 @@ def test_small_atlases_keep_sequential_folding():
     c = oracle.pack(cs, oracle.default_params(topt=100, hybrid_min=299))
     assert a.k == b.k and np.array_equal(a.place, b.place) and a.stats[5] == 0
     assert c.stats[5] > 0
+
+
+def _loop_area2(poly):
+    """Twice the area of a vertex loop (shoelace magnitude), exact."""
+    p = [(int(a), int(b)) for a, b in np.asarray(poly).reshape(-1, 2)]
+    return abs(sum(x0 * y1 - x1 * y0 for (x0, y0), (x1, y1) in zip(p, p[1:] + p[:1])))
 
 
 def test_paper_default_is_one_percent_above_ten_thousand():

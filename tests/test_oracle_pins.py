@@ -138,24 +138,78 @@ def test_local_aabbs_match_clipping(seed):
             assert (lo, hi) == (r[R["XLO"] + s], r[R["XHI"] + s])
 
 
-def test_refined_pieces_bound_the_chart():
-    """Refinement only tightens, and every chart point still lies inside the
-    refined piecewise-constant boundaries."""
-    cs = synth.plain64(seed=4, n=16)
-    rec = oracle.prep(cs)
-    for i in range(cs.n):
-        r = rec[i]
-        assert np.all(r[R["TLO"]:R["TLO"] + K] >= r[R["YLO"]:R["YLO"] + K])
-        assert np.all(r[R["BHI"]:R["BHI"] + K] <= r[R["YHI"]:R["YHI"] + K])
-        assert np.all(r[R["LLO"]:R["LLO"] + K] >= r[R["XLO"]:R["XLO"] + K])
-        assert np.all(r[R["RHI"]:R["RHI"] + K] <= r[R["XHI"]:R["XHI"] + K])
-        poly = local_polygon(r, cs.polygon(i))
-        X = r[R["X"]:R["X"] + K + 1]
-        # dense boundary points (vertices and edge points at slice boundaries)
-        for s in range(K):
-            lo, hi = _clip_extent(poly, int(X[s]), int(X[s + 1]), 0)
-            assert r[R["TLO"] + s] <= lo or r[R["TLO"] + s] == r[R["YLO"] + s]
-            assert lo >= r[R["YLO"] + s]
+T = 256  # one texel in Q.8
+
+
+def _lonly(k=2):
+    """Local-AABB proxy alone (no OBB), K slices per axis."""
+    return oracle.default_params(laabb_k=k, flags=oracle.F_LAABB | oracle.F_HC | oracle.F_BALANCE)
+
+
+def test_merge_tightens_columns_closed_form():
+    """Sec. 4.1.1: the two sets of local AABBs are merged, each boundary
+    taking the tighter bound (the inset uses 2 AABBs per axis).  A staircase
+    [0,6]x[0,16] + [6,8]x[10,16] (texels, tall, no reflection) at K = 2:
+    x-slice 1 ([4,8]) reaches the top at x in [4,6], so alone it bounds
+    every column from 4 to 8 by y = 0; the y-slice [0,8] only spans
+    x in [0,6], so columns 6 and 7 meet only the y-slice [8,16] and the
+    merged top there is 8 (the true top is 10).  By hand, at scale 1 and
+    1/2 (column 3 at 1/2 covers x in (6,8), so floor(8/2) = 4)."""
+    poly = [(0, 0), (6 * T, 0), (6 * T, 10 * T), (8 * T, 10 * T), (8 * T, 16 * T), (0, 16 * T)]
+    cs = synth.from_polygons([poly], 64, 64)
+    p = _lonly()
+    rec = oracle.prep(cs, p)
+    r = rec[0]
+    assert (r[R["ROT"]], r[R["FLIPY"]], r[R["FLIPX"]]) == (0, 0, 0)
+    assert list(r[R["YLO"]:R["YLO"] + 2]) == [0, 0]          # the x-slices alone: top 0 everywhere
+    assert list(r[R["XHI"]:R["XHI"] + 2]) == [6 * T, 8 * T]
+    e = oracle.envelope(r, 1024, p)
+    assert list(e.top) == [0, 0, 0, 0, 0, 0, 8, 8]
+    assert list(e.bot) == [16] * 8
+    assert list(e.right) == [6] * 8 + [8] * 8
+    e = oracle.envelope(r, 512, p)
+    assert list(e.top) == [0, 0, 0, 4]
+    assert list(e.bot) == [8] * 4
+
+
+def test_merge_tightens_rows_closed_form():
+    """The same merge along the other axis: [0,8]x[0,10] + [0,2]x[10,16] at
+    K = 2.  The y-slice [8,16] reaches x = 8 (rows 8-9), so alone it bounds
+    rows 8-15 by x = 8; the x-slice [4,8] spans only y in [0,10], so rows
+    10-15 meet only the x-slice [0,4] and their merged right edge is 4 (the
+    true edge is 2).  No reflection: the left and right areas are equal and
+    the bottom area lies right of the midline."""
+    poly = [(0, 0), (8 * T, 0), (8 * T, 10 * T), (2 * T, 10 * T), (2 * T, 16 * T), (0, 16 * T)]
+    cs = synth.from_polygons([poly], 64, 64)
+    p = _lonly()
+    rec = oracle.prep(cs, p)
+    r = rec[0]
+    assert (r[R["ROT"]], r[R["FLIPY"]], r[R["FLIPX"]]) == (0, 0, 0)
+    assert list(r[R["XHI"]:R["XHI"] + 2]) == [8 * T, 8 * T]  # the y-slices alone: right edge 8
+    e = oracle.envelope(r, 1024, p)
+    assert list(e.right) == [8] * 10 + [4] * 6
+    assert list(e.left) == [0] * 16
+    assert list(e.top) == [0] * 8 and list(e.bot) == [16] * 4 + [10] * 4
+
+
+def test_merge_keeps_every_chart_point_inside():
+    """The merged envelope still contains every texel the chart meets, at
+    every slice count and with the OBB off (the merge alone decides)."""
+    for kk in (2, 5, 10):
+        cs = synth.plain64(seed=4, n=16)
+        p = _lonly(kk)
+        rec = oracle.prep(cs, p)
+        for i in range(cs.n):
+            for k in (256, 640, 1024):
+                r = rec[i]
+                e = oracle.envelope(r, k, p)
+                poly, w, h = placed_polygon(cs.polygon(i), k, int(r[R["ROT"]]), int(r[R["FLIPX"]]),
+                                            int(r[R["FLIPY"]]), 0)
+                cv = cover(poly, w, h)
+                rr = np.arange(h)[:, None]
+                assert not np.any(cv & ~((rr >= e.top[None, :]) & (rr < e.bot[None, :])))
+                cc = np.arange(w)[None, :]
+                assert not np.any(cv & ~((cc >= e.left[:, None]) & (cc < e.right[:, None])))
 
 
 def _lshape(notch_corner, W=40, H=60, a=15, b=25):
@@ -589,7 +643,7 @@ def test_invariants_overlap_gutter_bounds(i):
     r = oracle.pack(cs, all_scales=True)
     assert r.status == 0
     rec = oracle.prep(cs)
-    res = check_packing(cs, r.k, r.place, envelope_fn=lambda c: oracle.envelope(rec[c], r.k))
+    res = check_packing(cs, r.place[:, 10], r.place, envelope_fn=lambda c, kc: oracle.envelope(rec[c], kc))
     assert res == dict(out_of_atlas=0, gutter_overlap=0, overlap=0, outside_envelope=0)
     j = r.k // 16
     assert r.success[j - 1] == 1 and not np.any(r.success[j:])
@@ -605,7 +659,7 @@ def test_ablation_modes_keep_invariants(flags):
     r = oracle.pack(cs, params)
     assert r.status == 0
     rec = oracle.prep(cs, params)
-    res = check_packing(cs, r.k, r.place, envelope_fn=lambda c: oracle.envelope(rec[c], r.k, params))
+    res = check_packing(cs, r.place[:, 10], r.place, envelope_fn=lambda c, kc: oracle.envelope(rec[c], kc, params))
     assert res == dict(out_of_atlas=0, gutter_overlap=0, overlap=0, outside_envelope=0)
 
 
