@@ -708,13 +708,15 @@ static int64_t lay_row(int m, const Env *env, const int32_t *dnext, int hc, int6
 /*  2. intermediate downscaling: READING (on the k/1024 grid, integer): the  */
 /*     tail charts take one scale k' <= S at which every tail row, re-laid   */
 /*     from its near end with the envelopes, widths and compacting distances */
-/*     at k', fits the padded width W'.  k' is found by a 16-way search:     */
-/*     with lo = 0 and hi = S + 1, each round tries the 15 scales            */
-/*     lo + floor(i (hi - lo) / 16), i = 1..15, sets lo to the largest that  */
-/*     fits (if any does) and hi to the smallest tried above the new lo, and */
-/*     three rounds end with hi = lo + 1; k' = lo, and the candidate fails   */
-/*     if lo = 0.  Where "every row fits" is monotone in the scale, this is  */
-/*     the largest k' <= S that fits;                                        */
+/*     at k', fits the padded width W'.  k' is searched in rounds of 15      */
+/*     trial scales: the first round tries S - 14 .. S; if one fits, lo is   */
+/*     the largest that does and hi the smallest tried above it (S + 1 if    */
+/*     none), else lo = 0 and hi = S - 14.  Each later round, while hi > lo  */
+/*     + 1, tries lo + floor(i (hi - lo) / 16), i = 1..15, and moves lo to   */
+/*     the largest of them that fits and hi to the smallest tried above the  */
+/*     new lo; three such rounds always end with hi = lo + 1.  k' = lo, and  */
+/*     the candidate fails if lo = 0.  Where "every row fits" is monotone    */
+/*     in the scale, this is the largest k' <= S that fits;                  */
 /*  3. the rows, drawn at k', go into the atlas in FastAtlas's fixed         */
 /*     alternation (READING: one left-to-right row, then two right-to-left   */
 /*     rows, starting with the first tail row) and are pushed up onto the    */
@@ -763,16 +765,19 @@ static int tail_pack(int n, int c0, int row, const Env *env, const int32_t *dnex
     if (t == 0 || P[t] / Wp != P[t - 1] / Wp) rstart[nr++] = t;
   rstart[nr] = m;
 
-  /* 2. intermediate scale k': the 16-way search */
-  int32_t lo = 0, hi = S + 1;
-  for (int round = 0; round < 3; ++round) {
-    int32_t tried[15];
-    int32_t best = lo;
-    for (int i = 1; i <= 15; ++i) {
-      tried[i - 1] = lo + (int32_t)(((int64_t)i * (hi - lo)) / 16);
-      if (tried[i - 1] > lo && tried[i - 1] < hi &&
-          tail_rows_fit(m, nr, rstart, rec, perm + c0, tried[i - 1], params, hc, Wp, x))
-        best = tried[i - 1] > best ? tried[i - 1] : best;
+  /* 2. intermediate scale k': rounds of 15 trial scales (round 0: S-14..S) */
+  int32_t lo = S - 15, hi = S + 1;
+  for (int round = 0; round < 4 && hi > lo + 1; ++round) {
+    int32_t tried[15], best = -1;
+    for (int i = 0; i < 15; ++i) {
+      tried[i] = lo + (int32_t)(((int64_t)(i + 1) * (hi - lo)) / 16);
+      if (tried[i] > lo && tried[i] < hi && tried[i] > best &&
+          tail_rows_fit(m, nr, rstart, rec, perm + c0, tried[i], params, hc, Wp, x))
+        best = tried[i];
+    }
+    if (best < 0) { /* none fits */
+      if (round == 0) { lo = 0; hi = S - 14; continue; }
+      best = lo;
     }
     int32_t nhi = hi;
     for (int i = 0; i < 15; ++i)
