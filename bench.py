@@ -237,7 +237,7 @@ def device_requests(tabi, torch, dev, sets):
     for i, cs in enumerate(sets):
         offs = torch.from_numpy(cs.offsets.view(np.int32).copy()).to(dev)
         verts = torch.from_numpy(cs.verts.copy()).to(dev)
-        out = torch.zeros(12 * cs.n, dtype=torch.uint8, device=dev)
+        out = torch.zeros(tabi.PLACEMENT_DTYPE.itemsize * cs.n, dtype=torch.uint8, device=dev)
         keep.append((offs, verts, out))
         reqs[i] = tabi.Request(cs.atlas_w, cs.atlas_h, cs.n, cs.nv, offs.data_ptr(), verts.data_ptr(),
                                out.data_ptr(), 0, 0)
@@ -339,7 +339,7 @@ def run_ours(args, rank, world, local, sets):
     for i, cs in enumerate(sets):
         offs_h = torch.from_numpy(cs.offsets.view(np.int32).copy()).pin_memory()
         verts_h = torch.from_numpy(cs.verts.copy()).pin_memory()
-        out_h = torch.zeros(12 * cs.n, dtype=torch.uint8).pin_memory()
+        out_h = torch.zeros(tabi.PLACEMENT_DTYPE.itemsize * cs.n, dtype=torch.uint8).pin_memory()
         hold.append((offs_h, verts_h, out_h))
         hreqs[i] = tabi.Request(cs.atlas_w, cs.atlas_h, cs.n, cs.nv, offs_h.data_ptr(), verts_h.data_ptr(),
                                 out_h.data_ptr(), 0, 0)
@@ -355,7 +355,7 @@ def run_ours(args, rank, world, local, sets):
             e2e.append(dt)
     e2e_s = float(np.sum(e2e))
     h2d = int(sum(4 * (cs.n + 1) + 8 * cs.nv for cs in sets))
-    d2h = int(sum(12 * cs.n for cs in sets)) + 16 * A
+    d2h = int(sum(tabi.PLACEMENT_DTYPE.itemsize * cs.n for cs in sets)) + 16 * A
 
     # roofline of the dominant stage
     jtops = [ctx.regions(a)[2] for a in range(A)]
@@ -477,7 +477,7 @@ def run_served(args, local, arrivals, body_of, bodies):
     for cs in bodies:
         offs = torch.from_numpy(cs.offsets.view(np.int32).copy()).to(dev)
         verts = torch.from_numpy(cs.verts.copy()).to(dev)
-        out = torch.zeros(12 * cs.n, dtype=torch.uint8, device=dev)
+        out = torch.zeros(tabi.PLACEMENT_DTYPE.itemsize * cs.n, dtype=torch.uint8, device=dev)
         ts = []
         for _ in range(3):
             torch.cuda.synchronize()

@@ -20,7 +20,8 @@
  *   2. if rot90:  p = (p.y, W0 - p.x)      (W0 = input AABB width, Q.8);
  *   3. if flip_y: p.y = Hq - p.y;  if flip_x: p.x = Wq - p.x
  *      (Wq, Hq = AABB size after step 2, Q.8);
- *   4. t = p * k / 2^18  (texels);  w = ceil(Wq * k / 2^18);
+ *   4. t = p * k / 2^18  (texels);  w = ceil(Wq * k / 2^18), with k the
+ *      placement's own scale (tabi_placement.k);
  *   5. if mirror: t.x = w - t.x;
  *   6. atlas point = (x, y) + t.
  * Every texel whose open square meets a placed chart lies in
@@ -123,26 +124,36 @@ typedef struct tabi_params {
                                 always folded one by one, Tab. 4's t_opt = 0):
                                 once no knee is live and a row's tallest
                                 chart is shorter than t_opt H at the
-                                candidate scale, the remaining charts are
-                                folded by a prefix sum of their offsets
+                                candidate scale k, the remaining charts are
+                                folded by the prefix sum of their offsets
                                 (padded width minus the compacting distance
                                 to the next chart; chart s+1 never left of
-                                chart s-1's right edge) into rows of width
-                                W + 2g - w'max + 1 (w'max the widest
-                                remaining padded chart: every chart ends
-                                inside the atlas without the intermediate
-                                downscaling of the paper, so all charts keep
-                                one scale), laid left-to-right, right-to-
-                                left, right-to-left in turn and dropped
-                                onto the skyline; 0..1000                   */
+                                chart s-1's right edge) with rows cut
+                                modulo W + 2g, so a row's last chart may
+                                overflow; then drawn at one intermediate
+                                scale k' <= k at which every such row, laid
+                                from its near end, fits (searched in rounds
+                                of 15 trial scales, the first k-14 .. k; the
+                                candidate fails if none fits), laid
+                                left-to-right, right-to-left, right-to-left
+                                in turn and dropped onto the skyline.  The
+                                pack's scale is then the successful
+                                candidate with the largest area-weighted
+                                mean scale of its charts (ties: the larger
+                                candidate); each placement carries its
+                                chart's scale; 0..1000                      */
   int32_t hybrid_min_charts; /* the prefix folding applies to atlases of more
                                 than this many charts (the paper: 10,000)   */
 } tabi_params;
 
-/* One placed chart; see "Placement semantics" above. */
+/* One placed chart; see "Placement semantics" above.  k is the chart's
+ * scale k/1024: the pack's scale, or for the charts laid out by the
+ * prefix-sum tail (Sec. 4.4, topt_permille) the tail's intermediate scale,
+ * which is at most the pack's. */
 typedef struct tabi_placement {
   int32_t x, y;
   uint8_t rot90, flip_x, flip_y, mirror;
+  int32_t k;
 } tabi_placement;
 
 typedef struct tabi_ctx tabi_ctx;
@@ -171,13 +182,16 @@ size_t tabi_arena_bytes(int32_t n_charts, int32_t n_verts, int32_t atlas_w, int3
                         int64_t sum_extent_texels, int32_t gutter);
 
 /* Pack one atlas (Sec. 4.3 Algorithm Summary; Algorithm 5 per candidate
- * scale; largest successful scale, Sec. 3.1 / Sec. 5).  HOST buffers:
+ * scale; largest successful scale, Sec. 3.1 / Sec. 5, or with the
+ * prefix-sum tail the largest area-weighted one, Sec. 4.4).  HOST buffers:
  *   offsets[n_charts + 1]  vertex offsets (CSR), offsets[0] = 0,
  *                          offsets[n_charts] = n_verts;
  *   verts[2 * n_verts]     x0, y0, x1, y1, ... (Q.8), one closed loop per
  *                          chart;
  *   out[n_charts]          placements, input order (written on TABI_OK);
- *   out_k                  the chosen k (scale k/1024); 0 on NO_FIT.
+ *   out_k                  the chosen candidate k (scale k/1024); 0 on
+ *                          NO_FIT (each placement's k is its chart's
+ *                          scale: out_k, or the tail's smaller k');
  * The inputs are copied to the device on `stream`, the result back:
  * buffers in pinned (cudaHostAlloc / cudaHostRegister) memory, 4-byte
  * aligned, are read and written by a copy kernel over the host link (one
@@ -387,16 +401,23 @@ tabi_status tabi_server_get_stats(tabi_server *srv, tabi_server_stats *out);
  *   TABI_INSPECT_PAIRS   int32[n] compacting distance d(s, s+1) then
  *                        uint8[n] flags (bit0 CannotMoveAbove(s, s+1),
  *                        bit1 CannotMoveAbove(s+1, s)) for `scale`;
- *   TABI_INSPECT_SCALE   int32[8]: success, rows, knee-folded rows, knees
- *                        found, final max frontline, charts placed,
+ *   TABI_INSPECT_SCALE   int32[12]: success, rows, knee-folded rows,
+ *                        knees found, final max frontline, charts placed,
  *                        evaluated (0 not run: above the area bound or
- *                        below a success; 1 ran to its end; 2 abandoned
- *                        after a larger candidate succeeded), rows folded
- *                        by the prefix sum (topt_permille)
+ *                        moot; 1 ran to its end; 2 abandoned once it could
+ *                        no longer win), rows pushed by the prefix-sum
+ *                        tail (topt_permille), the tail's scale k' (0:
+ *                        none), its first sorted chart (n: none), two
+ *                        unused; then uint64[2] (low, high) the sum over
+ *                        the charts of twice their area (Q.8^2) times
+ *                        their scale (set on success: the quantity the
+ *                        search maximises, Sec. 4.4)
  *                        -- then int32[4n] per sorted chart: x, y, row,
  *                        bits (bit0 mirror, bit1 compacting on, bit2
  *                        knee-folded, bit3 folded by the prefix sum) for
- *                        `scale`.
+ *                        `scale` (the tail's charts at k': their envelopes
+ *                        in TABI_INSPECT_ENV and pairs in
+ *                        TABI_INSPECT_PAIRS are those at k' too).
  * Only candidates the last pack ran to their end are meaningful (all of
  * them with TABI_F_EVAL_ALL and scale_fanout 64; with a smaller fan-out a
  * later wave reuses the envelope regions).  *needed receives the byte
@@ -459,8 +480,11 @@ tabi_status tabi_sort_heights_noalloc(const int32_t *heights, int32_t n, int32_t
 typedef struct tabi_chart_info {
   int32_t orig, Wq, Hq, rot90, flip_y, flip_x, obb_m, valid;
   int64_t u0, u1, v0, v1;                      /* OBB strips at angle obb_m */
-  int32_t ylo[10], yhi[10], xlo[10], xhi[10]; /* final local AABBs        */
-  int32_t tlo[10], bhi[10], llo[10], rhi[10]; /* refined pieces            */
+  int32_t ylo[10], yhi[10], xlo[10], xhi[10]; /* final local AABBs: y
+                                                 extremes of the x-slices,
+                                                 x extremes of the y-slices
+                                                 (merged per scanline,
+                                                 Sec. 4.1.1)              */
   int64_t area_top, area_bot, area_left, area_right, area_bl2, area_br2;
 } tabi_chart_info;
 

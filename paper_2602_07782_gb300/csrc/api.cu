@@ -125,10 +125,10 @@ void add_pieces(std::vector<CopyPiece> &v, const void *src, void *dst, uint64_t 
 // Arena bytes of the per-chart and per-atlas arrays of one atlas (all but
 // the envelope pools), with the host-input copies.
 size_t fixed_bytes(int64_t n, int64_t nv) {
-  const size_t per_chart = 4 + sizeof(tabi_chart_info) + 2 * sizeof(ChartShape) + 3 * 4 + 16 + 32 +
+  const size_t per_chart = 4 + sizeof(tabi_chart_info) + 2 * sizeof(ChartShape) + 3 * 4 + 16 + 40 +
                            (size_t)kScales * (4 + 4 + 16 + 4 + 1 + 16) + 4 + 4 + sizeof(tabi_placement);
   const size_t per_atlas = sizeof(AtlasDesc) + (size_t)kScales * 2 * 8 * 2 + sizeof(ScaleOut) * kScales +
-                           8 + sizeof(PackResult) + 8 + 40 * 256;
+                           8 + sizeof(PackResult) + 8 + 40 * 256 + (size_t)kScales * (kCtlSave * 4 + 16) + 8;
   const size_t pieces = pieces_of(4 * (uint64_t)(n + 1)) + pieces_of(8 * (uint64_t)nv) +
                         pieces_of(sizeof(tabi_placement) * (uint64_t)n);
   return (size_t)n * per_chart + 8 * (size_t)nv + per_atlas + sizeof(CopyPiece) * pieces + 256 + sizeof(Pack) +
@@ -143,7 +143,7 @@ __global__ void init_kernel(const Pack *__restrict__ pp) {
   const int t = threadIdx.x;
   if (blockIdx.x == 0) {
     if (t < 2 * kScales) p.jtot[t] = 0;
-    for (int i = t; i < kScales * kMaxChunks; i += blockDim.x) {
+    for (int i = t; i < kScales * kChunkSlots; i += blockDim.x) {
       p.counter[i] = 0;
       p.rcounter[i] = 0;
     }
@@ -153,7 +153,7 @@ __global__ void init_kernel(const Pack *__restrict__ pp) {
     }
   }
   for (int at = blockIdx.x; at < p.A; at += gridDim.x) {
-    if (t < kScales) p.scale_out[at * kScales + t] = ScaleOut{0, 0, 0, 0, 0, 0, 0, 0};
+    if (t < kScales) p.scale_out[at * kScales + t] = ScaleOut{};
     if (t == 0) {
       p.found[at] = -1;
       p.err[at] = 0;
@@ -166,8 +166,11 @@ __global__ void init_kernel(const Pack *__restrict__ pp) {
   }
 }
 
-// Per atlas: the largest successful candidate (Sec. 3.1 / Sec. 5), then the
-// placements of that candidate gathered back into input order.
+// Per atlas: the successful candidate (Sec. 3.1 / Sec. 5) whose
+// area-weighted mean scale is largest (Sec. 4.4; without a prefix-sum tail
+// that is the largest successful candidate; ties keep the larger one), then
+// its placements gathered back into input order, each with its chart's
+// scale (the candidate's, or the tail's k').
 __global__ void select_kernel(const Pack *__restrict__ pp) {
   __shared__ int best;
   __shared__ uint32_t err;
@@ -175,8 +178,13 @@ __global__ void select_kernel(const Pack *__restrict__ pp) {
   for (int at = blockIdx.x; at < p.A; at += gridDim.x) {
     if (threadIdx.x == 0) {
       int b = -1;
-      for (int j = kScales - 1; j >= 0; --j)
-        if (p.scale_out[at * kScales + j].success) { b = j; break; }
+      unsigned __int128 bw = 0;
+      for (int j = kScales - 1; j >= 0; --j) {
+        const ScaleOut &so = p.scale_out[at * kScales + j];
+        if (!so.success) continue;
+        const unsigned __int128 w = ((unsigned __int128)so.wsum[1] << 64) | so.wsum[0];
+        if (b < 0 || w > bw) { b = j; bw = w; }
+      }
       best = b;
       err = p.err[at];
       PackResult r{0, 0, err, b};
@@ -190,6 +198,8 @@ __global__ void select_kernel(const Pack *__restrict__ pp) {
     if (best >= 0 && !err) {
       const AtlasDesc &ad = p.atl[at];
       const int4 *place = p.place + (int64_t)best * p.N;
+      const ScaleOut &so = p.scale_out[at * kScales + best];
+      const int32_t kb = 16 * (best + 1), t0 = so.tail_start, kt = so.tail_k;
       for (int s = ad.cb + threadIdx.x; s < ad.cb + ad.n; s += blockDim.x) {
         const int c = p.perm[s];
         const int4 pl = place[s];
@@ -201,6 +211,7 @@ __global__ void select_kernel(const Pack *__restrict__ pp) {
         o.flip_x = (uint8_t)inf.flip_x;
         o.flip_y = (uint8_t)inf.flip_y;
         o.mirror = (uint8_t)(pl.w & 1);
+        o.k = s - ad.cb >= t0 ? kt : kb;
         ad.out[c - ad.cb] = o;
       }
     }
@@ -273,6 +284,12 @@ void enqueue_wave(const Pack *dp, const Launch &L, int F, cudaStream_t st, Stage
     e();
     b(5);
     launch_rowloop(dp, L, q, F, st);
+    e();
+  }
+  if (L.tail) {  // the prefix-sum tail (Sec. 4.4): its scale, redraw, push (with the row loop's time)
+    b(5);
+    launch_tail(dp, L, F, st);
+    launch_rowloop(dp, L, L.Q, F, st);
     e();
   }
   launch_wave_end(dp, h, in_graph, st);
@@ -358,7 +375,7 @@ tabi_status capture_graph(tabi_ctx *ctx, const Launch &L, int F, cudaGraph_t *ou
 tabi_status get_graph(tabi_ctx *ctx, const Launch &L, int F, cudaGraphExec_t *out) {
   for (const GraphEntry &g : ctx->graphs)
     if (g.F == F && g.smem == L.rowloop_smem && g.threads == L.rowloop_threads && g.ctas == L.rowloop_ctas &&
-        g.Q == L.Q && g.prep_group == L.prep_group && g.laabb_k == L.laabb_k) {
+        g.Q == L.Q && g.prep_group == L.prep_group && g.laabb_k == L.laabb_k && g.tail == L.tail) {
       *out = g.exec;
       return TABI_OK;
     }
@@ -370,7 +387,7 @@ tabi_status get_graph(tabi_ctx *ctx, const Launch &L, int F, cudaGraphExec_t *ou
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphInstantiate");
   ctx->graphs.push_back(
-      GraphEntry{F, L.rowloop_smem, L.rowloop_threads, L.rowloop_ctas, L.Q, L.prep_group, L.laabb_k, exec});
+      GraphEntry{F, L.rowloop_smem, L.rowloop_threads, L.rowloop_ctas, L.Q, L.prep_group, L.laabb_k, L.tail, exec});
   *out = exec;
   return TABI_OK;
 }
@@ -508,6 +525,8 @@ tabi_status batch_launch(tabi_ctx *ctx, const tabi_params *params, tabi_request 
   p.laabb_k = params->laabb_count;
   p.topt = params->topt_permille;
   p.hyb_min = params->hybrid_min_charts;
+  p.tail = 0;
+  for (int i = 0; i < A && p.topt > 0; ++i) p.tail |= desc[i].n > p.hyb_min;
   // launch shape: forced (autotuner), else tuned for this batch class,
   // else the default; an explicit fan-out in params wins over both
   int maxW = 1;
@@ -559,17 +578,21 @@ tabi_status batch_launch(tabi_ctx *ctx, const tabi_params *params, tabi_request 
   p.act_atl = cv.take<int32_t>(A);
   p.act_pre = cv.take<int32_t>(A);
   p.act_chart = cv.take<int32_t>(n);
-  p.counter = cv.take<int32_t>(kScales * kMaxChunks);
-  p.rcounter = cv.take<uint32_t>(kScales * kMaxChunks);
+  p.counter = cv.take<int32_t>(kScales * kChunkSlots);
+  p.rcounter = cv.take<uint32_t>(kScales * kChunkSlots);
   p.cur_wave = cv.take<int32_t>(1);
   p.raster_words = cv.take<unsigned long long>(2);
   p.carea = cv.take<unsigned long long>(n);
   p.barea = cv.take<unsigned long long>(n);
   p.pre2 = cv.take<unsigned long long>(n);
   p.preE = cv.take<unsigned long long>(n);
+  p.prea = cv.take<unsigned long long>(n);
+  p.area_tot = cv.take<unsigned long long>(A);
   p.tstate = cv.take<int32_t>((size_t)A * kScales);
   p.front_save = cv.take<int32_t>((size_t)A * p.F * p.wps_stride);
-  p.ctl_save = cv.take<int32_t>((size_t)A * p.F * 16);
+  p.ctl_save = cv.take<int32_t>((size_t)A * p.F * kCtlSave);
+  p.ttask = cv.take<int4>((size_t)A * p.F);
+  p.tcount = cv.take<int32_t>(1);
   if (!cv.ok) return fail(ctx, TABI_ERR_OOM, "arena too small for the per-chart arrays");
   // the rest in equal thirds: column words, their chart indices, row words
   const size_t left = (cv.cap - cv.used) / sizeof(uint32_t);
@@ -637,7 +660,7 @@ tabi_status batch_launch(tabi_ctx *ctx, const tabi_params *params, tabi_request 
   for (int i = 0; i < A; ++i) want = std::max(want, rowloop_smem_wanted(desc[i].W, p.g));
   int smem = (int)((want + 16383) & ~(size_t)16383);
   if (smem > ctx->rowloop_dyn_max) smem = ctx->rowloop_dyn_max;
-  Launch L{ctx->sms, smem, tn.threads == 512 ? 512 : 1024, 1, p.Q, p.prep_group, p.laabb_k};
+  Launch L{ctx->sms, smem, tn.threads == 512 ? 512 : 1024, 1, p.Q, p.prep_group, p.laabb_k, p.tail != 0};
   if (L.rowloop_threads == 512 && tn.ctas == 2) {
     // two CTAs per multiprocessor if both fit its shared memory
     const int two = (ctx->smem_per_sm - 2 * (ctx->smem_reserved + rowloop_static_smem())) / 2 & ~255;

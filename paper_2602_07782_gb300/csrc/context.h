@@ -16,6 +16,7 @@ namespace tabi {
 // the record at the arena's start, so the graph serves any batch.
 struct GraphEntry {
   int F, smem, threads, ctas, Q, prep_group, laabb_k;  // (the progressive bound is read from the record)
+  bool tail;                                           // the prefix-sum tail's kernels follow each wave
   cudaGraphExec_t exec;
 };
 
@@ -61,8 +62,9 @@ struct tabi_ctx {
   // optional per-stage timing (direct launches with events between stages)
   bool timing = false;
   // event pairs around the stages of one pack: prologue (3), per wave and
-  // chart chunk plan, raster, compaction, row loop (4), selection
-  static constexpr int kStageMarks = 4 + 4 * tabi::kScales * tabi::kMaxChunks + 4;
+  // chart chunk plan, raster, compaction, row loop (4), per wave the tail
+  // (1), selection
+  static constexpr int kStageMarks = 4 + (4 * tabi::kMaxChunks + 1) * tabi::kScales + 4;
   cudaEvent_t ev[2 * kStageMarks] = {};
   int n_ev = 0;
   double stage_ms[8] = {};

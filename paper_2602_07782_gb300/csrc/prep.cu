@@ -159,7 +159,7 @@ __device__ __forceinline__ void prep_chart(const Pack &p, int c) {
       atomicOr(p.err + at, kErrInvalid);
     }
     for (int i = lane; i < kSlices; i += G) {
-      sh->tlo[i] = 0; sh->bhi[i] = 256; sh->llo[i] = 0; sh->rhi[i] = 256;
+      sh->ylo[i] = 0; sh->yhi[i] = 256; sh->xlo[i] = 0; sh->xhi[i] = 256;
     }
     return;
   }
@@ -279,45 +279,17 @@ __device__ __forceinline__ void prep_chart(const Pack &p, int c) {
     group_slices<G, K>(v, nv, xf, true, Wq, ylo, yhi);
   }
 
-  // Sec. 4.1.1 merge: tighten each slice by the other axis' slices (task
-  // t of the group's lanes: record slot t of the x-slices for t < 10, slot
-  // t - 16 of the y-slices for 16 <= t < 26), written out at once
-  for (int t = lane; t < 32; t += G) {
-    if (t < kSlices) {
-      const int i = t * K / kSlices;
-      const int64_t Xi = (int64_t)i * Wq / K, Xi1 = (int64_t)(i + 1) * Wq / K;
-      int64_t t2 = kI64Max, b2v = kI64Min;
+  // the final slices into the shape record (ten slots per axis, slot t
+  // holding slice t K / 10); Sec. 4.1.1's merge of the two sets happens per
+  // scanline in the rasterizer
+  for (int t = lane; t < 2 * kSlices; t += G) {
+    const int ax = t >= kSlices, i = (t - ax * kSlices) * K / kSlices;
+    int32_t lo = 0, hi = 0;
 #pragma unroll
-      for (int j = 0; j < K; ++j)
-        if (xlo[j] <= Xi1 && xhi[j] >= Xi) {
-          const int64_t Yj = (int64_t)j * Hq / K, Yj1 = (int64_t)(j + 1) * Hq / K;
-          t2 = min(t2, Yj);
-          b2v = max(b2v, Yj1);
-        }
-      int64_t yl = 0, yh = 0;
-#pragma unroll
-      for (int q = 0; q < K; ++q) if (q == i) { yl = ylo[q]; yh = yhi[q]; }
-      const int32_t r0 = (int32_t)max(yl, t2), r1 = (int32_t)min(yh, b2v);
-      inf->tlo[t] = r0; inf->bhi[t] = r1;
-      sh->tlo[t] = r0; sh->bhi[t] = r1;
-    } else if (t >= 16 && t < 16 + kSlices) {
-      const int j = (t - 16) * K / kSlices;
-      const int64_t Yj = (int64_t)j * Hq / K, Yj1 = (int64_t)(j + 1) * Hq / K;
-      int64_t l2 = kI64Max, r2 = kI64Min;
-#pragma unroll
-      for (int i = 0; i < K; ++i)
-        if (ylo[i] <= Yj1 && yhi[i] >= Yj) {
-          const int64_t Xi = (int64_t)i * Wq / K, Xi1 = (int64_t)(i + 1) * Wq / K;
-          l2 = min(l2, Xi);
-          r2 = max(r2, Xi1);
-        }
-      int64_t xl = 0, xh = 0;
-#pragma unroll
-      for (int q = 0; q < K; ++q) if (q == j) { xl = xlo[q]; xh = xhi[q]; }
-      const int32_t r0 = (int32_t)max(xl, l2), r1 = (int32_t)min(xh, r2);
-      inf->llo[t - 16] = r0; inf->rhi[t - 16] = r1;
-      sh->llo[t - 16] = r0; sh->rhi[t - 16] = r1;
-    }
+    for (int q = 0; q < K; ++q)
+      if (q == i) { lo = ax ? xlo[q] : ylo[q]; hi = ax ? xhi[q] : yhi[q]; }
+    if (ax) { sh->xlo[t - kSlices] = lo; sh->xhi[t - kSlices] = hi; }
+    else { sh->ylo[t] = lo; sh->yhi[t] = hi; }
   }
 
   // App. A OBB: 8 angles, extents of u = xC + yS, v = -xS + yC.  Lane l
@@ -455,6 +427,46 @@ __global__ void __launch_bounds__(kPrepThreads, 2) prep_kernel(const Pack *__res
 // ---------------------------------------------------------------------------
 constexpr int kSortThreads = kRadixThreads;
 
+// Exclusive scan of three counters over the threads of a CTA (kSortThreads
+// threads, in thread order); every thread also gets the totals.
+__device__ __forceinline__ void block_scan3(unsigned long long (&v)[3], unsigned long long (&tot)[3]) {
+  __shared__ unsigned long long part[3][kSortThreads / 32 + 1];
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  unsigned long long inc[3];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    inc[q] = v[q];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long u = __shfl_up_sync(0xffffffffu, inc[q], o);
+      if (lane >= o) inc[q] += u;
+    }
+    if (lane == 31) part[q][w] = inc[q];
+  }
+  __syncthreads();
+  if (w == 0) {
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const unsigned long long x = part[q][lane];
+      unsigned long long y = x;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long u = __shfl_up_sync(0xffffffffu, y, o);
+        if (lane >= o) y += u;
+      }
+      part[q][lane] = y - x;
+      if (lane == 31) part[q][32] = y;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    v[q] = part[q][w] + inc[q] - v[q];
+    tot[q] = part[q][32];
+  }
+  __syncthreads();
+}
+
 __device__ void sort_atlas(const Pack &p, int at) {
   const int cb = p.atl[at].cb;
   const int n = p.atl[at].n, tid = threadIdx.x;
@@ -463,9 +475,36 @@ __device__ void sort_atlas(const Pack &p, int at) {
     kA[c] = (uint32_t)((1 << 21) - 1 - p.shape_in[cb + c].Hq);
     vA[c] = (uint32_t)c;
   }
-  radix_sort21(kA, vA, kB, vB, n);  // sorted values in vB
-  for (int s = tid; s < n; s += kSortThreads) p.perm[cb + s] = cb + (int32_t)vB[s];
+  radix_sort21(kA, vA, kB, vB, n);  // sorted values in vB, keys in kB
+  // the permutation, the sorted heights, and per sorted position the areas
+  // and heights of the charts before it (exclusive prefix sums: the area
+  // bounds take the certified areas and heights, Sec. 4.4's choice the
+  // areas); each thread sums a run of consecutive positions, then a scan
+  const int P = (n + kSortThreads - 1) / kSortThreads;
+  const int s0 = min(n, tid * P), s1 = min(n, s0 + P);
+  unsigned long long v[3] = {0, 0, 0}, tot[3];
+  for (int s = s0; s < s1; ++s) {
+    const int c = cb + (int32_t)vB[s];
+    const int32_t hq = (1 << 21) - 1 - (int32_t)kB[s];
+    p.perm[cb + s] = c;
+    p.hq[cb + s] = hq;
+    v[0] += p.barea[c];
+    v[1] += (unsigned long long)hq;
+    v[2] += p.carea[c];
+  }
+  block_scan3(v, tot);
+  for (int s = s0; s < s1; ++s) {
+    const int c = cb + (int32_t)vB[s];
+    p.pre2[cb + s] = v[0];
+    p.preE[cb + s] = v[1];
+    p.prea[cb + s] = v[2];
+    v[0] += p.barea[c];
+    v[1] += (unsigned long long)((1 << 21) - 1 - (int32_t)kB[s]);
+    v[2] += p.carea[c];
+  }
+  __syncthreads();
   if (tid == 0) {
+    p.area_tot[at] = tot[2];
     // Area bound: placed charts' covers, each dilated by the gutter g, are
     // disjoint and lie in the padded atlas (W + 2g) x (H + 2g).  A connected
     // polygon of area A and larger extent E dilated by g covers at least
@@ -474,17 +513,23 @@ __device__ void sort_atlas(const Pack &p, int at) {
     // area is area2 k^2 / 2^37 and the extent E k / 2^18 texels (area2 =
     // twice the area in Q.8^2, E in Q.8), so candidate k can succeed only if
     //   area2 k^2 + 2g 2^19 k sum(E) + 4 g^2 2^37 n <= (W + 2g)(H + 2g) 2^37.
-    // Larger candidates are skipped.
+    // Where the prefix-sum tail may apply (Sec. 4.4) its charts may end at
+    // a smaller scale than k, so only the charts surely folded row by row
+    // at k (head_prefix) count with their area and extent; every chart
+    // keeps its 4 g^2.  Larger candidates are skipped.
     int jt = kScales - 1;
     if (!(p.flags & TABI_F_EVAL_ALL)) {
       const uint64_t g = (uint64_t)p.g;
       const unsigned __int128 lim =
           (unsigned __int128)(((uint64_t)p.atl[at].W + 2 * g) * ((uint64_t)p.atl[at].H + 2 * g)) << 37;
-      const unsigned __int128 s2 = p.area2[at], ex = p.ext_sum[at];
       const unsigned __int128 fixed = (unsigned __int128)(4 * g * g * (uint64_t)n) << 37;
+      const bool hybrid = p.topt > 0 && n > p.hyb_min;
       jt = -1;
       for (int j = 0; j < kScales; ++j) {
         const uint64_t k = 16 * (uint64_t)(j + 1);
+        const int hp = head_prefix(p.hq + cb, n, (int64_t)k, p.topt, p.atl[at].H, hybrid);
+        const unsigned __int128 s2 = hp < n ? p.pre2[cb + hp] : p.area2[at];
+        const unsigned __int128 ex = hp < n ? p.preE[cb + hp] : p.ext_sum[at];
         const unsigned __int128 need = s2 * (k * k) + ((ex * (2 * g * k)) << 19) + fixed;
         if (need <= lim) jt = j;
       }

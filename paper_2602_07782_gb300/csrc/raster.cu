@@ -21,49 +21,13 @@
 // the regions of one wave tile the pools and the next wave reuses them.
 // Every kernel here is persistent: a fixed grid loops over the work the
 // wave plan left on the device (the charts of atlases still searching).
-#include "raster_math.cuh"
-#include "tabi_internal.cuh"
+#include "raster_dev.cuh"
 
 namespace tabi {
 namespace {
 
-constexpr int32_t kBig = 0x3fffffff;
 constexpr int kRasterThreads = 256;
 constexpr int kRasterWarps = kRasterThreads / 32;
-
-// One axis of one chart: raw scanlines 0..len-1 from the per-warp constants,
-// padded scanlines 0..len+2g-1 written to dst.  Returns max upper' (axis 0:
-// the chart's deepest padded BottomEdge).
-__device__ __forceinline__ int32_t warp_axis(const rmath::AxisK &ak, int g, uint32_t *__restrict__ dst) {
-  const int lane = threadIdx.x & 31;
-  const int32_t len = ak.len;
-  const int32_t padded = len + 2 * g;
-  int32_t prev_lo = kBig, prev_hi = -kBig;
-  int32_t maxhi = 0;
-  for (int32_t base = 0; base < padded; base += 32) {
-    const int32_t c = base + lane;
-    int32_t lo = kBig, hi = -kBig;
-    if (c < len) rmath::scanline(ak, c, lo, hi);
-    int32_t dlo = lo, dhi = hi;
-    for (int o = 1; o <= 2 * g; ++o) {
-      const int32_t clo = __shfl_sync(0xffffffffu, lo, (lane - o) & 31);
-      const int32_t chi = __shfl_sync(0xffffffffu, hi, (lane - o) & 31);
-      const int32_t plo = __shfl_sync(0xffffffffu, prev_lo, (lane - o) & 31);
-      const int32_t phi = __shfl_sync(0xffffffffu, prev_hi, (lane - o) & 31);
-      const int32_t vlo = lane >= o ? clo : plo, vhi = lane >= o ? chi : phi;
-      dlo = vlo < dlo ? vlo : dlo;
-      dhi = vhi > dhi ? vhi : dhi;
-    }
-    if (c < padded) {
-      const int32_t hi2 = dhi + 2 * g;
-      dst[c] = (uint32_t)dlo | ((uint32_t)hi2 << 16);
-      maxhi = hi2 > maxhi ? hi2 : maxhi;
-    }
-    prev_lo = lo;
-    prev_hi = hi;
-  }
-  return warp_max(maxhi);
-}
 
 // Warp-items: (chart of an atlas still searching, run of G consecutive
 // candidates of the atlas's wave range).  G is chosen so that the wave has
@@ -91,7 +55,7 @@ __global__ void __launch_bounds__(kRasterThreads, 3) raster_kernel(const Pack *_
   // an item's cost follows its chart's size, which spans orders of
   // magnitude, so a fixed assignment leaves most warps idle behind the few
   // that drew the largest charts
-  uint32_t *next_item = p.rcounter + wave * kMaxChunks + q;
+  uint32_t *next_item = p.rcounter + wave * kChunkSlots + q;
   while (true) {
     uint32_t grab = 0;
     if (lane == 0) grab = atomicAdd(next_item, 1u);
@@ -111,15 +75,25 @@ __global__ void __launch_bounds__(kRasterThreads, 3) raster_kernel(const Pack *_
     rmath::CornerQ cq;
     const bool corner_lane = lane >= 24 && use_o && m > 0;
     // per chart, kept across the run of candidates: the piece lanes' slice
-    // bounds (registers) and the OBB lanes' scale-free terms (shared)
-    uint32_t pb0 = 0, pb1 = 0, plq = 0, phq = 0;
+    // bounds and their cross slice's extent and bounds (registers) and the
+    // OBB lanes' scale-free terms (shared).  Lane i < 10 holds x-slice slot
+    // i as a column piece and y-slice slot i as a column cross piece; lane
+    // 10 + i the same with the axes swapped.  A cross slot's bounds are
+    // those of its K-slice: slot i holds slice s = i K / 10, whose bounds
+    // are the ten-slot boundaries 10 s / K and 10 (s + 1) / K.
+    uint32_t pb0 = 0, pb1 = 0, plq = 0, phq = 0, ce0 = 0, ce1 = 0, cb0 = 0, cb1 = 0;
     if (lane < 2 * rmath::kK) {
       const int ax = lane >= rmath::kK, i = lane - ax * rmath::kK;
-      const uint32_t ext = (uint32_t)(ax ? sh.Hq : sh.Wq);
+      const uint32_t ext = (uint32_t)(ax ? sh.Hq : sh.Wq), oth = (uint32_t)(ax ? sh.Wq : sh.Hq);
       pb0 = i * ext / rmath::kK;
       pb1 = (i + 1) * ext / rmath::kK;
-      plq = (uint32_t)(ax ? sh.llo[i] : sh.tlo[i]);
-      phq = (uint32_t)(ax ? sh.rhi[i] : sh.bhi[i]);
+      plq = (uint32_t)(ax ? sh.xlo[i] : sh.ylo[i]);
+      phq = (uint32_t)(ax ? sh.xhi[i] : sh.yhi[i]);
+      ce0 = (uint32_t)(ax ? sh.ylo[i] : sh.xlo[i]);
+      ce1 = (uint32_t)(ax ? sh.yhi[i] : sh.xhi[i]);
+      const int sl = i * p.laabb_k / rmath::kK;
+      cb0 = (uint32_t)(sl * rmath::kK / p.laabb_k) * oth / rmath::kK;
+      cb1 = (uint32_t)((sl + 1) * rmath::kK / p.laabb_k) * oth / rmath::kK;
     } else if (lane < 2 * rmath::kK + 2) {
       const int ax = lane - 2 * rmath::kK;
       rmath::setup_obb_fixed(ax ? a1 : a0, ax, m, C, S, kObbDivCos[m], kObbDivSin[m], use_l, use_o);
@@ -133,7 +107,7 @@ __global__ void __launch_bounds__(kRasterThreads, 3) raster_kernel(const Pack *_
       const int64_t k = 16 * (j + 1);
       // a finished candidate (later chunks): nothing to draw; the corner
       // quantities still step to the next candidate
-      if (!all && (p.tstate[at * kScales + j] != 0 || *(volatile int32_t *)(p.found + at) >= j)) {
+      if (!all && (p.tstate[at * kScales + j] != 0 || *(volatile int32_t *)(p.found + at) > j)) {
         if (corner_lane) rmath::corner_advance(cq);
         continue;
       }
@@ -142,6 +116,7 @@ __global__ void __launch_bounds__(kRasterThreads, 3) raster_kernel(const Pack *_
       if (lane < 2 * rmath::kK) {
         const int ax = lane >= rmath::kK, i = lane - ax * rmath::kK;
         rmath::setup_piece(ax ? a1 : a0, i, pb0, pb1, (uint32_t)k, plq, phq);
+        rmath::setup_cross(ax ? a1 : a0, i, ce0, ce1, (uint32_t)(ax ? sh.Hq : sh.Wq), (uint32_t)k, cb0, cb1);
       } else if (lane < 2 * rmath::kK + 2) {
         const int ax = lane - 2 * rmath::kK;
         rmath::setup_obb_k(ax ? a1 : a0, ax, sh.Wq, sh.Hq, k, C, S, sh.u0, sh.u1, sh.v0, sh.v1);
@@ -219,9 +194,8 @@ __global__ void __launch_bounds__(1024) layout_kernel(const Pack *__restrict__ p
   const int g2 = 2 * p.g;
   for (int64_t item = blockIdx.x; item < (int64_t)p.A * kScales; item += gridDim.x) {
     const int at = (int)(item / kScales), j = (int)(item % kScales);
-    // candidates above the area bound's top are never evaluated (the first
-    // item still builds the atlas's prefix sums)
-    if (j > p.jtop[at] && j != 0) continue;
+    // candidates above the area bound's top are never evaluated
+    if (j > p.jtop[at]) continue;
     const int n = p.atl[at].n, cb = p.atl[at].cb;
     const int64_t k = 16 * (j + 1);
     const int P = (n + 1023) >> 10;
@@ -232,23 +206,6 @@ __global__ void __launch_bounds__(1024) layout_kernel(const Pack *__restrict__ p
       sr += ((p.hq[cb + s] * k + kFix - 1) >> 18) + g2;
     }
     int64_t tx = 0, ty = 0;
-    if (j == 0 && p.prog_bound) {
-      // once per atlas: prefix sums, in sorted order, of the charts' doubled
-      // areas and larger extents (the row loop's progressive area bound)
-      int64_t sa = 0, se = 0, ta = 0, te = 0;
-      for (int s = s0; s < s1; ++s) {
-        sa += (int64_t)p.barea[p.perm[cb + s]];
-        se += p.hq[cb + s];
-      }
-      block_scan2(sa, se, ta, te, part);
-      for (int s = s0; s < s1; ++s) {
-        p.pre2[cb + s] = (unsigned long long)sa;
-        p.preE[cb + s] = (unsigned long long)se;
-        sa += (int64_t)p.barea[p.perm[cb + s]];
-        se += p.hq[cb + s];
-      }
-      __syncthreads();  // part is reused by the next scan
-    }
     block_scan2(sc, sr, tx, ty, part);
     const bool meta = j <= p.jtop[at];  // candidates the search may evaluate
     for (int s = s0; s < s1; ++s) {
@@ -327,17 +284,17 @@ __global__ void __launch_bounds__(1024) plan_kernel(const Pack *__restrict__ pp,
   __syncthreads();
   for (int base = 0; base < p.A; base += 1024) {
     const int at = base + tid;
-    // a success in an earlier wave ends the atlas's search; within this
-    // wave only the candidates above the success still matter
+    // candidates below the atlas's moot bound (`found`: set by successes,
+    // Sec. 4.4's choice) can no longer win; the atlas takes part while the
+    // wave holds a candidate at or above it
     const int top = at < p.A ? p.jtop[at] - wave * p.F : -1;
     const int fnd = at < p.A ? *(volatile int32_t *)(p.found + at) : 0;
-    bool live = at < p.A && *(volatile uint32_t *)(p.err + at) == 0 && top >= 0 &&
-                (fnd < 0 || (q > 0 && fnd < top));
+    bool live = at < p.A && *(volatile uint32_t *)(p.err + at) == 0 && top >= 0 && top >= fnd;
     if (live && q > 0 && !(p.flags & TABI_F_EVAL_ALL)) {
       // a later chunk only for atlases with a candidate of the wave still running
       const WaveRange wr = wave_range(p.jtop[at], wave, p.F);
       bool running = false;
-      for (int j = max(wr.lo, fnd + 1); j <= wr.hi && !running; ++j) running = p.tstate[at * kScales + j] == 0;
+      for (int j = max(wr.lo, fnd); j <= wr.hi && !running; ++j) running = p.tstate[at * kScales + j] == 0;
       live = running;
     }
     const int n = live ? p.atl[at].n : 0;
@@ -355,7 +312,7 @@ __global__ void __launch_bounds__(1024) plan_kernel(const Pack *__restrict__ pp,
   if (tid == 0) {
     p.act_info[0] = (int32_t)carry[0];
     p.act_info[1] = (int32_t)carry[1];
-    p.counter[wave * kMaxChunks + q] = 0;
+    p.counter[wave * kChunkSlots + q] = 0;
   }
 }
 
@@ -373,18 +330,6 @@ __global__ void __launch_bounds__(256) plan_fill_kernel(const Pack *__restrict__
 // ---------------------------------------------------------------------------
 // horizontal compactor (Sec. 4.1.2, App. A interlock)
 // ---------------------------------------------------------------------------
-// Inclusive max / min scan over an aligned group of G lanes.
-template <int G, bool kMax>
-__device__ __forceinline__ int32_t group_scan_incl(int32_t v, unsigned gm) {
-  const int lane = threadIdx.x & (G - 1);
-#pragma unroll
-  for (int o = 1; o < G; o <<= 1) {
-    const int32_t u = __shfl_up_sync(gm, v, o, G);
-    if (lane >= o) v = kMax ? (u > v ? u : v) : (u < v ? u : v);
-  }
-  return v;
-}
-
 // One group of G lanes per (scale, sorted pair (s, s+1)), A = s left of
 // B = s+1, top-aligned:  d = w'_A - max_r (R'_A(r) - L'_B(r));  B may move
 // up relative to A iff every row of B stays right of all rows of A above
@@ -418,55 +363,14 @@ __global__ void __launch_bounds__(256, 8) hcompact_kernel(const Pack *__restrict
       p.pflags[(int64_t)j * N + c] = 0;
     }
     if (c == cb) continue;
-    const int s = c - 1;
-    const int64_t ps = (int64_t)j * N + s;
-    const int32_t *ma = p.meta + ps * 4, *mb = ma + 4;
-    const int32_t wA = ma[0], hA = ma[1], hB = mb[1];
-    const uint32_t *pool = p.pool + p.abase[region(at, j, 1)];
-    const uint32_t *rowA = pool + p.rowstart[ps];
-    const uint32_t *rowB = pool + p.rowstart[ps + 1];
-    const int hmin = hA < hB ? hA : hB;
-    int32_t M = -kBig;
-    for (int r = lane; r < hmin; r += G) {
-      const int32_t ra = (int32_t)(rowA[r] >> 16), lb = (int32_t)(rowB[r] & 0xffffu);
-      M = max(M, ra - lb);
-    }
-    M = group_max<G>(M, gm);
-    int32_t d = wA - M;
-    if (d < 0) d = 0;
-    const int32_t off = wA - d;
-    int a_free = 1, b_free = 1;
-    int32_t carry_max = -kBig, carry_min = kBig;  // over rows of A / of B above the chunk
-    const int hmax = hA > hB ? hA : hB;
-    for (int base = 0; base < hmax; base += G) {
-      const int r = base + lane;
-      const int32_t ra = r < hA ? (int32_t)(rowA[r] >> 16) : -kBig;
-      const int32_t lb = r < hB ? off + (int32_t)(rowB[r] & 0xffffu) : kBig;
-      // exclusive prefix max of R'_A and prefix min of off + L'_B
-      const int32_t imax = group_scan_incl<G, true>(ra, gm);
-      const int32_t imin = group_scan_incl<G, false>(lb, gm);
-      int32_t emax = __shfl_up_sync(gm, imax, 1, G);
-      int32_t emin = __shfl_up_sync(gm, imin, 1, G);
-      if (lane == 0) { emax = -kBig; emin = kBig; }
-      emax = max(emax, carry_max);
-      emin = min(emin, carry_min);
-      if (r >= 1 && r < hB && lb < emax) b_free = 0;
-      if (r >= 1 && r < hA && ra > emin) a_free = 0;
-      carry_max = max(carry_max, __shfl_sync(gm, imax, G - 1, G));
-      carry_min = min(carry_min, __shfl_sync(gm, imin, G - 1, G));
-    }
-    a_free = __all_sync(gm, a_free);
-    b_free = __all_sync(gm, b_free);
-    if (lane == 0) {
-      p.dnext[ps] = d;
-      p.pflags[ps] = (uint8_t)((a_free ? 0 : 1) | (b_free ? 0 : 2));
-    }
+    compact_pair<G>(p, at, j, c - 1, lane, gm);
   }
 }
 
 // After a wave: the next wave index, and whether any atlas can still search
-// in it (no success, no error, candidates left below its top); inside a
-// captured graph that decides whether the wave loop runs again.
+// in it (no error, and the next wave's top candidate exists and is not
+// below the atlas's moot bound); inside a captured graph that decides
+// whether the wave loop runs again.
 __global__ void __launch_bounds__(1024) wave_end_kernel(const Pack *__restrict__ pp, cudaGraphConditionalHandle h,
                                                         int in_graph) {
   __shared__ int any;
@@ -475,7 +379,7 @@ __global__ void __launch_bounds__(1024) wave_end_kernel(const Pack *__restrict__
   if (threadIdx.x == 0) any = 0;
   __syncthreads();
   for (int at = threadIdx.x; at < p.A; at += blockDim.x)
-    if (p.found[at] < 0 && p.err[at] == 0 && p.jtop[at] - w * p.F >= 0) any = 1;
+    if (p.err[at] == 0 && p.jtop[at] - w * p.F >= max(p.found[at], 0)) any = 1;
   __syncthreads();
   if (threadIdx.x == 0) {
     *p.cur_wave = w;

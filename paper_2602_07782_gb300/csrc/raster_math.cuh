@@ -92,8 +92,13 @@ TABI_HD int32_t fdiv_magic(int32_t a, const Magic &mg) {
 struct AxisK {
   // local-AABB pieces: first scanline, span (last - first), scaled bounds
   // lo, hi -- one 16-byte record each, so a scanline tests a piece with one
-  // broadcast vector load, one unsigned compare and two min/max
+  // broadcast vector load, one unsigned compare and two min/max.  piece[]
+  // are the slices along this axis (bounded by their extremes), cross[] the
+  // slices along the other axis, whose extent on this axis bounds the
+  // scanlines they meet by their own boundaries (Sec. 4.1.1's merge keeps
+  // the tighter of the two)
   int4 piece[kK];
+  int4 cross[kK];
   // OBB, fast path (X = multiple of F)
   int32_t ah1, ah2, bh1, bh2;   // floor(A1/F), floor(A2/F), floor(B1/F), floor(B2/F)
   int32_t b1, b2, d1, d2;
@@ -141,9 +146,9 @@ TABI_HD int32_t fdiv32(int32_t a, int32_t d, float rcp) {
 
 // Local-AABB piece i of an axis at scale k, from its slice bounds
 // b0 = floor(i ext / K), b1 = floor((i + 1) ext / K) (ext = Wq or Hq) and
-// the refined piece bounds lo_q8, hi_q8 (tlo/bhi or llo/rhi), all in
-// [0, 2^21): the scaled values stay below 2^31 (k <= 1024), so 32-bit
-// unsigned arithmetic is exact.
+// the slice's extremes lo_q8, hi_q8 on the other axis (ylo/yhi or
+// xlo/xhi), all in [0, 2^21): the scaled values stay below 2^31
+// (k <= 1024), so 32-bit unsigned arithmetic is exact.
 TABI_HD void setup_piece(AxisK &ak, int i, uint32_t b0, uint32_t b1, uint32_t k, uint32_t lo_q8, uint32_t hi_q8) {
   const uint32_t s0 = b0 * k, s1 = b1 * k;
   const int32_t plo = (int32_t)(s0 >> 18);                 // floor(s0 / F)
@@ -151,6 +156,23 @@ TABI_HD void setup_piece(AxisK &ak, int i, uint32_t b0, uint32_t b1, uint32_t k,
   const int32_t lo = (int32_t)((lo_q8 * k) >> 18);
   const int32_t hi = (int32_t)((hi_q8 * k + kF - 1) >> 18);
   ak.piece[i] = make_int4(plo, phi - plo, lo, hi);
+}
+
+// Cross piece i of an axis at scale k: a slice of the other axis, whose
+// extent on this axis is [e0, e1] (xlo/xhi of a y-slice for columns,
+// ylo/yhi of an x-slice for rows) and whose own boundaries are b0, b1
+// (Y_i, Y_i+1 or X_i, X_i+1), all Q.8 in [0, 2^21].  It meets scanline c
+// (the open interval (cF, min((c+1)F, end))) iff e0 k < min((c+1)F, end)
+// and e1 k > cF, i.e. for floor(e0 k / F) <= c <= ceil(e1 k / F) - 1 when
+// e0 < ext (never otherwise: such a slice only touches the far end); on
+// them the chart lies between floor(b0 k / F) and ceil(b1 k / F).
+TABI_HD void setup_cross(AxisK &ak, int i, uint32_t e0, uint32_t e1, uint32_t ext, uint32_t k, uint32_t b0,
+                         uint32_t b1) {
+  const int32_t plo = (int32_t)((e0 * k) >> 18);
+  const int32_t phi = (int32_t)((e1 * k + kF - 1) >> 18) - 1;
+  const int32_t lo = (int32_t)((b0 * k) >> 18);
+  const int32_t hi = (int32_t)((b1 * k + kF - 1) >> 18);
+  ak.cross[i] = (e0 < ext && phi >= plo) ? make_int4(plo, phi - plo, lo, hi) : make_int4(kInf, 0, lo, hi);
 }
 
 // OBB terms of one axis that do not depend on the scale (once per chart).
@@ -263,6 +285,24 @@ TABI_HD void corner_init(CornerQ &cq, int item, int j0, int64_t C, int64_t S, in
   cq.r = r;
 }
 
+// The same quantity at any scale k <= 1024 directly: k num (|k num| <
+// 2^61) divided by D, with the remainder (only its being non-zero is used,
+// for the positions).
+TABI_HD void corner_at(CornerQ &cq, int item, int64_t k, int64_t C, int64_t S, int64_t u0, int64_t u1,
+                       int64_t v0, int64_t v1) {
+  const int64_t a = k * corner_num(item, C, S, u0, u1, v0, v1);
+  const int64_t N = C * C + S * S;
+  cq.D = corner_den(item, C, S);
+  cq.qs = cq.rs = 0;
+  if ((item & 3) < 2) {
+    cq.q = fdiv_n(a >> 18, N);  // floor(a / (N F)) = floor(floor(a / F) / N)
+    cq.r = 0;
+  } else {
+    cq.q = fdiv_n(a, N);
+    cq.r = a - cq.q * N;
+  }
+}
+
 TABI_HD void corner_advance(CornerQ &cq) {
   cq.q += cq.qs;
   cq.r += cq.rs;
@@ -339,7 +379,11 @@ TABI_HD void scanline_from(const AxisK &ak, int32_t c, int32_t pl, int32_t ph, i
   hi_out = hi;
 }
 
-// The same with the pieces tested here (all ten per scanline).
+// The same with the pieces tested here (all ten per scanline, then the
+// ten cross pieces: the tighter of the two bounds).  Some cross piece meets
+// every scanline of a valid chart (the chart's boundary crosses every
+// scanline and each of its points lies in some slice), which the guard
+// only makes explicit.
 TABI_HD void scanline(const AxisK &ak, int32_t c, int32_t &lo_out, int32_t &hi_out) {
   int32_t pl = kInf, ph = -kInf;
 #pragma unroll
@@ -348,6 +392,21 @@ TABI_HD void scanline(const AxisK &ak, int32_t c, int32_t &lo_out, int32_t &hi_o
     if ((uint32_t)(c - pc.x) <= (uint32_t)pc.y) {  // plo <= c <= plo + span
       pl = imin32(pl, pc.z);
       ph = imax32(ph, pc.w);
+    }
+  }
+  if (ak.use_l) {
+    int32_t ql = kInf, qh = -kInf;
+#pragma unroll
+    for (int i = 0; i < kK; ++i) {
+      const int4 pc = ak.cross[i];
+      if ((uint32_t)(c - pc.x) <= (uint32_t)pc.y) {
+        ql = imin32(ql, pc.z);
+        qh = imax32(qh, pc.w);
+      }
+    }
+    if (ql != kInf) {
+      pl = imax32(pl, ql);
+      ph = imin32(ph, qh);
     }
   }
   scanline_from(ak, c, pl, ph, lo_out, hi_out);

@@ -47,12 +47,19 @@
 //
 // Prefix-sum tail (Sec. 4.4): once no knee is live and a row's first
 // (tallest) chart is below t_opt of the atlas height (atlases of more than
-// hybrid_min charts), phase T switches the task to the tail for good.  A
-// tail row is the same fold, continued from the carried unwrapped prefix
-// (the offsets' running sum, clamp included) and cut where the prefix
-// passes the next multiple of L = W' - w'max + 1; its direction follows
-// the fixed pattern left-to-right, right-to-left, right-to-left; phases D,
-// E and H run it as the one configuration of the row.
+// hybrid_min charts), phase T switches the task to the tail for good, in
+// two passes.  First the fold at the candidate scale: a tail row is the
+// same fold, continued from the carried unwrapped prefix (the offsets'
+// running sum, clamp included) and cut where the prefix passes the next
+// multiple of W' (its last chart may overflow); the row is only recorded
+// (its charts' place records carry the tail row and, at its first chart,
+// the row length) and nothing is pushed.  Once every chart is folded the
+// task parks (state kTaskTailSearch) and the tail kernels search the
+// intermediate scale k', redraw the tail charts at k' and compact them.
+// Then the push pass (q = Q, state kTaskTailPush): each recorded row is
+// laid from its near end by the same fold at k', in the fixed direction
+// pattern left-to-right, right-to-left, right-to-left, and phases D, E and
+// H push it as the one configuration of the row.
 #include "tabi_internal.cuh"
 
 namespace tabi {
@@ -71,10 +78,13 @@ struct Ctl {
   int32_t knee_rows, knees, knee_t[2], stage_lo, stage_hi, abort;
   int32_t t_at, t_j, t_skip;
   int32_t front_sum;     // the committed frontline summed over the padded columns
-  // prefix-sum tail (Sec. 4.4): on, fold width L, unwrapped prefix of the
+  // prefix-sum tail (Sec. 4.4): mode (0 off, 1 folding at the candidate
+  // scale, 3 pushing at the tail scale), cut width, unwrapped prefix of the
   // next row's first chart and of the chart before it (have_prev: one
-  // exists) with that chart's width, tail rows committed
-  int32_t tail, tL, tP, tPrev, tWprev, tHave, trows;
+  // exists) with that chart's width, tail rows folded or pushed, first tail
+  // chart, rows before it, the tail scale, the pushed row's length
+  int32_t tail, tL, tP, tPrev, tWprev, tHave, trows, c0, head_rows, kt, plen;
+  int32_t head_p;        // charts surely folded row by row (the progressive bound's share)
   int32_t red[kMaxWarps];
 };
 
@@ -178,18 +188,27 @@ __global__ void __launch_bounds__(NT) rowloop_kernel(const Pack *__restrict__ pp
 
   while (true) {
     if (tid == 0) {
-      const int t = atomicAdd(p.counter + wave * kMaxChunks + q, 1);
+      const int t = atomicAdd(p.counter + wave * kChunkSlots + q, 1);
       int at = -1, j = 0, skip = 1;
-      if (t < *(volatile int32_t *)p.act_info * nj) {
-        at = p.act_atl[t / nj];
-        const WaveRange wr = wave_range(p.jtop[at], wave, nj);
-        j = wr.hi - t % nj;
-        skip = j < wr.lo || (q > 0 && p.tstate[at * kScales + j] != 0);  // outside the wave, or finished
+      const bool push = q >= p.Q;  // the tail's push pass: its tasks come from the tail list
+      const int ntask = push ? *(volatile int32_t *)p.tcount : *(volatile int32_t *)p.act_info * nj;
+      if (t < ntask) {
+        if (push) {
+          const int4 tt = p.ttask[t];
+          at = tt.x;
+          j = tt.y;
+          skip = p.tstate[at * kScales + j] != kTaskTailPush;
+        } else {
+          at = p.act_atl[t / nj];
+          const WaveRange wr = wave_range(p.jtop[at], wave, nj);
+          j = wr.hi - t % nj;
+          skip = j < wr.lo || (q > 0 && p.tstate[at * kScales + j] != kTaskRun);  // outside the wave, or parked
+        }
         if (!skip && !eval_all && *(volatile int32_t *)(p.found + at) > j) {
           // a larger candidate has succeeded: this one is moot
           skip = 1;
           if (q > 0) p.scale_out[at * kScales + j].evaluated = 2;  // it ran in an earlier chunk
-          p.tstate[at * kScales + j] = 1;                         // no later chunk runs it
+          p.tstate[at * kScales + j] = kTaskDone;                 // no later chunk runs it
         }
         // the host sizes the CTA for the widest atlas; never overrun it
         const int W = p.atl[at].W;
@@ -242,10 +261,10 @@ __global__ void __launch_bounds__(NT) rowloop_kernel(const Pack *__restrict__ pp
       int4 *place = p.place + js;
 
       // charts drawn so far (chunks 0..q); rows are decided on them only
-      const int avail = q == p.Q - 1 ? n : chunk_end(n, q, p.Q);
+      const int avail = q >= p.Q - 1 ? n : chunk_end(n, q, p.Q);
       const int64_t slot = (int64_t)at * p.F + (wave_range(p.jtop[at], wave, nj).hi - j);
       int32_t *fsave = p.front_save + slot * p.wps_stride;
-      int32_t *csave = p.ctl_save + slot * 16;
+      int32_t *csave = p.ctl_save + slot * kCtlSave;
       if (q == 0) {
         for (int x = tid; x < wp_pad; x += kNT) front[x] = 0;
         if (tid == 0) {
@@ -253,17 +272,28 @@ __global__ void __launch_bounds__(NT) rowloop_kernel(const Pack *__restrict__ pp
           ctl.knee_valid = 0; ctl.knee_ltr = 0; ctl.knee_l = 0; ctl.knee_r = 0;
           ctl.knee_rows = 0; ctl.knees = 0;
           ctl.tail = 0; ctl.tL = 1; ctl.tP = 0; ctl.tPrev = 0; ctl.tWprev = 0; ctl.tHave = 0; ctl.trows = 0;
+          ctl.c0 = n; ctl.head_rows = 0; ctl.kt = 0;
         }
-      } else {  // resume where the previous chunk stopped
+      } else {  // resume where the previous chunk (or the tail search) stopped
         for (int x = tid; x < wp_pad; x += kNT) front[x] = fsave[x];
         if (tid == 0) {
           ctl.row_start = csave[0]; ctl.row = csave[1]; ctl.committed = csave[2]; ctl.prev_ltr = csave[3];
           ctl.knee_valid = csave[4]; ctl.knee_ltr = csave[5]; ctl.knee_l = csave[6]; ctl.knee_r = csave[7];
           ctl.knee_rows = csave[8]; ctl.knees = csave[9];
-          ctl.tail = csave[10] & 1; ctl.tHave = (csave[10] >> 1) & 1; ctl.trows = csave[10] >> 2;
+          ctl.tail = csave[kCsTail] & 3; ctl.tHave = (csave[kCsTail] >> 2) & 1; ctl.trows = csave[kCsTail] >> 3;
           ctl.tL = csave[11]; ctl.tP = csave[12]; ctl.tPrev = csave[13]; ctl.tWprev = csave[14];
+          ctl.c0 = csave[kCsC0]; ctl.head_rows = csave[kCsHeadRows]; ctl.kt = csave[kCsKt];
+          if (q >= p.Q) {  // the push pass: the tail rows again from the first, at the tail scale
+            ctl.tail = 3;
+            ctl.row_start = ctl.c0;
+            ctl.row = ctl.head_rows;
+            ctl.trows = 0;
+            ctl.committed = csave[kCsCommitted];
+          }
         }
       }
+      if (tid == 0)  // charts surely folded row by row at this scale (the rest may end smaller)
+        ctl.head_p = area_bound ? head_prefix(hqa, n, 16 * (int64_t)(j + 1), p.topt, ad.H, hybrid) : n;
       {  // the frontline's sum (atlas sides <= 8192: below 2^31), kept up to date by the commits
         int32_t fs = 0;
         if (q > 0 && area_bound)
@@ -284,24 +314,24 @@ __global__ void __launch_bounds__(NT) rowloop_kernel(const Pack *__restrict__ pp
 
         // ---- T: switch to the prefix-sum tail (Sec. 4.4) ----------------------
         // once no knee is live and the row's first (tallest) chart is shorter
-        // than t_opt H at this scale; the rows are then folded to the width
-        // L = W' - w'max + 1 (w'max over the remaining charts, known from the
-        // layout before any is drawn), so every chart ends inside the atlas
+        // than t_opt H at this scale: from here on the charts are folded by
+        // the prefix of their offsets with rows cut modulo W' (recorded, not
+        // pushed; see the file comment)
         if (hybrid && !ctl.tail && !ctl.knee_valid &&
             1000 * (int64_t)(meta[(int64_t)row_start * 4 + 1] - 2 * g) < (int64_t)p.topt * ad.H) {
-          int32_t wm = 0;
-          for (int s = row_start + tid; s < n; s += kNT) wm = max(wm, meta[(int64_t)s * 4]);
-          wm = block_max<kNW>(wm, ctl);
           if (tid == 0) {
-            if (wm > Wp) ctl.fail = 1;  // a chart wider than the atlas
-            ctl.tail = 1; ctl.tL = Wp - wm + 1; ctl.tP = 0; ctl.tHave = 0;
+            ctl.tail = 1; ctl.tL = Wp; ctl.tP = 0; ctl.tHave = 0;
+            ctl.c0 = row_start; ctl.head_rows = row;
           }
           __syncthreads();
-          if (ctl.fail) break;
         }
-        const bool tail = ctl.tail;
-        // a tail row's start in the unwrapped prefix, and its fold width
-        const int32_t tB = tail ? (ctl.tP / ctl.tL) * ctl.tL : 0, tL = ctl.tL;
+        if (ctl.tail == 3 && tid == 0) ctl.plen = place[row_start].w & ~kTailFirst;  // a recorded row
+        __syncthreads();
+        const int tmode = ctl.tail;
+        const bool tail = tmode != 0;
+        // a folded tail row's start in the unwrapped prefix, and its cut width
+        const int32_t tB = tmode == 1 ? (ctl.tP / ctl.tL) * ctl.tL : 0, tL = ctl.tL;
+        const int32_t plen = ctl.plen;
 
         // ---- A: knee refresh (Algorithm 3) and the concavity's max -----------
         const bool knee = ctl.knee_valid;
@@ -341,7 +371,7 @@ __global__ void __launch_bounds__(NT) rowloop_kernel(const Pack *__restrict__ pp
             // state at the chunk start: x of its first chart, x and right edge
             // of the chart before it (none at the row start)
             int32_t carry_x = 0, carry_xprev = kNeg, carry_re = kNeg, carry_wprev = kNeg;
-            if (tail) {  // continue the prefix, relative to this row's start
+            if (tmode == 1) {  // continue the prefix, relative to this row's start
               carry_x = ctl.tP - tB;
               if (ctl.tHave) {
                 carry_xprev = ctl.tPrev - tB;
@@ -403,9 +433,11 @@ __global__ void __launch_bounds__(NT) rowloop_kernel(const Pack *__restrict__ pp
                   carry_wprev = __shfl_sync(0xffffffffu, w, 31);
                 }
                 carry_x = __shfl_sync(0xffffffffu, xnext, 31);
-                // the first chart that does not fit ends the row
-                // (a tail row: the first chart starting at or past L)
-                const unsigned overF = __ballot_sync(0xffffffffu, !valid || (tail ? xt >= tL : xt + w > foldF));
+                // the first chart that does not fit ends the row (a tail row
+                // being folded: the first starting at or past the cut; one
+                // being pushed: its recorded length)
+                const unsigned overF = __ballot_sync(
+                    0xffffffffu, !valid || (tmode == 1 ? xt >= tL : tmode == 3 ? t >= plen : xt + w > foldF));
                 const unsigned overK = __ballot_sync(0xffffffffu, !valid || xt + w > foldK);
                 if (!doneF && overF) { lenF = t0 + __ffs(overF) - 1; doneF = true; }
                 else if (!doneF) lenF = t0 + 32;
@@ -456,11 +488,17 @@ __global__ void __launch_bounds__(NT) rowloop_kernel(const Pack *__restrict__ pp
               // Once the charts not yet placed cannot fit that way into the
               // area under the frontline, the candidate fails now instead of
               // rows later (checked after every committed row).
-              if (area_bound && row > 0) {
+              // Charts the prefix-sum tail may draw smaller count with their
+              // 4g^2 only (head_p: those surely drawn at this scale), and the
+              // tail's rows are not checked.
+              if (area_bound && row > 0 && !tail) {
+                const int hp = ctl.head_p;
                 const unsigned long long nxt2 = p.pre2[cb + row_start], nxtE = p.preE[cb + row_start];
+                const unsigned long long end2 = hp < n ? p.pre2[cb + hp] : tot2;
+                const unsigned long long endE = hp < n ? p.preE[cb + hp] : totE;
                 const int32_t fr = Wp * Hp - ctl.front_sum;  // free texels under the frontline (sides <= 8192)
                 const uint64_t kk = 16 * (uint64_t)(j + 1), gg = (uint64_t)g;
-                const unsigned __int128 S2 = tot2 - nxt2, SE = totE - nxtE;
+                const unsigned __int128 S2 = row_start < hp ? end2 - nxt2 : 0, SE = row_start < hp ? endE - nxtE : 0;
                 const unsigned __int128 need = S2 * (kk * kk) + ((SE * (2 * gg * kk)) << 19) +
                                                ((unsigned __int128)(4 * gg * gg * (uint64_t)(n - row_start)) << 37);
                 if (need > ((unsigned __int128)(uint32_t)fr << 37)) ctl.bound_fail = 1;
@@ -499,6 +537,27 @@ __global__ void __launch_bounds__(NT) rowloop_kernel(const Pack *__restrict__ pp
         if (ctl.len[tail ? vt : 0] == 0) {  // a chart wider than the atlas: this scale fails
           if (tid == 0) ctl.fail = 1;
           break;
+        }
+        if (tmode == 1) {
+          // a tail row folded at the candidate scale: record its charts (the
+          // row, and its length at the first) and continue the prefix
+          const int len = ctl.len[vt];
+          for (int t = tid; t < len; t += kNT)
+            place[row_start + t] = make_int4(0, 0, trows, t == 0 ? (len | kTailFirst) : 0);
+          if (tid == 0) {
+            const int32_t *pos = vt ? posH : posN;
+            if (row_start + len < n) {
+              ctl.tP = tB + pos[len];
+              ctl.tPrev = tB + pos[len - 1];
+              ctl.tWprev = wps[len - 1];
+              ctl.tHave = 1;
+            }
+            ctl.trows = trows + 1;
+            ctl.row_start = row_start + len;
+            ctl.fail = ctl.abort ? 2 : 0;
+          }
+          __syncthreads();
+          continue;
         }
 
         // ---- D: push ----------------------------------------------------------
@@ -659,14 +718,7 @@ __global__ void __launch_bounds__(NT) rowloop_kernel(const Pack *__restrict__ pp
         if (tid == 0) {
           const int v = best >> 1, dir = best & 1, fold = v >> 1, hc = v & 1;
           const int len = ctl.len[v];
-          if (tail) {
-            const int32_t *pos = vt ? posH : posN;
-            if (row_start + len < n) {  // the next row continues the prefix from here
-              ctl.tP = tB + pos[len];
-              ctl.tPrev = tB + pos[len - 1];
-              ctl.tWprev = wps[len - 1];
-              ctl.tHave = 1;
-            }
+          if (tail) {  // a tail row pushed at the tail scale
             ctl.trows = trows + 1;
           } else if (fold == 0) {
             // App. A: a knee in this row starts the concavity at the taller
@@ -706,7 +758,10 @@ __global__ void __launch_bounds__(NT) rowloop_kernel(const Pack *__restrict__ pp
           if (fB <= shi - slo) {
             for (int f = fA + tid; f < fB; f += kNT) {  // lane per staged column word
               // the word's chart and column, from its staged owner index
-              // (checked: a wrong owner raises an error, never a stray access)
+              // (checked: a wrong owner raises an error, never a stray access;
+              // -1: a word no chart owns, left between the tail's charts when
+              // they were redrawn narrower at the tail scale)
+              if (sown[f] < 0) continue;
               const int t = sown[f] - row_start;
               if ((unsigned)t >= (unsigned)len) { atomicOr(p.err + at, kErrRow); continue; }
               const int w = wps[t];
@@ -751,18 +806,23 @@ __global__ void __launch_bounds__(NT) rowloop_kernel(const Pack *__restrict__ pp
 
       }
 
-      if (deferred) {  // keep the state for the next chunk
+      // the tail folded at the candidate scale: park it for the tail search
+      const bool parked = !deferred && ctl.tail == 1 && !ctl.fail && ctl.row_start >= n;
+      if (deferred || parked) {  // keep the state for the next chunk, or for the tail's push
         for (int x = tid; x < wp_pad; x += kNT) fsave[x] = front[x];
         if (tid == 0) {
           csave[0] = ctl.row_start; csave[1] = ctl.row; csave[2] = ctl.committed; csave[3] = ctl.prev_ltr;
           csave[4] = ctl.knee_valid; csave[5] = ctl.knee_ltr; csave[6] = ctl.knee_l; csave[7] = ctl.knee_r;
           csave[8] = ctl.knee_rows; csave[9] = ctl.knees;
-          csave[10] = ctl.tail | (ctl.tHave << 1) | (ctl.trows << 2);
+          csave[kCsTail] = ctl.tail | (ctl.tHave << 2) | (ctl.trows << 3);
           csave[11] = ctl.tL; csave[12] = ctl.tP; csave[13] = ctl.tPrev; csave[14] = ctl.tWprev;
-          p.tstate[at * kScales + j] = 0;
+          csave[kCsC0] = ctl.c0; csave[kCsHeadRows] = ctl.head_rows; csave[kCsTrows] = ctl.trows;
+          csave[kCsCommitted] = ctl.committed;
+          p.tstate[at * kScales + j] = parked ? kTaskTailSearch : kTaskRun;
         }
       } else if (tid == 0) {
         const int ok = !ctl.fail && ctl.row_start >= n;
+        const bool tailed = ctl.tail == 3;
         so->success = ok;
         so->rows = ctl.row;
         so->knee_rows = ctl.knee_rows;
@@ -771,8 +831,20 @@ __global__ void __launch_bounds__(NT) rowloop_kernel(const Pack *__restrict__ pp
         so->placed = ctl.row_start;
         so->evaluated = ctl.fail == 2 ? 2 : 1;
         so->tail_rows = ctl.trows;
-        p.tstate[at * kScales + j] = 1;
-        if (ok) atomicMax(p.found + at, j);
+        so->tail_k = tailed ? ctl.kt : 0;
+        so->tail_start = tailed ? ctl.c0 : n;
+        if (ok) {
+          // Sec. 4.4: the candidate's area-weighted scale sum (its charts at
+          // k, the tail's at k'); candidates that cannot exceed it are moot
+          const unsigned long long tot = p.area_tot[at];
+          const unsigned long long head = tailed ? p.prea[cb + ctl.c0] : tot;
+          const unsigned __int128 w = (unsigned __int128)head * (uint64_t)(16 * (j + 1)) +
+                                      (unsigned __int128)(tot - head) * (uint64_t)(tailed ? ctl.kt : 0);
+          so->wsum[0] = (unsigned long long)w;
+          so->wsum[1] = (unsigned long long)(w >> 64);
+          atomicMax(p.found + at, moot_below(w, tot));
+        }
+        p.tstate[at * kScales + j] = kTaskDone;
       }
     }  // task not skipped
     __syncthreads();  // ctl is rewritten by the next task

@@ -22,18 +22,42 @@ constexpr int64_t kFix = 1LL << 18;  // scaled units per texel (Q.8 * k)
 enum : uint32_t { kErrInvalid = 1u, kErrPool = 2u, kErrRow = 4u };
 
 // Scale-independent shape record of one chart, in sorted order (what the
-// envelope rasterizer reads).  32-byte aligned for vector loads.
+// envelope rasterizer reads).  32-byte aligned for vector loads.  Slot t of
+// the slice arrays holds slice floor(t K / 10) of K: ylo/yhi the extremes
+// of y over the x-slice, xlo/xhi those of x over the y-slice (Q.8).
 struct __align__(16) ChartShape {
   int32_t Wq, Hq, m, pad;
   int64_t u0, u1, v0, v1;
-  int32_t tlo[kSlices], bhi[kSlices], llo[kSlices], rhi[kSlices];
+  int32_t ylo[kSlices], yhi[kSlices], xlo[kSlices], xhi[kSlices];
 };
 
 // Per-(atlas, candidate scale) summary (TABI_INSPECT_SCALE header).
-// evaluated: 0 not run, 1 ran to its end, 2 abandoned once a larger
-// candidate of the same atlas had succeeded.
+// evaluated: 0 not run, 1 ran to its end, 2 abandoned once the candidate
+// could no longer win.  The prefix-sum tail (Sec. 4.4): its rows, its
+// scale k' (0: none, or none fitted) and its first chart (n: no tail).
+// wsum: sum over the charts of twice the area (Q.8^2) times the chart's
+// scale (the area-weighted mean scale times the total), set on success.
 struct ScaleOut {
   int32_t success, rows, knee_rows, knees, score, placed, evaluated, tail_rows;
+  int32_t tail_k, tail_start, pad0, pad1;
+  unsigned long long wsum[2];  // low, high 64 bits
+};
+
+// Row-loop task state of an (atlas, candidate) per wave: 0 running (or not
+// begun), 1 finished, 2 prefix-sum tail folded at the candidate scale and
+// waiting for its intermediate scale, 3 intermediate scale found, tail rows
+// waiting to be pushed.
+enum : int32_t { kTaskRun = 0, kTaskDone = 1, kTaskTailSearch = 2, kTaskTailPush = 3 };
+// A tail chart's place record between the fold and the push: (0, 0, tail
+// row, row length | kTailFirst) for the first chart of a row, (0, 0, tail
+// row, 0) for the others.
+constexpr int32_t kTailFirst = 0x40000000;
+// ints per parked row-loop state (ctl_save)
+constexpr int kCtlSave = 32;
+// fields of a parked state used by the tail
+enum : int {
+  kCsTail = 10, kCsC0 = 15, kCsHeadRows = 16, kCsTrows = 17, kCsLo = 18, kCsHi = 19, kCsMask = 20,
+  kCsRound = 21, kCsKt = 22, kCsCommitted = 23
 };
 
 // Result of one atlas, written on the device and read once by the host.
@@ -74,6 +98,7 @@ struct Pack {
   int32_t laabb_k;              // local AABBs per axis (2, 5 or 10; record slot t holds slice t K / 10)
   int32_t topt;                 // t_opt of the prefix-sum tail, permille of the atlas height (0: off)
   int32_t hyb_min;              // the tail applies to atlases of more charts than this
+  int32_t tail;                 // some atlas of the batch may take the tail (the launch sequence has its kernels)
   const AtlasDesc *atl;         // [A]
   int32_t *catl;                // [N] atlas of each chart
   tabi_chart_info *info;        // [N] input order
@@ -106,17 +131,21 @@ struct Pack {
   int32_t *act_atl;             // [A] those atlases, in batch order
   int32_t *act_pre;             // [A] their first position in act_chart
   int32_t *act_chart;           // [N] their charts (global sorted index)
-  int32_t *counter;             // [64][kMaxChunks] row-loop task counter of each (wave, chunk)
-  uint32_t *rcounter;           // [64][kMaxChunks] raster warp-item counter of each (wave, chunk)
+  int32_t *counter;             // [64][kChunkSlots] row-loop task counter of each (wave, chunk; tail push)
+  uint32_t *rcounter;           // [64][kChunkSlots] raster warp-item counter of each (wave, chunk)
   int32_t *cur_wave;            // the wave the kernels work on (advanced by wave_end)
   unsigned long long *raster_words;  // [2] padded scanline words / column words the raster evaluated
   unsigned long long *carea;    // [N] twice each chart's polygon area |shoelace| (Q.8^2), input order
   unsigned long long *barea;    // [N] carea if the loop is certified simple, else 0 (the area bounds)
   unsigned long long *pre2;     // [N] sorted order: barea summed over the atlas's earlier charts
   unsigned long long *preE;     // [N] sorted order: Hq summed over the atlas's earlier charts
-  int32_t *tstate;              // [A][64] row-loop task: 0 running (or not begun), 1 finished
+  unsigned long long *prea;     // [N] sorted order: carea summed over the atlas's earlier charts
+  unsigned long long *area_tot; // [A] carea summed over the atlas (the weights of Sec. 4.4's choice)
+  int32_t *tstate;              // [A][64] row-loop task state (kTask*)
   int32_t *front_save;          // [A][F][wps_stride] frontline of a task between chunks
-  int32_t *ctl_save;            // [A][F][16] row state of a task between chunks
+  int32_t *ctl_save;            // [A][F][kCtlSave] row state of a task between chunks (and its tail search)
+  int4 *ttask;                  // [A F] tail tasks of the wave: atlas, candidate, slot, first tail chart
+  int32_t *tcount;              // [1] how many
 };
 
 // Region of (atlas a, candidate j) in the column / row pools.
@@ -131,6 +160,7 @@ __host__ __device__ __forceinline__ int64_t region(int a, int j, int which) {
 // (the first chunks are short -- the sorted charts come tallest first, and
 // a candidate far above the answer fails within its first rows).
 constexpr int kMaxChunks = 8;
+constexpr int kChunkSlots = kMaxChunks + 1;  // per wave: the chunks, then the tail's push pass
 __host__ __device__ __forceinline__ int chunk_end(int n, int q, int Q) {
   int e;
   switch (Q) {
@@ -165,6 +195,7 @@ struct Launch {
   int Q;               // chart chunks per wave
   int prep_group;      // prep lanes per chart: 32, 16, 8 or 4
   int laabb_k;         // local AABBs per axis: 2, 5 or 10 (selects the prep kernel)
+  bool tail;           // the batch may take the prefix-sum tail: its kernels follow each wave
 };
 void launch_init(const Pack *dp, const Launch &L, cudaStream_t st);
 void launch_prep(const Pack *dp, const Launch &L, cudaStream_t st);
@@ -181,6 +212,11 @@ cudaError_t rowloop_prepare(int smem);  // raise the CTA's shared-memory limit (
 int rowloop_static_smem();              // the row-loop kernel's static shared memory
 void launch_rowloop(const Pack *dp, const Launch &L, int q, int F, cudaStream_t st);
 void launch_select(const Pack *dp, const Launch &L, cudaStream_t st);
+// The prefix-sum tail after a wave's last chunk (Sec. 4.4): the tasks that
+// folded their tail, the rounds of trial scales, the redraw and the
+// compaction at the chosen scale (the row loop pushes the rows after).
+void launch_tail(const Pack *dp, const Launch &L, int F, cudaStream_t st);
+constexpr int kTailRounds = 4;
 size_t rowloop_smem_bytes(int W, int g);       // shared memory a row-loop CTA needs without the stage
 size_t rowloop_smem_wanted(int W, int g);      // ... with a stage of two atlas widths
 
@@ -322,6 +358,36 @@ __device__ __forceinline__ void radix_sort21(uint32_t *kA, uint32_t *vA, uint32_
     }
     __syncthreads();
   }
+}
+
+// Sec. 4.4's choice among the successful candidates: the largest
+// sum_c area_c * scale_c (wsum).  No chart's scale exceeds its candidate's,
+// so once a candidate with sum w has succeeded, candidate j can only win if
+// 16 (j + 1) * total > w: candidates below floor(w / (16 total)) are moot
+// (all of them, if the charts have no area).  This is the atlas's `found`.
+__device__ __forceinline__ int32_t moot_below(unsigned __int128 w, unsigned long long total) {
+  if (total == 0) return kScales;
+  const unsigned __int128 q = w / ((unsigned __int128)total * 16u);
+  return q > (unsigned __int128)kScales ? kScales : (int32_t)q;
+}
+
+// Charts surely folded row by row at candidate k (Sec. 4.4): the tail only
+// takes charts no taller than the first chart of its first row, which is
+// shorter than t_opt H, so every chart with 1000 ceil(Hq k / 2^18) >=
+// t_opt H is placed before it.  hq_sorted is the atlas's sorted Hq
+// (non-increasing); returns how many such charts lead it (n when the tail
+// cannot apply).
+__host__ __device__ __forceinline__ int head_prefix(const int32_t *hq_sorted, int n, int64_t k, int topt, int H,
+                                                    bool hybrid) {
+  if (!hybrid) return n;
+  int lo = 0, hi = n;  // first index whose chart is short enough for the tail
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    const int64_t h = ((int64_t)hq_sorted[mid] * k + kFix - 1) >> 18;
+    if (1000 * h >= (int64_t)topt * H) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
 }
 
 // OBB angle table (App. A: 8 rotations evenly spaced in [0, 7*pi/16]):

@@ -1,0 +1,268 @@
+// The prefix-sum tail of Sec. 4.4 between its two row-loop passes.
+//
+// When a wave's last chunk is done, every (atlas, candidate S) task that
+// switched to the tail has folded its remaining charts at S: the prefix of
+// the offsets cut modulo W' into rows, recorded in the tasks' place records
+// (tail row per chart, row length at each row's first chart).  Those rows
+// may overflow W'.  The kernels here choose the intermediate scale k' at
+// which every row, re-laid from its near end with the charts drawn at k',
+// fits W' (rounds of 15 trial scales, the first round S - 14 .. S, later
+// rounds splitting the remaining interval in 16), then redraw the tail
+// charts at k' into the task's own envelope region (at k' <= S a chart's
+// padded sizes are no larger than at S, so it fits the place it had) and
+// compact them; the row loop's push pass then drops the rows onto the
+// frontline.
+//
+//   tail_plan     the tail tasks of the wave, their search state;
+//   tail_trial    a warp per (task, row, trial scale): the row's extent at
+//                 that scale, its compacting distances drawn on the fly
+//                 (warp_pair_reach), against W';
+//   tail_pick     a thread per task: the round's outcome (the largest trial
+//                 that fits, the next interval), k' after the last round;
+//   tail_raster   a warp per (task, tail chart): its envelope at k';
+//   tail_compact  a group of 16 lanes per (task, tail pair): distances and
+//                 interlock flags at k'.
+#include "raster_dev.cuh"
+
+namespace tabi {
+namespace {
+
+constexpr int kTailThreads = 256;
+constexpr int kTailWarps = kTailThreads / 32;
+
+// The parked state of a task (its row-loop slot in the wave).
+__device__ __forceinline__ int32_t *task_state(const Pack &p, int at, int j, int wave) {
+  const int64_t slot = (int64_t)at * p.F + (wave_range(p.jtop[at], wave, p.F).hi - j);
+  return p.ctl_save + slot * kCtlSave;
+}
+
+// Trial scale i (0..14) of a round: lo + floor((i + 1)(hi - lo) / 16).
+__device__ __forceinline__ int32_t trial_scale(int32_t lo, int32_t hi, int i) {
+  return lo + (int32_t)(((int64_t)(i + 1) * (hi - lo)) / 16);
+}
+
+__global__ void __launch_bounds__(1024) tail_plan_kernel(const Pack *__restrict__ pp) {
+  __shared__ int32_t count;
+  const Pack &p = *pp;
+  const int wave = *(volatile const int32_t *)p.cur_wave;
+  if (threadIdx.x == 0) count = 0;
+  __syncthreads();
+  const int64_t items = (int64_t)p.A * p.F;
+  for (int64_t it = threadIdx.x; it < items; it += blockDim.x) {
+    const int at = (int)(it / p.F);
+    const WaveRange wr = wave_range(p.jtop[at], wave, p.F);
+    const int j = wr.hi - (int)(it % p.F);
+    if (j < wr.lo || p.tstate[at * kScales + j] != kTaskTailSearch) continue;
+    int32_t *cs = task_state(p, at, j, wave);
+    const int32_t S = 16 * (j + 1);
+    cs[kCsLo] = S - 15;  // the first round tries S - 14 .. S
+    cs[kCsHi] = S + 1;
+    cs[kCsMask] = 0;
+    cs[kCsRound] = 0;
+    cs[kCsKt] = 0;
+    p.ttask[atomicAdd(&count, 1)] = make_int4(at, j, 0, cs[kCsC0]);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    *p.tcount = count;
+    p.counter[wave * kChunkSlots + p.Q] = 0;  // the push pass's task counter
+  }
+}
+
+// Whether the tail row starting at sorted chart s0 (len charts) fits W' when
+// laid from its near end at scale k: Algorithm 4's recurrence x_{t+1} = x_t
+// + w'_t - d_t, with compaction never left of the right edge of chart t-1,
+// the distances drawn on the fly.  a[0], a[1]: the warp's two row-constant
+// buffers (chart t and chart t + 1).
+__device__ bool row_fits(const Pack &p, int s0, int len, int64_t k, int Wp, rmath::AxisK *a) {
+  const bool hc = (p.flags & TABI_F_HC) != 0;
+  const int g = p.g;
+  int64_t x = 0, xprev = 0, wprev = 0, ext = 0;
+  int cur = 0;
+  if (hc) setup_at_k(p, p.shape[s0], k, nullptr, &a[0]);
+  for (int t = 0; t < len; ++t) {
+    const int s = s0 + t;
+    const int64_t w = ((p.wq[s] * k + kFix - 1) >> 18) + 2 * g;
+    ext = ext > x + w ? ext : x + w;
+    if (ext > Wp) return false;
+    if (t + 1 == len) break;
+    int64_t nx = x + w;
+    if (hc) {
+      setup_at_k(p, p.shape[s + 1], k, nullptr, &a[cur ^ 1]);
+      const int32_t M = warp_pair_reach(a[cur], a[cur ^ 1], g);
+      const int64_t d = w - M > 0 ? w - M : 0;
+      nx = x + w - d;
+      if (t >= 1 && nx < xprev + wprev) nx = xprev + wprev;
+      __syncwarp();  // a[cur] is redrawn for the chart after next
+      cur ^= 1;
+    }
+    xprev = x;
+    wprev = w;
+    x = nx;
+  }
+  return true;
+}
+
+__global__ void __launch_bounds__(kTailThreads) tail_trial_kernel(const Pack *__restrict__ pp) {
+  __shared__ rmath::AxisK axk[kTailWarps][2];
+  const Pack &p = *pp;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int64_t gw = (int64_t)blockIdx.x * kTailWarps + wib, nw = (int64_t)gridDim.x * kTailWarps;
+  const int wave = *(volatile const int32_t *)p.cur_wave;
+  const int ntask = *p.tcount;
+  for (int ti = 0; ti < ntask; ++ti) {
+    const int4 tt = p.ttask[ti];
+    const int at = tt.x, j = tt.y, c0 = tt.w;
+    if (p.tstate[at * kScales + j] != kTaskTailSearch) continue;
+    const int32_t *cs = task_state(p, at, j, wave);
+    const int32_t lo = cs[kCsLo], hi = cs[kCsHi];
+    if (hi <= lo + 1) continue;  // searched
+    const AtlasDesc &ad = p.atl[at];
+    const int cb = ad.cb, n = ad.n, Wp = ad.W + 2 * p.g;
+    const int4 *place = p.place + (int64_t)j * p.N + cb;
+    const int64_t items = (int64_t)(n - c0) * 15;
+    for (int64_t it = gw; it < items; it += nw) {
+      const int s = c0 + (int)(it / 15), i = (int)(it % 15);
+      const int32_t w = place[s].w;
+      if (!(w & kTailFirst)) continue;  // rows are tried from their first chart
+      const int32_t k = trial_scale(lo, hi, i);
+      if (k <= lo || k >= hi || (i > 0 && k == trial_scale(lo, hi, i - 1))) continue;
+      if (!row_fits(p, cb + s, w & ~kTailFirst, k, Wp, axk[wib]) && lane == 0)
+        atomicOr((unsigned *)(cs + kCsMask), 1u << i);
+    }
+  }
+}
+
+// One round's outcome per task (a thread each): the largest trial scale
+// that fit becomes lo and the smallest tried above it hi; if none of the
+// first round's fit, the search goes on over [1, S - 15].  After the last
+// round k' = lo: the task waits for its push (or fails if lo = 0).
+__global__ void tail_pick_kernel(const Pack *__restrict__ pp, int round) {
+  const Pack &p = *pp;
+  const int wave = *(volatile const int32_t *)p.cur_wave;
+  const int ntask = *p.tcount;
+  for (int ti = blockIdx.x * blockDim.x + threadIdx.x; ti < ntask; ti += gridDim.x * blockDim.x) {
+    const int4 tt = p.ttask[ti];
+    const int at = tt.x, j = tt.y;
+    if (p.tstate[at * kScales + j] != kTaskTailSearch) continue;
+    int32_t *cs = task_state(p, at, j, wave);
+    int32_t lo = cs[kCsLo], hi = cs[kCsHi];
+    const bool moot = !(p.flags & TABI_F_EVAL_ALL) && *(volatile int32_t *)(p.found + at) > j;
+    if (hi > lo + 1 && !moot) {
+      const uint32_t mask = (uint32_t)cs[kCsMask];
+      int32_t best = -1, tried[15];
+      for (int i = 0; i < 15; ++i) {
+        tried[i] = trial_scale(lo, hi, i);
+        int f = i;  // a repeated scale was tried at its first occurrence
+        while (f > 0 && tried[f - 1] == tried[i]) --f;
+        if (tried[i] > lo && tried[i] < hi && !((mask >> f) & 1u) && tried[i] > best) best = tried[i];
+      }
+      if (best < 0 && round == 0) {
+        lo = 0;
+        hi = 16 * (j + 1) - 14;
+      } else {
+        if (best < 0) best = lo;
+        int32_t nhi = hi;
+        for (int i = 0; i < 15; ++i)
+          if (tried[i] > best && tried[i] < nhi) nhi = tried[i];
+        lo = best;
+        hi = nhi;
+      }
+      cs[kCsLo] = lo;
+      cs[kCsHi] = hi;
+      cs[kCsMask] = 0;
+      cs[kCsRound] = round + 1;
+    }
+    if (moot || hi <= lo + 1 || round + 1 >= kTailRounds) {
+      ScaleOut &so = p.scale_out[at * kScales + j];
+      if (!moot && lo > 0) {
+        cs[kCsKt] = lo;
+        p.tstate[at * kScales + j] = kTaskTailPush;
+      } else {  // no scale fits every row (or the candidate can no longer win)
+        so.success = 0;
+        so.rows = cs[kCsHeadRows];
+        so.placed = cs[kCsC0];
+        so.score = cs[kCsCommitted];
+        so.knee_rows = cs[8];
+        so.knees = cs[9];
+        so.tail_rows = 0;  // none pushed
+        so.tail_k = 0;
+        so.tail_start = cs[kCsC0];
+        so.evaluated = moot ? 2 : 1;
+        p.tstate[at * kScales + j] = kTaskDone;
+      }
+    }
+  }
+}
+
+// The tail charts at k', in the place their envelopes had at S: columns
+// (and their owners), rows, and the padded sizes and deepest bottom.
+__global__ void __launch_bounds__(kTailThreads) tail_raster_kernel(const Pack *__restrict__ pp) {
+  __shared__ rmath::AxisK axk[kTailWarps][2];
+  const Pack &p = *pp;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int64_t gw = (int64_t)blockIdx.x * kTailWarps + wib, nw = (int64_t)gridDim.x * kTailWarps;
+  const int wave = *(volatile const int32_t *)p.cur_wave;
+  const int ntask = *p.tcount;
+  const int g = p.g;
+  for (int ti = 0; ti < ntask; ++ti) {
+    const int4 tt = p.ttask[ti];
+    const int at = tt.x, j = tt.y, c0 = tt.w;
+    if (p.tstate[at * kScales + j] != kTaskTailPush) continue;
+    const int32_t kt = task_state(p, at, j, wave)[kCsKt];
+    const AtlasDesc &ad = p.atl[at];
+    const int cb = ad.cb, n = ad.n;
+    const int64_t cbase = p.abase[region(at, j, 0)], rbase = p.abase[region(at, j, 1)];
+    for (int64_t s = c0 + gw; s < n; s += nw) {
+      const int64_t js = (int64_t)j * p.N + cb + s;
+      rmath::AxisK &a0 = axk[wib][0], &a1 = axk[wib][1];
+      setup_at_k(p, p.shape[cb + s], kt, &a0, &a1);
+      const int32_t cstart = p.colstart[js];
+      const int32_t wold = p.meta[js * 4];  // padded width at S: the words this chart owns
+      __syncwarp();
+      const int32_t maxbot = warp_axis(a0, g, p.colpool + cbase + cstart);
+      int32_t *own = p.colown + cbase + cstart;
+      // the words past the narrower envelope belong to no chart (-1): the row
+      // loop's commit skips them
+      for (int c = lane; c < wold; c += 32) own[c] = c < a0.len + 2 * g ? (int32_t)s : -1;
+      warp_axis(a1, g, p.pool + rbase + p.rowstart[js]);
+      if (lane == 0)
+        *reinterpret_cast<int4 *>(p.meta + js * 4) = make_int4(a0.len + 2 * g, a1.len + 2 * g, cstart, maxbot);
+      __syncwarp();
+    }
+  }
+}
+
+constexpr int kCompactGroup = 16;
+
+__global__ void __launch_bounds__(256) tail_compact_kernel(const Pack *__restrict__ pp) {
+  const Pack &p = *pp;
+  constexpr int G = kCompactGroup;
+  const int lane = threadIdx.x & (G - 1);
+  const unsigned gm = group_mask<G>();
+  const int64_t gg = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
+  const int64_t ng = ((int64_t)gridDim.x * blockDim.x) / G;
+  const int ntask = *p.tcount;
+  for (int ti = 0; ti < ntask; ++ti) {
+    const int4 tt = p.ttask[ti];
+    const int at = tt.x, j = tt.y, c0 = tt.w;
+    if (p.tstate[at * kScales + j] != kTaskTailPush) continue;
+    const int cb = p.atl[at].cb, n = p.atl[at].n;
+    for (int64_t s = c0 + gg; s + 1 < n; s += ng) compact_pair<G>(p, at, j, cb + (int)s, lane, gm);
+  }
+}
+
+}  // namespace
+
+void launch_tail(const Pack *dp, const Launch &L, int F, cudaStream_t st) {
+  (void)F;
+  tail_plan_kernel<<<1, 1024, 0, st>>>(dp);
+  for (int r = 0; r < kTailRounds; ++r) {
+    tail_trial_kernel<<<L.sms * 4, kTailThreads, 0, st>>>(dp);
+    tail_pick_kernel<<<L.sms, 128, 0, st>>>(dp, r);
+  }
+  tail_raster_kernel<<<L.sms * 3, kTailThreads, 0, st>>>(dp);
+  tail_compact_kernel<<<L.sms * 8, 256, 0, st>>>(dp);
+}
+
+}  // namespace tabi

@@ -65,14 +65,13 @@ class ServerStats(ctypes.Structure):
 
 
 PLACEMENT_DTYPE = np.dtype([("x", "<i4"), ("y", "<i4"), ("rot90", "u1"), ("flip_x", "u1"),
-                            ("flip_y", "u1"), ("mirror", "u1")])
+                            ("flip_y", "u1"), ("mirror", "u1"), ("k", "<i4")])
 
 CHART_INFO_DTYPE = np.dtype([
     ("orig", "<i4"), ("Wq", "<i4"), ("Hq", "<i4"), ("rot90", "<i4"), ("flip_y", "<i4"),
     ("flip_x", "<i4"), ("obb_m", "<i4"), ("valid", "<i4"),
     ("u0", "<i8"), ("u1", "<i8"), ("v0", "<i8"), ("v1", "<i8"),
     ("ylo", "<i4", 10), ("yhi", "<i4", 10), ("xlo", "<i4", 10), ("xhi", "<i4", 10),
-    ("tlo", "<i4", 10), ("bhi", "<i4", 10), ("llo", "<i4", 10), ("rhi", "<i4", 10),
     ("area_top", "<i8"), ("area_bot", "<i8"), ("area_left", "<i8"), ("area_right", "<i8"),
     ("area_bl2", "<i8"), ("area_br2", "<i8")])
 
@@ -172,15 +171,17 @@ def waves(fanout: int) -> int:
     return (N_SCALES + fanout - 1) // fanout
 
 
-def kernels_per_pack(fanout: int, chunks: int = 4, waves_run: int | None = None) -> int:
+def kernels_per_pack(fanout: int, chunks: int = 4, waves_run: int | None = None, tail: bool = False) -> int:
     """Kernels one (batched) pack launches: init, prep, sort + gather,
     layout + bases; per wave, for each chart chunk plan + fill, raster,
-    compaction, row loop, then the wave's end; selection.  The graph runs
-    waves only while some atlas still searches (`waves_run` of them: the
-    most any atlas of the batch needs, at least one); direct launches
-    (stage timing) run every wave."""
+    compaction, row loop, then (if some atlas may take the prefix-sum tail)
+    the tail's plan, four rounds of trial and pick, redraw, compaction and
+    push pass, then the wave's end; selection.  The graph runs waves only
+    while some atlas still searches (`waves_run` of them: the most any
+    atlas of the batch needs, at least one); direct launches (stage timing)
+    run every wave."""
     w = waves(fanout) if waves_run is None else max(1, waves_run)
-    return 7 + (5 * chunks + 1) * w
+    return 7 + (5 * chunks + 1 + (12 if tail else 0)) * w
 
 
 @dataclass
@@ -244,7 +245,7 @@ class Context:
 
     def pack_device(self, n, nv, W, H, offs_t, verts_t, out_t, params=None, stream=None):
         """tabi_pack_device: offs_t (int32/uint32 view), verts_t (int32) and
-        out_t (uint8, 12*n bytes) are CUDA tensors."""
+        out_t (uint8, PLACEMENT_DTYPE.itemsize * n bytes) are CUDA tensors."""
         params = params or params_default()
         k = ctypes.c_int32(0)
         st = self.lib.tabi_pack_device(self.h, ctypes.byref(params), W, H, n,
@@ -373,10 +374,15 @@ class Context:
         return d, (fl & 1).astype(np.uint8), ((fl >> 1) & 1).astype(np.uint8)
 
     def scale_result(self, scale: int, n: int, atlas: int = 0):
+        """(header int32[12], place int32[n, 4]) of candidate `scale`: success,
+        rows, knee rows, knees, max frontline, placed, evaluated, tail rows,
+        tail scale, first tail chart, then the area-weighted scale sum as
+        header[12] (a Python int)."""
         raw = self._inspect(INSPECT_SCALE, scale, atlas)
-        hdr = raw[:32].view(np.int32)
-        place = raw[32:32 + 16 * n].view(np.int32).reshape(n, 4)
-        return hdr, place
+        hdr = raw[:48].view(np.int32).copy()
+        lo, hi = (int(v) for v in raw[48:64].view(np.uint64))
+        place = raw[64:64 + 16 * n].view(np.int32).reshape(n, 4)
+        return [int(v) for v in hdr] + [(hi << 64) | lo], place
 
 
 def server_config_default(**kw) -> ServerConfig:

@@ -51,7 +51,7 @@ def compare(cs, res, op):
     assert res.k == o.k, cs.name
     if o.status == 0:
         pl = res.place
-        for f, col in (("x", 0), ("y", 1), ("rot90", 2), ("flip_x", 3), ("flip_y", 4), ("mirror", 5)):
+        for f, col in (("x", 0), ("y", 1), ("rot90", 2), ("flip_x", 3), ("flip_y", 4), ("mirror", 5), ("k", 10)):
             assert np.array_equal(pl[f], o.place[:, col]), (cs.name, f)
 
 
@@ -318,7 +318,7 @@ def test_batch_device_entry_point(ctx):
     for i, cs in enumerate(sets):
         offs = torch.from_numpy(cs.offsets.view(np.int32).copy()).to(dev)
         verts = torch.from_numpy(cs.verts.copy()).to(dev)
-        out = torch.zeros(12 * cs.n, dtype=torch.uint8, device=dev)
+        out = torch.zeros(tabi.PLACEMENT_DTYPE.itemsize * cs.n, dtype=torch.uint8, device=dev)
         keep.append((offs, verts, out))
         reqs[i] = tabi.Request(cs.atlas_w, cs.atlas_h, cs.n, cs.nv, offs.data_ptr(), verts.data_ptr(),
                                out.data_ptr(), 0, 0)
@@ -336,7 +336,7 @@ def _device_requests(sets):
     for i, cs in enumerate(sets):
         offs = torch.from_numpy(cs.offsets.view(np.int32).copy()).to(dev)
         verts = torch.from_numpy(cs.verts.copy()).to(dev)
-        out = torch.zeros(12 * cs.n, dtype=torch.uint8, device=dev)
+        out = torch.zeros(tabi.PLACEMENT_DTYPE.itemsize * cs.n, dtype=torch.uint8, device=dev)
         keep.append((offs, verts, out))
         reqs[i] = tabi.Request(cs.atlas_w, cs.atlas_h, cs.n, cs.nv, offs.data_ptr(), verts.data_ptr(),
                                out.data_ptr(), 0, 0)
@@ -428,15 +428,15 @@ def test_pinned_host_buffers_match(ctx):
         if pinned:
             ob = torch.zeros(4 * (cs.n + 1) + 16, dtype=torch.uint8).pin_memory()
             vb = torch.zeros(8 * cs.nv + 16, dtype=torch.uint8).pin_memory()
-            out_b = torch.zeros(12 * cs.n + 16, dtype=torch.uint8).pin_memory()
+            out_b = torch.zeros(tabi.PLACEMENT_DTYPE.itemsize * cs.n + 16, dtype=torch.uint8).pin_memory()
             ob.numpy()[sh:sh + 4 * (cs.n + 1)] = cs.offsets.view(np.uint8)
             vb.numpy()[sh:sh + 8 * cs.nv] = cs.verts.view(np.uint8)
             hold.append((ob, vb, out_b))
             optr, vptr, outp = ob.data_ptr() + sh, vb.data_ptr() + sh, out_b.data_ptr() + sh
-            outs.append(out_b.numpy()[sh:sh + 12 * cs.n])
+            outs.append(out_b.numpy()[sh:sh + tabi.PLACEMENT_DTYPE.itemsize * cs.n])
         else:
             o, v = np.ascontiguousarray(cs.offsets, np.uint32), np.ascontiguousarray(cs.verts, np.int32)
-            out_np = np.zeros(12 * cs.n, np.uint8)
+            out_np = np.zeros(tabi.PLACEMENT_DTYPE.itemsize * cs.n, np.uint8)
             hold.append((o, v, out_np))
             optr, vptr, outp = o.ctypes.data, v.ctypes.data, out_np.ctypes.data
             outs.append(out_np)

@@ -66,8 +66,7 @@ def _check_prep(ctx, cs, op):
                    ("area_left", "ALEFT"), ("area_right", "ARIGHT"), ("area_bl2", "ABL2"),
                    ("area_br2", "ABR2")):
         assert np.array_equal(info[f].astype(np.int64), rec[:, R[col]]), f
-    for f, col in (("ylo", "YLO"), ("yhi", "YHI"), ("xlo", "XLO"), ("xhi", "XHI"),
-                   ("tlo", "TLO"), ("bhi", "BHI"), ("llo", "LLO"), ("rhi", "RHI")):
+    for f, col in (("ylo", "YLO"), ("yhi", "YHI"), ("xlo", "XLO"), ("xhi", "XHI")):
         assert np.array_equal(info[f].astype(np.int64), rec[:, R[col] + slot]), f
     perm = ctx.perm()
     assert np.array_equal(perm, oracle.sort(rec))
@@ -104,9 +103,18 @@ def test_steps_parity(ctx, name, topt):
     rec, perm = _check_prep(ctx, cs, op)
     for j in range(0, 64, 1 if cs.n <= 300 else 7):
         k = 16 * (j + 1)
+        hdr, place = ctx.scale_result(j, cs.n)
+        ok, opl, ost = oracle.pack_scale(rec, perm, cs.atlas_w, cs.atlas_h, k, op)
+        assert hdr[0] == int(ok), j
+        assert list(hdr[1:6]) == [ost[0], ost[1], ost[2], ost[3], ost[4]], j
+        # Sec. 4.4: rows pushed by the tail, its scale k' and first chart
+        assert [hdr[7], hdr[8], hdr[9]] == [ost[5], ost[6], ost[7]], j
+        # the tail's charts are drawn (and compacted) at k' once it is found
+        kt, c0 = int(ost[6]), int(ost[7])
+        ks = [kt if (kt and s >= c0) else k for s in range(cs.n)]
         env = ctx.envelopes(j, cs.n)
         for s in range(cs.n):
-            e = oracle.envelope_padded(rec[perm[s]], k, op)
+            e = oracle.envelope_padded(rec[perm[s]], ks[s], op)
             wp, hp, top, bot, left, right, mb = env[s]
             assert (wp, hp) == (e.w, e.h), (j, s)
             assert np.array_equal(top, e.top) and np.array_equal(bot, e.bot), (j, s)
@@ -114,13 +122,13 @@ def test_steps_parity(ctx, name, topt):
             assert mb == e.bot.max()
         d, ca, cb = ctx.pairs(j, cs.n)
         od, oca, ocb, owp, ohp = oracle.scale_pairs(rec, perm, k, op)
-        assert np.array_equal(d[:-1], od[:-1]), j
-        assert np.array_equal(ca[:-1], oca[:-1]) and np.array_equal(cb[:-1], ocb[:-1]), j
-        hdr, place = ctx.scale_result(j, cs.n)
-        ok, opl, ost = oracle.pack_scale(rec, perm, cs.atlas_w, cs.atlas_h, k, op)
-        assert hdr[0] == int(ok), j
-        assert list(hdr[1:6]) == [ost[0], ost[1], ost[2], ost[3], ost[4]], j
-        assert hdr[7] == ost[5], j  # rows folded by the prefix sum (Sec. 4.4)
+        lim = c0 if kt else cs.n - 1  # pairs at k; with a tail at k', those from the first tail chart on
+        assert np.array_equal(d[:lim], od[:lim]), j
+        assert np.array_equal(ca[:lim], oca[:lim]) and np.array_equal(cb[:lim], ocb[:lim]), j
+        if kt:
+            td, tca, tcb, _, _ = oracle.scale_pairs(rec, perm, kt, op)
+            assert np.array_equal(d[c0:-1], td[c0:-1]), j
+            assert np.array_equal(ca[c0:-1], tca[c0:-1]) and np.array_equal(cb[c0:-1], tcb[c0:-1]), j
         placed = int(ost[4])
         bits = opl[:placed, 2] | (opl[:placed, 4] << 1) | (opl[:placed, 5] << 2)
         assert np.array_equal(place[:placed, 0], opl[:placed, 0]), j
@@ -141,6 +149,7 @@ def _compare_pack(cs, res, op):
         assert np.array_equal(pl["flip_x"], o.place[:, 3])
         assert np.array_equal(pl["flip_y"], o.place[:, 4])
         assert np.array_equal(pl["mirror"], o.place[:, 5])
+        assert np.array_equal(pl["k"], o.place[:, 10])  # each chart's scale (the tail's k')
     return o
 
 
@@ -317,7 +326,7 @@ def test_device_entry_point_matches_host(ctx):
     dev = torch.device("cuda:0")
     offs = torch.from_numpy(cs.offsets.view(np.int32).copy()).to(dev)
     verts = torch.from_numpy(cs.verts.copy()).to(dev)
-    out = torch.zeros(12 * cs.n, dtype=torch.uint8, device=dev)
+    out = torch.zeros(tabi.PLACEMENT_DTYPE.itemsize * cs.n, dtype=torch.uint8, device=dev)
     st, k = ctx.pack_device(cs.n, cs.nv, cs.atlas_w, cs.atlas_h, offs, verts, out, p)
     torch.cuda.synchronize()
     assert st == 0 and k == host.k

@@ -3,7 +3,8 @@
 multiply-high division by the OBB table's divisors, the estimated 64-bit
 floor division, the single-precision division by the OBB norms and the OBB
 corner runs (started from one step's quotient, then advanced per
-candidate) equal exact floor division.  The GPU parity tests check the
+candidate) and the corner quantities at any scale equal exact floor
+division.  The GPU parity tests check the
 envelopes they produce against the oracle."""
 from __future__ import annotations
 
@@ -100,6 +101,26 @@ int main() {
         ++bad;
       }
       corner_advance(cq);
+    }
+  }
+  // the same quantities at any scale k (the prefix-sum tail's trial and
+  // intermediate scales): one division, floor(k num / D), and for the
+  // positions whether it was exact
+  for (int t = 0; t < 20000; ++t) {
+    int64_t C, S;
+    do { C = (int64_t)(rng() % 16385); S = (int64_t)(rng() % 16385); } while (C * C + S * S <= (1ll << 23));
+    auto r36 = [&]() { return (int64_t)(rng() % (1ull << 37)) - (1ll << 36); };
+    const int64_t u0 = r36(), u1 = r36(), v0 = r36(), v1 = r36();
+    const int item = (int)(rng() % 8);
+    const int64_t k = 1 + (int64_t)(rng() % 1024);
+    const int64_t kn = k * corner_num(item, C, S, u0, u1, v0, v1), D = corner_den(item, C, S);
+    CornerQ cq;
+    corner_at(cq, item, k, C, S, u0, u1, v0, v1);
+    const int64_t q = floor_div(kn, D);
+    ++checked;
+    if (cq.q != q || ((item & 3) >= 2 && (cq.r != 0) != (kn - q * D != 0))) {
+      if (bad < 5) std::printf("corner_at item %d k %lld got %lld want %lld\n", item, (long long)k, (long long)cq.q, (long long)q);
+      ++bad;
     }
   }
   std::printf("checked %ld bad %ld\n", checked, bad);
