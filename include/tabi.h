@@ -131,12 +131,13 @@ typedef struct tabi_params {
                                 chart s-1's right edge) with rows cut
                                 modulo W + 2g, so a row's last chart may
                                 overflow; then drawn at one intermediate
-                                scale k' <= k at which every such row, laid
-                                from its near end, fits (searched in rounds
-                                of 15 trial scales, the first k-14 .. k; the
-                                candidate fails if none fits), laid
-                                left-to-right, right-to-left, right-to-left
-                                in turn and dropped onto the skyline.  The
+                                scale k': the largest of k-14 .. k at which
+                                every such row, laid from its near end, fits
+                                (if none does, the remaining charts are
+                                folded row by row as before the switch),
+                                laid left-to-right, right-to-left,
+                                right-to-left in turn and dropped onto the
+                                skyline.  The
                                 pack's scale is then the successful
                                 candidate with the largest area-weighted
                                 mean scale of its charts (ties: the larger

@@ -706,17 +706,16 @@ static int64_t lay_row(int m, const Env *env, const int32_t *dnext, int hc, int6
 /*     belongs to tail row floor(P_s / W'), so a row's last chart may        */
 /*     overflow the width;                                                   */
 /*  2. intermediate downscaling: READING (on the k/1024 grid, integer): the  */
-/*     tail charts take one scale k' <= S at which every tail row, re-laid   */
-/*     from its near end with the envelopes, widths and compacting distances */
-/*     at k', fits the padded width W'.  k' is searched in rounds of 15      */
-/*     trial scales: the first round tries S - 14 .. S; if one fits, lo is   */
-/*     the largest that does and hi the smallest tried above it (S + 1 if    */
-/*     none), else lo = 0 and hi = S - 14.  Each later round, while hi > lo  */
-/*     + 1, tries lo + floor(i (hi - lo) / 16), i = 1..15, and moves lo to   */
-/*     the largest of them that fits and hi to the smallest tried above the  */
-/*     new lo; three such rounds always end with hi = lo + 1.  k' = lo, and  */
-/*     the candidate fails if lo = 0.  Where "every row fits" is monotone    */
-/*     in the scale, this is the largest k' <= S that fits;                  */
+/*     tail charts take the largest scale k' in S - 14 .. S at which every  */
+/*     tail row, re-laid from its near end with the envelopes, widths and    */
+/*     compacting distances at k', fits the padded width W'.  The paper     */
+/*     downscales continuously and finds the effect negligible for charts   */
+/*     this small; here widths are whole texels with a fixed 2g gutter, so a */
+/*     row of one- or two-texel charts can need a large downscale, or none  */
+/*     fits.  The tail is therefore taken only when the downscale stays      */
+/*     within one step of the candidate grid (15/1024); otherwise nothing   */
+/*     is committed and the remaining charts are folded row by row as       */
+/*     before the switch (t_opt = 0 for them);                              */
 /*  3. the rows, drawn at k', go into the atlas in FastAtlas's fixed         */
 /*     alternation (READING: one left-to-right row, then two right-to-left   */
 /*     rows, starting with the first tail row) and are pushed up onto the    */
@@ -724,9 +723,10 @@ static int64_t lay_row(int m, const Env *env, const int32_t *dnext, int hc, int6
 /*     right-to-left row, Algorithm 2 when compacting).                      */
 /* The tail charts' final scale is k', the others' S; the search then keeps */
 /* the candidate whose area-weighted mean final scale is largest.           */
-/* Returns 1 if every row fits below the padded height, else 0; the tail    */
-/* placements go to place (sorted positions), the rows it committed and its */
-/* scale to stats.                                                           */
+/* Returns 1 if every row fits below the padded height, 0 if one does not,  */
+/* -1 if no tail scale fits (nothing placed: the rows continue one by one); */
+/* the tail placements go to place (sorted positions), the rows it          */
+/* committed and its scale to stats.                                         */
 /* Whether every tail row, re-laid at scale k2, fits the padded width. */
 static int tail_rows_fit(int m, int nr, const int32_t *rstart, const int64_t *rec, const int32_t *perm,
                          int32_t k2, const int32_t *params, int hc, int64_t Wp, int64_t *x) {
@@ -765,36 +765,21 @@ static int tail_pack(int n, int c0, int row, const Env *env, const int32_t *dnex
     if (t == 0 || P[t] / Wp != P[t - 1] / Wp) rstart[nr++] = t;
   rstart[nr] = m;
 
-  /* 2. intermediate scale k': rounds of 15 trial scales (round 0: S-14..S) */
-  int32_t lo = S - 15, hi = S + 1;
-  for (int round = 0; round < 4 && hi > lo + 1; ++round) {
-    int32_t tried[15], best = -1;
-    for (int i = 0; i < 15; ++i) {
-      tried[i] = lo + (int32_t)(((int64_t)(i + 1) * (hi - lo)) / 16);
-      if (tried[i] > lo && tried[i] < hi && tried[i] > best &&
-          tail_rows_fit(m, nr, rstart, rec, perm + c0, tried[i], params, hc, Wp, x))
-        best = tried[i];
-    }
-    if (best < 0) { /* none fits */
-      if (round == 0) { lo = 0; hi = S - 14; continue; }
-      best = lo;
-    }
-    int32_t nhi = hi;
-    for (int i = 0; i < 15; ++i)
-      if (tried[i] > best && tried[i] < nhi) nhi = tried[i];
-    lo = best;
-    hi = nhi;
+  /* 2. intermediate scale k': the largest of S - 14 .. S at which every */
+  /*    row fits, else no tail                                            */
+  int32_t kt = 0;
+  for (int32_t k2 = S; k2 >= 1 && k2 >= S - 14 && !kt; --k2)
+    if (tail_rows_fit(m, nr, rstart, rec, perm + c0, k2, params, hc, Wp, x)) kt = k2;
+  if (!kt) {
+    free(P); free(rstart); free(x); free(y);
+    return -1;
   }
-  const int32_t kt = lo;
   stats[6] = kt;
   stats[7] = c0;
-  int ok = kt > 0;
   ScaleData sd;
-  if (kt) {
-    ok = !build_scale(m, rec, perm + c0, kt, params, &sd, 1);
-    for (int r = 0; r < nr && ok; ++r) lay_row(rstart[r + 1] - rstart[r], sd.env + rstart[r],
-                                               sd.dnext + rstart[r], hc, x + rstart[r]);
-  }
+  int ok = !build_scale(m, rec, perm + c0, kt, params, &sd, 1);
+  for (int r = 0; r < nr && ok; ++r)
+    lay_row(rstart[r + 1] - rstart[r], sd.env + rstart[r], sd.dnext + rstart[r], hc, x + rstart[r]);
 
   /* 3. the rows at k', FastAtlas's directions, pushed onto the frontline */
   for (int r = 0; r < nr && ok; ++r) {
@@ -832,7 +817,7 @@ static int tail_pack(int n, int c0, int row, const Env *env, const int32_t *dnex
     stats[4] = c0 + b;
     stats[5] = r + 1;
   }
-  if (kt) free_scale(&sd);
+  free_scale(&sd);
   free(P); free(rstart); free(x); free(y);
   return ok;
 }
@@ -866,7 +851,7 @@ static int pack_scale_env(int n, const Env *env, const int64_t *hq, const int32_
   stats[7] = n;
   /* Sec. 4.4: the hybrid applies to atlases of more than hybrid_min charts */
   /* (the paper: t_opt = 1 % above 10,000 charts, none below).             */
-  const int hybrid = params[P_TOPT] > 0 && n > params[P_HYBRID_MIN];
+  int hybrid = params[P_TOPT] > 0 && n > params[P_HYBRID_MIN];
   int tail_ok = -1; /* -1: no tail */
 
   int rowStart = 0, overflow = 0, row = 0;
@@ -882,9 +867,12 @@ static int pack_scale_env(int n, const Env *env, const int64_t *hq, const int32_
       stats[0] = row;
       tail_ok = tail_pack(n, rowStart, row, env, dnext, rec, perm, S, params, Wp, Hp, front, place, stats,
                           &committed);
-      row = stats[0];
-      rowStart = stats[4];
-      break;
+      if (tail_ok >= 0) {
+        row = stats[0];
+        rowStart = stats[4];
+        break;
+      }
+      hybrid = 0; /* no tail scale within one grid step: the rows go on one by one */
     }
     if (kd.valid) update_knee(&kd, front);
     int nfold = kd.valid ? 2 : 1;

@@ -55,11 +55,13 @@
 // (its charts' place records carry the tail row and, at its first chart,
 // the row length) and nothing is pushed.  Once every chart is folded the
 // task parks (state kTaskTailSearch) and the tail kernels search the
-// intermediate scale k', redraw the tail charts at k' and compact them.
-// Then the push pass (q = Q, state kTaskTailPush): each recorded row is
-// laid from its near end by the same fold at k', in the fixed direction
-// pattern left-to-right, right-to-left, right-to-left, and phases D, E and
-// H push it as the one configuration of the row.
+// intermediate scale k' (within one grid step below the candidate), redraw
+// the tail charts at k' and compact them.  Then the push pass (q = Q, state
+// kTaskTailPush): each recorded row is laid from its near end by the same
+// fold at k', in the fixed direction pattern left-to-right, right-to-left,
+// right-to-left, and phases D, E and H push it as the one configuration of
+// the row.  If no k' fitted, the push pass instead folds the remaining
+// charts row by row from the switch, exactly as without a tail.
 #include "tabi_internal.cuh"
 
 namespace tabi {
@@ -79,7 +81,8 @@ struct Ctl {
   int32_t t_at, t_j, t_skip;
   int32_t front_sum;     // the committed frontline summed over the padded columns
   // prefix-sum tail (Sec. 4.4): mode (0 off, 1 folding at the candidate
-  // scale, 3 pushing at the tail scale), cut width, unwrapped prefix of the
+  // scale, 3 pushing at the tail scale, 4 abandoned: no tail scale within a
+  // grid step, rows one by one), cut width, unwrapped prefix of the
   // next row's first chart and of the chart before it (have_prev: one
   // exists) with that chart's width, tail rows folded or pushed, first tail
   // chart, rows before it, the tail scale, the pushed row's length
@@ -280,11 +283,11 @@ __global__ void __launch_bounds__(NT) rowloop_kernel(const Pack *__restrict__ pp
           ctl.row_start = csave[0]; ctl.row = csave[1]; ctl.committed = csave[2]; ctl.prev_ltr = csave[3];
           ctl.knee_valid = csave[4]; ctl.knee_ltr = csave[5]; ctl.knee_l = csave[6]; ctl.knee_r = csave[7];
           ctl.knee_rows = csave[8]; ctl.knees = csave[9];
-          ctl.tail = csave[kCsTail] & 3; ctl.tHave = (csave[kCsTail] >> 2) & 1; ctl.trows = csave[kCsTail] >> 3;
+          ctl.tail = csave[kCsTail] & 7; ctl.tHave = (csave[kCsTail] >> 3) & 1; ctl.trows = csave[kCsTail] >> 4;
           ctl.tL = csave[11]; ctl.tP = csave[12]; ctl.tPrev = csave[13]; ctl.tWprev = csave[14];
           ctl.c0 = csave[kCsC0]; ctl.head_rows = csave[kCsHeadRows]; ctl.kt = csave[kCsKt];
           if (q >= p.Q) {  // the push pass: the tail rows again from the first, at the tail scale
-            ctl.tail = 3;
+            ctl.tail = ctl.kt > 0 ? 3 : 4;  // 4: no tail scale fitted, the rows go on one by one
             ctl.row_start = ctl.c0;
             ctl.row = ctl.head_rows;
             ctl.trows = 0;
@@ -328,7 +331,7 @@ __global__ void __launch_bounds__(NT) rowloop_kernel(const Pack *__restrict__ pp
         if (ctl.tail == 3 && tid == 0) ctl.plen = place[row_start].w & ~kTailFirst;  // a recorded row
         __syncthreads();
         const int tmode = ctl.tail;
-        const bool tail = tmode != 0;
+        const bool tail = tmode == 1 || tmode == 3;
         // a folded tail row's start in the unwrapped prefix, and its cut width
         const int32_t tB = tmode == 1 ? (ctl.tP / ctl.tL) * ctl.tL : 0, tL = ctl.tL;
         const int32_t plen = ctl.plen;
@@ -814,7 +817,7 @@ __global__ void __launch_bounds__(NT) rowloop_kernel(const Pack *__restrict__ pp
           csave[0] = ctl.row_start; csave[1] = ctl.row; csave[2] = ctl.committed; csave[3] = ctl.prev_ltr;
           csave[4] = ctl.knee_valid; csave[5] = ctl.knee_ltr; csave[6] = ctl.knee_l; csave[7] = ctl.knee_r;
           csave[8] = ctl.knee_rows; csave[9] = ctl.knees;
-          csave[kCsTail] = ctl.tail | (ctl.tHave << 2) | (ctl.trows << 3);
+          csave[kCsTail] = ctl.tail | (ctl.tHave << 3) | (ctl.trows << 4);
           csave[11] = ctl.tL; csave[12] = ctl.tP; csave[13] = ctl.tPrev; csave[14] = ctl.tWprev;
           csave[kCsC0] = ctl.c0; csave[kCsHeadRows] = ctl.head_rows; csave[kCsTrows] = ctl.trows;
           csave[kCsCommitted] = ctl.committed;

@@ -45,8 +45,8 @@ struct ScaleOut {
 
 // Row-loop task state of an (atlas, candidate) per wave: 0 running (or not
 // begun), 1 finished, 2 prefix-sum tail folded at the candidate scale and
-// waiting for its intermediate scale, 3 intermediate scale found, tail rows
-// waiting to be pushed.
+// waiting for its intermediate scale, 3 searched: the tail rows wait to be
+// pushed at that scale (or, if none fitted, the rows to go on one by one).
 enum : int32_t { kTaskRun = 0, kTaskDone = 1, kTaskTailSearch = 2, kTaskTailPush = 3 };
 // A tail chart's place record between the fold and the push: (0, 0, tail
 // row, row length | kTailFirst) for the first chart of a row, (0, 0, tail
@@ -216,7 +216,7 @@ void launch_select(const Pack *dp, const Launch &L, cudaStream_t st);
 // folded their tail, the rounds of trial scales, the redraw and the
 // compaction at the chosen scale (the row loop pushes the rows after).
 void launch_tail(const Pack *dp, const Launch &L, int F, cudaStream_t st);
-constexpr int kTailRounds = 4;
+constexpr int kTailRounds = 1;  // trial scales k - 14 .. k (one candidate step), one launch
 size_t rowloop_smem_bytes(int W, int g);       // shared memory a row-loop CTA needs without the stage
 size_t rowloop_smem_wanted(int W, int g);      // ... with a stage of two atlas widths
 

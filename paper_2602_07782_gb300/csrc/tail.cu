@@ -4,21 +4,20 @@
 // switched to the tail has folded its remaining charts at S: the prefix of
 // the offsets cut modulo W' into rows, recorded in the tasks' place records
 // (tail row per chart, row length at each row's first chart).  Those rows
-// may overflow W'.  The kernels here choose the intermediate scale k' at
-// which every row, re-laid from its near end with the charts drawn at k',
-// fits W' (rounds of 15 trial scales, the first round S - 14 .. S, later
-// rounds splitting the remaining interval in 16), then redraw the tail
-// charts at k' into the task's own envelope region (at k' <= S a chart's
-// padded sizes are no larger than at S, so it fits the place it had) and
-// compact them; the row loop's push pass then drops the rows onto the
-// frontline.
+// may overflow W'.  The kernels here choose the intermediate scale k': the
+// largest of S - 14 .. S (one step of the candidate grid) at which every
+// row, re-laid from its near end with the charts drawn at k', fits W';
+// then redraw the tail charts at k' into the task's own envelope region (at
+// k' <= S a chart's padded sizes are no larger than at S, so it fits the
+// place it had) and compact them.  The row loop's second pass then drops
+// the rows onto the frontline -- or, where no such k' exists, folds the
+// remaining charts row by row as before the switch.
 //
-//   tail_plan     the tail tasks of the wave, their search state;
+//   tail_plan     the tail tasks of the wave;
 //   tail_trial    a warp per (task, row, trial scale): the row's extent at
 //                 that scale, its compacting distances drawn on the fly
 //                 (warp_pair_reach), against W';
-//   tail_pick     a thread per task: the round's outcome (the largest trial
-//                 that fits, the next interval), k' after the last round;
+//   tail_pick     a thread per task: the largest trial scale every row fit;
 //   tail_raster   a warp per (task, tail chart): its envelope at k';
 //   tail_compact  a group of 16 lanes per (task, tail pair): distances and
 //                 interlock flags at k'.
@@ -55,7 +54,7 @@ __global__ void __launch_bounds__(1024) tail_plan_kernel(const Pack *__restrict_
     if (j < wr.lo || p.tstate[at * kScales + j] != kTaskTailSearch) continue;
     int32_t *cs = task_state(p, at, j, wave);
     const int32_t S = 16 * (j + 1);
-    cs[kCsLo] = S - 15;  // the first round tries S - 14 .. S
+    cs[kCsLo] = S - 15;  // the trial scales S - 14 .. S
     cs[kCsHi] = S + 1;
     cs[kCsMask] = 0;
     cs[kCsRound] = 0;
@@ -133,11 +132,11 @@ __global__ void __launch_bounds__(kTailThreads) tail_trial_kernel(const Pack *__
   }
 }
 
-// One round's outcome per task (a thread each): the largest trial scale
-// that fit becomes lo and the smallest tried above it hi; if none of the
-// first round's fit, the search goes on over [1, S - 15].  After the last
-// round k' = lo: the task waits for its push (or fails if lo = 0).
+// The outcome per task (a thread each): k' is the largest trial scale at
+// which every row fit (its bit in the mask is clear), 0 if none did; either
+// way the task goes on to the push pass.
 __global__ void tail_pick_kernel(const Pack *__restrict__ pp, int round) {
+  (void)round;
   const Pack &p = *pp;
   const int wave = *(volatile const int32_t *)p.cur_wave;
   const int ntask = *p.tcount;
@@ -146,52 +145,16 @@ __global__ void tail_pick_kernel(const Pack *__restrict__ pp, int round) {
     const int at = tt.x, j = tt.y;
     if (p.tstate[at * kScales + j] != kTaskTailSearch) continue;
     int32_t *cs = task_state(p, at, j, wave);
-    int32_t lo = cs[kCsLo], hi = cs[kCsHi];
-    const bool moot = !(p.flags & TABI_F_EVAL_ALL) && *(volatile int32_t *)(p.found + at) > j;
-    if (hi > lo + 1 && !moot) {
-      const uint32_t mask = (uint32_t)cs[kCsMask];
-      int32_t best = -1, tried[15];
-      for (int i = 0; i < 15; ++i) {
-        tried[i] = trial_scale(lo, hi, i);
-        int f = i;  // a repeated scale was tried at its first occurrence
-        while (f > 0 && tried[f - 1] == tried[i]) --f;
-        if (tried[i] > lo && tried[i] < hi && !((mask >> f) & 1u) && tried[i] > best) best = tried[i];
-      }
-      if (best < 0 && round == 0) {
-        lo = 0;
-        hi = 16 * (j + 1) - 14;
-      } else {
-        if (best < 0) best = lo;
-        int32_t nhi = hi;
-        for (int i = 0; i < 15; ++i)
-          if (tried[i] > best && tried[i] < nhi) nhi = tried[i];
-        lo = best;
-        hi = nhi;
-      }
-      cs[kCsLo] = lo;
-      cs[kCsHi] = hi;
-      cs[kCsMask] = 0;
-      cs[kCsRound] = round + 1;
+    const int32_t lo = cs[kCsLo], hi = cs[kCsHi];
+    const uint32_t mask = (uint32_t)cs[kCsMask];
+    int32_t best = 0;
+    for (int i = 0; i < 15; ++i) {
+      const int32_t k = trial_scale(lo, hi, i);
+      if (k > lo && k < hi && !((mask >> i) & 1u) && k > best) best = k;
     }
-    if (moot || hi <= lo + 1 || round + 1 >= kTailRounds) {
-      ScaleOut &so = p.scale_out[at * kScales + j];
-      if (!moot && lo > 0) {
-        cs[kCsKt] = lo;
-        p.tstate[at * kScales + j] = kTaskTailPush;
-      } else {  // no scale fits every row (or the candidate can no longer win)
-        so.success = 0;
-        so.rows = cs[kCsHeadRows];
-        so.placed = cs[kCsC0];
-        so.score = cs[kCsCommitted];
-        so.knee_rows = cs[8];
-        so.knees = cs[9];
-        so.tail_rows = 0;  // none pushed
-        so.tail_k = 0;
-        so.tail_start = cs[kCsC0];
-        so.evaluated = moot ? 2 : 1;
-        p.tstate[at * kScales + j] = kTaskDone;
-      }
-    }
+    cs[kCsKt] = best;
+    cs[kCsMask] = 0;
+    p.tstate[at * kScales + j] = kTaskTailPush;
   }
 }
 
@@ -210,6 +173,7 @@ __global__ void __launch_bounds__(kTailThreads) tail_raster_kernel(const Pack *_
     const int at = tt.x, j = tt.y, c0 = tt.w;
     if (p.tstate[at * kScales + j] != kTaskTailPush) continue;
     const int32_t kt = task_state(p, at, j, wave)[kCsKt];
+    if (kt == 0) continue;  // no tail scale: the rows go on at S
     const AtlasDesc &ad = p.atl[at];
     const int cb = ad.cb, n = ad.n;
     const int64_t cbase = p.abase[region(at, j, 0)], rbase = p.abase[region(at, j, 1)];
@@ -247,6 +211,7 @@ __global__ void __launch_bounds__(256) tail_compact_kernel(const Pack *__restric
     const int4 tt = p.ttask[ti];
     const int at = tt.x, j = tt.y, c0 = tt.w;
     if (p.tstate[at * kScales + j] != kTaskTailPush) continue;
+    if (task_state(p, at, j, *(volatile const int32_t *)p.cur_wave)[kCsKt] == 0) continue;
     const int cb = p.atl[at].cb, n = p.atl[at].n;
     for (int64_t s = c0 + gg; s + 1 < n; s += ng) compact_pair<G>(p, at, j, cb + (int)s, lane, gm);
   }

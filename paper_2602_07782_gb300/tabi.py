@@ -175,13 +175,13 @@ def kernels_per_pack(fanout: int, chunks: int = 4, waves_run: int | None = None,
     """Kernels one (batched) pack launches: init, prep, sort + gather,
     layout + bases; per wave, for each chart chunk plan + fill, raster,
     compaction, row loop, then (if some atlas may take the prefix-sum tail)
-    the tail's plan, four rounds of trial and pick, redraw, compaction and
-    push pass, then the wave's end; selection.  The graph runs waves only
+    the tail's plan, trial scales, pick, redraw, compaction and push pass,
+    then the wave's end; selection.  The graph runs waves only
     while some atlas still searches (`waves_run` of them: the most any
     atlas of the batch needs, at least one); direct launches (stage timing)
     run every wave."""
     w = waves(fanout) if waves_run is None else max(1, waves_run)
-    return 7 + (5 * chunks + 1 + (12 if tail else 0)) * w
+    return 7 + (5 * chunks + 1 + (6 if tail else 0)) * w
 
 
 @dataclass

@@ -201,11 +201,48 @@ def test_tail_ablation_parity(ctx, flags):
 
 def test_tail_threshold_by_chart_count(ctx):
     """The tail applies above hybrid_min_charts only (the paper: 10,000)."""
-    cs = synth.stars(6, 400, 512)
-    for hmin in (399, 400):
-        p = gpu_params(topt_permille=100, hybrid_min_charts=hmin)
+    cs = synth.stars(17, 2000, 1024)
+    for hmin in (1999, 2000):
+        p = gpu_params(topt_permille=50, hybrid_min_charts=hmin)
         o = _compare_pack(cs, ctx.pack(cs, p), oracle_params(p))
-        assert (o.stats[5] > 0) == (hmin < 400)
+        assert (o.stats[5] > 0) == (hmin < 2000)
+
+
+@pytest.mark.parametrize("topt", [50, 150])
+def test_tail_candidates_taken_and_abandoned(ctx, topt):
+    """Every candidate of a 2,000-chart atlas with the tail from 5 % (15 %) of
+    the atlas height: candidates whose rows fit within a grid step push the
+    tail at its own scale, the others fold the rest row by row; each
+    candidate's outcome, tail scale, first tail chart and placements, and the
+    envelopes at the tail scale, against the oracle."""
+    cs = synth.stars(17, 2000, 1024)
+    p = gpu_params(flags=tabi.F_ALL | tabi.F_EVAL_ALL, topt_permille=topt, hybrid_min_charts=0)
+    op = oracle_params(p)
+    res = ctx.pack(cs, p)
+    assert res.status == tabi.TABI_OK, ctx.last_error()
+    rec = oracle.prep(cs, op)
+    perm = oracle.sort(rec)
+    taken = abandoned = 0
+    for j in range(20, 40):
+        k = 16 * (j + 1)
+        hdr, place = ctx.scale_result(j, cs.n)
+        ok, opl, ost = oracle.pack_scale(rec, perm, cs.atlas_w, cs.atlas_h, k, op)
+        assert hdr[0] == int(ok) and list(hdr[1:6]) == [int(v) for v in ost[:5]], j
+        assert [hdr[7], hdr[8], hdr[9]] == [int(ost[5]), int(ost[6]), int(ost[7])], j
+        placed = int(ost[4])
+        assert np.array_equal(place[:placed, 0], opl[:placed, 0]), j
+        assert np.array_equal(place[:placed, 1], opl[:placed, 1]), j
+        kt, c0 = int(ost[6]), int(ost[7])
+        if kt:
+            taken += 1
+            env = ctx.envelopes(j, cs.n)
+            for s in range(c0, cs.n, 37):
+                e = oracle.envelope_padded(rec[perm[s]], kt, op)
+                assert (env[s][0], env[s][1]) == (e.w, e.h) and np.array_equal(env[s][2], e.top), (j, s)
+        elif ost[7] == cs.n and ok:
+            abandoned += 1
+    assert taken > 0
+    _compare_pack(cs, res, op)
 
 
 @pytest.mark.parametrize("count", [2, 5])

@@ -35,14 +35,12 @@ def skyline_tail(sizes, W, H, S, g=1):
     """Independent brute force for boxes folded entirely by the tail
     (Sec. 4.4): sorted by height, padded widths at the candidate S, the
     prefix of the widths (boxes have compacting distance 0) cut into rows
-    modulo W'; the intermediate scale is the largest k' <= S at which every
-    row's widths sum to at most W' (for boxes the widths, hence the fit,
-    are monotone in the scale, where the oracle's 16-way search finds the
-    largest fit); rows in FastAtlas's
-    directions (left, right, right, ...) from their near end, each box
-    dropped onto the skyline.  Returns (success, k', {sorted pos: (X, y,
-    mirror, tail row)}).  Boxes wider than tall are turned upright first
-    (Sec. 3.1)."""
+    modulo W'; the intermediate scale is the largest k' in S - 14 .. S at
+    which every row's widths sum to at most W' (if there is none the tail is
+    not taken: (None, 0, {})); rows in FastAtlas's directions (left, right,
+    right, ...) from their near end, each box dropped onto the skyline.
+    Returns (success, k', {sorted pos: (X, y, mirror, tail row)}).  Boxes
+    wider than tall are turned upright first (Sec. 3.1)."""
     sizes = [(min(w, h), max(w, h)) for w, h in sizes]
     order = sorted(range(len(sizes)), key=lambda i: -sizes[i][1])  # stable
     Wp, Hp = W + 2 * g, H + 2 * g
@@ -57,12 +55,12 @@ def skyline_tail(sizes, W, H, S, g=1):
     P = np.concatenate([[0], np.cumsum(w)[:-1]]).astype(int)
     rows = _rows_modulo(P, Wp)
     kt = 0
-    for k2 in range(S, 0, -1):
+    for k2 in range(S, max(0, S - 15), -1):
         if all(sum(wp(k2)[s] for s in row) <= Wp for row in rows):
             kt = k2
             break
     if not kt:
-        return False, 0, {}
+        return None, 0, {}
     w2, h2 = wp(kt), hp(kt)
     front = np.zeros(Wp, np.int64)
     out = {}
@@ -85,23 +83,36 @@ def _area2(sizes):
     return [2 * (w * 256) * (h * 256) for w, h in sizes]
 
 
-BOXES = [[(3, 5), (2, 2), (4, 6), (1, 3), (5, 5), (2, 4), (3, 3), (1, 1), (2, 6), (4, 4)] * 3,
-         [(1, 2), (2, 3), (3, 3), (1, 1)] * 9 + [(6, 7), (5, 8)],
-         [(9, 11), (7, 9), (8, 8), (6, 10), (5, 7), (9, 6), (4, 9), (8, 5)] * 4]
+def _wide_boxes(seed):
+    rng = np.random.default_rng(seed)
+    return [(int(w), int(w + rng.integers(5, 60))) for w in rng.integers(80, 121, 24)]
+
+
+# (sizes in texels, atlas W, H): small boxes (whose overflowing rows no
+# downscale within a grid step can fix: the rows go on one by one) and boxes
+# wide enough that one step of downscale narrows each by a texel
+BOXES = [([(3, 5), (2, 2), (4, 6), (1, 3), (5, 5), (2, 4), (3, 3), (1, 1), (2, 6), (4, 4)] * 3, 17, 40),
+         ([(1, 2), (2, 3), (3, 3), (1, 1)] * 9 + [(6, 7), (5, 8)], 17, 40),
+         ([(9, 11), (7, 9), (8, 8), (6, 10), (5, 7), (9, 6), (4, 9), (8, 5)] * 4, 41, 40),
+         (_wide_boxes(7), 520, 900),
+         (_wide_boxes(8), 520, 900)]
 
 
 @pytest.mark.parametrize("case", range(len(BOXES)))
 @pytest.mark.parametrize("k", [256, 512, 768, 1024])
 @pytest.mark.parametrize("g", [1, 0, 2])
 def test_boxes_match_skyline_brute_force(case, k, g):
-    sizes = BOXES[case]
-    W, H = 17 if case < 2 else 41, 40
+    sizes, W, H = BOXES[case]
     cs = synth.rectangles(sizes, W, H)
     params = oracle.default_params(topt=1000, hybrid_min=0, gutter=g)  # every row is a tail row
     rec = oracle.prep(cs, params)
     perm = oracle.sort(rec)
     ok, place, stats = oracle.pack_scale(rec, perm, W, H, k, params)
     bok, kt, exp = skyline_tail(sizes, W, H, k, g)
+    if bok is None:  # no tail scale within one grid step: the rows are folded one by one
+        assert stats[6] == 0 and stats[5] == 0 and stats[7] == cs.n
+        assert not np.any(place[:int(stats[4]), 5] == 2)
+        return
     assert ok == bok
     assert stats[6] == kt and stats[7] == 0
     placed = int(stats[4])
@@ -114,79 +125,89 @@ def test_boxes_match_skyline_brute_force(case, k, g):
 
 
 def test_three_rows_downscaled_by_hand():
-    """Nine boxes 100 texels wide and 130 down to 122 tall, in a 300 x 400
-    atlas with 1-px gutters (W' = 302): at S = 1024 their padded widths are
+    """Nine boxes 100 texels wide and 130 down to 122 tall, in a 301 x 400
+    atlas with 1-px gutters (W' = 303): at S = 1024 their padded widths are
     102, the prefix 0, 102, ..., 816 puts three boxes in each of rows 0, 1,
-    2 (floor(P / 302)), and each row overflows (306 > 302).  At k the padded
+    2 (floor(P / 303)), and each row overflows (306 > 303).  At k the padded
     width is ceil(100 k / 1024) + 2, so three fit iff ceil(100 k / 1024) <=
-    98, i.e. k <= 1003: k' = 1003 (padded widths 100, padded heights
-    ceil(h 1003 / 1024) + 2 = 130, 129, ..., 122).  Row 0 runs left to
-    right at x = 0, 100, 200; rows 1 and 2 run right to left at x = 202,
-    102, 2 and drop onto the skyline: row 1 lands at 128, 129, 130 and
-    levels it at 255, row 2 lands at 255 and tops out at 379.  S = 1008
-    gives the same k' and so the same weighted scale; the tie keeps the
-    larger candidate, and 992 (whose rows need k' = 747) cannot beat 1003."""
+    99, i.e. k <= 1013 (within 14 of S): k' = 1013, padded widths 101,
+    padded heights ceil(h 1013 / 1024) + 2 = 131, 130, ..., 123.  Row 0 runs
+    left to right at x = 0, 101, 202; rows 1 and 2 run right to left at
+    x = 202, 101, 0 and drop onto the skyline: row 1 lands at 129, 130, 131
+    and levels it at 257, row 2 lands at 257 and tops out at 382.  The next
+    candidate, 1008, cannot beat a weighted scale of 1013, so the search
+    stops there.  In a 300-wide atlas the rows overflow by 4 and fit only
+    from k = 1003 down: too far below 1024, no tail is taken."""
     sizes = [(100, h) for h in range(130, 121, -1)]
-    cs = synth.rectangles(sizes, 300, 400)
+    cs = synth.rectangles(sizes, 301, 400)
     params = oracle.default_params(topt=1000, hybrid_min=0)
     rec = oracle.prep(cs, params)
     perm = oracle.sort(rec)
     assert list(perm) == list(range(9)) and not rec[:, R["ROT"]].any()
-    ok, place, stats = oracle.pack_scale(rec, perm, 300, 400, 1024, params)
-    assert ok and stats[6] == 1003 and stats[5] == 3 and stats[3] == 379
+    ok, place, stats = oracle.pack_scale(rec, perm, 301, 400, 1024, params)
+    assert ok and stats[6] == 1013 and stats[5] == 3 and stats[3] == 382
     assert list(place[:, 3]) == [0, 0, 0, 1, 1, 1, 2, 2, 2]
     assert list(place[:, 2]) == [0, 0, 0, 1, 1, 1, 1, 1, 1]
-    assert list(place[:, 0]) == [0, 100, 200, 202, 102, 2, 202, 102, 2]
-    assert list(place[:, 1]) == [0, 0, 0, 128, 129, 130, 255, 255, 255]
-    assert list(place[:, 6]) == [1003] * 9
-    ok2, _, st2 = oracle.pack_scale(rec, perm, 300, 400, 1008, params)
-    assert ok2 and st2[6] == 1003
-    # at 992 the padded widths are 99: the prefix puts four boxes in row 0,
-    # which fit only at ceil(100 k / 1024) <= 73, i.e. k' = 747
-    ok3, _, st3 = oracle.pack_scale(rec, perm, 300, 400, 992, params)
-    assert ok3 and st3[6] == 747
-    r = oracle.pack(cs, params)
-    assert r.status == 0 and r.k == 1024 and list(r.place[:, 10]) == [1003] * 9
-    assert r.score == 1003 * sum(_area2(sizes))
+    assert list(place[:, 0]) == [0, 101, 202, 202, 101, 0, 202, 101, 0]
+    assert list(place[:, 1]) == [0, 0, 0, 129, 130, 131, 257, 257, 257]
+    assert list(place[:, 6]) == [1013] * 9
+    ok2, _, st2 = oracle.pack_scale(rec, perm, 301, 400, 1008, params)
+    assert ok2 and st2[6] == 1008  # rows of 3 x 101 fit at 1008 itself
+    r = oracle.pack(cs, params, all_scales=False)
+    assert r.status == 0 and r.k == 1024 and list(r.place[:, 10]) == [1013] * 9
+    assert r.score == 1013 * sum(_area2(sizes))
+    narrow = synth.rectangles(sizes, 300, 400)
+    rec = oracle.prep(narrow, params)
+    ok3, pl3, st3 = oracle.pack_scale(rec, oracle.sort(rec), 300, 400, 1024, params)
+    assert st3[6] == 0 and st3[5] == 0 and st3[7] == 9 and not np.any(pl3[:, 5] == 2)
 
 
 @pytest.mark.parametrize("case", range(len(BOXES)))
 def test_boxes_search_matches_brute_force(case):
     """The search keeps the successful candidate with the largest
     area-weighted scale, ties to the larger candidate (Sec. 4.4)."""
-    sizes = BOXES[case]
-    W, H = 17 if case < 2 else 41, 40
+    sizes, W, H = BOXES[case]
     cs = synth.rectangles(sizes, W, H)
     params = oracle.default_params(topt=1000, hybrid_min=0)
     r = oracle.pack(cs, params, all_scales=True)
     area = sum(_area2(sizes))
-    best, best_score = 0, -1
+    best, best_score, tails = 0, -1, 0
+    rec = oracle.prep(cs, params)
+    perm = oracle.sort(rec)
     for j in range(64, 0, -1):
         ok, kt, _ = skyline_tail(sizes, W, H, 16 * j)
+        if ok is None:  # no tail taken: the oracle's own row-by-row result, every box at S
+            ok, kt = oracle.pack_scale(rec, perm, W, H, 16 * j, params)[0], 16 * j
+        else:
+            tails += 1
         assert bool(r.success[j - 1]) == ok, j
         if ok and kt * area > best_score:
             best, best_score = 16 * j, kt * area
+    assert tails > 10 or case < 3
     assert r.k == best and r.score == best_score
     assert r.status == 0 and np.all(r.place[:, 10] == best_score // area)
 
 
 def _tall_then_small():
     rng = np.random.default_rng(5)
-    sizes = [(int(rng.integers(8, 30)), int(h)) for h in np.linspace(60, 20, 12).astype(int)]
-    sizes += [(int(rng.integers(1, 8)), int(rng.integers(2, 12))) for _ in range(300)]
+    sizes = [(int(rng.integers(32, 120)), int(h)) for h in np.linspace(240, 80, 12).astype(int)]
+    sizes += [(int(rng.integers(4, 32)), int(rng.integers(8, 48))) for _ in range(300)]
     return sizes
 
 
 def test_switch_point():
     """Sec. 4.4: sequential rows until no knee is live and the row's first
-    (tallest) chart is below t_opt of the atlas height; tail rows after."""
+    (tallest) chart is below t_opt of the atlas height; tail rows after --
+    where a tail scale within one grid step fits them, else the rows simply
+    continue one by one (no row is folded by the prefix sum)."""
     sizes = _tall_then_small()
-    W = H = 160
+    W = H = 640
     cs = synth.rectangles(sizes, W, H)
     params = oracle.default_params(topt=50, hybrid_min=0)
     rec = oracle.prep(cs, params)
     perm = oracle.sort(rec)
-    for k in (512, 768, 1024):
+    taken = 0
+    for k in range(512, 1025, 32):
         ok, place, stats = oracle.pack_scale(rec, perm, W, H, k, params)
         placed = int(stats[4])
         assert stats[2] == 0  # no knees in this set (drops below 10 % of H)
@@ -195,17 +216,22 @@ def test_switch_point():
         h = [_ceil_div(int(rec[perm[s], R["HQ"]]) * k, 1 << 18) for s in firsts]
         below = [1000 * hh < 50 * H for hh in h]
         tail_rows = [bool(place[s, 5] == 2) for s in firsts]
+        if stats[6] == 0:  # no tail scale fitted: every row folded one by one
+            assert not any(tail_rows) and stats[5] == 0 and stats[7] == cs.n
+            continue
+        taken += 1
         first_tail = below.index(True) if True in below else len(below)
         assert tail_rows == [r >= first_tail for r in range(len(firsts))]
         assert stats[5] == len(firsts) - first_tail
         assert stats[5] > 0 and first_tail > 0
         assert stats[7] == firsts[first_tail]
-        # the head keeps the candidate scale, the tail its own
+        # the head keeps the candidate scale, the tail its own, within a step
         assert np.all(place[:firsts[first_tail], 6] == k)
-        assert np.all(place[firsts[first_tail]:placed, 6] == stats[6]) and 0 < stats[6] <= k
+        assert np.all(place[firsts[first_tail]:placed, 6] == stats[6]) and k - 14 <= stats[6] <= k
         # FastAtlas's alternation: one left-to-right row, then two right-to-left
         mirrors = [int(place[s, 2]) for s in firsts[first_tail:]]
         assert mirrors == [int(t % 3 != 0) for t in range(len(mirrors))]
+    assert taken >= 2
 
 
 def test_compacted_rows_are_tight_at_the_tail_scale():
@@ -213,8 +239,8 @@ def test_compacted_rows_are_tight_at_the_tail_scale():
     (at the tail's scale k') from its predecessor, unless the clamp (chart
     s+1 never left of chart s-1's right edge) binds, in which case it
     touches that right edge; each row starts at the atlas's left edge."""
-    cs = synth.stars(17, 400, 512)
-    params = oracle.default_params(topt=200, hybrid_min=0)
+    cs = synth.stars(17, 2000, 1024)
+    params = oracle.default_params(topt=50, hybrid_min=0)
     rec = oracle.prep(cs, params)
     perm = oracle.sort(rec)
     k = 448
@@ -244,8 +270,8 @@ def test_rows_follow_the_prefix_modulo_the_width():
     """The tail's rows are the prefix fold at the candidate scale cut modulo
     W' (each row's last chart may overflow it), recomputed here from the
     oracle's own widths and distances at S; every row fits W' at k'."""
-    cs = synth.stars(19, 600, 512)
-    params = oracle.default_params(topt=200, hybrid_min=0)
+    cs = synth.stars(19, 3000, 2048)
+    params = oracle.default_params(topt=50, hybrid_min=0)
     rec = oracle.prep(cs, params)
     perm = oracle.sort(rec)
     S = 480
@@ -273,14 +299,15 @@ def test_rows_follow_the_prefix_modulo_the_width():
         assert lo >= 0 and hi <= Wp
 
 
-@pytest.mark.parametrize("make", [lambda: synth.stars(23, 600, 512), lambda: synth.knees(3, 500, 1024),
-                                  lambda: synth.pareto20k(seed=4, n=1200, atlas=1024)])
+@pytest.mark.parametrize("make", [lambda: synth.stars(17, 2000, 1024), lambda: synth.knees(3, 1500, 1024),
+                                  lambda: synth.pareto20k(seed=4, n=2000, atlas=1024)])
 @pytest.mark.parametrize("flags", [oracle.F_ALL, oracle.F_ALL & ~oracle.F_HC])
 def test_invariants_with_the_tail(make, flags):
-    """Overlap-free, gutters respected, inside the atlas, the largest
-    successful candidate returned -- with most rows folded by the prefix."""
+    """Overlap-free, gutters respected, inside the atlas, the candidate
+    with the largest area-weighted scale returned -- with most rows folded
+    by the prefix and drawn at the tail's own scale."""
     cs = make()
-    params = oracle.default_params(topt=100, hybrid_min=0, flags=flags)
+    params = oracle.default_params(topt=50, hybrid_min=0, flags=flags)
     r = oracle.pack(cs, params, all_scales=True)
     assert r.status == 0
     assert r.stats[5] > 0
@@ -301,10 +328,10 @@ def test_invariants_with_the_tail(make, flags):
 def test_small_atlases_keep_sequential_folding():
     """The tail applies only above hybrid_min charts (the paper: 10,000);
     at or below it the result is that of t_opt = 0."""
-    cs = synth.stars(29, 300, 512)
-    a = oracle.pack(cs, oracle.default_params(topt=100, hybrid_min=300))
+    cs = synth.stars(17, 2000, 1024)
+    a = oracle.pack(cs, oracle.default_params(topt=50, hybrid_min=2000))
     b = oracle.pack(cs, oracle.default_params(topt=0))
-    c = oracle.pack(cs, oracle.default_params(topt=100, hybrid_min=299))
+    c = oracle.pack(cs, oracle.default_params(topt=50, hybrid_min=1999))
     assert a.k == b.k and np.array_equal(a.place, b.place) and a.stats[5] == 0
     assert c.stats[5] > 0
 
