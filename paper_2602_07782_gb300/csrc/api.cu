@@ -288,8 +288,10 @@ void enqueue_wave(const Pack *dp, const Launch &L, int F, cudaStream_t st, Stage
   }
   if (L.tail) {  // the prefix-sum tail (Sec. 4.4): its scale, redraw, push (with the row loop's time)
     b(5);
-    launch_tail(dp, L, F, st);
-    launch_rowloop(dp, L, L.Q, F, st);
+    for (int r = 0; r < tail_rounds(F); ++r) {
+      launch_tail_round(dp, L, F, r, st);
+      launch_rowloop(dp, L, L.Q, F, st);
+    }
     e();
   }
   launch_wave_end(dp, h, in_graph, st);
@@ -375,7 +377,8 @@ tabi_status capture_graph(tabi_ctx *ctx, const Launch &L, int F, cudaGraph_t *ou
 tabi_status get_graph(tabi_ctx *ctx, const Launch &L, int F, cudaGraphExec_t *out) {
   for (const GraphEntry &g : ctx->graphs)
     if (g.F == F && g.smem == L.rowloop_smem && g.threads == L.rowloop_threads && g.ctas == L.rowloop_ctas &&
-        g.Q == L.Q && g.prep_group == L.prep_group && g.laabb_k == L.laabb_k && g.tail == L.tail) {
+        g.Q == L.Q && g.prep_group == L.prep_group && g.laabb_k == L.laabb_k && g.tail == L.tail &&
+        g.gutter == L.gutter) {
       *out = g.exec;
       return TABI_OK;
     }
@@ -387,7 +390,8 @@ tabi_status get_graph(tabi_ctx *ctx, const Launch &L, int F, cudaGraphExec_t *ou
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphInstantiate");
   ctx->graphs.push_back(
-      GraphEntry{F, L.rowloop_smem, L.rowloop_threads, L.rowloop_ctas, L.Q, L.prep_group, L.laabb_k, L.tail, exec});
+      GraphEntry{F, L.rowloop_smem, L.rowloop_threads, L.rowloop_ctas, L.Q, L.prep_group, L.laabb_k, L.tail, L.gutter,
+                 exec});
   *out = exec;
   return TABI_OK;
 }
@@ -660,7 +664,7 @@ tabi_status batch_launch(tabi_ctx *ctx, const tabi_params *params, tabi_request 
   for (int i = 0; i < A; ++i) want = std::max(want, rowloop_smem_wanted(desc[i].W, p.g));
   int smem = (int)((want + 16383) & ~(size_t)16383);
   if (smem > ctx->rowloop_dyn_max) smem = ctx->rowloop_dyn_max;
-  Launch L{ctx->sms, smem, tn.threads == 512 ? 512 : 1024, 1, p.Q, p.prep_group, p.laabb_k, p.tail != 0};
+  Launch L{ctx->sms, smem, tn.threads == 512 ? 512 : 1024, 1, p.Q, p.prep_group, p.laabb_k, p.tail != 0, p.g};
   if (L.rowloop_threads == 512 && tn.ctas == 2) {
     // two CTAs per multiprocessor if both fit its shared memory
     const int two = (ctx->smem_per_sm - 2 * (ctx->smem_reserved + rowloop_static_smem())) / 2 & ~255;

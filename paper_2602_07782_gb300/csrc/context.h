@@ -17,6 +17,7 @@ namespace tabi {
 struct GraphEntry {
   int F, smem, threads, ctas, Q, prep_group, laabb_k;  // (the progressive bound is read from the record)
   bool tail;                                           // the prefix-sum tail's kernels follow each wave
+  int gutter;                                          // (selects the tail's trial kernel)
   cudaGraphExec_t exec;
 };
 

@@ -514,9 +514,9 @@ __device__ void sort_atlas(const Pack &p, int at) {
     // twice the area in Q.8^2, E in Q.8), so candidate k can succeed only if
     //   area2 k^2 + 2g 2^19 k sum(E) + 4 g^2 2^37 n <= (W + 2g)(H + 2g) 2^37.
     // Where the prefix-sum tail may apply (Sec. 4.4) its charts may end at
-    // a smaller scale than k, so only the charts surely folded row by row
-    // at k (head_prefix) count with their area and extent; every chart
-    // keeps its 4 g^2.  Larger candidates are skipped.
+    // the tail's scale, at least k - 14: the charts surely folded row by
+    // row at k (head_prefix) count at k, the others at k - 14.  Larger
+    // candidates are skipped.
     int jt = kScales - 1;
     if (!(p.flags & TABI_F_EVAL_ALL)) {
       const uint64_t g = (uint64_t)p.g;
@@ -526,11 +526,12 @@ __device__ void sort_atlas(const Pack &p, int at) {
       const bool hybrid = p.topt > 0 && n > p.hyb_min;
       jt = -1;
       for (int j = 0; j < kScales; ++j) {
-        const uint64_t k = 16 * (uint64_t)(j + 1);
+        const uint64_t k = 16 * (uint64_t)(j + 1), kr = hybrid ? k - kTailSteps : k;
         const int hp = head_prefix(p.hq + cb, n, (int64_t)k, p.topt, p.atl[at].H, hybrid);
         const unsigned __int128 s2 = hp < n ? p.pre2[cb + hp] : p.area2[at];
         const unsigned __int128 ex = hp < n ? p.preE[cb + hp] : p.ext_sum[at];
-        const unsigned __int128 need = s2 * (k * k) + ((ex * (2 * g * k)) << 19) + fixed;
+        const unsigned __int128 s2r = p.area2[at] - s2, exr = p.ext_sum[at] - ex;
+        const unsigned __int128 need = s2 * (k * k) + s2r * (kr * kr) + (((ex * k + exr * kr) * (2 * g)) << 19) + fixed;
         if (need <= lim) jt = j;
       }
     }

@@ -184,4 +184,60 @@ __device__ __forceinline__ int32_t warp_pair_reach(const rmath::AxisK &A, const 
   return warp_max(M);
 }
 
+// The row constants (axis 1) of one chart at any scale k by an aligned
+// group of G >= 8 lanes (glane: the lane within the group): the pieces and
+// cross pieces spread over the lanes, the OBB lines on lane 0, the four row
+// corners on lanes 4-7.  The caller synchronises the group after.
+template <int G>
+__device__ __forceinline__ void group_setup_rows(const Pack &p, const ChartShape &sh, int64_t k, rmath::AxisK &a,
+                                                 int glane) {
+  const bool use_l = (p.flags & TABI_F_LAABB) != 0, use_o = (p.flags & TABI_F_OBB) != 0;
+  const int m = sh.m;
+  const int64_t C = kObbCos[m], S = kObbSin[m];
+  const uint32_t ext = (uint32_t)sh.Hq, oth = (uint32_t)sh.Wq;
+  for (int i = glane; i < rmath::kK; i += G) {
+    const int sl = i * p.laabb_k / rmath::kK;
+    rmath::setup_piece(a, i, i * ext / rmath::kK, (i + 1) * ext / rmath::kK, (uint32_t)k, (uint32_t)sh.xlo[i],
+                       (uint32_t)sh.xhi[i]);
+    rmath::setup_cross(a, i, (uint32_t)sh.ylo[i], (uint32_t)sh.yhi[i], ext, (uint32_t)k,
+                       (uint32_t)(sl * rmath::kK / p.laabb_k) * oth / rmath::kK,
+                       (uint32_t)((sl + 1) * rmath::kK / p.laabb_k) * oth / rmath::kK);
+  }
+  if (glane == 0) {
+    rmath::setup_obb_fixed(a, 1, m, C, S, kObbDivCos[m], kObbDivSin[m], use_l, use_o);
+    rmath::setup_obb_k(a, 1, sh.Wq, sh.Hq, k, C, S, sh.u0, sh.u1, sh.v0, sh.v1);
+  } else if (glane >= 4 && glane < 8 && use_o && m > 0) {
+    rmath::CornerQ cq;
+    rmath::corner_at(cq, glane, k, C, S, sh.u0, sh.u1, sh.v0, sh.v1);  // items 4-7: the row corners
+    rmath::corner_store(cq, glane, a, sh.Hq * k);
+  }
+}
+
+// warp_pair_reach by an aligned group of G lanes (2g < G: the gutter
+// dilation reaches back one chunk at most).
+template <int G>
+__device__ __forceinline__ int32_t group_pair_reach(const rmath::AxisK &A, const rmath::AxisK &B, int g, int glane,
+                                                    unsigned gm) {
+  const int32_t hmin = min(A.len, B.len) + 2 * g;
+  int32_t prev_hi = -kBig, prev_lo = kBig, M = -kBig;
+  for (int32_t base = 0; base < hmin; base += G) {
+    const int32_t c = base + glane;
+    int32_t alo, ahi = -kBig, blo = kBig, bhi;
+    if (c < A.len) rmath::scanline(A, c, alo, ahi);
+    if (c < B.len) rmath::scanline(B, c, blo, bhi);
+    int32_t dhi = ahi, dlo = blo;
+    for (int o = 1; o <= 2 * g; ++o) {
+      const int src = (glane - o) & (G - 1);
+      const int32_t ch = __shfl_sync(gm, ahi, src, G), ph = __shfl_sync(gm, prev_hi, src, G);
+      const int32_t cl = __shfl_sync(gm, blo, src, G), pl = __shfl_sync(gm, prev_lo, src, G);
+      dhi = max(dhi, glane >= o ? ch : ph);
+      dlo = min(dlo, glane >= o ? cl : pl);
+    }
+    if (c < hmin) M = max(M, dhi + 2 * g - dlo);
+    prev_hi = ahi;
+    prev_lo = blo;
+  }
+  return group_max<G>(M, gm);
+}
+
 }  // namespace tabi

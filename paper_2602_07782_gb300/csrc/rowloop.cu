@@ -491,18 +491,19 @@ __global__ void __launch_bounds__(NT) rowloop_kernel(const Pack *__restrict__ pp
               // Once the charts not yet placed cannot fit that way into the
               // area under the frontline, the candidate fails now instead of
               // rows later (checked after every committed row).
-              // Charts the prefix-sum tail may draw smaller count with their
-              // 4g^2 only (head_p: those surely drawn at this scale), and the
-              // tail's rows are not checked.
+              // Charts the prefix-sum tail may draw at its scale count at
+              // k - 14 (head_p: those surely drawn at k), and the tail's rows
+              // are not checked.
               if (area_bound && row > 0 && !tail) {
-                const int hp = ctl.head_p;
-                const unsigned long long nxt2 = p.pre2[cb + row_start], nxtE = p.preE[cb + row_start];
-                const unsigned long long end2 = hp < n ? p.pre2[cb + hp] : tot2;
-                const unsigned long long endE = hp < n ? p.preE[cb + hp] : totE;
+                const int hp = ctl.head_p, rs = row_start;
+                const unsigned long long p2 = p.pre2[cb + rs], pE = p.preE[cb + rs];
+                const unsigned long long h2 = hp < n ? p.pre2[cb + hp] : tot2, hE = hp < n ? p.preE[cb + hp] : totE;
                 const int32_t fr = Wp * Hp - ctl.front_sum;  // free texels under the frontline (sides <= 8192)
-                const uint64_t kk = 16 * (uint64_t)(j + 1), gg = (uint64_t)g;
-                const unsigned __int128 S2 = row_start < hp ? end2 - nxt2 : 0, SE = row_start < hp ? endE - nxtE : 0;
-                const unsigned __int128 need = S2 * (kk * kk) + ((SE * (2 * gg * kk)) << 19) +
+                const uint64_t kk = 16 * (uint64_t)(j + 1), kr = hybrid ? kk - kTailSteps : kk, gg = (uint64_t)g;
+                // at k: the charts from rs to hp; at k - 14: those from max(rs, hp) on
+                const unsigned __int128 S2 = rs < hp ? h2 - p2 : 0, SE = rs < hp ? hE - pE : 0;
+                const unsigned __int128 R2 = tot2 - (rs < hp ? h2 : p2), RE = totE - (rs < hp ? hE : pE);
+                const unsigned __int128 need = S2 * (kk * kk) + R2 * (kr * kr) + (((SE * kk + RE * kr) * (2 * gg)) << 19) +
                                                ((unsigned __int128)(4 * gg * gg * (uint64_t)(n - row_start)) << 37);
                 if (need > ((unsigned __int128)(uint32_t)fr << 37)) ctl.bound_fail = 1;
               }

@@ -196,6 +196,7 @@ struct Launch {
   int prep_group;      // prep lanes per chart: 32, 16, 8 or 4
   int laabb_k;         // local AABBs per axis: 2, 5 or 10 (selects the prep kernel)
   bool tail;           // the batch may take the prefix-sum tail: its kernels follow each wave
+  int gutter;          // g (the tail's trial kernel picks its lane groups by it)
 };
 void launch_init(const Pack *dp, const Launch &L, cudaStream_t st);
 void launch_prep(const Pack *dp, const Launch &L, cudaStream_t st);
@@ -212,11 +213,14 @@ cudaError_t rowloop_prepare(int smem);  // raise the CTA's shared-memory limit (
 int rowloop_static_smem();              // the row-loop kernel's static shared memory
 void launch_rowloop(const Pack *dp, const Launch &L, int q, int F, cudaStream_t st);
 void launch_select(const Pack *dp, const Launch &L, cudaStream_t st);
-// The prefix-sum tail after a wave's last chunk (Sec. 4.4): the tasks that
-// folded their tail, the rounds of trial scales, the redraw and the
-// compaction at the chosen scale (the row loop pushes the rows after).
-void launch_tail(const Pack *dp, const Launch &L, int F, cudaStream_t st);
+// The prefix-sum tail after a wave's last chunk (Sec. 4.4), in rounds: per
+// round the largest parked tail tasks of each atlas (1, 2, 4, ..., then the
+// rest), their trial scales, the redraw and the compaction at the chosen
+// scale (the row loop's push pass follows each round).
+int tail_rounds(int F);
+void launch_tail_round(const Pack *dp, const Launch &L, int F, int round, cudaStream_t st);
 constexpr int kTailRounds = 1;  // trial scales k - 14 .. k (one candidate step), one launch
+constexpr int kTailSteps = 14;  // the tail's scale is at least k - 14
 size_t rowloop_smem_bytes(int W, int g);       // shared memory a row-loop CTA needs without the stage
 size_t rowloop_smem_wanted(int W, int g);      // ... with a stage of two atlas widths
 
@@ -374,9 +378,10 @@ __device__ __forceinline__ int32_t moot_below(unsigned __int128 w, unsigned long
 // Charts surely folded row by row at candidate k (Sec. 4.4): the tail only
 // takes charts no taller than the first chart of its first row, which is
 // shorter than t_opt H, so every chart with 1000 ceil(Hq k / 2^18) >=
-// t_opt H is placed before it.  hq_sorted is the atlas's sorted Hq
-// (non-increasing); returns how many such charts lead it (n when the tail
-// cannot apply).
+// t_opt H is placed before it, at k; the others end at k or at the tail's
+// scale, which is at least k - kTailSteps.  hq_sorted is the atlas's
+// sorted Hq (non-increasing); returns how many such charts lead it (n
+// when the tail cannot apply).
 __host__ __device__ __forceinline__ int head_prefix(const int32_t *hq_sorted, int n, int64_t k, int topt, int H,
                                                     bool hybrid) {
   if (!hybrid) return n;

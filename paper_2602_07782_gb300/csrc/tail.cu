@@ -40,26 +40,52 @@ __device__ __forceinline__ int32_t trial_scale(int32_t lo, int32_t hi, int i) {
   return lo + (int32_t)(((int64_t)(i + 1) * (hi - lo)) / 16);
 }
 
-__global__ void __launch_bounds__(1024) tail_plan_kernel(const Pack *__restrict__ pp) {
+// Round r of the wave's tail: per atlas, the largest 2^r parked tasks (all
+// of them in the last round) that can still win -- a parked candidate below
+// the atlas's moot bound is finished as moot.  Only the largest successful
+// candidate can win once the tail's downscale is bounded by a grid step (a
+// smaller candidate's area-weighted scale stays below the larger one's), so
+// the tails are searched and pushed from the top down and the ones a
+// success makes moot are never searched.
+__global__ void __launch_bounds__(1024) tail_plan_kernel(const Pack *__restrict__ pp, int round, int rounds) {
   __shared__ int32_t count;
   const Pack &p = *pp;
   const int wave = *(volatile const int32_t *)p.cur_wave;
   if (threadIdx.x == 0) count = 0;
   __syncthreads();
-  const int64_t items = (int64_t)p.A * p.F;
-  for (int64_t it = threadIdx.x; it < items; it += blockDim.x) {
-    const int at = (int)(it / p.F);
+  const bool eval_all = (p.flags & TABI_F_EVAL_ALL) != 0;
+  const int quota = round + 1 >= rounds ? kScales : 1 << round;
+  for (int at = threadIdx.x; at < p.A; at += blockDim.x) {
     const WaveRange wr = wave_range(p.jtop[at], wave, p.F);
-    const int j = wr.hi - (int)(it % p.F);
-    if (j < wr.lo || p.tstate[at * kScales + j] != kTaskTailSearch) continue;
-    int32_t *cs = task_state(p, at, j, wave);
-    const int32_t S = 16 * (j + 1);
-    cs[kCsLo] = S - 15;  // the trial scales S - 14 .. S
-    cs[kCsHi] = S + 1;
-    cs[kCsMask] = 0;
-    cs[kCsRound] = 0;
-    cs[kCsKt] = 0;
-    p.ttask[atomicAdd(&count, 1)] = make_int4(at, j, 0, cs[kCsC0]);
+    int taken = 0;
+    for (int j = wr.hi; j >= wr.lo && j >= 0; --j) {
+      if (p.tstate[at * kScales + j] != kTaskTailSearch) continue;
+      int32_t *cs = task_state(p, at, j, wave);
+      if (!eval_all && *(volatile int32_t *)(p.found + at) > j) {  // moot: a larger candidate succeeded
+        ScaleOut &so = p.scale_out[at * kScales + j];
+        so.success = 0;
+        so.rows = cs[kCsHeadRows];
+        so.placed = cs[kCsC0];
+        so.score = cs[kCsCommitted];
+        so.knee_rows = cs[8];
+        so.knees = cs[9];
+        so.tail_rows = 0;
+        so.tail_k = 0;
+        so.tail_start = p.atl[at].n;
+        so.evaluated = 2;
+        p.tstate[at * kScales + j] = kTaskDone;
+        continue;
+      }
+      if (taken == quota) continue;
+      ++taken;
+      const int32_t S = 16 * (j + 1);
+      cs[kCsLo] = S - 15;  // the trial scales S - 14 .. S
+      cs[kCsHi] = S + 1;
+      cs[kCsMask] = 0;
+      cs[kCsRound] = round;
+      cs[kCsKt] = 0;
+      p.ttask[atomicAdd(&count, 1)] = make_int4(at, j, 0, cs[kCsC0]);
+    }
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -70,40 +96,59 @@ __global__ void __launch_bounds__(1024) tail_plan_kernel(const Pack *__restrict_
 
 // Whether the tail row starting at sorted chart s0 (len charts) fits W' when
 // laid from its near end at scale k: Algorithm 4's recurrence x_{t+1} = x_t
-// + w'_t - d_t, with compaction never left of the right edge of chart t-1,
-// the distances drawn on the fly.  a[0], a[1]: the warp's two row-constant
-// buffers (chart t and chart t + 1).
+// + w'_t - d_t, with compaction never left of the right edge of chart t-1.
+// A warp walks the row; its 32 / G aligned groups of G lanes each draw one
+// pair's rows at k on the fly (group_pair_reach) per step, so a step
+// advances 32 / G charts.  a: the warp's 2 (32 / G) row-constant buffers.
+template <int G>
 __device__ bool row_fits(const Pack &p, int s0, int len, int64_t k, int Wp, rmath::AxisK *a) {
+  constexpr int PG = 32 / G;
   const bool hc = (p.flags & TABI_F_HC) != 0;
   const int g = p.g;
+  const int lane = threadIdx.x & 31, grp = lane / G, glane = lane & (G - 1);
+  const unsigned gm = group_mask<G>();
   int64_t x = 0, xprev = 0, wprev = 0, ext = 0;
-  int cur = 0;
-  if (hc) setup_at_k(p, p.shape[s0], k, nullptr, &a[0]);
-  for (int t = 0; t < len; ++t) {
-    const int s = s0 + t;
-    const int64_t w = ((p.wq[s] * k + kFix - 1) >> 18) + 2 * g;
-    ext = ext > x + w ? ext : x + w;
-    if (ext > Wp) return false;
-    if (t + 1 == len) break;
-    int64_t nx = x + w;
-    if (hc) {
-      setup_at_k(p, p.shape[s + 1], k, nullptr, &a[cur ^ 1]);
-      const int32_t M = warp_pair_reach(a[cur], a[cur ^ 1], g);
-      const int64_t d = w - M > 0 ? w - M : 0;
-      nx = x + w - d;
-      if (t >= 1 && nx < xprev + wprev) nx = xprev + wprev;
-      __syncwarp();  // a[cur] is redrawn for the chart after next
-      cur ^= 1;
+  for (int t = 0; t < len; t += PG) {
+    // pair (u, u + 1) of this group, its offset x_{u+1} - x_u before the clamp
+    const int u = s0 + t + grp;
+    const bool has = t + grp < len;
+    int64_t w = 0, o = 0;
+    if (has) {
+      w = ((p.wq[u] * k + kFix - 1) >> 18) + 2 * g;
+      o = w;
     }
-    xprev = x;
-    wprev = w;
-    x = nx;
+    if (hc) {
+      const bool pair = t + grp + 1 < len;
+      if (pair) {
+        group_setup_rows<G>(p, p.shape[u], k, a[2 * grp], glane);
+        group_setup_rows<G>(p, p.shape[u + 1], k, a[2 * grp + 1], glane);
+      }
+      __syncwarp();
+      if (pair) {
+        const int32_t M = group_pair_reach<G>(a[2 * grp], a[2 * grp + 1], g, glane, gm);
+        o = w - M > 0 ? M : w;  // w - max(0, w - M)
+      }
+      __syncwarp();  // the buffers are redrawn next step
+    }
+    for (int q = 0; q < PG; ++q) {
+      const int64_t oq = __shfl_sync(0xffffffffu, o, q * G), wq = __shfl_sync(0xffffffffu, w, q * G);
+      const int tt = t + q;
+      if (tt >= len) break;
+      ext = ext > x + wq ? ext : x + wq;
+      if (ext > Wp) return false;
+      int64_t nx = x + oq;
+      if (hc && tt >= 1 && nx < xprev + wprev) nx = xprev + wprev;
+      xprev = x;
+      wprev = wq;
+      x = nx;
+    }
   }
   return true;
 }
 
+template <int G>
 __global__ void __launch_bounds__(kTailThreads) tail_trial_kernel(const Pack *__restrict__ pp) {
-  __shared__ rmath::AxisK axk[kTailWarps][2];
+  __shared__ rmath::AxisK axk[kTailWarps][2 * (32 / G)];
   const Pack &p = *pp;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int64_t gw = (int64_t)blockIdx.x * kTailWarps + wib, nw = (int64_t)gridDim.x * kTailWarps;
@@ -115,7 +160,6 @@ __global__ void __launch_bounds__(kTailThreads) tail_trial_kernel(const Pack *__
     if (p.tstate[at * kScales + j] != kTaskTailSearch) continue;
     const int32_t *cs = task_state(p, at, j, wave);
     const int32_t lo = cs[kCsLo], hi = cs[kCsHi];
-    if (hi <= lo + 1) continue;  // searched
     const AtlasDesc &ad = p.atl[at];
     const int cb = ad.cb, n = ad.n, Wp = ad.W + 2 * p.g;
     const int4 *place = p.place + (int64_t)j * p.N + cb;
@@ -125,8 +169,8 @@ __global__ void __launch_bounds__(kTailThreads) tail_trial_kernel(const Pack *__
       const int32_t w = place[s].w;
       if (!(w & kTailFirst)) continue;  // rows are tried from their first chart
       const int32_t k = trial_scale(lo, hi, i);
-      if (k <= lo || k >= hi || (i > 0 && k == trial_scale(lo, hi, i - 1))) continue;
-      if (!row_fits(p, cb + s, w & ~kTailFirst, k, Wp, axk[wib]) && lane == 0)
+      if (k <= lo || k >= hi) continue;
+      if (!row_fits<G>(p, cb + s, w & ~kTailFirst, k, Wp, axk[wib]) && lane == 0)
         atomicOr((unsigned *)(cs + kCsMask), 1u << i);
     }
   }
@@ -219,13 +263,19 @@ __global__ void __launch_bounds__(256) tail_compact_kernel(const Pack *__restric
 
 }  // namespace
 
-void launch_tail(const Pack *dp, const Launch &L, int F, cudaStream_t st) {
-  (void)F;
-  tail_plan_kernel<<<1, 1024, 0, st>>>(dp);
-  for (int r = 0; r < kTailRounds; ++r) {
-    tail_trial_kernel<<<L.sms * 4, kTailThreads, 0, st>>>(dp);
-    tail_pick_kernel<<<L.sms, 128, 0, st>>>(dp, r);
-  }
+int tail_rounds(int F) {
+  int r = 1;
+  while ((1 << r) - 1 < F && r < 7) ++r;  // quotas 1, 2, 4, ... then the rest
+  return r;
+}
+
+void launch_tail_round(const Pack *dp, const Launch &L, int F, int round, cudaStream_t st) {
+  tail_plan_kernel<<<1, 1024, 0, st>>>(dp, round, tail_rounds(F));
+  // groups of 8 lanes per pair while the gutter dilation (2g) stays inside
+  // one chunk of 8 rows, else a warp per pair
+  if (L.gutter <= 3) tail_trial_kernel<8><<<L.sms * 4, kTailThreads, 0, st>>>(dp);
+  else tail_trial_kernel<32><<<L.sms * 4, kTailThreads, 0, st>>>(dp);
+  tail_pick_kernel<<<L.sms, 128, 0, st>>>(dp, 0);
   tail_raster_kernel<<<L.sms * 3, kTailThreads, 0, st>>>(dp);
   tail_compact_kernel<<<L.sms * 8, 256, 0, st>>>(dp);
 }
