@@ -321,7 +321,9 @@ typedef struct tabi_server_config {
   int32_t device;      /* CUDA device                                        */
   int32_t lanes;       /* batches in flight at once, 1..64 (4)               */
   int32_t max_batch;   /* requests per batch, 1..TABI_MAX_BATCH (64)         */
-  int32_t pad;
+  int32_t check;       /* 1: count overlaps and gutter violations of every
+                          result on the device behind its batch
+                          (tabi_result.*_texels; the default), 0: not      */
   size_t arena_bytes;  /* device memory budget, split over the lanes (8 GiB) */
   tabi_params params;  /* for every request; scale_fanout 1..64 (8)          */
 } tabi_server_config;
@@ -333,12 +335,20 @@ typedef struct tabi_result {
   int32_t status;  /* tabi_status of the request (as in tabi_request)        */
   int32_t scale_k;
   int64_t t_submit_ns, t_start_ns, t_done_ns;
+  /* with tabi_server_config.check: the result's tabi_quality counts (all 0
+     for a correct packing); -1 when unchecked (check off, an error status,
+     or no room for the counter's planes) */
+  int64_t overlap_texels, gutter_texels, outside_texels;
 } tabi_result;
 
 typedef struct tabi_server_stats {
   int64_t submitted, launched, completed; /* requests                        */
   int64_t batches, max_batch;             /* batches launched, largest       */
   int64_t queued, busy_lanes;             /* now                             */
+  int64_t checked, check_violations;      /* results counted by the overlap
+                                             check, those with a nonzero
+                                             count                          */
+  int64_t check_ns;                       /* device time of the checks       */
 } tabi_server_stats;
 
 void tabi_server_config_default(tabi_server_config *cfg);
@@ -447,6 +457,34 @@ tabi_status tabi_inspect_atlas(tabi_ctx *ctx, int32_t atlas, int32_t what, int32
  * Timing adds event records between kernels; leave it off otherwise. */
 tabi_status tabi_stage_times(tabi_ctx *ctx, int32_t enable, double *stage_ms, int64_t *launches,
                              int64_t *packs);
+
+/* Quality check of a packing: the paper's overlap metric (App. B: texels
+ * covered by two or more charts, with and without the gutter dilation),
+ * counted on the device.  A texel (c, r) is covered by a placed chart iff
+ * its open square (c, c+1) x (r, r+1) meets the chart (see "Placement
+ * semantics"; each chart drawn at its placement's k); the dilated cover
+ * adds every texel within g (Chebyshev) of one and lies in the padded atlas
+ * (W + 2g) x (H + 2g), as the packer's gutters do.  A correct packing has
+ * all three counts 0. */
+typedef struct tabi_quality {
+  int64_t overlap_texels; /* atlas texels covered by two or more charts      */
+  int64_t gutter_texels;  /* padded texels covered by two or more dilated
+                             covers (gutter violations)                     */
+  int64_t outside_texels; /* cover texels outside [0, W) x [0, H)            */
+} tabi_quality;
+
+/* Count them for one atlas: DEVICE pointers offsets[n + 1], verts[2 nv]
+ * (as for tabi_pack_device) and place[n] (input order, e.g. the output of
+ * a pack); *out is host memory.  Uses the context's arena for its bit
+ * planes (4 bits per padded texel: TABI_ERR_OOM if it does not fit) and so
+ * ends the inspectability of the last pack (tabi_inspect returns
+ * TABI_ERR_INVALID_ARG until the next one).  Synchronous on `stream`.
+ * Returns TABI_OK, TABI_ERR_INVALID_ARG, TABI_ERR_OOM, TABI_ERR_CUDA or
+ * TABI_ERR_BUSY. */
+tabi_status tabi_check_packing_device(tabi_ctx *ctx, int32_t atlas_w, int32_t atlas_h, int32_t gutter,
+                                      int32_t n_charts, const uint32_t *offsets, const int32_t *verts,
+                                      int32_t n_verts, const tabi_placement *place, tabi_quality *out,
+                                      void *stream);
 
 /* Height sort with no device allocation.  The paper has no counterpart:
  * this entry point exists for callers that cannot call cudaMalloc -- engines

@@ -451,7 +451,7 @@ std::string check_request(const tabi_request &r, const tabi_params *params, int 
 // with stage timing on).  The caller holds the context and calls
 // batch_finish once the stream has reached this point.
 tabi_status batch_launch(tabi_ctx *ctx, const tabi_params *params, tabi_request *reqs, int32_t R, void *stream,
-                         bool host, const Tuning *force, Tuning *used, InFlight &fl) {
+                         bool host, const Tuning *force, Tuning *used, InFlight &fl, bool check) {
   fl = InFlight{};
   if (!valid_params(params)) return fail(ctx, TABI_ERR_INVALID_ARG, "bad params");
   if (!reqs || R < 1 || R > TABI_MAX_BATCH) return fail(ctx, TABI_ERR_INVALID_ARG, "bad request list");
@@ -634,8 +634,11 @@ tabi_status batch_launch(tabi_ctx *ctx, const tabi_params *params, tabi_request 
   if (npcs && (!dpieces || reinterpret_cast<char *>(dpieces) != reinterpret_cast<char *>(dpack) + pcs_off ||
                npcs > max_pieces))
     return fail(ctx, TABI_ERR_CUDA, "copy pieces misplaced");  // cannot happen: the carve is contiguous
-  if (!ensure_hstage(ctx, res_off + sizeof(PackResult) * (size_t)A))
-    return fail(ctx, TABI_ERR_CUDA, "pinned staging allocation failed");
+  // with the overlap counter: its atlas table (up) and counts (down)
+  const size_t chk_tab = round256(res_off + sizeof(PackResult) * (size_t)A);
+  const size_t chk_cnt = round256(chk_tab + sizeof(CheckAtlas) * (size_t)A);
+  const size_t stage_end = check ? chk_cnt + 24 * (size_t)A : res_off + sizeof(PackResult) * (size_t)A;
+  if (!ensure_hstage(ctx, stage_end)) return fail(ctx, TABI_ERR_CUDA, "pinned staging allocation failed");
   memcpy(ctx->hstage, &p, sizeof(Pack));
   memcpy(ctx->hstage + desc_off, desc.data(), sizeof(AtlasDesc) * (size_t)A);
   if (npcs) {
@@ -692,6 +695,50 @@ tabi_status batch_launch(tabi_ctx *ctx, const tabi_params *params, tabi_request 
     fl.timed = true;
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphLaunch");
   }
+  if (check) {
+    // App. B's overlap and gutter counts of every atlas, behind the pack:
+    // the table, the counts and the bit planes in the (now free) envelope
+    // pools; an atlas whose planes do not fit is left unchecked
+    char *pools = reinterpret_cast<char *>(p.colpool);
+    const size_t pool_bytes = 3 * (size_t)p.col_cap * sizeof(uint32_t);
+    const size_t tab_bytes = round256(sizeof(CheckAtlas) * (size_t)A), cnt_bytes = round256(24 * (size_t)A);
+    CheckAtlas *htab = reinterpret_cast<CheckAtlas *>(ctx->hstage + chk_tab);
+    int64_t words = 0;
+    const int64_t cap = pool_bytes > tab_bytes + cnt_bytes ? (int64_t)((pool_bytes - tab_bytes - cnt_bytes) / 4) : 0;
+    for (int i = 0; i < A; ++i) {
+      CheckAtlas &ca = htab[i];
+      fill_check_atlas(ca, desc[i].W, desc[i].H, p.g);
+      ca.offsets = desc[i].offsets;
+      ca.verts = desc[i].verts;
+      ca.place = desc[i].out;
+      ca.n = desc[i].n;
+      ca.cb = desc[i].cb;
+      ca.pad = 0;
+      const int64_t need = check_plane_words(desc[i].W, desc[i].H, p.g);
+      ca.plane0 = words + need <= cap ? words : -1;
+      if (ca.plane0 >= 0) words += need;
+    }
+    CheckAtlas *dtab = reinterpret_cast<CheckAtlas *>(pools);
+    unsigned long long *dcnt = reinterpret_cast<unsigned long long *>(pools + tab_bytes);
+    uint32_t *planes = reinterpret_cast<uint32_t *>(pools + tab_bytes + cnt_bytes);
+    if (!ctx->cev[0]) {
+      cudaEventCreate(&ctx->cev[0]);
+      cudaEventCreate(&ctx->cev[1]);
+    }
+    cudaEventRecord(ctx->cev[0], st);
+    e = cudaMemcpyAsync(dtab, htab, sizeof(CheckAtlas) * (size_t)A, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dcnt, 0, 24 * (size_t)A, st);
+    if (e == cudaSuccess) {
+      launch_check(dtab, A, p.catl, p.N, planes, words, dcnt, ctx->sms, st);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(ctx->hstage + chk_cnt, dcnt, 24 * (size_t)A, cudaMemcpyDeviceToHost, st);
+    cudaEventRecord(ctx->cev[1], st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "overlap check");
+    fl.checked = true;
+    fl.check_off = chk_cnt;
+  }
   PackResult *hres = reinterpret_cast<PackResult *>(ctx->hstage + res_off);
   e = cudaMemcpyAsync(hres, p.result, sizeof(PackResult) * (size_t)A, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess && !pout.empty()) {
@@ -731,6 +778,14 @@ tabi_status batch_finish(tabi_ctx *ctx, tabi_request *reqs, int32_t R, InFlight 
   ctx->has_last = true;
   ctx->last_error = fl.first_error;
   return TABI_OK;
+}
+
+void batch_quality(tabi_ctx *ctx, const InFlight &fl, int r, int64_t out[3]) {
+  out[0] = out[1] = out[2] = -1;
+  if (!fl.checked || r < 0 || r >= (int)ctx->last_map.size() || ctx->last_map[r] < 0) return;
+  const unsigned long long *c = reinterpret_cast<const unsigned long long *>(ctx->hstage + fl.check_off);
+  const int i = ctx->last_map[r];
+  for (int q = 0; q < 3; ++q) out[q] = c[3 * i + q] == ~0ull ? -1 : (int64_t)c[3 * i + q];
 }
 
 namespace {
@@ -853,6 +908,8 @@ void tabi_ctx_destroy(tabi_ctx *c) {
   for (GraphEntry &g : c->graphs) cudaGraphExecDestroy(g.exec);
   for (int i = 0; i < c->n_ev; ++i) cudaEventDestroy(c->ev[i]);
   for (cudaEvent_t ev : c->tev)
+    if (ev) cudaEventDestroy(ev);
+  for (cudaEvent_t ev : c->cev)
     if (ev) cudaEventDestroy(ev);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   if (c->owned) cudaFree(c->arena);
@@ -1130,6 +1187,50 @@ tabi_status tabi_inspect_atlas(tabi_ctx *ctx, int32_t atlas, int32_t what, int32
     int32_t *pm = (int32_t *)dst;
     for (size_t s = 0; s < n; ++s) pm[s] -= ad.cb;
   }
+  return TABI_OK;
+}
+
+tabi_status tabi_check_packing_device(tabi_ctx *ctx, int32_t W, int32_t H, int32_t gutter, int32_t n,
+                                      const uint32_t *offsets, const int32_t *verts, int32_t nv,
+                                      const tabi_placement *place, tabi_quality *out, void *stream) {
+  if (!ctx) return TABI_ERR_INVALID_ARG;
+  if (!out || !offsets || !verts || !place || n < 1 || nv < 3 || W < 1 || H < 1 || W > kMaxAtlas ||
+      H > kMaxAtlas || gutter < 0 || gutter > kMaxGutter)
+    return fail(ctx, TABI_ERR_INVALID_ARG, "bad check arguments");
+  Guard guard(ctx);
+  if (!guard.ok) return fail(ctx, TABI_ERR_BUSY, "context in use");
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
+  const cudaStream_t st = (cudaStream_t)stream;
+  const int64_t words = check_plane_words(W, H, gutter);
+  if (512 + (size_t)words * 4 > ctx->arena_bytes) return fail(ctx, TABI_ERR_OOM, "arena too small for the check");
+  if (!ensure_hstage(ctx, 512)) return fail(ctx, TABI_ERR_CUDA, "pinned staging allocation failed");
+  ctx->has_last = false;  // the arena is reused: the last pack can no longer be inspected
+  CheckAtlas *h = reinterpret_cast<CheckAtlas *>(ctx->hstage);
+  fill_check_atlas(*h, W, H, gutter);
+  h->offsets = offsets;
+  h->verts = verts;
+  h->place = place;
+  h->n = n;
+  h->cb = 0;
+  h->pad = 0;
+  h->plane0 = 0;
+  CheckAtlas *dtab = reinterpret_cast<CheckAtlas *>(ctx->arena);
+  unsigned long long *dcnt = reinterpret_cast<unsigned long long *>(ctx->arena + 256);
+  uint32_t *planes = reinterpret_cast<uint32_t *>(ctx->arena + 512);
+  unsigned long long *hcnt = reinterpret_cast<unsigned long long *>(ctx->hstage + 256);
+  e = cudaMemcpyAsync(dtab, h, sizeof(CheckAtlas), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(dcnt, 0, 24, st);
+  if (e == cudaSuccess) {
+    launch_check(dtab, 1, nullptr, n, planes, words, dcnt, ctx->sms, st);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hcnt, dcnt, 24, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "overlap check");
+  out->overlap_texels = (int64_t)hcnt[0];
+  out->gutter_texels = (int64_t)hcnt[1];
+  out->outside_texels = (int64_t)hcnt[2];
   return TABI_OK;
 }
 

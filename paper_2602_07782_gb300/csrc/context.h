@@ -52,6 +52,7 @@ struct tabi_ctx {
   std::vector<tabi::GraphEntry> graphs;
   std::vector<tabi::TuneEntry> tuned;  // autotuner results per batch class
   cudaEvent_t tev[2] = {};             // batch timing (autotuner)
+  cudaEvent_t cev[2] = {};             // the overlap counter behind a batch (serving)
   // pinned host staging: the batch record going up, the results coming down
   char *hstage = nullptr;
   size_t hstage_bytes = 0;
@@ -85,10 +86,16 @@ struct InFlight {
   std::string first_error;       // first host-check failure
   int A = 0;                     // atlases launched (0: nothing launched)
   bool timed = false;            // graph launch bracketed by tev[0..1]
+  bool checked = false;          // the overlap counter ran behind the pack (cev[0..1] around it)
+  size_t check_off = 0;          // its counts (3 x uint64 per atlas) in the pinned staging
 };
 
 }  // namespace tabi
 
 tabi_status batch_launch(tabi_ctx *ctx, const tabi_params *params, tabi_request *reqs, int32_t R, void *stream,
-                         bool host, const tabi::Tuning *force, tabi::Tuning *used, tabi::InFlight &fl);
+                         bool host, const tabi::Tuning *force, tabi::Tuning *used, tabi::InFlight &fl,
+                         bool check = false);
+// The overlap and gutter counts (overlap, gutter, outside; -1: unchecked) of
+// request r of a finished batch that ran with check = true.
+void batch_quality(tabi_ctx *ctx, const tabi::InFlight &fl, int r, int64_t out[3]);
 tabi_status batch_finish(tabi_ctx *ctx, tabi_request *reqs, int32_t R, tabi::InFlight &fl, float *ms_out);

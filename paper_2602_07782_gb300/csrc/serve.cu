@@ -46,6 +46,7 @@ struct Ticket {
   size_t est = 0;      // arena bytes the request may need
   int64_t t_submit = 0, t_start = 0, t_done = 0;
   int32_t status = TABI_PENDING, k = 0;
+  int64_t quality[3] = {-1, -1, -1};  // overlap, gutter, outside texels (-1: unchecked)
   bool done = false;
 };
 
@@ -148,11 +149,23 @@ void finish_ticket(tabi_server *s, uint64_t id, int32_t status, int32_t k) {
 void finish_lane(tabi_server *s, Lane &ln) {
   const int R = (int)ln.ids.size();
   batch_finish(ln.ctx, ln.reqs.data(), R, ln.fl, nullptr);
+  if (ln.fl.checked) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, ln.ctx->cev[0], ln.ctx->cev[1]) == cudaSuccess)
+      s->stats.check_ns += (int64_t)(ms * 1e6f);
+  }
   for (int i = 0; i < R; ++i) {
     const tabi_request &r = ln.reqs[i];
     Ticket &t = s->tickets[ln.ids[i]];
     if (r.status == TABI_OK)
       memcpy(t.req.out, r.out, sizeof(tabi_placement) * (size_t)r.n_charts);
+    if (r.status == TABI_OK && ln.fl.checked) {
+      batch_quality(ln.ctx, ln.fl, i, t.quality);
+      if (t.quality[0] >= 0) {
+        s->stats.checked += 1;
+        s->stats.check_violations += (t.quality[0] | t.quality[1] | t.quality[2]) != 0;
+      }
+    }
     finish_ticket(s, ln.ids[i], r.status, r.scale_k);
   }
   s->stats.completed += R;
@@ -205,7 +218,7 @@ bool launch_lane(tabi_server *s, Lane &ln) {
     p += align16(sizeof(tabi_placement) * (size_t)r.n_charts);
   }
   tabi_status st = batch_launch(ln.ctx, &s->params, ln.reqs.data(), (int)ln.reqs.size(), ln.st, true, nullptr,
-                                nullptr, ln.fl);
+                                nullptr, ln.fl, s->cfg.check != 0);
   if (st == TABI_OK) {
     auto *arg = new std::pair<tabi_server *, Lane *>(s, &ln);
     if (cudaLaunchHostFunc(ln.st, lane_finished, arg) != cudaSuccess) {
@@ -273,6 +286,9 @@ tabi_status take_result(tabi_server *s, uint64_t ticket, tabi_result *res) {
     res->t_submit_ns = t.t_submit;
     res->t_start_ns = t.t_start;
     res->t_done_ns = t.t_done;
+    res->overlap_texels = t.quality[0];
+    res->gutter_texels = t.quality[1];
+    res->outside_texels = t.quality[2];
   }
   s->tickets.erase(it);
   return TABI_OK;
@@ -289,6 +305,7 @@ void tabi_server_config_default(tabi_server_config *c) {
   c->arena_bytes = (size_t)8 << 30;
   c->lanes = 4;
   c->max_batch = 64;
+  c->check = 1;
   tabi_params_default(&c->params);
   c->params.scale_fanout = 8;
 }
@@ -298,7 +315,8 @@ tabi_status tabi_server_create(tabi_server **out, const tabi_server_config *cfg)
   *out = nullptr;
   if (cfg->lanes < 1 || cfg->lanes > 64 || cfg->max_batch < 1 || cfg->max_batch > TABI_MAX_BATCH ||
       cfg->arena_bytes < ((size_t)cfg->lanes << 24) || cfg->params.scale_fanout < 1 ||
-      cfg->params.scale_fanout > kScales || cfg->params.version != TABI_PARAMS_VERSION)
+      cfg->params.scale_fanout > kScales || cfg->params.version != TABI_PARAMS_VERSION || cfg->check < 0 ||
+      cfg->check > 1)
     return TABI_ERR_INVALID_ARG;
   if (cudaSetDevice(cfg->device) != cudaSuccess) return TABI_ERR_INVALID_ARG;
   auto *s = new tabi_server();

@@ -148,6 +148,27 @@ struct Pack {
   int32_t *tcount;              // [1] how many
 };
 
+// One atlas for the overlap and gutter counter (check.cu): its charts
+// (device pointers, input order), placements, size and gutter, and where
+// its four bit planes start in the planes buffer (-1: no room, unchecked).
+struct CheckAtlas {
+  const uint32_t *offsets;
+  const int32_t *verts;
+  const tabi_placement *place;
+  int32_t n, W, H, g;
+  int32_t wpp, wpd;  // words per plain row (W bits), per padded row (W + 2g bits)
+  int32_t cb, pad;   // first chart in the batch's chart index space
+  int64_t plane0;
+};
+int64_t check_plane_words(int W, int H, int g);
+void fill_check_atlas(CheckAtlas &ca, int W, int H, int g);
+// Counts per atlas (3 x uint64: plain texels covered twice, dilated
+// texels covered twice, cover texels outside the atlas; all ~0 when the
+// atlas was not checked); counts must be zero on entry.  catl: the atlas
+// of each of the N charts (NULL: all in atlas 0).
+void launch_check(const CheckAtlas *datl, int A, const int32_t *catl, int64_t N, uint32_t *planes, int64_t words,
+                  unsigned long long *counts, int sms, cudaStream_t st);
+
 // Region of (atlas a, candidate j) in the column / row pools.
 __host__ __device__ __forceinline__ int64_t region(int a, int j, int which) {
   return ((int64_t)a * kScales + j) * 2 + which;

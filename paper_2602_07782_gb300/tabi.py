@@ -51,17 +51,25 @@ class Tuning(ctypes.Structure):
 
 class ServerConfig(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int32), ("lanes", ctypes.c_int32), ("max_batch", ctypes.c_int32),
-                ("pad", ctypes.c_int32), ("arena_bytes", ctypes.c_size_t), ("params", Params)]
+                ("check", ctypes.c_int32), ("arena_bytes", ctypes.c_size_t), ("params", Params)]
 
 
 class Result(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("scale_k", ctypes.c_int32), ("t_submit_ns", ctypes.c_int64),
-                ("t_start_ns", ctypes.c_int64), ("t_done_ns", ctypes.c_int64)]
+                ("t_start_ns", ctypes.c_int64), ("t_done_ns", ctypes.c_int64),
+                ("overlap_texels", ctypes.c_int64), ("gutter_texels", ctypes.c_int64),
+                ("outside_texels", ctypes.c_int64)]
 
 
 class ServerStats(ctypes.Structure):
     _fields_ = [(f, ctypes.c_int64) for f in ("submitted", "launched", "completed", "batches", "max_batch",
-                                              "queued", "busy_lanes")]
+                                              "queued", "busy_lanes", "checked", "check_violations",
+                                              "check_ns")]
+
+
+class Quality(ctypes.Structure):
+    _fields_ = [("overlap_texels", ctypes.c_int64), ("gutter_texels", ctypes.c_int64),
+                ("outside_texels", ctypes.c_int64)]
 
 
 PLACEMENT_DTYPE = np.dtype([("x", "<i4"), ("y", "<i4"), ("rot90", "u1"), ("flip_x", "u1"),
@@ -79,7 +87,8 @@ EXPORTS = ["tabi_params_default", "tabi_ctx_create", "tabi_ctx_destroy", "tabi_l
            "tabi_status_str", "tabi_arena_bytes", "tabi_pack", "tabi_pack_device", "tabi_pack_batch",
            "tabi_pack_batch_device", "tabi_pack_batch_shaped", "tabi_autotune", "tabi_inspect", "tabi_inspect_atlas",
            "tabi_stage_times", "tabi_server_config_default", "tabi_server_create", "tabi_server_destroy",
-           "tabi_submit", "tabi_poll", "tabi_wait", "tabi_server_get_stats"]
+           "tabi_submit", "tabi_poll", "tabi_wait", "tabi_server_get_stats", "tabi_check_packing_device",
+           "tabi_sort_heights_noalloc"]
 STAGES = ["prep", "sort", "layout", "raster", "hcompact", "rowloop", "select", "pack"]
 
 _lib = None
@@ -133,6 +142,8 @@ def load(path: str = LIB_PATH):
     lib.tabi_inspect_atlas.restype = ctypes.c_int
     lib.tabi_stage_times.argtypes = [P, i32, P, P, P]
     lib.tabi_stage_times.restype = ctypes.c_int
+    lib.tabi_check_packing_device.argtypes = [P, i32, i32, i32, i32, P, P, i32, P, P, P]
+    lib.tabi_check_packing_device.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -262,6 +273,17 @@ class Context:
                                        nv, ctypes.c_void_p(out_t.data_ptr()), ctypes.byref(k),
                                        ctypes.c_void_p(_stream_ptr(stream)))
         return int(st), int(k.value)
+
+    def check_packing_device(self, W, H, gutter, n, nv, offs_t, verts_t, place_t, stream=None):
+        """tabi_check_packing_device on CUDA tensors (offsets, vertices,
+        placements as a uint8 view): the paper's overlap metric as
+        (overlap, gutter, outside) texel counts."""
+        q = Quality()
+        st = self.lib.tabi_check_packing_device(self.h, W, H, gutter, n, ctypes.c_void_p(offs_t.data_ptr()),
+                                                ctypes.c_void_p(verts_t.data_ptr()), nv,
+                                                ctypes.c_void_p(place_t.data_ptr()), ctypes.byref(q),
+                                                ctypes.c_void_p(_stream_ptr(stream)))
+        return int(st), (int(q.overlap_texels), int(q.gutter_texels), int(q.outside_texels))
 
     def stage_times(self, enable: bool):
         """Accumulated per-stage device ms and launch counts since the last
