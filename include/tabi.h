@@ -476,7 +476,8 @@ typedef struct tabi_quality {
 /* Count them for one atlas: DEVICE pointers offsets[n + 1], verts[2 nv]
  * (as for tabi_pack_device) and place[n] (input order, e.g. the output of
  * a pack); *out is host memory.  Uses the context's arena for its bit
- * planes (4 bits per padded texel: TABI_ERR_OOM if it does not fit) and so
+ * planes (4 bits per padded texel) and 40 bytes per chart (TABI_ERR_OOM if
+ * they do not fit) and so
  * ends the inspectability of the last pack (tabi_inspect returns
  * TABI_ERR_INVALID_ARG until the next one).  Synchronous on `stream`.
  * Returns TABI_OK, TABI_ERR_INVALID_ARG, TABI_ERR_OOM, TABI_ERR_CUDA or
@@ -485,6 +486,16 @@ tabi_status tabi_check_packing_device(tabi_ctx *ctx, int32_t atlas_w, int32_t at
                                       int32_t n_charts, const uint32_t *offsets, const int32_t *verts,
                                       int32_t n_verts, const tabi_placement *place, tabi_quality *out,
                                       void *stream);
+
+/* Measurement aid (no counterpart in the paper): the device's rate of the
+ * 32-bit integer operation mix the envelope rasterizer is made of (add,
+ * min, max, multiply-high, exclusive or, compare-select, subtract), in
+ * operations per second over all multiprocessors, best of five timed runs
+ * (CUDA events) of a kernel with eight independent chains per thread.  It
+ * is the peak the rasterizer's integer-issue roofline is taken against.
+ * Allocates 4 bytes of device memory for the run.  Returns TABI_OK,
+ * TABI_ERR_INVALID_ARG or TABI_ERR_CUDA. */
+tabi_status tabi_measure_int_rate(int32_t device, double *ops_per_second);
 
 /* Height sort with no device allocation.  The paper has no counterpart:
  * this entry point exists for callers that cannot call cudaMalloc -- engines

@@ -79,6 +79,7 @@ def lib():
         _lib.oracle_pack.argtypes = [i32, P, P, i32, i32, P, i32, P, P, P, P]
         _lib.oracle_correct_y.argtypes = [i32, i32, P, P, P]
         _lib.oracle_obb_table.argtypes = [P]
+        _lib.oracle_chart_area2.argtypes = [i32, P, P, P]
         for f in ("oracle_prep", "oracle_envelope", "oracle_envelope_padded", "oracle_hcompact",
                   "oracle_scale_pairs", "oracle_pack_scale", "oracle_pack"):
             getattr(_lib, f).restype = ctypes.c_int
@@ -215,6 +216,15 @@ def pack(cs, params=None, all_scales=False):
     lo, hi = (int(v) for v in stats[8:12].view(np.int64))
     score = (hi << 64) + (lo & ((1 << 64) - 1))
     return PackResult(int(st), int(out_k[0]), place, succ if all_scales else None, stats[:8].copy(), score)
+
+
+def chart_area2(cs):
+    """Twice the area of every chart's loop (int64, input order): the
+    weights of the area-weighted choice in pack()."""
+    out = np.zeros(cs.n, np.int64)
+    lib().oracle_chart_area2(cs.n, _p(np.ascontiguousarray(cs.offsets, np.uint32)),
+                             _p(np.ascontiguousarray(cs.verts, np.int32)), _p(out))
+    return out
 
 
 def _pack_one(args):

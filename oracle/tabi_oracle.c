@@ -1160,4 +1160,11 @@ int oracle_pack(int32_t n, const uint32_t *offsets, const int32_t *verts, int32_
   return best_k ? 0 : 2;
 }
 
+/* Twice the area of every chart's loop, input order: the weights of the  */
+/* area-weighted mean scale above.                                          */
+void oracle_chart_area2(int32_t n, const uint32_t *offsets, const int32_t *verts, int64_t *out) {
+  for (int c = 0; c < n; ++c)
+    out[c] = loop_area2((int)(offsets[c + 1] - offsets[c]), verts + 2 * offsets[c]);
+}
+
 int oracle_rec_fields(void) { return OR_REC; }

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libtabi.so")
-SOURCES = ["prep.cu", "raster.cu", "rowloop.cu", "tail.cu", "check.cu", "api.cu", "serve.cu", "noalloc.cu"]
+SOURCES = ["prep.cu", "raster.cu", "rowloop.cu", "tail.cu", "check.cu", "api.cu", "serve.cu", "noalloc.cu", "measure.cu"]
 HEADERS = ["tabi_internal.cuh", "raster_math.cuh", "raster_dev.cuh", "context.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]

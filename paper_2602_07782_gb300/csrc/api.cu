@@ -702,9 +702,11 @@ tabi_status batch_launch(tabi_ctx *ctx, const tabi_params *params, tabi_request 
     char *pools = reinterpret_cast<char *>(p.colpool);
     const size_t pool_bytes = 3 * (size_t)p.col_cap * sizeof(uint32_t);
     const size_t tab_bytes = round256(sizeof(CheckAtlas) * (size_t)A), cnt_bytes = round256(24 * (size_t)A);
+    const size_t scr_bytes = check_scratch_bytes(p.N);
     CheckAtlas *htab = reinterpret_cast<CheckAtlas *>(ctx->hstage + chk_tab);
     int64_t words = 0;
-    const int64_t cap = pool_bytes > tab_bytes + cnt_bytes ? (int64_t)((pool_bytes - tab_bytes - cnt_bytes) / 4) : 0;
+    const size_t fixed = tab_bytes + cnt_bytes + scr_bytes;
+    const int64_t cap = pool_bytes > fixed ? (int64_t)((pool_bytes - fixed) / 4) : -1;
     for (int i = 0; i < A; ++i) {
       CheckAtlas &ca = htab[i];
       fill_check_atlas(ca, desc[i].W, desc[i].H, p.g);
@@ -715,22 +717,27 @@ tabi_status batch_launch(tabi_ctx *ctx, const tabi_params *params, tabi_request 
       ca.cb = desc[i].cb;
       ca.pad = 0;
       const int64_t need = check_plane_words(desc[i].W, desc[i].H, p.g);
-      ca.plane0 = words + need <= cap ? words : -1;
+      ca.plane0 = cap >= 0 && words + need <= cap ? words : -1;
       if (ca.plane0 >= 0) words += need;
     }
     CheckAtlas *dtab = reinterpret_cast<CheckAtlas *>(pools);
     unsigned long long *dcnt = reinterpret_cast<unsigned long long *>(pools + tab_bytes);
-    uint32_t *planes = reinterpret_cast<uint32_t *>(pools + tab_bytes + cnt_bytes);
+    void *scratch = pools + tab_bytes + cnt_bytes;
+    uint32_t *planes = reinterpret_cast<uint32_t *>(pools + fixed);
     if (!ctx->cev[0]) {
       cudaEventCreate(&ctx->cev[0]);
       cudaEventCreate(&ctx->cev[1]);
     }
     cudaEventRecord(ctx->cev[0], st);
     e = cudaMemcpyAsync(dtab, htab, sizeof(CheckAtlas) * (size_t)A, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(dcnt, 0, 24 * (size_t)A, st);
-    if (e == cudaSuccess) {
-      launch_check(dtab, A, p.catl, p.N, planes, words, dcnt, ctx->sms, st);
-      e = cudaGetLastError();
+    if (cap < 0) {  // no room for the charts' scratch: the batch stays unchecked
+      if (e == cudaSuccess) e = cudaMemsetAsync(dcnt, 0xff, 24 * (size_t)A, st);
+    } else {
+      if (e == cudaSuccess) e = cudaMemsetAsync(dcnt, 0, 24 * (size_t)A, st);
+      if (e == cudaSuccess) {
+        launch_check(dtab, A, p.catl, p.N, p.g, planes, words, scratch, dcnt, ctx->sms, st);
+        e = cudaGetLastError();
+      }
     }
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(ctx->hstage + chk_cnt, dcnt, 24 * (size_t)A, cudaMemcpyDeviceToHost, st);
@@ -1203,7 +1210,9 @@ tabi_status tabi_check_packing_device(tabi_ctx *ctx, int32_t W, int32_t H, int32
   if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
   const cudaStream_t st = (cudaStream_t)stream;
   const int64_t words = check_plane_words(W, H, gutter);
-  if (512 + (size_t)words * 4 > ctx->arena_bytes) return fail(ctx, TABI_ERR_OOM, "arena too small for the check");
+  const size_t scr_bytes = check_scratch_bytes(n);
+  if (512 + scr_bytes + (size_t)words * 4 > ctx->arena_bytes)
+    return fail(ctx, TABI_ERR_OOM, "arena too small for the check");
   if (!ensure_hstage(ctx, 512)) return fail(ctx, TABI_ERR_CUDA, "pinned staging allocation failed");
   ctx->has_last = false;  // the arena is reused: the last pack can no longer be inspected
   CheckAtlas *h = reinterpret_cast<CheckAtlas *>(ctx->hstage);
@@ -1217,12 +1226,13 @@ tabi_status tabi_check_packing_device(tabi_ctx *ctx, int32_t W, int32_t H, int32
   h->plane0 = 0;
   CheckAtlas *dtab = reinterpret_cast<CheckAtlas *>(ctx->arena);
   unsigned long long *dcnt = reinterpret_cast<unsigned long long *>(ctx->arena + 256);
-  uint32_t *planes = reinterpret_cast<uint32_t *>(ctx->arena + 512);
+  void *scratch = ctx->arena + 512;
+  uint32_t *planes = reinterpret_cast<uint32_t *>(ctx->arena + 512 + scr_bytes);
   unsigned long long *hcnt = reinterpret_cast<unsigned long long *>(ctx->hstage + 256);
   e = cudaMemcpyAsync(dtab, h, sizeof(CheckAtlas), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(dcnt, 0, 24, st);
   if (e == cudaSuccess) {
-    launch_check(dtab, 1, nullptr, n, planes, words, dcnt, ctx->sms, st);
+    launch_check(dtab, 1, nullptr, n, gutter, planes, words, scratch, dcnt, ctx->sms, st);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaMemcpyAsync(hcnt, dcnt, 24, cudaMemcpyDeviceToHost, st);

@@ -165,9 +165,12 @@ void fill_check_atlas(CheckAtlas &ca, int W, int H, int g);
 // Counts per atlas (3 x uint64: plain texels covered twice, dilated
 // texels covered twice, cover texels outside the atlas; all ~0 when the
 // atlas was not checked); counts must be zero on entry.  catl: the atlas
-// of each of the N charts (NULL: all in atlas 0).
-void launch_check(const CheckAtlas *datl, int A, const int32_t *catl, int64_t N, uint32_t *planes, int64_t words,
-                  unsigned long long *counts, int sms, cudaStream_t st);
+// of each of the N charts (NULL: all in atlas 0); gmax: the largest
+// gutter of the atlases (sets the row masks' shared memory); scratch:
+// check_scratch_bytes(N) bytes of device memory (256-byte aligned).
+size_t check_scratch_bytes(int64_t N);
+void launch_check(const CheckAtlas *datl, int A, const int32_t *catl, int64_t N, int gmax, uint32_t *planes,
+                  int64_t words, void *scratch, unsigned long long *counts, int sms, cudaStream_t st);
 
 // Region of (atlas a, candidate j) in the column / row pools.
 __host__ __device__ __forceinline__ int64_t region(int a, int j, int which) {

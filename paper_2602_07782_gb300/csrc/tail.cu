@@ -101,7 +101,8 @@ __global__ void __launch_bounds__(1024) tail_plan_kernel(const Pack *__restrict_
 // pair's rows at k on the fly (group_pair_reach) per step, so a step
 // advances 32 / G charts.  a: the warp's 2 (32 / G) row-constant buffers.
 template <int G>
-__device__ bool row_fits(const Pack &p, int s0, int len, int64_t k, int Wp, rmath::AxisK *a) {
+__device__ bool row_fits(const Pack &p, int s0, int len, int64_t k, int Wp, rmath::AxisK *a,
+                         const volatile int32_t *mask, int bit) {
   constexpr int PG = 32 / G;
   const bool hc = (p.flags & TABI_F_HC) != 0;
   const int g = p.g;
@@ -109,6 +110,8 @@ __device__ bool row_fits(const Pack &p, int s0, int len, int64_t k, int Wp, rmat
   const unsigned gm = group_mask<G>();
   int64_t x = 0, xprev = 0, wprev = 0, ext = 0;
   for (int t = 0; t < len; t += PG) {
+    // another row has already failed at this scale: the outcome is known
+    if (__shfl_sync(0xffffffffu, lane == 0 ? (*mask >> bit) & 1 : 0, 0)) return true;
     // pair (u, u + 1) of this group, its offset x_{u+1} - x_u before the clamp
     const int u = s0 + t + grp;
     const bool has = t + grp < len;
@@ -170,7 +173,11 @@ __global__ void __launch_bounds__(kTailThreads) tail_trial_kernel(const Pack *__
       if (!(w & kTailFirst)) continue;  // rows are tried from their first chart
       const int32_t k = trial_scale(lo, hi, i);
       if (k <= lo || k >= hi) continue;
-      if (!row_fits<G>(p, cb + s, w & ~kTailFirst, k, Wp, axk[wib]) && lane == 0)
+      // a scale at which some row has failed is decided: its other rows are
+      // skipped (the mask only gathers failures, so the outcome is the same)
+      const volatile int32_t *mask = cs + kCsMask;
+      if ((*mask >> i) & 1) continue;
+      if (!row_fits<G>(p, cb + s, w & ~kTailFirst, k, Wp, axk[wib], mask, i) && lane == 0)
         atomicOr((unsigned *)(cs + kCsMask), 1u << i);
     }
   }

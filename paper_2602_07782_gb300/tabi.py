@@ -88,7 +88,7 @@ EXPORTS = ["tabi_params_default", "tabi_ctx_create", "tabi_ctx_destroy", "tabi_l
            "tabi_pack_batch_device", "tabi_pack_batch_shaped", "tabi_autotune", "tabi_inspect", "tabi_inspect_atlas",
            "tabi_stage_times", "tabi_server_config_default", "tabi_server_create", "tabi_server_destroy",
            "tabi_submit", "tabi_poll", "tabi_wait", "tabi_server_get_stats", "tabi_check_packing_device",
-           "tabi_sort_heights_noalloc"]
+           "tabi_sort_heights_noalloc", "tabi_measure_int_rate"]
 STAGES = ["prep", "sort", "layout", "raster", "hcompact", "rowloop", "select", "pack"]
 
 _lib = None
@@ -144,6 +144,8 @@ def load(path: str = LIB_PATH):
     lib.tabi_stage_times.restype = ctypes.c_int
     lib.tabi_check_packing_device.argtypes = [P, i32, i32, i32, i32, P, P, i32, P, P, P]
     lib.tabi_check_packing_device.restype = ctypes.c_int
+    lib.tabi_measure_int_rate.argtypes = [i32, ctypes.POINTER(ctypes.c_double)]
+    lib.tabi_measure_int_rate.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -154,6 +156,16 @@ def params_default(**kw) -> Params:
     for k, v in kw.items():
         setattr(p, k, v)
     return p
+
+
+def measure_int_rate(device: int = 0) -> float:
+    """tabi_measure_int_rate: the device's integer-operation rate of the
+    rasterizer's mix, operations per second."""
+    v = ctypes.c_double(0.0)
+    st = load().tabi_measure_int_rate(device, ctypes.byref(v))
+    if st != TABI_OK:
+        raise RuntimeError(f"tabi_measure_int_rate failed: {status_str(st)}")
+    return float(v.value)
 
 
 def status_str(s: int) -> str:

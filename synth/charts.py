@@ -380,3 +380,78 @@ WORKLOADS = {
     "pareto20k": pareto20k,
     "knees": knees,
 }
+
+
+# --------------------------------------------------------------------------
+# vectorised star sets for the served stream (same shape law as ``stars``,
+# drawn with whole-request array operations so that a stream of tens of
+# millions of charts is generated in seconds; a different random stream
+# from ``stars``, so the sets differ from it chart by chart)
+# --------------------------------------------------------------------------
+
+def stars_fast(seed: int, n: int, atlas: int, sigma: float = 1.0, density: float = DENSITY) -> ChartSet:
+    """Star-shaped charts as ``stars`` draws them (6-64 vertices, radii
+    jittered +-40 %, angular jitter +-30 % of a step, aspect log-uniform
+    1:1-1:8, random rotation, log-normal box areas with the summed box
+    area ``density`` x the atlas area), every vertex of the set in one
+    flat array."""
+    rng = np.random.default_rng([seed, 8, n, atlas])
+    mu = math.log(density * atlas * atlas / n) - sigma * sigma / 2.0
+    area = rng.lognormal(mu, sigma, n)
+    aspect = np.exp(rng.uniform(0.0, math.log(8.0), n))
+    nv = rng.integers(6, 65, n)
+    theta = rng.uniform(0.0, math.pi, n)
+    start = np.zeros(n + 1, np.int64)
+    np.cumsum(nv, out=start[1:])
+    T = int(start[-1])
+    seg = np.repeat(np.arange(n), nv)
+    idx = np.arange(T) - start[seg]
+    step = (2.0 * math.pi) / nv[seg]
+    ang = (idx + rng.uniform(-0.3, 0.3, T)) * step
+    rad = 1.0 + rng.uniform(-0.4, 0.4, T)
+    x0 = rad * np.cos(ang)
+    y0 = rad * np.sin(ang) * aspect[seg]
+    c, s = np.cos(theta)[seg], np.sin(theta)[seg]
+    x = x0 * c - y0 * s
+    y = x0 * s + y0 * c
+    st = start[:-1]
+    mnx, mny = np.minimum.reduceat(x, st), np.minimum.reduceat(y, st)
+    exx = np.maximum.reduceat(x, st) - mnx
+    exy = np.maximum.reduceat(y, st) - mny
+    max_side = min(4000.0, 2.0 * atlas)
+    sc = np.sqrt(area / np.maximum(exx * exy, 1e-9))
+    box_w = np.maximum(Q, np.rint(np.clip(exx * sc, 1.0, max_side) * Q)).astype(np.int64)
+    box_h = np.maximum(Q, np.rint(np.clip(exy * sc, 1.0, max_side) * Q)).astype(np.int64)
+    X = np.rint((x - mnx[seg]) / exx[seg] * box_w[seg]).astype(np.int64)
+    Y = np.rint((y - mny[seg]) / exy[seg] * box_h[seg]).astype(np.int64)
+    keep = np.ones(T, bool)
+    keep[1:] = (X[1:] != X[:-1]) | (Y[1:] != Y[:-1])
+    keep[st] = True
+    cnt = np.add.reduceat(keep.astype(np.int64), st)
+    # the last kept vertex of a loop equal to its first closes the loop twice
+    pos = np.flatnonzero(keep)
+    kst = np.zeros(n + 1, np.int64)
+    np.cumsum(cnt, out=kst[1:])
+    last = pos[kst[1:] - 1]
+    closing = (cnt > 1) & (X[last] == X[st]) & (Y[last] == Y[st])
+    keep[last[closing]] = False
+    cnt -= closing
+    bad = np.flatnonzero(cnt < 3)
+    lim = COORD_LIMIT - 1
+    ox = rng.integers(-(lim // 2), lim - box_w - lim // 2)
+    oy = rng.integers(-(lim // 2), lim - box_h - lim // 2)
+    for b in bad:  # degenerate outline (rare): its box instead
+        a = int(st[b])
+        keep[a:a + int(nv[b])] = False
+        keep[a:a + 4] = True
+        X[a:a + 4] = (0, box_w[b], box_w[b], 0)
+        Y[a:a + 4] = (0, 0, box_h[b], box_h[b])
+        cnt[b] = 4
+    X += ox[seg]
+    Y += oy[seg]
+    offs = np.zeros(n + 1, np.uint32)
+    verts = np.empty(2 * int(cnt.sum()), np.int32)
+    np.cumsum(cnt, out=offs[1:])
+    verts[0::2] = X[keep]
+    verts[1::2] = Y[keep]
+    return ChartSet(offs, verts, atlas, atlas, f"stars_fast[{n},{atlas}]")

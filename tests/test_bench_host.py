@@ -36,18 +36,27 @@ def test_wave_ranges(jtop, k_best, F):
 
 def test_algorithmic_bytes_closed_form():
     """Equal squares of side a texels: at candidate k each has w' = h' =
-    ceil(a k / 1024) + 2g, so the raster writes 12 w' B per chart (8 per
-    column word with its owner, 4 per row word) plus 24 B of offsets and
-    meta, and the compactor reads 4 h' B plus 25 B per chart."""
+    ceil(a k / 1024) + 2g, so the raster writes 4 (w' + h') B per chart (4 B
+    per padded scanline word) and the compactor reads 4 h' B plus 25 B per
+    chart."""
     a, n = 7, 5
     cs = synth.rectangles([(a, a)] * n, 64, 64)
     jtop, k_best, F = 63, 1024, 1
     got = bench.algorithmic_bytes([cs], [k_best], [jtop], F)
     wp = -(-a * 1024 // 1024) + 2
-    assert got["raster"] == 208 * n + n * (12 * wp + 24)
+    assert got["raster"] == n * 8 * wp
     assert got["hcompact"] == n * (4 * wp + 25)
 
 
 def test_raster_ops_per_word():
-    assert bench.raster_ops_per_word(1) == 77
-    assert bench.raster_ops_per_word(0) == 73 and bench.raster_ops_per_word(2) == 81
+    assert bench.raster_ops_per_word(1) == 120
+    assert bench.raster_ops_per_word(0) == 116 and bench.raster_ops_per_word(2) == 124
+
+
+def test_p99_crossing_rate():
+    """Linear in p99 over log(rate) between the bracketing rates."""
+    c = bench.crossing([(1000, 5.0), (2000, 10.0), (4000, 20.0), (8000, 40.0)])
+    assert c["between"] == [2000, 4000]
+    assert abs(c["rate"] - 2000 * 2 ** 0.5) < 0.1
+    assert bench.crossing([(1000, 16.0), (2000, 30.0)])["rate"] is None
+    assert bench.crossing([(1000, 1.0), (2000, 3.0)])["rate"] is None
