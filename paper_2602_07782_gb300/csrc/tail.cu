@@ -16,8 +16,13 @@
 //   tail_plan     the tail tasks of the wave;
 //   tail_trial    a warp per (task, row, trial scale): the row's extent at
 //                 that scale, its compacting distances drawn on the fly
-//                 (warp_pair_reach), against W';
-//   tail_pick     a thread per task: the largest trial scale every row fit;
+//                 (warp_pair_reach), against W' -- the trial scales in four
+//                 phases from the top (S .. S - 3, S - 4 .. S - 7, ...);
+//   tail_pick     a thread per task, after each phase: the largest scale of
+//                 the phase at which every row fit settles the task (every
+//                 larger scale has failed); a task none fit goes on to the
+//                 next phase, and after the last one to the row-by-row
+//                 fallback;
 //   tail_raster   a warp per (task, tail chart): its envelope at k';
 //   tail_compact  a group of 16 lanes per (task, tail pair): distances and
 //                 interlock flags at k'.
@@ -39,6 +44,12 @@ __device__ __forceinline__ int32_t *task_state(const Pack &p, int at, int j, int
 __device__ __forceinline__ int32_t trial_scale(int32_t lo, int32_t hi, int i) {
   return lo + (int32_t)(((int64_t)(i + 1) * (hi - lo)) / 16);
 }
+
+// The trial scales of phase ph: indices 14 - 4 ph down to 11 - 4 ph (and
+// not below 0).
+constexpr int kTailPhases = 4;
+constexpr int kPhaseScales = 4;
+__device__ __forceinline__ int phase_top(int ph) { return 14 - kPhaseScales * ph; }
 
 // Round r of the wave's tail: per atlas, the largest 2^r parked tasks (all
 // of them in the last round) that can still win -- a parked candidate below
@@ -94,53 +105,100 @@ __global__ void __launch_bounds__(1024) tail_plan_kernel(const Pack *__restrict_
   }
 }
 
-// Whether the tail row starting at sorted chart s0 (len charts) fits W' when
-// laid from its near end at scale k: Algorithm 4's recurrence x_{t+1} = x_t
-// + w'_t - d_t, with compaction never left of the right edge of chart t-1.
-// A warp walks the row; its 32 / G aligned groups of G lanes each draw one
-// pair's rows at k on the fly (group_pair_reach) per step, so a step
-// advances 32 / G charts.  a: the warp's 2 (32 / G) row-constant buffers.
+// The compacting offsets of a phase (Algorithm 4's x_{t+1} - x_t before the
+// clamp, w'_t - d_t = min(w'_t, reach)) of every tail pair (u, u + 1) in one
+// row, at the phase's four trial scales: a group of G lanes per (pair,
+// scale) draws the two charts' rows at that scale on the fly
+// (group_pair_reach).  They go to the tail charts' place records, whose x
+// and y are free until the push pass: four int16 (|offset| <= 8192), the
+// phase's scale i in slot phase_top - i.
+__device__ __forceinline__ int16_t *offset_slot(int4 *place, int u, int slot) {
+  return reinterpret_cast<int16_t *>(&place[u].x) + slot;
+}
+
 template <int G>
-__device__ bool row_fits(const Pack &p, int s0, int len, int64_t k, int Wp, rmath::AxisK *a,
-                         const volatile int32_t *mask, int bit) {
+__global__ void __launch_bounds__(kTailThreads) tail_offsets_kernel(const Pack *__restrict__ pp, int phase) {
   constexpr int PG = 32 / G;
-  const bool hc = (p.flags & TABI_F_HC) != 0;
-  const int g = p.g;
-  const int lane = threadIdx.x & 31, grp = lane / G, glane = lane & (G - 1);
+  __shared__ rmath::AxisK axk[kTailWarps][2 * PG];
+  const Pack &p = *pp;
+  if (!(p.flags & TABI_F_HC)) return;  // no compaction: the offsets are the widths
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, grp = lane / G, glane = lane & (G - 1);
   const unsigned gm = group_mask<G>();
-  int64_t x = 0, xprev = 0, wprev = 0, ext = 0;
-  for (int t = 0; t < len; t += PG) {
-    // another row has already failed at this scale: the outcome is known
-    if (__shfl_sync(0xffffffffu, lane == 0 ? (*mask >> bit) & 1 : 0, 0)) return true;
-    // pair (u, u + 1) of this group, its offset x_{u+1} - x_u before the clamp
-    const int u = s0 + t + grp;
-    const bool has = t + grp < len;
-    int64_t w = 0, o = 0;
-    if (has) {
-      w = ((p.wq[u] * k + kFix - 1) >> 18) + 2 * g;
-      o = w;
-    }
-    if (hc) {
-      const bool pair = t + grp + 1 < len;
+  const int g = p.g;
+  rmath::AxisK *a = axk[wib];
+  const int64_t gw = (int64_t)blockIdx.x * kTailWarps + wib, nw = (int64_t)gridDim.x * kTailWarps;
+  const int wave = *(volatile const int32_t *)p.cur_wave;
+  const int ntask = *p.tcount;
+  for (int ti = 0; ti < ntask; ++ti) {
+    const int4 tt = p.ttask[ti];
+    const int at = tt.x, j = tt.y, c0 = tt.w;
+    if (p.tstate[at * kScales + j] != kTaskTailSearch) continue;
+    const int32_t *cs = task_state(p, at, j, wave);
+    const int32_t lo = cs[kCsLo], hi = cs[kCsHi];
+    const AtlasDesc &ad = p.atl[at];
+    const int cb = ad.cb, n = ad.n;
+    int4 *place = p.place + (int64_t)j * p.N + cb;
+    // items (pair u, scale of the phase), the groups of a warp take PG
+    // consecutive ones
+    const int64_t items = (int64_t)(n - 1 - c0) * kPhaseScales;
+    for (int64_t base = gw * PG; base < items; base += nw * PG) {
+      const int64_t it = base + grp;
+      int u = 0, slot = 0;
+      int32_t k = 0;
+      bool pair = false;
+      if (it < items) {
+        u = c0 + (int)(it / kPhaseScales);
+        slot = (int)(it % kPhaseScales);
+        const int i = phase_top(phase) - slot;
+        if (i >= 0) {
+          k = trial_scale(lo, hi, i);
+          pair = k > lo && k < hi && !(place[u + 1].w & kTailFirst);
+        }
+      }
       if (pair) {
-        group_setup_rows<G>(p, p.shape[u], k, a[2 * grp], glane);
-        group_setup_rows<G>(p, p.shape[u + 1], k, a[2 * grp + 1], glane);
+        group_setup_rows<G>(p, p.shape[cb + u], k, a[2 * grp], glane);
+        group_setup_rows<G>(p, p.shape[cb + u + 1], k, a[2 * grp + 1], glane);
       }
       __syncwarp();
       if (pair) {
         const int32_t M = group_pair_reach<G>(a[2 * grp], a[2 * grp + 1], g, glane, gm);
-        o = w - M > 0 ? M : w;  // w - max(0, w - M)
+        const int32_t w = (int32_t)((p.wq[cb + u] * (int64_t)k + kFix - 1) >> 18) + 2 * g;
+        if (glane == 0) *offset_slot(place, u, slot) = (int16_t)(w - M > 0 ? M : w);
       }
       __syncwarp();  // the buffers are redrawn next step
     }
-    for (int q = 0; q < PG; ++q) {
-      const int64_t oq = __shfl_sync(0xffffffffu, o, q * G), wq = __shfl_sync(0xffffffffu, w, q * G);
-      const int tt = t + q;
-      if (tt >= len) break;
+  }
+}
+
+// Whether the tail row starting at sorted chart s0 (len charts) fits W' when
+// laid from its near end at scale k, the phase's slot `slot`: Algorithm 4's
+// recurrence x_{t+1} = x_t + o_t, with compaction never left of the right
+// edge of chart t-1, from the stored offsets; a warp loads 32 charts at a
+// time and walks them.
+__device__ bool row_fits(const Pack &p, const int4 *place, int cb, int s0, int len, int64_t k, int Wp, int slot,
+                         const volatile int32_t *mask, int bit) {
+  const bool hc = (p.flags & TABI_F_HC) != 0;
+  const int g = p.g;
+  const int lane = threadIdx.x & 31;
+  int64_t x = 0, xprev = 0, wprev = 0, ext = 0;
+  for (int t = 0; t < len; t += 32) {
+    // another row has already failed at this scale: the outcome is known
+    if (__shfl_sync(0xffffffffu, lane == 0 ? (*mask >> bit) & 1 : 0, 0)) return true;
+    const int u = s0 + t + lane;
+    int64_t w = 0, o = 0;
+    if (t + lane < len) {
+      w = ((p.wq[cb + u] * k + kFix - 1) >> 18) + 2 * g;
+      o = (hc && t + lane + 1 < len) ? (int64_t)*reinterpret_cast<const int16_t *>(
+                                           reinterpret_cast<const int16_t *>(&place[u].x) + slot)
+                                     : w;
+    }
+    const int cnt = min(32, len - t);
+    for (int q = 0; q < cnt; ++q) {
+      const int64_t oq = __shfl_sync(0xffffffffu, o, q), wq = __shfl_sync(0xffffffffu, w, q);
       ext = ext > x + wq ? ext : x + wq;
       if (ext > Wp) return false;
       int64_t nx = x + oq;
-      if (hc && tt >= 1 && nx < xprev + wprev) nx = xprev + wprev;
+      if (hc && t + q >= 1 && nx < xprev + wprev) nx = xprev + wprev;
       xprev = x;
       wprev = wq;
       x = nx;
@@ -149,9 +207,7 @@ __device__ bool row_fits(const Pack &p, int s0, int len, int64_t k, int Wp, rmat
   return true;
 }
 
-template <int G>
-__global__ void __launch_bounds__(kTailThreads) tail_trial_kernel(const Pack *__restrict__ pp) {
-  __shared__ rmath::AxisK axk[kTailWarps][2 * (32 / G)];
+__global__ void __launch_bounds__(kTailThreads) tail_trial_kernel(const Pack *__restrict__ pp, int phase) {
   const Pack &p = *pp;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int64_t gw = (int64_t)blockIdx.x * kTailWarps + wib, nw = (int64_t)gridDim.x * kTailWarps;
@@ -166,9 +222,10 @@ __global__ void __launch_bounds__(kTailThreads) tail_trial_kernel(const Pack *__
     const AtlasDesc &ad = p.atl[at];
     const int cb = ad.cb, n = ad.n, Wp = ad.W + 2 * p.g;
     const int4 *place = p.place + (int64_t)j * p.N + cb;
-    const int64_t items = (int64_t)(n - c0) * 15;
+    const int64_t items = (int64_t)(n - c0) * kPhaseScales;
     for (int64_t it = gw; it < items; it += nw) {
-      const int s = c0 + (int)(it / 15), i = (int)(it % 15);
+      const int s = c0 + (int)(it / kPhaseScales), slot = (int)(it % kPhaseScales), i = phase_top(phase) - slot;
+      if (i < 0) continue;
       const int32_t w = place[s].w;
       if (!(w & kTailFirst)) continue;  // rows are tried from their first chart
       const int32_t k = trial_scale(lo, hi, i);
@@ -177,17 +234,18 @@ __global__ void __launch_bounds__(kTailThreads) tail_trial_kernel(const Pack *__
       // skipped (the mask only gathers failures, so the outcome is the same)
       const volatile int32_t *mask = cs + kCsMask;
       if ((*mask >> i) & 1) continue;
-      if (!row_fits<G>(p, cb + s, w & ~kTailFirst, k, Wp, axk[wib], mask, i) && lane == 0)
+      if (!row_fits(p, place, cb, s, w & ~kTailFirst, k, Wp, slot, mask, i) && lane == 0)
         atomicOr((unsigned *)(cs + kCsMask), 1u << i);
     }
   }
 }
 
-// The outcome per task (a thread each): k' is the largest trial scale at
-// which every row fit (its bit in the mask is clear), 0 if none did; either
-// way the task goes on to the push pass.
-__global__ void tail_pick_kernel(const Pack *__restrict__ pp, int round) {
-  (void)round;
+// The outcome of a phase per task (a thread each): k' is the largest trial
+// scale of the phase at which every row fit (its bit in the mask is clear;
+// every scale of the earlier phases failed); a task without one stays in
+// the search for the next phase, or after the last takes k' = 0.  A
+// settled task goes on to the push pass.
+__global__ void tail_pick_kernel(const Pack *__restrict__ pp, int phase) {
   const Pack &p = *pp;
   const int wave = *(volatile const int32_t *)p.cur_wave;
   const int ntask = *p.tcount;
@@ -199,10 +257,11 @@ __global__ void tail_pick_kernel(const Pack *__restrict__ pp, int round) {
     const int32_t lo = cs[kCsLo], hi = cs[kCsHi];
     const uint32_t mask = (uint32_t)cs[kCsMask];
     int32_t best = 0;
-    for (int i = 0; i < 15; ++i) {
+    for (int i = max(0, phase_top(phase) - kPhaseScales + 1); i <= phase_top(phase); ++i) {
       const int32_t k = trial_scale(lo, hi, i);
       if (k > lo && k < hi && !((mask >> i) & 1u) && k > best) best = k;
     }
+    if (best == 0 && phase + 1 < kTailPhases) continue;  // the next phase's scales
     cs[kCsKt] = best;
     cs[kCsMask] = 0;
     p.tstate[at * kScales + j] = kTaskTailPush;
@@ -224,9 +283,12 @@ __global__ void __launch_bounds__(kTailThreads) tail_raster_kernel(const Pack *_
     const int at = tt.x, j = tt.y, c0 = tt.w;
     if (p.tstate[at * kScales + j] != kTaskTailPush) continue;
     const int32_t kt = task_state(p, at, j, wave)[kCsKt];
-    if (kt == 0) continue;  // no tail scale: the rows go on at S
     const AtlasDesc &ad = p.atl[at];
     const int cb = ad.cb, n = ad.n;
+    // the trial offsets leave the tail records' x and y as they were (zero)
+    int2 *xy = reinterpret_cast<int2 *>(p.place + (int64_t)j * p.N + cb);
+    for (int64_t s = c0 + gw * 32 + lane; s < n; s += nw * 32) xy[2 * s] = make_int2(0, 0);
+    if (kt == 0) continue;  // no tail scale: the rows go on at S
     const int64_t cbase = p.abase[region(at, j, 0)], rbase = p.abase[region(at, j, 1)];
     for (int64_t s = c0 + gw; s < n; s += nw) {
       const int64_t js = (int64_t)j * p.N + cb + s;
@@ -278,11 +340,14 @@ int tail_rounds(int F) {
 
 void launch_tail_round(const Pack *dp, const Launch &L, int F, int round, cudaStream_t st) {
   tail_plan_kernel<<<1, 1024, 0, st>>>(dp, round, tail_rounds(F));
-  // groups of 8 lanes per pair while the gutter dilation (2g) stays inside
-  // one chunk of 8 rows, else a warp per pair
-  if (L.gutter <= 3) tail_trial_kernel<8><<<L.sms * 4, kTailThreads, 0, st>>>(dp);
-  else tail_trial_kernel<32><<<L.sms * 4, kTailThreads, 0, st>>>(dp);
-  tail_pick_kernel<<<L.sms, 128, 0, st>>>(dp, 0);
+  for (int ph = 0; ph < kTailPhases; ++ph) {
+    // groups of 8 lanes per pair while the gutter dilation (2g) stays inside
+    // one chunk of 8 rows, else a warp per pair
+    if (L.gutter <= 3) tail_offsets_kernel<8><<<L.sms * 4, kTailThreads, 0, st>>>(dp, ph);
+    else tail_offsets_kernel<32><<<L.sms * 4, kTailThreads, 0, st>>>(dp, ph);
+    tail_trial_kernel<<<L.sms * 4, kTailThreads, 0, st>>>(dp, ph);
+    tail_pick_kernel<<<L.sms, 128, 0, st>>>(dp, ph);
+  }
   tail_raster_kernel<<<L.sms * 3, kTailThreads, 0, st>>>(dp);
   tail_compact_kernel<<<L.sms * 8, 256, 0, st>>>(dp);
 }

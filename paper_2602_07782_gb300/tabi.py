@@ -198,13 +198,14 @@ def kernels_per_pack(fanout: int, chunks: int = 4, waves_run: int | None = None,
     """Kernels one (batched) pack launches: init, prep, sort + gather,
     layout + bases; per wave, for each chart chunk plan + fill, raster,
     compaction, row loop, then (if some atlas may take the prefix-sum tail)
-    per tail round the tail's plan, trial scales, pick, redraw, compaction
-    and push pass, then the wave's end; selection.  The graph runs waves only
+    per tail round the tail's plan, four phases of trial offsets, trial
+    scales and pick, redraw, compaction and push pass, then the wave's end;
+    selection.  The graph runs waves only
     while some atlas still searches (`waves_run` of them: the most any
     atlas of the batch needs, at least one); direct launches (stage timing)
     run every wave."""
     w = waves(fanout) if waves_run is None else max(1, waves_run)
-    return 7 + (5 * chunks + 1 + (6 * tail_rounds(fanout) if tail else 0)) * w
+    return 7 + (5 * chunks + 1 + (16 * tail_rounds(fanout) if tail else 0)) * w
 
 
 def tail_rounds(fanout: int) -> int:
