@@ -121,7 +121,7 @@ __device__ __forceinline__ void row_begin(uint32_t *row, uint32_t *tog, int nwr,
 // the crossing rule are symmetric), x at the band's top line (nc + fc),
 // at its centre line (floor ny) and at its bottom line (nd + fd), where
 // those lines cross the edge's y-range.
-__device__ __forceinline__ void edge_in_band(int64_t x0, int64_t y0, int64_t x1, int64_t y1, int64_t c,
+__device__ __noinline__ void edge_in_band(int64_t x0, int64_t y0, int64_t x1, int64_t y1, int64_t c,
                                              int64_t nc, bool fc, int64_t ny, int64_t nd, bool fd, int32_t w,
                                              int32_t px, uint32_t *row, uint32_t *tog) {
   const int64_t d = c + kFix, cy = c + kFix / 2;
@@ -262,6 +262,7 @@ __device__ __forceinline__ void cover_row_dda(EdgeDDA (&ed)[2], int ne, int32_t 
 
 // Bits of the 32-column word starting at atlas column X0 that lie in [0, lim).
 __device__ __forceinline__ uint32_t valid_bits(int64_t X0, int64_t lim) {
+  if (X0 >= 0 && X0 + 32 <= lim) return ~0u;
   const int64_t lo = imax(0, -X0), hi = imin(32, lim - X0);
   if (lo >= hi) return 0u;
   const uint32_t up = hi >= 32 ? ~0u : ((1u << hi) - 1u);
@@ -375,11 +376,13 @@ __device__ __forceinline__ int64_t unit_chart(const int64_t *__restrict__ off, i
 // Units: (chart, block of kRowBlock dilated rows), balanced over the warps.
 // Shared memory per warp: the ring of 2g + 1 cover rows and one scratch
 // row, kRowWords words each.
-__global__ void __launch_bounds__(kCheckThreads, 1) check_mark_kernel(const CheckAtlas *__restrict__ atl,
-                                                                      const CheckChart *__restrict__ cc,
-                                                                      const int64_t *__restrict__ off, int64_t N,
-                                                                      int gmax, uint32_t *planes,
-                                                                      unsigned long long *counts) {
+// kDDA: the units of charts of at most 64 vertices (edges stepped down the
+// rows, two blocks per multiprocessor), else those of larger charts.
+template <bool kDDA>
+__global__ void __launch_bounds__(kCheckThreads, kDDA ? 2 : 1)
+    check_mark_kernel(const CheckAtlas *__restrict__ atl, const CheckChart *__restrict__ cc,
+                      const int64_t *__restrict__ off, int64_t N, int gmax, uint32_t *planes,
+                      unsigned long long *counts) {
   extern __shared__ uint32_t csm[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   uint32_t *ring = csm + (size_t)wib * (2 * gmax + 2) * kRowWords;
@@ -394,6 +397,7 @@ __global__ void __launch_bounds__(kCheckThreads, 1) check_mark_kernel(const Chec
     const int c = (int)(gc - ca.cb);
     const uint32_t o0 = ca.offsets[c];
     const int nv = (int)(ca.offsets[c + 1] - o0);
+    if ((nv <= 64) != kDDA) continue;  // the other kernel's unit
     const int32_t *v = ca.verts + 2 * (int64_t)o0;
     const tabi_placement pl = ca.place[c];
     PlacedXf xf;
@@ -412,10 +416,9 @@ __global__ void __launch_bounds__(kCheckThreads, 1) check_mark_kernel(const Chec
     // up to 64 vertices: each lane keeps its (at most two) edges and steps
     // them down the rows from the block's first cover row
     const int32_t J0 = -g + blk * kRowBlock, J1 = min(J0 + kRowBlock, h + g);
-    const bool dda = nv <= 64;
     EdgeDDA ed[2];
     int ne = 0;
-    if (dda) {
+    if (kDDA) {
       const int32_t Jstart = max(J0 - g, 0);
 #pragma unroll
       for (int s2 = 0; s2 < 2; ++s2) {
@@ -434,7 +437,7 @@ __global__ void __launch_bounds__(kCheckThreads, 1) check_mark_kernel(const Chec
       uint32_t *rw = ring + (size_t)ld * kRowWords;
       ld = ld + 1 == S ? 0 : ld + 1;
       if (J >= 0 && J < h) {
-        if (dda)
+        if (kDDA)
           cover_row_dda(ed, ne, J, w, px, nwr, rw, tog, lane);
         else
           cover_row(xf, v, nv, J, w, px, nwr, rw, tog, lane);
@@ -548,8 +551,9 @@ void launch_check(const CheckAtlas *datl, int A, const int32_t *catl, int64_t N,
                   int64_t words, void *scratch, unsigned long long *counts, int sms, cudaStream_t st) {
   static std::once_flag attr;
   std::call_once(attr, [] {  // the most the gutter limit needs
-    cudaFuncSetAttribute(check_mark_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)(sizeof(uint32_t) * kCheckWarps * (2 * kMaxGutter + 2) * kRowWords));
+    const int most = (int)(sizeof(uint32_t) * kCheckWarps * (2 * kMaxGutter + 2) * kRowWords);
+    cudaFuncSetAttribute(check_mark_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+    cudaFuncSetAttribute(check_mark_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
   });
   CheckChart *cc = reinterpret_cast<CheckChart *>(scratch);
   int64_t *off = reinterpret_cast<int64_t *>(reinterpret_cast<char *>(scratch) +
@@ -558,7 +562,8 @@ void launch_check(const CheckAtlas *datl, int A, const int32_t *catl, int64_t N,
   check_clear_kernel<<<sms * 4, 256, 0, st>>>(planes, words);
   check_size_kernel<<<sms * 4, kCheckThreads, 0, st>>>(datl, catl, N, gmax, cc, off);
   check_scan_kernel<<<1, 1024, 0, st>>>(off, N);
-  check_mark_kernel<<<sms, kCheckThreads, smem, st>>>(datl, cc, off, N, gmax, planes, counts);
+  check_mark_kernel<true><<<sms * 2, kCheckThreads, smem, st>>>(datl, cc, off, N, gmax, planes, counts);
+  check_mark_kernel<false><<<sms, kCheckThreads, smem, st>>>(datl, cc, off, N, gmax, planes, counts);
   check_count_kernel<<<sms * 4, kCheckThreads, 0, st>>>(datl, A, planes, counts);
 }
 

@@ -4,6 +4,8 @@ A fixed, small driver for profilers (ncu) and quick checks:
 
     python run_case.py stars2k --reps 2
     python run_case.py batch --atlases 16 --reps 2
+    python run_case.py pareto20k --reps 1 --check 3   # then the overlap counter
+
 
 Exits non-zero if a pack fails.  Builds the library first if needed.
 """
@@ -27,6 +29,8 @@ def main(argv=None) -> int:
     ap.add_argument("--direct", action="store_true",
                     help="launch the kernels directly (stage timing) instead of replaying the graph, whose "
                          "device-side wave loop profilers cannot enter")
+    ap.add_argument("--check", type=int, default=0,
+                    help="single-atlas cases: run the overlap and gutter counter this many times on the result")
     args = ap.parse_args(argv)
 
     import synth
@@ -57,6 +61,19 @@ def main(argv=None) -> int:
             return 1
         ks = [r.k for r in res]
     print(args.case, "atlases", len(sets), "k", ks[:8], "..." if len(ks) > 8 else "")
+    if args.check and len(sets) == 1:
+        import numpy as np
+        import torch
+        cs, dev = sets[0], torch.device("cuda:0")
+        offs = torch.from_numpy(cs.offsets.view(np.int32).copy()).to(dev)
+        verts = torch.from_numpy(cs.verts.copy()).to(dev)
+        place = torch.from_numpy(np.ascontiguousarray(res[0].place).view(np.uint8).copy()).to(dev)
+        for _ in range(args.check):
+            st, q = ctx.check_packing_device(cs.atlas_w, cs.atlas_h, params.gutter, cs.n, cs.nv, offs, verts, place)
+            if st != tabi.TABI_OK or q != (0, 0, 0):
+                print("check failed:", tabi.status_str(st), q, ctx.last_error())
+                return 1
+        print("overlap, gutter, outside texels:", q)
     ctx.close()
     return 0
 
