@@ -220,9 +220,10 @@ def cpu_baseline(sets, configs, budget_s: float):
 # DRAM read + write of every raster_kernel launch of one batch of this
 # workload (ncu, direct launches, the launch shape below), with a digest of
 # the kernel's sources at capture time; the bench reports it per launch
-# while the sources and the shape match, else null.  None: no capture of
-# the current sources.
-RASTER_NCU = None
+# while the sources and the shape match, else null.
+RASTER_NCU = {"dram_bytes_per_step": 2674673920, "sources_sha256_16": "826ad269563297c5",
+              "shape": {"scale_fanout": 2, "chunks": 4, "progressive_bound": 1},
+              "profile": "ncu capture of this workload's raster launches (profiles/raster_kernel_batch256.md)"}
 
 
 def raster_sources_digest() -> str:
