@@ -246,14 +246,15 @@ __device__ __forceinline__ void cover_row_dda(EdgeDDA (&ed)[2], int ne, int32_t 
   for (int s = 0; s < 2; ++s) {
     if (s >= ne) break;
     EdgeDDA &E = ed[s];
+    const bool meets = E.y1 > c && E.y0 < c + kFix;  // the edge meets the band
     if (E.dy > 0) {
       const int64_t nc = E.x0 + E.q;
       const bool fc = E.r != 0;
       E.step();
       const int64_t ny = E.x0 + E.q;
       E.step();
-      edge_in_band(E.x0, E.y0, E.x1, E.y1, c, nc, fc, ny, E.x0 + E.q, E.r != 0, w, px, row, tog);
-    } else {
+      if (meets) edge_in_band(E.x0, E.y0, E.x1, E.y1, c, nc, fc, ny, E.x0 + E.q, E.r != 0, w, px, row, tog);
+    } else if (meets) {
       edge_in_band(E.x0, E.y0, E.x1, E.y1, c, 0, false, 0, 0, false, w, px, row, tog);
     }
   }
@@ -469,13 +470,16 @@ __global__ void __launch_bounds__(kCheckThreads, kDDA ? 2 : 1)
         // (-g <= i < w + g) is padded texel (x + i + g, y + Jd + g), the
         // union of the cover rows Jd - g .. Jd + g (the whole ring), each
         // spread g columns either way -- here shifted by 0 .. 2g bits up
-        uint32_t dm = 0;
+        // (the spread of a union is the union of the spreads: the rows are
+        // joined first and spread once)
+        uint32_t cur = 0, prv = 0;
         for (int sl = 0; sl < S; ++sl) {
           const uint32_t *rw = ring + (size_t)sl * kRowWords;
-          const uint32_t cur = rw[t], prv = t > 0 ? rw[t - 1] : 0u;
-          dm |= cur;
-          for (int q = 1; q <= 2 * g; ++q) dm |= (cur << q) | (prv >> (32 - q));
+          cur |= rw[t];
+          prv |= t > 0 ? rw[t - 1] : 0u;
         }
+        uint32_t dm = cur;
+        for (int q = 1; q <= 2 * g; ++q) dm |= (cur << q) | (prv >> (32 - q));
         const int64_t Yd = Y + g;
         dm = (Yd >= 0 && Yd < ca.H + 2 * g) ? dm & valid_bits(X0, ca.W + 2 * g) : 0u;
         // both words' atomics in flight together; the bits already set go
