@@ -156,7 +156,7 @@ def host_info() -> dict:
             "machine": platform.machine()}
 
 
-def cpu_baseline(sets, configs, budget_s: float):
+def cpu_baseline(sets, singles, budget_s: float):
     """The CPU oracle as it stands: (a) single-threaded (descending candidates
     with the area-weighted stop), (b) with its candidates evaluated in waves
     of one per host core by a spawned process pool (oracle.parallel; the
@@ -169,7 +169,7 @@ def cpu_baseline(sets, configs, budget_s: float):
     info = host_info()
     P = int(info["nproc"] or 1)
     per = {}
-    for name, cs in configs:
+    for name, cs in singles:
         t0 = time.perf_counter()
         r = oracle.pack(cs)
         per[name] = {"charts": cs.n, "k": r.k, "single_ms": round(1e3 * (time.perf_counter() - t0), 3)}
@@ -194,8 +194,8 @@ def cpu_baseline(sets, configs, budget_s: float):
 
     n1, c1, t1, k1 = batch_leg(single)
     with parallel.pool(P) as ex:
-        parallel.pack_parallel(configs[0][1] if configs else sets[0], ex, P)  # start the workers
-        for name, cs in configs:
+        parallel.pack_parallel(singles[0][1] if singles else sets[0], ex, P)  # start the workers
+        for name, cs in singles:
             t0 = time.perf_counter()
             st, k, _, _ = parallel.pack_parallel(cs, ex, P)
             per[name]["multi_ms"] = round(1e3 * (time.perf_counter() - t0), 3)
@@ -317,7 +317,7 @@ def device_requests(tabi, torch, dev, sets):
     return keep, reqs
 
 
-def run_ours(args, rank, world, local, sets, configs):
+def run_ours(args, rank, world, local, sets, singles):
     import torch
 
     from paper_2602_07782_gb300 import tabi
@@ -405,7 +405,7 @@ def run_ours(args, rank, world, local, sets, configs):
         plain_ms.append(1e3 * (time.perf_counter() - t0))
         assert st == 0 and k == ks[i]
     plain_ms = np.array(plain_ms)
-    cfg_res = plain_configs(tabi, torch, ctx, dev, stream, flush, configs, args.warmup) if configs else None
+    cfg_res = plain_configs(tabi, torch, ctx, dev, stream, flush, singles, args.warmup) if singles else None
 
     # end to end through tabi_pack_batch: pinned host buffers, copies inside
     hold = []
@@ -529,13 +529,13 @@ def single_atlas_configs():
     return [("C1_plain64", synth.plain64()), ("C2_stars2k", synth.stars2k()), ("C3_pareto20k", synth.pareto20k())]
 
 
-def plain_configs(tabi, torch, ctx, dev, stream, flush, configs, warm, reps=10):
+def plain_configs(tabi, torch, ctx, dev, stream, flush, singles, warm, reps=10):
     """Each single-atlas workload through the plain packer: tabi_pack_device
     (inputs resident) and tabi_pack (host buffers, copies inside), L2 flushed
     before every call, wall clock around the stream-synchronous call."""
     params = tabi.params_default()
     out = {}
-    for name, cs in configs:
+    for name, cs in singles:
         keep, _ = device_requests(tabi, torch, dev, [cs])
         offs, verts, o = keep[0]
         dts, hts, ks = [], [], set()
@@ -857,19 +857,19 @@ def main():
             print(json.dumps(res))
         return
     sets = workload(args.atlases)  # spawned generator pool, before any CUDA work
-    configs = [] if args.no_configs or rank != 0 else single_atlas_configs()
+    singles = [] if args.no_configs or rank != 0 else single_atlas_configs()
     served_inputs = None if args.no_serve or rank != 0 else serve_workload(args)
     if world > 1:
         import torch
         torch.distributed.init_process_group("nccl")
     import __graft_entry__
     __graft_entry__.build()
-    res = run_ours(args, rank, world, local, sets, configs)
+    res = run_ours(args, rank, world, local, sets, singles)
     if served_inputs is not None:
         res["served"] = run_served(args, local, served_inputs)
     if rank == 0:
         if not args.no_cpu_baseline:
-            res["cpu_baseline"] = cpu_baseline(sets, configs, args.cpu_budget)
+            res["cpu_baseline"] = cpu_baseline(sets, singles, args.cpu_budget)
         print(json.dumps(res))
     if world > 1:
         import torch
