@@ -158,3 +158,38 @@ def test_shutdown_with_requests_queued_is_bounded():
     t0 = time.time()
     srv.close()
     assert time.time() - t0 < 60
+
+
+def test_served_stream_sample_matches_oracle():
+    """A sample of the benchmark's served stream -- its own request bodies
+    (stars_fast over serve_specs), every atlas side, chart counts up to the
+    prefix-sum tail's range -- through the server in the benchmark's
+    configuration (4 lanes over 8 GiB, fan-out 8, the overlap counter on),
+    all submitted at once so they share batches: each result is the
+    oracle's, and its overlap, gutter and outside counts are zero."""
+    specs = synth.serve_specs()
+    picked, seen = [], set()
+    for t, seed, n, side in specs:
+        cls = (side, n > 10000, n > 2000)
+        if cls not in seen and n <= 14000:
+            seen.add(cls)
+            picked.append(synth.stars_fast(seed, n, side))
+    assert any(cs.n > 10000 for cs in picked) and len({cs.atlas_w for cs in picked}) == 4
+    srv = tabi.Server(lanes=4, max_batch=64, arena_bytes=8 << 30,
+                      params=tabi.params_default(scale_fanout=8), check=1)
+    try:
+        subs = [srv.submit(cs) for cs in picked]
+        got = []
+        for st, t, out in subs:
+            assert st == tabi.TABI_OK
+            st, r = srv.wait(t, 120000)
+            assert st == tabi.TABI_OK and r.status == tabi.TABI_OK
+            assert (r.overlap_texels, r.gutter_texels, r.outside_texels) == (0, 0, 0)
+            got.append((r.scale_k, out.copy()))
+    finally:
+        srv.close()
+    ref = oracle.pack_many(picked)
+    for cs, (k, out), (st, ko, place) in zip(picked, got, ref):
+        assert st == 0 and k == ko, cs.name
+        assert np.array_equal(out["x"], place[:, 0]) and np.array_equal(out["y"], place[:, 1]), cs.name
+        assert np.array_equal(out["mirror"], place[:, 5]) and np.array_equal(out["k"], place[:, 10]), cs.name
