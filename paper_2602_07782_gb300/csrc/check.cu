@@ -31,9 +31,9 @@
 // bits either way).  Each word of a row goes to the plane with one
 // atomicOr; bits that were already set go to the "twice" plane.  A chart's
 // rows are disjoint across its warps and a word is written once per row,
-// so only two charts can set a bit twice.  The counts are the population
-// counts of the "twice" planes and the cover texels that fall outside the
-// atlas.
+// so only two charts can set a bit twice.  The counts are the bits each
+// "twice" plane gains (counted as they are first set) and the cover texels
+// that fall outside the atlas.
 #include <mutex>
 
 #include "context.h"
@@ -449,7 +449,7 @@ __global__ void __launch_bounds__(kCheckThreads, kDDA ? 2 : 1)
     };
     uint32_t *pocc = planes + ca.plane0, *ptwice = pocc + (int64_t)ca.wpp * ca.H;
     uint32_t *docc = ptwice + (int64_t)ca.wpp * ca.H, *dtwice = docc + (int64_t)ca.wpd * (ca.H + 2 * g);
-    unsigned long long outside = 0;
+    unsigned long long outside = 0, twice_p = 0, twice_d = 0;
     for (int32_t J = J0 - g; J < J0 + g; ++J) load_row(J);
     int mid = g;  // the ring slot of the dilated row's own cover row
     for (int32_t Jd = J0; Jd < J1; ++Jd) {
@@ -487,45 +487,29 @@ __global__ void __launch_bounds__(kCheckThreads, kDDA ? 2 : 1)
         const int64_t ip = Y * ca.wpp + (X0 >> 5), id = Yd * ca.wpd + (X0 >> 5);
         const uint32_t op = pm ? atomicOr(pocc + ip, pm) : 0u;
         const uint32_t od = dm ? atomicOr(docc + id, dm) : 0u;
-        if (op & pm) atomicOr(ptwice + ip, op & pm);
-        if (od & dm) atomicOr(dtwice + id, od & dm);
+        // a bit newly set in a "twice" plane is a texel counted once
+        if (op & pm) twice_p += __popc(op & pm & ~atomicOr(ptwice + ip, op & pm));
+        if (od & dm) twice_d += __popc(od & dm & ~atomicOr(dtwice + id, od & dm));
       }
       mid = mid + 1 == S ? 0 : mid + 1;
       __syncwarp();
     }
     outside = warp_sum_ull(outside);
-    if (lane == 0 && outside) atomicAdd(counts + 3 * a + 2, outside);
+    twice_p = warp_sum_ull(twice_p);
+    twice_d = warp_sum_ull(twice_d);
+    if (lane == 0) {
+      if (twice_p) atomicAdd(counts + 3 * a + 0, twice_p);
+      if (twice_d) atomicAdd(counts + 3 * a + 1, twice_d);
+      if (outside) atomicAdd(counts + 3 * a + 2, outside);
+    }
   }
 }
 
-constexpr int kCountParts = 32;  // blocks sharing one atlas's planes
-
-// Per atlas: population counts of the two "twice" planes (kCountParts
-// slices each, added up); ~0 for an atlas without planes.
-__global__ void __launch_bounds__(kCheckThreads) check_count_kernel(const CheckAtlas *__restrict__ atl, int A,
-                                                                    const uint32_t *planes,
-                                                                    unsigned long long *counts) {
-  for (int64_t it = blockIdx.x; it < (int64_t)A * kCountParts; it += gridDim.x) {
-    const int a = (int)(it / kCountParts), part = (int)(it % kCountParts);
-    const CheckAtlas &ca = atl[a];
-    if (ca.plane0 < 0) {
-      if (part == 0 && threadIdx.x == 0) counts[3 * a + 0] = counts[3 * a + 1] = counts[3 * a + 2] = ~0ull;
-      continue;
-    }
-    const int64_t np = (int64_t)ca.wpp * ca.H, nd = (int64_t)ca.wpd * (ca.H + 2 * ca.g);
-    const uint32_t *ptwice = planes + ca.plane0 + np, *dtwice = ptwice + np + nd;
-    unsigned long long s0 = 0, s1 = 0;
-    for (int64_t i = np * part / kCountParts + threadIdx.x; i < np * (part + 1) / kCountParts; i += blockDim.x)
-      s0 += __popc(ptwice[i]);
-    for (int64_t i = nd * part / kCountParts + threadIdx.x; i < nd * (part + 1) / kCountParts; i += blockDim.x)
-      s1 += __popc(dtwice[i]);
-    s0 = warp_sum_ull(s0);
-    s1 = warp_sum_ull(s1);
-    if ((threadIdx.x & 31) == 0) {
-      if (s0) atomicAdd(counts + 3 * a + 0, s0);
-      if (s1) atomicAdd(counts + 3 * a + 1, s1);
-    }
-  }
+// The counts of an atlas without planes: all ~0 (unchecked).  The others
+// were counted by the mark kernels as their "twice" bits were first set.
+__global__ void check_count_kernel(const CheckAtlas *__restrict__ atl, int A, unsigned long long *counts) {
+  for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < A; a += gridDim.x * blockDim.x)
+    if (atl[a].plane0 < 0) counts[3 * a + 0] = counts[3 * a + 1] = counts[3 * a + 2] = ~0ull;
 }
 
 }  // namespace
@@ -568,7 +552,7 @@ void launch_check(const CheckAtlas *datl, int A, const int32_t *catl, int64_t N,
   check_scan_kernel<<<1, 1024, 0, st>>>(off, N);
   check_mark_kernel<true><<<sms * 2, kCheckThreads, smem, st>>>(datl, cc, off, N, gmax, planes, counts);
   check_mark_kernel<false><<<sms, kCheckThreads, smem, st>>>(datl, cc, off, N, gmax, planes, counts);
-  check_count_kernel<<<sms * 4, kCheckThreads, 0, st>>>(datl, A, planes, counts);
+  check_count_kernel<<<(A + 255) / 256, 256, 0, st>>>(datl, A, counts);
 }
 
 }  // namespace tabi
