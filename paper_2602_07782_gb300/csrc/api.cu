@@ -126,7 +126,7 @@ void add_pieces(std::vector<CopyPiece> &v, const void *src, void *dst, uint64_t 
 // the envelope pools), with the host-input copies.
 size_t fixed_bytes(int64_t n, int64_t nv) {
   const size_t per_chart = 4 + sizeof(tabi_chart_info) + 2 * sizeof(ChartShape) + 3 * 4 + 16 + 40 +
-                           (size_t)kScales * (4 + 4 + 16 + 4 + 1 + 16) + 4 + 4 + sizeof(tabi_placement);
+                           (size_t)kScales * (4 + 4 + 16 + 4 + 1 + 16) + 4 + 4 + 16 + sizeof(tabi_placement);
   const size_t per_atlas = sizeof(AtlasDesc) + (size_t)kScales * 2 * 8 * 2 + sizeof(ScaleOut) * kScales +
                            8 + sizeof(PackResult) + 8 + 40 * 256 + (size_t)kScales * (kCtlSave * 4 + 16) + 8;
   const size_t pieces = pieces_of(4 * (uint64_t)(n + 1)) + pieces_of(8 * (uint64_t)nv) +
@@ -582,6 +582,7 @@ tabi_status batch_launch(tabi_ctx *ctx, const tabi_params *params, tabi_request 
   p.act_atl = cv.take<int32_t>(A);
   p.act_pre = cv.take<int32_t>(A);
   p.act_chart = cv.take<int32_t>(n);
+  p.act_ext = cv.take<int4>(n);
   p.counter = cv.take<int32_t>(kScales * kChunkSlots);
   p.rcounter = cv.take<uint32_t>(kScales * kChunkSlots);
   p.cur_wave = cv.take<int32_t>(1);

@@ -321,9 +321,13 @@ __global__ void __launch_bounds__(256) plan_fill_kernel(const Pack *__restrict__
   const int na = p.act_info[0];
   for (int i = blockIdx.x; i < na; i += gridDim.x) {
     const int at = p.act_atl[i], pre = p.act_pre[i];
-    const int n = p.atl[at].n, cb = p.atl[at].cb;
+    const int n = p.atl[at].n, cb = p.atl[at].cb, jt = p.jtop[at];
     const int c0 = q ? chunk_end(n, q - 1, p.Q) : 0, c1 = chunk_end(n, q, p.Q);
-    for (int t = threadIdx.x; t < c1 - c0; t += blockDim.x) p.act_chart[pre + t] = cb + c0 + t;
+    for (int t = threadIdx.x; t < c1 - c0; t += blockDim.x) {
+      const int c = c0 + t;
+      p.act_chart[pre + t] = cb + c;
+      p.act_ext[pre + t] = make_int4(cb + c, at, jt, (c == 0 ? 1 : 0) | (c == n - 1 ? 2 : 0));
+    }
   }
 }
 
@@ -339,7 +343,7 @@ __global__ void __launch_bounds__(256) plan_fill_kernel(const Pack *__restrict__
 // Items are the charts c of chunk q: the pair (c - 1, c) (both charts are
 // drawn by the end of the chunk), and the atlas's last chart's empty pair.
 template <int G>
-__global__ void __launch_bounds__(256, 8) hcompact_kernel(const Pack *__restrict__ pp, int q, int nj) {
+__global__ void __launch_bounds__(256, 6) hcompact_kernel(const Pack *__restrict__ pp, int q, int nj) {
   const Pack &p = *pp;
   const int wave = *(volatile const int32_t *)p.cur_wave;
   const int lane = threadIdx.x & (G - 1);
@@ -349,21 +353,26 @@ __global__ void __launch_bounds__(256, 8) hcompact_kernel(const Pack *__restrict
   const int64_t ngroups = ((int64_t)gridDim.x * blockDim.x) / G;
   const int64_t N = p.N;
   const bool all = q == 0 || (p.flags & TABI_F_EVAL_ALL);
+  // the chain of dependent loads per item is kept short: the chart, its
+  // atlas and top candidate in one record; the pair's sizes and row
+  // starts issued together with the candidate's state
   for (int64_t it = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G; it < items; it += ngroups) {
-    const int c = p.act_chart[it % total];
-    const int at = p.catl[c];
-    const WaveRange wr = wave_range(p.jtop[at], wave, nj);
+    const int4 e = p.act_ext[it % total];
+    const int c = e.x, at = e.y;
+    const WaveRange wr = wave_range(e.z, wave, nj);
     const int j = wr.hi - (int)(it / total);
     if (j < wr.lo) continue;  // this atlas has fewer candidates left than the wave
+    const bool first = (e.w & 1) != 0;
+    PairRows pr{};
+    if (!first) pr = pair_rows(p, at, j, c - 1);
     if (!all && (p.tstate[at * kScales + j] || *(volatile int32_t *)(p.found + at) > j))
       continue;  // the candidate has finished, or a larger one has succeeded
-    const int cb = p.atl[at].cb;
-    if (c == cb + p.atl[at].n - 1 && lane == 0) {  // no right neighbour
+    if ((e.w & 2) && lane == 0) {  // no right neighbour
       p.dnext[(int64_t)j * N + c] = 0;
       p.pflags[(int64_t)j * N + c] = 0;
     }
-    if (c == cb) continue;
-    compact_pair<G>(p, at, j, c - 1, lane, gm);
+    if (first) continue;
+    compact_rows<G>(p, pr, lane, gm);
   }
 }
 
@@ -406,9 +415,9 @@ void launch_raster(const Pack *dp, const Launch &L, int q, int F, cudaStream_t s
 
 constexpr int kHcGroup = 16;
 void launch_hcompact(const Pack *dp, const Launch &L, int q, int F, cudaStream_t st) {
-  // persistent: eight 256-thread CTAs per multiprocessor (full occupancy for a
-  // kernel that waits on its loads)
-  hcompact_kernel<kHcGroup><<<L.sms * 8, 256, 0, st>>>(dp, q, F);
+  // persistent: six 256-thread CTAs per multiprocessor (40 registers with
+  // the loads hoisted; eight CTAs at 32 registers spill)
+  hcompact_kernel<kHcGroup><<<L.sms * 6, 256, 0, st>>>(dp, q, F);
 }
 
 void launch_wave_end(const Pack *dp, cudaGraphConditionalHandle h, bool in_graph, cudaStream_t st) {

@@ -63,15 +63,31 @@ __device__ __forceinline__ int32_t group_scan_incl(int32_t v, unsigned gm) {
 // move up relative to A iff every row of B stays right of all rows of A
 // above it; A may move up relative to B iff every row of A stays left of
 // all rows of B above it.
-template <int G>
-__device__ __forceinline__ void compact_pair(const Pack &p, int at, int j, int s, int lane, unsigned gm) {
-  const int64_t N = p.N;
-  const int64_t ps = (int64_t)j * N + s;
-  const int32_t *ma = p.meta + ps * 4, *mb = ma + 4;
-  const int32_t wA = ma[0], hA = ma[1], hB = mb[1];
+// The pair's sizes and rows (loads only, so a caller can issue them before
+// it knows whether it needs them).
+struct PairRows {
+  int64_t ps;
+  int32_t wA, hA, hB;
+  const uint32_t *rowA, *rowB;
+};
+__device__ __forceinline__ PairRows pair_rows(const Pack &p, int at, int j, int s) {
+  PairRows r;
+  r.ps = (int64_t)j * p.N + s;
+  const int32_t *ma = p.meta + r.ps * 4, *mb = ma + 4;
+  r.wA = ma[0];
+  r.hA = ma[1];
+  r.hB = mb[1];
   const uint32_t *pool = p.pool + p.abase[region(at, j, 1)];
-  const uint32_t *rowA = pool + p.rowstart[ps];
-  const uint32_t *rowB = pool + p.rowstart[ps + 1];
+  r.rowA = pool + p.rowstart[r.ps];
+  r.rowB = pool + p.rowstart[r.ps + 1];
+  return r;
+}
+
+template <int G>
+__device__ __forceinline__ void compact_rows(const Pack &p, const PairRows &pr, int lane, unsigned gm) {
+  const int64_t ps = pr.ps;
+  const int32_t wA = pr.wA, hA = pr.hA, hB = pr.hB;
+  const uint32_t *rowA = pr.rowA, *rowB = pr.rowB;
   const int hmin = hA < hB ? hA : hB;
   int32_t M = -kBig;
   for (int r = lane; r < hmin; r += G) {
@@ -108,6 +124,11 @@ __device__ __forceinline__ void compact_pair(const Pack &p, int at, int j, int s
     p.dnext[ps] = d;
     p.pflags[ps] = (uint8_t)((a_free ? 0 : 1) | (b_free ? 0 : 2));
   }
+}
+
+template <int G>
+__device__ __forceinline__ void compact_pair(const Pack &p, int at, int j, int s, int lane, unsigned gm) {
+  compact_rows<G>(p, pair_rows(p, at, j, s), lane, gm);
 }
 
 // The constants of one chart at any scale k (1 <= k <= 1024) for one or both
