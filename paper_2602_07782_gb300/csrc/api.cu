@@ -581,7 +581,6 @@ tabi_status batch_launch(tabi_ctx *ctx, const tabi_params *params, tabi_request 
   p.act_info = cv.take<int32_t>(2);
   p.act_atl = cv.take<int32_t>(A);
   p.act_pre = cv.take<int32_t>(A);
-  p.act_chart = cv.take<int32_t>(n);
   p.act_ext = cv.take<int4>(n);
   p.counter = cv.take<int32_t>(kScales * kChunkSlots);
   p.rcounter = cv.take<uint32_t>(kScales * kChunkSlots);

@@ -61,10 +61,10 @@ __global__ void __launch_bounds__(kRasterThreads, 3) raster_kernel(const Pack *_
     if (lane == 0) grab = atomicAdd(next_item, 1u);
     const uint32_t it = __shfl_sync(0xffffffffu, grab, 0);
     if (it >= items) break;
-    const int s = p.act_chart[it / (uint32_t)ngroups];
-    const int at = p.catl[s];
-    const int cb = p.atl[at].cb;
-    const WaveRange wr = wave_range(p.jtop[at], wave, nj);
+    const int4 e = p.act_ext[it / (uint32_t)ngroups];  // chart, atlas, top candidate, first chart
+    const int s = e.x, at = e.y;
+    const int cb = e.w & 0x7fffffff;
+    const WaveRange wr = wave_range(e.z, wave, nj);
     const int j0 = wr.lo + (int)(it % (uint32_t)ngroups) * G;
     const int j1 = min(j0 + G, wr.hi + 1);
     if (j0 >= j1) continue;  // this atlas has fewer candidates left than the wave
@@ -325,8 +325,7 @@ __global__ void __launch_bounds__(256) plan_fill_kernel(const Pack *__restrict__
     const int c0 = q ? chunk_end(n, q - 1, p.Q) : 0, c1 = chunk_end(n, q, p.Q);
     for (int t = threadIdx.x; t < c1 - c0; t += blockDim.x) {
       const int c = c0 + t;
-      p.act_chart[pre + t] = cb + c;
-      p.act_ext[pre + t] = make_int4(cb + c, at, jt, (c == 0 ? 1 : 0) | (c == n - 1 ? 2 : 0));
+      p.act_ext[pre + t] = make_int4(cb + c, at, jt, (int32_t)((uint32_t)cb | (c == n - 1 ? 1u << 31 : 0u)));
     }
   }
 }
@@ -362,12 +361,12 @@ __global__ void __launch_bounds__(256, 6) hcompact_kernel(const Pack *__restrict
     const WaveRange wr = wave_range(e.z, wave, nj);
     const int j = wr.hi - (int)(it / total);
     if (j < wr.lo) continue;  // this atlas has fewer candidates left than the wave
-    const bool first = (e.w & 1) != 0;
+    const bool first = c == (e.w & 0x7fffffff);
     PairRows pr{};
     if (!first) pr = pair_rows(p, at, j, c - 1);
     if (!all && (p.tstate[at * kScales + j] || *(volatile int32_t *)(p.found + at) > j))
       continue;  // the candidate has finished, or a larger one has succeeded
-    if ((e.w & 2) && lane == 0) {  // no right neighbour
+    if (e.w < 0 && lane == 0) {  // no right neighbour
       p.dnext[(int64_t)j * N + c] = 0;
       p.pflags[(int64_t)j * N + c] = 0;
     }

@@ -129,10 +129,9 @@ struct Pack {
   PackResult *result;           // [A]
   int32_t *act_info;            // [2]: atlases still searching, their charts
   int32_t *act_atl;             // [A] those atlases, in batch order
-  int32_t *act_pre;             // [A] their first position in act_chart
-  int32_t *act_chart;           // [N] their charts (global sorted index)
-  int4 *act_ext;                // [N] the same: chart, atlas, the atlas's top candidate, flags
-                                //     (1: the atlas's first chart, 2: its last)
+  int32_t *act_pre;             // [A] their first position in act_ext
+  int4 *act_ext;                // [N] their charts: chart (global sorted index), atlas, the
+                                //     atlas's top candidate, its first chart | 1 << 31 for its last
   int32_t *counter;             // [64][kChunkSlots] row-loop task counter of each (wave, chunk; tail push)
   uint32_t *rcounter;           // [64][kChunkSlots] raster warp-item counter of each (wave, chunk)
   int32_t *cur_wave;            // the wave the kernels work on (advanced by wave_end)
