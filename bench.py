@@ -221,7 +221,7 @@ def cpu_baseline(sets, singles, budget_s: float):
 # workload (ncu, direct launches, the launch shape below), with a digest of
 # the kernel's sources at capture time; the bench reports it per launch
 # while the sources and the shape match, else null.
-RASTER_NCU = {"dram_bytes_per_step": 2674673920, "sources_sha256_16": "826ad269563297c5",
+RASTER_NCU = {"dram_bytes_per_step": 2720220160, "sources_sha256_16": "43b3a91043a33beb",
               "shape": {"scale_fanout": 2, "chunks": 4, "progressive_bound": 1},
               "profile": "ncu capture of this workload's raster launches (profiles/raster_kernel_batch256.md)"}
 
