@@ -476,7 +476,7 @@ typedef struct tabi_quality {
 /* Count them for one atlas: DEVICE pointers offsets[n + 1], verts[2 nv]
  * (as for tabi_pack_device) and place[n] (input order, e.g. the output of
  * a pack); *out is host memory.  Uses the context's arena for its bit
- * planes (4 bits per padded texel) and 40 bytes per chart (TABI_ERR_OOM if
+ * planes (4 bits per padded texel) and 48 bytes per chart (TABI_ERR_OOM if
  * they do not fit) and so
  * ends the inspectability of the last pack (tabi_inspect returns
  * TABI_ERR_INVALID_ARG until the next one).  Synchronous on `stream`.

@@ -282,7 +282,9 @@ struct CheckChart {
 
 // Per chart (a warp each): its box at its placement's scale and its number
 // of blocks of kRowBlock dilated rows (0: not drawn -- its atlas has no
-// planes, fewer than three vertices, a scale outside 1..1024).
+// planes, fewer than three vertices, a scale outside 1..1024), counted in
+// nblk[0 .. N) for charts of at most 64 vertices and in nblk[N + 1 ..
+// 2N + 1) for larger ones (each mark kernel walks its own units).
 __global__ void __launch_bounds__(kCheckThreads) check_size_kernel(const CheckAtlas *__restrict__ atl,
                                                                    const int32_t *__restrict__ catl, int64_t N,
                                                                    int gmax, CheckChart *__restrict__ cc,
@@ -296,7 +298,7 @@ __global__ void __launch_bounds__(kCheckThreads) check_size_kernel(const CheckAt
     const uint32_t o0 = ca.offsets[c], o1 = ca.offsets[c + 1];
     const tabi_placement pl = ca.place[c];
     if (ca.plane0 < 0 || ca.g > gmax || o1 < o0 + 3 || pl.k < 1 || pl.k > 1024) {
-      if (lane == 0) nblk[gc] = 0;
+      if (lane == 0) nblk[gc] = nblk[N + 1 + gc] = 0;
       continue;
     }
     const int nv = (int)(o1 - o0);
@@ -318,14 +320,18 @@ __global__ void __launch_bounds__(kCheckThreads) check_size_kernel(const CheckAt
       r.h = (int32_t)(((int64_t)r.Hq * pl.k + kFix - 1) >> 18);
       r.a = a;
       cc[gc] = r;
-      nblk[gc] = r.w > kMaxAtlas ? 0 : (r.h + 2 * ca.g + kRowBlock - 1) / kRowBlock;
+      const int64_t b = r.w > kMaxAtlas ? 0 : (r.h + 2 * ca.g + kRowBlock - 1) / kRowBlock;
+      const bool small = o1 - o0 <= 64;
+      nblk[gc] = small ? b : 0;
+      nblk[N + 1 + gc] = small ? 0 : b;
     }
   }
 }
 
 // Exclusive prefix sum of v[0..N) in place, v[N] = the total (one block of
-// 1024 threads, each a contiguous run).
+// 1024 threads, each a contiguous run); block b scans the array at v + b (N + 1).
 __global__ void __launch_bounds__(1024) check_scan_kernel(int64_t *v, int64_t N) {
+  v += blockIdx.x * (N + 1);
   __shared__ int64_t wsum[32];
   const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
   const int64_t run = (N + 1023) / 1024, b = (int64_t)t * run, e = b + run < N ? b + run : N;
@@ -398,7 +404,6 @@ __global__ void __launch_bounds__(kCheckThreads, kDDA ? 2 : 1)
     const int c = (int)(gc - ca.cb);
     const uint32_t o0 = ca.offsets[c];
     const int nv = (int)(ca.offsets[c + 1] - o0);
-    if ((nv <= 64) != kDDA) continue;  // the other kernel's unit
     const int32_t *v = ca.verts + 2 * (int64_t)o0;
     const tabi_placement pl = ca.place[c];
     PlacedXf xf;
@@ -528,7 +533,7 @@ void fill_check_atlas(CheckAtlas &ca, int W, int H, int g) {
 }
 
 size_t check_scratch_bytes(int64_t N) {
-  return ((sizeof(CheckChart) * (size_t)N + 255) & ~(size_t)255) + ((8 * ((size_t)N + 1) + 255) & ~(size_t)255);
+  return ((sizeof(CheckChart) * (size_t)N + 255) & ~(size_t)255) + ((16 * ((size_t)N + 1) + 255) & ~(size_t)255);
 }
 
 // Clears the planes, sizes every chart, lays the (chart, row block) units
@@ -549,9 +554,9 @@ void launch_check(const CheckAtlas *datl, int A, const int32_t *catl, int64_t N,
   const size_t smem = sizeof(uint32_t) * kCheckWarps * (2 * (size_t)gmax + 2) * kRowWords;
   check_clear_kernel<<<sms * 4, 256, 0, st>>>(planes, words);
   check_size_kernel<<<sms * 4, kCheckThreads, 0, st>>>(datl, catl, N, gmax, cc, off);
-  check_scan_kernel<<<1, 1024, 0, st>>>(off, N);
+  check_scan_kernel<<<2, 1024, 0, st>>>(off, N);
   check_mark_kernel<true><<<sms * 2, kCheckThreads, smem, st>>>(datl, cc, off, N, gmax, planes, counts);
-  check_mark_kernel<false><<<sms, kCheckThreads, smem, st>>>(datl, cc, off, N, gmax, planes, counts);
+  check_mark_kernel<false><<<sms, kCheckThreads, smem, st>>>(datl, cc, off + N + 1, N, gmax, planes, counts);
   check_count_kernel<<<(A + 255) / 256, 256, 0, st>>>(datl, A, counts);
 }
 
